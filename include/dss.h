@@ -1,0 +1,175 @@
+/*
+ * dss.h -- C ABI of the GB300 dense-suspension time-step library (libdss.so).
+ *
+ * The library advances N rigid spheres in a sheared periodic box following
+ * Monti, Rathee, Shen & Rosti, "A fast and efficient tool to study the
+ * rheology of dense suspensions" (arXiv:2108.01013):
+ *   - fixed-radius near-neighbour search by counting sort into cells with the
+ *     symmetric half-stencil (Sec. II A, Fig. 5 and 6) and the per-particle
+ *     list capacity estimated from the shell around the largest particle
+ *     (Sec. II A, last paragraphs);
+ *   - pair forces: lubrication (Eq. 3, App. A Eq. A2-A7) and stick-and-slide
+ *     frictional contact with tangential-spring history (Eq. 4, 5);
+ *   - Stokes drag (Eq. A1) and the modified velocity-Verlet update (Eq. 15)
+ *     in the Lees-Edwards box (Eq. 16);
+ *   - bulk stress from stresslets (Eq. 8, 9).
+ *
+ * Conventions: flow along x, gradient along y, vorticity along z;
+ * U_inf = (gdot y, 0, 0), Omega_inf = (0, 0, -gdot/2).  Vector arrays are
+ * SoA with three planes: v[0*n + k], v[1*n + k], v[2*n + k].
+ *
+ * Pointers: every array argument may be host memory (pageable or pinned) or
+ * device memory of the handle's device; the library copies with
+ * cudaMemcpyDefault on the handle's stream.  The caller owns every buffer it
+ * passes; the library owns its internal state, cell, list, history and pair
+ * buffers, allocated in dss_create (and re-allocated when a pair-capacity
+ * overflow is recovered, see dss_step).
+ *
+ * Particle order: ids passed to dss_set_state must be a permutation of
+ * 0..n-1 (NULL means k -> k).  Every per-particle output is written in id
+ * order (entry id), whatever order the library keeps internally.
+ *
+ * Errors: every int-returning call returns DSS_OK (0) or a negative code;
+ * dss_strerror gives a message.  No call aborts, traps or waits without a
+ * bound on the device.  After DSS_ERR_CUDA the handle should be destroyed.
+ */
+#ifndef DSS_H_
+#define DSS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum dss_status {
+  DSS_OK = 0,
+  DSS_ERR_ARG = -1,        /* bad argument (NULL, size, range, ids not a permutation) */
+  DSS_ERR_BOX = -2,        /* box too small: < 3 cells per axis (4 along x) */
+  DSS_ERR_CAPACITY = -3,   /* a particle exceeded the list capacity M; step not committed */
+  DSS_ERR_NONFINITE = -4,  /* non-finite force or state; step not committed */
+  DSS_ERR_UNSTABLE = -5,   /* dt above the explicit stability estimate (dss_create, strict only) */
+  DSS_ERR_CUDA = -6,       /* CUDA runtime error */
+  DSS_ERR_TIMEOUT = -7,    /* a bounded device-side wait gave up */
+  DSS_ERR_STATE = -8,      /* call order (e.g. dss_step before dss_set_state) */
+  DSS_ERR_INTERNAL = -9    /* internal consistency check failed on the device */
+};
+
+enum dss_precision {
+  DSS_FP64 = 0,   /* everything in FP64 */
+  DSS_MIXED = 1   /* pair forces in FP32; positions, gaps, Lees-Edwards offset,
+                     tangential stretch and stress accumulation in FP64 */
+};
+
+typedef struct dss_params {
+  double kn, kt, gamma_n, mu;   /* Eq. 4-5: normal and tangential spring, dashpot, Coulomb */
+  double eta0, rho;             /* fluid viscosity; particle density (m = 4/3 pi rho a^3) */
+  double delta_lub, lub_eps;    /* lubrication range, regulariser eps of Eq. A6 */
+  double a0;                    /* reference radius (cutoff mode 1) */
+  int32_t lub_cutoff_mode;      /* 0: pair listed iff d* = 2d/(a_i+a_j) < delta_lub;
+                                   1: iff d < delta_lub*a0 (d = surface gap) */
+  int32_t precision;            /* enum dss_precision */
+  double shear_rate, dt;        /* gdot, time step */
+  double cell_size;             /* 0: smallest size >= largest interaction range */
+  int32_t capacity_M;           /* half-list capacity per particle; 0: Sec. II A estimate */
+  int32_t pair_capacity;        /* mean half-list pairs per particle to allocate for; 0: 16 */
+} dss_params;
+
+typedef struct dss_handle dss_handle;
+
+/* Counters of the last force evaluation (dss_get_counters). */
+typedef struct dss_counters {
+  int64_t steps_done;       /* committed time steps since dss_set_state */
+  int64_t nstep;            /* time = nstep * dt */
+  int64_t npairs;           /* listed half pairs */
+  int64_t ncontacts;        /* pairs with d < 0 */
+  int64_t max_row;          /* largest half-list row */
+  int64_t band_checks;      /* candidates decided by the exact FP64 predicate */
+  int32_t M, pad_;
+  int64_t ncell[3];
+} dss_counters;
+
+/* Half-list capacity M from the shell estimate of Sec. II A: the number of
+ * smallest spheres (radius a_min) whose volume fits in the shell of
+ * thickness 2*a0 around the largest sphere (radius a_max),
+ * ceil(((a_max + 2 a0)^3 - a_max^3) / a_min^3).  Host-only, needs no GPU.
+ * Returns -1 for non-positive radii. */
+int32_t dss_capacity_estimate(double a_min, double a_max, double a0);
+
+/* Creates a handle for n particles in the box (edges box[0..2]) on the
+ * current CUDA device, stream-ordered on cuda_stream (a cudaStream_t, NULL
+ * for the legacy default stream).  Validates the parameters and the cell
+ * grid (needs >= 4 cells along x and >= 3 along y and z; the cutoff must be
+ * below half of every edge).  The radius range used for the cell size and
+ * M is fixed by dss_set_state; dss_create only stores the parameters.
+ * On success *h receives the handle. */
+int dss_create(dss_handle **h, const dss_params *p, int64_t n, const double box[3],
+               void *cuda_stream);
+
+/* Loads the state: x (3n, inside [0, L) on every axis), radii a (n, > 0),
+ * ids (n, permutation of 0..n-1, or NULL), velocity u (3n, NULL: U_inf(x)),
+ * angular velocity w (3n, NULL: Omega_inf), accelerations alpha_lin,
+ * alpha_ang (3n each; when both are NULL they are computed by one force
+ * evaluation at the loaded state, with an empty contact history), and the
+ * step count nstep (time nstep*dt).  Clears the contact history.  Sizes the
+ * cell grid and the list capacity for the radii on the first call
+ * (DSS_ERR_BOX / DSS_ERR_CAPACITY when they do not fit). */
+int dss_set_state(dss_handle *h, const double *x, const double *a, const int32_t *ids,
+                  const double *u, const double *w, const double *alpha_lin,
+                  const double *alpha_ang, int64_t nstep);
+
+/* Copies the current state out in id order; any pointer may be NULL. */
+int dss_get_state(dss_handle *h, double *x, double *u, double *w, double *alpha_lin,
+                  double *alpha_ang);
+
+/* Replaces the contact history: k entries with keys (lo_id << 32 | hi_id)
+ * and tangential stretch xi (3 per entry, row-major [k][3], orientation
+ * lo -> hi).  Used to resume from a checkpoint. */
+int dss_set_history(dss_handle *h, int64_t k, const int64_t *keys, const double *xi);
+
+/* Copies the committed contact history out, sorted by key.  Writes up to
+ * cap entries; *count receives the number of entries. */
+int dss_get_history(dss_handle *h, int64_t *keys, double *xi, int64_t cap, int64_t *count);
+
+/* Counting sort and half-stencil enumeration at the current state (no time
+ * advance).  The pairs can then be read with dss_get_pairs. */
+int dss_neighbour_build(dss_handle *h);
+
+/* Pairs of the last neighbour build / force evaluation as (lo id, hi id),
+ * row-major [count][2], sorted lexicographically.  Writes up to cap pairs;
+ * *count receives the total.  Synchronises the stream. */
+int dss_get_pairs(dss_handle *h, int64_t *lohi, int64_t cap, int64_t *count);
+
+/* One force evaluation at the current state with the committed history,
+ * without advancing or committing: total force F and torque T on every
+ * particle (pairs + Stokes drag), in id order; either may be NULL.  Also
+ * sets the stress read by dss_stress. */
+int dss_force_eval(dss_handle *h, double *F, double *T);
+
+/* Advances nsteps time steps (Eq. 15, 16): predictor and wrap, counting
+ * sort, half-stencil enumeration, history carry, pair forces, symmetric
+ * deterministic accumulation, drag, corrector, stress.  Steps run as CUDA
+ * graph replays; the host synchronises once at the end.  When a step fails
+ * (capacity, non-finite, timeout) it is not committed, later steps do
+ * nothing, and the state stays at the last committed step; a pair-capacity
+ * overflow is recovered by growing the pair buffers and resuming. */
+int dss_step(dss_handle *h, int64_t nsteps);
+
+/* Bulk stress of the last force evaluation (Eq. 8), row-major 3x3, host
+ * memory.  Synchronises the stream. */
+int dss_stress(dss_handle *h, double sigma[9]);
+
+/* Counters of the last force evaluation (synchronises). */
+int dss_get_counters(dss_handle *h, dss_counters *c);
+
+/* Bytes of device memory the handle holds. */
+int64_t dss_device_bytes(const dss_handle *h);
+
+void dss_destroy(dss_handle *h);
+const char *dss_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DSS_H_ */

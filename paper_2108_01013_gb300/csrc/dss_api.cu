@@ -1,0 +1,715 @@
+// Host side of the C ABI declared in include/dss.h: validation, buffer
+// management, the per-step launch sequence and its CUDA-graph capture.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "dss_internal.cuh"
+
+namespace {
+
+#define CK(x)                                   \
+  do {                                          \
+    cudaError_t e_ = (x);                       \
+    if (e_ != cudaSuccess) return DSS_ERR_CUDA; \
+  } while (0)
+
+template <typename T>
+int dalloc(dss_handle* h, T** p, size_t count) {
+  size_t b = sizeof(T) * (count > 0 ? count : 1);
+  if (cudaMalloc((void**)p, b) != cudaSuccess) return DSS_ERR_CUDA;
+  h->bytes += (int64_t)b;
+  return DSS_OK;
+}
+
+void dfree(void* p) {
+  if (p) cudaFree(p);
+}
+
+void free_buffers(dss_handle* h) {
+  for (int b = 0; b < 2; ++b) {
+    StateBuf& s = h->st[b];
+    dfree(s.x); dfree(s.u); dfree(s.w); dfree(s.al); dfree(s.aw); dfree(s.a); dfree(s.id);
+    memset(&s, 0, sizeof(s));
+    ListBuf& L = h->lb[b];
+    dfree(L.count); dfree(L.list); dfree(L.start); dfree(L.xi); dfree(L.cflag); dfree(L.slot_of_id);
+    dfree(L.id_of_slot);
+    memset(&L, 0, sizeof(L));
+  }
+  dfree(h->posf); dfree(h->cellid); dfree(h->perm); dfree(h->key); dfree(h->offs);
+  dfree(h->cell_count); dfree(h->cell_start); dfree(h->tmp); dfree(h->rec); dfree(h->spart);
+  dfree(h->io3); dfree(h->io3b); dfree(h->io_id); dfree(h->scan_status); dfree(h->scan_ticket);
+  dfree(h->sigma);
+  h->sigma = nullptr;
+  h->posf = nullptr; h->cellid = nullptr; h->perm = nullptr; h->key = nullptr; h->offs = nullptr;
+  h->cell_count = nullptr; h->cell_start = nullptr; h->tmp = nullptr; h->rec = nullptr;
+  h->spart = nullptr; h->io3 = nullptr; h->io3b = nullptr; h->io_id = nullptr; h->scan_status = nullptr;
+  h->scan_ticket = nullptr;
+  h->bytes = 0;
+  h->sized = false;
+}
+
+void drop_graphs(dss_handle* h) {
+  for (int k = 0; k < 4; ++k) {
+    if (h->graph_ok[k]) cudaGraphExecDestroy(h->step_graph[k]);
+    h->graph_ok[k] = false;
+  }
+}
+
+// Pair-capacity dependent buffers: per-pair records, stretch, contact flags,
+// stress partials.  keep_hist copies the committed history's pair arrays.
+int alloc_pair_buffers(dss_handle* h, int64_t pcap, bool keep_hist) {
+  const int64_t old = h->pcap;
+  double* rec = nullptr;
+  int r = dalloc(h, &rec, 9 * (size_t)pcap);
+  if (r) return r;
+  dfree(h->rec);
+  h->rec = rec;
+  for (int b = 0; b < 2; ++b) {
+    ListBuf& L = h->lb[b];
+    double* xi = nullptr;
+    unsigned char* cf = nullptr;
+    if ((r = dalloc(h, &xi, 3 * (size_t)pcap))) return r;
+    if ((r = dalloc(h, &cf, (size_t)pcap))) return r;
+    if (keep_hist && b == h->hist && L.xi && old > 0) {
+      for (int c = 0; c < 3; ++c)
+        CK(cudaMemcpyAsync(xi + c * pcap, L.xi + c * old, sizeof(double) * old,
+                           cudaMemcpyDeviceToDevice, h->stream));
+      CK(cudaMemcpyAsync(cf, L.cflag, old, cudaMemcpyDeviceToDevice, h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+    }
+    dfree(L.xi);
+    dfree(L.cflag);
+    L.xi = xi;
+    L.cflag = cf;
+  }
+  h->pcap = pcap;
+  h->g.pcap = pcap;
+  double* sp = nullptr;
+  const int pb = pair_grid_blocks(h);
+  if ((r = dalloc(h, &sp, 9 * (size_t)pb))) return r;
+  dfree(h->spart);
+  h->spart = sp;
+  h->spart_blocks = pb;
+  drop_graphs(h);
+  return DSS_OK;
+}
+
+int alloc_buffers(dss_handle* h) {
+  const size_t n = (size_t)h->n;
+  int r;
+  for (int b = 0; b < 2; ++b) {
+    StateBuf& s = h->st[b];
+    if ((r = dalloc(h, &s.x, 3 * n)) || (r = dalloc(h, &s.u, 3 * n)) || (r = dalloc(h, &s.w, 3 * n)) ||
+        (r = dalloc(h, &s.al, 3 * n)) || (r = dalloc(h, &s.aw, 3 * n)) || (r = dalloc(h, &s.a, n)) ||
+        (r = dalloc(h, &s.id, n)))
+      return r;
+    ListBuf& L = h->lb[b];
+    if ((r = dalloc(h, &L.count, n)) || (r = dalloc(h, &L.list, n * (size_t)h->g.M)) ||
+        (r = dalloc(h, &L.start, n + 1)) || (r = dalloc(h, &L.slot_of_id, n)) ||
+        (r = dalloc(h, &L.id_of_slot, n)))
+      return r;
+  }
+  if ((r = dalloc(h, &h->posf, n)) || (r = dalloc(h, &h->cellid, n)) || (r = dalloc(h, &h->perm, n)) ||
+      (r = dalloc(h, &h->key, n)) || (r = dalloc(h, &h->offs, n)) ||
+      (r = dalloc(h, &h->cell_count, (size_t)h->g.ncell)) ||
+      (r = dalloc(h, &h->cell_start, (size_t)h->g.ncell + 1)) || (r = dalloc(h, &h->tmp, n)) ||
+      (r = dalloc(h, &h->io3, 3 * n)) || (r = dalloc(h, &h->io3b, 3 * n)) ||
+      (r = dalloc(h, &h->io_id, n)) || (r = dalloc(h, &h->sigma, 9)))
+    return r;
+  CK(cudaMemsetAsync(h->sigma, 0, 9 * sizeof(double), h->stream));
+  int tiles = std::max(scan_tiles_for(h->g.ncell), scan_tiles_for((int)n));
+  h->scan_tiles_max = std::max(tiles, 1);
+  if ((r = dalloc(h, &h->scan_status, 2 * (size_t)h->scan_tiles_max)) ||
+      (r = dalloc(h, &h->scan_ticket, 2)))
+    return r;
+  CK(cudaMemsetAsync(h->cell_count, 0, sizeof(int) * h->g.ncell, h->stream));
+  h->pcap = 0;
+  int per = h->p.pair_capacity > 0 ? h->p.pair_capacity : 16;
+  if ((r = alloc_pair_buffers(h, std::max<int64_t>((int64_t)n * per, 1024), false))) return r;
+  h->sized = true;
+  return DSS_OK;
+}
+
+// Orders the library's stream after everything queued on the caller's stream.
+int enter(dss_handle* h) {
+  CK(cudaEventRecord(h->ev_enter, h->user_stream));
+  CK(cudaStreamWaitEvent(h->stream, h->ev_enter, 0));
+  return DSS_OK;
+}
+
+#define ENTER(h)            \
+  do {                      \
+    int e__ = enter(h);     \
+    if (e__) return e__;    \
+  } while (0)
+
+int sync_status(dss_handle* h) {
+  CK(cudaMemcpyAsync(h->status_host, h->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return DSS_OK;
+}
+
+int clear_err(dss_handle* h) {
+  CK(cudaMemsetAsync(&h->status->w[ST_ERR], 0, sizeof(int), h->stream));
+  return DSS_OK;
+}
+
+__global__ void k_scatter_by_id(int n, const double* __restrict__ src, const int* __restrict__ id,
+                                double* __restrict__ dst) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int k = id[i];
+  dst[k] = src[i];
+  dst[n + k] = src[n + i];
+  dst[2 * n + k] = src[2 * n + i];
+}
+
+__global__ void k_set_nstep(DevStatus* st, long long nstep) {
+  st->w[ST_NSTEP_LO] = (int)(unsigned)(nstep & 0xffffffffll);
+  st->w[ST_NSTEP_HI] = (int)(nstep >> 32);
+  st->w[ST_STEPS] = 0;
+  st->w[ST_ERR] = 0;
+}
+
+__global__ void k_iota(int n, int* __restrict__ v) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[i] = i;
+}
+
+__global__ void k_default_vel(int n, const double* __restrict__ x, double gdot, double* __restrict__ u,
+                              double* __restrict__ w, bool du, bool dw) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (du) { u[i] = gdot * x[n + i]; u[n + i] = 0.0; u[2 * n + i] = 0.0; }
+  if (dw) { w[i] = 0.0; w[n + i] = 0.0; w[2 * n + i] = -0.5 * gdot; }
+}
+
+// Attach the stretch of a given history (sorted keys) to a freshly built list.
+__global__ void k_attach_history(Geo g, StateBuf s, ListBuf L, const long long* __restrict__ keys,
+                                 const double* __restrict__ xi, int k) {
+  const int n = g.n;
+  const int P = L.start[n];
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+      int mid = (lo + hi) >> 1;
+      if (L.start[mid] <= p) lo = mid; else hi = mid;
+    }
+    const int j = L.list[(int64_t)lo * g.M + (p - L.start[lo])];
+    const long long a = s.id[lo], b = s.id[j];
+    const long long key = a < b ? (a << 32) | b : (b << 32) | a;
+    int l = 0, r = k - 1, f = -1;
+    while (l <= r) {
+      int m = (l + r) >> 1;
+      if (keys[m] == key) { f = m; break; }
+      if (keys[m] < key) l = m + 1; else r = m - 1;
+    }
+    if (f >= 0) {
+      L.xi[p] = xi[3 * (int64_t)f];
+      L.xi[g.pcap + p] = xi[3 * (int64_t)f + 1];
+      L.xi[2 * g.pcap + p] = xi[3 * (int64_t)f + 2];
+      L.cflag[p] = 1;
+    } else {
+      L.xi[p] = 0.0; L.xi[g.pcap + p] = 0.0; L.xi[2 * g.pcap + p] = 0.0;
+      L.cflag[p] = 0;
+    }
+  }
+}
+
+__global__ void k_history_out(Geo g, ListBuf L, long long* __restrict__ keys,
+                              double* __restrict__ xi, int* __restrict__ counter, int cap) {
+  const int n = g.n;
+  const int P = L.start[n];
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
+    if (!L.cflag[p]) continue;
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+      int mid = (lo + hi) >> 1;
+      if (L.start[mid] <= p) lo = mid; else hi = mid;
+    }
+    const int j = L.list[(int64_t)lo * g.M + (p - L.start[lo])];
+    const long long a = L.id_of_slot[lo], b = L.id_of_slot[j];
+    int q = atomicAdd(counter, 1);
+    if (q < cap) {
+      keys[q] = a < b ? (a << 32) | b : (b << 32) | a;
+      xi[3 * (int64_t)q] = L.xi[p];
+      xi[3 * (int64_t)q + 1] = L.xi[g.pcap + p];
+      xi[3 * (int64_t)q + 2] = L.xi[2 * g.pcap + p];
+    }
+  }
+}
+
+// The operation sequences.  stbuf/list indices follow the handle's
+// committed (cur, hist) pair; "w" is the scratch side.
+void seq_sort_enum(dss_handle* h, bool predict, int adv) {
+  const int w = 1 - h->cur;
+  launch_sort(h, predict, h->cur, w);
+  launch_enumerate(h, w, 1 - h->hist, adv);
+}
+
+void seq_step(dss_handle* h) {
+  const int w = 1 - h->cur;
+  seq_sort_enum(h, true, 1);
+  launch_forces(h, w, 1 - h->hist, h->hist, 1, G_STEP, nullptr, nullptr);
+}
+
+int capture_step(dss_handle* h, int key) {
+  cudaGraph_t graph;
+  CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  seq_step(h);
+  cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+  if (e != cudaSuccess) return DSS_ERR_CUDA;
+  e = cudaGraphInstantiate(&h->step_graph[key], graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return DSS_ERR_CUDA;
+  h->graph_ok[key] = true;
+  return DSS_OK;
+}
+
+int status_error(dss_handle* h) {
+  int e = h->status_host->w[ST_ERR];
+  return e ? e : DSS_OK;
+}
+
+int geometry(dss_handle* h) {
+  Geo& g = h->g;
+  const dss_params& p = h->p;
+  double dmax = p.lub_cutoff_mode == 1 ? p.delta_lub * p.a0 : p.delta_lub * h->a_max;
+  double range = 2.0 * h->a_max + dmax;
+  double cmin = range * (1.0 + 1e-9) + 1e-12;
+  if (p.cell_size > 0.0) {
+    if (p.cell_size < cmin) return DSS_ERR_ARG;
+    cmin = p.cell_size;
+  }
+  for (int d = 0; d < 3; ++d) {
+    g.L[d] = h->L[d];
+    g.halfL[d] = 0.5 * h->L[d];
+    g.nc[d] = (int)std::floor(h->L[d] / cmin);
+    if (g.nc[d] < 1) g.nc[d] = 1;
+    g.cs[d] = h->L[d] / g.nc[d];
+    g.inv_cs[d] = 1.0 / g.cs[d];
+    g.halfLf[d] = (float)(0.5 * h->L[d]) * (1.0f - 1e-5f);
+  }
+  if (g.nc[0] < 4 || g.nc[1] < 3 || g.nc[2] < 3) return DSS_ERR_BOX;
+  if ((double)g.nc[0] * g.nc[1] * g.nc[2] > 2.0e9) return DSS_ERR_ARG;
+  g.ncell = g.nc[0] * g.nc[1] * g.nc[2];
+  double csmax = std::max(g.cs[0], std::max(g.cs[1], g.cs[2]));
+  g.r2_margin = (float)(1e-4 * csmax * csmax);
+  int M = p.capacity_M > 0 ? p.capacity_M : dss_capacity_estimate(h->a_min, h->a_max, p.a0);
+  if (M <= 0) return DSS_ERR_ARG;
+  g.M = M;
+  return DSS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t dss_capacity_estimate(double a_min, double a_max, double a0) {
+  if (!(a_min > 0.0) || !(a_max >= a_min) || !(a0 > 0.0)) return -1;
+  double outer = a_max + 2.0 * a0;
+  double shell = outer * outer * outer - a_max * a_max * a_max;
+  double v = shell / (a_min * a_min * a_min);
+  double c = std::ceil(v - 1e-9 * v);
+  if (c < 1.0) c = 1.0;
+  if (c > 1e8) return -1;
+  return (int32_t)c;
+}
+
+const char* dss_strerror(int code) {
+  switch (code) {
+    case DSS_OK: return "ok";
+    case DSS_ERR_ARG: return "invalid argument";
+    case DSS_ERR_BOX: return "box too small for the cell grid (need >= 4 cells along x, >= 3 along y, z)";
+    case DSS_ERR_CAPACITY: return "neighbour-list capacity exceeded";
+    case DSS_ERR_NONFINITE: return "non-finite force or state";
+    case DSS_ERR_UNSTABLE: return "time step above the stability estimate";
+    case DSS_ERR_CUDA: return "CUDA runtime error";
+    case DSS_ERR_TIMEOUT: return "bounded device wait gave up";
+    case DSS_ERR_STATE: return "call out of order (no state loaded)";
+    case DSS_ERR_INTERNAL: return "internal consistency check failed";
+    default: return "unknown error";
+  }
+}
+
+int dss_create(dss_handle** out, const dss_params* p, int64_t n, const double box[3],
+               void* cuda_stream) {
+  if (!out || !p || !box || n < 2 || n > (int64_t)1 << 30) return DSS_ERR_ARG;
+  *out = nullptr;
+  for (int d = 0; d < 3; ++d)
+    if (!(box[d] > 0.0) || !std::isfinite(box[d])) return DSS_ERR_ARG;
+  if (!(p->kn >= 0) || !(p->kt > 0) || !(p->gamma_n >= 0) || !(p->mu >= 0) || !(p->eta0 >= 0) ||
+      !(p->rho > 0) || !(p->delta_lub >= 0) || !(p->lub_eps > 0) || !(p->a0 > 0) || !(p->dt > 0) ||
+      !std::isfinite(p->shear_rate) || (p->lub_cutoff_mode != 0 && p->lub_cutoff_mode != 1) ||
+      (p->precision != DSS_FP64 && p->precision != DSS_MIXED))
+    return DSS_ERR_ARG;
+  dss_handle* h = new dss_handle();
+  memset((void*)h, 0, sizeof(dss_handle));
+  h->p = *p;
+  h->n = n;
+  for (int d = 0; d < 3; ++d) h->L[d] = box[d];
+  h->user_stream = (cudaStream_t)cuda_stream;
+  if (cudaGetDevice(&h->device) != cudaSuccess) { delete h; return DSS_ERR_CUDA; }
+  // a stream of our own: graph capture is not allowed on the legacy stream
+  if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    delete h;
+    return DSS_ERR_CUDA;
+  }
+  if (cudaEventCreateWithFlags(&h->ev_enter, cudaEventDisableTiming) != cudaSuccess) {
+    cudaStreamDestroy(h->stream);
+    delete h;
+    return DSS_ERR_CUDA;
+  }
+  if (cudaMalloc((void**)&h->status, sizeof(DevStatus)) != cudaSuccess) {
+    dss_destroy(h);
+    return DSS_ERR_CUDA;
+  }
+  if (cudaMallocHost((void**)&h->status_host, sizeof(DevStatus)) != cudaSuccess) {
+    dss_destroy(h);
+    return DSS_ERR_CUDA;
+  }
+  cudaMemsetAsync(h->status, 0, sizeof(DevStatus), h->stream);
+  Geo& g = h->g;
+  g.n = (int)n;
+  g.kn = p->kn; g.kt = p->kt; g.gn = p->gamma_n; g.mu = p->mu;
+  g.eta0 = p->eta0; g.rho = p->rho;
+  g.delta = p->delta_lub; g.eps = p->lub_eps; g.a0 = p->a0;
+  g.mode = p->lub_cutoff_mode; g.precision = p->precision;
+  g.gdot = p->shear_rate; g.dt = p->dt;
+  g.k6 = 6.0 * DSS_PI * p->eta0;
+  g.k8 = 8.0 * DSS_PI * p->eta0;
+  *out = h;
+  return DSS_OK;
+}
+
+int dss_set_state(dss_handle* h, const double* x, const double* a, const int32_t* ids,
+                  const double* u, const double* w, const double* alpha_lin,
+                  const double* alpha_ang, int64_t nstep) {
+  if (!h || !x || !a || nstep < 0) return DSS_ERR_ARG;
+  if ((alpha_lin == nullptr) != (alpha_ang == nullptr)) return DSS_ERR_ARG;
+  ENTER(h);
+  const int64_t n = h->n;
+  // host-side validation of radii, positions and ids
+  std::vector<double> ha(n), hx(3 * n);
+  CK(cudaMemcpy(ha.data(), a, sizeof(double) * n, cudaMemcpyDefault));
+  CK(cudaMemcpy(hx.data(), x, sizeof(double) * 3 * n, cudaMemcpyDefault));
+  double amin = INFINITY, amax = 0.0, s3 = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    if (!(ha[i] > 0.0) || !std::isfinite(ha[i])) return DSS_ERR_ARG;
+    amin = std::min(amin, ha[i]);
+    amax = std::max(amax, ha[i]);
+    s3 += ha[i] * ha[i] * ha[i];
+  }
+  for (int d = 0; d < 3; ++d)
+    for (int64_t i = 0; i < n; ++i) {
+      double v = hx[d * n + i];
+      if (!(v >= 0.0 && v < h->L[d])) return DSS_ERR_ARG;
+    }
+  std::vector<int32_t> hid(n);
+  if (ids) {
+    CK(cudaMemcpy(hid.data(), ids, sizeof(int32_t) * n, cudaMemcpyDefault));
+    std::vector<char> seen(n, 0);
+    for (int64_t i = 0; i < n; ++i) {
+      if (hid[i] < 0 || hid[i] >= n || seen[hid[i]]) return DSS_ERR_ARG;
+      seen[hid[i]] = 1;
+    }
+  } else {
+    for (int64_t i = 0; i < n; ++i) hid[i] = (int32_t)i;
+  }
+  if (!h->sized || amax > h->a_max || amin < h->a_min) {
+    if (h->sized) free_buffers(h);
+    drop_graphs(h);
+    h->a_min = amin;
+    h->a_max = amax;
+    int r = geometry(h);
+    if (r) return r;
+    r = alloc_buffers(h);
+    if (r) { free_buffers(h); return r; }
+  }
+  h->g.sumA3 = s3;
+  drop_graphs(h);
+  h->cur = 0;
+  h->hist = 0;
+  StateBuf& s = h->st[0];
+  CK(cudaMemcpyAsync(s.x, hx.data(), sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(s.a, ha.data(), sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(s.id, hid.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, h->stream));
+  if (u) CK(cudaMemcpyAsync(s.u, u, sizeof(double) * 3 * n, cudaMemcpyDefault, h->stream));
+  if (w) CK(cudaMemcpyAsync(s.w, w, sizeof(double) * 3 * n, cudaMemcpyDefault, h->stream));
+  const int nb = (int)((n + 255) / 256);
+  if (!u || !w) k_default_vel<<<nb, 256, 0, h->stream>>>((int)n, s.x, h->g.gdot, s.u, s.w, !u, !w);
+  if (alpha_lin) {
+    CK(cudaMemcpyAsync(s.al, alpha_lin, sizeof(double) * 3 * n, cudaMemcpyDefault, h->stream));
+    CK(cudaMemcpyAsync(s.aw, alpha_ang, sizeof(double) * 3 * n, cudaMemcpyDefault, h->stream));
+  }
+  // empty history: no rows, identity id map
+  for (int b = 0; b < 2; ++b) {
+    CK(cudaMemsetAsync(h->lb[b].count, 0, sizeof(int) * n, h->stream));
+    CK(cudaMemsetAsync(h->lb[b].start, 0, sizeof(int) * (n + 1), h->stream));
+    k_iota<<<nb, 256, 0, h->stream>>>((int)n, h->lb[b].slot_of_id);
+  }
+  k_set_nstep<<<1, 1, 0, h->stream>>>(h->status, (long long)nstep);
+  CK(cudaGetLastError());
+  h->have_state = true;
+  h->host_steps_done = 0;
+  if (!alpha_lin) {
+    // alpha^0 from one force evaluation at the initial state (empty history)
+    seq_sort_enum(h, false, 0);
+    h->cur = 1 - h->cur;
+    launch_forces(h, h->cur, 1 - h->hist, h->hist, 0, G_ACCEL, nullptr, nullptr);
+    CK(cudaGetLastError());
+    int r = sync_status(h);
+    if (r) return r;
+    if ((r = status_error(h))) { clear_err(h); return r; }
+  } else {
+    CK(cudaStreamSynchronize(h->stream));
+  }
+  return DSS_OK;
+}
+
+int dss_get_state(dss_handle* h, double* x, double* u, double* w, double* alpha_lin,
+                  double* alpha_ang) {
+  if (!h) return DSS_ERR_ARG;
+  if (!h->have_state) return DSS_ERR_STATE;
+  ENTER(h);
+  const int n = (int)h->n;
+  const StateBuf& s = h->st[h->cur];
+  const double* src[5] = {s.x, s.u, s.w, s.al, s.aw};
+  double* dst[5] = {x, u, w, alpha_lin, alpha_ang};
+  for (int k = 0; k < 5; ++k) {
+    if (!dst[k]) continue;
+    k_scatter_by_id<<<(n + 255) / 256, 256, 0, h->stream>>>(n, src[k], s.id, h->io3);
+    CK(cudaMemcpyAsync(dst[k], h->io3, sizeof(double) * 3 * n, cudaMemcpyDefault, h->stream));
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  return DSS_OK;
+}
+
+int dss_neighbour_build(dss_handle* h) {
+  if (!h) return DSS_ERR_ARG;
+  if (!h->have_state) return DSS_ERR_STATE;
+  ENTER(h);
+  seq_sort_enum(h, false, 0);
+  h->cur = 1 - h->cur;
+  CK(cudaGetLastError());
+  int r = sync_status(h);
+  if (r) return r;
+  if ((r = status_error(h))) { clear_err(h); return r; }
+  return DSS_OK;
+}
+
+int dss_get_pairs(dss_handle* h, int64_t* lohi, int64_t cap, int64_t* count) {
+  if (!h || !count || cap < 0 || (cap > 0 && !lohi)) return DSS_ERR_ARG;
+  if (!h->have_state) return DSS_ERR_STATE;
+  ENTER(h);
+  const int list = h->last_list;
+  int P = 0;
+  CK(cudaMemcpyAsync(&P, h->lb[list].start + h->n, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  *count = P;
+  if (P == 0 || cap == 0) return DSS_OK;
+  if (P > h->pcap) return DSS_ERR_CAPACITY;
+  long long* dev = (long long*)h->rec;   // scratch: 9*pcap doubles >= 2*P int64
+  launch_pairs_out(h, list, dev);
+  std::vector<long long> hp(2 * (size_t)P);
+  CK(cudaMemcpyAsync(hp.data(), dev, sizeof(long long) * 2 * P, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  std::vector<std::pair<long long, long long>> v(P);
+  for (int p = 0; p < P; ++p) v[p] = {hp[2 * p], hp[2 * p + 1]};
+  std::sort(v.begin(), v.end());
+  int64_t m = std::min<int64_t>(cap, P);
+  for (int64_t p = 0; p < m; ++p) {
+    lohi[2 * p] = v[p].first;
+    lohi[2 * p + 1] = v[p].second;
+  }
+  return DSS_OK;
+}
+
+int dss_force_eval(dss_handle* h, double* F, double* T) {
+  if (!h) return DSS_ERR_ARG;
+  if (!h->have_state) return DSS_ERR_STATE;
+  ENTER(h);
+  const int n = (int)h->n;
+  seq_sort_enum(h, false, 0);
+  h->cur = 1 - h->cur;
+  launch_forces(h, h->cur, 1 - h->hist, h->hist, 0, G_EVAL, F ? h->io3 : nullptr,
+                T ? h->io3b : nullptr);
+  CK(cudaGetLastError());
+  if (F) CK(cudaMemcpyAsync(F, h->io3, sizeof(double) * 3 * n, cudaMemcpyDefault, h->stream));
+  if (T) CK(cudaMemcpyAsync(T, h->io3b, sizeof(double) * 3 * n, cudaMemcpyDefault, h->stream));
+  int r = sync_status(h);
+  if (r) return r;
+  if ((r = status_error(h))) { clear_err(h); return r; }
+  return DSS_OK;
+}
+
+int dss_step(dss_handle* h, int64_t nsteps) {
+  if (!h || nsteps < 0) return DSS_ERR_ARG;
+  if (!h->have_state) return DSS_ERR_STATE;
+  ENTER(h);
+  int64_t remaining = nsteps;
+  int retries = 0;
+  while (remaining > 0) {
+    int r = sync_status(h);
+    if (r) return r;
+    const int steps0 = h->status_host->w[ST_STEPS];
+    const int cur0 = h->cur, hist0 = h->hist;
+    int c = cur0, hs = hist0;
+    for (int64_t k = 0; k < remaining; ++k) {
+      const int key = c * 2 + hs;
+      h->cur = c;
+      h->hist = hs;
+      if (!h->graph_ok[key]) {
+        r = capture_step(h, key);
+        if (r) return r;
+      }
+      CK(cudaGraphLaunch(h->step_graph[key], h->stream));
+      c = 1 - c;
+      hs = 1 - hs;
+    }
+    r = sync_status(h);
+    if (r) return r;
+    const int done = h->status_host->w[ST_STEPS] - steps0;
+    h->cur = (done & 1) ? 1 - cur0 : cur0;
+    h->hist = (done & 1) ? 1 - hist0 : hist0;
+    h->host_steps_done += done;
+    remaining -= done;
+    if (done > 0) h->last_list = h->hist;
+    const int err = status_error(h);
+    if (!err) break;
+    clear_err(h);
+    // a pair-capacity overflow is recovered by growing the pair buffers
+    const int P = h->status_host->w[ST_NPAIRS];
+    if (err == DSS_ERR_CAPACITY && P > h->pcap && retries < 4) {
+      ++retries;
+      r = alloc_pair_buffers(h, (int64_t)(P * 1.25) + 1024, true);
+      if (r) return r;
+      continue;
+    }
+    return err;
+  }
+  return DSS_OK;
+}
+
+int dss_stress(dss_handle* h, double sigma[9]) {
+  if (!h || !sigma) return DSS_ERR_ARG;
+  if (!h->have_state) return DSS_ERR_STATE;
+  ENTER(h);
+  CK(cudaMemcpyAsync(sigma, h->sigma, 9 * sizeof(double), cudaMemcpyDefault, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return DSS_OK;
+}
+
+int dss_get_counters(dss_handle* h, dss_counters* c) {
+  if (!h || !c) return DSS_ERR_ARG;
+  int r = sync_status(h);
+  if (r) return r;
+  const DevStatus& s = *h->status_host;
+  memset(c, 0, sizeof(*c));
+  c->steps_done = h->host_steps_done;
+  c->nstep = (int64_t)(uint32_t)s.w[ST_NSTEP_LO] | ((int64_t)s.w[ST_NSTEP_HI] << 32);
+  int P = 0;
+  CK(cudaMemcpy(&P, h->lb[h->last_list].start + h->n, sizeof(int), cudaMemcpyDeviceToHost));
+  c->npairs = P;
+  c->ncontacts = s.w[ST_NCONT];
+  c->max_row = s.w[ST_MAXROW];
+  c->band_checks = s.w[ST_BAND];
+  c->M = h->g.M;
+  for (int d = 0; d < 3; ++d) c->ncell[d] = h->g.nc[d];
+  return DSS_OK;
+}
+
+int dss_set_history(dss_handle* h, int64_t k, const int64_t* keys, const double* xi) {
+  if (!h || k < 0 || (k > 0 && (!keys || !xi))) return DSS_ERR_ARG;
+  if (!h->have_state) return DSS_ERR_STATE;
+  ENTER(h);
+  std::vector<std::pair<int64_t, int64_t>> order(k);
+  std::vector<int64_t> hk(k);
+  std::vector<double> hx(3 * k);
+  if (k) {
+    CK(cudaMemcpy(hk.data(), keys, sizeof(int64_t) * k, cudaMemcpyDefault));
+    CK(cudaMemcpy(hx.data(), xi, sizeof(double) * 3 * k, cudaMemcpyDefault));
+  }
+  for (int64_t q = 0; q < k; ++q) order[q] = {hk[q], q};
+  std::sort(order.begin(), order.end());
+  std::vector<long long> sk(std::max<int64_t>(k, 1));
+  std::vector<double> sx(3 * std::max<int64_t>(k, 1));
+  for (int64_t q = 0; q < k; ++q) {
+    sk[q] = order[q].first;
+    for (int c = 0; c < 3; ++c) sx[3 * q + c] = hx[3 * order[q].second + c];
+  }
+  long long* dk = nullptr;
+  double* dx = nullptr;
+  CK(cudaMalloc((void**)&dk, sizeof(long long) * sk.size()));
+  CK(cudaMalloc((void**)&dx, sizeof(double) * sx.size()));
+  CK(cudaMemcpy(dk, sk.data(), sizeof(long long) * sk.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(dx, sx.data(), sizeof(double) * sx.size(), cudaMemcpyHostToDevice));
+  // neighbour build at the current state, attach the stretch, commit as history
+  seq_sort_enum(h, false, 0);
+  h->cur = 1 - h->cur;
+  const int L = 1 - h->hist;
+  k_attach_history<<<pair_grid_blocks(h), 256, 0, h->stream>>>(h->g, h->st[h->cur], h->lb[L], dk, dx, (int)k);
+  CK(cudaGetLastError());
+  int r = sync_status(h);
+  cudaFree(dk);
+  cudaFree(dx);
+  if (r) return r;
+  if ((r = status_error(h))) { clear_err(h); return r; }
+  h->hist = L;
+  return DSS_OK;
+}
+
+int dss_get_history(dss_handle* h, int64_t* keys, double* xi, int64_t cap, int64_t* count) {
+  if (!h || !count || cap < 0 || (cap > 0 && (!keys || !xi))) return DSS_ERR_ARG;
+  if (!h->have_state) return DSS_ERR_STATE;
+  ENTER(h);
+  int P = 0;
+  CK(cudaMemcpy(&P, h->lb[h->hist].start + h->n, sizeof(int), cudaMemcpyDeviceToHost));
+  long long* dk = nullptr;
+  double* dx = nullptr;
+  int* cnt = nullptr;
+  size_t m = std::max(P, 1);
+  CK(cudaMalloc((void**)&dk, sizeof(long long) * m));
+  CK(cudaMalloc((void**)&dx, sizeof(double) * 3 * m));
+  CK(cudaMalloc((void**)&cnt, sizeof(int)));
+  CK(cudaMemsetAsync(cnt, 0, sizeof(int), h->stream));
+  k_history_out<<<pair_grid_blocks(h), 256, 0, h->stream>>>(h->g, h->lb[h->hist], dk, dx, cnt, (int)m);
+  int K = 0;
+  CK(cudaMemcpyAsync(&K, cnt, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  std::vector<long long> hk(std::max(K, 1));
+  std::vector<double> hx(3 * (size_t)std::max(K, 1));
+  CK(cudaMemcpy(hk.data(), dk, sizeof(long long) * K, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(hx.data(), dx, sizeof(double) * 3 * K, cudaMemcpyDeviceToHost));
+  cudaFree(dk); cudaFree(dx); cudaFree(cnt);
+  std::vector<std::pair<long long, int>> order(K);
+  for (int q = 0; q < K; ++q) order[q] = {hk[q], q};
+  std::sort(order.begin(), order.end());
+  *count = K;
+  int64_t mm = std::min<int64_t>(cap, K);
+  for (int64_t q = 0; q < mm; ++q) {
+    keys[q] = order[q].first;
+    for (int c = 0; c < 3; ++c) xi[3 * q + c] = hx[3 * order[q].second + c];
+  }
+  return DSS_OK;
+}
+
+int64_t dss_device_bytes(const dss_handle* h) { return h ? h->bytes : 0; }
+
+void dss_destroy(dss_handle* h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  drop_graphs(h);
+  free_buffers(h);
+  if (h->status) cudaFree(h->status);
+  if (h->status_host) cudaFreeHost(h->status_host);
+  if (h->ev_enter) cudaEventDestroy(h->ev_enter);
+  if (h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,340 @@
+// Internal definitions shared by the libdss CUDA translation units.
+// Geometry, cell stencils and the exact neighbour predicate live here so that
+// every kernel evaluates them with the same instruction sequence.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/dss.h"
+
+#define DSS_PI 3.14159265358979323846
+
+// Device status word layout (int32 slots in DevStatus::w).
+enum {
+  ST_ERR = 0,        // first error code seen (0 = none); later kernels early-exit
+  ST_MAXROW = 1,     // largest half-list row of the last enumeration
+  ST_NPAIRS = 2,     // pairs of the last enumeration
+  ST_NCONT = 3,      // contacts of the last force pass
+  ST_BAND = 4,       // exact-predicate fallbacks of the last enumeration
+  ST_STEPS = 5,      // committed steps (low 32 bits)
+  ST_NSTEP_LO = 6,   // time step counter (64 bit, lo/hi)
+  ST_NSTEP_HI = 7,
+  ST_BADPOS = 8,     // set_state: positions outside the box
+  ST_WORDS = 16
+};
+
+struct DevStatus {
+  int w[ST_WORDS];
+};
+
+// Everything a kernel needs to know about the model and the grid, by value.
+struct Geo {
+  // box and grid
+  double L[3];
+  double halfL[3];
+  double cs[3];       // cell edge per axis
+  double inv_cs[3];
+  int nc[3];
+  int ncell;
+  int n;
+  int M;              // half-list capacity per particle
+  int64_t pcap;       // pair capacity
+  // model
+  double kn, kt, gn, mu;
+  double eta0, rho;
+  double delta, eps, a0;
+  int mode;           // cutoff mode
+  int precision;
+  double gdot, dt;
+  double k6;          // 6 pi eta0
+  double k8;          // 8 pi eta0
+  double sumA3;       // sum of a^3 (Einstein stresslet of Eq. 9)
+  // FP32 prefilter margin on r^2 (absolute)
+  float r2_margin;
+  float halfLf[3];
+};
+
+// ------------------------------------------------------------------------
+// Small device helpers
+// ------------------------------------------------------------------------
+__device__ __forceinline__ int dev_err(const DevStatus* s) {
+  return *((volatile const int*)&s->w[ST_ERR]);
+}
+__device__ __forceinline__ void set_err(DevStatus* s, int code) {
+  atomicCAS(&s->w[ST_ERR], 0, code);
+}
+__device__ __forceinline__ int64_t dev_nstep(const DevStatus* s) {
+  const volatile int* w = (const volatile int*)s->w;
+  return (int64_t)(uint32_t)w[ST_NSTEP_LO] | ((int64_t)w[ST_NSTEP_HI] << 32);
+}
+
+// Lees-Edwards offset at step count nstep: fmod(gdot * L_y * (nstep dt), L_x),
+// with the product taken in that order and no fused operations.
+__device__ __forceinline__ double le_offset(const Geo& g, int64_t nstep) {
+  double t = __dmul_rn((double)nstep, g.dt);
+  return fmod(__dmul_rn(__dmul_rn(g.gdot, g.L[1]), t), g.L[0]);
+}
+
+// Interaction range beyond contact for the pair.
+__device__ __forceinline__ double pair_delta(const Geo& g, double ai, double aj) {
+  if (g.mode == 1) return __dmul_rn(g.delta, g.a0);
+  return __dmul_rn(__dmul_rn(g.delta, __dadd_rn(ai, aj)), 0.5);
+}
+
+// Minimum-image separation r = x_j - x_i under Lees-Edwards conditions,
+// spelled out operation by operation (no contraction) so that the neighbour
+// decision is the same bit pattern on every path.  sy: image shift in y
+// (-1: image one box below, +1: above).
+__device__ __forceinline__ void min_image(const Geo& g, double off, double xi, double yi,
+                                          double zi, double xj, double yj, double zj,
+                                          double& dx, double& dy, double& dz, int& sy) {
+  dx = __dsub_rn(xj, xi);
+  dy = __dsub_rn(yj, yi);
+  dz = __dsub_rn(zj, zi);
+  sy = 0;
+  if (dy > g.halfL[1]) {
+    dy = __dsub_rn(dy, g.L[1]);
+    dx = __dsub_rn(dx, off);
+    sy = -1;
+  } else if (dy < -g.halfL[1]) {
+    dy = __dadd_rn(dy, g.L[1]);
+    dx = __dadd_rn(dx, off);
+    sy = 1;
+  }
+  dx = __dsub_rn(dx, __dmul_rn(g.L[0], rint(__ddiv_rn(dx, g.L[0]))));
+  dz = __dsub_rn(dz, __dmul_rn(g.L[2], rint(__ddiv_rn(dz, g.L[2]))));
+}
+
+// Exact neighbour predicate: r^2 < (a_i + a_j + delta_ij)^2, strict.
+__device__ __forceinline__ bool exact_is_pair(const Geo& g, double off, double xi, double yi,
+                                              double zi, double ai, double xj, double yj,
+                                              double zj, double aj) {
+  double dx, dy, dz;
+  int sy;
+  min_image(g, off, xi, yi, zi, xj, yj, zj, dx, dy, dz, sy);
+  double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+  double s = __dadd_rn(__dadd_rn(ai, aj), pair_delta(g, ai, aj));
+  return r2 < __dmul_rn(s, s);
+}
+
+__device__ __forceinline__ int cell_coord(double v, double inv, int nc) {
+  int k = (int)floor(v * inv);
+  return k < 0 ? 0 : (k >= nc ? nc - 1 : k);
+}
+
+__device__ __forceinline__ int wrapi(int v, int n) {
+  v %= n;
+  return v < 0 ? v + n : v;
+}
+
+// Shift (in cells) of the Lees-Edwards row: floor(off / cs_x).
+__device__ __forceinline__ int le_shift_cells(const Geo& g, double off) {
+  return (int)floor(off * g.inv_cs[0]);
+}
+
+// One stencil cell: linear cell id and the (unwrapped) displacement of that
+// cell's origin relative to the owner cell origin, plus the Lees-Edwards
+// x offset (0 or off) to add for images across y = L_y.
+struct StencilCell {
+  int cell;
+  int ox, oy, oz;
+  int le;   // 1: reached through y = L_y (image shifted by +off); 2: own cell
+};
+
+// Forward half-stencil of owner cell (cx, cy, cz) (Sec. II A, Fig. 6): the
+// layer y+1 (3x3 cells; across y = L_y the 4 x-cells covering the shifted
+// image range), the layer y with z+1 (3 cells), the cell x+1, and the own
+// cell (marked le = 2; there only partners after the owner count).
+// Returned sorted by linear cell id.
+__device__ __forceinline__ int forward_cells(const Geo& g, int cx, int cy, int cz, int fsh,
+                                             StencilCell* out) {
+  int k = 0;
+  const int nx = g.nc[0], ny = g.nc[1], nz = g.nc[2];
+  if (cy < ny - 1) {
+    for (int oz = -1; oz <= 1; ++oz)
+      for (int ox = -1; ox <= 1; ++ox) {
+        int qx = wrapi(cx + ox, nx), qz = wrapi(cz + oz, nz);
+        out[k++] = StencilCell{(qz * ny + (cy + 1)) * nx + qx, ox, 1, oz, 0};
+      }
+  } else {
+    for (int oz = -1; oz <= 1; ++oz)
+      for (int ox = -2 - fsh; ox <= 1 - fsh; ++ox) {
+        int qx = wrapi(cx + ox, nx), qz = wrapi(cz + oz, nz);
+        out[k++] = StencilCell{(qz * ny + 0) * nx + qx, ox, 1, oz, 1};
+      }
+  }
+  for (int ox = -1; ox <= 1; ++ox) {
+    int qx = wrapi(cx + ox, nx), qz = wrapi(cz + 1, nz);
+    out[k++] = StencilCell{(qz * ny + cy) * nx + qx, ox, 0, 1, 0};
+  }
+  out[k++] = StencilCell{(cz * ny + cy) * nx + wrapi(cx + 1, nx), 1, 0, 0, 0};
+  out[k++] = StencilCell{(cz * ny + cy) * nx + cx, 0, 0, 0, 2};   // own cell
+  // insertion sort by cell id (at most 17 entries)
+  for (int a = 1; a < k; ++a) {
+    StencilCell t = out[a];
+    int b = a - 1;
+    while (b >= 0 && out[b].cell > t.cell) {
+      out[b + 1] = out[b];
+      --b;
+    }
+    out[b + 1] = t;
+  }
+  return k;
+}
+
+// Inverse of forward_cells: the cells whose forward stencil contains cell
+// (cx, cy, cz), i.e. where the owners of this cell's particles live, plus the
+// own cell (le = 2; owners before the particle); the displacement stored is
+// that of the owner cell relative to this cell.  Sorted by cell id.
+__device__ __forceinline__ int backward_cells(const Geo& g, int cx, int cy, int cz, int fsh,
+                                              StencilCell* out) {
+  int k = 0;
+  const int nx = g.nc[0], ny = g.nc[1], nz = g.nc[2];
+  if (cy > 0) {
+    for (int oz = -1; oz <= 1; ++oz)
+      for (int ox = -1; ox <= 1; ++ox) {
+        int qx = wrapi(cx + ox, nx), qz = wrapi(cz + oz, nz);
+        out[k++] = StencilCell{(qz * ny + (cy - 1)) * nx + qx, ox, -1, oz, 0};
+      }
+  } else {
+    // owners in the top row with this cell in their shifted window:
+    // cx = (cx_owner + ox_f) mod nx with ox_f in [-2-fsh, 1-fsh]
+    for (int oz = -1; oz <= 1; ++oz)
+      for (int ox = -1 + fsh; ox <= 2 + fsh; ++ox) {
+        int qx = wrapi(cx + ox, nx), qz = wrapi(cz + oz, nz);
+        out[k++] = StencilCell{(qz * ny + (ny - 1)) * nx + qx, ox, -1, oz, 1};
+      }
+  }
+  for (int ox = -1; ox <= 1; ++ox) {
+    int qx = wrapi(cx + ox, nx), qz = wrapi(cz - 1, nz);
+    out[k++] = StencilCell{(qz * ny + cy) * nx + qx, ox, 0, -1, 0};
+  }
+  out[k++] = StencilCell{(cz * ny + cy) * nx + wrapi(cx - 1, nx), -1, 0, 0, 0};
+  out[k++] = StencilCell{(cz * ny + cy) * nx + cx, 0, 0, 0, 2};   // own cell
+  for (int a = 1; a < k; ++a) {
+    StencilCell t = out[a];
+    int b = a - 1;
+    while (b >= 0 && out[b].cell > t.cell) {
+      out[b + 1] = out[b];
+      --b;
+    }
+    out[b + 1] = t;
+  }
+  return k;
+}
+
+// FP32 conservative prefilter.  Positions are stored relative to their cell
+// origin in FP32 (|error| <= 2^-24 cs).  For a candidate in a stencil cell
+// with displacement (ox, oy, oz) the separation is
+//   d = (xl_j - xl_i) + (o * cs [+ off for a Lees-Edwards image])
+// up to a bounded rounding error; the decision is:
+//   1: certainly a pair, 0: certainly not, -1: decide with exact_is_pair.
+__device__ __forceinline__ int prefilter(const Geo& g, float4 pi, float4 pj, float cxo, float cyo,
+                                         float czo, float s) {
+  float dx = (pj.x - pi.x) + cxo;
+  float dy = (pj.y - pi.y) + cyo;
+  float dz = (pj.z - pi.z) + czo;
+  if (fabsf(dx) > g.halfLf[0] || fabsf(dy) > g.halfLf[1] || fabsf(dz) > g.halfLf[2]) return -1;
+  float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+  float s2 = s * s;
+  if (r2 < s2 - g.r2_margin) return 1;
+  if (r2 > s2 + g.r2_margin) return 0;
+  return -1;
+}
+
+__device__ __forceinline__ float pair_delta_f(const Geo& g, float ai, float aj) {
+  if (g.mode == 1) return (float)(g.delta * g.a0);
+  return (float)g.delta * (ai + aj) * 0.5f;
+}
+
+// ------------------------------------------------------------------------
+// Host-side handle
+// ------------------------------------------------------------------------
+struct StateBuf {
+  double* x;    // 3n positions
+  double* u;    // 3n velocity (u^{n+1/2} after the sort of a step)
+  double* w;    // 3n angular velocity
+  double* al;   // 3n linear acceleration
+  double* aw;   // 3n angular acceleration
+  double* a;    // n radius
+  int* id;      // n persistent id
+};
+
+struct ListBuf {
+  int* count;       // n half-list row lengths
+  int* list;        // n*M partner sorted indices
+  int* start;       // n+1 row offsets into the pair arrays (exclusive scan of count)
+  double* xi;       // 3*pcap tangential stretch (lo->hi orientation), per pair slot
+  unsigned char* cflag;  // pcap: 1 when the pair was in contact (d < 0)
+  int* slot_of_id;  // n: sorted index of each id in this list's index space
+  int* id_of_slot;  // n: id of each sorted index of this list
+};
+
+struct dss_handle {
+  dss_params p;
+  int64_t n;
+  double L[3];
+  cudaStream_t stream;       // the library's own stream (all work is issued here)
+  cudaStream_t user_stream;  // the caller's stream; work starts after it
+  cudaEvent_t ev_enter;
+  int device;
+  bool have_state;
+  bool sized;
+  double a_min, a_max;
+  Geo g;
+  // state: cur holds the committed state; the other buffer is scratch
+  StateBuf st[2];
+  int cur;
+  // sorted-order extras of the last sort (belong to st[cur] after a sort)
+  float4* posf;      // n: cell-local FP32 position + radius
+  int* cellid;       // n
+  int* perm;         // n: new sorted index -> previous index
+  // counting sort scratch
+  int* key;          // n
+  int* offs;         // n
+  int* cell_count;   // ncell
+  int* cell_start;   // ncell+1
+  int* tmp;          // n
+  // lists: hist = committed (history source), work = being built
+  ListBuf lb[2];
+  int hist;
+  bool hist_empty;
+  // per-pair records of the last force pass
+  double* rec;       // 9*pcap: F_i (3), T_i (3), T_j (3)
+  int64_t pcap;
+  // stress
+  double* spart;     // 9 * max pair blocks
+  int spart_blocks;
+  double* sigma;     // 9
+  // scans
+  unsigned long long* scan_status;  // tile status words (2 scans)
+  int* scan_ticket;                 // 2 tickets
+  int scan_tiles_max;
+  // status
+  DevStatus* status;
+  DevStatus* status_host;           // pinned mirror
+  // user-order io scratch
+  double* io3;       // 3n
+  double* io3b;      // 3n
+  int* io_id;        // n
+  int last_list;     // list written by the last enumeration
+  // graphs: one per (cur, hist) combination
+  cudaGraphExec_t step_graph[4];
+  bool graph_ok[4];
+  int64_t bytes;
+  int64_t host_steps_done;
+};
+
+// Kernel launchers (defined in the .cu files).  adv = 1 inside a time step
+// (positions are at time (nstep+1) dt), 0 for an evaluation at the current
+// time.
+void launch_sort(dss_handle* h, bool predict, int src, int dst);
+void launch_enumerate(dss_handle* h, int stbuf, int dst_list, int adv);
+enum GatherMode { G_STEP = 0, G_EVAL = 1, G_ACCEL = 2 };
+void launch_forces(dss_handle* h, int stbuf, int work_list, int hist_list, int adv, int mode,
+                   double* F_out, double* T_out);
+void launch_pairs_out(dss_handle* h, int list, long long* out);
+int pair_grid_blocks(const dss_handle* h);
+void launch_scan(dss_handle* h, const int* in, int* out, int count, int which, bool zero_in);
+int scan_tiles_for(int count);

@@ -1,0 +1,277 @@
+// Counting sort of the particles into cells (Sec. II A; the paper follows
+// Hoetzlein's counting sort), redone every step with no Verlet skin:
+//   1. predictor + Lees-Edwards wrap (Eq. 15a-b, 16) fused with the cell key
+//      and a warp-aggregated histogram (one atomic per distinct key per warp);
+//   2. exclusive scan of the histogram (single-pass decoupled look-back);
+//   3. scatter to the cell's slot range;
+//   4. deterministic in-cell order (by previous index) and the gather of the
+//      state into the new sorted order, recomputing the predictor.
+#include "dss_internal.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;
+
+// Predictor of Eq. 15a-b and the wrap of Eq. 16 for one particle, with the
+// rounding of every operation fixed so that both sort kernels obtain the
+// same bits.  Returns the y crossing (-1 out through the top, +1 bottom).
+struct Pred {
+  double x, y, z, ux, uy, uz;
+  int cross;
+};
+
+__device__ __forceinline__ Pred predict_one(const Geo& g, double off, const StateBuf& s, int i,
+                                            bool predict) {
+  const int n = g.n;
+  Pred r;
+  double x = s.x[i], y = s.x[n + i], z = s.x[2 * n + i];
+  double ux = s.u[i], uy = s.u[n + i], uz = s.u[2 * n + i];
+  r.cross = 0;
+  if (predict) {
+    const double dt = g.dt;
+    const double hdt2 = __dmul_rn(__dmul_rn(0.5, dt), dt);
+    const double hdt = __dmul_rn(0.5, dt);
+    double ax = s.al[i], ay = s.al[n + i], az = s.al[2 * n + i];
+    x = __dadd_rn(__dadd_rn(x, __dmul_rn(dt, ux)), __dmul_rn(hdt2, ax));
+    y = __dadd_rn(__dadd_rn(y, __dmul_rn(dt, uy)), __dmul_rn(hdt2, ay));
+    z = __dadd_rn(__dadd_rn(z, __dmul_rn(dt, uz)), __dmul_rn(hdt2, az));
+    ux = __dadd_rn(ux, __dmul_rn(hdt, ax));
+    uy = __dadd_rn(uy, __dmul_rn(hdt, ay));
+    uz = __dadd_rn(uz, __dmul_rn(hdt, az));
+    // Lees-Edwards wrap: leaving through y >= L_y re-enters at the bottom
+    // shifted by -off along x with u_x - gdot L_y, and vice versa.
+    const double Ly = g.L[1];
+    if (y >= Ly) {
+      y = __dsub_rn(y, Ly);
+      x = __dsub_rn(x, off);
+      r.cross = -1;
+    } else if (y < 0.0) {
+      y = __dadd_rn(y, Ly);
+      x = __dadd_rn(x, off);
+      r.cross = 1;
+      if (y >= Ly) y = 0.0;
+    }
+    x = fmod(x, g.L[0]);
+    if (x < 0.0) x = __dadd_rn(x, g.L[0]);
+    if (x >= g.L[0]) x = __dsub_rn(x, g.L[0]);
+    if (z >= g.L[2]) {
+      z = __dsub_rn(z, g.L[2]);
+    } else if (z < 0.0) {
+      z = __dadd_rn(z, g.L[2]);
+      if (z >= g.L[2]) z = 0.0;
+    }
+    if (r.cross != 0)
+      ux = __dadd_rn(ux, __dmul_rn(__dmul_rn((double)r.cross, g.gdot), Ly));
+  }
+  r.x = x; r.y = y; r.z = z;
+  r.ux = ux; r.uy = uy; r.uz = uz;
+  return r;
+}
+
+__device__ __forceinline__ int cell_key(const Geo& g, double x, double y, double z) {
+  int cx = cell_coord(x, g.inv_cs[0], g.nc[0]);
+  int cy = cell_coord(y, g.inv_cs[1], g.nc[1]);
+  int cz = cell_coord(z, g.inv_cs[2], g.nc[2]);
+  return (cz * g.nc[1] + cy) * g.nc[0] + cx;
+}
+
+// 1. key + warp-aggregated histogram
+__global__ void __launch_bounds__(kThreads)
+k_key_hist(Geo g, StateBuf s, int* __restrict__ key, int* __restrict__ offs,
+           int* __restrict__ cell_count, DevStatus* st, bool predict,
+           unsigned long long* scan_status, int* scan_ticket, int scan_tiles) {
+  if (dev_err(st)) return;
+  // reset the look-back state of both scans of this step
+  if (blockIdx.x == 0) {
+    for (int t = threadIdx.x; t < 2 * scan_tiles; t += blockDim.x) scan_status[t] = 0ull;
+    if (threadIdx.x < 2) scan_ticket[threadIdx.x] = 0;
+  }
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= g.n) return;
+  double off = le_offset(g, dev_nstep(st) + (predict ? 1 : 0));
+  Pred p = predict_one(g, off, s, i, predict);
+  int k = cell_key(g, p.x, p.y, p.z);
+  unsigned act = __activemask();
+  unsigned peers = __match_any_sync(act, k);
+  int lane = threadIdx.x & 31;
+  int leader = __ffs(peers) - 1;
+  int rank = __popc(peers & ((1u << lane) - 1u));
+  int base = 0;
+  if (lane == leader) base = atomicAdd(&cell_count[k], __popc(peers));
+  base = __shfl_sync(peers, base, leader);
+  key[i] = k;
+  offs[i] = base + rank;
+}
+
+// 3. scatter to the cell slot range (order inside a cell not yet fixed)
+__global__ void __launch_bounds__(kThreads)
+k_scatter(int n, const int* __restrict__ key, const int* __restrict__ offs,
+          const int* __restrict__ cell_start, int* __restrict__ tmp, const DevStatus* st) {
+  if (dev_err(st)) return;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  tmp[cell_start[key[i]] + offs[i]] = i;
+}
+
+// 4. stable order inside each cell (by previous index) and state gather
+__global__ void __launch_bounds__(kThreads)
+k_rank_gather(Geo g, StateBuf src, StateBuf dst, const int* __restrict__ key,
+              const int* __restrict__ cell_start, const int* __restrict__ tmp,
+              int* __restrict__ perm, int* __restrict__ cellid, float4* __restrict__ posf,
+              DevStatus* st, bool predict) {
+  if (dev_err(st)) return;
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = g.n;
+  if (s >= n) return;
+  int o = tmp[s];
+  int k = key[o];
+  int c0 = cell_start[k], c1 = cell_start[k + 1];
+  int rank = 0;
+  for (int q = c0; q < c1; ++q) rank += (tmp[q] < o);
+  int f = c0 + rank;
+  perm[f] = o;
+  cellid[f] = k;
+  double off = le_offset(g, dev_nstep(st) + (predict ? 1 : 0));
+  Pred p = predict_one(g, off, src, o, predict);
+  dst.x[f] = p.x; dst.x[n + f] = p.y; dst.x[2 * n + f] = p.z;
+  dst.u[f] = p.ux; dst.u[n + f] = p.uy; dst.u[2 * n + f] = p.uz;
+  if (predict) {
+    const double hdt = __dmul_rn(0.5, g.dt);
+    for (int c = 0; c < 3; ++c)
+      dst.w[c * n + f] = __dadd_rn(src.w[c * n + o], __dmul_rn(hdt, src.aw[c * n + o]));
+  } else {
+    for (int c = 0; c < 3; ++c) {
+      dst.w[c * n + f] = src.w[c * n + o];
+      dst.al[c * n + f] = src.al[c * n + o];
+      dst.aw[c * n + f] = src.aw[c * n + o];
+    }
+  }
+  double a = src.a[o];
+  dst.a[f] = a;
+  dst.id[f] = src.id[o];
+  // cell-local FP32 position for the enumeration prefilter
+  int cx = k % g.nc[0];
+  int cy = (k / g.nc[0]) % g.nc[1];
+  int cz = k / (g.nc[0] * g.nc[1]);
+  float4 pf;
+  pf.x = (float)(p.x - cx * g.cs[0]);
+  pf.y = (float)(p.y - cy * g.cs[1]);
+  pf.z = (float)(p.z - cz * g.cs[2]);
+  pf.w = (float)a;
+  posf[f] = pf;
+}
+
+}  // namespace
+
+// Single-pass exclusive scan with decoupled look-back.  Tiles are taken in
+// launch order through an atomic ticket, so every predecessor a tile waits
+// on is already running; each wait is bounded and reports DSS_ERR_TIMEOUT.
+namespace {
+constexpr int kScanThreads = 512;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+constexpr unsigned long long kFlagAgg = 1ull << 32;
+constexpr unsigned long long kFlagPre = 2ull << 32;
+
+__global__ void __launch_bounds__(kScanThreads)
+k_scan(const int* __restrict__ in, int* __restrict__ out, int count,
+       unsigned long long* status, int* ticket, DevStatus* st, int zero_in) {
+  if (dev_err(st)) return;
+  __shared__ int s_tile;
+  __shared__ int s_warp[kScanThreads / 32];
+  __shared__ int s_prefix;
+  if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1);
+  __syncthreads();
+  const int tile = s_tile;
+  const int base = tile * kScanTile;
+  int v[kScanItems];
+  int local = 0;
+  for (int k = 0; k < kScanItems; ++k) {
+    int idx = base + threadIdx.x * kScanItems + k;
+    v[k] = idx < count ? in[idx] : 0;
+    local += v[k];
+  }
+  // block exclusive scan of the per-thread sums
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int incl = local;
+  for (int d = 1; d < 32; d <<= 1) {
+    int t = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += t;
+  }
+  if (lane == 31) s_warp[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    int w = lane < kScanThreads / 32 ? s_warp[lane] : 0;
+    int wi = w;
+    for (int d = 1; d < 32; d <<= 1) {
+      int t = __shfl_up_sync(0xffffffffu, wi, d);
+      if (lane >= d) wi += t;
+    }
+    if (lane < kScanThreads / 32) s_warp[lane] = wi - w;   // exclusive warp offsets
+  }
+  __syncthreads();
+  int excl = incl - local + s_warp[wid];
+  // tile aggregate and look-back
+  if (threadIdx.x == kScanThreads - 1) {
+    int agg = excl + local;
+    int prefix = 0;
+    if (tile == 0) {
+      atomicExch(&status[tile], kFlagPre | (unsigned)agg);
+    } else {
+      atomicExch(&status[tile], kFlagAgg | (unsigned)agg);
+      int t = tile - 1;
+      long long spins = 0;
+      bool ok = true;
+      while (t >= 0) {
+        unsigned long long w = atomicAdd(&status[t], 0ull);
+        unsigned long long f = w & (3ull << 32);
+        if (f == 0ull) {
+          if (++spins > (1ll << 24)) { ok = false; break; }
+          __nanosleep(32);
+          continue;
+        }
+        prefix += (int)(unsigned)(w & 0xffffffffull);
+        if (f == kFlagPre) break;
+        --t;
+      }
+      if (!ok) set_err(st, DSS_ERR_TIMEOUT);
+      atomicExch(&status[tile], kFlagPre | (unsigned)(prefix + agg));
+    }
+    s_prefix = prefix;
+    if (base + kScanTile >= count) out[count] = prefix + agg;   // total
+  }
+  __syncthreads();
+  int run = s_prefix + excl;
+  for (int k = 0; k < kScanItems; ++k) {
+    int idx = base + threadIdx.x * kScanItems + k;
+    if (idx < count) {
+      out[idx] = run;
+      run += v[k];
+      if (zero_in) const_cast<int*>(in)[idx] = 0;
+    }
+  }
+}
+}  // namespace
+
+int scan_tiles_for(int count) { return (count + kScanTile - 1) / kScanTile; }
+
+void launch_scan(dss_handle* h, const int* in, int* out, int count, int which, bool zero_in) {
+  int tiles = scan_tiles_for(count);
+  if (tiles < 1) tiles = 1;
+  k_scan<<<tiles, kScanThreads, 0, h->stream>>>(in, out, count,
+                                                 h->scan_status + which * h->scan_tiles_max,
+                                                 h->scan_ticket + which, h->status, zero_in ? 1 : 0);
+}
+
+void launch_sort(dss_handle* h, bool predict, int src, int dst) {
+  const int n = (int)h->n;
+  const int blocks = (n + kThreads - 1) / kThreads;
+  k_key_hist<<<blocks, kThreads, 0, h->stream>>>(h->g, h->st[src], h->key, h->offs, h->cell_count,
+                                                 h->status, predict, h->scan_status, h->scan_ticket,
+                                                 h->scan_tiles_max);
+  launch_scan(h, h->cell_count, h->cell_start, h->g.ncell, 0, true);
+  k_scatter<<<blocks, kThreads, 0, h->stream>>>(n, h->key, h->offs, h->cell_start, h->tmp, h->status);
+  k_rank_gather<<<blocks, kThreads, 0, h->stream>>>(h->g, h->st[src], h->st[dst], h->key,
+                                                    h->cell_start, h->tmp, h->perm, h->cellid,
+                                                    h->posf, h->status, predict);
+}

@@ -1,0 +1,162 @@
+"""Python face of libdss: a ``Suspension`` handle over the C ABI.
+
+Argument marshalling only: every step of the time step runs in the CUDA
+kernels of libdss.so.  PyTorch provides device memory and the CUDA stream.
+Arrays may be torch tensors (CPU or CUDA) or numpy arrays; vector quantities
+have shape (3, n) (SoA), per-particle outputs are in id order.
+"""
+from __future__ import annotations
+
+import ctypes
+from ctypes import byref, c_double, c_int64, c_void_p
+
+import numpy as np
+
+from . import _native as nat
+
+
+def default_params(box=None, *, kn=1e4, kt=None, gamma_n=None, mu=0.5, eta0=1.0, rho=1.0,
+                   delta_lub=0.05, lub_eps=1e-3, a0=1.0, lub_cutoff_mode=0, precision="fp64",
+                   shear_rate=1.0, dt=1e-4, cell_size=0.0, capacity_M=0, pair_capacity=0):
+    """Model parameters; kt defaults to kn/2 and gamma_n to 1e-7 kn / gdot."""
+    p = nat.Params()
+    p.kn = kn
+    p.kt = 0.5 * kn if kt is None else kt
+    if gamma_n is None:
+        gamma_n = 1e-7 * kn / shear_rate if shear_rate != 0 else 0.0
+    p.gamma_n = gamma_n
+    p.mu, p.eta0, p.rho = mu, eta0, rho
+    p.delta_lub, p.lub_eps, p.a0 = delta_lub, lub_eps, a0
+    p.lub_cutoff_mode = lub_cutoff_mode
+    p.precision = {"fp64": nat.FP64, "mixed": nat.MIXED}[precision] if isinstance(precision, str) else precision
+    p.shear_rate, p.dt = shear_rate, dt
+    p.cell_size, p.capacity_M, p.pair_capacity = cell_size, capacity_M, pair_capacity
+    return p
+
+
+class _Arg:
+    """Holds a contiguous buffer alive and exposes its address."""
+
+    def __init__(self, v, dtype):
+        import torch
+        if v is None:
+            self.obj, self.ptr = None, None
+            return
+        if isinstance(v, torch.Tensor):
+            tdt = {np.float64: torch.float64, np.int32: torch.int32, np.int64: torch.int64}[dtype]
+            t = v.detach()
+            if t.dtype != tdt:
+                t = t.to(tdt)
+            t = t.contiguous()
+            self.obj, self.ptr = t, t.data_ptr()
+        else:
+            a = np.ascontiguousarray(v, dtype=dtype)
+            self.obj, self.ptr = a, a.ctypes.data
+
+
+def capacity_estimate(a_min: float, a_max: float, a0: float = 1.0) -> int:
+    """Half-list capacity M from the shell estimate (host only)."""
+    return int(nat.load().dss_capacity_estimate(a_min, a_max, a0))
+
+
+class Suspension:
+    """N spheres in a Lees-Edwards sheared periodic box on one GPU."""
+
+    def __init__(self, x, a, box, params=None, *, ids=None, u=None, w=None, alpha_lin=None,
+                 alpha_ang=None, nstep=0, stream=None, **kw):
+        import torch
+        self.lib = nat.load()
+        self.n = int(np.asarray(a).shape[0] if not isinstance(a, torch.Tensor) else a.shape[0])
+        self.box = np.asarray(box, dtype=np.float64).copy()
+        self.params = params if params is not None else default_params(self.box, **kw)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        self._h = c_void_p()
+        boxc = (c_double * 3)(*self.box.tolist())
+        nat.check(self.lib.dss_create(byref(self._h), byref(self.params), self.n, boxc,
+                                      c_void_p(stream.cuda_stream)), "dss_create")
+        self.set_state(x, a, ids=ids, u=u, w=w, alpha_lin=alpha_lin, alpha_ang=alpha_ang, nstep=nstep)
+
+    # -- state -------------------------------------------------------------
+    def set_state(self, x, a, *, ids=None, u=None, w=None, alpha_lin=None, alpha_ang=None, nstep=0):
+        args = [_Arg(x, np.float64), _Arg(a, np.float64), _Arg(ids, np.int32), _Arg(u, np.float64),
+                _Arg(w, np.float64), _Arg(alpha_lin, np.float64), _Arg(alpha_ang, np.float64)]
+        nat.check(self.lib.dss_set_state(self._h, *[c_void_p(g.ptr) for g in args], int(nstep)),
+                  "dss_set_state")
+
+    def state(self, device="cuda"):
+        """Current x, u, w, alpha_lin, alpha_ang as (3, n) float64 tensors (id order)."""
+        import torch
+        out = {k: torch.empty((3, self.n), dtype=torch.float64, device=device)
+               for k in ("x", "u", "w", "al", "aw")}
+        nat.check(self.lib.dss_get_state(self._h, *[c_void_p(out[k].data_ptr())
+                                                    for k in ("x", "u", "w", "al", "aw")]),
+                  "dss_get_state")
+        return out
+
+    # -- the time step and its phases ---------------------------------------
+    def step(self, nsteps: int = 1):
+        nat.check(self.lib.dss_step(self._h, int(nsteps)), "dss_step")
+
+    def neighbour_build(self):
+        nat.check(self.lib.dss_neighbour_build(self._h), "dss_neighbour_build")
+
+    def pairs(self) -> np.ndarray:
+        """(lo id, hi id) pairs of the last build, sorted."""
+        cnt = c_int64(0)
+        nat.check(self.lib.dss_get_pairs(self._h, None, 0, byref(cnt)), "dss_get_pairs")
+        out = np.zeros((max(cnt.value, 1), 2), dtype=np.int64)
+        nat.check(self.lib.dss_get_pairs(self._h, c_void_p(out.ctypes.data), cnt.value, byref(cnt)),
+                  "dss_get_pairs")
+        return out[:cnt.value]
+
+    def forces(self, device="cuda"):
+        """Total force and torque (pairs + drag) at the current state, (3, n) each."""
+        import torch
+        F = torch.empty((3, self.n), dtype=torch.float64, device=device)
+        T = torch.empty((3, self.n), dtype=torch.float64, device=device)
+        nat.check(self.lib.dss_force_eval(self._h, c_void_p(F.data_ptr()), c_void_p(T.data_ptr())),
+                  "dss_force_eval")
+        return F, T
+
+    def stress(self) -> np.ndarray:
+        s = (c_double * 9)()
+        nat.check(self.lib.dss_stress(self._h, s), "dss_stress")
+        return np.array(list(s)).reshape(3, 3)
+
+    def counters(self) -> dict:
+        c = nat.Counters()
+        nat.check(self.lib.dss_get_counters(self._h, byref(c)), "dss_get_counters")
+        return dict(steps_done=c.steps_done, nstep=c.nstep, npairs=c.npairs, ncontacts=c.ncontacts,
+                    max_row=c.max_row, band_checks=c.band_checks, M=c.M, ncell=tuple(c.ncell))
+
+    def history(self):
+        cnt = c_int64(0)
+        nat.check(self.lib.dss_get_history(self._h, None, None, 0, byref(cnt)), "dss_get_history")
+        k = cnt.value
+        keys = np.zeros(max(k, 1), dtype=np.int64)
+        xi = np.zeros((max(k, 1), 3))
+        nat.check(self.lib.dss_get_history(self._h, c_void_p(keys.ctypes.data), c_void_p(xi.ctypes.data),
+                                           k, byref(cnt)), "dss_get_history")
+        return keys[:k], xi[:k]
+
+    def set_history(self, keys, xi):
+        keys = np.ascontiguousarray(keys, dtype=np.int64)
+        xi = np.ascontiguousarray(xi, dtype=np.float64).reshape(-1, 3)
+        nat.check(self.lib.dss_set_history(self._h, keys.shape[0], c_void_p(keys.ctypes.data),
+                                           c_void_p(xi.ctypes.data)), "dss_set_history")
+
+    def device_bytes(self) -> int:
+        return int(self.lib.dss_device_bytes(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self.lib.dss_destroy(self._h)
+            self._h = c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,240 @@
+"""GPU path (libdss via the C ABI) against the CPU FP64 oracle.
+
+Neighbour sets must be equal bit for bit (as sorted (lo id, hi id) pairs);
+FP64 forces, torques and stresses within 1e-10 relative (normwise over the
+particles); FP64 trajectories within the bound stated in each test.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import oracle
+    import paper_2108_01013_gb300 as dss
+    from paper_2108_01013_gb300 import synth
+    oracle.build()
+    dss.build()
+    synth.build()
+    return dict(oracle=oracle, dss=dss, synth=synth, torch=torch)
+
+
+def _params(env, box, **kw):
+    return env["dss"].default_params(box, **kw), env["oracle"].make_params(box, **kw)
+
+
+def relerr(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def periodic_diff(x, y, box):
+    d = np.abs(np.asarray(x) - np.asarray(y))
+    return np.minimum(d, box[:, None] - d)
+
+
+CASES = [
+    # n, phi, seed, nstep (Lees-Edwards offset), cutoff mode, delta
+    (300, 0.45, 1, 0, 0, 0.05),
+    (777, 0.55, 2, 12345, 0, 0.05),
+    (1000, 0.50, 3, 987654, 0, 0.05),
+    (1501, 0.52, 4, 31, 1, 0.08),
+    (2048, 0.40, 5, 4567, 0, 0.25),
+]
+
+
+@pytest.mark.parametrize("n,phi,seed,nstep,mode,delta", CASES)
+def test_neighbour_pairs_bit_exact(env, n, phi, seed, nstep, mode, delta):
+    g = env["synth"].small(n, phi, seed)
+    box = g["box"]
+    p, po = _params(env, box, lub_cutoff_mode=mode, delta_lub=delta, shear_rate=1.3, dt=1e-3)
+    s = env["dss"].Suspension(g["x"], g["a"], box, p, ids=g["ids"], nstep=nstep,
+                              alpha_lin=np.zeros((3, n)), alpha_ang=np.zeros((3, n)))
+    s.neighbour_build()
+    got = s.pairs()
+    off = env["oracle"].le_offset(po, nstep)
+    want = env["oracle"].pairs_bruteforce(g["x"], g["a"], g["ids"], po, off)
+    assert len(want) > n // 2
+    np.testing.assert_array_equal(got, want)
+    c = s.counters()
+    assert c["npairs"] == len(want)
+    s.close()
+
+
+def test_neighbour_pairs_polydisperse_and_boundary_layer(env):
+    """Radii log-uniform in [1, 3], many particles at the Lees-Edwards
+    boundary, offsets across one full period of the shift."""
+    rng = np.random.default_rng(9)
+    synth = env["synth"]
+    spec = synth.Spec("poly", 1200, 0.45, radii="loguniform", a_min=1.0, a_max=3.0, seed=21)
+    g = synth.generate(spec)
+    box = g["box"]
+    x = g["x"].copy()
+    # push a third of the particles into the top and bottom layers
+    k = rng.choice(g["a"].shape[0], size=400, replace=False)
+    x[1, k[:200]] = rng.uniform(0, 2.0, size=200)
+    x[1, k[200:]] = box[1] - rng.uniform(1e-9, 2.0, size=200)
+    p, po = _params(env, box, shear_rate=0.9, dt=1e-2)
+    for nstep in (0, 7, 333, 1001, 5555):
+        s = env["dss"].Suspension(x, g["a"], box, p, ids=g["ids"], nstep=nstep,
+                                  alpha_lin=np.zeros_like(x), alpha_ang=np.zeros_like(x))
+        s.neighbour_build()
+        off = env["oracle"].le_offset(po, nstep)
+        want = env["oracle"].pairs_bruteforce(x, g["a"], g["ids"], po, off)
+        np.testing.assert_array_equal(s.pairs(), want)
+        s.close()
+
+
+def test_neighbour_pairs_near_cutoff(env):
+    """Pairs placed within a few ulps of the cutoff on both sides."""
+    rng = np.random.default_rng(4)
+    box = np.array([30.0, 30.0, 30.0])
+    pts, rad = [], []
+    for t in range(60):
+        c = rng.uniform(3, 27, size=3)
+        u = rng.normal(size=3)
+        u /= np.linalg.norm(u)
+        ai, aj = (1.0, 1.4) if t % 2 else (1.4, 1.4)
+        s = (ai + aj) * (1 + 0.05 / 2)
+        r = s * (1 + rng.choice([-1, 1]) * rng.uniform(0, 4e-16))
+        pts += [c, c + r * u]
+        rad += [ai, aj]
+    x = np.array(pts).T.copy()
+    x = np.mod(x, box[:, None])
+    a = np.array(rad)
+    n = a.shape[0]
+    ids = np.arange(n, dtype=np.int32)
+    p, po = _params(env, box, shear_rate=0.0)
+    s = env["dss"].Suspension(x, a, box, p, ids=ids, alpha_lin=np.zeros_like(x),
+                              alpha_ang=np.zeros_like(x))
+    s.neighbour_build()
+    want = env["oracle"].pairs_bruteforce(x, a, ids, po, 0.0)
+    np.testing.assert_array_equal(s.pairs(), want)
+    s.close()
+
+
+@pytest.mark.parametrize("seed,nstep,mu", [(1, 0, 0.5), (2, 4321, 1.0)])
+def test_forces_and_stress_fp64(env, seed, nstep, mu):
+    g = env["synth"].small(1000, 0.50, seed)
+    box = g["box"]
+    p, po = _params(env, box, mu=mu)
+    rng = np.random.default_rng(seed)
+    n = g["a"].shape[0]
+    u = np.zeros((3, n))
+    u[0] = 1.0 * g["x"][1]
+    u += 0.3 * rng.normal(size=(3, n))
+    w = 0.3 * rng.normal(size=(3, n))
+    s = env["dss"].Suspension(g["x"], g["a"], box, p, ids=g["ids"], u=u, w=w, nstep=nstep,
+                              alpha_lin=np.zeros((3, n)), alpha_ang=np.zeros((3, n)))
+    F, T = s.forces()
+    S = s.stress()
+    o = env["oracle"].System(po, g["x"], g["a"], ids=g["ids"], u=u, w=w, nstep=nstep)
+    Fo, To, So = o.forces()
+    assert o.ncontacts > 10
+    assert relerr(F.cpu().numpy(), Fo) < FP64_TOL
+    assert relerr(T.cpu().numpy(), To) < FP64_TOL
+    assert relerr(S, So) < FP64_TOL
+    c = s.counters()
+    assert c["npairs"] == o.npairs and c["ncontacts"] == o.ncontacts
+    s.close()
+
+
+def test_forces_with_carried_history(env):
+    """History handed over from the oracle gives the same tangential forces."""
+    g = env["synth"].small(800, 0.52, 7)
+    box = g["box"]
+    p, po = _params(env, box, mu=0.7, shear_rate=20.0)
+    o = env["oracle"].System(po, g["x"], g["a"], ids=g["ids"])
+    o.init_accel()
+    o.step(40)
+    st = o.get_state()
+    keys, xi = o.get_history()
+    assert len(keys) > 20 and np.abs(xi).max() > 0
+    s = env["dss"].Suspension(st["x"], g["a"], box, p, ids=g["ids"], u=st["u"], w=st["w"],
+                              alpha_lin=st["al"], alpha_ang=st["aw"], nstep=o.nstep)
+    s.set_history(keys, xi)
+    k2, x2 = s.history()
+    np.testing.assert_array_equal(k2, keys)
+    np.testing.assert_array_equal(x2, xi)
+    F, T = s.forces()
+    Fo, To, So = o.forces()
+    assert relerr(F.cpu().numpy(), Fo) < FP64_TOL
+    assert relerr(T.cpu().numpy(), To) < FP64_TOL
+    assert relerr(s.stress(), So) < FP64_TOL
+    s.close()
+
+
+def test_trajectory_fp64_c1(env):
+    """The 1000-particle FP64 configuration: 300 steps on both sides."""
+    synth = env["synth"]
+    g = synth.generate(synth.SPECS["c1"])
+    box = g["box"]
+    p, po = _params(env, box, mu=0.5)
+    s = env["dss"].Suspension(g["x"], g["a"], box, p, ids=g["ids"])
+    o = env["oracle"].System(po, g["x"], g["a"], ids=g["ids"])
+    o.init_accel()
+    st0 = s.state()
+    so = o.get_state()
+    assert relerr(st0["al"].cpu().numpy(), so["al"]) < FP64_TOL
+    for chunk in range(3):
+        s.step(100)
+        o.step(100)
+        st = s.state()
+        so = o.get_state()
+        assert periodic_diff(st["x"].cpu().numpy(), so["x"], box).max() < 1e-10
+        assert relerr(st["u"].cpu().numpy(), so["u"]) < 1e-9
+        assert relerr(st["w"].cpu().numpy(), so["w"]) < 1e-9
+        assert relerr(s.stress(), o.get_forces()[2]) < 1e-8
+    k1, x1 = s.history()
+    k2, x2 = o.get_history()
+    np.testing.assert_array_equal(k1, k2)
+    assert np.abs(x1 - x2).max() < 1e-9 * max(np.abs(x2).max(), 1e-12)
+    assert s.counters()["steps_done"] == 300
+    s.close()
+
+
+def test_deterministic_bitwise(env):
+    g = env["synth"].small(1500, 0.52, 12)
+    box = g["box"]
+    p, _ = _params(env, box, mu=0.5, shear_rate=5.0)
+    out = []
+    for rep in range(2):
+        s = env["dss"].Suspension(g["x"], g["a"], box, p, ids=g["ids"])
+        s.step(50)
+        st = s.state()
+        out.append((st["x"].cpu().numpy(), st["u"].cpu().numpy(), st["w"].cpu().numpy(), s.stress()))
+        s.close()
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
+
+
+def test_error_reporting(env):
+    dss = env["dss"]
+    g = env["synth"].small(500, 0.5, 3)
+    box = g["box"]
+    p = dss.default_params(box, capacity_M=1)
+    with pytest.raises(dss.DssError) as e:
+        s = dss.Suspension(g["x"], g["a"], box, p, ids=g["ids"])
+    assert e.value.code == -3
+    small = np.array([6.0, 6.0, 6.0])
+    with pytest.raises(dss.DssError) as e:
+        dss.Suspension(np.full((3, 4), 1.0) + np.arange(4), np.ones(4), small, dss.default_params())
+    assert e.value.code == -2
+    x = g["x"].copy()
+    x[0, 5] = box[0] + 1.0
+    with pytest.raises(dss.DssError) as e:
+        dss.Suspension(x, g["a"], box, dss.default_params(box))
+    assert e.value.code == -1
+    ids = g["ids"].copy()
+    ids[3] = ids[4]
+    with pytest.raises(dss.DssError) as e:
+        dss.Suspension(g["x"], g["a"], box, dss.default_params(box), ids=ids)
+    assert e.value.code == -1
