@@ -1,0 +1,356 @@
+#!/usr/bin/env python
+"""Throughput of the dense-suspension time step on GB300 (particle-steps/s).
+
+One step = the whole per-timestep path on one synthetic suspension: predictor
+and Lees-Edwards wrap, counting sort, half-stencil neighbour enumeration,
+contact-history carry, pair forces (lubrication + frictional contact),
+deterministic symmetric accumulation, Stokes drag, corrector and bulk stress.
+
+Workload (default): 100,000 bidisperse spheres (radii 1.0 / 1.4, equal
+numbers), volume fraction 0.55, friction mu = 1.0, k_n = 1e4, shear rate 1,
+dt = 1e-4, seeded random packing.  Its working set (~70 MB) fits in the 129 MB
+L2, so the L2 is flushed (a 256 MB write) before every timed step and every
+step is timed on its own with CUDA events recorded inside the step's CUDA
+graph (per-kernel events; the step time runs from the first kernel's start to
+the last kernel's end).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+Under torchrun each rank runs an independent replica (replicas only: the
+single-instance path has no data-parallel exchange); value = total particle
+steps of all ranks / max over ranks of the timed GPU time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
+METRIC = "particle-timesteps/s"
+L2_FLUSH_BYTES = 256 << 20
+
+# Algorithmic bytes per launch unit of each kernel (FP64 state), the minimum
+# traffic the step's definition needs: every particle's state read and the
+# permuted state written once, pair list and per-pair records written and
+# read once, history read/written per contact.  Units: particles (n), cells
+# (c) or pairs (p).  See the design notes for the derivation.
+ALG_BYTES = {
+    "k_key_hist": ("n", 72 + 8),          # x, u, alpha read; key, offset written
+    "k_scan_cells": ("c", 12),            # count read + zeroed, start written
+    "k_scatter": ("n", 16),               # key, offset, start read; slot written
+    "k_rank_gather": ("n", 136 + 124),    # state gathered (x,u,w,al,aw,a,id) -> x,u,w,a,id,perm,cell,posf
+    "k_reset_counters": ("n", 0),
+    "k_enumerate": ("n", 16 + 4 + 8),     # own posf, count, id maps (+4 per pair written)
+    "k_scan_rows": ("n", 8),
+    "k_pairs": ("p", 4 + 72 + 24 + 1),    # list entry; record F,Ti,Tj; stretch; flag (+ state per n)
+    "k_gather": ("n", 56 + 96),           # x,u,w,a read; u,w,al,aw written (+96 per pair of records)
+    "k_finalize": ("n", 0),
+}
+
+# DRAM traffic per launch from an ncu capture of the named kernel (bytes), and
+# the hash of the CUDA sources it was taken on; reported only while the
+# sources are unchanged.
+NCU_TRAFFIC = {}
+
+
+def csrc_hash() -> str:
+    d = os.path.join(ROOT, "paper_2108_01013_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return PEAKS_FALLBACK, "fallback"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="c2")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", "dss_clocks_%d_%d.csv" % (os.getpid(), index))
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 10:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), smax=float(parts[2]), util=float(parts[4]),
+                                 hw=parts[6], hwt=parts[7], swt=parts[8], pcap=parts[9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        load = [r for r in rows if r["util"] > 0] or rows
+        reasons = set()
+        for r in load:
+            for k, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                            ("swt", "sw_thermal_slowdown"), ("pcap", "sw_power_cap")):
+                if r[k].lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median([r["sm"] for r in load])),
+                "sm_max_mhz": max(r["smax"] for r in rows), "samples": len(load),
+                "reasons": sorted(reasons)}
+
+
+def cpu_baseline(g, params_kw, seconds: float, nstep: int = 0):
+    """The oracle (single thread, brute force) timed on a sample of the
+    workload: forces on m particles, each against all N.  A full oracle step
+    visits every pair once (N(N-1)/2 checks) while a sampled particle checks
+    all N-1 partners, so the full step's rate is 2m / t."""
+    import oracle
+    oracle.build()
+    po = oracle.make_params(g["box"], **params_kw)
+    o = oracle.System(po, g["x"], g["a"], ids=g["ids"], nstep=nstep)
+    n = g["a"].shape[0]
+    rng = np.random.default_rng(0)
+    m = 64
+    t0 = time.perf_counter()
+    o.forces_sampled(rng.choice(n, size=m, replace=False))
+    dt = time.perf_counter() - t0
+    m = max(16, int(m * seconds / max(dt, 1e-6)))
+    m = min(m, n)
+    idx = rng.choice(n, size=m, replace=False)
+    t0 = time.perf_counter()
+    o.forces_sampled(idx)
+    dt = time.perf_counter() - t0
+    return {"value": 2.0 * m / dt, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": "forces on %d of the %d particles (brute force over all N, FP64, one "
+                      "thread) in %.1f s; full-step rate = 2 m / t" % (m, n, dt)}
+
+
+def workload(name: str, rank: int):
+    from paper_2108_01013_gb300 import synth
+    spec = synth.SPECS[name]
+    if rank:
+        from dataclasses import replace
+        spec = replace(spec, seed=spec.seed + 1000 * rank)
+    return spec, synth.generate(spec)
+
+
+def run_reference(args, rank, world):
+    spec, g = workload(args.workload, 0)
+    if rank != 0:
+        return
+    kw = dict(mu=spec.mu, kn=spec.kn, shear_rate=spec.shear_rate, dt=spec.dt)
+    import oracle
+    oracle.build()
+    po = oracle.make_params(g["box"], **kw)
+    o = oracle.System(po, g["x"], g["a"], ids=g["ids"])
+    n = g["a"].shape[0]
+    rng = np.random.default_rng(1)
+    budget = 150.0 / max(args.steps + args.warmup, 1)          # seconds per step
+    t0 = time.perf_counter()
+    o.forces_sampled(rng.choice(n, size=32, replace=False))
+    per = (time.perf_counter() - t0) / 32
+    m = int(min(n, max(16, budget / max(per, 1e-9))))
+    for _ in range(args.warmup):
+        o.forces_sampled(rng.choice(n, size=m, replace=False))
+    times = []
+    for _ in range(args.steps):
+        idx = rng.choice(n, size=m, replace=False)
+        t0 = time.perf_counter()
+        o.forces_sampled(idx)
+        times.append(time.perf_counter() - t0)
+    t = float(np.mean(times))
+    value = 2.0 * m / t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "particle-steps/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * n / value, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": spec.name, "n": n, "phi": spec.phi, "mu": spec.mu,
+                       "radii": "1.0/1.4 equal numbers", "precision": "fp64", "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+                             "sample": "each step: forces on %d of %d particles (brute force over all "
+                                       "N, FP64, one thread); full-step rate = 2 m / t" % (m, n)},
+            "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_2108_01013_gb300 as dss
+    dss.build()
+
+    spec, g = workload(args.workload, rank)
+    n = g["a"].shape[0]
+    kw = dict(mu=spec.mu, kn=spec.kn, shear_rate=spec.shear_rate, dt=spec.dt)
+    params = dss.default_params(g["box"], precision=args.precision, **kw)
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        s = dss.Suspension(g["x"], g["a"], g["box"], params, ids=g["ids"], stream=stream)
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+        s.set_profiling(True)
+        for _ in range(args.warmup):
+            flush.fill_(1.0)
+            s.step(1)
+        s.set_profiling(True)                      # reset sums after warm-up
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        clocks = Clocks(local)
+        clocks.start()
+        t_wall = time.perf_counter()
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            s.step(1)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        t_wall = time.perf_counter() - t_wall
+        clk = clocks.stop()
+        prof, nprof = s.profile()
+        c = s.counters()
+        step_ms = sum(prof.values()) / max(nprof, 1)      # first kernel start -> last kernel end
+        t_gpu = step_ms * 1e-3 * args.steps
+        if world > 1:
+            tt = torch.tensor([t_gpu], device=dev, dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t_gpu = float(tt.item())
+        value = world * n * args.steps / t_gpu
+
+        # end to end through the public API: per step upload the full state
+        # from pinned host memory, advance, read state and stress back
+        s.set_profiling(False)
+        host = {k: torch.empty((3, n), dtype=torch.float64, pin_memory=True)
+                for k in ("x", "u", "w", "al", "aw")}
+        s.get_state_into(*(host[k] for k in ("x", "u", "w", "al", "aw")))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            s.load_state(*(host[k] for k in ("x", "u", "w", "al", "aw")))
+            s.step(1)
+            s.get_state_into(*(host[k] for k in ("x", "u", "w", "al", "aw")))
+            sig = s.stress()
+        torch.cuda.synchronize()
+        t_e2e = time.perf_counter() - t0
+        e2e_value = n * args.e2e_steps / t_e2e * world
+        bytes_state = 5 * 3 * n * 8
+
+    # roofline of the dominant kernel
+    peaks, src = load_peaks()
+    P = c["npairs"]
+    ncell = int(np.prod(c["ncell"]))
+    units = {"n": n, "c": ncell, "p": P}
+    per_kernel = {}
+    for k, ms in prof.items():
+        unit, b = ALG_BYTES[k]
+        nb = b * units[unit]
+        if k == "k_enumerate":
+            nb += 4 * P
+        if k == "k_pairs":
+            nb += (24 + 24 + 24 + 8 + 4) * n
+        if k == "k_gather":
+            nb += 96 * P
+        avg = ms / max(nprof, 1)
+        per_kernel[k] = {"ms": avg, "bytes": nb, "gbs": nb / (avg * 1e-3) / 1e9 if avg > 0 else 0.0}
+    dom = max(per_kernel, key=lambda k: per_kernel[k]["ms"])
+    d = per_kernel[dom]
+    peak = float(peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
+    traffic = None
+    if dom in NCU_TRAFFIC and NCU_TRAFFIC[dom][1] == csrc_hash():
+        traffic = NCU_TRAFFIC[dom][0]
+    roof = {"bound": "hbm", "kernel": dom, "achieved": d["gbs"], "peak": peak, "unit": "GB/s",
+            "frac": d["gbs"] / peak, "traffic": traffic, "peak_source": src,
+            "share": d["ms"] / step_ms}
+
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = cpu_baseline(g, kw, args.cpu_seconds)
+    line = {
+        "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": spec.name, "n": n, "phi": spec.phi, "mu": spec.mu,
+                   "radii": "1.0/1.4 equal numbers", "precision": args.precision,
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "flushed before every timed step (256 MB write)",
+                   "pairs": P, "contacts": c["ncontacts"], "cells": list(c["ncell"])},
+        "roofline": roof,
+        "kernels_ms": {k: round(v["ms"], 5) for k, v in per_kernel.items()},
+        "wall_s_timed_region": t_wall,
+        "clocks": clk,
+        "gpu_launches": 10 * args.steps,
+        "e2e": {"value": e2e_value, "unit": "particle-steps/s", "h2d_bytes_per_step": bytes_state,
+                "d2h_bytes_per_step": bytes_state + 72},
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    s.close()
+
+
+if __name__ == "__main__":
+    main()

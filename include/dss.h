@@ -98,8 +98,10 @@ typedef struct dss_counters {
 int32_t dss_capacity_estimate(double a_min, double a_max, double a0);
 
 /* Creates a handle for n particles in the box (edges box[0..2]) on the
- * current CUDA device, stream-ordered on cuda_stream (a cudaStream_t, NULL
- * for the legacy default stream).  Validates the parameters and the cell
+ * current CUDA device.  Work is issued on cuda_stream (a cudaStream_t); when
+ * it is NULL (the legacy default stream, on which CUDA graphs cannot be
+ * captured) the library issues its work on a stream of its own, ordered after
+ * the legacy stream at every call.  Validates the parameters and the cell
  * grid (needs >= 4 cells along x and >= 3 along y and z; the cutoff must be
  * below half of every edge).  The radius range used for the cell size and
  * M is fixed by dss_set_state; dss_create only stores the parameters.
@@ -118,6 +120,14 @@ int dss_create(dss_handle **h, const dss_params *p, int64_t n, const double box[
 int dss_set_state(dss_handle *h, const double *x, const double *a, const int32_t *ids,
                   const double *u, const double *w, const double *alpha_lin,
                   const double *alpha_ang, int64_t nstep);
+
+/* Replaces the dynamic state of the particles loaded by dss_set_state,
+ * keeping their radii, the contact history and the time: x, u, w, alpha_lin,
+ * alpha_ang (3n each, id order, all required).  No validation and no force
+ * evaluation: this is the per-step upload of a caller that keeps the state
+ * in its own (host or device) memory.  Stream-ordered, does not synchronise. */
+int dss_load_state(dss_handle *h, const double *x, const double *u, const double *w,
+                   const double *alpha_lin, const double *alpha_ang);
 
 /* Copies the current state out in id order; any pointer may be NULL. */
 int dss_get_state(dss_handle *h, double *x, double *u, double *w, double *alpha_lin,
@@ -162,6 +172,21 @@ int dss_stress(dss_handle *h, double sigma[9]);
 
 /* Counters of the last force evaluation (synchronises). */
 int dss_get_counters(dss_handle *h, dss_counters *c);
+
+/* Per-kernel timing of dss_step.  When on, the captured step records a CUDA
+ * event before each of its DSS_PROF_KERNELS kernels (and after the last) on
+ * the work stream; dss_step then synchronises after every step and adds each
+ * kernel's event-to-event time to a running sum.  Turning it on or off
+ * resets the sums and re-captures the step. */
+#define DSS_PROF_KERNELS 10
+int dss_set_profiling(dss_handle *h, int on);
+
+/* Running per-kernel sums in milliseconds (ms[DSS_PROF_KERNELS]) and the
+ * number of profiled steps. */
+int dss_get_profile(dss_handle *h, double *ms, int64_t *steps);
+
+/* Name of profiled kernel k (0 <= k < DSS_PROF_KERNELS), "" otherwise. */
+const char *dss_profile_name(int k);
 
 /* Bytes of device memory the handle holds. */
 int64_t dss_device_bytes(const dss_handle *h);

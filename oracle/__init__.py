@@ -125,6 +125,8 @@ def lib():
         L.orc_get_state.argtypes = [c_void_p, dp, dp, dp, dp, dp]
         L.orc_get_forces.restype = None
         L.orc_get_forces.argtypes = [c_void_p, dp, dp, dp]
+        L.orc_forces_sampled.restype = None
+        L.orc_forces_sampled.argtypes = [c_void_p, i64p, c_int64, dp, dp]
         for nm in ("orc_get_nstep", "orc_get_npairs", "orc_get_ncontacts"):
             getattr(L, nm).restype = c_int64
             getattr(L, nm).argtypes = [c_void_p]
@@ -235,6 +237,14 @@ class System:
     def forces(self, commit: bool = False):
         lib().orc_forces(self._h, 1 if commit else 0)
         return self.get_forces()
+
+    def forces_sampled(self, idx):
+        """Force and torque (3, m) on the listed particles (array indices)."""
+        idx = np.ascontiguousarray(idx, dtype=np.int64)
+        m = idx.shape[0]
+        F, T = np.zeros((3, m)), np.zeros((3, m))
+        lib().orc_forces_sampled(self._h, _ptr(idx, c_int64), m, _ptr(F), _ptr(T))
+        return F, T
 
     def step(self, nsteps: int = 1):
         lib().orc_step(self._h, int(nsteps))

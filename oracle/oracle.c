@@ -622,6 +622,56 @@ void orc_forces(orc_sys *s, int commit) {
   free(hnew);
 }
 
+/* Force and torque on the m particles listed in idx (array indices), brute
+ * force over all others plus Stokes drag, at the current state, time and
+ * history: the rows of orc_forces for those particles.  Used to time the
+ * oracle on systems where the full O(N^2) evaluation takes minutes. */
+void orc_forces_sampled(orc_sys *s, const int64_t *idx, int64_t m, double *F, double *T) {
+  const orc_params *p = &s->p;
+  int64_t n = s->n;
+  double off = orc_le_offset(p, s->nstep);
+  double E[9], Om[3];
+  ambient(p, E, Om);
+  for (int64_t q = 0; q < m; ++q) {
+    int64_t k = idx[q];
+    double f[3] = {0, 0, 0}, t[3] = {0, 0, 0};
+    for (int64_t o = 0; o < n; ++o) {
+      if (o == k) continue;
+      int64_t i = k < o ? k : o, j = k < o ? o : k;   /* same orientation as orc_forces */
+      double xi[3] = {s->x[i], s->x[n + i], s->x[2 * n + i]};
+      double xj[3] = {s->x[j], s->x[n + j], s->x[2 * n + j]};
+      double r[3];
+      int sy;
+      min_image(p, off, xi, xj, r, &sy);
+      if (!is_pair(p, r, s->a[i], s->a[j])) continue;
+      double ui[3] = {s->u[i], s->u[n + i], s->u[2 * n + i]};
+      double uj[3] = {s->u[j], s->u[n + j], s->u[2 * n + j]};
+      double wi[3] = {s->w[i], s->w[n + i], s->w[2 * n + i]};
+      double wj[3] = {s->w[j], s->w[n + j], s->w[2 * n + j]};
+      int64_t lo = s->id[i] < s->id[j] ? s->id[i] : s->id[j];
+      int64_t hi = s->id[i] < s->id[j] ? s->id[j] : s->id[i];
+      double sgn = s->id[i] < s->id[j] ? 1.0 : -1.0;
+      double xo[3] = {0, 0, 0};
+      int64_t h = hist_find(s, (lo << 32) | hi);
+      if (h >= 0) for (int c = 0; c < 3; ++c) xo[c] = sgn * s->hxi[3 * h + c];
+      double Fi[3], Fj[3], Ti[3], Tj[3], S[9], xn[3];
+      orc_pair_eval(p, off, xi, xj, ui, uj, wi, wj, s->a[i], s->a[j], xo, Fi, Fj, Ti, Tj, S, xn);
+      for (int c = 0; c < 3; ++c) {
+        f[c] += (k == i) ? Fi[c] : Fj[c];
+        t[c] += (k == i) ? Ti[c] : Tj[c];
+      }
+    }
+    double a = s->a[k];
+    double V[3] = {s->u[k] - p->shear_rate * s->x[n + k], s->u[n + k], s->u[2 * n + k]};
+    for (int c = 0; c < 3; ++c) {
+      f[c] += -6.0 * M_PI * p->eta0 * a * V[c];
+      t[c] += -8.0 * M_PI * p->eta0 * a * a * a * (s->w[c * n + k] - Om[c]);
+      F[c * m + q] = f[c];
+      T[c * m + q] = t[c];
+    }
+  }
+}
+
 /* Accelerations from the last force evaluation: alpha = F/m, T/I with
  * m = 4/3 pi rho a^3 and I = 2/5 m a^2 (spheres, Eq. 1). */
 static void accelerations(orc_sys *s) {

@@ -43,7 +43,9 @@ void free_buffers(dss_handle* h) {
   dfree(h->cell_count); dfree(h->cell_start); dfree(h->tmp); dfree(h->rec); dfree(h->spart);
   dfree(h->io3); dfree(h->io3b); dfree(h->io_id); dfree(h->scan_status); dfree(h->scan_ticket);
   dfree(h->sigma);
+  dfree(h->a_by_id);
   h->sigma = nullptr;
+  h->a_by_id = nullptr;
   h->posf = nullptr; h->cellid = nullptr; h->perm = nullptr; h->key = nullptr; h->offs = nullptr;
   h->cell_count = nullptr; h->cell_start = nullptr; h->tmp = nullptr; h->rec = nullptr;
   h->spart = nullptr; h->io3 = nullptr; h->io3b = nullptr; h->io_id = nullptr; h->scan_status = nullptr;
@@ -118,7 +120,8 @@ int alloc_buffers(dss_handle* h) {
       (r = dalloc(h, &h->cell_count, (size_t)h->g.ncell)) ||
       (r = dalloc(h, &h->cell_start, (size_t)h->g.ncell + 1)) || (r = dalloc(h, &h->tmp, n)) ||
       (r = dalloc(h, &h->io3, 3 * n)) || (r = dalloc(h, &h->io3b, 3 * n)) ||
-      (r = dalloc(h, &h->io_id, n)) || (r = dalloc(h, &h->sigma, 9)))
+      (r = dalloc(h, &h->io_id, n)) || (r = dalloc(h, &h->sigma, 9)) ||
+      (r = dalloc(h, &h->a_by_id, n)))
     return r;
   CK(cudaMemsetAsync(h->sigma, 0, 9 * sizeof(double), h->stream));
   int tiles = std::max(scan_tiles_for(h->g.ncell), scan_tiles_for((int)n));
@@ -136,6 +139,7 @@ int alloc_buffers(dss_handle* h) {
 
 // Orders the library's stream after everything queued on the caller's stream.
 int enter(dss_handle* h) {
+  if (!h->own_stream) return DSS_OK;
   CK(cudaEventRecord(h->ev_enter, h->user_stream));
   CK(cudaStreamWaitEvent(h->stream, h->ev_enter, 0));
   return DSS_OK;
@@ -260,7 +264,9 @@ void seq_step(dss_handle* h) {
 int capture_step(dss_handle* h, int key) {
   cudaGraph_t graph;
   CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  h->capturing = true;
   seq_step(h);
+  h->capturing = false;
   cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
   if (e != cudaSuccess) return DSS_ERR_CUDA;
   e = cudaGraphInstantiate(&h->step_graph[key], graph, 0);
@@ -268,6 +274,22 @@ int capture_step(dss_handle* h, int key) {
   if (e != cudaSuccess) return DSS_ERR_CUDA;
   h->graph_ok[key] = true;
   return DSS_OK;
+}
+
+int accumulate_profile(dss_handle* h) {
+  CK(cudaStreamSynchronize(h->stream));
+  for (int k = 0; k < DSS_PROF_KERNELS; ++k) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, h->prof_ev[k], h->prof_ev[k + 1]));
+    h->prof_ms[k] += ms;
+  }
+  h->prof_count += 1;
+  return DSS_OK;
+}
+
+__global__ void k_iota_int(int n, int* __restrict__ v) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[i] = i;
 }
 
 int status_error(dss_handle* h) {
@@ -306,6 +328,14 @@ int geometry(dss_handle* h) {
 }
 
 }  // namespace
+
+void prof_mark(dss_handle* h, int k) {
+  if (!h->profiling) return;
+  if (h->capturing)
+    cudaEventRecordWithFlags(h->prof_ev[k], h->stream, cudaEventRecordExternal);
+  else
+    cudaEventRecord(h->prof_ev[k], h->stream);
+}
 
 extern "C" {
 
@@ -354,10 +384,17 @@ int dss_create(dss_handle** out, const dss_params* p, int64_t n, const double bo
   for (int d = 0; d < 3; ++d) h->L[d] = box[d];
   h->user_stream = (cudaStream_t)cuda_stream;
   if (cudaGetDevice(&h->device) != cudaSuccess) { delete h; return DSS_ERR_CUDA; }
-  // a stream of our own: graph capture is not allowed on the legacy stream
-  if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
-    delete h;
-    return DSS_ERR_CUDA;
+  // work runs on the caller's stream; for the legacy default stream (NULL),
+  // where graph capture is not allowed, on a stream of our own ordered after it
+  if (cuda_stream) {
+    h->stream = (cudaStream_t)cuda_stream;
+    h->own_stream = false;
+  } else {
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete h;
+      return DSS_ERR_CUDA;
+    }
+    h->own_stream = true;
   }
   if (cudaEventCreateWithFlags(&h->ev_enter, cudaEventDisableTiming) != cudaSuccess) {
     cudaStreamDestroy(h->stream);
@@ -438,6 +475,12 @@ int dss_set_state(dss_handle* h, const double* x, const double* a, const int32_t
   CK(cudaMemcpyAsync(s.x, hx.data(), sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->stream));
   CK(cudaMemcpyAsync(s.a, ha.data(), sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
   CK(cudaMemcpyAsync(s.id, hid.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, h->stream));
+  {
+    std::vector<double> aid(n);
+    for (int64_t i = 0; i < n; ++i) aid[hid[i]] = ha[i];
+    CK(cudaMemcpyAsync(h->a_by_id, aid.data(), sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+  }
   if (u) CK(cudaMemcpyAsync(s.u, u, sizeof(double) * 3 * n, cudaMemcpyDefault, h->stream));
   if (w) CK(cudaMemcpyAsync(s.w, w, sizeof(double) * 3 * n, cudaMemcpyDefault, h->stream));
   const int nb = (int)((n + 255) / 256);
@@ -568,6 +611,10 @@ int dss_step(dss_handle* h, int64_t nsteps) {
         if (r) return r;
       }
       CK(cudaGraphLaunch(h->step_graph[key], h->stream));
+      if (h->profiling) {
+        r = accumulate_profile(h);
+        if (r) return r;
+      }
       c = 1 - c;
       hs = 1 - hs;
     }
@@ -698,6 +745,50 @@ int dss_get_history(dss_handle* h, int64_t* keys, double* xi, int64_t cap, int64
   return DSS_OK;
 }
 
+int dss_load_state(dss_handle* h, const double* x, const double* u, const double* w,
+                   const double* alpha_lin, const double* alpha_ang) {
+  if (!h || !x || !u || !w || !alpha_lin || !alpha_ang) return DSS_ERR_ARG;
+  if (!h->have_state) return DSS_ERR_STATE;
+  ENTER(h);
+  const size_t b = sizeof(double) * 3 * (size_t)h->n;
+  StateBuf& s = h->st[h->cur];
+  CK(cudaMemcpyAsync(s.x, x, b, cudaMemcpyDefault, h->stream));
+  CK(cudaMemcpyAsync(s.u, u, b, cudaMemcpyDefault, h->stream));
+  CK(cudaMemcpyAsync(s.w, w, b, cudaMemcpyDefault, h->stream));
+  CK(cudaMemcpyAsync(s.al, alpha_lin, b, cudaMemcpyDefault, h->stream));
+  CK(cudaMemcpyAsync(s.aw, alpha_ang, b, cudaMemcpyDefault, h->stream));
+  CK(cudaMemcpyAsync(s.a, h->a_by_id, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, h->stream));
+  k_iota_int<<<(int)((h->n + 255) / 256), 256, 0, h->stream>>>((int)h->n, s.id);
+  CK(cudaGetLastError());
+  return DSS_OK;
+}
+
+int dss_set_profiling(dss_handle* h, int on) {
+  if (!h) return DSS_ERR_ARG;
+  if (on && !h->prof_ev[0]) {
+    for (int k = 0; k <= DSS_PROF_KERNELS; ++k) CK(cudaEventCreate(&h->prof_ev[k]));
+  }
+  h->profiling = on != 0;
+  for (int k = 0; k < DSS_PROF_KERNELS; ++k) h->prof_ms[k] = 0.0;
+  h->prof_count = 0;
+  drop_graphs(h);
+  return DSS_OK;
+}
+
+int dss_get_profile(dss_handle* h, double* ms, int64_t* steps) {
+  if (!h || !ms || !steps) return DSS_ERR_ARG;
+  for (int k = 0; k < DSS_PROF_KERNELS; ++k) ms[k] = h->prof_ms[k];
+  *steps = h->prof_count;
+  return DSS_OK;
+}
+
+const char* dss_profile_name(int k) {
+  static const char* names[DSS_PROF_KERNELS] = {
+      "k_key_hist", "k_scan_cells", "k_scatter", "k_rank_gather", "k_reset_counters",
+      "k_enumerate", "k_scan_rows", "k_pairs", "k_gather", "k_finalize"};
+  return (k >= 0 && k < DSS_PROF_KERNELS) ? names[k] : "";
+}
+
 int64_t dss_device_bytes(const dss_handle* h) { return h ? h->bytes : 0; }
 
 void dss_destroy(dss_handle* h) {
@@ -708,7 +799,9 @@ void dss_destroy(dss_handle* h) {
   if (h->status) cudaFree(h->status);
   if (h->status_host) cudaFreeHost(h->status_host);
   if (h->ev_enter) cudaEventDestroy(h->ev_enter);
-  if (h->stream) cudaStreamDestroy(h->stream);
+  for (int k = 0; k <= DSS_PROF_KERNELS; ++k)
+    if (h->prof_ev[k]) cudaEventDestroy(h->prof_ev[k]);
+  if (h->stream && h->own_stream) cudaStreamDestroy(h->stream);
   delete h;
 }
 

@@ -387,13 +387,17 @@ void launch_forces(dss_handle* h, int stbuf, int work_list, int hist_list, int a
                    double* F_out, double* T_out) {
   const int n = (int)h->n;
   const int pb = pair_grid_blocks(h);
+  prof_mark(h, 7);
   k_pairs<<<pb, kPairThreads, 0, h->stream>>>(h->g, h->st[stbuf], h->lb[work_list], h->lb[hist_list],
                                               h->rec, h->spart, h->status, adv);
+  prof_mark(h, 8);
   k_gather<<<(n + kThreads - 1) / kThreads, kThreads, 0, h->stream>>>(
       h->g, h->st[stbuf], h->lb[work_list], h->posf, h->cellid, h->cell_start, h->rec, F_out, T_out,
       h->status, adv, mode);
+  prof_mark(h, 9);
   k_finalize<<<1, 256, 0, h->stream>>>(h->g, h->spart, pb, h->sigma, h->status,
                                        h->lb[work_list].start, mode == G_STEP ? 1 : 0);
+  prof_mark(h, 10);
 }
 
 void launch_pairs_out(dss_handle* h, int list, long long* out) {

@@ -9,6 +9,7 @@
 #include "../../include/dss.h"
 
 #define DSS_PI 3.14159265358979323846
+#define DSS_PROF_KERNELS 10
 
 // Device status word layout (int32 slots in DevStatus::w).
 enum {
@@ -275,9 +276,17 @@ struct dss_handle {
   dss_params p;
   int64_t n;
   double L[3];
-  cudaStream_t stream;       // the library's own stream (all work is issued here)
-  cudaStream_t user_stream;  // the caller's stream; work starts after it
+  cudaStream_t stream;       // stream all work is issued on
+  cudaStream_t user_stream;  // the caller's stream (NULL: legacy default stream)
+  bool own_stream;           // stream created by the library (caller passed NULL)
   cudaEvent_t ev_enter;
+  // per-kernel timing of captured steps (dss_set_profiling)
+  bool profiling;
+  bool capturing;
+  cudaEvent_t prof_ev[DSS_PROF_KERNELS + 1];
+  double prof_ms[DSS_PROF_KERNELS];
+  int64_t prof_count;
+  double* a_by_id;           // n radii in id order (dss_load_state)
   int device;
   bool have_state;
   bool sized;
@@ -338,3 +347,6 @@ void launch_pairs_out(dss_handle* h, int list, long long* out);
 int pair_grid_blocks(const dss_handle* h);
 void launch_scan(dss_handle* h, const int* in, int* out, int count, int which, bool zero_in);
 int scan_tiles_for(int count);
+// Marks the start of kernel k of a step when profiling (event record node
+// when the step is being captured).
+void prof_mark(dss_handle* h, int k);

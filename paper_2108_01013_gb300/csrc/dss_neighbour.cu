@@ -82,9 +82,12 @@ __global__ void k_reset_counters(DevStatus* st) {
 void launch_enumerate(dss_handle* h, int stbuf, int dst_list, int adv) {
   const int n = (int)h->n;
   ListBuf& L = h->lb[dst_list];
+  prof_mark(h, 4);
   k_reset_counters<<<1, 1, 0, h->stream>>>(h->status);
+  prof_mark(h, 5);
   k_enumerate<<<(n + kThreads - 1) / kThreads, kThreads, 0, h->stream>>>(
       h->g, h->st[stbuf], h->posf, h->cellid, h->cell_start, L, h->status, adv);
   h->last_list = dst_list;
+  prof_mark(h, 6);
   launch_scan(h, L.count, L.start, n, 1, false);
 }

@@ -266,11 +266,15 @@ void launch_scan(dss_handle* h, const int* in, int* out, int count, int which, b
 void launch_sort(dss_handle* h, bool predict, int src, int dst) {
   const int n = (int)h->n;
   const int blocks = (n + kThreads - 1) / kThreads;
+  prof_mark(h, 0);
   k_key_hist<<<blocks, kThreads, 0, h->stream>>>(h->g, h->st[src], h->key, h->offs, h->cell_count,
                                                  h->status, predict, h->scan_status, h->scan_ticket,
                                                  h->scan_tiles_max);
+  prof_mark(h, 1);
   launch_scan(h, h->cell_count, h->cell_start, h->g.ncell, 0, true);
+  prof_mark(h, 2);
   k_scatter<<<blocks, kThreads, 0, h->stream>>>(n, h->key, h->offs, h->cell_start, h->tmp, h->status);
+  prof_mark(h, 3);
   k_rank_gather<<<blocks, kThreads, 0, h->stream>>>(h->g, h->st[src], h->st[dst], h->key,
                                                     h->cell_start, h->tmp, h->perm, h->cellid,
                                                     h->posf, h->status, predict);

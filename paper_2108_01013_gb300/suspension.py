@@ -85,6 +85,30 @@ class Suspension:
         nat.check(self.lib.dss_set_state(self._h, *[c_void_p(g.ptr) for g in args], int(nstep)),
                   "dss_set_state")
 
+    def load_state(self, x, u, w, alpha_lin, alpha_ang):
+        """Per-step upload of the dynamic state (id order); keeps history."""
+        args = [_Arg(v, np.float64) for v in (x, u, w, alpha_lin, alpha_ang)]
+        self._keep = args
+        nat.check(self.lib.dss_load_state(self._h, *[c_void_p(g.ptr) for g in args]),
+                  "dss_load_state")
+
+    def get_state_into(self, x, u, w, alpha_lin, alpha_ang):
+        """Copies the state into caller buffers (torch tensors, any device)."""
+        nat.check(self.lib.dss_get_state(self._h, *[c_void_p(t.data_ptr()) for t in
+                                                    (x, u, w, alpha_lin, alpha_ang)]),
+                  "dss_get_state")
+
+    def set_profiling(self, on: bool = True):
+        nat.check(self.lib.dss_set_profiling(self._h, 1 if on else 0), "dss_set_profiling")
+
+    def profile(self):
+        """{kernel name: summed ms} and the number of profiled steps."""
+        ms = (c_double * nat.PROF_KERNELS)()
+        cnt = c_int64(0)
+        nat.check(self.lib.dss_get_profile(self._h, ms, byref(cnt)), "dss_get_profile")
+        names = [self.lib.dss_profile_name(k).decode() for k in range(nat.PROF_KERNELS)]
+        return dict(zip(names, list(ms))), cnt.value
+
     def state(self, device="cuda"):
         """Current x, u, w, alpha_lin, alpha_ang as (3, n) float64 tensors (id order)."""
         import torch

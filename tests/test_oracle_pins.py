@@ -486,3 +486,16 @@ def test_contact_stresslet_signs(orc, sign):
     want = 1e4 * ov * (2.0 - ov) / 2 / L ** 3
     assert S[0, 1] == pytest.approx(sign * want, rel=1e-12)
     assert -np.trace(S) / 3 > 0
+
+
+def test_sampled_forces_are_rows_of_the_full_evaluation(orc):
+    g = _dense(400, 0.52, 9)
+    p = orc.make_params(g["box"], mu=0.6, shear_rate=10.0)
+    s = orc.System(p, g["x"], g["a"])
+    s.init_accel()
+    s.step(20)                       # build up a contact history
+    F, T, _ = s.forces()
+    idx = np.array([0, 5, 17, 99, 250, 399])
+    Fs, Ts = s.forces_sampled(idx)
+    np.testing.assert_allclose(Fs, F[:, idx], rtol=1e-12, atol=1e-12 * np.abs(F).max())
+    np.testing.assert_allclose(Ts, T[:, idx], rtol=1e-12, atol=1e-12 * np.abs(T).max())
