@@ -53,7 +53,8 @@ enum dss_status {
   DSS_ERR_CUDA = -6,       /* CUDA runtime error */
   DSS_ERR_TIMEOUT = -7,    /* a bounded device-side wait gave up */
   DSS_ERR_STATE = -8,      /* call order (e.g. dss_step before dss_set_state) */
-  DSS_ERR_INTERNAL = -9    /* internal consistency check failed on the device */
+  DSS_ERR_INTERNAL = -9,   /* internal consistency check failed on the device */
+  DSS_ERR_SCRATCH_LIMIT = -10  /* dss_pairs_noalloc: problem larger than its fixed scratch array */
 };
 
 enum dss_precision {
@@ -193,6 +194,43 @@ int64_t dss_device_bytes(const dss_handle *h);
 
 void dss_destroy(dss_handle *h);
 const char *dss_strerror(int code);
+
+/* ---- Neighbour pairs without any device allocation ----------------------
+ * The paper has no counterpart of this entry point.  It exists for callers
+ * that may not allocate GPU memory themselves or through us: code embedded in
+ * a host application that owns every device allocation (a plugin inside
+ * another framework's memory pool), or a process whose device memory is
+ * fully reserved in advance.  Every other entry point allocates its buffers
+ * in dss_create / dss_set_state; this one calls no cudaMalloc, cudaFree or
+ * allocating library routine.
+ *
+ * It computes the same pair set as dss_neighbour_build + dss_get_pairs for
+ * the state (x, a, ids) at time nstep*dt, with the parameters p (only the
+ * cutoff fields and gdot, dt are used): every pair with
+ * r^2 < (a_i + a_j + delta_ij)^2 under Lees-Edwards minimum images, written
+ * as (lo id, hi id) into pairs[2*k], pairs[2*k+1] in no particular order.
+ *
+ * Arguments: x (3n, SoA, inside [0, L)), a (n), ids (n, or NULL for k -> k)
+ * and pairs (2*cap int64) are DEVICE memory of the current device; box,
+ * p and count are host memory.  a_max must bound every radius from above
+ * (it sets the cell size; a larger radius returns DSS_ERR_ARG).  *count
+ * receives the number of pairs; at most cap are written.  The call is
+ * ordered on cuda_stream (NULL: legacy stream) and synchronises it.
+ *
+ * Working memory: one file-scope __device__ array of DSS_NOALLOC_SCRATCH_INTS
+ * 32-bit words (8 MiB), which every GPU that loads the library holds until
+ * the process exits.  A problem needs n + 3*cells + 17 words (cells: the
+ * cell grid of edge >= 2 a_max + max delta_ij); larger problems are rejected
+ * with DSS_ERR_SCRATCH_LIMIT.  All calls share the array and each call clears
+ * what it needs at its start, so calls whose GPU work overlaps (on different
+ * streams, or from several host threads) race and must be serialised by the
+ * caller.  The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress, with that device current); make that first
+ * call outside any stream capture. */
+#define DSS_NOALLOC_SCRATCH_INTS (1 << 21)
+int dss_pairs_noalloc(const double *x, const double *a, const int32_t *ids, int64_t n,
+                      const double box[3], const dss_params *p, double a_max, int64_t nstep,
+                      int64_t *pairs, int64_t cap, int64_t *count, void *cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -18,7 +18,7 @@ _CSRC = os.path.join(_HERE, "csrc")
 _BUILD = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(_BUILD, "libdss.so")
 INCLUDE = os.path.join(os.path.dirname(_HERE), "include")
-SOURCES = ["dss_sort.cu", "dss_neighbour.cu", "dss_force.cu", "dss_api.cu"]
+SOURCES = ["dss_sort.cu", "dss_neighbour.cu", "dss_force.cu", "dss_api.cu", "dss_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v"]
 
@@ -86,7 +86,8 @@ FP64, MIXED = 0, 1
 PROF_KERNELS = 10
 ERRORS = {0: "DSS_OK", -1: "DSS_ERR_ARG", -2: "DSS_ERR_BOX", -3: "DSS_ERR_CAPACITY",
           -4: "DSS_ERR_NONFINITE", -5: "DSS_ERR_UNSTABLE", -6: "DSS_ERR_CUDA",
-          -7: "DSS_ERR_TIMEOUT", -8: "DSS_ERR_STATE", -9: "DSS_ERR_INTERNAL"}
+          -7: "DSS_ERR_TIMEOUT", -8: "DSS_ERR_STATE", -9: "DSS_ERR_INTERNAL",
+          -10: "DSS_ERR_SCRATCH_LIMIT"}
 
 # every symbol include/dss.h declares, with (restype, argtypes)
 _dp, _ip, _lp, _vp = POINTER(c_double), POINTER(c_int32), POINTER(c_int64), c_void_p
@@ -110,6 +111,8 @@ SIGNATURES = {
     "dss_device_bytes": (c_int64, [c_void_p]),
     "dss_destroy": (None, [c_void_p]),
     "dss_strerror": (c_char_p, [c_int]),
+    "dss_pairs_noalloc": (c_int, [_vp, _vp, _vp, c_int64, _dp, POINTER(Params), c_double, c_int64,
+                                  _vp, c_int64, _lp, c_void_p]),
 }
 
 _lib = None

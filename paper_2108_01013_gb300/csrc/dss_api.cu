@@ -362,6 +362,9 @@ const char* dss_strerror(int code) {
     case DSS_ERR_TIMEOUT: return "bounded device wait gave up";
     case DSS_ERR_STATE: return "call out of order (no state loaded)";
     case DSS_ERR_INTERNAL: return "internal consistency check failed";
+    case DSS_ERR_SCRATCH_LIMIT:
+      return "problem too large for the fixed scratch array of dss_pairs_noalloc "
+             "(needs n + 3*cells + 17 <= DSS_NOALLOC_SCRATCH_INTS words)";
     default: return "unknown error";
   }
 }
