@@ -39,23 +39,22 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 METRIC = "particle-timesteps/s"
 L2_FLUSH_BYTES = 256 << 20
 
-# Algorithmic bytes per launch unit of each kernel (FP64 state), the minimum
-# traffic the step's definition needs: every particle's state read and the
-# permuted state written once, pair list and per-pair records written and
-# read once, history read/written per contact.  Units: particles (n), cells
-# (c) or pairs (p).  See the design notes for the derivation.
+# Algorithmic bytes of each kernel: the minimum traffic its definition
+# needs (every input read once, every output written once).  Per particle
+# (n), per cell (c), per listed pair (p) and per contact (k); values for FP64
+# and mixed precision (FP32 records).  The derivation is in the design notes.
 ALG_BYTES = {
-    "k_key_hist": ("n", 72 + 8),          # x, u, alpha read; key, offset written
-    "k_scan_cells": ("c", 12),            # count read + zeroed, start written
-    "k_scatter": ("n", 16),               # key, offset, start read; slot written
-    "k_rank_gather": ("n", 136 + 124),    # state gathered (x,u,w,al,aw,a,id) -> x,u,w,a,id,perm,cell,posf
-    "k_reset_counters": ("n", 0),
-    "k_enumerate": ("n", 16 + 4 + 8),     # own posf, count, id maps (+4 per pair written)
-    "k_scan_rows": ("n", 8),
-    "k_pairs": ("p", 4 + 72 + 24 + 1),    # list entry; record F,Ti,Tj; stretch; flag (+ state per n)
-    "k_gather": ("n", 56 + 96),           # x,u,w,a read; u,w,al,aw written (+96 per pair of records)
-    "k_finalize": ("n", 0),
+    #                  fp64 (n, c, p, k)      mixed (n, c, p, k)
+    "k_key_hist":    ((84, 0, 0, 0),        (84, 0, 0, 0)),
+    "k_scan_cells":  ((0, 12, 0, 0),        (0, 12, 0, 0)),
+    "k_scatter":     ((16, 0, 0, 0),        (16, 0, 0, 0)),
+    "k_rank_gather": ((260, 0, 0, 0),       (292, 0, 0, 0)),
+    "k_enumerate":   ((52, 8, 4, 0),        (52, 8, 4, 0)),
+    "k_pairs":       ((140, 0, 93, 40),     (100, 0, 61, 40)),
+    "k_gather":      ((216, 0, 64, 0),      (216, 0, 32, 0)),
+    "k_finalize":    ((0, 0, 0, 0),         (0, 0, 0, 0)),
 }
+KERNELS_PER_STEP = len(ALG_BYTES)
 
 # DRAM traffic per launch from an ncu capture of the named kernel (bytes), and
 # the hash of the CUDA sources it was taken on; reported only while the
@@ -300,17 +299,11 @@ def main():
     peaks, src = load_peaks()
     P = c["npairs"]
     ncell = int(np.prod(c["ncell"]))
-    units = {"n": n, "c": ncell, "p": P}
     per_kernel = {}
+    mode = 0 if args.precision == "fp64" else 1
     for k, ms in prof.items():
-        unit, b = ALG_BYTES[k]
-        nb = b * units[unit]
-        if k == "k_enumerate":
-            nb += 4 * P
-        if k == "k_pairs":
-            nb += (24 + 24 + 24 + 8 + 4) * n
-        if k == "k_gather":
-            nb += 96 * P
+        bn, bc, bp, bk = ALG_BYTES[k][mode]
+        nb = bn * n + bc * ncell + bp * P + bk * c["ncontacts"]
         avg = ms / max(nprof, 1)
         per_kernel[k] = {"ms": avg, "bytes": nb, "gbs": nb / (avg * 1e-3) / 1e9 if avg > 0 else 0.0}
     dom = max(per_kernel, key=lambda k: per_kernel[k]["ms"])
@@ -343,7 +336,7 @@ def main():
         "kernels_ms": {k: round(v["ms"], 5) for k, v in per_kernel.items()},
         "wall_s_timed_region": t_wall,
         "clocks": clk,
-        "gpu_launches": 10 * args.steps,
+        "gpu_launches": KERNELS_PER_STEP * args.steps,
         "e2e": {"value": e2e_value, "unit": "particle-steps/s", "h2d_bytes_per_step": bytes_state,
                 "d2h_bytes_per_step": bytes_state + 72},
         "cpu_baseline": cpu,

@@ -179,7 +179,7 @@ int dss_get_counters(dss_handle *h, dss_counters *c);
  * the work stream; dss_step then synchronises after every step and adds each
  * kernel's event-to-event time to a running sum.  Turning it on or off
  * resets the sums and re-captures the step. */
-#define DSS_PROF_KERNELS 10
+#define DSS_PROF_KERNELS 8
 int dss_set_profiling(dss_handle *h, int on);
 
 /* Running per-kernel sums in milliseconds (ms[DSS_PROF_KERNELS]) and the

@@ -83,7 +83,7 @@ class Counters(Structure):
 
 
 FP64, MIXED = 0, 1
-PROF_KERNELS = 10
+PROF_KERNELS = 8
 ERRORS = {0: "DSS_OK", -1: "DSS_ERR_ARG", -2: "DSS_ERR_BOX", -3: "DSS_ERR_CAPACITY",
           -4: "DSS_ERR_NONFINITE", -5: "DSS_ERR_UNSTABLE", -6: "DSS_ERR_CUDA",
           -7: "DSS_ERR_TIMEOUT", -8: "DSS_ERR_STATE", -9: "DSS_ERR_INTERNAL",

@@ -33,6 +33,7 @@ void free_buffers(dss_handle* h) {
   for (int b = 0; b < 2; ++b) {
     StateBuf& s = h->st[b];
     dfree(s.x); dfree(s.u); dfree(s.w); dfree(s.al); dfree(s.aw); dfree(s.a); dfree(s.id);
+    dfree(s.vf); dfree(s.wf);
     memset(&s, 0, sizeof(s));
     ListBuf& L = h->lb[b];
     dfree(L.count); dfree(L.list); dfree(L.start); dfree(L.xi); dfree(L.cflag); dfree(L.slot_of_id);
@@ -40,14 +41,16 @@ void free_buffers(dss_handle* h) {
     memset(&L, 0, sizeof(L));
   }
   dfree(h->posf); dfree(h->cellid); dfree(h->perm); dfree(h->key); dfree(h->offs);
-  dfree(h->cell_count); dfree(h->cell_start); dfree(h->tmp); dfree(h->rec); dfree(h->spart);
+  dfree(h->cell_count); dfree(h->cell_start); dfree(h->tmp); dfree(h->spart);
+  dfree(h->own); dfree(h->bw_count); dfree(h->bw_rec);
+  h->own = nullptr; h->bw_count = nullptr; h->bw_rec = nullptr;
   dfree(h->io3); dfree(h->io3b); dfree(h->io_id); dfree(h->scan_status); dfree(h->scan_ticket);
   dfree(h->sigma);
   dfree(h->a_by_id);
   h->sigma = nullptr;
   h->a_by_id = nullptr;
   h->posf = nullptr; h->cellid = nullptr; h->perm = nullptr; h->key = nullptr; h->offs = nullptr;
-  h->cell_count = nullptr; h->cell_start = nullptr; h->tmp = nullptr; h->rec = nullptr;
+  h->cell_count = nullptr; h->cell_start = nullptr; h->tmp = nullptr;
   h->spart = nullptr; h->io3 = nullptr; h->io3b = nullptr; h->io_id = nullptr; h->scan_status = nullptr;
   h->scan_ticket = nullptr;
   h->bytes = 0;
@@ -65,11 +68,7 @@ void drop_graphs(dss_handle* h) {
 // stress partials.  keep_hist copies the committed history's pair arrays.
 int alloc_pair_buffers(dss_handle* h, int64_t pcap, bool keep_hist) {
   const int64_t old = h->pcap;
-  double* rec = nullptr;
-  int r = dalloc(h, &rec, 9 * (size_t)pcap);
-  if (r) return r;
-  dfree(h->rec);
-  h->rec = rec;
+  int r;
   for (int b = 0; b < 2; ++b) {
     ListBuf& L = h->lb[b];
     double* xi = nullptr;
@@ -109,6 +108,9 @@ int alloc_buffers(dss_handle* h) {
         (r = dalloc(h, &s.al, 3 * n)) || (r = dalloc(h, &s.aw, 3 * n)) || (r = dalloc(h, &s.a, n)) ||
         (r = dalloc(h, &s.id, n)))
       return r;
+    if (h->p.precision == DSS_MIXED &&
+        ((r = dalloc(h, &s.vf, n)) || (r = dalloc(h, &s.wf, n))))
+      return r;
     ListBuf& L = h->lb[b];
     if ((r = dalloc(h, &L.count, n)) || (r = dalloc(h, &L.list, n * (size_t)h->g.M)) ||
         (r = dalloc(h, &L.start, n + 1)) || (r = dalloc(h, &L.slot_of_id, n)) ||
@@ -124,7 +126,17 @@ int alloc_buffers(dss_handle* h) {
       (r = dalloc(h, &h->a_by_id, n)))
     return r;
   CK(cudaMemsetAsync(h->sigma, 0, 9 * sizeof(double), h->stream));
-  int tiles = std::max(scan_tiles_for(h->g.ncell), scan_tiles_for((int)n));
+  {
+    const size_t rb = h->p.precision == DSS_MIXED ? sizeof(float) : sizeof(double);
+    char* own = nullptr;
+    char* bwr = nullptr;
+    if ((r = dalloc(h, &own, 6 * n * rb)) || (r = dalloc(h, &h->bw_count, n)) ||
+        (r = dalloc(h, &bwr, n * (size_t)h->g.M * bw_slot_values() * rb)))
+      return r;
+    h->own = own;
+    h->bw_rec = bwr;
+  }
+  int tiles = std::max(scan_tiles_for(h->g.ncell), enum_tiles_for((int)n));
   h->scan_tiles_max = std::max(tiles, 1);
   if ((r = dalloc(h, &h->scan_status, 2 * (size_t)h->scan_tiles_max)) ||
       (r = dalloc(h, &h->scan_ticket, 2)))
@@ -315,6 +327,8 @@ int geometry(dss_handle* h) {
     g.cs[d] = h->L[d] / g.nc[d];
     g.inv_cs[d] = 1.0 / g.cs[d];
     g.halfLf[d] = (float)(0.5 * h->L[d]) * (1.0f - 1e-5f);
+    g.csf[d] = (float)g.cs[d];
+    g.invL[d] = 1.0 / h->L[d];
   }
   if (g.nc[0] < 4 || g.nc[1] < 3 || g.nc[2] < 3) return DSS_ERR_BOX;
   if ((double)g.nc[0] * g.nc[1] * g.nc[2] > 2.0e9) return DSS_ERR_ARG;
@@ -559,7 +573,8 @@ int dss_get_pairs(dss_handle* h, int64_t* lohi, int64_t cap, int64_t* count) {
   *count = P;
   if (P == 0 || cap == 0) return DSS_OK;
   if (P > h->pcap) return DSS_ERR_CAPACITY;
-  long long* dev = (long long*)h->rec;   // scratch: 9*pcap doubles >= 2*P int64
+  // scratch: the partner-row buffer (n*M slots of >= 32 bytes >= 16 bytes per pair)
+  long long* dev = (long long*)h->bw_rec;
   launch_pairs_out(h, list, dev);
   std::vector<long long> hp(2 * (size_t)P);
   CK(cudaMemcpyAsync(hp.data(), dev, sizeof(long long) * 2 * P, cudaMemcpyDeviceToHost, h->stream));
@@ -786,9 +801,9 @@ int dss_get_profile(dss_handle* h, double* ms, int64_t* steps) {
 }
 
 const char* dss_profile_name(int k) {
-  static const char* names[DSS_PROF_KERNELS] = {
-      "k_key_hist", "k_scan_cells", "k_scatter", "k_rank_gather", "k_reset_counters",
-      "k_enumerate", "k_scan_rows", "k_pairs", "k_gather", "k_finalize"};
+  static const char* names[DSS_PROF_KERNELS] = {"k_key_hist", "k_scan_cells", "k_scatter",
+                                                  "k_rank_gather", "k_enumerate", "k_pairs",
+                                                  "k_gather", "k_finalize"};
   return (k >= 0 && k < DSS_PROF_KERNELS) ? names[k] : "";
 }
 

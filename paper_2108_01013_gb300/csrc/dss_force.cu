@@ -1,32 +1,35 @@
-// Pair forces and their deterministic accumulation.
+// Pair forces and their deterministic symmetric accumulation.
 //
-// k_pairs: one thread per listed pair (owner-sorted order).  Lubrication of
+// k_pairs<MIXED>: a warp takes 32 consecutive owners and deals out their
+//   listed pairs (owner-sorted) 32 at a time.  Per pair: lubrication of
 //   App. A (Eq. A2, A3 with the coefficients of Eq. A6, A7 and the
 //   6 pi eta0 prefactor), stick-and-slide contact of Eq. 4-5 with the
-//   tangential stretch carried from the previous step's sorted rows, and the
-//   pair stresslet of Eq. 9, reduced per block in a fixed order.  The
-//   per-pair records (force on the owner, torques on owner and partner) go
-//   to memory; nothing is accumulated with atomics.
-// k_gather: one thread per particle.  Sums its own records (its row, in
-//   order) and the records where it is the partner (found by the mirrored
-//   backward half-stencil, in increasing owner order: the transposed index),
-//   adds Stokes drag (Eq. A1) and applies the corrector of Eq. 15d.
-// k_finalize: bulk stress of Eq. 8 from the block partials, step counters.
+//   tangential stretch carried from the previous step's rows, and the pair
+//   stresslet of Eq. 9.  The owner's share is summed by a warp-segmented
+//   reduction (lanes holding the same owner are contiguous) into a per-warp
+//   shared-memory accumulator and written once per owner; the partner's share
+//   (-F and its torque) is appended to the partner's fixed-capacity row
+//   together with the owner's index.  No float is ever accumulated with an
+//   atomic.
+// k_gather<MIXED>: one thread per particle: its own sum plus the partner
+//   records of its row taken in increasing owner index (a fixed order, so the
+//   result is bitwise reproducible), Stokes drag (Eq. A1) and the corrector
+//   of Eq. 15d.
+// k_finalize: bulk stress of Eq. 8 from the per-block partials.
+#include <climits>
+
 #include "dss_internal.cuh"
 
 namespace {
 constexpr int kPairThreads = 256;
+constexpr int kWarps = kPairThreads / 32;
 constexpr int kThreads = 128;
+constexpr int kSlot = 8;   // partner-row slot: F (3), T (3), owner index, pad
 
-// Binary search of `target` in a sorted row; -1 when absent.
+// Position of `target` in a row (rows are in stencil visiting order); -1 if absent.
 __device__ __forceinline__ int row_find(const int* row, int cnt, int target) {
-  int lo = 0, hi = cnt - 1;
-  while (lo <= hi) {
-    int mid = (lo + hi) >> 1;
-    int v = row[mid];
-    if (v == target) return mid;
-    if (v < target) lo = mid + 1; else hi = mid - 1;
-  }
+  for (int k = 0; k < cnt; ++k)
+    if (row[k] == target) return k;
   return -1;
 }
 
@@ -141,10 +144,194 @@ __device__ __forceinline__ PairOut pair_fp64(const Geo& g, V3 r, double rr, doub
   return o;
 }
 
+struct F3 {
+  float x, y, z;
+};
+__device__ __forceinline__ F3 f3(float a, float b, float c) { return F3{a, b, c}; }
+__device__ __forceinline__ F3 operator+(F3 a, F3 b) { return f3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ F3 operator-(F3 a, F3 b) { return f3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ F3 operator*(float s, F3 a) { return f3(s * a.x, s * a.y, s * a.z); }
+__device__ __forceinline__ float dotf(F3 a, F3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ F3 crossf(F3 a, F3 b) {
+  return f3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ F3 tangf(F3 n, F3 v) { return v - dotf(n, v) * n; }
+
+
+// Result of one pair in the arithmetic precision R.
+template <typename R>
+struct PairRes {
+  R F[3], Ti[3], Tj[3], Fc[3], Fl[3], r[3];
+  double xi[3];
+  int contact;
+};
+
+// FP64 pair from the state (exact FP64 throughout).
+__device__ __forceinline__ PairRes<double> pair_eval_fp64(const Geo& g, const StateBuf& s, const ListBuf& H,
+                                                         double off, int i, int j) {
+  const int n = g.n;
+  const double xi = s.x[i], yi = s.x[n + i], zi = s.x[2 * n + i];
+  const double xj = s.x[j], yj = s.x[n + j], zj = s.x[2 * n + j];
+  double dx, dy, dz;
+  int sy;
+  min_image(g, off, xi, yi, zi, xj, yj, zj, dx, dy, dz, sy);
+  const V3 r = v3(dx, dy, dz);
+  const double ai = s.a[i], aj = s.a[j];
+  const V3 ui = v3(s.u[i], s.u[n + i], s.u[2 * n + i]);
+  const V3 uj = v3(s.u[j], s.u[n + j], s.u[2 * n + j]);
+  const V3 wi = v3(s.w[i], s.w[n + i], s.w[2 * n + i]);
+  const V3 wj = v3(s.w[j], s.w[n + j], s.w[2 * n + j]);
+  const int idi = s.id[i], idj = s.id[j];
+  const double sgn = idi < idj ? 1.0 : -1.0;
+  double xo[3] = {0.0, 0.0, 0.0};
+  const double rr = sqrt(dot(r, r));
+  if (rr - (ai + aj) < 0.0) {
+    history_lookup(g, H, idi, idj, xo);
+    xo[0] *= sgn; xo[1] *= sgn; xo[2] *= sgn;
+  }
+  const double Om = -0.5 * g.gdot;
+  const V3 Vi = v3(ui.x - g.gdot * yi, ui.y, ui.z);
+  const V3 Vj = v3(uj.x - g.gdot * yj, uj.y, uj.z);
+  const V3 Wi = v3(wi.x, wi.y, wi.z - Om);
+  const V3 Wj = v3(wj.x, wj.y, wj.z - Om);
+  const V3 du = v3(uj.x + sy * g.gdot * g.L[1] - ui.x, uj.y - ui.y, uj.z - ui.z);
+  const PairOut o = pair_fp64(g, r, rr, ai, aj, Vi, Vj, Wi, Wj, du, wi, wj, xo);
+  PairRes<double> q;
+  q.F[0] = o.F.x; q.F[1] = o.F.y; q.F[2] = o.F.z;
+  q.Ti[0] = o.Ti.x; q.Ti[1] = o.Ti.y; q.Ti[2] = o.Ti.z;
+  q.Tj[0] = o.Tj.x; q.Tj[1] = o.Tj.y; q.Tj[2] = o.Tj.z;
+  q.Fc[0] = o.Fc.x; q.Fc[1] = o.Fc.y; q.Fc[2] = o.Fc.z;
+  q.Fl[0] = o.Fl.x; q.Fl[1] = o.Fl.y; q.Fl[2] = o.Fl.z;
+  q.r[0] = dx; q.r[1] = dy; q.r[2] = dz;
+  q.xi[0] = sgn * o.xi.x; q.xi[1] = sgn * o.xi.y; q.xi[2] = sgn * o.xi.z;
+  q.contact = o.contact;
+  return q;
+}
+
+// Mixed precision.  The separation and the gap numerator r^2 - S^2 are taken
+// in FP64 from the FP64 positions (the lubrication coefficients diverge as
+// 1/(d* + eps), so the gap needs far more than FP32's 7 digits); the gap is
+// then d = (r^2 - S^2)/(r + S) with the division in FP32.  The tangential
+// stretch is carried and updated in FP64; the rest of the pair arithmetic is
+// FP32, on velocities taken relative to the ambient flow.
+__device__ __forceinline__ PairRes<float> pair_eval_mixed(const Geo& g, const StateBuf& s, const ListBuf& H,
+                                                         double off, int i, int j) {
+  const int n = g.n;
+  const float gd = (float)g.gdot;
+  const float k6 = (float)g.k6;
+  double dx = s.x[j] - s.x[i];
+  double dy = s.x[n + j] - s.x[n + i];
+  double dz = s.x[2 * n + j] - s.x[2 * n + i];
+  if (dy > g.halfL[1]) { dy -= g.L[1]; dx -= off; }
+  else if (dy < -g.halfL[1]) { dy += g.L[1]; dx += off; }
+  if (dx > g.halfL[0]) dx -= g.L[0]; else if (dx < -g.halfL[0]) dx += g.L[0];
+  if (dx > g.halfL[0]) dx -= g.L[0]; else if (dx < -g.halfL[0]) dx += g.L[0];
+  if (dz > g.halfL[2]) dz -= g.L[2]; else if (dz < -g.halfL[2]) dz += g.L[2];
+  const double ai = s.a[i], aj = s.a[j];
+  const double S64 = ai + aj;
+  const double r2 = dx * dx + dy * dy + dz * dz;
+  const double num = r2 - S64 * S64;            // (r - S)(r + S) to FP64 rounding
+  const float rr = sqrtf((float)r2);
+  const float S = (float)S64;
+  const float d = (float)num / (rr + S);
+  const float ir = 1.0f / rr;
+  const F3 r = f3((float)dx, (float)dy, (float)dz);
+  const F3 nn = ir * r;
+  const float4 vi4 = s.vf[i], vj4 = s.vf[j], wi4 = s.wf[i], wj4 = s.wf[j];
+  const F3 Vi = f3(vi4.x, vi4.y, vi4.z), Vj = f3(vj4.x, vj4.y, vj4.z);
+  const F3 Wi = f3(wi4.x, wi4.y, wi4.z), Wj = f3(wj4.x, wj4.y, wj4.z);
+  const float Ai = (float)ai, Bj = (float)aj;
+  PairRes<float> q;
+  // ---- contact, Eq. 4-5
+  F3 Fc = f3(0, 0, 0), nxf = f3(0, 0, 0);
+  q.xi[0] = q.xi[1] = q.xi[2] = 0.0;
+  q.contact = num < 0.0;
+  if (q.contact) {
+    const int idi = s.id[i], idj = s.id[j];
+    const double sgn = idi < idj ? 1.0 : -1.0;
+    double xo[3];
+    history_lookup(g, H, idi, idj, xo);
+    // u_j(image) - u_i = (V_j - V_i) + gdot dy x
+    const F3 du = (Vj - Vi) + f3(gd * (float)dy, 0.f, 0.f);
+    const F3 wi = f3(Wi.x, Wi.y, Wi.z - 0.5f * gd), wj = f3(Wj.x, Wj.y, Wj.z - 0.5f * gd);
+    const float fn = (float)g.kn * d + (float)g.gn * dotf(nn, du);
+    const F3 ut = tangf(nn, du - crossf(Ai * wi + Bj * wj, nn));
+    const double n0 = nn.x, n1 = nn.y, n2 = nn.z;
+    const double x0 = sgn * xo[0], x1 = sgn * xo[1], x2 = sgn * xo[2];
+    const double pn = n0 * x0 + n1 * x1 + n2 * x2;
+    double xs0 = x0 - pn * n0 + (double)(ut.x * (float)g.dt);
+    double xs1 = x1 - pn * n1 + (double)(ut.y * (float)g.dt);
+    double xs2 = x2 - pn * n2 + (double)(ut.z * (float)g.dt);
+    const double cap = g.mu * fabs((double)fn) / g.kt;
+    const double xm2 = xs0 * xs0 + xs1 * xs1 + xs2 * xs2;
+    if (xm2 > cap * cap) {
+      const double f = cap / sqrt(xm2);
+      xs0 *= f; xs1 *= f; xs2 *= f;
+    }
+    const F3 Ft = (float)g.kt * f3((float)xs0, (float)xs1, (float)xs2);
+    Fc = fn * nn + Ft;
+    nxf = crossf(nn, Ft);
+    q.xi[0] = sgn * xs0; q.xi[1] = sgn * xs1; q.xi[2] = sgn * xs2;
+  }
+  // ---- lubrication, App. A (FP32)
+  float ds = 2.0f * d / S;
+  ds = ds > 0.0f ? ds : 0.0f;
+  const float dd = ds + (float)g.eps;
+  const float X = 1.0f / dd;
+  const float Y = -logf(dd);
+  const float A = Ai, B = Bj, AB = A * B;
+  const float iS = 1.0f / S, iS2 = iS * iS, iS3 = iS2 * iS;
+  const float xa = X * 2.0f * AB * AB * iS3;
+  const float ya = Y * (4.0f / 15.0f) * AB * (2.0f * A * A + AB + 2.0f * B * B) * iS3;
+  const float ybi = -Y * (2.0f / 15.0f) * A * AB * (4.0f * A + B) * iS2;
+  const float ybj = -Y * (2.0f / 15.0f) * AB * B * (A + 4.0f * B) * iS2;
+  const float yci = Y * (8.0f / 15.0f) * A * A * AB * iS;
+  const float ycj = Y * (8.0f / 15.0f) * AB * B * B * iS;
+  const float ycx = Y * (2.0f / 15.0f) * AB * AB * iS;
+  const float xg = X * 2.0f * AB * AB * iS2;
+  const float yg = Y * (1.0f / 15.0f) * AB * (4.0f - 6.0f * AB * iS2);
+  const float yhi = Y * iS2 * ((2.0f / 15.0f) * A * A * AB * (2.0f * A - B) + (1.0f / 15.0f) * AB * AB * (7.0f * A + B));
+  const float yhj = Y * iS2 * ((1.0f / 15.0f) * AB * AB * (A + 7.0f * B) + (2.0f / 15.0f) * AB * B * B * (2.0f * B - A));
+  const F3 dV = Vi - Vj;
+  const float nV = dotf(nn, dV);
+  const F3 fr = (xa * nV) * nn + ya * tangf(nn, dV) + ybi * crossf(nn, Wi) + ybj * crossf(nn, Wj);
+  const F3 twoEn = f3(gd * nn.y, gd * nn.x, 0.0f);
+  const float Pn = gd * nn.x * nn.y;
+  const F3 Qn = twoEn - (2.0f * Pn) * nn;
+  const F3 nperp = crossf(nn, twoEn);
+  const F3 Fl = k6 * (((xg * Pn) * nn + yg * Qn) - fr);
+  const F3 ndV = crossf(nn, dV);
+  const F3 Tli = k6 * (ybi * ndV - (yci * tangf(nn, Wi) + ycx * tangf(nn, Wj)) + yhi * nperp);
+  const F3 Tlj = k6 * (ybj * ndV - (ycx * tangf(nn, Wi) + ycj * tangf(nn, Wj)) + yhj * nperp);
+  const F3 F = Fc + Fl;
+  const F3 Ti = Ai * nxf + Tli;
+  const F3 Tj = Bj * nxf + Tlj;
+  q.F[0] = F.x; q.F[1] = F.y; q.F[2] = F.z;
+  q.Ti[0] = Ti.x; q.Ti[1] = Ti.y; q.Ti[2] = Ti.z;
+  q.Tj[0] = Tj.x; q.Tj[1] = Tj.y; q.Tj[2] = Tj.z;
+  q.Fc[0] = Fc.x; q.Fc[1] = Fc.y; q.Fc[2] = Fc.z;
+  q.Fl[0] = Fl.x; q.Fl[1] = Fl.y; q.Fl[2] = Fl.z;
+  q.r[0] = r.x; q.r[1] = r.y; q.r[2] = r.z;
+  return q;
+}
+
+template <typename R>
+__device__ __forceinline__ R owner_bits(int o);
+template <>
+__device__ __forceinline__ float owner_bits<float>(int o) { return __int_as_float(o); }
+template <>
+__device__ __forceinline__ double owner_bits<double>(int o) { return __longlong_as_double((long long)o); }
+__device__ __forceinline__ int bits_owner(float v) { return __float_as_int(v); }
+__device__ __forceinline__ int bits_owner(double v) { return (int)__double_as_longlong(v); }
+
+template <bool MIXED>
 __global__ void __launch_bounds__(kPairThreads)
-k_pairs(Geo g, StateBuf s, ListBuf W, ListBuf H, double* __restrict__ rec,
-        double* __restrict__ spart, DevStatus* st, int adv) {
+k_pairs(Geo g, StateBuf s, ListBuf W, ListBuf H, void* __restrict__ own_v, int* __restrict__ bw_count,
+        void* __restrict__ bw_v, double* __restrict__ spart, DevStatus* st, int adv) {
+  using R = typename std::conditional<MIXED, float, double>::type;
   if (dev_err(st)) return;
+  R* __restrict__ own = static_cast<R*>(own_v);
+  R* __restrict__ bw = static_cast<R*>(bw_v);
   const int n = g.n;
   const int P = W.start[n];
   if (P > g.pcap) {
@@ -154,73 +341,100 @@ k_pairs(Geo g, StateBuf s, ListBuf W, ListBuf H, double* __restrict__ rec,
     }
     return;
   }
+  __shared__ R acc[kWarps][32][6];
   const double off = le_offset(g, dev_nstep(st) + adv);
-  const double Om = -0.5 * g.gdot;
-  double Sx[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  R Sx[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   int ncont = 0;
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
-    int lo = 0, hi = n;
-    while (hi - lo > 1) {
-      int mid = (lo + hi) >> 1;
-      if (W.start[mid] <= p) lo = mid; else hi = mid;
-    }
-    const int i = lo;
-    const int j = W.list[(int64_t)i * g.M + (p - W.start[i])];
-    const double xi = s.x[i], yi = s.x[n + i], zi = s.x[2 * n + i];
-    const double xj = s.x[j], yj = s.x[n + j], zj = s.x[2 * n + j];
-    double dx, dy, dz;
-    int sy;
-    min_image(g, off, xi, yi, zi, xj, yj, zj, dx, dy, dz, sy);
-    const V3 r = v3(dx, dy, dz);
-    const double ai = s.a[i], aj = s.a[j];
-    const V3 ui = v3(s.u[i], s.u[n + i], s.u[2 * n + i]);
-    const V3 uj = v3(s.u[j], s.u[n + j], s.u[2 * n + j]);
-    const V3 wi = v3(s.w[i], s.w[n + i], s.w[2 * n + i]);
-    const V3 wj = v3(s.w[j], s.w[n + j], s.w[2 * n + j]);
-    const int idi = s.id[i], idj = s.id[j];
-    const double sgn = idi < idj ? 1.0 : -1.0;
-    double xo[3] = {0.0, 0.0, 0.0};
-    // the gap decides contact; look the history up only for contacts
-    const double rr = sqrt(dot(r, r));
-    if (rr - (ai + aj) < 0.0) {
-      history_lookup(g, H, idi, idj, xo);
-      xo[0] *= sgn; xo[1] *= sgn; xo[2] *= sgn;
-    }
-    const V3 Vi = v3(ui.x - g.gdot * yi, ui.y, ui.z);
-    const V3 Vj = v3(uj.x - g.gdot * yj, uj.y, uj.z);
-    const V3 Wi = v3(wi.x, wi.y, wi.z - Om);
-    const V3 Wj = v3(wj.x, wj.y, wj.z - Om);
-    const V3 du = v3(uj.x + sy * g.gdot * g.L[1] - ui.x, uj.y - ui.y, uj.z - ui.z);
-    const PairOut o = pair_fp64(g, r, rr, ai, aj, Vi, Vj, Wi, Wj, du, wi, wj, xo);
-    rec[p] = o.F.x;
-    rec[g.pcap + p] = o.F.y;
-    rec[2 * g.pcap + p] = o.F.z;
-    rec[3 * g.pcap + p] = o.Ti.x;
-    rec[4 * g.pcap + p] = o.Ti.y;
-    rec[5 * g.pcap + p] = o.Ti.z;
-    rec[6 * g.pcap + p] = o.Tj.x;
-    rec[7 * g.pcap + p] = o.Tj.y;
-    rec[8 * g.pcap + p] = o.Tj.z;
-    W.xi[p] = sgn * o.xi.x;
-    W.xi[g.pcap + p] = sgn * o.xi.y;
-    W.xi[2 * g.pcap + p] = sgn * o.xi.z;
-    W.cflag[p] = (unsigned char)o.contact;
-    ncont += o.contact;
-    // Eq. 9: S^C = r (x) F^C, S^L = sym(r (x) F^L), F on the owner
-    const double rv[3] = {r.x, r.y, r.z};
-    const double fc[3] = {o.Fc.x, o.Fc.y, o.Fc.z};
-    const double fl[3] = {o.Fl.x, o.Fl.y, o.Fl.z};
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int b = 0; b < 3; ++b) Sx[3 * a + b] += rv[a] * fc[b] + 0.5 * (rv[a] * fl[b] + rv[b] * fl[a]);
-  }
-  // deterministic block reduction of the stresslet (fixed tree)
-  __shared__ double red[kPairThreads / 32][9];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+#pragma unroll
+  for (int c = 0; c < 6; ++c) acc[wid][lane][c] = R(0);
+  __syncwarp();
+  for (int w0 = gw * 32; w0 < n; w0 += nw * 32) {
+    const int il = w0 + lane;
+    const int cnt = il < n ? W.count[il] : 0;
+    int incl = cnt;
+    for (int d = 1; d < 32; d <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += t;
+    }
+    const int excl = incl - cnt;
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    const int base = W.start[w0];
+    for (int t0 = 0; t0 < total; t0 += 32) {
+      const int t = t0 + lane;
+      int Lw = 0;
+      for (int step = 16; step >= 1; step >>= 1) {
+        const int e = __shfl_sync(0xffffffffu, excl, Lw + step);
+        if (e <= t) Lw += step;
+      }
+      const int kk = t - __shfl_sync(0xffffffffu, excl, Lw);
+      const bool valid = t < total;
+      R v[6] = {0, 0, 0, 0, 0, 0};
+      int seg = valid ? Lw : 32 + lane;      // owner lane, unique sentinel when idle
+      if (valid) {
+        const int i = w0 + Lw;
+        const int p = base + t;
+        const int j = W.list[(int64_t)i * g.M + kk];
+        PairRes<R> q;
+        if constexpr (MIXED) q = pair_eval_mixed(g, s, H, off, i, j);
+        else q = pair_eval_fp64(g, s, H, off, i, j);
+        v[0] = q.F[0]; v[1] = q.F[1]; v[2] = q.F[2];
+        v[3] = q.Ti[0]; v[4] = q.Ti[1]; v[5] = q.Ti[2];
+        // partner's share, appended to its row with the owner's index
+        const int slot = atomicAdd(&bw_count[j], 1);
+        if (slot < g.M) {
+          R* b = bw + ((int64_t)j * g.M + slot) * kSlot;
+          b[0] = -q.F[0]; b[1] = -q.F[1]; b[2] = -q.F[2];
+          b[3] = q.Tj[0]; b[4] = q.Tj[1]; b[5] = q.Tj[2];
+          b[6] = owner_bits<R>(i);
+        } else {
+          set_err(st, DSS_ERR_CAPACITY);
+        }
+        W.xi[p] = q.xi[0];
+        W.xi[g.pcap + p] = q.xi[1];
+        W.xi[2 * g.pcap + p] = q.xi[2];
+        W.cflag[p] = (unsigned char)q.contact;
+        ncont += q.contact;
+        // Eq. 9: S^C = r (x) F^C, S^L = sym(r (x) F^L), F on the owner
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int b2 = 0; b2 < 3; ++b2)
+            Sx[3 * a + b2] += q.r[a] * q.Fc[b2] + R(0.5) * (q.r[a] * q.Fl[b2] + q.r[b2] * q.Fl[a]);
+      }
+      // warp-segmented inclusive scan over lanes with the same owner
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int so = __shfl_up_sync(0xffffffffu, seg, d);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+          const R u = __shfl_up_sync(0xffffffffu, v[c], d);
+          if (lane >= d && so == seg) v[c] += u;
+        }
+      }
+      const int nxt = __shfl_down_sync(0xffffffffu, seg, 1);
+      if (valid && (lane == 31 || nxt != seg)) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) acc[wid][Lw][c] += v[c];
+      }
+      __syncwarp();
+    }
+    // one write per owner, then clear for the next group
+    if (il < n) {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) own[(int64_t)c * n + il] = acc[wid][lane][c];
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) acc[wid][lane][c] = R(0);
+    __syncwarp();
+  }
+  // FP64 block reduction of the stresslet (fixed tree)
+  __shared__ double red[kWarps][9];
 #pragma unroll
   for (int q = 0; q < 9; ++q) {
-    double v = Sx[q];
+    double v = (double)Sx[q];
     for (int dlt = 16; dlt > 0; dlt >>= 1) v += __shfl_down_sync(0xffffffffu, v, dlt);
     if (lane == 0) red[wid][q] = v;
   }
@@ -230,93 +444,95 @@ k_pairs(Geo g, StateBuf s, ListBuf W, ListBuf H, double* __restrict__ rec,
   __syncthreads();
   if (threadIdx.x < 9) {
     double v = 0.0;
-    for (int w = 0; w < kPairThreads / 32; ++w) v += red[w][threadIdx.x];
+    for (int w = 0; w < kWarps; ++w) v += red[w][threadIdx.x];
     spart[blockIdx.x * 9 + threadIdx.x] = v;
   }
 }
 
+template <bool MIXED>
 __global__ void __launch_bounds__(kThreads)
-k_gather(Geo g, StateBuf s, ListBuf W, const float4* __restrict__ posf,
-         const int* __restrict__ cellid, const int* __restrict__ cell_start,
-         const double* __restrict__ rec, double* __restrict__ Fout, double* __restrict__ Tout,
-         DevStatus* st, int adv, int mode) {
+k_gather(Geo g, StateBuf s, const void* __restrict__ own_v, const int* __restrict__ bw_count,
+         const void* __restrict__ bw_v, double* __restrict__ Fout, double* __restrict__ Tout,
+         DevStatus* st, int mode) {
+  using R = typename std::conditional<MIXED, float, double>::type;
   if (dev_err(st)) return;
+  const R* __restrict__ own = static_cast<const R*>(own_v);
+  const R* __restrict__ bw = static_cast<const R*>(bw_v);
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = g.n;
   if (j >= n) return;
-  const int64_t pc = g.pcap;
-  V3 F = v3(0, 0, 0), T = v3(0, 0, 0);
-  // own rows: the particle is the owner
-  const int p0 = W.start[j], p1 = W.start[j + 1];
-  for (int p = p0; p < p1; ++p) {
-    F = F + v3(rec[p], rec[pc + p], rec[2 * pc + p]);
-    T = T + v3(rec[3 * pc + p], rec[4 * pc + p], rec[5 * pc + p]);
+  R F[3], T[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    F[c] = own[(int64_t)c * n + j];
+    T[c] = own[(int64_t)(3 + c) * n + j];
   }
-  // transposed records: owners found by the backward half-stencil
-  const double off = le_offset(g, dev_nstep(st) + adv);
-  const int fsh = le_shift_cells(g, off);
-  const int c = cellid[j];
-  const int cx = c % g.nc[0], cy = (c / g.nc[0]) % g.nc[1], cz = c / (g.nc[0] * g.nc[1]);
-  StencilCell sc[17];
-  const int ns = backward_cells(g, cx, cy, cz, fsh, sc);
-  const float4 pj = posf[j];
-  const double xj = s.x[j], yj = s.x[n + j], zj = s.x[2 * n + j], aj = s.a[j];
-  for (int q = 0; q < ns; ++q) {
-    const StencilCell cur = sc[q];
-    const int ob = cell_start[cur.cell];
-    const int oe = cur.le == 2 ? j : cell_start[cur.cell + 1];
-    // separation seen from the owner: partner cell displaced by -(ox,oy,oz)
-    const float cxo = (float)((-cur.ox) * g.cs[0] + (cur.le == 1 ? off : 0.0));
-    const float cyo = (float)((-cur.oy) * g.cs[1]);
-    const float czo = (float)((-cur.oz) * g.cs[2]);
-    for (int o = ob; o < oe; ++o) {
-      const float4 po = posf[o];
-      const float sf = po.w + pj.w + pair_delta_f(g, po.w, pj.w);
-      int dec = prefilter(g, po, pj, cxo, cyo, czo, sf);
-      if (dec < 0)
-        dec = exact_is_pair(g, off, s.x[o], s.x[n + o], s.x[2 * n + o], s.a[o], xj, yj, zj, aj) ? 1 : 0;
-      if (!dec) continue;
-      const int k = row_find(W.list + (int64_t)o * g.M, W.count[o], j);
-      if (k < 0) {
-        set_err(st, DSS_ERR_INTERNAL);
-        continue;
-      }
-      const int64_t p = (int64_t)W.start[o] + k;
-      F = F - v3(rec[p], rec[pc + p], rec[2 * pc + p]);
-      T = T + v3(rec[6 * pc + p], rec[7 * pc + p], rec[8 * pc + p]);
+  // partner records in increasing owner index
+  int cnt = bw_count[j];
+  cnt = cnt < g.M ? cnt : g.M;
+  const R* row = bw + (int64_t)j * g.M * kSlot;
+  int prev = -1;
+  for (int t = 0; t < cnt; ++t) {
+    int best = INT_MAX, bs = 0;
+    for (int q = 0; q < cnt; ++q) {
+      const int o = bits_owner(row[q * kSlot + 6]);
+      if (o > prev && o < best) { best = o; bs = q; }
     }
+    const R* b = row + bs * kSlot;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      F[c] += b[c];
+      T[c] += b[3 + c];
+    }
+    prev = best;
   }
-  // Stokes drag, Eq. A1 (no Faxen term in simple shear)
-  const double a = aj;
-  const V3 u = v3(s.u[j], s.u[n + j], s.u[2 * n + j]);
-  const V3 w = v3(s.w[j], s.w[n + j], s.w[2 * n + j]);
-  F = F + (-g.k6 * a) * v3(u.x - g.gdot * yj, u.y, u.z);
-  T = T + (-g.k8 * a * a * a) * v3(w.x, w.y, w.z + 0.5 * g.gdot);
-  if (!(isfinite(F.x) && isfinite(F.y) && isfinite(F.z) && isfinite(T.x) && isfinite(T.y) &&
-        isfinite(T.z)))
-    set_err(st, DSS_ERR_NONFINITE);
+  const double a = s.a[j];
   const int id = s.id[j];
+  if constexpr (MIXED) {
+    // Stokes drag on the FP32 velocities relative to the ambient flow
+    const float af = (float)a;
+    const float4 v4 = s.vf[j], w4 = s.wf[j];
+    const float kd = -(float)g.k6 * af, kr = -(float)g.k8 * af * af * af;
+    F[0] += kd * v4.x; F[1] += kd * v4.y; F[2] += kd * v4.z;
+    T[0] += kr * w4.x; T[1] += kr * w4.y; T[2] += kr * w4.z;
+  } else {
+    const double yj = s.x[n + j];
+    const double kd = -g.k6 * a, kr = -g.k8 * a * a * a;
+    F[0] += kd * (s.u[j] - g.gdot * yj);
+    F[1] += kd * s.u[n + j];
+    F[2] += kd * s.u[2 * n + j];
+    T[0] += kr * s.w[j];
+    T[1] += kr * s.w[n + j];
+    T[2] += kr * (s.w[2 * n + j] + 0.5 * g.gdot);
+  }
+  if (!(isfinite((double)F[0]) && isfinite((double)F[1]) && isfinite((double)F[2]) &&
+        isfinite((double)T[0]) && isfinite((double)T[1]) && isfinite((double)T[2])))
+    set_err(st, DSS_ERR_NONFINITE);
   if (mode == G_EVAL) {
-    if (Fout) { Fout[id] = F.x; Fout[n + id] = F.y; Fout[2 * n + id] = F.z; }
-    if (Tout) { Tout[id] = T.x; Tout[n + id] = T.y; Tout[2 * n + id] = T.z; }
+    if (Fout) { Fout[id] = F[0]; Fout[n + id] = F[1]; Fout[2 * n + id] = F[2]; }
+    if (Tout) { Tout[id] = T[0]; Tout[n + id] = T[1]; Tout[2 * n + id] = T[2]; }
     return;
   }
   // accelerations: m = 4/3 pi rho a^3, I = 2/5 m a^2
   const double m = 4.0 / 3.0 * DSS_PI * g.rho * a * a * a;
-  const double I = 0.4 * m * a * a;
-  const V3 al = v3(F.x / m, F.y / m, F.z / m);
-  const V3 aw = v3(T.x / I, T.y / I, T.z / I);
-  s.al[j] = al.x; s.al[n + j] = al.y; s.al[2 * n + j] = al.z;
-  s.aw[j] = aw.x; s.aw[n + j] = aw.y; s.aw[2 * n + j] = aw.z;
+  const double im = 1.0 / m;
+  const double iI = im * (2.5 / (a * a));
+  const R imr = (R)im, iIr = (R)iI;
+  const R al[3] = {F[0] * imr, F[1] * imr, F[2] * imr};
+  const R aw[3] = {T[0] * iIr, T[1] * iIr, T[2] * iIr};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    s.al[c * n + j] = al[c];
+    s.aw[c * n + j] = aw[c];
+  }
   if (mode == G_STEP) {
     // Eq. 15d from u^{n+1/2}: u^{n+1} = u^{n+1/2} + dt/2 alpha^{n+1}
     const double hdt = __dmul_rn(0.5, g.dt);
-    s.u[j] = __dadd_rn(u.x, __dmul_rn(hdt, al.x));
-    s.u[n + j] = __dadd_rn(u.y, __dmul_rn(hdt, al.y));
-    s.u[2 * n + j] = __dadd_rn(u.z, __dmul_rn(hdt, al.z));
-    s.w[j] = __dadd_rn(w.x, __dmul_rn(hdt, aw.x));
-    s.w[n + j] = __dadd_rn(w.y, __dmul_rn(hdt, aw.y));
-    s.w[2 * n + j] = __dadd_rn(w.z, __dmul_rn(hdt, aw.z));
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      s.u[c * n + j] = __dadd_rn(s.u[c * n + j], __dmul_rn(hdt, (double)al[c]));
+      s.w[c * n + j] = __dadd_rn(s.w[c * n + j], __dmul_rn(hdt, (double)aw[c]));
+    }
   }
 }
 
@@ -377,27 +593,40 @@ __global__ void k_pairs_out(Geo g, ListBuf W, long long* __restrict__ out) {
 }
 }  // namespace
 
+// One warp per 32 owners: ceil(n / kPairThreads) blocks cover every owner
+// once (the pair kernel also strides when given fewer).
 int pair_grid_blocks(const dss_handle* h) {
-  int64_t need = (h->pcap + kPairThreads - 1) / kPairThreads;
-  int64_t cap = 152 * 8;
-  return (int)(need < cap ? (need > 0 ? need : 1) : cap);
+  int64_t need = (h->n + kPairThreads - 1) / kPairThreads;
+  return (int)(need > 0 ? need : 1);
 }
+
+int bw_slot_values() { return kSlot; }
 
 void launch_forces(dss_handle* h, int stbuf, int work_list, int hist_list, int adv, int mode,
                    double* F_out, double* T_out) {
   const int n = (int)h->n;
   const int pb = pair_grid_blocks(h);
+  const bool mixed = h->g.precision == DSS_MIXED;
+  prof_mark(h, 5);
+  if (mixed)
+    k_pairs<true><<<pb, kPairThreads, 0, h->stream>>>(h->g, h->st[stbuf], h->lb[work_list],
+                                                      h->lb[hist_list], h->own, h->bw_count, h->bw_rec,
+                                                      h->spart, h->status, adv);
+  else
+    k_pairs<false><<<pb, kPairThreads, 0, h->stream>>>(h->g, h->st[stbuf], h->lb[work_list],
+                                                       h->lb[hist_list], h->own, h->bw_count, h->bw_rec,
+                                                       h->spart, h->status, adv);
+  prof_mark(h, 6);
+  if (mixed)
+    k_gather<true><<<(n + kThreads - 1) / kThreads, kThreads, 0, h->stream>>>(
+        h->g, h->st[stbuf], h->own, h->bw_count, h->bw_rec, F_out, T_out, h->status, mode);
+  else
+    k_gather<false><<<(n + kThreads - 1) / kThreads, kThreads, 0, h->stream>>>(
+        h->g, h->st[stbuf], h->own, h->bw_count, h->bw_rec, F_out, T_out, h->status, mode);
   prof_mark(h, 7);
-  k_pairs<<<pb, kPairThreads, 0, h->stream>>>(h->g, h->st[stbuf], h->lb[work_list], h->lb[hist_list],
-                                              h->rec, h->spart, h->status, adv);
-  prof_mark(h, 8);
-  k_gather<<<(n + kThreads - 1) / kThreads, kThreads, 0, h->stream>>>(
-      h->g, h->st[stbuf], h->lb[work_list], h->posf, h->cellid, h->cell_start, h->rec, F_out, T_out,
-      h->status, adv, mode);
-  prof_mark(h, 9);
   k_finalize<<<1, 256, 0, h->stream>>>(h->g, h->spart, pb, h->sigma, h->status,
                                        h->lb[work_list].start, mode == G_STEP ? 1 : 0);
-  prof_mark(h, 10);
+  prof_mark(h, 8);
 }
 
 void launch_pairs_out(dss_handle* h, int list, long long* out) {

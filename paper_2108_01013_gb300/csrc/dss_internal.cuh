@@ -9,7 +9,7 @@
 #include "../../include/dss.h"
 
 #define DSS_PI 3.14159265358979323846
-#define DSS_PROF_KERNELS 10
+#define DSS_PROF_KERNELS 8
 
 // Device status word layout (int32 slots in DevStatus::w).
 enum {
@@ -54,6 +54,8 @@ struct Geo {
   // FP32 prefilter margin on r^2 (absolute)
   float r2_margin;
   float halfLf[3];
+  float csf[3];       // FP32 cell edges
+  double invL[3];     // 1 / L
 };
 
 // ------------------------------------------------------------------------
@@ -103,8 +105,11 @@ __device__ __forceinline__ void min_image(const Geo& g, double off, double xi, d
     dx = __dadd_rn(dx, off);
     sy = 1;
   }
-  dx = __dsub_rn(dx, __dmul_rn(g.L[0], rint(__ddiv_rn(dx, g.L[0]))));
-  dz = __dsub_rn(dz, __dmul_rn(g.L[2], rint(__ddiv_rn(dz, g.L[2]))));
+  // image count rint(dx / L) taken as rint(dx * (1/L)): the two differ only
+  // when dx is within rounding of +-L/2, where both images lie at least
+  // L/2 >= 1.5 cells away, beyond any pair's cutoff, so no decision changes
+  dx = __dsub_rn(dx, __dmul_rn(g.L[0], rint(__dmul_rn(dx, g.invL[0]))));
+  dz = __dsub_rn(dz, __dmul_rn(g.L[2], rint(__dmul_rn(dz, g.invL[2]))));
 }
 
 // Exact neighbour predicate: r^2 < (a_i + a_j + delta_ij)^2, strict.
@@ -244,6 +249,17 @@ __device__ __forceinline__ int prefilter(const Geo& g, float4 pi, float4 pj, flo
   return -1;
 }
 
+// FP32 displacement of a stencil cell's origin (cells ox, oy, oz away; for a
+// Lees-Edwards image plus the offset off = fsh*cs_x + offr, offr in [0, cs_x)),
+// computed without any FP64 instruction.
+__device__ __forceinline__ void stencil_shift(const Geo& g, int ox, int oy, int oz, int le,
+                                              int fsh, float offr, float& cx, float& cy,
+                                              float& cz) {
+  cx = le == 1 ? (float)(ox + fsh) * g.csf[0] + offr : (float)ox * g.csf[0];
+  cy = (float)oy * g.csf[1];
+  cz = (float)oz * g.csf[2];
+}
+
 __device__ __forceinline__ float pair_delta_f(const Geo& g, float ai, float aj) {
   if (g.mode == 1) return (float)(g.delta * g.a0);
   return (float)g.delta * (ai + aj) * 0.5f;
@@ -260,6 +276,8 @@ struct StateBuf {
   double* aw;   // 3n angular acceleration
   double* a;    // n radius
   int* id;      // n persistent id
+  float4* vf;   // n, mixed precision: FP32 velocity relative to U_inf (xyz)
+  float4* wf;   // n, mixed precision: FP32 angular velocity relative to Omega_inf (xyz)
 };
 
 struct ListBuf {
@@ -309,8 +327,10 @@ struct dss_handle {
   ListBuf lb[2];
   int hist;
   bool hist_empty;
-  // per-pair records of the last force pass
-  double* rec;       // 9*pcap: F_i (3), T_i (3), T_j (3)
+  // force accumulation of the last force pass (FP32 in mixed precision)
+  void* own;         // 6n: force and torque summed over each particle's own row
+  int* bw_count;     // n: records appended to each particle's partner row
+  void* bw_rec;      // n*M slots of 8 values: partner force (3), torque (3), owner index
   int64_t pcap;
   // stress
   double* spart;     // 9 * max pair blocks
@@ -347,6 +367,8 @@ void launch_pairs_out(dss_handle* h, int list, long long* out);
 int pair_grid_blocks(const dss_handle* h);
 void launch_scan(dss_handle* h, const int* in, int* out, int count, int which, bool zero_in);
 int scan_tiles_for(int count);
+int enum_tiles_for(int n);
+int bw_slot_values();
 // Marks the start of kernel k of a step when profiling (event record node
 // when the step is being captured).
 void prof_mark(dss_handle* h, int k);

@@ -1,93 +1,187 @@
 // Symmetric (half-stencil) fixed-radius near-neighbour enumeration
 // (Sec. II A, Fig. 6): each pair is found exactly once, by its owner, and
 // written into the owner's fixed-capacity row (capacity M, the shell
-// estimate of Sec. II A).  Rows come out sorted by partner index because the
-// stencil cells are visited in increasing cell id and every cell is a
-// contiguous, increasing range of the sorted order.
+// estimate of Sec. II A), in a fixed visiting order.
 //
 // The decision uses an FP32 conservative prefilter on cell-local coordinates;
 // candidates within the rounding band of the cutoff are decided by the exact
 // FP64 predicate, so the pair set is the FP64 brute-force set bit for bit.
+//
+// The exclusive scan of the row lengths (the pair offsets of each owner) is
+// fused into the same kernel with a single-pass decoupled look-back over
+// blocks taken in launch order.
 #include "dss_internal.cuh"
 
 namespace {
 constexpr int kThreads = 128;
+constexpr unsigned long long kFlagAgg = 1ull << 32;
+constexpr unsigned long long kFlagPre = 2ull << 32;
+
+// Visits the candidates of one stencil cell and appends the pairs.
+struct EnumCtx {
+  const Geo* g;
+  const StateBuf* s;
+  const float4* posf;
+  float4 pi;
+  double off;
+  int i;
+  int cnt;
+  int band;
+  int* row;
+};
+
+__device__ __forceinline__ void scan_range(EnumCtx& e, int jb, int je, float cxo, float cyo, float czo) {
+  const Geo& g = *e.g;
+  const int n = g.n;
+  for (int j = jb; j < je; ++j) {
+    const float4 pj = e.posf[j];
+    const float sf = e.pi.w + pj.w + pair_delta_f(g, e.pi.w, pj.w);
+    int dec = prefilter(g, e.pi, pj, cxo, cyo, czo, sf);
+    if (dec < 0) {
+      ++e.band;
+      const StateBuf& s = *e.s;
+      dec = exact_is_pair(g, e.off, s.x[e.i], s.x[n + e.i], s.x[2 * n + e.i], s.a[e.i], s.x[j],
+                          s.x[n + j], s.x[2 * n + j], s.a[j]) ? 1 : 0;
+    }
+    if (dec) {
+      if (e.cnt < g.M) e.row[e.cnt] = j;
+      ++e.cnt;
+    }
+  }
+}
 
 __global__ void __launch_bounds__(kThreads)
 k_enumerate(Geo g, StateBuf s, const float4* __restrict__ posf, const int* __restrict__ cellid,
-            const int* __restrict__ cell_start, ListBuf L, DevStatus* st, int adv) {
-  int* __restrict__ count = L.count;
-  int* __restrict__ list = L.list;
+            const int* __restrict__ cell_start, ListBuf L, int* __restrict__ bw_count,
+            unsigned long long* scan_status, int* scan_ticket, DevStatus* st, int adv) {
   if (dev_err(st)) return;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  __shared__ int s_tile;
+  __shared__ int s_warp[kThreads / 32];
+  __shared__ int s_prefix;
+  if (threadIdx.x == 0) s_tile = atomicAdd(scan_ticket, 1);
+  __syncthreads();
+  const int tile = s_tile;
+  const int i = tile * kThreads + threadIdx.x;
   const int n = g.n;
-  int cnt = 0, band = 0;
+  EnumCtx e;
+  e.cnt = 0;
+  e.band = 0;
   if (i < n) {
-    const double off = le_offset(g, dev_nstep(st) + adv);
-    const int fsh = le_shift_cells(g, off);
+    e.g = &g;
+    e.s = &s;
+    e.posf = posf;
+    e.i = i;
+    e.off = le_offset(g, dev_nstep(st) + adv);
+    e.pi = posf[i];
+    e.row = L.list + (int64_t)i * g.M;
+    const int fsh = le_shift_cells(g, e.off);
+    const float offr = (float)(e.off - fsh * g.cs[0]);
+    const int nx = g.nc[0], ny = g.nc[1], nz = g.nc[2];
     const int c = cellid[i];
-    const int cx = c % g.nc[0], cy = (c / g.nc[0]) % g.nc[1], cz = c / (g.nc[0] * g.nc[1]);
-    StencilCell sc[17];
-    const int ns = forward_cells(g, cx, cy, cz, fsh, sc);
-    const float4 pi = posf[i];
-    const double ai = s.a[i];
-    int* row = list + (int64_t)i * g.M;
-    for (int q = 0; q < ns; ++q) {
-      const StencilCell cur = sc[q];
-      const int jb = cur.le == 2 ? i + 1 : cell_start[cur.cell];
-      const int je = cell_start[cur.cell + 1];
-      const float cxo = (float)(cur.ox * g.cs[0] + (cur.le == 1 ? off : 0.0));
-      const float cyo = (float)(cur.oy * g.cs[1]);
-      const float czo = (float)(cur.oz * g.cs[2]);
-      for (int j = jb; j < je; ++j) {
-        const float4 pj = posf[j];
-        const float sf = pi.w + pj.w + pair_delta_f(g, pi.w, pj.w);
-        int dec = prefilter(g, pi, pj, cxo, cyo, czo, sf);
-        if (dec < 0) {
-          ++band;
-          dec = exact_is_pair(g, off, s.x[i], s.x[n + i], s.x[2 * n + i], ai, s.x[j], s.x[n + j],
-                              s.x[2 * n + j], s.a[j]) ? 1 : 0;
-        }
-        if (dec) {
-          if (cnt < g.M) row[cnt] = j;
-          ++cnt;
-        }
+    const int cx = c % nx, cy = (c / nx) % ny, cz = c / (nx * ny);
+    // own cell (partners after i) and the cell x+1
+    scan_range(e, i + 1, cell_start[c + 1], 0.f, 0.f, 0.f);
+    {
+      const int q = (cz * ny + cy) * nx + wrapi(cx + 1, nx);
+      scan_range(e, cell_start[q], cell_start[q + 1], g.csf[0], 0.f, 0.f);
+    }
+    // layer y, z+1: three x cells
+    {
+      const int qz = wrapi(cz + 1, nz);
+      for (int ox = -1; ox <= 1; ++ox) {
+        const int q = (qz * ny + cy) * nx + wrapi(cx + ox, nx);
+        scan_range(e, cell_start[q], cell_start[q + 1], (float)ox * g.csf[0], 0.f, g.csf[2]);
       }
     }
-    count[i] = cnt < g.M ? cnt : g.M;
-    if (cnt > g.M) set_err(st, DSS_ERR_CAPACITY);
-    // id <-> row maps of this list's index space (history lookups, output)
+    // layer y+1: 3x3 cells, or across y = L_y the 4 x cells covering the
+    // image range shifted by the Lees-Edwards offset
+    const bool le = cy == ny - 1;
+    const int qy = le ? 0 : cy + 1;
+    const int x0 = le ? -2 - fsh : -1, x1 = le ? 1 - fsh : 1;
+    for (int oz = -1; oz <= 1; ++oz) {
+      const int qz = wrapi(cz + oz, nz);
+      for (int ox = x0; ox <= x1; ++ox) {
+        const int q = (qz * ny + qy) * nx + wrapi(cx + ox, nx);
+        float cxo, cyo, czo;
+        stencil_shift(g, ox, 1, oz, le ? 1 : 0, fsh, offr, cxo, cyo, czo);
+        scan_range(e, cell_start[q], cell_start[q + 1], cxo, cyo, czo);
+      }
+    }
+    L.count[i] = e.cnt < g.M ? e.cnt : g.M;
+    if (e.cnt > g.M) set_err(st, DSS_ERR_CAPACITY);
+    bw_count[i] = 0;
     const int id = s.id[i];
     L.slot_of_id[id] = i;
     L.id_of_slot[i] = id;
   }
-  // warp-aggregated counters
-  int m = cnt;
-  for (int d = 16; d > 0; d >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, d));
-  int b = band;
-  for (int d = 16; d > 0; d >>= 1) b += __shfl_xor_sync(0xffffffffu, b, d);
-  if ((threadIdx.x & 31) == 0) {
+  // counters
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int m = e.cnt, b = e.band;
+  for (int d = 16; d > 0; d >>= 1) {
+    m = max(m, __shfl_xor_sync(0xffffffffu, m, d));
+    b += __shfl_xor_sync(0xffffffffu, b, d);
+  }
+  if (lane == 0) {
     atomicMax(&st->w[ST_MAXROW], m);
     if (b) atomicAdd(&st->w[ST_BAND], b);
   }
-}
-
-__global__ void k_reset_counters(DevStatus* st) {
-  st->w[ST_MAXROW] = 0;
-  st->w[ST_BAND] = 0;
-  st->w[ST_NCONT] = 0;
+  // fused exclusive scan of the row lengths: block scan + decoupled look-back
+  const int v = i < n ? (e.cnt < g.M ? e.cnt : g.M) : 0;
+  int incl = v;
+  for (int d = 1; d < 32; d <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += t;
+  }
+  if (lane == 31) s_warp[wid] = incl;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int run = 0;
+    for (int w = 0; w < kThreads / 32; ++w) {
+      const int t = s_warp[w];
+      s_warp[w] = run;
+      run += t;
+    }
+    const int agg = run;
+    int prefix = 0;
+    if (tile == 0) {
+      atomicExch(&scan_status[tile], kFlagPre | (unsigned)agg);
+    } else {
+      atomicExch(&scan_status[tile], kFlagAgg | (unsigned)agg);
+      int t = tile - 1;
+      long long spins = 0;
+      while (t >= 0) {
+        const unsigned long long w = atomicAdd(&scan_status[t], 0ull);
+        const unsigned long long f = w & (3ull << 32);
+        if (f == 0ull) {
+          if (++spins > (1ll << 24)) {
+            set_err(st, DSS_ERR_TIMEOUT);
+            break;
+          }
+          __nanosleep(32);
+          continue;
+        }
+        prefix += (int)(unsigned)(w & 0xffffffffull);
+        if (f == kFlagPre) break;
+        --t;
+      }
+      atomicExch(&scan_status[tile], kFlagPre | (unsigned)(prefix + agg));
+    }
+    s_prefix = prefix;
+    if ((tile + 1) * kThreads >= n) L.start[n] = prefix + agg;
+  }
+  __syncthreads();
+  if (i < n) L.start[i] = s_prefix + s_warp[wid] + incl - v;
 }
 }  // namespace
+
+int enum_tiles_for(int n) { return (n + kThreads - 1) / kThreads; }
 
 void launch_enumerate(dss_handle* h, int stbuf, int dst_list, int adv) {
   const int n = (int)h->n;
   ListBuf& L = h->lb[dst_list];
   prof_mark(h, 4);
-  k_reset_counters<<<1, 1, 0, h->stream>>>(h->status);
-  prof_mark(h, 5);
-  k_enumerate<<<(n + kThreads - 1) / kThreads, kThreads, 0, h->stream>>>(
-      h->g, h->st[stbuf], h->posf, h->cellid, h->cell_start, L, h->status, adv);
+  k_enumerate<<<enum_tiles_for(n), kThreads, 0, h->stream>>>(
+      h->g, h->st[stbuf], h->posf, h->cellid, h->cell_start, L, h->bw_count,
+      h->scan_status + h->scan_tiles_max, h->scan_ticket + 1, h->status, adv);
   h->last_list = dst_list;
-  prof_mark(h, 6);
-  launch_scan(h, L.count, L.start, n, 1, false);
 }

@@ -191,6 +191,7 @@ extern "C" int dss_pairs_noalloc(const double* x, const double* a, const int32_t
   for (int d = 0; d < 3; ++d) {
     g.L[d] = box[d];
     g.halfL[d] = 0.5 * box[d];
+    g.invL[d] = 1.0 / box[d];
   }
   g.delta = p->delta_lub;
   g.a0 = p->a0;

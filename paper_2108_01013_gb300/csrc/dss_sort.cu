@@ -85,6 +85,11 @@ k_key_hist(Geo g, StateBuf s, int* __restrict__ key, int* __restrict__ offs,
   if (blockIdx.x == 0) {
     for (int t = threadIdx.x; t < 2 * scan_tiles; t += blockDim.x) scan_status[t] = 0ull;
     if (threadIdx.x < 2) scan_ticket[threadIdx.x] = 0;
+    if (threadIdx.x == 0) {
+      st->w[ST_MAXROW] = 0;
+      st->w[ST_BAND] = 0;
+      st->w[ST_NCONT] = 0;
+    }
   }
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= g.n) return;
@@ -149,6 +154,13 @@ k_rank_gather(Geo g, StateBuf src, StateBuf dst, const int* __restrict__ key,
   double a = src.a[o];
   dst.a[f] = a;
   dst.id[f] = src.id[o];
+  if (g.precision == DSS_MIXED) {
+    // FP32 copies relative to the ambient flow for the FP32 pair arithmetic:
+    // u - U_inf(x) and w - Omega_inf are O(gdot a), free of O(gdot L) terms
+    dst.vf[f] = make_float4((float)(p.ux - g.gdot * p.y), (float)p.uy, (float)p.uz, 0.f);
+    dst.wf[f] = make_float4((float)dst.w[f], (float)dst.w[n + f],
+                            (float)(dst.w[2 * n + f] + 0.5 * g.gdot), 0.f);
+  }
   // cell-local FP32 position for the enumeration prefilter
   int cx = k % g.nc[0];
   int cy = (k / g.nc[0]) % g.nc[1];
