@@ -33,7 +33,7 @@ void free_buffers(dss_handle* h) {
   for (int b = 0; b < 2; ++b) {
     StateBuf& s = h->st[b];
     dfree(s.x); dfree(s.u); dfree(s.w); dfree(s.al); dfree(s.aw); dfree(s.a); dfree(s.id);
-    dfree(s.vf); dfree(s.wf);
+    dfree(s.vf); dfree(s.wf); dfree(s.posl); dfree(s.cellc);
     memset(&s, 0, sizeof(s));
     ListBuf& L = h->lb[b];
     dfree(L.count); dfree(L.list); dfree(L.start); dfree(L.xi); dfree(L.cflag); dfree(L.slot_of_id);
@@ -109,7 +109,8 @@ int alloc_buffers(dss_handle* h) {
         (r = dalloc(h, &s.id, n)))
       return r;
     if (h->p.precision == DSS_MIXED &&
-        ((r = dalloc(h, &s.vf, n)) || (r = dalloc(h, &s.wf, n))))
+        ((r = dalloc(h, &s.vf, n)) || (r = dalloc(h, &s.wf, n)) || (r = dalloc(h, &s.posl, n)) ||
+         (r = dalloc(h, &s.cellc, n))))
       return r;
     ListBuf& L = h->lb[b];
     if ((r = dalloc(h, &L.count, n)) || (r = dalloc(h, &L.list, n * (size_t)h->g.M)) ||
@@ -328,9 +329,11 @@ int geometry(dss_handle* h) {
     g.inv_cs[d] = 1.0 / g.cs[d];
     g.halfLf[d] = (float)(0.5 * h->L[d]) * (1.0f - 1e-5f);
     g.csf[d] = (float)g.cs[d];
+    g.cs_lo[d] = (float)(g.cs[d] - (double)g.csf[d]);
     g.invL[d] = 1.0 / h->L[d];
   }
   if (g.nc[0] < 4 || g.nc[1] < 3 || g.nc[2] < 3) return DSS_ERR_BOX;
+  if (g.nc[0] > 1023 || g.nc[1] > 1023 || g.nc[2] > 1023) return DSS_ERR_ARG;   // packed coords
   if ((double)g.nc[0] * g.nc[1] * g.nc[2] > 2.0e9) return DSS_ERR_ARG;
   g.ncell = g.nc[0] * g.nc[1] * g.nc[2];
   double csmax = std::max(g.cs[0], std::max(g.cs[1], g.cs[2]));
@@ -436,6 +439,16 @@ int dss_create(dss_handle** out, const dss_params* p, int64_t n, const double bo
   g.gdot = p->shear_rate; g.dt = p->dt;
   g.k6 = 6.0 * DSS_PI * p->eta0;
   g.k8 = 8.0 * DSS_PI * p->eta0;
+  g.f.kn = (float)p->kn;
+  g.f.kt = (float)p->kt;
+  g.f.gn = (float)p->gamma_n;
+  g.f.mu_kt = (float)(p->mu / p->kt);
+  g.f.dt = (float)p->dt;
+  g.f.eps = (float)p->lub_eps;
+  g.f.gdot = (float)p->shear_rate;
+  g.f.k6 = (float)g.k6;
+  g.f.k8 = (float)g.k8;
+  g.f.mass_c = (float)(4.0 / 3.0 * DSS_PI * p->rho);
   *out = h;
   return DSS_OK;
 }

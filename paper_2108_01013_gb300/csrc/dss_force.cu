@@ -215,72 +215,93 @@ __device__ __forceinline__ PairRes<double> pair_eval_fp64(const Geo& g, const St
 // stretch is carried and updated in FP64; the rest of the pair arithmetic is
 // FP32, on velocities taken relative to the ambient flow.
 __device__ __forceinline__ PairRes<float> pair_eval_mixed(const Geo& g, const StateBuf& s, const ListBuf& H,
-                                                         double off, int i, int j) {
-  const int n = g.n;
-  const float gd = (float)g.gdot;
-  const float k6 = (float)g.k6;
-  double dx = s.x[j] - s.x[i];
-  double dy = s.x[n + j] - s.x[n + i];
-  double dz = s.x[2 * n + j] - s.x[2 * n + i];
-  if (dy > g.halfL[1]) { dy -= g.L[1]; dx -= off; }
-  else if (dy < -g.halfL[1]) { dy += g.L[1]; dx += off; }
-  if (dx > g.halfL[0]) dx -= g.L[0]; else if (dx < -g.halfL[0]) dx += g.L[0];
-  if (dx > g.halfL[0]) dx -= g.L[0]; else if (dx < -g.halfL[0]) dx += g.L[0];
-  if (dz > g.halfL[2]) dz -= g.L[2]; else if (dz < -g.halfL[2]) dz += g.L[2];
-  const double ai = s.a[i], aj = s.a[j];
-  const double S64 = ai + aj;
-  const double r2 = dx * dx + dy * dy + dz * dz;
-  const double num = r2 - S64 * S64;            // (r - S)(r + S) to FP64 rounding
-  const float rr = sqrtf((float)r2);
-  const float S = (float)S64;
-  const float d = (float)num / (rr + S);
-  const float ir = 1.0f / rr;
-  const F3 r = f3((float)dx, (float)dy, (float)dz);
+                                                         const StepGeo& sg, const float4* __restrict__ posf,
+                                                         int i, int j) {
+  const float gd = g.f.gdot;
+  const float k6 = g.f.k6;
+  // double-float separation from cell-local hi/lo words and the cell offset
+  // (listed pairs are one cell apart at most; a pair across y = L_y has its
+  // owner in the top row and its partner in row 0, image shifted by off)
+  const float4 pi = posf[i], pj = posf[j], li = s.posl[i], lj = s.posl[j];
+  const int ci = s.cellc[i], cj = s.cellc[j];
+  const int nx = g.nc[0], ny = g.nc[1], nz = g.nc[2];
+  const int cyi = (ci >> 10) & 1023, cyj = (cj >> 10) & 1023;
+  const bool le = cyi == ny - 1 && cyj == 0;
+  int wx = (cj & 1023) - (ci & 1023) + (le ? sg.fsh : 0);
+  wx %= nx;
+  if (wx < 0) wx += nx;
+  if (wx >= nx - (le ? 2 : 1)) wx -= nx;
+  const int wy = le ? 1 : cyj - cyi;
+  int wz = (cj >> 20) - (ci >> 20);
+  if (wz > 1) wz -= nz; else if (wz < -1) wz += nz;
+  FF cx = FF{(float)wx * g.csf[0], (float)wx * g.cs_lo[0]};
+  if (le) cx = ff_add(cx, FF{sg.offr_hi, sg.offr_lo});
+  const FF dxf = ff_add(two_sum(pj.x, -pi.x), ff_add(cx, FF{lj.x - li.x, 0.f}));
+  const FF dyf = ff_add(two_sum(pj.y, -pi.y),
+                        ff_add(FF{(float)wy * g.csf[1], (float)wy * g.cs_lo[1]}, FF{lj.y - li.y, 0.f}));
+  const FF dzf = ff_add(two_sum(pj.z, -pi.z),
+                        ff_add(FF{(float)wz * g.csf[2], (float)wz * g.cs_lo[2]}, FF{lj.z - li.z, 0.f}));
+  const FF Sff = ff_add(FF{pi.w, li.w}, FF{pj.w, lj.w});
+  const FF r2ff = ff_add(ff_add(ff_sqr(dxf), ff_sqr(dyf)), ff_sqr(dzf));
+  const FF numff = ff_add(r2ff, ff_neg(ff_sqr(Sff)));          // r^2 - S^2, ~44 bits
+  const float num = numff.hi + numff.lo;
+  const float r2 = r2ff.hi + r2ff.lo;
+  const float ir = rsqrtf(r2);
+  const float rr = r2 * ir;
+  const float S = Sff.hi + Sff.lo;
+  const float d = __fdividef(num, rr + S);
+  const F3 r = f3(dxf.hi + dxf.lo, dyf.hi + dyf.lo, dzf.hi + dzf.lo);
   const F3 nn = ir * r;
   const float4 vi4 = s.vf[i], vj4 = s.vf[j], wi4 = s.wf[i], wj4 = s.wf[j];
   const F3 Vi = f3(vi4.x, vi4.y, vi4.z), Vj = f3(vj4.x, vj4.y, vj4.z);
   const F3 Wi = f3(wi4.x, wi4.y, wi4.z), Wj = f3(wj4.x, wj4.y, wj4.z);
-  const float Ai = (float)ai, Bj = (float)aj;
+  const float Ai = pi.w + li.w, Bj = pj.w + lj.w;
   PairRes<float> q;
-  // ---- contact, Eq. 4-5
+  // ---- contact, Eq. 4-5; the stretch stays in FP64
   F3 Fc = f3(0, 0, 0), nxf = f3(0, 0, 0);
   q.xi[0] = q.xi[1] = q.xi[2] = 0.0;
-  q.contact = num < 0.0;
+  q.contact = num < 0.0f;
   if (q.contact) {
     const int idi = s.id[i], idj = s.id[j];
-    const double sgn = idi < idj ? 1.0 : -1.0;
+    const float sg = idi < idj ? 1.0f : -1.0f;   // stored (lo -> hi) vs i -> j orientation
     double xo[3];
     history_lookup(g, H, idi, idj, xo);
     // u_j(image) - u_i = (V_j - V_i) + gdot dy x
-    const F3 du = (Vj - Vi) + f3(gd * (float)dy, 0.f, 0.f);
+    const F3 du = (Vj - Vi) + f3(gd * r.y, 0.f, 0.f);
     const F3 wi = f3(Wi.x, Wi.y, Wi.z - 0.5f * gd), wj = f3(Wj.x, Wj.y, Wj.z - 0.5f * gd);
-    const float fn = (float)g.kn * d + (float)g.gn * dotf(nn, du);
+    const float fn = g.f.kn * d + g.f.gn * dotf(nn, du);
     const F3 ut = tangf(nn, du - crossf(Ai * wi + Bj * wj, nn));
-    const double n0 = nn.x, n1 = nn.y, n2 = nn.z;
-    const double x0 = sgn * xo[0], x1 = sgn * xo[1], x2 = sgn * xo[2];
-    const double pn = n0 * x0 + n1 * x1 + n2 * x2;
-    double xs0 = x0 - pn * n0 + (double)(ut.x * (float)g.dt);
-    double xs1 = x1 - pn * n1 + (double)(ut.y * (float)g.dt);
-    double xs2 = x2 - pn * n2 + (double)(ut.z * (float)g.dt);
-    const double cap = g.mu * fabs((double)fn) / g.kt;
-    const double xm2 = xs0 * xs0 + xs1 * xs1 + xs2 * xs2;
+    // stretch (stored orientation) in FP64: xi + delta, with the small change
+    // delta = -n (n.xi) + s u_t dt (projection onto the new tangent plane and
+    // the increment) formed in FP32
+    const F3 xf = f3((float)xo[0], (float)xo[1], (float)xo[2]);
+    const float pn = dotf(nn, xf);
+    const float sdt = sg * g.f.dt;
+    double xs0 = xo[0] + (double)(sdt * ut.x - pn * nn.x);
+    double xs1 = xo[1] + (double)(sdt * ut.y - pn * nn.y);
+    double xs2 = xo[2] + (double)(sdt * ut.z - pn * nn.z);
+    F3 xsf = f3((float)xs0, (float)xs1, (float)xs2);
+    const float cap = g.f.mu_kt * fabsf(fn);
+    const float xm2 = dotf(xsf, xsf);
     if (xm2 > cap * cap) {
-      const double f = cap / sqrt(xm2);
-      xs0 *= f; xs1 *= f; xs2 *= f;
+      const float fs = cap * rsqrtf(xm2);
+      const double fd = (double)fs;
+      xs0 *= fd; xs1 *= fd; xs2 *= fd;
+      xsf = fs * xsf;
     }
-    const F3 Ft = (float)g.kt * f3((float)xs0, (float)xs1, (float)xs2);
+    const F3 Ft = (sg * g.f.kt) * xsf;
     Fc = fn * nn + Ft;
     nxf = crossf(nn, Ft);
-    q.xi[0] = sgn * xs0; q.xi[1] = sgn * xs1; q.xi[2] = sgn * xs2;
+    q.xi[0] = xs0; q.xi[1] = xs1; q.xi[2] = xs2;
   }
   // ---- lubrication, App. A (FP32)
-  float ds = 2.0f * d / S;
+  const float iS = __fdividef(1.0f, S), iS2 = iS * iS, iS3 = iS2 * iS;
+  float ds = 2.0f * d * iS;
   ds = ds > 0.0f ? ds : 0.0f;
-  const float dd = ds + (float)g.eps;
-  const float X = 1.0f / dd;
-  const float Y = -logf(dd);
+  const float dd = ds + g.f.eps;
+  const float X = __fdividef(1.0f, dd);
+  const float Y = -__logf(dd);
   const float A = Ai, B = Bj, AB = A * B;
-  const float iS = 1.0f / S, iS2 = iS * iS, iS3 = iS2 * iS;
   const float xa = X * 2.0f * AB * AB * iS3;
   const float ya = Y * (4.0f / 15.0f) * AB * (2.0f * A * A + AB + 2.0f * B * B) * iS3;
   const float ybi = -Y * (2.0f / 15.0f) * A * AB * (4.0f * A + B) * iS2;
@@ -326,8 +347,9 @@ __device__ __forceinline__ int bits_owner(double v) { return (int)__double_as_lo
 
 template <bool MIXED>
 __global__ void __launch_bounds__(kPairThreads)
-k_pairs(Geo g, StateBuf s, ListBuf W, ListBuf H, void* __restrict__ own_v, int* __restrict__ bw_count,
-        void* __restrict__ bw_v, double* __restrict__ spart, DevStatus* st, int adv) {
+k_pairs(Geo g, StateBuf s, ListBuf W, ListBuf H, const float4* __restrict__ posf, void* __restrict__ own_v,
+        int* __restrict__ bw_count, void* __restrict__ bw_v, double* __restrict__ spart, DevStatus* st,
+        int adv) {
   using R = typename std::conditional<MIXED, float, double>::type;
   if (dev_err(st)) return;
   R* __restrict__ own = static_cast<R*>(own_v);
@@ -342,7 +364,8 @@ k_pairs(Geo g, StateBuf s, ListBuf W, ListBuf H, void* __restrict__ own_v, int* 
     return;
   }
   __shared__ R acc[kWarps][32][6];
-  const double off = le_offset(g, dev_nstep(st) + adv);
+  const StepGeo sg = st->sg;
+  const double off = sg.off;
   R Sx[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   int ncont = 0;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -378,7 +401,7 @@ k_pairs(Geo g, StateBuf s, ListBuf W, ListBuf H, void* __restrict__ own_v, int* 
         const int p = base + t;
         const int j = W.list[(int64_t)i * g.M + kk];
         PairRes<R> q;
-        if constexpr (MIXED) q = pair_eval_mixed(g, s, H, off, i, j);
+        if constexpr (MIXED) q = pair_eval_mixed(g, s, H, sg, posf, i, j);
         else q = pair_eval_fp64(g, s, H, off, i, j);
         v[0] = q.F[0]; v[1] = q.F[1]; v[2] = q.F[2];
         v[3] = q.Ti[0]; v[4] = q.Ti[1]; v[5] = q.Ti[2];
@@ -431,12 +454,14 @@ k_pairs(Geo g, StateBuf s, ListBuf W, ListBuf H, void* __restrict__ own_v, int* 
     __syncwarp();
   }
   // FP64 block reduction of the stresslet (fixed tree)
+  // (in mixed precision the 32 lanes of a warp are pre-summed in FP32, the
+  // warps and blocks in FP64)
   __shared__ double red[kWarps][9];
 #pragma unroll
   for (int q = 0; q < 9; ++q) {
-    double v = (double)Sx[q];
+    R v = Sx[q];
     for (int dlt = 16; dlt > 0; dlt >>= 1) v += __shfl_down_sync(0xffffffffu, v, dlt);
-    if (lane == 0) red[wid][q] = v;
+    if (lane == 0) red[wid][q] = (double)v;
   }
   int c = ncont;
   for (int dlt = 16; dlt > 0; dlt >>= 1) c += __shfl_down_sync(0xffffffffu, c, dlt);
@@ -492,7 +517,7 @@ k_gather(Geo g, StateBuf s, const void* __restrict__ own_v, const int* __restric
     // Stokes drag on the FP32 velocities relative to the ambient flow
     const float af = (float)a;
     const float4 v4 = s.vf[j], w4 = s.wf[j];
-    const float kd = -(float)g.k6 * af, kr = -(float)g.k8 * af * af * af;
+    const float kd = -g.f.k6 * af, kr = -g.f.k8 * af * af * af;
     F[0] += kd * v4.x; F[1] += kd * v4.y; F[2] += kd * v4.z;
     T[0] += kr * w4.x; T[1] += kr * w4.y; T[2] += kr * w4.z;
   } else {
@@ -505,8 +530,8 @@ k_gather(Geo g, StateBuf s, const void* __restrict__ own_v, const int* __restric
     T[1] += kr * s.w[n + j];
     T[2] += kr * (s.w[2 * n + j] + 0.5 * g.gdot);
   }
-  if (!(isfinite((double)F[0]) && isfinite((double)F[1]) && isfinite((double)F[2]) &&
-        isfinite((double)T[0]) && isfinite((double)T[1]) && isfinite((double)T[2])))
+  if (!(isfinite(F[0]) && isfinite(F[1]) && isfinite(F[2]) && isfinite(T[0]) && isfinite(T[1]) &&
+        isfinite(T[2])))
     set_err(st, DSS_ERR_NONFINITE);
   if (mode == G_EVAL) {
     if (Fout) { Fout[id] = F[0]; Fout[n + id] = F[1]; Fout[2 * n + id] = F[2]; }
@@ -514,10 +539,16 @@ k_gather(Geo g, StateBuf s, const void* __restrict__ own_v, const int* __restric
     return;
   }
   // accelerations: m = 4/3 pi rho a^3, I = 2/5 m a^2
-  const double m = 4.0 / 3.0 * DSS_PI * g.rho * a * a * a;
-  const double im = 1.0 / m;
-  const double iI = im * (2.5 / (a * a));
-  const R imr = (R)im, iIr = (R)iI;
+  R imr, iIr;
+  if constexpr (MIXED) {
+    const float af = (float)a;
+    imr = 1.0f / (g.f.mass_c * af * af * af);
+    iIr = imr * (2.5f / (af * af));
+  } else {
+    const double m = 4.0 / 3.0 * DSS_PI * g.rho * a * a * a;
+    imr = 1.0 / m;
+    iIr = imr * (2.5 / (a * a));
+  }
   const R al[3] = {F[0] * imr, F[1] * imr, F[2] * imr};
   const R aw[3] = {T[0] * iIr, T[1] * iIr, T[2] * iIr};
 #pragma unroll
@@ -610,12 +641,12 @@ void launch_forces(dss_handle* h, int stbuf, int work_list, int hist_list, int a
   prof_mark(h, 5);
   if (mixed)
     k_pairs<true><<<pb, kPairThreads, 0, h->stream>>>(h->g, h->st[stbuf], h->lb[work_list],
-                                                      h->lb[hist_list], h->own, h->bw_count, h->bw_rec,
-                                                      h->spart, h->status, adv);
+                                                      h->lb[hist_list], h->posf, h->own, h->bw_count,
+                                                      h->bw_rec, h->spart, h->status, adv);
   else
     k_pairs<false><<<pb, kPairThreads, 0, h->stream>>>(h->g, h->st[stbuf], h->lb[work_list],
-                                                       h->lb[hist_list], h->own, h->bw_count, h->bw_rec,
-                                                       h->spart, h->status, adv);
+                                                       h->lb[hist_list], h->posf, h->own, h->bw_count,
+                                                       h->bw_rec, h->spart, h->status, adv);
   prof_mark(h, 6);
   if (mixed)
     k_gather<true><<<(n + kThreads - 1) / kThreads, kThreads, 0, h->stream>>>(

@@ -25,8 +25,18 @@ enum {
   ST_WORDS = 16
 };
 
+// Lees-Edwards geometry of the time the current operation evaluates at,
+// written once per operation by the first kernel (k_key_hist):
+// off = fsh * cs_x + offr, offr = offr_hi + offr_lo in [0, cs_x).
+struct StepGeo {
+  double off;
+  int fsh;
+  float offr_hi, offr_lo;
+};
+
 struct DevStatus {
   int w[ST_WORDS];
+  StepGeo sg;
 };
 
 // Everything a kernel needs to know about the model and the grid, by value.
@@ -54,7 +64,11 @@ struct Geo {
   // FP32 prefilter margin on r^2 (absolute)
   float r2_margin;
   float halfLf[3];
+  struct {             // FP32 copies of the model constants (mixed precision)
+    float kn, kt, gn, mu_kt, dt, eps, gdot, k6, k8, mass_c;
+  } f;
   float csf[3];       // FP32 cell edges
+  float cs_lo[3];     // cs - csf (double-float cell edges)
   double invL[3];     // 1 / L
 };
 
@@ -266,6 +280,40 @@ __device__ __forceinline__ float pair_delta_f(const Geo& g, float ai, float aj) 
 }
 
 // ------------------------------------------------------------------------
+// Double-float arithmetic (a value is hi + lo, |lo| <= ulp(hi)/2): error-free
+// transformations of Knuth (TwoSum) and Dekker (TwoProduct, with FMA), used
+// where the mixed-precision path needs more than FP32's 24 bits without
+// touching GB300's narrow FP64 pipe.
+// ------------------------------------------------------------------------
+struct FF {
+  float hi, lo;
+};
+__device__ __forceinline__ FF two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  const float e = (a - (s - bb)) + (b - bb);
+  return FF{s, e};
+}
+__device__ __forceinline__ FF fast_two_sum(float a, float b) {   // |a| >= |b|
+  const float s = a + b;
+  return FF{s, b - (s - a)};
+}
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  FF s = two_sum(a.hi, b.hi);
+  const FF t = two_sum(a.lo, b.lo);
+  s.lo += t.hi;
+  s = fast_two_sum(s.hi, s.lo);
+  s.lo += t.lo;
+  return fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ FF ff_neg(FF a) { return FF{-a.hi, -a.lo}; }
+__device__ __forceinline__ FF ff_sqr(FF a) {
+  const float p = a.hi * a.hi;
+  const float e = fmaf(a.hi, a.hi, -p);
+  return fast_two_sum(p, e + 2.0f * a.hi * a.lo);
+}
+
+// ------------------------------------------------------------------------
 // Host-side handle
 // ------------------------------------------------------------------------
 struct StateBuf {
@@ -278,6 +326,8 @@ struct StateBuf {
   int* id;      // n persistent id
   float4* vf;   // n, mixed precision: FP32 velocity relative to U_inf (xyz)
   float4* wf;   // n, mixed precision: FP32 angular velocity relative to Omega_inf (xyz)
+  float4* posl; // n, mixed precision: low words of the cell-local position and radius
+  int* cellc;   // n, mixed precision: cell coordinates packed cx | cy << 10 | cz << 20
 };
 
 struct ListBuf {

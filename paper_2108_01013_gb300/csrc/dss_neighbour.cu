@@ -71,11 +71,11 @@ k_enumerate(Geo g, StateBuf s, const float4* __restrict__ posf, const int* __res
     e.s = &s;
     e.posf = posf;
     e.i = i;
-    e.off = le_offset(g, dev_nstep(st) + adv);
+    e.off = st->sg.off;
     e.pi = posf[i];
     e.row = L.list + (int64_t)i * g.M;
-    const int fsh = le_shift_cells(g, e.off);
-    const float offr = (float)(e.off - fsh * g.cs[0]);
+    const int fsh = st->sg.fsh;
+    const float offr = st->sg.offr_hi;
     const int nx = g.nc[0], ny = g.nc[1], nz = g.nc[2];
     const int c = cellid[i];
     const int cx = c % nx, cy = (c / nx) % ny, cz = c / (nx * ny);

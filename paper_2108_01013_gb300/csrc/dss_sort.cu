@@ -89,6 +89,14 @@ k_key_hist(Geo g, StateBuf s, int* __restrict__ key, int* __restrict__ offs,
       st->w[ST_MAXROW] = 0;
       st->w[ST_BAND] = 0;
       st->w[ST_NCONT] = 0;
+      // Lees-Edwards geometry of this operation's time
+      const double off = le_offset(g, dev_nstep(st) + (predict ? 1 : 0));
+      const int fsh = le_shift_cells(g, off);
+      const double offr = off - fsh * g.cs[0];
+      st->sg.off = off;
+      st->sg.fsh = fsh;
+      st->sg.offr_hi = (float)offr;
+      st->sg.offr_lo = (float)(offr - (double)(float)offr);
     }
   }
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -161,16 +169,23 @@ k_rank_gather(Geo g, StateBuf src, StateBuf dst, const int* __restrict__ key,
     dst.wf[f] = make_float4((float)dst.w[f], (float)dst.w[n + f],
                             (float)(dst.w[2 * n + f] + 0.5 * g.gdot), 0.f);
   }
-  // cell-local FP32 position for the enumeration prefilter
+  // cell-local position (FP32 for the enumeration prefilter; in mixed
+  // precision also the low words, for double-float pair geometry)
   int cx = k % g.nc[0];
   int cy = (k / g.nc[0]) % g.nc[1];
   int cz = k / (g.nc[0] * g.nc[1]);
+  const double lx = p.x - cx * g.cs[0], ly = p.y - cy * g.cs[1], lz = p.z - cz * g.cs[2];
   float4 pf;
-  pf.x = (float)(p.x - cx * g.cs[0]);
-  pf.y = (float)(p.y - cy * g.cs[1]);
-  pf.z = (float)(p.z - cz * g.cs[2]);
+  pf.x = (float)lx;
+  pf.y = (float)ly;
+  pf.z = (float)lz;
   pf.w = (float)a;
   posf[f] = pf;
+  if (g.precision == DSS_MIXED) {
+    dst.posl[f] = make_float4((float)(lx - (double)pf.x), (float)(ly - (double)pf.y),
+                              (float)(lz - (double)pf.z), (float)(a - (double)pf.w));
+    dst.cellc[f] = cx | (cy << 10) | (cz << 20);
+  }
 }
 
 }  // namespace
