@@ -179,7 +179,7 @@ int dss_get_counters(dss_handle *h, dss_counters *c);
  * the work stream; dss_step then synchronises after every step and adds each
  * kernel's event-to-event time to a running sum.  Turning it on or off
  * resets the sums and re-captures the step. */
-#define DSS_PROF_KERNELS 8
+#define DSS_PROF_KERNELS 7
 int dss_set_profiling(dss_handle *h, int on);
 
 /* Running per-kernel sums in milliseconds (ms[DSS_PROF_KERNELS]) and the
@@ -188,6 +188,11 @@ int dss_get_profile(dss_handle *h, double *ms, int64_t *steps);
 
 /* Name of profiled kernel k (0 <= k < DSS_PROF_KERNELS), "" otherwise. */
 const char *dss_profile_name(int k);
+
+/* GPU time in milliseconds of the step graphs of the last dss_step call
+ * (CUDA events recorded on the work stream just before the first and just
+ * after the last graph launch; no per-kernel events). */
+int dss_last_step_ms(dss_handle *h, double *ms);
 
 /* Bytes of device memory the handle holds. */
 int64_t dss_device_bytes(const dss_handle *h);

@@ -83,7 +83,7 @@ class Counters(Structure):
 
 
 FP64, MIXED = 0, 1
-PROF_KERNELS = 8
+PROF_KERNELS = 7
 ERRORS = {0: "DSS_OK", -1: "DSS_ERR_ARG", -2: "DSS_ERR_BOX", -3: "DSS_ERR_CAPACITY",
           -4: "DSS_ERR_NONFINITE", -5: "DSS_ERR_UNSTABLE", -6: "DSS_ERR_CUDA",
           -7: "DSS_ERR_TIMEOUT", -8: "DSS_ERR_STATE", -9: "DSS_ERR_INTERNAL",
@@ -108,6 +108,7 @@ SIGNATURES = {
     "dss_set_profiling": (c_int, [c_void_p, c_int]),
     "dss_get_profile": (c_int, [c_void_p, _dp, _lp]),
     "dss_profile_name": (c_char_p, [c_int]),
+    "dss_last_step_ms": (c_int, [c_void_p, _dp]),
     "dss_device_bytes": (c_int64, [c_void_p]),
     "dss_destroy": (None, [c_void_p]),
     "dss_strerror": (c_char_p, [c_int]),

@@ -47,6 +47,8 @@ void free_buffers(dss_handle* h) {
   dfree(h->io3); dfree(h->io3b); dfree(h->io_id); dfree(h->scan_status); dfree(h->scan_ticket);
   dfree(h->sigma);
   dfree(h->a_by_id);
+  dfree(h->done_blocks);
+  h->done_blocks = nullptr;
   h->sigma = nullptr;
   h->a_by_id = nullptr;
   h->posf = nullptr; h->cellid = nullptr; h->perm = nullptr; h->key = nullptr; h->offs = nullptr;
@@ -124,9 +126,10 @@ int alloc_buffers(dss_handle* h) {
       (r = dalloc(h, &h->cell_start, (size_t)h->g.ncell + 1)) || (r = dalloc(h, &h->tmp, n)) ||
       (r = dalloc(h, &h->io3, 3 * n)) || (r = dalloc(h, &h->io3b, 3 * n)) ||
       (r = dalloc(h, &h->io_id, n)) || (r = dalloc(h, &h->sigma, 9)) ||
-      (r = dalloc(h, &h->a_by_id, n)))
+      (r = dalloc(h, &h->a_by_id, n)) || (r = dalloc(h, &h->done_blocks, 1)))
     return r;
   CK(cudaMemsetAsync(h->sigma, 0, 9 * sizeof(double), h->stream));
+  CK(cudaMemsetAsync(h->done_blocks, 0, sizeof(unsigned int), h->stream));
   {
     const size_t rb = h->p.precision == DSS_MIXED ? sizeof(float) : sizeof(double);
     char* own = nullptr;
@@ -529,6 +532,10 @@ int dss_set_state(dss_handle* h, const double* x, const double* a, const int32_t
   CK(cudaGetLastError());
   h->have_state = true;
   h->host_steps_done = 0;
+  if (alpha_lin) {
+    int r0 = sync_status(h);
+    if (r0) return r0;
+  }
   if (!alpha_lin) {
     // alpha^0 from one force evaluation at the initial state (empty history)
     seq_sort_enum(h, false, 0);
@@ -538,8 +545,6 @@ int dss_set_state(dss_handle* h, const double* x, const double* a, const int32_t
     int r = sync_status(h);
     if (r) return r;
     if ((r = status_error(h))) { clear_err(h); return r; }
-  } else {
-    CK(cudaStreamSynchronize(h->stream));
   }
   return DSS_OK;
 }
@@ -627,20 +632,33 @@ int dss_step(dss_handle* h, int64_t nsteps) {
   ENTER(h);
   int64_t remaining = nsteps;
   int retries = 0;
+  h->last_step_ms = 0.0;
+  if (!h->step_ev[0]) {
+    CK(cudaEventCreate(&h->step_ev[0]));
+    CK(cudaEventCreate(&h->step_ev[1]));
+  }
   while (remaining > 0) {
-    int r = sync_status(h);
-    if (r) return r;
+    int r;
+    // the host mirror holds the counter of the last synchronisation; only
+    // dss_step and dss_set_state change it, and both end synchronised
     const int steps0 = h->status_host->w[ST_STEPS];
     const int cur0 = h->cur, hist0 = h->hist;
     int c = cur0, hs = hist0;
     for (int64_t k = 0; k < remaining; ++k) {
-      const int key = c * 2 + hs;
-      h->cur = c;
-      h->hist = hs;
-      if (!h->graph_ok[key]) {
-        r = capture_step(h, key);
+      if (!h->graph_ok[c * 2 + hs]) {
+        h->cur = c;
+        h->hist = hs;
+        r = capture_step(h, c * 2 + hs);
         if (r) return r;
       }
+      c = 1 - c;
+      hs = 1 - hs;
+    }
+    c = cur0;
+    hs = hist0;
+    CK(cudaEventRecord(h->step_ev[0], h->stream));
+    for (int64_t k = 0; k < remaining; ++k) {
+      const int key = c * 2 + hs;
       CK(cudaGraphLaunch(h->step_graph[key], h->stream));
       if (h->profiling) {
         r = accumulate_profile(h);
@@ -649,8 +667,14 @@ int dss_step(dss_handle* h, int64_t nsteps) {
       c = 1 - c;
       hs = 1 - hs;
     }
+    CK(cudaEventRecord(h->step_ev[1], h->stream));
     r = sync_status(h);
     if (r) return r;
+    {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, h->step_ev[0], h->step_ev[1]));
+      h->last_step_ms += ms;
+    }
     const int done = h->status_host->w[ST_STEPS] - steps0;
     h->cur = (done & 1) ? 1 - cur0 : cur0;
     h->hist = (done & 1) ? 1 - hist0 : hist0;
@@ -816,8 +840,14 @@ int dss_get_profile(dss_handle* h, double* ms, int64_t* steps) {
 const char* dss_profile_name(int k) {
   static const char* names[DSS_PROF_KERNELS] = {"k_key_hist", "k_scan_cells", "k_scatter",
                                                   "k_rank_gather", "k_enumerate", "k_pairs",
-                                                  "k_gather", "k_finalize"};
+                                                  "k_gather"};
   return (k >= 0 && k < DSS_PROF_KERNELS) ? names[k] : "";
+}
+
+int dss_last_step_ms(dss_handle* h, double* ms) {
+  if (!h || !ms) return DSS_ERR_ARG;
+  *ms = h->last_step_ms;
+  return DSS_OK;
 }
 
 int64_t dss_device_bytes(const dss_handle* h) { return h ? h->bytes : 0; }
@@ -832,6 +862,8 @@ void dss_destroy(dss_handle* h) {
   if (h->ev_enter) cudaEventDestroy(h->ev_enter);
   for (int k = 0; k <= DSS_PROF_KERNELS; ++k)
     if (h->prof_ev[k]) cudaEventDestroy(h->prof_ev[k]);
+  for (int k = 0; k < 2; ++k)
+    if (h->step_ev[k]) cudaEventDestroy(h->step_ev[k]);
   if (h->stream && h->own_stream) cudaStreamDestroy(h->stream);
   delete h;
 }

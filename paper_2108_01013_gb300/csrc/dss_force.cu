@@ -15,7 +15,8 @@
 //   records of its row taken in increasing owner index (a fixed order, so the
 //   result is bitwise reproducible), Stokes drag (Eq. A1) and the corrector
 //   of Eq. 15d.
-// k_finalize: bulk stress of Eq. 8 from the per-block partials.
+//   The last block of the gather to finish computes the bulk stress of Eq. 8
+//   from the per-block partials and commits the step.
 #include <climits>
 
 #include "dss_internal.cuh"
@@ -474,13 +475,53 @@ k_pairs(Geo g, StateBuf s, ListBuf W, ListBuf H, const float4* __restrict__ posf
   }
 }
 
+// Bulk stress (Eq. 8) from the per-block partials and the step commit, done
+// by the last block of the gather to finish (fixed summation order).
+__device__ void finalize_block(const Geo& g, const double* __restrict__ spart, int nblocks,
+                               double* sigma, DevStatus* st, const int* __restrict__ start,
+                               int step) {
+  __shared__ double red[kThreads][9];
+  double v[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+#pragma unroll
+    for (int q = 0; q < 9; ++q) v[q] += spart[b * 9 + q];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) red[threadIdx.x][q] = v[q];
+  __syncthreads();
+  for (int s2 = blockDim.x / 2; s2 > 0; s2 >>= 1) {
+    if (threadIdx.x < s2)
+#pragma unroll
+      for (int q = 0; q < 9; ++q) red[threadIdx.x][q] += red[threadIdx.x + s2][q];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const int err = dev_err(st);
+    if (!err) {
+      // E_inf: only xy and yx are non-zero (gdot/2)
+      const double Exy = 0.5 * g.gdot;
+      const double V = g.L[0] * g.L[1] * g.L[2];
+      const double ein = 20.0 / 3.0 * DSS_PI * g.eta0 * g.sumA3;
+      for (int q = 0; q < 9; ++q) {
+        const double E = (q == 1 || q == 3) ? Exy : 0.0;
+        sigma[q] = 2.0 * g.eta0 * E + (ein * E + red[0][q]) / V;
+      }
+      st->w[ST_NPAIRS] = start[g.n];
+      if (step) {
+        st->w[ST_STEPS] += 1;
+        int64_t ns = dev_nstep(st) + 1;
+        st->w[ST_NSTEP_LO] = (int)(uint32_t)(ns & 0xffffffffll);
+        st->w[ST_NSTEP_HI] = (int)(ns >> 32);
+      }
+    }
+  }
+}
+
 template <bool MIXED>
-__global__ void __launch_bounds__(kThreads)
-k_gather(Geo g, StateBuf s, const void* __restrict__ own_v, const int* __restrict__ bw_count,
-         const void* __restrict__ bw_v, double* __restrict__ Fout, double* __restrict__ Tout,
-         DevStatus* st, int mode) {
+__device__ __forceinline__ void gather_one(const Geo& g, const StateBuf& s, const void* __restrict__ own_v,
+                                           const int* __restrict__ bw_count, const void* __restrict__ bw_v,
+                                           double* __restrict__ Fout, double* __restrict__ Tout,
+                                           DevStatus* st, int mode) {
   using R = typename std::conditional<MIXED, float, double>::type;
-  if (dev_err(st)) return;
   const R* __restrict__ own = static_cast<const R*>(own_v);
   const R* __restrict__ bw = static_cast<const R*>(bw_v);
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -567,42 +608,25 @@ k_gather(Geo g, StateBuf s, const void* __restrict__ own_v, const int* __restric
   }
 }
 
-// Bulk stress (Eq. 8) and counters.  One block, fixed reduction order.
-__global__ void k_finalize(Geo g, const double* __restrict__ spart, int nblocks, double* sigma,
-                           DevStatus* st, const int* __restrict__ start, int step) {
-  __shared__ double red[256][9];
-  double v[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-  for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
-#pragma unroll
-    for (int q = 0; q < 9; ++q) v[q] += spart[b * 9 + q];
-#pragma unroll
-  for (int q = 0; q < 9; ++q) red[threadIdx.x][q] = v[q];
+template <bool MIXED>
+__global__ void __launch_bounds__(kThreads)
+k_gather(Geo g, StateBuf s, const void* __restrict__ own_v, const int* __restrict__ bw_count,
+         const void* __restrict__ bw_v, double* __restrict__ Fout, double* __restrict__ Tout,
+         DevStatus* st, int mode, const double* __restrict__ spart, int nparts, double* sigma,
+         const int* __restrict__ start, unsigned int* done_blocks) {
+  // no early exit on an earlier error: every block must reach the counter;
+  // the step is committed only when no error is set
+  gather_one<MIXED>(g, s, own_v, bw_count, bw_v, Fout, Tout, st, mode);
+  // the last block to finish computes the stress and commits the step
+  __shared__ bool last;
+  __threadfence();
   __syncthreads();
-  for (int s2 = blockDim.x / 2; s2 > 0; s2 >>= 1) {
-    if (threadIdx.x < s2)
-#pragma unroll
-      for (int q = 0; q < 9; ++q) red[threadIdx.x][q] += red[threadIdx.x + s2][q];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    const int err = dev_err(st);
-    if (!err) {
-      // E_inf: only xy and yx are non-zero (gdot/2)
-      const double Exy = 0.5 * g.gdot;
-      const double V = g.L[0] * g.L[1] * g.L[2];
-      const double ein = 20.0 / 3.0 * DSS_PI * g.eta0 * g.sumA3;
-      for (int q = 0; q < 9; ++q) {
-        const double E = (q == 1 || q == 3) ? Exy : 0.0;
-        sigma[q] = 2.0 * g.eta0 * E + (ein * E + red[0][q]) / V;
-      }
-      st->w[ST_NPAIRS] = start[g.n];
-      if (step) {
-        st->w[ST_STEPS] += 1;
-        int64_t ns = dev_nstep(st) + 1;
-        st->w[ST_NSTEP_LO] = (int)(uint32_t)(ns & 0xffffffffll);
-        st->w[ST_NSTEP_HI] = (int)(ns >> 32);
-      }
-    }
+  if (threadIdx.x == 0) last = atomicAdd(done_blocks, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    finalize_block(g, spart, nparts, sigma, st, start, mode == G_STEP ? 1 : 0);
+    if (threadIdx.x == 0) *done_blocks = 0u;
   }
 }
 
@@ -648,16 +672,16 @@ void launch_forces(dss_handle* h, int stbuf, int work_list, int hist_list, int a
                                                        h->lb[hist_list], h->posf, h->own, h->bw_count,
                                                        h->bw_rec, h->spart, h->status, adv);
   prof_mark(h, 6);
+  const int gb = (n + kThreads - 1) / kThreads;
   if (mixed)
-    k_gather<true><<<(n + kThreads - 1) / kThreads, kThreads, 0, h->stream>>>(
-        h->g, h->st[stbuf], h->own, h->bw_count, h->bw_rec, F_out, T_out, h->status, mode);
+    k_gather<true><<<gb, kThreads, 0, h->stream>>>(h->g, h->st[stbuf], h->own, h->bw_count, h->bw_rec, F_out,
+                                                   T_out, h->status, mode, h->spart, pb, h->sigma,
+                                                   h->lb[work_list].start, h->done_blocks);
   else
-    k_gather<false><<<(n + kThreads - 1) / kThreads, kThreads, 0, h->stream>>>(
-        h->g, h->st[stbuf], h->own, h->bw_count, h->bw_rec, F_out, T_out, h->status, mode);
+    k_gather<false><<<gb, kThreads, 0, h->stream>>>(h->g, h->st[stbuf], h->own, h->bw_count, h->bw_rec, F_out,
+                                                    T_out, h->status, mode, h->spart, pb, h->sigma,
+                                                    h->lb[work_list].start, h->done_blocks);
   prof_mark(h, 7);
-  k_finalize<<<1, 256, 0, h->stream>>>(h->g, h->spart, pb, h->sigma, h->status,
-                                       h->lb[work_list].start, mode == G_STEP ? 1 : 0);
-  prof_mark(h, 8);
 }
 
 void launch_pairs_out(dss_handle* h, int list, long long* out) {

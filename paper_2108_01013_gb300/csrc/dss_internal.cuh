@@ -9,7 +9,7 @@
 #include "../../include/dss.h"
 
 #define DSS_PI 3.14159265358979323846
-#define DSS_PROF_KERNELS 8
+#define DSS_PROF_KERNELS 7
 
 // Device status word layout (int32 slots in DevStatus::w).
 enum {
@@ -280,6 +280,54 @@ __device__ __forceinline__ float pair_delta_f(const Geo& g, float ai, float aj) 
 }
 
 // ------------------------------------------------------------------------
+// Decoupled look-back for single-pass scans (tiles taken in launch order
+// through an atomic ticket, so every predecessor is already running).  One
+// warp publishes the tile's aggregate, then polls 32 predecessors per round:
+// it sums the aggregates up to the nearest predecessor holding an inclusive
+// prefix.  Every wait is bounded; on give-up it reports DSS_ERR_TIMEOUT.
+// Called by all 32 lanes of one warp; returns the exclusive prefix.
+// ------------------------------------------------------------------------
+constexpr unsigned long long kLbAgg = 1ull << 32;
+constexpr unsigned long long kLbPre = 2ull << 32;
+
+__device__ __forceinline__ int lookback_warp(unsigned long long* status, int tile, int agg,
+                                             DevStatus* st) {
+  const int lane = threadIdx.x & 31;
+  if (tile == 0) {
+    if (lane == 0) atomicExch(&status[0], kLbPre | (unsigned)agg);
+    return 0;
+  }
+  if (lane == 0) atomicExch(&status[tile], kLbAgg | (unsigned)agg);
+  int prefix = 0;
+  int t = tile - 1;
+  long long spins = 0;
+  while (true) {
+    const int idx = t - lane;                 // lane 0: nearest predecessor
+    const unsigned long long w = idx >= 0 ? atomicAdd(&status[idx], 0ull) : 0ull;
+    const unsigned f = (unsigned)(w >> 32);
+    const unsigned not_ready = __ballot_sync(0xffffffffu, f == 0u);
+    const unsigned pre = __ballot_sync(0xffffffffu, f == 2u);
+    const int p = pre ? __ffs(pre) - 1 : 32;
+    const unsigned need = p == 32 ? 0xffffffffu : (p == 31 ? 0xffffffffu : ((2u << p) - 1u));
+    if (not_ready & need) {
+      if (++spins > (1ll << 22)) {
+        if (lane == 0) set_err(st, DSS_ERR_TIMEOUT);
+        break;
+      }
+      __nanosleep(20);
+      continue;
+    }
+    int v = (lane <= p && idx >= 0) ? (int)(unsigned)(w & 0xffffffffull) : 0;
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+    prefix += v;
+    if (p < 32) break;
+    t -= 32;
+  }
+  if (lane == 0) atomicExch(&status[tile], kLbPre | (unsigned)(prefix + agg));
+  return prefix;
+}
+
+// ------------------------------------------------------------------------
 // Double-float arithmetic (a value is hi + lo, |lo| <= ulp(hi)/2): error-free
 // transformations of Knuth (TwoSum) and Dekker (TwoProduct, with FMA), used
 // where the mixed-precision path needs more than FP32's 24 bits without
@@ -352,6 +400,8 @@ struct dss_handle {
   bool profiling;
   bool capturing;
   cudaEvent_t prof_ev[DSS_PROF_KERNELS + 1];
+  cudaEvent_t step_ev[2];    // around the graph launches of one dss_step call
+  double last_step_ms;
   double prof_ms[DSS_PROF_KERNELS];
   int64_t prof_count;
   double* a_by_id;           // n radii in id order (dss_load_state)
@@ -386,6 +436,7 @@ struct dss_handle {
   double* spart;     // 9 * max pair blocks
   int spart_blocks;
   double* sigma;     // 9
+  unsigned int* done_blocks;  // last-block counter of the gather (reset by that block)
   // scans
   unsigned long long* scan_status;  // tile status words (2 scans)
   int* scan_ticket;                 // 2 tickets

@@ -14,8 +14,6 @@
 
 namespace {
 constexpr int kThreads = 128;
-constexpr unsigned long long kFlagAgg = 1ull << 32;
-constexpr unsigned long long kFlagPre = 2ull << 32;
 
 // Visits the candidates of one stencil cell and appends the pairs.
 struct EnumCtx {
@@ -134,40 +132,21 @@ k_enumerate(Geo g, StateBuf s, const float4* __restrict__ posf, const int* __res
   }
   if (lane == 31) s_warp[wid] = incl;
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (wid == 0) {
     int run = 0;
-    for (int w = 0; w < kThreads / 32; ++w) {
-      const int t = s_warp[w];
-      s_warp[w] = run;
-      run += t;
-    }
-    const int agg = run;
-    int prefix = 0;
-    if (tile == 0) {
-      atomicExch(&scan_status[tile], kFlagPre | (unsigned)agg);
-    } else {
-      atomicExch(&scan_status[tile], kFlagAgg | (unsigned)agg);
-      int t = tile - 1;
-      long long spins = 0;
-      while (t >= 0) {
-        const unsigned long long w = atomicAdd(&scan_status[t], 0ull);
-        const unsigned long long f = w & (3ull << 32);
-        if (f == 0ull) {
-          if (++spins > (1ll << 24)) {
-            set_err(st, DSS_ERR_TIMEOUT);
-            break;
-          }
-          __nanosleep(32);
-          continue;
-        }
-        prefix += (int)(unsigned)(w & 0xffffffffull);
-        if (f == kFlagPre) break;
-        --t;
+    if (lane == 0) {
+      for (int w = 0; w < kThreads / 32; ++w) {
+        const int t = s_warp[w];
+        s_warp[w] = run;
+        run += t;
       }
-      atomicExch(&scan_status[tile], kFlagPre | (unsigned)(prefix + agg));
     }
-    s_prefix = prefix;
-    if ((tile + 1) * kThreads >= n) L.start[n] = prefix + agg;
+    const int agg = __shfl_sync(0xffffffffu, run, 0);
+    const int prefix = lookback_warp(scan_status, tile, agg, st);
+    if (lane == 0) {
+      s_prefix = prefix;
+      if ((tile + 1) * kThreads >= n) L.start[n] = prefix + agg;
+    }
   }
   __syncthreads();
   if (i < n) L.start[i] = s_prefix + s_warp[wid] + incl - v;

@@ -20,8 +20,8 @@ struct Pred {
   int cross;
 };
 
-__device__ __forceinline__ Pred predict_one(const Geo& g, double off, const StateBuf& s, int i,
-                                            bool predict) {
+__device__ __forceinline__ Pred predict_one(const Geo& g, const DevStatus* st, int adv,
+                                            const StateBuf& s, int i, bool predict) {
   const int n = g.n;
   Pred r;
   double x = s.x[i], y = s.x[n + i], z = s.x[2 * n + i];
@@ -39,21 +39,23 @@ __device__ __forceinline__ Pred predict_one(const Geo& g, double off, const Stat
     uy = __dadd_rn(uy, __dmul_rn(hdt, ay));
     uz = __dadd_rn(uz, __dmul_rn(hdt, az));
     // Lees-Edwards wrap: leaving through y >= L_y re-enters at the bottom
-    // shifted by -off along x with u_x - gdot L_y, and vice versa.
+    // shifted by -off along x with u_x - gdot L_y, and vice versa
     const double Ly = g.L[1];
     if (y >= Ly) {
       y = __dsub_rn(y, Ly);
-      x = __dsub_rn(x, off);
+      x = __dsub_rn(x, le_offset(g, dev_nstep(st) + adv));
       r.cross = -1;
     } else if (y < 0.0) {
       y = __dadd_rn(y, Ly);
-      x = __dadd_rn(x, off);
+      x = __dadd_rn(x, le_offset(g, dev_nstep(st) + adv));
       r.cross = 1;
       if (y >= Ly) y = 0.0;
     }
-    x = fmod(x, g.L[0]);
-    if (x < 0.0) x = __dadd_rn(x, g.L[0]);
-    if (x >= g.L[0]) x = __dsub_rn(x, g.L[0]);
+    // x back into [0, L_x): two conditional shifts give the same bits as
+    // fmod followed by the two corrections, for |x| < 2 L_x
+    const double Lx = g.L[0];
+    if (x < 0.0) x = __dadd_rn(x, Lx); else if (x >= Lx) x = __dsub_rn(x, Lx);
+    if (x < 0.0) x = __dadd_rn(x, Lx); else if (x >= Lx) x = __dsub_rn(x, Lx);
     if (z >= g.L[2]) {
       z = __dsub_rn(z, g.L[2]);
     } else if (z < 0.0) {
@@ -101,8 +103,7 @@ k_key_hist(Geo g, StateBuf s, int* __restrict__ key, int* __restrict__ offs,
   }
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= g.n) return;
-  double off = le_offset(g, dev_nstep(st) + (predict ? 1 : 0));
-  Pred p = predict_one(g, off, s, i, predict);
+  Pred p = predict_one(g, st, predict ? 1 : 0, s, i, predict);
   int k = cell_key(g, p.x, p.y, p.z);
   unsigned act = __activemask();
   unsigned peers = __match_any_sync(act, k);
@@ -144,8 +145,7 @@ k_rank_gather(Geo g, StateBuf src, StateBuf dst, const int* __restrict__ key,
   int f = c0 + rank;
   perm[f] = o;
   cellid[f] = k;
-  double off = le_offset(g, dev_nstep(st) + (predict ? 1 : 0));
-  Pred p = predict_one(g, off, src, o, predict);
+  Pred p = predict_one(g, st, predict ? 1 : 0, src, o, predict);
   dst.x[f] = p.x; dst.x[n + f] = p.y; dst.x[2 * n + f] = p.z;
   dst.u[f] = p.ux; dst.u[n + f] = p.uy; dst.u[2 * n + f] = p.uz;
   if (predict) {
@@ -197,8 +197,6 @@ namespace {
 constexpr int kScanThreads = 512;
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanThreads * kScanItems;
-constexpr unsigned long long kFlagAgg = 1ull << 32;
-constexpr unsigned long long kFlagPre = 2ull << 32;
 
 __global__ void __launch_bounds__(kScanThreads)
 k_scan(const int* __restrict__ in, int* __restrict__ out, int count,
@@ -239,33 +237,16 @@ k_scan(const int* __restrict__ in, int* __restrict__ out, int count,
   __syncthreads();
   int excl = incl - local + s_warp[wid];
   // tile aggregate and look-back
-  if (threadIdx.x == kScanThreads - 1) {
-    int agg = excl + local;
-    int prefix = 0;
-    if (tile == 0) {
-      atomicExch(&status[tile], kFlagPre | (unsigned)agg);
-    } else {
-      atomicExch(&status[tile], kFlagAgg | (unsigned)agg);
-      int t = tile - 1;
-      long long spins = 0;
-      bool ok = true;
-      while (t >= 0) {
-        unsigned long long w = atomicAdd(&status[t], 0ull);
-        unsigned long long f = w & (3ull << 32);
-        if (f == 0ull) {
-          if (++spins > (1ll << 24)) { ok = false; break; }
-          __nanosleep(32);
-          continue;
-        }
-        prefix += (int)(unsigned)(w & 0xffffffffull);
-        if (f == kFlagPre) break;
-        --t;
-      }
-      if (!ok) set_err(st, DSS_ERR_TIMEOUT);
-      atomicExch(&status[tile], kFlagPre | (unsigned)(prefix + agg));
+  __shared__ int s_agg;
+  if (threadIdx.x == kScanThreads - 1) s_agg = excl + local;
+  __syncthreads();
+  if (wid == 0) {
+    const int agg = s_agg;
+    const int prefix = lookback_warp(status, tile, agg, st);
+    if (lane == 0) {
+      s_prefix = prefix;
+      if (base + kScanTile >= count) out[count] = prefix + agg;   // total
     }
-    s_prefix = prefix;
-    if (base + kScanTile >= count) out[count] = prefix + agg;   // total
   }
   __syncthreads();
   int run = s_prefix + excl;

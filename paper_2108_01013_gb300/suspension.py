@@ -101,6 +101,12 @@ class Suspension:
     def set_profiling(self, on: bool = True):
         nat.check(self.lib.dss_set_profiling(self._h, 1 if on else 0), "dss_set_profiling")
 
+    def last_step_ms(self) -> float:
+        """GPU time of the last step() call (events around the graph launches)."""
+        ms = c_double(0.0)
+        nat.check(self.lib.dss_last_step_ms(self._h, byref(ms)), "dss_last_step_ms")
+        return ms.value
+
     def profile(self):
         """{kernel name: summed ms} and the number of profiled steps."""
         ms = (c_double * nat.PROF_KERNELS)()
