@@ -110,6 +110,36 @@ int32_t dss_capacity_estimate(double a_min, double a_max, double a0);
 int dss_create(dss_handle **h, const dss_params *p, int64_t n, const double box[3],
                void *cuda_stream);
 
+/* Batch of K independent suspensions in one handle (the flow-curve sweep of
+ * Sec. IV runs one suspension per shear rate; here they share every launch).
+ * Instance k has n[k] particles (n[k] >= DSS_BATCH_MIN_N when K > 1), box
+ * edges box[3k..3k+2], shear rate shear_rate[k] and normal dashpot
+ * gamma_n[k] (gamma_n NULL: p->gamma_n for all); p->shear_rate and
+ * p->gamma_n are otherwise ignored, every other parameter (contact,
+ * lubrication, dt, precision) is shared.  Particles are numbered
+ * instance-major: instance k holds indices and ids
+ * [n[0]+...+n[k-1], n[0]+...+n[k]).  Every other entry point applies to the
+ * concatenated system: dss_set_state takes the concatenated arrays (ids of
+ * instance k a permutation of its own range), dss_step advances all
+ * instances together, one CUDA graph per step for the whole batch.  The
+ * instances do not interact; each has its own cell grid and Lees-Edwards
+ * offset.  All pointers are host memory.  dss_create is the case K = 1. */
+#define DSS_BATCH_MIN_N 256
+int dss_batch_create(dss_handle **h, const dss_params *p, int32_t K, const int64_t *n,
+                     const double *box, const double *shear_rate, const double *gamma_n,
+                     void *cuda_stream);
+
+/* Number of instances of the handle (0 for NULL). */
+int32_t dss_batch_size(const dss_handle *h);
+
+/* Stress of every instance (Eq. 8, row-major 3x3 each): sigma[9K] at the
+ * last force evaluation, and sigma_mean[9K] = the mean over the steps
+ * committed by dss_step since dss_set_state or the last reset (*steps
+ * receives their number; the mean is 0 when none).  Any of sigma,
+ * sigma_mean, steps may be NULL; reset != 0 restarts the mean after
+ * reading it.  Host or device pointers; synchronises the stream. */
+int dss_batch_stress(dss_handle *h, double *sigma, double *sigma_mean, int64_t *steps, int reset);
+
 /* Loads the state: x (3n, inside [0, L) on every axis), radii a (n, > 0),
  * ids (n, permutation of 0..n-1, or NULL), velocity u (3n, NULL: U_inf(x)),
  * angular velocity w (3n, NULL: Omega_inf), accelerations alpha_lin,
@@ -168,7 +198,7 @@ int dss_force_eval(dss_handle *h, double *F, double *T);
 int dss_step(dss_handle *h, int64_t nsteps);
 
 /* Bulk stress of the last force evaluation (Eq. 8), row-major 3x3, host
- * memory.  Synchronises the stream. */
+ * memory (instance 0 of a batch).  Synchronises the stream. */
 int dss_stress(dss_handle *h, double sigma[9]);
 
 /* Counters of the last force evaluation (synchronises). */

@@ -6,4 +6,4 @@ ABI of ``include/dss.h``); this package builds it, loads it through ctypes and
 offers ``Suspension`` on top.  ``synth`` makes seeded synthetic inputs.
 """
 from ._native import build, load, DssError, FP64, MIXED, Params  # noqa: F401
-from .suspension import Suspension, default_params, capacity_estimate  # noqa: F401
+from .suspension import Batch, Suspension, default_params, capacity_estimate  # noqa: F401

@@ -84,6 +84,7 @@ class Counters(Structure):
 
 FP64, MIXED = 0, 1
 PROF_KERNELS = 7
+BATCH_MIN_N = 256
 ERRORS = {0: "DSS_OK", -1: "DSS_ERR_ARG", -2: "DSS_ERR_BOX", -3: "DSS_ERR_CAPACITY",
           -4: "DSS_ERR_NONFINITE", -5: "DSS_ERR_UNSTABLE", -6: "DSS_ERR_CUDA",
           -7: "DSS_ERR_TIMEOUT", -8: "DSS_ERR_STATE", -9: "DSS_ERR_INTERNAL",
@@ -94,6 +95,10 @@ _dp, _ip, _lp, _vp = POINTER(c_double), POINTER(c_int32), POINTER(c_int64), c_vo
 SIGNATURES = {
     "dss_capacity_estimate": (c_int32, [c_double, c_double, c_double]),
     "dss_create": (c_int, [POINTER(c_void_p), POINTER(Params), c_int64, _dp, c_void_p]),
+    "dss_batch_create": (c_int, [POINTER(c_void_p), POINTER(Params), c_int32, _lp, _dp, _dp, _dp,
+                                 c_void_p]),
+    "dss_batch_size": (c_int32, [c_void_p]),
+    "dss_batch_stress": (c_int, [c_void_p, _vp, _vp, _lp, c_int]),
     "dss_set_state": (c_int, [c_void_p, _vp, _vp, _vp, _vp, _vp, _vp, _vp, c_int64]),
     "dss_get_state": (c_int, [c_void_p, _vp, _vp, _vp, _vp, _vp]),
     "dss_set_history": (c_int, [c_void_p, c_int64, _vp, _vp]),

@@ -32,7 +32,7 @@ void dfree(void* p) {
 void free_buffers(dss_handle* h) {
   for (int b = 0; b < 2; ++b) {
     StateBuf& s = h->st[b];
-    dfree(s.x); dfree(s.u); dfree(s.w); dfree(s.al); dfree(s.aw); dfree(s.a); dfree(s.id);
+    dfree(s.x); dfree(s.u); dfree(s.w); dfree(s.al); dfree(s.aw); dfree(s.a); dfree(s.id); dfree(s.inst);
     dfree(s.vf); dfree(s.wf); dfree(s.posl); dfree(s.cellc);
     memset(&s, 0, sizeof(s));
     ListBuf& L = h->lb[b];
@@ -46,7 +46,15 @@ void free_buffers(dss_handle* h) {
   h->own = nullptr; h->bw_count = nullptr; h->bw_rec = nullptr;
   dfree(h->io3); dfree(h->io3b); dfree(h->io_id); dfree(h->scan_status); dfree(h->scan_ticket);
   dfree(h->sigma);
+  dfree(h->sigma_sum);
   dfree(h->a_by_id);
+  dfree(h->inst_map);
+  dfree(h->ig);
+  dfree(h->sg);
+  h->sigma_sum = nullptr;
+  h->inst_map = nullptr;
+  h->ig = nullptr;
+  h->sg = nullptr;
   dfree(h->done_blocks);
   h->done_blocks = nullptr;
   h->sigma = nullptr;
@@ -93,7 +101,7 @@ int alloc_pair_buffers(dss_handle* h, int64_t pcap, bool keep_hist) {
   h->g.pcap = pcap;
   double* sp = nullptr;
   const int pb = pair_grid_blocks(h);
-  if ((r = dalloc(h, &sp, 9 * (size_t)pb))) return r;
+  if ((r = dalloc(h, &sp, 18 * (size_t)pb))) return r;
   dfree(h->spart);
   h->spart = sp;
   h->spart_blocks = pb;
@@ -108,7 +116,7 @@ int alloc_buffers(dss_handle* h) {
     StateBuf& s = h->st[b];
     if ((r = dalloc(h, &s.x, 3 * n)) || (r = dalloc(h, &s.u, 3 * n)) || (r = dalloc(h, &s.w, 3 * n)) ||
         (r = dalloc(h, &s.al, 3 * n)) || (r = dalloc(h, &s.aw, 3 * n)) || (r = dalloc(h, &s.a, n)) ||
-        (r = dalloc(h, &s.id, n)))
+        (r = dalloc(h, &s.id, n)) || (r = dalloc(h, &s.inst, n)))
       return r;
     if (h->p.precision == DSS_MIXED &&
         ((r = dalloc(h, &s.vf, n)) || (r = dalloc(h, &s.wf, n)) || (r = dalloc(h, &s.posl, n)) ||
@@ -125,10 +133,13 @@ int alloc_buffers(dss_handle* h) {
       (r = dalloc(h, &h->cell_count, (size_t)h->g.ncell)) ||
       (r = dalloc(h, &h->cell_start, (size_t)h->g.ncell + 1)) || (r = dalloc(h, &h->tmp, n)) ||
       (r = dalloc(h, &h->io3, 3 * n)) || (r = dalloc(h, &h->io3b, 3 * n)) ||
-      (r = dalloc(h, &h->io_id, n)) || (r = dalloc(h, &h->sigma, 9)) ||
-      (r = dalloc(h, &h->a_by_id, n)) || (r = dalloc(h, &h->done_blocks, 1)))
+      (r = dalloc(h, &h->io_id, n)) || (r = dalloc(h, &h->sigma, 9 * (size_t)h->K)) ||
+      (r = dalloc(h, &h->sigma_sum, 9 * (size_t)h->K)) || (r = dalloc(h, &h->a_by_id, n)) ||
+      (r = dalloc(h, &h->inst_map, n)) || (r = dalloc(h, &h->ig, (size_t)h->K)) ||
+      (r = dalloc(h, &h->sg, (size_t)h->K)) || (r = dalloc(h, &h->done_blocks, 1)))
     return r;
-  CK(cudaMemsetAsync(h->sigma, 0, 9 * sizeof(double), h->stream));
+  CK(cudaMemsetAsync(h->sigma, 0, 9 * sizeof(double) * h->K, h->stream));
+  CK(cudaMemsetAsync(h->sigma_sum, 0, 9 * sizeof(double) * h->K, h->stream));
   CK(cudaMemsetAsync(h->done_blocks, 0, sizeof(unsigned int), h->stream));
   {
     const size_t rb = h->p.precision == DSS_MIXED ? sizeof(float) : sizeof(double);
@@ -200,10 +211,12 @@ __global__ void k_iota(int n, int* __restrict__ v) {
   if (i < n) v[i] = i;
 }
 
-__global__ void k_default_vel(int n, const double* __restrict__ x, double gdot, double* __restrict__ u,
+__global__ void k_default_vel(int n, const double* __restrict__ x, const InstGeo* __restrict__ ig,
+                              const int* __restrict__ inst, double* __restrict__ u,
                               double* __restrict__ w, bool du, bool dw) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  const double gdot = ig[inst[i]].gdot;
   if (du) { u[i] = gdot * x[n + i]; u[n + i] = 0.0; u[2 * n + i] = 0.0; }
   if (dw) { w[i] = 0.0; w[n + i] = 0.0; w[2 * n + i] = -0.5 * gdot; }
 }
@@ -313,6 +326,8 @@ int status_error(dss_handle* h) {
   return e ? e : DSS_OK;
 }
 
+// Cell grid of every instance (Sec. II A: cells of edge >= the largest
+// interaction range, 2 a_max + delta_max); cells are numbered instance-major.
 int geometry(dss_handle* h) {
   Geo& g = h->g;
   const dss_params& p = h->p;
@@ -323,27 +338,122 @@ int geometry(dss_handle* h) {
     if (p.cell_size < cmin) return DSS_ERR_ARG;
     cmin = p.cell_size;
   }
-  for (int d = 0; d < 3; ++d) {
-    g.L[d] = h->L[d];
-    g.halfL[d] = 0.5 * h->L[d];
-    g.nc[d] = (int)std::floor(h->L[d] / cmin);
-    if (g.nc[d] < 1) g.nc[d] = 1;
-    g.cs[d] = h->L[d] / g.nc[d];
-    g.inv_cs[d] = 1.0 / g.cs[d];
-    g.halfLf[d] = (float)(0.5 * h->L[d]) * (1.0f - 1e-5f);
-    g.csf[d] = (float)g.cs[d];
-    g.cs_lo[d] = (float)(g.cs[d] - (double)g.csf[d]);
-    g.invL[d] = 1.0 / h->L[d];
+  int64_t cells = 0, pos = 0;
+  for (int k = 0; k < h->K; ++k) {
+    InstGeo& I = h->ig_host[k];
+    const double* L = h->inst_box + 3 * k;
+    for (int d = 0; d < 3; ++d) {
+      I.L[d] = L[d];
+      I.halfL[d] = 0.5 * L[d];
+      I.nc[d] = (int)std::floor(L[d] / cmin);
+      if (I.nc[d] < 1) I.nc[d] = 1;
+      I.cs[d] = L[d] / I.nc[d];
+      I.inv_cs[d] = 1.0 / I.cs[d];
+      I.halfLf[d] = (float)(0.5 * L[d]) * (1.0f - 1e-5f);
+      I.csf[d] = (float)I.cs[d];
+      I.cs_lo[d] = (float)(I.cs[d] - (double)I.csf[d]);
+      I.invL[d] = 1.0 / L[d];
+    }
+    if (I.nc[0] < 4 || I.nc[1] < 3 || I.nc[2] < 3) return DSS_ERR_BOX;
+    if (I.nc[0] > 1023 || I.nc[1] > 1023 || I.nc[2] > 1023) return DSS_ERR_ARG;   // packed coords
+    const int64_t nck = (int64_t)I.nc[0] * I.nc[1] * I.nc[2];
+    if (cells + nck > (int64_t)2000000000) return DSS_ERR_ARG;
+    I.cell_base = (int)cells;
+    I.ncell = (int)nck;
+    cells += nck;
+    const double csmax = std::max(I.cs[0], std::max(I.cs[1], I.cs[2]));
+    I.r2_margin = (float)(1e-4 * csmax * csmax);
+    I.p_begin = (int)pos;
+    pos += h->inst_n[k];
+    I.p_end = (int)pos;
+    I.gdot = h->inst_gdot[k];
+    I.gn = h->inst_gn[k];
+    I.gdot_f = (float)I.gdot;
+    I.gn_f = (float)I.gn;
   }
-  if (g.nc[0] < 4 || g.nc[1] < 3 || g.nc[2] < 3) return DSS_ERR_BOX;
-  if (g.nc[0] > 1023 || g.nc[1] > 1023 || g.nc[2] > 1023) return DSS_ERR_ARG;   // packed coords
-  if ((double)g.nc[0] * g.nc[1] * g.nc[2] > 2.0e9) return DSS_ERR_ARG;
-  g.ncell = g.nc[0] * g.nc[1] * g.nc[2];
-  double csmax = std::max(g.cs[0], std::max(g.cs[1], g.cs[2]));
-  g.r2_margin = (float)(1e-4 * csmax * csmax);
+  g.ncell = (int)cells;
   int M = p.capacity_M > 0 ? p.capacity_M : dss_capacity_estimate(h->a_min, h->a_max, p.a0);
   if (M <= 0) return DSS_ERR_ARG;
   g.M = M;
+  return DSS_OK;
+}
+
+bool valid_params(const dss_params* p) {
+  return (p->kn >= 0) && (p->kt > 0) && (p->gamma_n >= 0) && (p->mu >= 0) && (p->eta0 >= 0) &&
+         (p->rho > 0) && (p->delta_lub >= 0) && (p->lub_eps > 0) && (p->a0 > 0) && (p->dt > 0) &&
+         std::isfinite(p->shear_rate) && (p->lub_cutoff_mode == 0 || p->lub_cutoff_mode == 1) &&
+         (p->precision == DSS_FP64 || p->precision == DSS_MIXED);
+}
+
+// Common constructor: K instances of n[k] particles in boxes box[3k..3k+2]
+// with shear rates gdot[k] and normal dashpots gn[k].
+int create_handle(dss_handle** out, const dss_params* p, int K, const int64_t* n, const double* box,
+                  const double* gdot, const double* gn, void* cuda_stream) {
+  dss_handle* h = new dss_handle();
+  memset((void*)h, 0, sizeof(dss_handle));
+  h->p = *p;
+  h->K = K;
+  h->ig_host = new InstGeo[K];
+  memset((void*)h->ig_host, 0, sizeof(InstGeo) * K);
+  h->inst_box = new double[3 * K];
+  h->inst_gdot = new double[K];
+  h->inst_gn = new double[K];
+  h->inst_n = new int64_t[K];
+  int64_t total = 0;
+  for (int k = 0; k < K; ++k) {
+    for (int d = 0; d < 3; ++d) h->inst_box[3 * k + d] = box[3 * k + d];
+    h->inst_gdot[k] = gdot[k];
+    h->inst_gn[k] = gn[k];
+    h->inst_n[k] = n[k];
+    total += n[k];
+  }
+  h->n = total;
+  h->user_stream = (cudaStream_t)cuda_stream;
+  if (cudaGetDevice(&h->device) != cudaSuccess) { dss_destroy(h); return DSS_ERR_CUDA; }
+  // work runs on the caller's stream; for the legacy default stream (NULL),
+  // where graph capture is not allowed, on a stream of our own ordered after it
+  if (cuda_stream) {
+    h->stream = (cudaStream_t)cuda_stream;
+    h->own_stream = false;
+  } else {
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      dss_destroy(h);
+      return DSS_ERR_CUDA;
+    }
+    h->own_stream = true;
+  }
+  if (cudaEventCreateWithFlags(&h->ev_enter, cudaEventDisableTiming) != cudaSuccess) {
+    dss_destroy(h);
+    return DSS_ERR_CUDA;
+  }
+  if (cudaMalloc((void**)&h->status, sizeof(DevStatus)) != cudaSuccess) {
+    dss_destroy(h);
+    return DSS_ERR_CUDA;
+  }
+  if (cudaMallocHost((void**)&h->status_host, sizeof(DevStatus)) != cudaSuccess) {
+    dss_destroy(h);
+    return DSS_ERR_CUDA;
+  }
+  cudaMemsetAsync(h->status, 0, sizeof(DevStatus), h->stream);
+  Geo& g = h->g;
+  g.n = (int)total;
+  g.K = K;
+  g.kn = p->kn; g.kt = p->kt; g.mu = p->mu;
+  g.eta0 = p->eta0; g.rho = p->rho;
+  g.delta = p->delta_lub; g.eps = p->lub_eps; g.a0 = p->a0;
+  g.mode = p->lub_cutoff_mode; g.precision = p->precision;
+  g.dt = p->dt;
+  g.k6 = 6.0 * DSS_PI * p->eta0;
+  g.k8 = 8.0 * DSS_PI * p->eta0;
+  g.f.kn = (float)p->kn;
+  g.f.kt = (float)p->kt;
+  g.f.mu_kt = (float)(p->mu / p->kt);
+  g.f.dt = (float)p->dt;
+  g.f.eps = (float)p->lub_eps;
+  g.f.k6 = (float)g.k6;
+  g.f.k8 = (float)g.k8;
+  g.f.mass_c = (float)(4.0 / 3.0 * DSS_PI * p->rho);
+  *out = h;
   return DSS_OK;
 }
 
@@ -395,65 +505,31 @@ int dss_create(dss_handle** out, const dss_params* p, int64_t n, const double bo
   *out = nullptr;
   for (int d = 0; d < 3; ++d)
     if (!(box[d] > 0.0) || !std::isfinite(box[d])) return DSS_ERR_ARG;
-  if (!(p->kn >= 0) || !(p->kt > 0) || !(p->gamma_n >= 0) || !(p->mu >= 0) || !(p->eta0 >= 0) ||
-      !(p->rho > 0) || !(p->delta_lub >= 0) || !(p->lub_eps > 0) || !(p->a0 > 0) || !(p->dt > 0) ||
-      !std::isfinite(p->shear_rate) || (p->lub_cutoff_mode != 0 && p->lub_cutoff_mode != 1) ||
-      (p->precision != DSS_FP64 && p->precision != DSS_MIXED))
-    return DSS_ERR_ARG;
-  dss_handle* h = new dss_handle();
-  memset((void*)h, 0, sizeof(dss_handle));
-  h->p = *p;
-  h->n = n;
-  for (int d = 0; d < 3; ++d) h->L[d] = box[d];
-  h->user_stream = (cudaStream_t)cuda_stream;
-  if (cudaGetDevice(&h->device) != cudaSuccess) { delete h; return DSS_ERR_CUDA; }
-  // work runs on the caller's stream; for the legacy default stream (NULL),
-  // where graph capture is not allowed, on a stream of our own ordered after it
-  if (cuda_stream) {
-    h->stream = (cudaStream_t)cuda_stream;
-    h->own_stream = false;
-  } else {
-    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
-      delete h;
-      return DSS_ERR_CUDA;
-    }
-    h->own_stream = true;
+  if (!valid_params(p)) return DSS_ERR_ARG;
+  const double gd = p->shear_rate, gn = p->gamma_n;
+  return create_handle(out, p, 1, &n, box, &gd, &gn, cuda_stream);
+}
+
+int dss_batch_create(dss_handle** out, const dss_params* p, int32_t K, const int64_t* n,
+                     const double* box, const double* shear_rate, const double* gamma_n,
+                     void* cuda_stream) {
+  if (!out || !p || !n || !box || !shear_rate || K < 1 || K > (1 << 20)) return DSS_ERR_ARG;
+  *out = nullptr;
+  if (!valid_params(p)) return DSS_ERR_ARG;
+  int64_t total = 0;
+  for (int k = 0; k < K; ++k) {
+    // a pair block (256 owners) spans at most two instances
+    if (n[k] < (K > 1 ? DSS_BATCH_MIN_N : 2)) return DSS_ERR_ARG;
+    total += n[k];
+    if (total > (int64_t)1 << 30) return DSS_ERR_ARG;
+    for (int d = 0; d < 3; ++d)
+      if (!(box[3 * k + d] > 0.0) || !std::isfinite(box[3 * k + d])) return DSS_ERR_ARG;
+    if (!std::isfinite(shear_rate[k])) return DSS_ERR_ARG;
+    if (gamma_n && !(gamma_n[k] >= 0.0 && std::isfinite(gamma_n[k]))) return DSS_ERR_ARG;
   }
-  if (cudaEventCreateWithFlags(&h->ev_enter, cudaEventDisableTiming) != cudaSuccess) {
-    cudaStreamDestroy(h->stream);
-    delete h;
-    return DSS_ERR_CUDA;
-  }
-  if (cudaMalloc((void**)&h->status, sizeof(DevStatus)) != cudaSuccess) {
-    dss_destroy(h);
-    return DSS_ERR_CUDA;
-  }
-  if (cudaMallocHost((void**)&h->status_host, sizeof(DevStatus)) != cudaSuccess) {
-    dss_destroy(h);
-    return DSS_ERR_CUDA;
-  }
-  cudaMemsetAsync(h->status, 0, sizeof(DevStatus), h->stream);
-  Geo& g = h->g;
-  g.n = (int)n;
-  g.kn = p->kn; g.kt = p->kt; g.gn = p->gamma_n; g.mu = p->mu;
-  g.eta0 = p->eta0; g.rho = p->rho;
-  g.delta = p->delta_lub; g.eps = p->lub_eps; g.a0 = p->a0;
-  g.mode = p->lub_cutoff_mode; g.precision = p->precision;
-  g.gdot = p->shear_rate; g.dt = p->dt;
-  g.k6 = 6.0 * DSS_PI * p->eta0;
-  g.k8 = 8.0 * DSS_PI * p->eta0;
-  g.f.kn = (float)p->kn;
-  g.f.kt = (float)p->kt;
-  g.f.gn = (float)p->gamma_n;
-  g.f.mu_kt = (float)(p->mu / p->kt);
-  g.f.dt = (float)p->dt;
-  g.f.eps = (float)p->lub_eps;
-  g.f.gdot = (float)p->shear_rate;
-  g.f.k6 = (float)g.k6;
-  g.f.k8 = (float)g.k8;
-  g.f.mass_c = (float)(4.0 / 3.0 * DSS_PI * p->rho);
-  *out = h;
-  return DSS_OK;
+  std::vector<double> gn(K);
+  for (int k = 0; k < K; ++k) gn[k] = gamma_n ? gamma_n[k] : p->gamma_n;
+  return create_handle(out, p, K, n, box, shear_rate, gn.data(), cuda_stream);
 }
 
 int dss_set_state(dss_handle* h, const double* x, const double* a, const int32_t* ids,
@@ -467,24 +543,31 @@ int dss_set_state(dss_handle* h, const double* x, const double* a, const int32_t
   std::vector<double> ha(n), hx(3 * n);
   CK(cudaMemcpy(ha.data(), a, sizeof(double) * n, cudaMemcpyDefault));
   CK(cudaMemcpy(hx.data(), x, sizeof(double) * 3 * n, cudaMemcpyDefault));
-  double amin = INFINITY, amax = 0.0, s3 = 0.0;
+  double amin = INFINITY, amax = 0.0;
   for (int64_t i = 0; i < n; ++i) {
     if (!(ha[i] > 0.0) || !std::isfinite(ha[i])) return DSS_ERR_ARG;
     amin = std::min(amin, ha[i]);
     amax = std::max(amax, ha[i]);
-    s3 += ha[i] * ha[i] * ha[i];
+  }
+  // instance of each index (instance-major); positions inside their box
+  std::vector<int32_t> imap(n);
+  std::vector<int64_t> ibeg(h->K + 1, 0);
+  for (int k = 0; k < h->K; ++k) {
+    ibeg[k + 1] = ibeg[k] + h->inst_n[k];
+    for (int64_t i = ibeg[k]; i < ibeg[k + 1]; ++i) imap[i] = k;
   }
   for (int d = 0; d < 3; ++d)
     for (int64_t i = 0; i < n; ++i) {
       double v = hx[d * n + i];
-      if (!(v >= 0.0 && v < h->L[d])) return DSS_ERR_ARG;
+      if (!(v >= 0.0 && v < h->inst_box[3 * imap[i] + d])) return DSS_ERR_ARG;
     }
   std::vector<int32_t> hid(n);
   if (ids) {
+    // ids of instance k are a permutation of its own index range
     CK(cudaMemcpy(hid.data(), ids, sizeof(int32_t) * n, cudaMemcpyDefault));
     std::vector<char> seen(n, 0);
     for (int64_t i = 0; i < n; ++i) {
-      if (hid[i] < 0 || hid[i] >= n || seen[hid[i]]) return DSS_ERR_ARG;
+      if (hid[i] < 0 || hid[i] >= n || seen[hid[i]] || imap[hid[i]] != imap[i]) return DSS_ERR_ARG;
       seen[hid[i]] = 1;
     }
   } else {
@@ -500,11 +583,20 @@ int dss_set_state(dss_handle* h, const double* x, const double* a, const int32_t
     r = alloc_buffers(h);
     if (r) { free_buffers(h); return r; }
   }
-  h->g.sumA3 = s3;
+  for (int k = 0; k < h->K; ++k) {
+    double s3 = 0.0;
+    for (int64_t i = ibeg[k]; i < ibeg[k + 1]; ++i) s3 += ha[i] * ha[i] * ha[i];
+    h->ig_host[k].sumA3 = s3;
+  }
   drop_graphs(h);
   h->cur = 0;
   h->hist = 0;
+  h->mean_steps = 0;
   StateBuf& s = h->st[0];
+  CK(cudaMemcpyAsync(h->ig, h->ig_host, sizeof(InstGeo) * h->K, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->inst_map, imap.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(s.inst, h->inst_map, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, h->stream));
+  CK(cudaMemsetAsync(h->sigma_sum, 0, 9 * sizeof(double) * h->K, h->stream));
   CK(cudaMemcpyAsync(s.x, hx.data(), sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->stream));
   CK(cudaMemcpyAsync(s.a, ha.data(), sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
   CK(cudaMemcpyAsync(s.id, hid.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, h->stream));
@@ -517,7 +609,7 @@ int dss_set_state(dss_handle* h, const double* x, const double* a, const int32_t
   if (u) CK(cudaMemcpyAsync(s.u, u, sizeof(double) * 3 * n, cudaMemcpyDefault, h->stream));
   if (w) CK(cudaMemcpyAsync(s.w, w, sizeof(double) * 3 * n, cudaMemcpyDefault, h->stream));
   const int nb = (int)((n + 255) / 256);
-  if (!u || !w) k_default_vel<<<nb, 256, 0, h->stream>>>((int)n, s.x, h->g.gdot, s.u, s.w, !u, !w);
+  if (!u || !w) k_default_vel<<<nb, 256, 0, h->stream>>>((int)n, s.x, h->ig, s.inst, s.u, s.w, !u, !w);
   if (alpha_lin) {
     CK(cudaMemcpyAsync(s.al, alpha_lin, sizeof(double) * 3 * n, cudaMemcpyDefault, h->stream));
     CK(cudaMemcpyAsync(s.aw, alpha_ang, sizeof(double) * 3 * n, cudaMemcpyDefault, h->stream));
@@ -679,6 +771,7 @@ int dss_step(dss_handle* h, int64_t nsteps) {
     h->cur = (done & 1) ? 1 - cur0 : cur0;
     h->hist = (done & 1) ? 1 - hist0 : hist0;
     h->host_steps_done += done;
+    h->mean_steps += done;
     remaining -= done;
     if (done > 0) h->last_list = h->hist;
     const int err = status_error(h);
@@ -706,6 +799,31 @@ int dss_stress(dss_handle* h, double sigma[9]) {
   return DSS_OK;
 }
 
+int dss_batch_stress(dss_handle* h, double* sigma, double* sigma_mean, int64_t* steps, int reset) {
+  if (!h) return DSS_ERR_ARG;
+  if (!h->have_state) return DSS_ERR_STATE;
+  ENTER(h);
+  const size_t b = 9 * sizeof(double) * h->K;
+  if (sigma) CK(cudaMemcpyAsync(sigma, h->sigma, b, cudaMemcpyDefault, h->stream));
+  if (sigma_mean) {
+    std::vector<double> sum(9 * (size_t)h->K);
+    CK(cudaMemcpyAsync(sum.data(), h->sigma_sum, b, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    const double c = h->mean_steps > 0 ? 1.0 / (double)h->mean_steps : 0.0;
+    for (auto& v : sum) v *= c;
+    CK(cudaMemcpyAsync(sigma_mean, sum.data(), b, cudaMemcpyDefault, h->stream));
+  }
+  if (steps) *steps = h->mean_steps;
+  if (reset) {
+    CK(cudaMemsetAsync(h->sigma_sum, 0, b, h->stream));
+    h->mean_steps = 0;
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  return DSS_OK;
+}
+
+int32_t dss_batch_size(const dss_handle* h) { return h ? h->K : 0; }
+
 int dss_get_counters(dss_handle* h, dss_counters* c) {
   if (!h || !c) return DSS_ERR_ARG;
   int r = sync_status(h);
@@ -721,7 +839,7 @@ int dss_get_counters(dss_handle* h, dss_counters* c) {
   c->max_row = s.w[ST_MAXROW];
   c->band_checks = s.w[ST_BAND];
   c->M = h->g.M;
-  for (int d = 0; d < 3; ++d) c->ncell[d] = h->g.nc[d];
+  for (int d = 0; d < 3; ++d) c->ncell[d] = h->ig_host[0].nc[d];
   return DSS_OK;
 }
 
@@ -813,6 +931,7 @@ int dss_load_state(dss_handle* h, const double* x, const double* u, const double
   CK(cudaMemcpyAsync(s.al, alpha_lin, b, cudaMemcpyDefault, h->stream));
   CK(cudaMemcpyAsync(s.aw, alpha_ang, b, cudaMemcpyDefault, h->stream));
   CK(cudaMemcpyAsync(s.a, h->a_by_id, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, h->stream));
+  CK(cudaMemcpyAsync(s.inst, h->inst_map, sizeof(int32_t) * h->n, cudaMemcpyDeviceToDevice, h->stream));
   k_iota_int<<<(int)((h->n + 255) / 256), 256, 0, h->stream>>>((int)h->n, s.id);
   CK(cudaGetLastError());
   return DSS_OK;
@@ -865,6 +984,11 @@ void dss_destroy(dss_handle* h) {
   for (int k = 0; k < 2; ++k)
     if (h->step_ev[k]) cudaEventDestroy(h->step_ev[k]);
   if (h->stream && h->own_stream) cudaStreamDestroy(h->stream);
+  delete[] h->ig_host;
+  delete[] h->inst_box;
+  delete[] h->inst_gdot;
+  delete[] h->inst_gn;
+  delete[] h->inst_n;
   delete h;
 }
 

@@ -77,8 +77,8 @@ struct PairOut {
   int contact;
 };
 
-__device__ __forceinline__ PairOut pair_fp64(const Geo& g, V3 r, double rr, double ai, double aj,
-                                             V3 Vi, V3 Vj, V3 Wi, V3 Wj, V3 du, V3 wi, V3 wj,
+__device__ __forceinline__ PairOut pair_fp64(const Geo& g, const InstGeo& I, V3 r, double rr, double ai,
+                                             double aj, V3 Vi, V3 Vj, V3 Wi, V3 Wj, V3 du, V3 wi, V3 wj,
                                              const double xo[3]) {
   PairOut o;
   const double ir = 1.0 / rr;
@@ -92,7 +92,7 @@ __device__ __forceinline__ PairOut pair_fp64(const Geo& g, V3 r, double rr, doub
   o.contact = 0;
   if (d < 0.0) {
     o.contact = 1;
-    const double fn = g.kn * d + g.gn * dot(n, du);
+    const double fn = g.kn * d + I.gn * dot(n, du);
     const V3 rel = du - cross(ai * wi + aj * wj, n);
     const V3 ut = tang(n, rel);
     V3 xs = tang(n, v3(xo[0], xo[1], xo[2])) + g.dt * ut;
@@ -129,8 +129,8 @@ __device__ __forceinline__ PairOut pair_fp64(const Geo& g, V3 r, double rr, doub
   const double nV = dot(n, dV);
   const V3 fr = (xa * nV) * n + ya * tang(n, dV) + ybi * cross(n, Wi) + ybj * cross(n, Wj);
   // simple shear: 2 E n = gdot (n_y, n_x, 0), P = gdot n_x n_y, Q.n = 2 E n - 2 P n
-  const V3 twoEn = v3(g.gdot * n.y, g.gdot * n.x, 0.0);
-  const double P = g.gdot * n.x * n.y;
+  const V3 twoEn = v3(I.gdot * n.y, I.gdot * n.x, 0.0);
+  const double P = I.gdot * n.x * n.y;
   const V3 Qn = twoEn - (2.0 * P) * n;
   const V3 nperp = cross(n, twoEn);
   const V3 fe = (xg * P) * n + yg * Qn;
@@ -168,14 +168,14 @@ struct PairRes {
 };
 
 // FP64 pair from the state (exact FP64 throughout).
-__device__ __forceinline__ PairRes<double> pair_eval_fp64(const Geo& g, const StateBuf& s, const ListBuf& H,
-                                                         double off, int i, int j) {
+__device__ __forceinline__ PairRes<double> pair_eval_fp64(const Geo& g, const InstGeo& I, const StateBuf& s,
+                                                         const ListBuf& H, double off, int i, int j) {
   const int n = g.n;
   const double xi = s.x[i], yi = s.x[n + i], zi = s.x[2 * n + i];
   const double xj = s.x[j], yj = s.x[n + j], zj = s.x[2 * n + j];
   double dx, dy, dz;
   int sy;
-  min_image(g, off, xi, yi, zi, xj, yj, zj, dx, dy, dz, sy);
+  min_image(I, off, xi, yi, zi, xj, yj, zj, dx, dy, dz, sy);
   const V3 r = v3(dx, dy, dz);
   const double ai = s.a[i], aj = s.a[j];
   const V3 ui = v3(s.u[i], s.u[n + i], s.u[2 * n + i]);
@@ -190,13 +190,13 @@ __device__ __forceinline__ PairRes<double> pair_eval_fp64(const Geo& g, const St
     history_lookup(g, H, idi, idj, xo);
     xo[0] *= sgn; xo[1] *= sgn; xo[2] *= sgn;
   }
-  const double Om = -0.5 * g.gdot;
-  const V3 Vi = v3(ui.x - g.gdot * yi, ui.y, ui.z);
-  const V3 Vj = v3(uj.x - g.gdot * yj, uj.y, uj.z);
+  const double Om = -0.5 * I.gdot;
+  const V3 Vi = v3(ui.x - I.gdot * yi, ui.y, ui.z);
+  const V3 Vj = v3(uj.x - I.gdot * yj, uj.y, uj.z);
   const V3 Wi = v3(wi.x, wi.y, wi.z - Om);
   const V3 Wj = v3(wj.x, wj.y, wj.z - Om);
-  const V3 du = v3(uj.x + sy * g.gdot * g.L[1] - ui.x, uj.y - ui.y, uj.z - ui.z);
-  const PairOut o = pair_fp64(g, r, rr, ai, aj, Vi, Vj, Wi, Wj, du, wi, wj, xo);
+  const V3 du = v3(uj.x + sy * I.gdot * I.L[1] - ui.x, uj.y - ui.y, uj.z - ui.z);
+  const PairOut o = pair_fp64(g, I, r, rr, ai, aj, Vi, Vj, Wi, Wj, du, wi, wj, xo);
   PairRes<double> q;
   q.F[0] = o.F.x; q.F[1] = o.F.y; q.F[2] = o.F.z;
   q.Ti[0] = o.Ti.x; q.Ti[1] = o.Ti.y; q.Ti[2] = o.Ti.z;
@@ -215,17 +215,17 @@ __device__ __forceinline__ PairRes<double> pair_eval_fp64(const Geo& g, const St
 // then d = (r^2 - S^2)/(r + S) with the division in FP32.  The tangential
 // stretch is carried and updated in FP64; the rest of the pair arithmetic is
 // FP32, on velocities taken relative to the ambient flow.
-__device__ __forceinline__ PairRes<float> pair_eval_mixed(const Geo& g, const StateBuf& s, const ListBuf& H,
-                                                         const StepGeo& sg, const float4* __restrict__ posf,
-                                                         int i, int j) {
-  const float gd = g.f.gdot;
+__device__ __forceinline__ PairRes<float> pair_eval_mixed(const Geo& g, const InstGeo& I, const StateBuf& s,
+                                                         const ListBuf& H, const StepGeo& sg,
+                                                         const float4* __restrict__ posf, int i, int j) {
+  const float gd = I.gdot_f;
   const float k6 = g.f.k6;
   // double-float separation from cell-local hi/lo words and the cell offset
   // (listed pairs are one cell apart at most; a pair across y = L_y has its
   // owner in the top row and its partner in row 0, image shifted by off)
   const float4 pi = posf[i], pj = posf[j], li = s.posl[i], lj = s.posl[j];
   const int ci = s.cellc[i], cj = s.cellc[j];
-  const int nx = g.nc[0], ny = g.nc[1], nz = g.nc[2];
+  const int nx = I.nc[0], ny = I.nc[1], nz = I.nc[2];
   const int cyi = (ci >> 10) & 1023, cyj = (cj >> 10) & 1023;
   const bool le = cyi == ny - 1 && cyj == 0;
   int wx = (cj & 1023) - (ci & 1023) + (le ? sg.fsh : 0);
@@ -235,13 +235,13 @@ __device__ __forceinline__ PairRes<float> pair_eval_mixed(const Geo& g, const St
   const int wy = le ? 1 : cyj - cyi;
   int wz = (cj >> 20) - (ci >> 20);
   if (wz > 1) wz -= nz; else if (wz < -1) wz += nz;
-  FF cx = FF{(float)wx * g.csf[0], (float)wx * g.cs_lo[0]};
+  FF cx = FF{(float)wx * I.csf[0], (float)wx * I.cs_lo[0]};
   if (le) cx = ff_add(cx, FF{sg.offr_hi, sg.offr_lo});
   const FF dxf = ff_add(two_sum(pj.x, -pi.x), ff_add(cx, FF{lj.x - li.x, 0.f}));
   const FF dyf = ff_add(two_sum(pj.y, -pi.y),
-                        ff_add(FF{(float)wy * g.csf[1], (float)wy * g.cs_lo[1]}, FF{lj.y - li.y, 0.f}));
+                        ff_add(FF{(float)wy * I.csf[1], (float)wy * I.cs_lo[1]}, FF{lj.y - li.y, 0.f}));
   const FF dzf = ff_add(two_sum(pj.z, -pi.z),
-                        ff_add(FF{(float)wz * g.csf[2], (float)wz * g.cs_lo[2]}, FF{lj.z - li.z, 0.f}));
+                        ff_add(FF{(float)wz * I.csf[2], (float)wz * I.cs_lo[2]}, FF{lj.z - li.z, 0.f}));
   const FF Sff = ff_add(FF{pi.w, li.w}, FF{pj.w, lj.w});
   const FF r2ff = ff_add(ff_add(ff_sqr(dxf), ff_sqr(dyf)), ff_sqr(dzf));
   const FF numff = ff_add(r2ff, ff_neg(ff_sqr(Sff)));          // r^2 - S^2, ~44 bits
@@ -270,7 +270,7 @@ __device__ __forceinline__ PairRes<float> pair_eval_mixed(const Geo& g, const St
     // u_j(image) - u_i = (V_j - V_i) + gdot dy x
     const F3 du = (Vj - Vi) + f3(gd * r.y, 0.f, 0.f);
     const F3 wi = f3(Wi.x, Wi.y, Wi.z - 0.5f * gd), wj = f3(Wj.x, Wj.y, Wj.z - 0.5f * gd);
-    const float fn = g.f.kn * d + g.f.gn * dotf(nn, du);
+    const float fn = g.f.kn * d + I.gn_f * dotf(nn, du);
     const F3 ut = tangf(nn, du - crossf(Ai * wi + Bj * wj, nn));
     // stretch (stored orientation) in FP64: xi + delta, with the small change
     // delta = -n (n.xi) + s u_t dt (projection onto the new tangent plane and
@@ -347,10 +347,10 @@ __device__ __forceinline__ int bits_owner(float v) { return __float_as_int(v); }
 __device__ __forceinline__ int bits_owner(double v) { return (int)__double_as_longlong(v); }
 
 template <bool MIXED>
-__global__ void __launch_bounds__(kPairThreads)
-k_pairs(Geo g, StateBuf s, ListBuf W, ListBuf H, const float4* __restrict__ posf, void* __restrict__ own_v,
-        int* __restrict__ bw_count, void* __restrict__ bw_v, double* __restrict__ spart, DevStatus* st,
-        int adv) {
+__global__ void __launch_bounds__(kPairThreads, MIXED ? 3 : 2)
+k_pairs(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ sgk, StateBuf s, ListBuf W,
+        ListBuf H, const float4* __restrict__ posf, void* __restrict__ own_v, int* __restrict__ bw_count,
+        void* __restrict__ bw_v, double* __restrict__ spart, DevStatus* st, int adv) {
   using R = typename std::conditional<MIXED, float, double>::type;
   if (dev_err(st)) return;
   R* __restrict__ own = static_cast<R*>(own_v);
@@ -365,8 +365,13 @@ k_pairs(Geo g, StateBuf s, ListBuf W, ListBuf H, const float4* __restrict__ posf
     return;
   }
   __shared__ R acc[kWarps][32][6];
-  const StepGeo sg = st->sg;
-  const double off = sg.off;
+  // The block's owners span at most two instances (an instance has at least
+  // as many particles as a block has threads), and a lane meets its pairs in
+  // increasing owner order, so its instance changes at most once: the
+  // stresslet sum of the first instance is parked in shared memory then.
+  __shared__ R park[kPairThreads][9];
+  const int inst0 = s.inst[min((int)(blockIdx.x * blockDim.x), n - 1)];
+  int cur_inst = inst0;
   R Sx[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   int ncont = 0;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -401,9 +406,12 @@ k_pairs(Geo g, StateBuf s, ListBuf W, ListBuf H, const float4* __restrict__ posf
         const int i = w0 + Lw;
         const int p = base + t;
         const int j = W.list[(int64_t)i * g.M + kk];
+        const int inst = s.inst[i];
+        const InstGeo& I = ig[inst];
+        const StepGeo sg = sgk[inst];
         PairRes<R> q;
-        if constexpr (MIXED) q = pair_eval_mixed(g, s, H, sg, posf, i, j);
-        else q = pair_eval_fp64(g, s, H, off, i, j);
+        if constexpr (MIXED) q = pair_eval_mixed(g, I, s, H, sg, posf, i, j);
+        else q = pair_eval_fp64(g, I, s, H, sg.off, i, j);
         v[0] = q.F[0]; v[1] = q.F[1]; v[2] = q.F[2];
         v[3] = q.Ti[0]; v[4] = q.Ti[1]; v[5] = q.Ti[2];
         // partner's share, appended to its row with the owner's index
@@ -422,6 +430,14 @@ k_pairs(Geo g, StateBuf s, ListBuf W, ListBuf H, const float4* __restrict__ posf
         W.cflag[p] = (unsigned char)q.contact;
         ncont += q.contact;
         // Eq. 9: S^C = r (x) F^C, S^L = sym(r (x) F^L), F on the owner
+        if (inst != cur_inst) {
+#pragma unroll
+          for (int c = 0; c < 9; ++c) {
+            park[threadIdx.x][c] = Sx[c];
+            Sx[c] = R(0);
+          }
+          cur_inst = inst;
+        }
 #pragma unroll
         for (int a = 0; a < 3; ++a)
 #pragma unroll
@@ -457,10 +473,11 @@ k_pairs(Geo g, StateBuf s, ListBuf W, ListBuf H, const float4* __restrict__ posf
   // FP64 block reduction of the stresslet (fixed tree)
   // (in mixed precision the 32 lanes of a warp are pre-summed in FP32, the
   // warps and blocks in FP64)
-  __shared__ double red[kWarps][9];
+  __shared__ double red[kWarps][18];
+  const bool moved = cur_inst != inst0;
 #pragma unroll
-  for (int q = 0; q < 9; ++q) {
-    R v = Sx[q];
+  for (int q = 0; q < 18; ++q) {
+    R v = q < 9 ? (moved ? park[threadIdx.x][q] : Sx[q]) : (moved ? Sx[q - 9] : R(0));
     for (int dlt = 16; dlt > 0; dlt >>= 1) v += __shfl_down_sync(0xffffffffu, v, dlt);
     if (lane == 0) red[wid][q] = (double)v;
   }
@@ -468,56 +485,61 @@ k_pairs(Geo g, StateBuf s, ListBuf W, ListBuf H, const float4* __restrict__ posf
   for (int dlt = 16; dlt > 0; dlt >>= 1) c += __shfl_down_sync(0xffffffffu, c, dlt);
   if (lane == 0 && c) atomicAdd(&st->w[ST_NCONT], c);
   __syncthreads();
-  if (threadIdx.x < 9) {
+  if (threadIdx.x < 18) {
     double v = 0.0;
     for (int w = 0; w < kWarps; ++w) v += red[w][threadIdx.x];
-    spart[blockIdx.x * 9 + threadIdx.x] = v;
+    spart[blockIdx.x * 18 + threadIdx.x] = v;
   }
 }
 
-// Bulk stress (Eq. 8) from the per-block partials and the step commit, done
-// by the last block of the gather to finish (fixed summation order).
-__device__ void finalize_block(const Geo& g, const double* __restrict__ spart, int nblocks,
-                               double* sigma, DevStatus* st, const int* __restrict__ start,
-                               int step) {
-  __shared__ double red[kThreads][9];
+// Bulk stress (Eq. 8) of one instance from the pair blocks' partials, by one
+// block of the gather (fixed strided assignment and fixed tree).  Pair block b
+// holds the sums of the instance containing its first owner (slot 0) and of
+// the next instance (slot 1).
+__device__ void inst_stress(const Geo& g, const InstGeo& I, const double* __restrict__ spart,
+                            double* __restrict__ sigma) {
+  __shared__ double red[kThreads / 32][9];
   double v[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-  for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+  const int b0 = I.p_begin / kPairThreads, b1 = (I.p_end - 1) / kPairThreads;
+  for (int b = b0 + threadIdx.x; b <= b1; b += blockDim.x) {
+    const double* p = spart + b * 18 + (b * kPairThreads >= I.p_begin ? 0 : 9);
 #pragma unroll
-    for (int q = 0; q < 9; ++q) v[q] += spart[b * 9 + q];
-#pragma unroll
-  for (int q = 0; q < 9; ++q) red[threadIdx.x][q] = v[q];
-  __syncthreads();
-  for (int s2 = blockDim.x / 2; s2 > 0; s2 >>= 1) {
-    if (threadIdx.x < s2)
-#pragma unroll
-      for (int q = 0; q < 9; ++q) red[threadIdx.x][q] += red[threadIdx.x + s2][q];
-    __syncthreads();
+    for (int q = 0; q < 9; ++q) v[q] += p[q];
   }
-  if (threadIdx.x == 0) {
-    const int err = dev_err(st);
-    if (!err) {
-      // E_inf: only xy and yx are non-zero (gdot/2)
-      const double Exy = 0.5 * g.gdot;
-      const double V = g.L[0] * g.L[1] * g.L[2];
-      const double ein = 20.0 / 3.0 * DSS_PI * g.eta0 * g.sumA3;
-      for (int q = 0; q < 9; ++q) {
-        const double E = (q == 1 || q == 3) ? Exy : 0.0;
-        sigma[q] = 2.0 * g.eta0 * E + (ein * E + red[0][q]) / V;
-      }
-      st->w[ST_NPAIRS] = start[g.n];
-      if (step) {
-        st->w[ST_STEPS] += 1;
-        int64_t ns = dev_nstep(st) + 1;
-        st->w[ST_NSTEP_LO] = (int)(uint32_t)(ns & 0xffffffffll);
-        st->w[ST_NSTEP_HI] = (int)(ns >> 32);
-      }
-    }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < 9; ++q) {
+    for (int d = 16; d > 0; d >>= 1) v[q] += __shfl_down_sync(0xffffffffu, v[q], d);
+    if (lane == 0) red[wid][q] = v[q];
+  }
+  __syncthreads();
+  if (threadIdx.x < 9) {
+    const int q = threadIdx.x;
+    double S = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) S += red[w][q];
+    // E_inf: only xy and yx are non-zero (gdot/2)
+    const double E = (q == 1 || q == 3) ? 0.5 * I.gdot : 0.0;
+    const double V = I.L[0] * I.L[1] * I.L[2];
+    const double ein = 20.0 / 3.0 * DSS_PI * g.eta0 * I.sumA3;
+    sigma[q] = 2.0 * g.eta0 * E + (ein * E + S) / V;
+  }
+}
+
+// Step commit, by the last block of the gather to finish.
+__device__ void commit_step(const Geo& g, DevStatus* st, const int* __restrict__ start, int step) {
+  if (dev_err(st)) return;
+  st->w[ST_NPAIRS] = start[g.n];
+  if (step) {
+    st->w[ST_STEPS] += 1;
+    int64_t ns = dev_nstep(st) + 1;
+    st->w[ST_NSTEP_LO] = (int)(uint32_t)(ns & 0xffffffffll);
+    st->w[ST_NSTEP_HI] = (int)(ns >> 32);
   }
 }
 
 template <bool MIXED>
-__device__ __forceinline__ void gather_one(const Geo& g, const StateBuf& s, const void* __restrict__ own_v,
+__device__ __forceinline__ void gather_one(const Geo& g, const InstGeo* __restrict__ ig, const StateBuf& s,
+                                           const void* __restrict__ own_v,
                                            const int* __restrict__ bw_count, const void* __restrict__ bw_v,
                                            double* __restrict__ Fout, double* __restrict__ Tout,
                                            DevStatus* st, int mode) {
@@ -564,12 +586,13 @@ __device__ __forceinline__ void gather_one(const Geo& g, const StateBuf& s, cons
   } else {
     const double yj = s.x[n + j];
     const double kd = -g.k6 * a, kr = -g.k8 * a * a * a;
-    F[0] += kd * (s.u[j] - g.gdot * yj);
+    const double gd = ig[s.inst[j]].gdot;
+    F[0] += kd * (s.u[j] - gd * yj);
     F[1] += kd * s.u[n + j];
     F[2] += kd * s.u[2 * n + j];
     T[0] += kr * s.w[j];
     T[1] += kr * s.w[n + j];
-    T[2] += kr * (s.w[2 * n + j] + 0.5 * g.gdot);
+    T[2] += kr * (s.w[2 * n + j] + 0.5 * gd);
   }
   if (!(isfinite(F[0]) && isfinite(F[1]) && isfinite(F[2]) && isfinite(T[0]) && isfinite(T[1]) &&
         isfinite(T[2])))
@@ -610,14 +633,17 @@ __device__ __forceinline__ void gather_one(const Geo& g, const StateBuf& s, cons
 
 template <bool MIXED>
 __global__ void __launch_bounds__(kThreads)
-k_gather(Geo g, StateBuf s, const void* __restrict__ own_v, const int* __restrict__ bw_count,
-         const void* __restrict__ bw_v, double* __restrict__ Fout, double* __restrict__ Tout,
-         DevStatus* st, int mode, const double* __restrict__ spart, int nparts, double* sigma,
-         const int* __restrict__ start, unsigned int* done_blocks) {
+k_gather(Geo g, const InstGeo* __restrict__ ig, StateBuf s, const void* __restrict__ own_v,
+         const int* __restrict__ bw_count, const void* __restrict__ bw_v, double* __restrict__ Fout,
+         double* __restrict__ Tout, DevStatus* st, int mode, const double* __restrict__ spart,
+         double* sigma, double* sigma_sum, const int* __restrict__ start, unsigned int* done_blocks) {
+  // block k < K also reduces the stress of instance k (the grid has at least
+  // two blocks per instance)
+  if (blockIdx.x < (unsigned)g.K) inst_stress(g, ig[blockIdx.x], spart, sigma + 9 * blockIdx.x);
   // no early exit on an earlier error: every block must reach the counter;
   // the step is committed only when no error is set
-  gather_one<MIXED>(g, s, own_v, bw_count, bw_v, Fout, Tout, st, mode);
-  // the last block to finish computes the stress and commits the step
+  gather_one<MIXED>(g, ig, s, own_v, bw_count, bw_v, Fout, Tout, st, mode);
+  // the last block to finish commits the step
   __shared__ bool last;
   __threadfence();
   __syncthreads();
@@ -625,7 +651,13 @@ k_gather(Geo g, StateBuf s, const void* __restrict__ own_v, const int* __restric
   __syncthreads();
   if (last) {
     __threadfence();
-    finalize_block(g, spart, nparts, sigma, st, start, mode == G_STEP ? 1 : 0);
+    __shared__ int s_err;
+    if (threadIdx.x == 0) s_err = dev_err(st);
+    __syncthreads();
+    // a committed step adds every instance's stress to the running sums
+    if (!s_err && mode == G_STEP)
+      for (int t = threadIdx.x; t < 9 * g.K; t += blockDim.x) sigma_sum[t] += __ldcg(sigma + t);
+    if (threadIdx.x == 0) commit_step(g, st, start, mode == G_STEP ? 1 : 0);
     if (threadIdx.x == 0) *done_blocks = 0u;
   }
 }
@@ -664,22 +696,24 @@ void launch_forces(dss_handle* h, int stbuf, int work_list, int hist_list, int a
   const bool mixed = h->g.precision == DSS_MIXED;
   prof_mark(h, 5);
   if (mixed)
-    k_pairs<true><<<pb, kPairThreads, 0, h->stream>>>(h->g, h->st[stbuf], h->lb[work_list],
+    k_pairs<true><<<pb, kPairThreads, 0, h->stream>>>(h->g, h->ig, h->sg, h->st[stbuf], h->lb[work_list],
                                                       h->lb[hist_list], h->posf, h->own, h->bw_count,
                                                       h->bw_rec, h->spart, h->status, adv);
   else
-    k_pairs<false><<<pb, kPairThreads, 0, h->stream>>>(h->g, h->st[stbuf], h->lb[work_list],
+    k_pairs<false><<<pb, kPairThreads, 0, h->stream>>>(h->g, h->ig, h->sg, h->st[stbuf], h->lb[work_list],
                                                        h->lb[hist_list], h->posf, h->own, h->bw_count,
                                                        h->bw_rec, h->spart, h->status, adv);
   prof_mark(h, 6);
   const int gb = (n + kThreads - 1) / kThreads;
   if (mixed)
-    k_gather<true><<<gb, kThreads, 0, h->stream>>>(h->g, h->st[stbuf], h->own, h->bw_count, h->bw_rec, F_out,
-                                                   T_out, h->status, mode, h->spart, pb, h->sigma,
+    k_gather<true><<<gb, kThreads, 0, h->stream>>>(h->g, h->ig, h->st[stbuf], h->own, h->bw_count, h->bw_rec,
+                                                   F_out, T_out, h->status, mode, h->spart, h->sigma,
+                                                   h->sigma_sum,
                                                    h->lb[work_list].start, h->done_blocks);
   else
-    k_gather<false><<<gb, kThreads, 0, h->stream>>>(h->g, h->st[stbuf], h->own, h->bw_count, h->bw_rec, F_out,
-                                                    T_out, h->status, mode, h->spart, pb, h->sigma,
+    k_gather<false><<<gb, kThreads, 0, h->stream>>>(h->g, h->ig, h->st[stbuf], h->own, h->bw_count,
+                                                    h->bw_rec, F_out, T_out, h->status, mode, h->spart, h->sigma,
+                                                    h->sigma_sum,
                                                     h->lb[work_list].start, h->done_blocks);
   prof_mark(h, 7);
 }

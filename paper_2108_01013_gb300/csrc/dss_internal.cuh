@@ -25,8 +25,8 @@ enum {
   ST_WORDS = 16
 };
 
-// Lees-Edwards geometry of the time the current operation evaluates at,
-// written once per operation by the first kernel (k_key_hist):
+// Lees-Edwards geometry of one instance at the time the current operation
+// evaluates at, written once per operation by the first kernel (k_key_hist):
 // off = fsh * cs_x + offr, offr = offr_hi + offr_lo in [0, cs_x).
 struct StepGeo {
   double off;
@@ -36,40 +36,44 @@ struct StepGeo {
 
 struct DevStatus {
   int w[ST_WORDS];
-  StepGeo sg;
 };
 
-// Everything a kernel needs to know about the model and the grid, by value.
+// Model constants shared by every instance, by value.
 struct Geo {
-  // box and grid
-  double L[3];
-  double halfL[3];
-  double cs[3];       // cell edge per axis
-  double inv_cs[3];
-  int nc[3];
-  int ncell;
-  int n;
+  int n;              // particles of all instances
+  int K;              // instances
+  int ncell;          // cells of all instances
   int M;              // half-list capacity per particle
   int64_t pcap;       // pair capacity
-  // model
-  double kn, kt, gn, mu;
+  double kn, kt, mu;
   double eta0, rho;
   double delta, eps, a0;
   int mode;           // cutoff mode
   int precision;
-  double gdot, dt;
+  double dt;
   double k6;          // 6 pi eta0
   double k8;          // 8 pi eta0
-  double sumA3;       // sum of a^3 (Einstein stresslet of Eq. 9)
-  // FP32 prefilter margin on r^2 (absolute)
-  float r2_margin;
-  float halfLf[3];
   struct {             // FP32 copies of the model constants (mixed precision)
-    float kn, kt, gn, mu_kt, dt, eps, gdot, k6, k8, mass_c;
+    float kn, kt, mu_kt, dt, eps, k6, k8, mass_c;
   } f;
-  float csf[3];       // FP32 cell edges
-  float cs_lo[3];     // cs - csf (double-float cell edges)
-  double invL[3];     // 1 / L
+};
+
+// One instance (an independent suspension): its box, cell grid, shear rate
+// and dashpot; read by each thread from a small device table.  Its particles
+// occupy sorted positions [p_begin, p_end) (cell ids are instance-major) and
+// ids [p_begin, p_end).
+struct InstGeo {
+  double L[3], halfL[3], invL[3];
+  double cs[3], inv_cs[3];      // cell edge per axis
+  float csf[3], cs_lo[3];       // double-float cell edges
+  float halfLf[3];
+  float r2_margin;              // FP32 prefilter margin on r^2 (absolute)
+  int nc[3];
+  int cell_base, ncell;
+  int p_begin, p_end;
+  double gdot, gn;              // shear rate, normal dashpot
+  float gdot_f, gn_f;
+  double sumA3;                 // sum of a^3 (Einstein stresslet of Eq. 9)
 };
 
 // ------------------------------------------------------------------------
@@ -88,9 +92,9 @@ __device__ __forceinline__ int64_t dev_nstep(const DevStatus* s) {
 
 // Lees-Edwards offset at step count nstep: fmod(gdot * L_y * (nstep dt), L_x),
 // with the product taken in that order and no fused operations.
-__device__ __forceinline__ double le_offset(const Geo& g, int64_t nstep) {
+__device__ __forceinline__ double le_offset(const Geo& g, const InstGeo& I, int64_t nstep) {
   double t = __dmul_rn((double)nstep, g.dt);
-  return fmod(__dmul_rn(__dmul_rn(g.gdot, g.L[1]), t), g.L[0]);
+  return fmod(__dmul_rn(__dmul_rn(I.gdot, I.L[1]), t), I.L[0]);
 }
 
 // Interaction range beyond contact for the pair.
@@ -103,7 +107,7 @@ __device__ __forceinline__ double pair_delta(const Geo& g, double ai, double aj)
 // spelled out operation by operation (no contraction) so that the neighbour
 // decision is the same bit pattern on every path.  sy: image shift in y
 // (-1: image one box below, +1: above).
-__device__ __forceinline__ void min_image(const Geo& g, double off, double xi, double yi,
+__device__ __forceinline__ void min_image(const InstGeo& g, double off, double xi, double yi,
                                           double zi, double xj, double yj, double zj,
                                           double& dx, double& dy, double& dz, int& sy) {
   dx = __dsub_rn(xj, xi);
@@ -127,12 +131,12 @@ __device__ __forceinline__ void min_image(const Geo& g, double off, double xi, d
 }
 
 // Exact neighbour predicate: r^2 < (a_i + a_j + delta_ij)^2, strict.
-__device__ __forceinline__ bool exact_is_pair(const Geo& g, double off, double xi, double yi,
-                                              double zi, double ai, double xj, double yj,
-                                              double zj, double aj) {
+__device__ __forceinline__ bool exact_is_pair(const Geo& g, const InstGeo& I, double off, double xi,
+                                              double yi, double zi, double ai, double xj,
+                                              double yj, double zj, double aj) {
   double dx, dy, dz;
   int sy;
-  min_image(g, off, xi, yi, zi, xj, yj, zj, dx, dy, dz, sy);
+  min_image(I, off, xi, yi, zi, xj, yj, zj, dx, dy, dz, sy);
   double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
   double s = __dadd_rn(__dadd_rn(ai, aj), pair_delta(g, ai, aj));
   return r2 < __dmul_rn(s, s);
@@ -149,99 +153,8 @@ __device__ __forceinline__ int wrapi(int v, int n) {
 }
 
 // Shift (in cells) of the Lees-Edwards row: floor(off / cs_x).
-__device__ __forceinline__ int le_shift_cells(const Geo& g, double off) {
+__device__ __forceinline__ int le_shift_cells(const InstGeo& g, double off) {
   return (int)floor(off * g.inv_cs[0]);
-}
-
-// One stencil cell: linear cell id and the (unwrapped) displacement of that
-// cell's origin relative to the owner cell origin, plus the Lees-Edwards
-// x offset (0 or off) to add for images across y = L_y.
-struct StencilCell {
-  int cell;
-  int ox, oy, oz;
-  int le;   // 1: reached through y = L_y (image shifted by +off); 2: own cell
-};
-
-// Forward half-stencil of owner cell (cx, cy, cz) (Sec. II A, Fig. 6): the
-// layer y+1 (3x3 cells; across y = L_y the 4 x-cells covering the shifted
-// image range), the layer y with z+1 (3 cells), the cell x+1, and the own
-// cell (marked le = 2; there only partners after the owner count).
-// Returned sorted by linear cell id.
-__device__ __forceinline__ int forward_cells(const Geo& g, int cx, int cy, int cz, int fsh,
-                                             StencilCell* out) {
-  int k = 0;
-  const int nx = g.nc[0], ny = g.nc[1], nz = g.nc[2];
-  if (cy < ny - 1) {
-    for (int oz = -1; oz <= 1; ++oz)
-      for (int ox = -1; ox <= 1; ++ox) {
-        int qx = wrapi(cx + ox, nx), qz = wrapi(cz + oz, nz);
-        out[k++] = StencilCell{(qz * ny + (cy + 1)) * nx + qx, ox, 1, oz, 0};
-      }
-  } else {
-    for (int oz = -1; oz <= 1; ++oz)
-      for (int ox = -2 - fsh; ox <= 1 - fsh; ++ox) {
-        int qx = wrapi(cx + ox, nx), qz = wrapi(cz + oz, nz);
-        out[k++] = StencilCell{(qz * ny + 0) * nx + qx, ox, 1, oz, 1};
-      }
-  }
-  for (int ox = -1; ox <= 1; ++ox) {
-    int qx = wrapi(cx + ox, nx), qz = wrapi(cz + 1, nz);
-    out[k++] = StencilCell{(qz * ny + cy) * nx + qx, ox, 0, 1, 0};
-  }
-  out[k++] = StencilCell{(cz * ny + cy) * nx + wrapi(cx + 1, nx), 1, 0, 0, 0};
-  out[k++] = StencilCell{(cz * ny + cy) * nx + cx, 0, 0, 0, 2};   // own cell
-  // insertion sort by cell id (at most 17 entries)
-  for (int a = 1; a < k; ++a) {
-    StencilCell t = out[a];
-    int b = a - 1;
-    while (b >= 0 && out[b].cell > t.cell) {
-      out[b + 1] = out[b];
-      --b;
-    }
-    out[b + 1] = t;
-  }
-  return k;
-}
-
-// Inverse of forward_cells: the cells whose forward stencil contains cell
-// (cx, cy, cz), i.e. where the owners of this cell's particles live, plus the
-// own cell (le = 2; owners before the particle); the displacement stored is
-// that of the owner cell relative to this cell.  Sorted by cell id.
-__device__ __forceinline__ int backward_cells(const Geo& g, int cx, int cy, int cz, int fsh,
-                                              StencilCell* out) {
-  int k = 0;
-  const int nx = g.nc[0], ny = g.nc[1], nz = g.nc[2];
-  if (cy > 0) {
-    for (int oz = -1; oz <= 1; ++oz)
-      for (int ox = -1; ox <= 1; ++ox) {
-        int qx = wrapi(cx + ox, nx), qz = wrapi(cz + oz, nz);
-        out[k++] = StencilCell{(qz * ny + (cy - 1)) * nx + qx, ox, -1, oz, 0};
-      }
-  } else {
-    // owners in the top row with this cell in their shifted window:
-    // cx = (cx_owner + ox_f) mod nx with ox_f in [-2-fsh, 1-fsh]
-    for (int oz = -1; oz <= 1; ++oz)
-      for (int ox = -1 + fsh; ox <= 2 + fsh; ++ox) {
-        int qx = wrapi(cx + ox, nx), qz = wrapi(cz + oz, nz);
-        out[k++] = StencilCell{(qz * ny + (ny - 1)) * nx + qx, ox, -1, oz, 1};
-      }
-  }
-  for (int ox = -1; ox <= 1; ++ox) {
-    int qx = wrapi(cx + ox, nx), qz = wrapi(cz - 1, nz);
-    out[k++] = StencilCell{(qz * ny + cy) * nx + qx, ox, 0, -1, 0};
-  }
-  out[k++] = StencilCell{(cz * ny + cy) * nx + wrapi(cx - 1, nx), -1, 0, 0, 0};
-  out[k++] = StencilCell{(cz * ny + cy) * nx + cx, 0, 0, 0, 2};   // own cell
-  for (int a = 1; a < k; ++a) {
-    StencilCell t = out[a];
-    int b = a - 1;
-    while (b >= 0 && out[b].cell > t.cell) {
-      out[b + 1] = out[b];
-      --b;
-    }
-    out[b + 1] = t;
-  }
-  return k;
 }
 
 // FP32 conservative prefilter.  Positions are stored relative to their cell
@@ -250,7 +163,7 @@ __device__ __forceinline__ int backward_cells(const Geo& g, int cx, int cy, int 
 //   d = (xl_j - xl_i) + (o * cs [+ off for a Lees-Edwards image])
 // up to a bounded rounding error; the decision is:
 //   1: certainly a pair, 0: certainly not, -1: decide with exact_is_pair.
-__device__ __forceinline__ int prefilter(const Geo& g, float4 pi, float4 pj, float cxo, float cyo,
+__device__ __forceinline__ int prefilter(const InstGeo& g, float4 pi, float4 pj, float cxo, float cyo,
                                          float czo, float s) {
   float dx = (pj.x - pi.x) + cxo;
   float dy = (pj.y - pi.y) + cyo;
@@ -266,7 +179,7 @@ __device__ __forceinline__ int prefilter(const Geo& g, float4 pi, float4 pj, flo
 // FP32 displacement of a stencil cell's origin (cells ox, oy, oz away; for a
 // Lees-Edwards image plus the offset off = fsh*cs_x + offr, offr in [0, cs_x)),
 // computed without any FP64 instruction.
-__device__ __forceinline__ void stencil_shift(const Geo& g, int ox, int oy, int oz, int le,
+__device__ __forceinline__ void stencil_shift(const InstGeo& g, int ox, int oy, int oz, int le,
                                               int fsh, float offr, float& cx, float& cy,
                                               float& cz) {
   cx = le == 1 ? (float)(ox + fsh) * g.csf[0] + offr : (float)ox * g.csf[0];
@@ -372,6 +285,7 @@ struct StateBuf {
   double* aw;   // 3n angular acceleration
   double* a;    // n radius
   int* id;      // n persistent id
+  int* inst;    // n instance index
   float4* vf;   // n, mixed precision: FP32 velocity relative to U_inf (xyz)
   float4* wf;   // n, mixed precision: FP32 angular velocity relative to Omega_inf (xyz)
   float4* posl; // n, mixed precision: low words of the cell-local position and radius
@@ -390,8 +304,15 @@ struct ListBuf {
 
 struct dss_handle {
   dss_params p;
-  int64_t n;
-  double L[3];
+  int64_t n;                 // particles of all instances
+  int K;                     // instances
+  InstGeo* ig_host;          // K (host)
+  InstGeo* ig;               // K (device)
+  StepGeo* sg;               // K (device): Lees-Edwards geometry of the current operation
+  double* inst_box;          // 3K (host) box edges
+  double* inst_gdot;         // K (host) shear rates
+  double* inst_gn;           // K (host) dashpots
+  int64_t* inst_n;           // K (host) particle counts
   cudaStream_t stream;       // stream all work is issued on
   cudaStream_t user_stream;  // the caller's stream (NULL: legacy default stream)
   bool own_stream;           // stream created by the library (caller passed NULL)
@@ -433,9 +354,12 @@ struct dss_handle {
   void* bw_rec;      // n*M slots of 8 values: partner force (3), torque (3), owner index
   int64_t pcap;
   // stress
-  double* spart;     // 9 * max pair blocks
+  double* spart;     // 18 per pair block: stresslet sums for the block's first instance and the next
   int spart_blocks;
-  double* sigma;     // 9
+  double* sigma;     // 9K: stress of each instance at the last force pass
+  double* sigma_sum; // 9K: sum over committed steps since the last reset
+  int64_t mean_steps;         // steps summed in sigma_sum
+  int* inst_map;     // n: instance of each index in instance-major (id) order
   unsigned int* done_blocks;  // last-block counter of the gather (reset by that block)
   // scans
   unsigned long long* scan_status;  // tile status words (2 scans)

@@ -18,6 +18,7 @@ constexpr int kThreads = 128;
 // Visits the candidates of one stencil cell and appends the pairs.
 struct EnumCtx {
   const Geo* g;
+  const InstGeo* I;
   const StateBuf* s;
   const float4* posf;
   float4 pi;
@@ -30,15 +31,16 @@ struct EnumCtx {
 
 __device__ __forceinline__ void scan_range(EnumCtx& e, int jb, int je, float cxo, float cyo, float czo) {
   const Geo& g = *e.g;
+  const InstGeo& I = *e.I;
   const int n = g.n;
   for (int j = jb; j < je; ++j) {
     const float4 pj = e.posf[j];
     const float sf = e.pi.w + pj.w + pair_delta_f(g, e.pi.w, pj.w);
-    int dec = prefilter(g, e.pi, pj, cxo, cyo, czo, sf);
+    int dec = prefilter(I, e.pi, pj, cxo, cyo, czo, sf);
     if (dec < 0) {
       ++e.band;
       const StateBuf& s = *e.s;
-      dec = exact_is_pair(g, e.off, s.x[e.i], s.x[n + e.i], s.x[2 * n + e.i], s.a[e.i], s.x[j],
+      dec = exact_is_pair(g, I, e.off, s.x[e.i], s.x[n + e.i], s.x[2 * n + e.i], s.a[e.i], s.x[j],
                           s.x[n + j], s.x[2 * n + j], s.a[j]) ? 1 : 0;
     }
     if (dec) {
@@ -48,8 +50,9 @@ __device__ __forceinline__ void scan_range(EnumCtx& e, int jb, int je, float cxo
   }
 }
 
-__global__ void __launch_bounds__(kThreads)
-k_enumerate(Geo g, StateBuf s, const float4* __restrict__ posf, const int* __restrict__ cellid,
+__global__ void __launch_bounds__(kThreads, 8)
+k_enumerate(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ sgk, StateBuf s,
+            const float4* __restrict__ posf, const int* __restrict__ cellid,
             const int* __restrict__ cell_start, ListBuf L, int* __restrict__ bw_count,
             unsigned long long* scan_status, int* scan_ticket, DevStatus* st, int adv) {
   if (dev_err(st)) return;
@@ -65,30 +68,35 @@ k_enumerate(Geo g, StateBuf s, const float4* __restrict__ posf, const int* __res
   e.cnt = 0;
   e.band = 0;
   if (i < n) {
+    const int inst = s.inst[i];
+    const InstGeo& I = ig[inst];
+    const StepGeo sg = sgk[inst];
     e.g = &g;
+    e.I = &I;
     e.s = &s;
     e.posf = posf;
     e.i = i;
-    e.off = st->sg.off;
+    e.off = sg.off;
     e.pi = posf[i];
     e.row = L.list + (int64_t)i * g.M;
-    const int fsh = st->sg.fsh;
-    const float offr = st->sg.offr_hi;
-    const int nx = g.nc[0], ny = g.nc[1], nz = g.nc[2];
-    const int c = cellid[i];
+    const int fsh = sg.fsh;
+    const float offr = sg.offr_hi;
+    const int nx = I.nc[0], ny = I.nc[1], nz = I.nc[2];
+    const int cb = I.cell_base;
+    const int c = cellid[i] - cb;
     const int cx = c % nx, cy = (c / nx) % ny, cz = c / (nx * ny);
     // own cell (partners after i) and the cell x+1
-    scan_range(e, i + 1, cell_start[c + 1], 0.f, 0.f, 0.f);
+    scan_range(e, i + 1, cell_start[cb + c + 1], 0.f, 0.f, 0.f);
     {
-      const int q = (cz * ny + cy) * nx + wrapi(cx + 1, nx);
-      scan_range(e, cell_start[q], cell_start[q + 1], g.csf[0], 0.f, 0.f);
+      const int q = cb + (cz * ny + cy) * nx + wrapi(cx + 1, nx);
+      scan_range(e, cell_start[q], cell_start[q + 1], I.csf[0], 0.f, 0.f);
     }
     // layer y, z+1: three x cells
     {
       const int qz = wrapi(cz + 1, nz);
       for (int ox = -1; ox <= 1; ++ox) {
-        const int q = (qz * ny + cy) * nx + wrapi(cx + ox, nx);
-        scan_range(e, cell_start[q], cell_start[q + 1], (float)ox * g.csf[0], 0.f, g.csf[2]);
+        const int q = cb + (qz * ny + cy) * nx + wrapi(cx + ox, nx);
+        scan_range(e, cell_start[q], cell_start[q + 1], (float)ox * I.csf[0], 0.f, I.csf[2]);
       }
     }
     // layer y+1: 3x3 cells, or across y = L_y the 4 x cells covering the
@@ -99,9 +107,9 @@ k_enumerate(Geo g, StateBuf s, const float4* __restrict__ posf, const int* __res
     for (int oz = -1; oz <= 1; ++oz) {
       const int qz = wrapi(cz + oz, nz);
       for (int ox = x0; ox <= x1; ++ox) {
-        const int q = (qz * ny + qy) * nx + wrapi(cx + ox, nx);
+        const int q = cb + (qz * ny + qy) * nx + wrapi(cx + ox, nx);
         float cxo, cyo, czo;
-        stencil_shift(g, ox, 1, oz, le ? 1 : 0, fsh, offr, cxo, cyo, czo);
+        stencil_shift(I, ox, 1, oz, le ? 1 : 0, fsh, offr, cxo, cyo, czo);
         scan_range(e, cell_start[q], cell_start[q + 1], cxo, cyo, czo);
       }
     }
@@ -160,7 +168,7 @@ void launch_enumerate(dss_handle* h, int stbuf, int dst_list, int adv) {
   ListBuf& L = h->lb[dst_list];
   prof_mark(h, 4);
   k_enumerate<<<enum_tiles_for(n), kThreads, 0, h->stream>>>(
-      h->g, h->st[stbuf], h->posf, h->cellid, h->cell_start, L, h->bw_count,
+      h->g, h->ig, h->sg, h->st[stbuf], h->posf, h->cellid, h->cell_start, L, h->bw_count,
       h->scan_status + h->scan_tiles_max, h->scan_ticket + 1, h->status, adv);
   h->last_list = dst_list;
 }

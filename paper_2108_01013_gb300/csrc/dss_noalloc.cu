@@ -95,7 +95,7 @@ __global__ void k_na_fill(NoAllocGrid q, int n, const double* __restrict__ x,
   order[start[c] + atomicAdd(&cursor[c], 1)] = i;
 }
 
-__global__ void k_na_pairs(NoAllocGrid q, Geo g, int n, const double* __restrict__ x,
+__global__ void k_na_pairs(NoAllocGrid q, Geo g, InstGeo I, int n, const double* __restrict__ x,
                            const double* __restrict__ a, const int* __restrict__ ids, double off,
                            const int* __restrict__ start, const int* __restrict__ order, int* s,
                            long long* __restrict__ out, long long cap) {
@@ -119,7 +119,7 @@ __global__ void k_na_pairs(NoAllocGrid q, Geo g, int n, const double* __restrict
         for (int t = start[qc]; t < start[qc + 1]; ++t) {
           const int j = order[t];
           if (j <= i) continue;
-          if (!exact_is_pair(g, off, xi, yi, zi, ai, x[j], x[n + j], x[2 * n + j], a[j])) continue;
+          if (!exact_is_pair(g, I, off, xi, yi, zi, ai, x[j], x[n + j], x[2 * n + j], a[j])) continue;
           const unsigned long long k = atomicAdd(counter, 1ull);
           if ((long long)k < cap) {
             const long long u = ids ? ids[i] : i, v = ids ? ids[j] : j;
@@ -188,15 +188,17 @@ extern "C" int dss_pairs_noalloc(const double* x, const double* a, const int32_t
   int* order = cursor + q.ncell;
   Geo g;
   memset(&g, 0, sizeof(g));
+  InstGeo I;
+  memset(&I, 0, sizeof(I));
   for (int d = 0; d < 3; ++d) {
-    g.L[d] = box[d];
-    g.halfL[d] = 0.5 * box[d];
-    g.invL[d] = 1.0 / box[d];
+    I.L[d] = box[d];
+    I.halfL[d] = 0.5 * box[d];
+    I.invL[d] = 1.0 / box[d];
   }
   g.delta = p->delta_lub;
   g.a0 = p->a0;
   g.mode = p->lub_cutoff_mode;
-  g.gdot = p->shear_rate;
+  I.gdot = p->shear_rate;
   g.dt = p->dt;
   // Lees-Edwards offset at time nstep*dt, with the same operations as the main path
   const double t = (double)nstep * p->dt;
@@ -209,7 +211,7 @@ extern "C" int dss_pairs_noalloc(const double* x, const double* a, const int32_t
   k_na_count<<<nb, 256, 0, st>>>(q, (int)n, x, a, a_max, s, cnt);
   k_na_scan<<<1, 1024, 0, st>>>(q.ncell, cnt, start);
   k_na_fill<<<nb, 256, 0, st>>>(q, (int)n, x, start, cursor, order);
-  k_na_pairs<<<nb, 256, 0, st>>>(q, g, (int)n, x, a, ids, off, start, order, s,
+  k_na_pairs<<<nb, 256, 0, st>>>(q, g, I, (int)n, x, a, ids, off, start, order, s,
                                  reinterpret_cast<long long*>(pairs), (long long)cap);
   if (cudaGetLastError() != cudaSuccess) return DSS_ERR_CUDA;
   int head[4] = {0, 0, 0, 0};

@@ -20,8 +20,8 @@ struct Pred {
   int cross;
 };
 
-__device__ __forceinline__ Pred predict_one(const Geo& g, const DevStatus* st, int adv,
-                                            const StateBuf& s, int i, bool predict) {
+__device__ __forceinline__ Pred predict_one(const Geo& g, const InstGeo& I, const DevStatus* st,
+                                            int adv, const StateBuf& s, int i, bool predict) {
   const int n = g.n;
   Pred r;
   double x = s.x[i], y = s.x[n + i], z = s.x[2 * n + i];
@@ -40,50 +40,52 @@ __device__ __forceinline__ Pred predict_one(const Geo& g, const DevStatus* st, i
     uz = __dadd_rn(uz, __dmul_rn(hdt, az));
     // Lees-Edwards wrap: leaving through y >= L_y re-enters at the bottom
     // shifted by -off along x with u_x - gdot L_y, and vice versa
-    const double Ly = g.L[1];
+    const double Ly = I.L[1];
     if (y >= Ly) {
       y = __dsub_rn(y, Ly);
-      x = __dsub_rn(x, le_offset(g, dev_nstep(st) + adv));
+      x = __dsub_rn(x, le_offset(g, I, dev_nstep(st) + adv));
       r.cross = -1;
     } else if (y < 0.0) {
       y = __dadd_rn(y, Ly);
-      x = __dadd_rn(x, le_offset(g, dev_nstep(st) + adv));
+      x = __dadd_rn(x, le_offset(g, I, dev_nstep(st) + adv));
       r.cross = 1;
       if (y >= Ly) y = 0.0;
     }
     // x back into [0, L_x): two conditional shifts give the same bits as
     // fmod followed by the two corrections, for |x| < 2 L_x
-    const double Lx = g.L[0];
+    const double Lx = I.L[0];
     if (x < 0.0) x = __dadd_rn(x, Lx); else if (x >= Lx) x = __dsub_rn(x, Lx);
     if (x < 0.0) x = __dadd_rn(x, Lx); else if (x >= Lx) x = __dsub_rn(x, Lx);
-    if (z >= g.L[2]) {
-      z = __dsub_rn(z, g.L[2]);
+    if (z >= I.L[2]) {
+      z = __dsub_rn(z, I.L[2]);
     } else if (z < 0.0) {
-      z = __dadd_rn(z, g.L[2]);
-      if (z >= g.L[2]) z = 0.0;
+      z = __dadd_rn(z, I.L[2]);
+      if (z >= I.L[2]) z = 0.0;
     }
     if (r.cross != 0)
-      ux = __dadd_rn(ux, __dmul_rn(__dmul_rn((double)r.cross, g.gdot), Ly));
+      ux = __dadd_rn(ux, __dmul_rn(__dmul_rn((double)r.cross, I.gdot), Ly));
   }
   r.x = x; r.y = y; r.z = z;
   r.ux = ux; r.uy = uy; r.uz = uz;
   return r;
 }
 
-__device__ __forceinline__ int cell_key(const Geo& g, double x, double y, double z) {
-  int cx = cell_coord(x, g.inv_cs[0], g.nc[0]);
-  int cy = cell_coord(y, g.inv_cs[1], g.nc[1]);
-  int cz = cell_coord(z, g.inv_cs[2], g.nc[2]);
-  return (cz * g.nc[1] + cy) * g.nc[0] + cx;
+__device__ __forceinline__ int cell_key(const InstGeo& I, double x, double y, double z) {
+  int cx = cell_coord(x, I.inv_cs[0], I.nc[0]);
+  int cy = cell_coord(y, I.inv_cs[1], I.nc[1]);
+  int cz = cell_coord(z, I.inv_cs[2], I.nc[2]);
+  return I.cell_base + (cz * I.nc[1] + cy) * I.nc[0] + cx;
 }
 
 // 1. key + warp-aggregated histogram
 __global__ void __launch_bounds__(kThreads)
-k_key_hist(Geo g, StateBuf s, int* __restrict__ key, int* __restrict__ offs,
-           int* __restrict__ cell_count, DevStatus* st, bool predict,
-           unsigned long long* scan_status, int* scan_ticket, int scan_tiles) {
+k_key_hist(Geo g, const InstGeo* __restrict__ ig, StepGeo* __restrict__ sg, StateBuf s,
+           int* __restrict__ key, int* __restrict__ offs, int* __restrict__ cell_count,
+           DevStatus* st, bool predict, unsigned long long* scan_status, int* scan_ticket,
+           int scan_tiles) {
   if (dev_err(st)) return;
-  // reset the look-back state of both scans of this step
+  // reset the look-back state of both scans of this operation, the
+  // counters, and set every instance's Lees-Edwards geometry for its time
   if (blockIdx.x == 0) {
     for (int t = threadIdx.x; t < 2 * scan_tiles; t += blockDim.x) scan_status[t] = 0ull;
     if (threadIdx.x < 2) scan_ticket[threadIdx.x] = 0;
@@ -91,20 +93,25 @@ k_key_hist(Geo g, StateBuf s, int* __restrict__ key, int* __restrict__ offs,
       st->w[ST_MAXROW] = 0;
       st->w[ST_BAND] = 0;
       st->w[ST_NCONT] = 0;
-      // Lees-Edwards geometry of this operation's time
-      const double off = le_offset(g, dev_nstep(st) + (predict ? 1 : 0));
-      const int fsh = le_shift_cells(g, off);
-      const double offr = off - fsh * g.cs[0];
-      st->sg.off = off;
-      st->sg.fsh = fsh;
-      st->sg.offr_hi = (float)offr;
-      st->sg.offr_lo = (float)(offr - (double)(float)offr);
+    }
+    for (int k = threadIdx.x; k < g.K; k += blockDim.x) {
+      const InstGeo& I = ig[k];
+      const double off = le_offset(g, I, dev_nstep(st) + (predict ? 1 : 0));
+      const int fsh = le_shift_cells(I, off);
+      const double offr = off - fsh * I.cs[0];
+      StepGeo q;
+      q.off = off;
+      q.fsh = fsh;
+      q.offr_hi = (float)offr;
+      q.offr_lo = (float)(offr - (double)q.offr_hi);
+      sg[k] = q;
     }
   }
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= g.n) return;
-  Pred p = predict_one(g, st, predict ? 1 : 0, s, i, predict);
-  int k = cell_key(g, p.x, p.y, p.z);
+  const InstGeo& I = ig[s.inst[i]];
+  Pred p = predict_one(g, I, st, predict ? 1 : 0, s, i, predict);
+  int k = cell_key(I, p.x, p.y, p.z);
   unsigned act = __activemask();
   unsigned peers = __match_any_sync(act, k);
   int lane = threadIdx.x & 31;
@@ -129,10 +136,10 @@ k_scatter(int n, const int* __restrict__ key, const int* __restrict__ offs,
 
 // 4. stable order inside each cell (by previous index) and state gather
 __global__ void __launch_bounds__(kThreads)
-k_rank_gather(Geo g, StateBuf src, StateBuf dst, const int* __restrict__ key,
-              const int* __restrict__ cell_start, const int* __restrict__ tmp,
-              int* __restrict__ perm, int* __restrict__ cellid, float4* __restrict__ posf,
-              DevStatus* st, bool predict) {
+k_rank_gather(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ sgk, StateBuf src,
+              StateBuf dst, const int* __restrict__ key, const int* __restrict__ cell_start,
+              const int* __restrict__ tmp, int* __restrict__ perm, int* __restrict__ cellid,
+              float4* __restrict__ posf, DevStatus* st, bool predict) {
   if (dev_err(st)) return;
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = g.n;
@@ -145,7 +152,9 @@ k_rank_gather(Geo g, StateBuf src, StateBuf dst, const int* __restrict__ key,
   int f = c0 + rank;
   perm[f] = o;
   cellid[f] = k;
-  Pred p = predict_one(g, st, predict ? 1 : 0, src, o, predict);
+  const int inst = src.inst[o];
+  const InstGeo& I = ig[inst];
+  Pred p = predict_one(g, I, st, predict ? 1 : 0, src, o, predict);
   dst.x[f] = p.x; dst.x[n + f] = p.y; dst.x[2 * n + f] = p.z;
   dst.u[f] = p.ux; dst.u[n + f] = p.uy; dst.u[2 * n + f] = p.uz;
   if (predict) {
@@ -162,19 +171,21 @@ k_rank_gather(Geo g, StateBuf src, StateBuf dst, const int* __restrict__ key,
   double a = src.a[o];
   dst.a[f] = a;
   dst.id[f] = src.id[o];
+  dst.inst[f] = inst;
   if (g.precision == DSS_MIXED) {
     // FP32 copies relative to the ambient flow for the FP32 pair arithmetic:
     // u - U_inf(x) and w - Omega_inf are O(gdot a), free of O(gdot L) terms
-    dst.vf[f] = make_float4((float)(p.ux - g.gdot * p.y), (float)p.uy, (float)p.uz, 0.f);
+    dst.vf[f] = make_float4((float)(p.ux - I.gdot * p.y), (float)p.uy, (float)p.uz, 0.f);
     dst.wf[f] = make_float4((float)dst.w[f], (float)dst.w[n + f],
-                            (float)(dst.w[2 * n + f] + 0.5 * g.gdot), 0.f);
+                            (float)(dst.w[2 * n + f] + 0.5 * I.gdot), 0.f);
   }
   // cell-local position (FP32 for the enumeration prefilter; in mixed
   // precision also the low words, for double-float pair geometry)
-  int cx = k % g.nc[0];
-  int cy = (k / g.nc[0]) % g.nc[1];
-  int cz = k / (g.nc[0] * g.nc[1]);
-  const double lx = p.x - cx * g.cs[0], ly = p.y - cy * g.cs[1], lz = p.z - cz * g.cs[2];
+  const int kl = k - I.cell_base;
+  int cx = kl % I.nc[0];
+  int cy = (kl / I.nc[0]) % I.nc[1];
+  int cz = kl / (I.nc[0] * I.nc[1]);
+  const double lx = p.x - cx * I.cs[0], ly = p.y - cy * I.cs[1], lz = p.z - cz * I.cs[2];
   float4 pf;
   pf.x = (float)lx;
   pf.y = (float)ly;
@@ -186,6 +197,7 @@ k_rank_gather(Geo g, StateBuf src, StateBuf dst, const int* __restrict__ key,
                               (float)(lz - (double)pf.z), (float)(a - (double)pf.w));
     dst.cellc[f] = cx | (cy << 10) | (cz << 20);
   }
+  (void)sgk;
 }
 
 }  // namespace
@@ -275,15 +287,15 @@ void launch_sort(dss_handle* h, bool predict, int src, int dst) {
   const int n = (int)h->n;
   const int blocks = (n + kThreads - 1) / kThreads;
   prof_mark(h, 0);
-  k_key_hist<<<blocks, kThreads, 0, h->stream>>>(h->g, h->st[src], h->key, h->offs, h->cell_count,
-                                                 h->status, predict, h->scan_status, h->scan_ticket,
-                                                 h->scan_tiles_max);
+  k_key_hist<<<blocks, kThreads, 0, h->stream>>>(h->g, h->ig, h->sg, h->st[src], h->key, h->offs,
+                                                 h->cell_count, h->status, predict, h->scan_status,
+                                                 h->scan_ticket, h->scan_tiles_max);
   prof_mark(h, 1);
   launch_scan(h, h->cell_count, h->cell_start, h->g.ncell, 0, true);
   prof_mark(h, 2);
   k_scatter<<<blocks, kThreads, 0, h->stream>>>(n, h->key, h->offs, h->cell_start, h->tmp, h->status);
   prof_mark(h, 3);
-  k_rank_gather<<<blocks, kThreads, 0, h->stream>>>(h->g, h->st[src], h->st[dst], h->key,
+  k_rank_gather<<<blocks, kThreads, 0, h->stream>>>(h->g, h->ig, h->sg, h->st[src], h->st[dst], h->key,
                                                     h->cell_start, h->tmp, h->perm, h->cellid,
                                                     h->posf, h->status, predict);
 }

@@ -190,3 +190,53 @@ class Suspension:
             self.close()
         except Exception:
             pass
+
+
+class Batch(Suspension):
+    """K independent suspensions advanced together in one handle.
+
+    ``n`` lists the particle counts, ``boxes`` the (K, 3) box edges and
+    ``shear_rates`` the K shear rates; ``gamma_n`` (K) defaults to
+    1e-7 kn / gdot per instance.  x (3, sum n), a and the optional per-particle
+    arrays are concatenated instance-major; ``ids`` (optional) permutes each
+    instance's own index range.  Every ``Suspension`` method applies to the
+    concatenated system; ``batch_stress`` returns every instance's stress.
+    """
+
+    def __init__(self, x, a, n, boxes, shear_rates, params=None, *, gamma_n=None, ids=None, u=None,
+                 w=None, alpha_lin=None, alpha_ang=None, nstep=0, stream=None, **kw):
+        import torch
+        self.lib = nat.load()
+        self.sizes = np.asarray(n, dtype=np.int64).copy()
+        self.K = int(self.sizes.shape[0])
+        self.n = int(self.sizes.sum())
+        self.boxes = np.ascontiguousarray(boxes, dtype=np.float64).reshape(self.K, 3).copy()
+        self.box = self.boxes[0]
+        self.shear_rates = np.ascontiguousarray(shear_rates, dtype=np.float64).reshape(self.K).copy()
+        self.params = params if params is not None else default_params(**kw)
+        if gamma_n is None:
+            kn = self.params.kn
+            gamma_n = np.array([1e-7 * kn / g if g != 0 else 0.0 for g in self.shear_rates])
+        self.gamma_n = np.ascontiguousarray(gamma_n, dtype=np.float64).reshape(self.K).copy()
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        self._h = c_void_p()
+        dp = ctypes.POINTER(c_double)
+        nat.check(self.lib.dss_batch_create(
+            byref(self._h), byref(self.params), self.K,
+            self.sizes.ctypes.data_as(ctypes.POINTER(c_int64)), self.boxes.ctypes.data_as(dp),
+            self.shear_rates.ctypes.data_as(dp), self.gamma_n.ctypes.data_as(dp),
+            c_void_p(stream.cuda_stream)), "dss_batch_create")
+        self.set_state(x, a, ids=ids, u=u, w=w, alpha_lin=alpha_lin, alpha_ang=alpha_ang, nstep=nstep)
+
+    def batch_stress(self, reset: bool = False):
+        """(sigma, sigma_mean, steps): (K, 3, 3) stress of the last force
+        evaluation, its mean over the steps since set_state / the last reset,
+        and the number of those steps."""
+        s = np.zeros((self.K, 9))
+        m = np.zeros((self.K, 9))
+        cnt = c_int64(0)
+        nat.check(self.lib.dss_batch_stress(self._h, c_void_p(s.ctypes.data), c_void_p(m.ctypes.data),
+                                            byref(cnt), 1 if reset else 0), "dss_batch_stress")
+        return s.reshape(self.K, 3, 3), m.reshape(self.K, 3, 3), cnt.value
