@@ -14,7 +14,15 @@ step is timed on its own with CUDA events recorded inside the step's CUDA
 graph (per-kernel events; the step time runs from the first kernel's start to
 the last kernel's end).
 
+Two more modes are measured in the same run and reported under "modes":
+"fp64", the same workload with the FP64 pair arithmetic, and "batched", a
+flow-curve sweep of 256 independent bidisperse suspensions (N uniform in
+[500, 20000], volume fraction uniform in [0.40, 0.58], shear rate log-uniform
+in [1e-2, 1e2], mixed precision) advanced together in one handle after the
+cell edge is autotuned; its working set (~1.5 GB) exceeds the L2.
+
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+                       [--modes fp64,batched|none]
 Under torchrun each rank runs an independent replica (replicas only: the
 single-instance path has no data-parallel exchange); value = total particle
 steps of all ranks / max over ranks of the timed GPU time.
@@ -90,6 +98,10 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--modes", default="fp64,batched",
+                    help="extra modes measured in the same run: fp64 (the headline workload in "
+                         "FP64), batched (256-instance flow-curve sweep, mixed); 'none' for neither")
+    ap.add_argument("--mode-steps", type=int, default=400)
     return ap.parse_args()
 
 
@@ -182,6 +194,76 @@ def workload(name: str, rank: int):
     return spec, synth.generate(spec)
 
 
+def time_steps(s, steps, flush=None):
+    """GPU time (ms) of ``steps`` single-step graph replays, each after an
+    optional L2 flush; returns the total."""
+    t = 0.0
+    for _ in range(steps):
+        if flush is not None:
+            flush.fill_(1.0)
+        s.step(1)
+        t += s.last_step_ms()
+    return t
+
+
+def profile_pass(s, steps, flush=None):
+    s.set_profiling(True)
+    for _ in range(steps):
+        if flush is not None:
+            flush.fill_(1.0)
+        s.step(1)
+    prof, nprof = s.profile()
+    s.set_profiling(False)
+    return {k: round(v / max(nprof, 1), 5) for k, v in prof.items()}
+
+
+def mode_fp64(dss, g, spec, kw, args, flush, stream):
+    """The headline workload with the FP64 pair arithmetic."""
+    n = g["a"].shape[0]
+    p = dss.default_params(g["box"], precision="fp64", **kw)
+    s = dss.Suspension(g["x"], g["a"], g["box"], p, ids=g["ids"], stream=stream)
+    time_steps(s, 5, flush)
+    steps = min(args.mode_steps * 2, args.steps)
+    t = time_steps(s, steps, flush)
+    out = {"value": n * steps / (t * 1e-3), "unit": "particle-steps/s", "ms_per_step": t / steps,
+           "steps": steps, "dtype": "f64", "config": {"workload": spec.name, "n": n, "precision": "fp64",
+                                                      "l2": "flushed before every timed step"},
+           "kernels_ms": profile_pass(s, 20, flush)}
+    s.close()
+    return out
+
+
+def mode_batched(dss, b, bspec, args, stream):
+    """The flow-curve sweep: every instance of the batch advanced together,
+    cell edge autotuned first."""
+    p = dss.default_params(precision="mixed", mu=bspec.mu, kn=bspec.kn, dt=bspec.dt)
+    s = dss.Batch(b["x"], b["a"], b["n"], b["boxes"], b["shear_rates"], p, ids=b["ids"], stream=stream)
+    N = int(b["n"].sum())
+    cs, trials = s.autotune(trial_steps=10)
+    time_steps(s, 5)
+    s.batch_stress(reset=True)
+    steps = args.mode_steps
+    t = time_steps(s, steps)
+    _, mean, nmean = s.batch_stress()
+    eta = mean[:, 0, 1] / b["shear_rates"]          # eta0 = 1: relative viscosity per instance
+    c = s.counters()
+    out = {"value": N * steps / (t * 1e-3), "unit": "particle-steps/s", "ms_per_step": t / steps,
+           "steps": steps, "dtype": "f32+f64",
+           "config": {"workload": bspec.name, "instances": int(bspec.K), "n_total": N,
+                      "n_range": [int(b["n"].min()), int(b["n"].max())],
+                      "phi_range": [round(float(b["phi"].min()), 4), round(float(b["phi"].max()), 4)],
+                      "shear_rate_range": [float(b["shear_rates"].min()), float(b["shear_rates"].max())],
+                      "precision": "mixed", "mu": bspec.mu,
+                      "l2": "working set > L2 (no flush)",
+                      "packing": "random insertion + %d relaxation sweeps" % bspec.max_iter},
+           "autotune": {"cell_edge": cs, "ms_per_step_by_factor": trials},
+           "mean_stress_steps": nmean,
+           "eta_r_quartiles": [float(q) for q in np.percentile(eta, [0, 25, 50, 75, 100])],
+           "pairs": c["npairs"], "kernels_ms": profile_pass(s, 10)}
+    s.close()
+    return out
+
+
 def run_reference(args, rank, world):
     spec, g = workload(args.workload, 0)
     if rank != 0:
@@ -229,6 +311,17 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+
+    modes = [] if args.modes in ("", "none") else args.modes.split(",")
+    batch = None
+    if "batched" in modes:
+        # packed by spawned worker processes before the first CUDA call
+        from paper_2108_01013_gb300 import synth
+        bspec = synth.BATCH_SPECS["c4"]
+        if rank:
+            from dataclasses import replace
+            bspec = replace(bspec, seed=bspec.seed + 1000 * rank)
+        batch = synth.generate_batch(bspec)
 
     import torch
     import torch.distributed as dist
@@ -298,6 +391,23 @@ def main():
         t_e2e = time.perf_counter() - t0
         e2e_value = n * args.e2e_steps / t_e2e * world
         bytes_state = 5 * 3 * n * 8
+        s.close()
+        extra = {}
+        if "fp64" in modes:
+            extra["fp64"] = mode_fp64(dss, g, spec, kw, args, flush, stream)
+        del flush
+        if batch is not None:
+            extra["batched"] = mode_batched(dss, batch, bspec, args, stream)
+        if world > 1:
+            for m in extra.values():
+                tt = torch.tensor([m["ms_per_step"]], device=dev, dtype=torch.float64)
+                dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+                m["value"] = m["value"] * m["ms_per_step"] / float(tt.item()) * world
+                m["ms_per_step"] = float(tt.item())
+        if "fp64" in extra:
+            extra["mixed_vs_fp64"] = value / extra["fp64"]["value"]
+            if "batched" in extra:
+                extra["batched_vs_fp64_single"] = extra["batched"]["value"] / extra["fp64"]["value"]
 
     # roofline of the dominant kernel
     peaks, src = load_peaks()
@@ -342,12 +452,13 @@ def main():
         "wall_s_timed_region": t_wall,
         "clocks": clk,
         "gpu_launches": KERNELS_PER_STEP * args.steps,
+        "gpu_launches_note": "headline timed region: %d kernels per step graph" % KERNELS_PER_STEP,
         "e2e": {"value": e2e_value, "unit": "particle-steps/s", "h2d_bytes_per_step": bytes_state,
                 "d2h_bytes_per_step": bytes_state + 72},
         "cpu_baseline": cpu,
+        "modes": extra,
     }
     print(json.dumps(line), flush=True)
-    s.close()
 
 
 if __name__ == "__main__":

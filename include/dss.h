@@ -224,6 +224,34 @@ const char *dss_profile_name(int k);
  * after the last graph launch; no per-kernel events). */
 int dss_last_step_ms(dss_handle *h, double *ms);
 
+/* Checkpoint of the whole dynamic state: positions, velocities, angular
+ * velocities and both accelerations (id order), radii, the contact history
+ * (keys and tangential stretch), the step count, the last stress and the
+ * running stress sums of every instance.  With buf == NULL, *len receives the
+ * size needed; otherwise buf (host memory, *len bytes) receives the
+ * checkpoint and *len its size (DSS_ERR_ARG, with *len set, when too small).
+ * Synchronises the stream. */
+int dss_save(dss_handle *h, void *buf, size_t *len);
+
+/* Restores a checkpoint written by dss_save into a handle created with the
+ * same instances, boxes, shear rates, dashpots and model constants
+ * (DSS_ERR_ARG otherwise, or for a damaged buffer).  Because the library's
+ * sorted order depends only on positions and ids, the resumed run repeats the
+ * uninterrupted one bit for bit.  Synchronises the stream. */
+int dss_load(dss_handle *h, const void *buf, size_t len);
+
+/* Chooses the cell edge from timed trials.  Candidate k uses a cell edge of
+ * factors[k] (>= 1) times the smallest admissible one, 2 a_max + delta_max
+ * (Sec. II A); factors == NULL with ncand == 0 tries 1.0, 1.1, 1.25, 1.5.
+ * Each candidate rebuilds the grid, runs 2 untimed and trial_steps timed
+ * steps (GPU time of the step graphs) from the state at the call, and
+ * writes its ms per step to ms_per_step[k] (may be NULL; INFINITY for a
+ * grid the box does not admit).  The fastest edge is kept (*cell_size, may
+ * be NULL) and the state at the call is restored exactly (dss_save /
+ * dss_load), so the trials leave no trace in the trajectory.  ncand <= 16. */
+int dss_autotune(dss_handle *h, int32_t trial_steps, int32_t ncand, const double *factors,
+                 double *ms_per_step, double *cell_size);
+
 /* Bytes of device memory the handle holds. */
 int64_t dss_device_bytes(const dss_handle *h);
 

@@ -11,7 +11,7 @@ import ctypes
 import os
 import subprocess
 from concurrent.futures import ThreadPoolExecutor
-from ctypes import POINTER, Structure, c_char_p, c_double, c_int, c_int32, c_int64, c_void_p
+from ctypes import POINTER, Structure, c_char_p, c_double, c_int, c_int32, c_int64, c_size_t, c_void_p
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _CSRC = os.path.join(_HERE, "csrc")
@@ -99,6 +99,9 @@ SIGNATURES = {
                                  c_void_p]),
     "dss_batch_size": (c_int32, [c_void_p]),
     "dss_batch_stress": (c_int, [c_void_p, _vp, _vp, _lp, c_int]),
+    "dss_save": (c_int, [c_void_p, _vp, POINTER(c_size_t)]),
+    "dss_load": (c_int, [c_void_p, _vp, c_size_t]),
+    "dss_autotune": (c_int, [c_void_p, c_int32, c_int32, _dp, _dp, _dp]),
     "dss_set_state": (c_int, [c_void_p, _vp, _vp, _vp, _vp, _vp, _vp, _vp, c_int64]),
     "dss_get_state": (c_int, [c_void_p, _vp, _vp, _vp, _vp, _vp]),
     "dss_set_history": (c_int, [c_void_p, c_int64, _vp, _vp]),

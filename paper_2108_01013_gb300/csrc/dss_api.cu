@@ -969,6 +969,212 @@ int dss_last_step_ms(dss_handle* h, double* ms) {
   return DSS_OK;
 }
 
+// ------------------------------------------------------------------------
+// Checkpoint / resume.  Layout (host byte order):
+//   CkptHeader, then x, u, w, alpha_lin, alpha_ang (3n doubles each, id
+//   order), a (n doubles, id order), history keys (nhist int64), stretch
+//   (3*nhist doubles), sigma and sigma_sum (9K doubles each).
+// The sorted order inside the library is a function of positions and ids
+// alone, so a run resumed from a checkpoint repeats the uninterrupted run bit
+// for bit.
+// ------------------------------------------------------------------------
+namespace {
+struct CkptHeader {
+  char magic[8];
+  uint32_t version;
+  int32_t K;
+  int64_t n;
+  int64_t nstep;
+  int64_t nhist;
+  int64_t mean_steps;
+  uint64_t config;
+};
+constexpr char kMagic[8] = {'D', 'S', 'S', 'C', 'K', 'P', 'T', '1'};
+
+uint64_t fnv1a(uint64_t hsh, const void* p, size_t len) {
+  const unsigned char* b = static_cast<const unsigned char*>(p);
+  for (size_t i = 0; i < len; ++i) {
+    hsh ^= b[i];
+    hsh *= 1099511628211ull;
+  }
+  return hsh;
+}
+
+// Fingerprint of what a checkpoint must agree with: instance layout, boxes,
+// shear rates, dashpots and the model constants.
+uint64_t config_hash(const dss_handle* h) {
+  uint64_t v = 1469598103934665603ull;
+  v = fnv1a(v, &h->K, sizeof(h->K));
+  v = fnv1a(v, h->inst_n, sizeof(int64_t) * h->K);
+  v = fnv1a(v, h->inst_box, sizeof(double) * 3 * h->K);
+  v = fnv1a(v, h->inst_gdot, sizeof(double) * h->K);
+  v = fnv1a(v, h->inst_gn, sizeof(double) * h->K);
+  const dss_params& p = h->p;
+  const double c[9] = {p.kn, p.kt, p.mu, p.eta0, p.rho, p.delta_lub, p.lub_eps, p.a0, p.dt};
+  v = fnv1a(v, c, sizeof(c));
+  const int32_t m[2] = {p.lub_cutoff_mode, p.precision};
+  v = fnv1a(v, m, sizeof(m));
+  return v;
+}
+
+size_t ckpt_bytes(int64_t n, int64_t nhist, int K) {
+  return sizeof(CkptHeader) + sizeof(double) * 16 * (size_t)n + (sizeof(int64_t) + 3 * sizeof(double)) * nhist +
+         sizeof(double) * 18 * (size_t)K;
+}
+
+// Forces the next dss_set_state to rebuild the cell grid and buffers.
+void unsize(dss_handle* h) {
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  drop_graphs(h);
+  if (h->sized) free_buffers(h);
+  h->sized = false;
+  h->have_state = false;
+}
+}  // namespace
+
+int dss_save(dss_handle* h, void* buf, size_t* len) {
+  if (!h || !len) return DSS_ERR_ARG;
+  if (!h->have_state) return DSS_ERR_STATE;
+  int64_t nh = 0;
+  int r = dss_get_history(h, nullptr, nullptr, 0, &nh);
+  if (r) return r;
+  const int64_t n = h->n;
+  const size_t need = ckpt_bytes(n, nh, h->K);
+  if (!buf) {
+    *len = need;
+    return DSS_OK;
+  }
+  if (*len < need) {
+    *len = need;
+    return DSS_ERR_ARG;
+  }
+  CkptHeader hd;
+  memset(&hd, 0, sizeof(hd));
+  memcpy(hd.magic, kMagic, 8);
+  hd.version = 1;
+  hd.K = h->K;
+  hd.n = n;
+  hd.nhist = nh;
+  hd.mean_steps = h->mean_steps;
+  hd.config = config_hash(h);
+  char* out = static_cast<char*>(buf);
+  double* x = reinterpret_cast<double*>(out + sizeof(CkptHeader));
+  double* a = x + 15 * n;
+  int64_t* keys = reinterpret_cast<int64_t*>(a + n);
+  double* xi = reinterpret_cast<double*>(keys + nh);
+  double* sig = xi + 3 * nh;
+  std::vector<double> st(15 * (size_t)n);
+  if ((r = dss_get_state(h, st.data(), st.data() + 3 * n, st.data() + 6 * n, st.data() + 9 * n,
+                         st.data() + 12 * n)))
+    return r;
+  memcpy(x, st.data(), sizeof(double) * 15 * n);
+  int64_t nh2 = 0;
+  if (nh > 0 && (r = dss_get_history(h, keys, xi, nh, &nh2))) return r;
+  if (nh2 != nh && nh > 0) return DSS_ERR_INTERNAL;
+  CK(cudaMemcpyAsync(a, h->a_by_id, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(sig, h->sigma, sizeof(double) * 9 * h->K, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(sig + 9 * h->K, h->sigma_sum, sizeof(double) * 9 * h->K, cudaMemcpyDeviceToHost,
+                     h->stream));
+  if ((r = sync_status(h))) return r;
+  hd.nstep = (int64_t)(uint32_t)h->status_host->w[ST_NSTEP_LO] |
+             ((int64_t)h->status_host->w[ST_NSTEP_HI] << 32);
+  memcpy(out, &hd, sizeof(hd));
+  *len = need;
+  return DSS_OK;
+}
+
+int dss_load(dss_handle* h, const void* buf, size_t len) {
+  if (!h || !buf || len < sizeof(CkptHeader)) return DSS_ERR_ARG;
+  CkptHeader hd;
+  memcpy(&hd, buf, sizeof(hd));
+  if (memcmp(hd.magic, kMagic, 8) != 0 || hd.version != 1 || hd.K != h->K || hd.n != h->n ||
+      hd.nhist < 0 || hd.nstep < 0 || hd.mean_steps < 0 || hd.config != config_hash(h))
+    return DSS_ERR_ARG;
+  const int64_t n = hd.n, nh = hd.nhist;
+  if (len < ckpt_bytes(n, nh, h->K)) return DSS_ERR_ARG;
+  // copies keep the arrays aligned whatever the caller's buffer alignment
+  const char* in = static_cast<const char*>(buf) + sizeof(CkptHeader);
+  std::vector<double> st(16 * (size_t)n);
+  memcpy(st.data(), in, sizeof(double) * 16 * n);
+  in += sizeof(double) * 16 * n;
+  std::vector<int64_t> keys(std::max<int64_t>(nh, 1));
+  std::vector<double> xi(3 * (size_t)std::max<int64_t>(nh, 1));
+  memcpy(keys.data(), in, sizeof(int64_t) * nh);
+  in += sizeof(int64_t) * nh;
+  memcpy(xi.data(), in, sizeof(double) * 3 * nh);
+  in += sizeof(double) * 3 * nh;
+  std::vector<double> sig(18 * (size_t)h->K);
+  memcpy(sig.data(), in, sizeof(double) * 18 * h->K);
+  const double* x = st.data();
+  int r = dss_set_state(h, x, x + 15 * n, nullptr, x + 3 * n, x + 6 * n, x + 9 * n, x + 12 * n, hd.nstep);
+  if (r) return r;
+  if ((r = dss_set_history(h, nh, keys.data(), xi.data()))) return r;
+  CK(cudaMemcpyAsync(h->sigma, sig.data(), sizeof(double) * 9 * h->K, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->sigma_sum, sig.data() + 9 * h->K, sizeof(double) * 9 * h->K,
+                     cudaMemcpyHostToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  h->mean_steps = hd.mean_steps;
+  return DSS_OK;
+}
+
+int dss_autotune(dss_handle* h, int32_t trial_steps, int32_t ncand, const double* factors,
+                 double* ms_per_step, double* cell_size) {
+  static const double kDefault[4] = {1.0, 1.1, 1.25, 1.5};
+  if (!h || trial_steps < 1 || ncand < 0 || ncand > 16 || (ncand > 0 && !factors)) return DSS_ERR_ARG;
+  if (!h->have_state) return DSS_ERR_STATE;
+  if (ncand == 0) {
+    ncand = 4;
+    factors = kDefault;
+  }
+  for (int c = 0; c < ncand; ++c)
+    if (!(factors[c] >= 1.0) || !std::isfinite(factors[c])) return DSS_ERR_ARG;
+  size_t len = 0;
+  int r = dss_save(h, nullptr, &len);
+  if (r) return r;
+  std::vector<char> ck(len);
+  if ((r = dss_save(h, ck.data(), &len))) return r;
+  const dss_params& p = h->p;
+  const double dmax = p.lub_cutoff_mode == 1 ? p.delta_lub * p.a0 : p.delta_lub * h->a_max;
+  const double cmin = (2.0 * h->a_max + dmax) * (1.0 + 1e-9) + 1e-12;
+  const double base = p.cell_size > 0.0 ? p.cell_size : cmin;
+  const bool prof_was = h->profiling;
+  h->profiling = false;
+  double best = INFINITY, best_cs = base;
+  for (int c = 0; c < ncand; ++c) {
+    const double cs = factors[c] * cmin;
+    double ms = INFINITY;
+    h->p.cell_size = cs;
+    unsize(h);
+    r = dss_load(h, ck.data(), len);
+    if (r == DSS_OK) {
+      r = dss_step(h, 2);   // captures the step graphs
+      double t = 0.0;
+      if (r == DSS_OK) r = dss_step(h, trial_steps);
+      if (r == DSS_OK && dss_last_step_ms(h, &t) == DSS_OK) ms = t / trial_steps;
+    }
+    if (r != DSS_OK && r != DSS_ERR_BOX && r != DSS_ERR_ARG) {
+      h->p.cell_size = base;
+      unsize(h);
+      dss_load(h, ck.data(), len);
+      h->profiling = prof_was;
+      return r;
+    }
+    if (ms_per_step) ms_per_step[c] = ms;
+    if (ms < best) {
+      best = ms;
+      best_cs = cs;
+    }
+  }
+  // keep the fastest grid and return to the saved state
+  h->p.cell_size = best < INFINITY ? best_cs : base;
+  unsize(h);
+  r = dss_load(h, ck.data(), len);
+  h->profiling = prof_was;
+  if (r) return r;
+  if (cell_size) *cell_size = h->p.cell_size;
+  return best < INFINITY ? DSS_OK : DSS_ERR_BOX;
+}
+
 int64_t dss_device_bytes(const dss_handle* h) { return h ? h->bytes : 0; }
 
 void dss_destroy(dss_handle* h) {

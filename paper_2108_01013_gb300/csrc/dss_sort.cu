@@ -134,7 +134,9 @@ k_scatter(int n, const int* __restrict__ key, const int* __restrict__ offs,
   tmp[cell_start[key[i]] + offs[i]] = i;
 }
 
-// 4. stable order inside each cell (by previous index) and state gather
+// 4. order inside each cell by id (so the sorted order, and with it every
+// summation order downstream, is a function of positions and ids alone) and
+// state gather
 __global__ void __launch_bounds__(kThreads)
 k_rank_gather(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ sgk, StateBuf src,
               StateBuf dst, const int* __restrict__ key, const int* __restrict__ cell_start,
@@ -147,8 +149,9 @@ k_rank_gather(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__
   int o = tmp[s];
   int k = key[o];
   int c0 = cell_start[k], c1 = cell_start[k + 1];
+  const int id = src.id[o];
   int rank = 0;
-  for (int q = c0; q < c1; ++q) rank += (tmp[q] < o);
+  for (int q = c0; q < c1; ++q) rank += (src.id[tmp[q]] < id);
   int f = c0 + rank;
   perm[f] = o;
   cellid[f] = k;
@@ -170,7 +173,7 @@ k_rank_gather(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__
   }
   double a = src.a[o];
   dst.a[f] = a;
-  dst.id[f] = src.id[o];
+  dst.id[f] = id;
   dst.inst[f] = inst;
   if (g.precision == DSS_MIXED) {
     // FP32 copies relative to the ambient flow for the FP32 pair arithmetic:

@@ -177,6 +177,30 @@ class Suspension:
         nat.check(self.lib.dss_set_history(self._h, keys.shape[0], c_void_p(keys.ctypes.data),
                                            c_void_p(xi.ctypes.data)), "dss_set_history")
 
+    def save(self) -> bytes:
+        """Checkpoint of the dynamic state, history, step count and stress sums."""
+        ln = ctypes.c_size_t(0)
+        nat.check(self.lib.dss_save(self._h, None, byref(ln)), "dss_save")
+        buf = ctypes.create_string_buffer(ln.value)
+        nat.check(self.lib.dss_save(self._h, buf, byref(ln)), "dss_save")
+        return buf.raw[:ln.value]
+
+    def load(self, ckpt: bytes):
+        """Resume from a checkpoint of a handle with the same configuration."""
+        buf = ctypes.create_string_buffer(bytes(ckpt), len(ckpt))
+        nat.check(self.lib.dss_load(self._h, buf, len(ckpt)), "dss_load")
+
+    def autotune(self, trial_steps: int = 20, factors=None):
+        """Time candidate cell edges (factors of the smallest admissible one),
+        keep the fastest, restore the state.  Returns (cell edge, {factor: ms/step})."""
+        f = np.ascontiguousarray(factors if factors is not None else [1.0, 1.1, 1.25, 1.5], dtype=np.float64)
+        ms = np.zeros(f.shape[0])
+        cs = c_double(0.0)
+        dp = ctypes.POINTER(c_double)
+        nat.check(self.lib.dss_autotune(self._h, int(trial_steps), f.shape[0], f.ctypes.data_as(dp),
+                                        ms.ctypes.data_as(dp), byref(cs)), "dss_autotune")
+        return cs.value, dict(zip(f.tolist(), ms.tolist()))
+
     def device_bytes(self) -> int:
         return int(self.lib.dss_device_bytes(self._h))
 

@@ -170,6 +170,78 @@ def generate(spec: Spec, relax: bool = True):
                 info=dict(inserted=int(placed), sweeps=int(sweeps), max_overlap=float(mo.value)))
 
 
+@dataclass(frozen=True)
+class BatchSpec:
+    """K independent bidisperse suspensions of a flow-curve sweep: particle
+    count uniform in ``n_range``, volume fraction uniform in ``phi_range`` and
+    shear rate log-uniform in ``gdot_range``, each drawn per instance."""
+    name: str
+    K: int
+    n_range: tuple = (500, 20_000)
+    phi_range: tuple = (0.40, 0.58)
+    gdot_range: tuple = (1e-2, 1e2)
+    mu: float = 0.5
+    kn: float = 1e4
+    dt: float = 1e-4
+    steps: int = 5000
+    seed: int = 4
+    max_iter: int = 60
+
+
+BATCH_SPECS = {
+    "c4": BatchSpec("c4_batched_256_flow_curve", 256),
+}
+
+
+def batch_members(spec: BatchSpec):
+    """[(Spec, shear rate)] of the instances (seeded draws, no packing yet)."""
+    un = uniform(spec.seed, 10, spec.K)
+    up = uniform(spec.seed, 11, spec.K)
+    ug = uniform(spec.seed, 12, spec.K)
+    n0, n1 = spec.n_range
+    out = []
+    for k in range(spec.K):
+        n = n0 + min(int(un[k] * (n1 - n0 + 1)), n1 - n0)
+        phi = spec.phi_range[0] + up[k] * (spec.phi_range[1] - spec.phi_range[0])
+        g0, g1 = math.log(spec.gdot_range[0]), math.log(spec.gdot_range[1])
+        gdot = math.exp(g0 + ug[k] * (g1 - g0))
+        s = Spec("%s_%d" % (spec.name, k), n, phi, mu=spec.mu, kn=spec.kn, shear_rate=gdot, dt=spec.dt,
+                 steps=spec.steps, seed=spec.seed * 100_003 + k, max_iter=spec.max_iter)
+        out.append((s, gdot))
+    return out
+
+
+def _generate_member(spec: Spec):
+    os.environ["OMP_NUM_THREADS"] = "1"     # one core per worker process
+    build()
+    return generate(spec)
+
+
+def generate_batch(spec: BatchSpec, workers: int = 0) -> dict:
+    """Packs every instance (in ``workers`` spawned processes; 0: one per
+    core, up to 16) and concatenates them instance-major.  Returns dict(x
+    (3, N), a (N), ids (N, instance k holds its own index range), n (K),
+    boxes (K, 3), shear_rates (K), phi (K))."""
+    members = batch_members(spec)
+    build()
+    if workers == 0:
+        workers = min(16, os.cpu_count() or 1)
+    if workers > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(workers) as pool:
+            gs = pool.map(_generate_member, [m[0] for m in members], chunksize=1)
+    else:
+        gs = [generate(m[0]) for m in members]
+    n = np.array([g["a"].shape[0] for g in gs], dtype=np.int64)
+    off = np.concatenate([[0], np.cumsum(n)])
+    return dict(x=np.ascontiguousarray(np.concatenate([g["x"] for g in gs], axis=1)),
+                a=np.ascontiguousarray(np.concatenate([g["a"] for g in gs])),
+                ids=np.concatenate([g["ids"] + off[k] for k, g in enumerate(gs)]).astype(np.int32),
+                n=n, boxes=np.array([g["box"] for g in gs]),
+                shear_rates=np.array([m[1] for m in members]),
+                phi=np.array([m[0].phi for m in members]))
+
+
 def small(n: int, phi: float, seed: int, **kw) -> dict:
     """A small bidisperse (1 : 1.4) packing for tests."""
     return generate(replace(Spec("small", n, phi, seed=seed), **kw))
