@@ -63,18 +63,20 @@ ALG_BYTES = {
 }
 KERNELS_PER_STEP = len(ALG_BYTES)
 
-# DRAM traffic per launch from an ncu capture of the named kernel (bytes), and
-# the hash of the CUDA sources it was taken on; reported only while the
-# sources are unchanged.
-NCU_TRAFFIC = {}
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
+# an ncu capture of the kernel on the headline workload, with the sources it
+# was built from and their hash; reported only while those files are
+# unchanged (profiles/ncu_full_c2_mixed_100k.md).
+NCU_TRAFFIC = {
+    ("k_pairs", "mixed"): (30_065_920, ("dss_force.cu", "dss_internal.cuh"), "b4a8848201957cf5"),
+}
 
 
-def csrc_hash() -> str:
+def src_hash(files) -> str:
     d = os.path.join(ROOT, "paper_2108_01013_gb300", "csrc")
     h = hashlib.sha256()
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(d, f), "rb").read())
+    for f in files:
+        h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -424,8 +426,9 @@ def main():
     d = per_kernel[dom]
     peak = float(peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
     traffic = None
-    if dom in NCU_TRAFFIC and NCU_TRAFFIC[dom][1] == csrc_hash():
-        traffic = NCU_TRAFFIC[dom][0]
+    rec = NCU_TRAFFIC.get((dom, args.precision))
+    if rec is not None and src_hash(rec[1]) == rec[2]:
+        traffic = rec[0]
     roof = {"bound": "hbm", "kernel": dom, "achieved": d["gbs"], "peak": peak, "unit": "GB/s",
             "frac": d["gbs"] / peak, "traffic": traffic, "peak_source": src,
             "share": d["ms"] / max(sum(v["ms"] for v in per_kernel.values()), 1e-12)}
