@@ -60,12 +60,13 @@ class Params(ctypes.Structure):
                 ("mu", c_double), ("eta0", c_double), ("rho", c_double),
                 ("delta_lub", c_double), ("lub_eps", c_double), ("a0", c_double),
                 ("lub_cutoff_mode", c_int32), ("pad_", c_int32),
-                ("shear_rate", c_double), ("dt", c_double), ("L", c_double * 3)]
+                ("shear_rate", c_double), ("dt", c_double), ("L", c_double * 3),
+                ("lub_taper", c_double)]
 
 
 def make_params(box, kn=1e4, kt=None, gamma_n=None, mu=0.5, eta0=1.0, rho=1.0,
                 delta_lub=0.05, lub_eps=1e-3, a0=1.0, lub_cutoff_mode=0,
-                shear_rate=1.0, dt=1e-4) -> Params:
+                shear_rate=1.0, dt=1e-4, lub_taper=0.0) -> Params:
     """Oracle parameters; kt defaults to kn/2 and gamma_n to 1e-7 kn/gdot."""
     if kt is None:
         kt = 0.5 * kn
@@ -76,6 +77,7 @@ def make_params(box, kn=1e4, kt=None, gamma_n=None, mu=0.5, eta0=1.0, rho=1.0,
     p.eta0, p.rho, p.delta_lub, p.lub_eps, p.a0 = eta0, rho, delta_lub, lub_eps, a0
     p.lub_cutoff_mode = lub_cutoff_mode
     p.shear_rate, p.dt = shear_rate, dt
+    p.lub_taper = lub_taper
     for k in range(3):
         p.L[k] = float(box[k])
     return p

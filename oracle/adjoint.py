@@ -1,0 +1,344 @@
+"""Reverse-mode derivatives of a rollout, CPU FP64 (oracle of the adjoint).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/`` may import this module.  It shares
+no code with the CUDA path.
+
+The rollout is restated with plain PyTorch CPU float64 tensor operations,
+following oracle.c step for step: the brute-force pair set (taken from the C
+oracle; it is discrete and carries no derivative), the stick-and-slide
+contact of Eq. 4-5, the lubrication blocks of Eq. A2/A3 with the g functions
+of Eq. A7 (6 pi eta0 prefactor) and the optional taper of the cutoff, the
+Stokes drag of Eq. A1, the modified velocity-Verlet step of Eq. 15 in the
+Lees-Edwards box of Eq. 16, and the bulk stress of Eq. 8.  The objective is a
+weighted sum of the stress over the steps,
+
+    J = sum_{n=1..T} sum_q W[n-1, q] sigma^n_q      (sigma row major 3x3),
+
+so W[n-1] = e_xy / (T eta0 gdot) gives the time-averaged relative viscosity.
+Derivatives come from torch.autograd (a library primitive).  Branch decisions
+(pair set, contact, Coulomb slip, gap clamp, taper ends, box wraps) are taken
+on the values and held fixed, so these are the derivatives of the branch
+taken (pathwise derivatives).
+
+Parity status: the forward rollout is pinned to oracle.c (same trajectory and
+stress series); the gradient is pinned to central finite differences of
+oracle.c with the event set checked unchanged (tests/test_oracle_adjoint.py).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import torch
+
+from . import make_params, pairs_bruteforce
+
+TD = torch.float64
+
+
+def _gfun(name, al, ai, aj):
+    """g coefficients of Eq. A7 (lengths only), numpy, per pair."""
+    s = ai + aj
+    if name == "XA_ii":
+        return 2.0 * ai * al * al / (1.0 + al) ** 3
+    if name == "XA_ij":
+        return -2.0 * s * al * al / (1.0 + al) ** 4
+    if name == "YA_ii":
+        return 4.0 * ai / 15.0 * al * (2.0 + al + 2.0 * al * al) / (1.0 + al) ** 3
+    if name == "YA_ij":
+        return -4.0 * s / 15.0 * al * (2.0 + al + 2.0 * al * al) / (1.0 + al) ** 4
+    if name == "YB_ii":
+        return -2.0 * ai * ai / 15.0 * al * (4.0 + al) / (1.0 + al) ** 2
+    if name == "YB_ij":
+        return 2.0 * s ** 2 / 15.0 * al * (4.0 + al) / (1.0 + al) ** 4
+    if name == "YC_ii":
+        return 8.0 * ai ** 3 / 15.0 * al / (1.0 + al)
+    if name == "YC_ij":
+        return 2.0 * s ** 3 / 15.0 * al * al / (1.0 + al) ** 4
+    if name == "XG_ii":
+        return 2.0 * ai * ai * al * al / (1.0 + al) ** 3
+    if name == "XG_ij":
+        return -2.0 * s ** 2 * al * al / (1.0 + al) ** 5
+    if name == "YG_ii":
+        return ai * ai / 15.0 * al * (4.0 - al + 7.0 * al * al) / (1.0 + al) ** 3
+    if name == "YG_ij":
+        return -s ** 2 / 15.0 * al * (4.0 - al + 7.0 * al * al) / (1.0 + al) ** 5
+    if name == "YH_ii":
+        return 2.0 * ai ** 3 / 15.0 * al * (2.0 - al) / (1.0 + al) ** 2
+    if name == "YH_ij":
+        return s ** 3 / 15.0 * al * al * (1.0 + 7.0 * al) / (1.0 + al) ** 5
+    raise KeyError(name)
+
+
+def _coefficients(ai, aj):
+    """Radius-only factors of every block (the X or Y factor is applied
+    later): the ii, jj, ij, ji entries of Eq. A7 for each pair."""
+    al = aj / ai
+    ial = 1.0 / al
+    c = {}
+    for blk, jjf, jif in (("XA", al, 1.0), ("YA", al, 1.0), ("YB", -al * al, -1.0),
+                          ("YC", al ** 3, 1.0), ("XG", -al * al, -1.0), ("YG", -al * al, -1.0),
+                          ("YH", al ** 3, 1.0)):
+        c[blk + "_ii"] = _gfun(blk + "_ii", al, ai, aj)
+        c[blk + "_jj"] = jjf * _gfun(blk + "_ii", ial, ai, aj)
+        c[blk + "_ij"] = _gfun(blk + "_ij", al, ai, aj)
+        c[blk + "_ji"] = jif * _gfun(blk + "_ij", ial, ai, aj)
+    return {k: torch.as_tensor(v, dtype=TD) for k, v in c.items()}
+
+
+def _dot(a, b):
+    return (a * b).sum(-1, keepdim=True)
+
+
+def _cross(a, b):
+    return torch.stack([a[:, 1] * b[:, 2] - a[:, 2] * b[:, 1],
+                        a[:, 2] * b[:, 0] - a[:, 0] * b[:, 2],
+                        a[:, 0] * b[:, 1] - a[:, 1] * b[:, 0]], dim=1)
+
+
+class Model:
+    """Fixed settings of a differentiable rollout (everything except the
+    differentiated inputs)."""
+
+    def __init__(self, box, a, *, eta0=1.0, rho=1.0, lub_eps=1e-3, a0=1.0, lub_cutoff_mode=0,
+                 shear_rate=1.0, dt=1e-4, lub_taper=0.0, nstep0=0):
+        self.box = np.asarray(box, dtype=np.float64)
+        self.a = np.asarray(a, dtype=np.float64)
+        self.n = self.a.shape[0]
+        self.eta0, self.rho, self.eps, self.a0 = eta0, rho, lub_eps, a0
+        self.mode, self.gdot, self.dt, self.taper = lub_cutoff_mode, shear_rate, dt, lub_taper
+        self.nstep0 = nstep0
+        at = torch.as_tensor(self.a, dtype=TD)
+        self.at = at
+        self.mass = 4.0 / 3.0 * math.pi * rho * at ** 3
+        self.inertia = 0.4 * self.mass * at ** 2
+        self.k6 = 6.0 * math.pi * eta0
+        self.k8 = 8.0 * math.pi * eta0
+
+    def offset(self, nstep):
+        t = float(nstep) * self.dt
+        return math.fmod(self.gdot * self.box[1] * t, self.box[0])
+
+    # -- one force evaluation ------------------------------------------------
+    def forces(self, x, u, w, th, hist, nstep):
+        """Forces, torques, stress and the new history at time nstep*dt.
+        x, u, w: (3, n) tensors; th: dict of scalar tensors kn, kt, gn, mu,
+        delta; hist: (keys ndarray sorted, xi (k, 3) tensor) in lo -> hi
+        orientation.  Returns F, T (3, n), sigma (9,), new hist, counts."""
+        n, L, gd = self.n, self.box, self.gdot
+        off = self.offset(nstep)
+        p = make_params(L, kn=th["kn"].item(), kt=th["kt"].item(), gamma_n=th["gn"].item(),
+                        mu=th["mu"].item(), eta0=self.eta0, rho=self.rho,
+                        delta_lub=th["delta"].item(), lub_eps=self.eps, a0=self.a0,
+                        lub_cutoff_mode=self.mode, shear_rate=gd, dt=self.dt, lub_taper=self.taper)
+        xn = x.detach().numpy()
+        pr = pairs_bruteforce(xn, self.a, np.arange(n, dtype=np.int32), p, off)
+        i = torch.as_tensor(pr[:, 0])
+        j = torch.as_tensor(pr[:, 1])
+        P = pr.shape[0]
+        # minimum image, Eq. 16 (shifts decided on the values)
+        dx = x[0, j] - x[0, i]
+        dy = x[1, j] - x[1, i]
+        dz = x[2, j] - x[2, i]
+        dyv = dy.detach().numpy()
+        sy = np.where(dyv > 0.5 * L[1], -1, np.where(dyv < -0.5 * L[1], 1, 0))
+        syt = torch.as_tensor(sy, dtype=TD)
+        dy = dy + syt * L[1]
+        dx = dx + syt * off
+        dx = dx - L[0] * torch.as_tensor(np.rint(dx.detach().numpy() / L[0]), dtype=TD)
+        dz = dz - L[2] * torch.as_tensor(np.rint(dz.detach().numpy() / L[2]), dtype=TD)
+        r = torch.stack([dx, dy, dz], dim=1)
+        ai = torch.as_tensor(self.a[pr[:, 0]], dtype=TD)
+        aj = torch.as_tensor(self.a[pr[:, 1]], dtype=TD)
+        S = ai + aj
+        dist = torch.sqrt((r * r).sum(1))
+        nv = r / dist[:, None]
+        d = dist - S
+        ui, uj = u[:, i].T, u[:, j].T
+        wi, wj = w[:, i].T, w[:, j].T
+        ujm = uj + torch.stack([syt * gd * L[1], torch.zeros_like(syt), torch.zeros_like(syt)], 1)
+        yjm = x[1, j] + syt * L[1]
+        # ---- contact, Eq. 4-5
+        cmask = (d.detach() < 0.0)
+        keys = (pr[:, 0].astype(np.int64) << 32) | pr[:, 1].astype(np.int64)
+        hk, hxi = hist
+        xo = torch.zeros((P, 3), dtype=TD)
+        if len(hk):
+            pos = np.searchsorted(hk, keys)
+            pos = np.minimum(pos, len(hk) - 1)
+            found = (hk[pos] == keys) if len(hk) else np.zeros(P, bool)
+            if found.any():
+                idx = torch.as_tensor(np.nonzero(found)[0])
+                xo = xo.index_copy(0, idx, hxi[torch.as_tensor(pos[found])])
+        du = ujm - ui
+        un = _dot(nv, du) * nv
+        Fnor = th["kn"] * d[:, None] * nv + th["gn"] * un
+        aw = ai[:, None] * wi + aj[:, None] * wj
+        rel = du - _cross(aw, nv)
+        ut = rel - _dot(nv, rel) * nv
+        xp = xo - _dot(nv, xo) * nv
+        xs = xp + ut * self.dt
+        cap = th["mu"] * torch.sqrt((Fnor * Fnor).sum(1)) / th["kt"]
+        xm = torch.sqrt((xs * xs).sum(1))
+        slip = (xm.detach() > cap.detach()) & cmask
+        scale = torch.where(slip, cap / torch.where(slip, xm, torch.ones_like(xm)), torch.ones_like(xm))
+        xs = xs * scale[:, None]
+        Ftan = th["kt"] * xs
+        cm = cmask.to(TD)[:, None]
+        Fc = (Fnor + Ftan) * cm
+        nxf = _cross(nv, Ftan)
+        Tci = ai[:, None] * nxf * cm
+        Tcj = aj[:, None] * nxf * cm
+        xinew = xs * cm
+        # ---- lubrication, App. A (block form of Eq. A2/A3)
+        ds = 2.0 * d / S
+        ds = torch.where(ds.detach() < 0.0, torch.zeros_like(ds), ds)
+        X = 1.0 / (ds + self.eps)
+        Y = torch.log(1.0 / (ds + self.eps))
+        c = _coefficients(ai.numpy(), aj.numpy())
+        XY = {"XA": X, "YA": Y, "YB": Y, "YC": Y, "XG": X, "YG": Y, "YH": Y}
+        cc = {k: (XY[k[:2]] * v)[:, None] for k, v in c.items()}
+        Vi = ui - torch.stack([gd * x[1, i], torch.zeros(P, dtype=TD), torch.zeros(P, dtype=TD)], 1)
+        Vj = ujm - torch.stack([gd * yjm, torch.zeros(P, dtype=TD), torch.zeros(P, dtype=TD)], 1)
+        Om = torch.tensor([0.0, 0.0, -0.5 * gd], dtype=TD)
+        Wi = wi - Om
+        Wj = wj - Om
+
+        def N(v):
+            return _dot(nv, v) * nv
+
+        def T(v):
+            return v - _dot(nv, v) * nv
+
+        nxWi, nxWj = _cross(nv, Wi), _cross(nv, Wj)
+        nxVi, nxVj = _cross(nv, Vi), _cross(nv, Vj)
+        E = torch.zeros((3, 3), dtype=TD)
+        E[0, 1] = E[1, 0] = 0.5 * gd
+        En = nv @ E.T
+        EnT = nv @ E
+        Enn = _dot(nv, En)
+        Pq = Enn - (E[0, 0] + E[1, 1] + E[2, 2]) / 3.0
+        Qn = 2.0 * En - 2.0 * Enn * nv
+        nperp = _cross(nv, En + EnT)
+        fi = (cc["XA_ii"] * N(Vi) + cc["YA_ii"] * T(Vi) + cc["XA_ij"] * N(Vj) + cc["YA_ij"] * T(Vj)
+              + cc["YB_ii"] * nxWi + cc["YB_ji"] * nxWj)
+        fj = (cc["XA_ji"] * N(Vi) + cc["YA_ji"] * T(Vi) + cc["XA_jj"] * N(Vj) + cc["YA_jj"] * T(Vj)
+              + cc["YB_ij"] * nxWi + cc["YB_jj"] * nxWj)
+        ti = -cc["YB_ii"] * nxVi - cc["YB_ij"] * nxVj + cc["YC_ii"] * T(Wi) + cc["YC_ij"] * T(Wj)
+        tj = -cc["YB_ji"] * nxVi - cc["YB_jj"] * nxVj + cc["YC_ji"] * T(Wi) + cc["YC_jj"] * T(Wj)
+        gi = (cc["XG_ii"] * Pq * nv + cc["YG_ii"] * Qn) + (cc["XG_ji"] * Pq * nv + cc["YG_ji"] * Qn)
+        gj = (cc["XG_ij"] * Pq * nv + cc["YG_ij"] * Qn) + (cc["XG_jj"] * Pq * nv + cc["YG_jj"] * Qn)
+        hi = cc["YH_ii"] * nperp + cc["YH_ji"] * nperp
+        hj = cc["YH_ij"] * nperp + cc["YH_jj"] * nperp
+        k = self.k6
+        Fli, Flj = -k * fi + k * gi, -k * fj + k * gj
+        Tli, Tlj = -k * ti + k * hi, -k * tj + k * hj
+        if self.taper > 0.0:
+            dl = th["delta"] * self.a0 if self.mode == 1 else th["delta"] * 0.5 * S
+            t = (dl - d) / (self.taper * dl)
+            tv = t.detach()
+            s = torch.where(tv >= 1.0, torch.ones_like(t),
+                            torch.where(tv <= 0.0, torch.zeros_like(t), t * t * (3.0 - 2.0 * t)))
+            Fli, Flj, Tli, Tlj = (s[:, None] * v for v in (Fli, Flj, Tli, Tlj))
+        Fi = Fc + Fli
+        Fj = -Fc + Flj
+        Ti = Tci + Tli
+        Tj = Tcj + Tlj
+        F = torch.zeros((n, 3), dtype=TD).index_add(0, i, Fi).index_add(0, j, Fj)
+        Tq = torch.zeros((n, 3), dtype=TD).index_add(0, i, Ti).index_add(0, j, Tj)
+        # Stokes drag, Eq. A1
+        V = torch.stack([u[0] - gd * x[1], u[1], u[2]], 1)
+        F = F - self.k6 * self.at[:, None] * V
+        Tq = Tq - self.k8 * (self.at ** 3)[:, None] * (w.T - Om)
+        # stress, Eq. 8 and 9
+        Sp = (r[:, :, None] * Fc[:, None, :] + 0.5 * (r[:, :, None] * Fli[:, None, :]
+                                                     + Fli[:, :, None] * r[:, None, :])).sum(0)
+        Vol = float(L[0] * L[1] * L[2])
+        sumA3 = float((self.a ** 3).sum())
+        sigma = (2.0 * self.eta0 * E + (20.0 / 3.0 * math.pi * self.eta0 * sumA3 * E + Sp) / Vol).reshape(9)
+        # new history: the pairs in contact, sorted by key (ids are indices, lo = i)
+        cm_np = cmask.numpy()
+        nk = keys[cm_np]
+        order = np.argsort(nk, kind="stable")
+        new_hist = (nk[order], xinew[torch.as_tensor(np.nonzero(cm_np)[0][order])])
+        # event signature: pair count, contact count, slip count, and the
+        # identities of the contacts, slips and pairs in the taper band
+        band = np.zeros(P, bool)
+        if self.taper > 0.0:
+            dlv = (th["delta"].item() * (self.a0 if self.mode == 1 else 0.5 * S.numpy()))
+            band = (d.detach().numpy() > (1.0 - self.taper) * dlv)
+        sl = slip.numpy()
+        ev = (P, int(cm_np.sum()), int(sl.sum()), hash(keys[cm_np].tobytes()),
+              hash(keys[sl].tobytes()), hash(keys[band].tobytes()), hash(keys.tobytes()))
+        return F.T, Tq.T, sigma, new_hist, ev
+
+    # -- the rollout -----------------------------------------------------------
+    def rollout(self, x0, u0, w0, th, nsteps, weights=None):
+        """J and the stress series of nsteps steps from (x0, u0, w0) with the
+        initial accelerations from one force evaluation (empty history).
+        Returns (J, sigma list, event counts per step, final state dict)."""
+        dt, L, gd = self.dt, self.box, self.gdot
+        nstep = self.nstep0
+        F, Tq, _, _, ev0 = self.forces(x0, u0, w0, th, (np.zeros(0, np.int64), None), nstep)
+        al = F / self.mass
+        aw = Tq / self.inertia
+        x, u, w = x0, u0, w0
+        hist = (np.zeros(0, np.int64), None)
+        J = torch.zeros((), dtype=TD)
+        sig, events = [], [ev0]
+        for k in range(nsteps):
+            nstep += 1
+            off = self.offset(nstep)
+            x = x + dt * u + 0.5 * dt * dt * al
+            u = u + 0.5 * dt * al
+            w = w + 0.5 * dt * aw
+            # Lees-Edwards wrap, Eq. 16 (decisions on the values)
+            xv = x.detach().numpy()
+            up = xv[1] >= L[1]
+            dn = xv[1] < 0.0
+            cross = np.where(up, -1.0, np.where(dn, 1.0, 0.0))
+            ct = torch.as_tensor(cross, dtype=TD)
+            ny = x[1] + ct * L[1]
+            nx = x[0] + ct * off
+            # x into [0, L_x), z into [0, L_z): fmod then the corrections
+            nxv = nx.detach().numpy()
+            q = np.fmod(nxv, L[0]) - nxv
+            q = q + np.where(nxv + q < 0.0, L[0], 0.0)
+            q = q - np.where(nxv + q >= L[0], L[0], 0.0)
+            nx = nx + torch.as_tensor(q, dtype=TD)
+            nz = x[2]
+            zv = nz.detach().numpy()
+            nz = nz + torch.as_tensor(np.where(zv >= L[2], -L[2], np.where(zv < 0.0, L[2], 0.0)), dtype=TD)
+            x = torch.stack([nx, ny, nz])
+            u = torch.stack([u[0] + ct * gd * L[1], u[1], u[2]])
+            F, Tq, s, hist, ev = self.forces(x, u, w, th, hist, nstep)
+            al = F / self.mass
+            aw = Tq / self.inertia
+            u = u + 0.5 * dt * al
+            w = w + 0.5 * dt * aw
+            sig.append(s)
+            events.append(ev)
+            if weights is not None:
+                J = J + (torch.as_tensor(weights[k], dtype=TD) * s).sum()
+        return J, sig, events, dict(x=x, u=u, w=w, al=al, aw=aw)
+
+
+def gradients(box, x0, a, u0, w0, nsteps, weights, *, kn=1e4, kt=None, gamma_n=None, mu=0.5,
+              delta_lub=0.05, **kw):
+    """J and dJ/d{x0, u0, w0, kn, kt, gamma_n, mu, delta_lub} (pathwise)."""
+    gd = kw.get("shear_rate", 1.0)
+    kt = 0.5 * kn if kt is None else kt
+    gamma_n = 1e-7 * kn / gd if gamma_n is None else gamma_n
+    m = Model(box, a, **kw)
+    xs = torch.tensor(np.asarray(x0, dtype=np.float64), requires_grad=True)
+    us = torch.tensor(np.asarray(u0, dtype=np.float64), requires_grad=True)
+    ws = torch.tensor(np.asarray(w0, dtype=np.float64), requires_grad=True)
+    th = {k: torch.tensor(float(v), dtype=TD, requires_grad=True)
+          for k, v in (("kn", kn), ("kt", kt), ("gn", gamma_n), ("mu", mu), ("delta", delta_lub))}
+    J, sig, events, fin = m.rollout(xs, us, ws, th, nsteps, weights)
+    gx, gu, gw, *gp = torch.autograd.grad(J, [xs, us, ws] + [th[k] for k in ("kn", "kt", "gn", "mu", "delta")],
+                                          allow_unused=True)
+    gp = [0.0 if g is None else float(g) for g in gp]
+    return dict(J=J.item(), x0=gx.numpy(), u0=gu.numpy(), w0=gw.numpy(),
+                params=np.array(gp), sigma=np.array([s.detach().numpy() for s in sig]),
+                events=events, final={k: v.detach().numpy() for k, v in fin.items()})

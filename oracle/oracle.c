@@ -35,7 +35,12 @@
  *    stored for the (lower id -> higher id) orientation;
  *  - u^{n+1} = u^{n+1/2} + dt/2 alpha^{n+1}, algebraically Eq. 15d, so that a
  *    Lees-Edwards velocity jump applied to u^{n+1/2} carries over;
- *  - each pair's stresslet is counted once in Eq. 8.
+ *  - each pair's stresslet is counted once in Eq. 8;
+ *  - optional lubrication taper (an extension for differentiation, not in
+ *    the paper): with w = lub_taper > 0 the lubrication force, torques and
+ *    stresslet of a listed pair are scaled by s = t^2 (3 - 2t),
+ *    t = clamp((delta_ij - d) / (w delta_ij), 0, 1), so that they fall to
+ *    zero continuously at the cutoff; w = 0 is the hard cutoff.
  */
 #include <math.h>
 #include <stdint.h>
@@ -55,6 +60,7 @@ typedef struct orc_params {
   int32_t pad_;
   double shear_rate, dt;        /* gdot, time step */
   double L[3];                  /* box edges */
+  double lub_taper;             /* w of the lubrication taper; 0: hard cutoff */
 } orc_params;
 
 typedef struct orc_sys {
@@ -395,6 +401,16 @@ void orc_lubrication(const orc_params *p, const double r[3], double ai, double a
   }
 }
 
+/* Lubrication taper factor of a listed pair at gap d (1 for w = 0). */
+static double lub_taper_factor(const orc_params *p, double d, double ai, double aj) {
+  if (!(p->lub_taper > 0.0)) return 1.0;
+  double dl = pair_delta(p, ai, aj);
+  double t = (dl - d) / (p->lub_taper * dl);
+  if (t >= 1.0) return 1.0;
+  if (t <= 0.0) return 0.0;
+  return t * t * (3.0 - 2.0 * t);
+}
+
 /* ------------------------------------------------------------------------ */
 /* One pair, everything: contact (if overlapping) + lubrication + stresslet  */
 /* ------------------------------------------------------------------------ */
@@ -434,6 +450,10 @@ int orc_pair_eval(const orc_params *p, double off, const double xi[3], const dou
   double Wj[3] = {wj[0] - Om[0], wj[1] - Om[1], wj[2] - Om[2]};
   double Fli[3], Flj[3], Tli[3], Tlj[3];
   orc_lubrication(p, r, ai, aj, Vi, Vj, Wi, Wj, Fli, Flj, Tli, Tlj);
+  double tap = lub_taper_factor(p, d, ai, aj);
+  for (int q = 0; q < 3; ++q) {
+    Fli[q] *= tap; Flj[q] *= tap; Tli[q] *= tap; Tlj[q] *= tap;
+  }
   for (int q = 0; q < 3; ++q) {
     Fi[q] = Fc[q] + Fli[q];
     Fj[q] = -Fc[q] + Flj[q];
