@@ -75,6 +75,10 @@ typedef struct dss_params {
   double cell_size;             /* 0: smallest size >= largest interaction range */
   int32_t capacity_M;           /* half-list capacity per particle; 0: Sec. II A estimate */
   int32_t pair_capacity;        /* mean half-list pairs per particle to allocate for; 0: 16 */
+  double lub_taper;             /* w in [0, 1): lubrication scaled by s = t^2 (3 - 2t),
+                                   t = clamp((delta_ij - d) / (w delta_ij), 0, 1), so it
+                                   vanishes continuously at the cutoff (an extension for
+                                   differentiation, not in the paper); 0: hard cutoff */
 } dss_params;
 
 typedef struct dss_handle dss_handle;
@@ -251,6 +255,33 @@ int dss_load(dss_handle *h, const void *buf, size_t len);
  * dss_load), so the trials leave no trace in the trajectory.  ncand <= 16. */
 int dss_autotune(dss_handle *h, int32_t trial_steps, int32_t ncand, const double *factors,
                  double *ms_per_step, double *cell_size);
+
+/* Gradient of a stress functional of a rollout (reverse mode).  Runs nsteps
+ * steps from the current state (as dss_step would), with
+ *     J = sum_{n=1..nsteps} sum_q weights[(n-1)*9 + q] * sigma^n_q
+ * (sigma^n: the bulk stress of Eq. 8 after step n, row major; weights are
+ * host or device memory, [nsteps][9]; e.g. e_xy / (nsteps eta0 gdot) gives
+ * the time-averaged relative viscosity), and returns J and its derivatives
+ * with respect to the model constants, dJ_dparams[5] = (k_n, k_t, gamma_n,
+ * mu, delta_lub) (partials: a caller tying k_t = k_n/2 adds them up), and to
+ * the initial state in id order: positions, velocities, angular velocities
+ * (3n each) and, unless initial_forces, the initial accelerations.  With
+ * initial_forces != 0 the initial accelerations are taken to be those of a
+ * force evaluation at the initial state with an empty contact history (what
+ * dss_set_state computes when given none), and their dependence is folded
+ * into the other derivatives (dJ_dalpha0/beta0 then return zero).
+ * The forward keeps a checkpoint (dss_save) every ckpt_every steps; the
+ * reverse sweep replays one segment at a time, taping each step, and walks it
+ * backwards: memory is one segment of tapes plus the checkpoints.
+ * Derivatives are pathwise: the pair set, contacts, Coulomb slips and the
+ * taper ends of each step are those of the forward run and held fixed; with
+ * the hard cutoff (lub_taper = 0) J has no pathwise dependence on delta_lub.
+ * Single-instance handles only (DSS_ERR_ARG for a batch).  The handle is left
+ * in the state after the rollout.  Output pointers are host or device
+ * memory and may be NULL.  Synchronises the stream. */
+int dss_adjoint(dss_handle *h, int64_t nsteps, int32_t ckpt_every, const double *weights,
+                int32_t initial_forces, double *J, double *dJ_dparams, double *dJ_dx0,
+                double *dJ_du0, double *dJ_dw0, double *dJ_dalpha0, double *dJ_dbeta0);
 
 /* Bytes of device memory the handle holds. */
 int64_t dss_device_bytes(const dss_handle *h);

@@ -7,3 +7,4 @@ offers ``Suspension`` on top.  ``synth`` makes seeded synthetic inputs.
 """
 from ._native import build, load, DssError, FP64, MIXED, Params  # noqa: F401
 from .suspension import Batch, Suspension, default_params, capacity_estimate  # noqa: F401
+from .adjoint import rollout_stress, viscosity_weights  # noqa: F401

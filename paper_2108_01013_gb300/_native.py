@@ -18,7 +18,8 @@ _CSRC = os.path.join(_HERE, "csrc")
 _BUILD = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(_BUILD, "libdss.so")
 INCLUDE = os.path.join(os.path.dirname(_HERE), "include")
-SOURCES = ["dss_sort.cu", "dss_neighbour.cu", "dss_force.cu", "dss_api.cu", "dss_noalloc.cu"]
+SOURCES = ["dss_sort.cu", "dss_neighbour.cu", "dss_force.cu", "dss_api.cu", "dss_noalloc.cu",
+           "dss_adjoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v"]
 
@@ -72,7 +73,8 @@ class Params(Structure):
                 ("eta0", c_double), ("rho", c_double), ("delta_lub", c_double),
                 ("lub_eps", c_double), ("a0", c_double), ("lub_cutoff_mode", c_int32),
                 ("precision", c_int32), ("shear_rate", c_double), ("dt", c_double),
-                ("cell_size", c_double), ("capacity_M", c_int32), ("pair_capacity", c_int32)]
+                ("cell_size", c_double), ("capacity_M", c_int32), ("pair_capacity", c_int32),
+                ("lub_taper", c_double)]
 
 
 class Counters(Structure):
@@ -102,6 +104,7 @@ SIGNATURES = {
     "dss_save": (c_int, [c_void_p, _vp, POINTER(c_size_t)]),
     "dss_load": (c_int, [c_void_p, _vp, c_size_t]),
     "dss_autotune": (c_int, [c_void_p, c_int32, c_int32, _dp, _dp, _dp]),
+    "dss_adjoint": (c_int, [c_void_p, c_int64, c_int32, _vp, c_int32, _dp, _dp, _vp, _vp, _vp, _vp, _vp]),
     "dss_set_state": (c_int, [c_void_p, _vp, _vp, _vp, _vp, _vp, _vp, _vp, c_int64]),
     "dss_get_state": (c_int, [c_void_p, _vp, _vp, _vp, _vp, _vp]),
     "dss_set_history": (c_int, [c_void_p, c_int64, _vp, _vp]),

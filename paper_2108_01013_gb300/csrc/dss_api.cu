@@ -382,7 +382,8 @@ bool valid_params(const dss_params* p) {
   return (p->kn >= 0) && (p->kt > 0) && (p->gamma_n >= 0) && (p->mu >= 0) && (p->eta0 >= 0) &&
          (p->rho > 0) && (p->delta_lub >= 0) && (p->lub_eps > 0) && (p->a0 > 0) && (p->dt > 0) &&
          std::isfinite(p->shear_rate) && (p->lub_cutoff_mode == 0 || p->lub_cutoff_mode == 1) &&
-         (p->precision == DSS_FP64 || p->precision == DSS_MIXED);
+         (p->precision == DSS_FP64 || p->precision == DSS_MIXED) &&
+         (p->lub_taper >= 0.0 && p->lub_taper < 1.0);
 }
 
 // Common constructor: K instances of n[k] particles in boxes box[3k..3k+2]
@@ -453,6 +454,10 @@ int create_handle(dss_handle** out, const dss_params* p, int K, const int64_t* n
   g.f.k6 = (float)g.k6;
   g.f.k8 = (float)g.k8;
   g.f.mass_c = (float)(4.0 / 3.0 * DSS_PI * p->rho);
+  g.taper = p->lub_taper;
+  g.f.taper = (float)p->lub_taper;
+  g.f.delta = (float)p->delta_lub;
+  g.f.delta_a0 = (float)(p->delta_lub * p->a0);
   *out = h;
   return DSS_OK;
 }
@@ -1010,7 +1015,7 @@ uint64_t config_hash(const dss_handle* h) {
   v = fnv1a(v, h->inst_gdot, sizeof(double) * h->K);
   v = fnv1a(v, h->inst_gn, sizeof(double) * h->K);
   const dss_params& p = h->p;
-  const double c[9] = {p.kn, p.kt, p.mu, p.eta0, p.rho, p.delta_lub, p.lub_eps, p.a0, p.dt};
+  const double c[10] = {p.kn, p.kt, p.mu, p.eta0, p.rho, p.delta_lub, p.lub_eps, p.a0, p.dt, p.lub_taper};
   v = fnv1a(v, c, sizeof(c));
   const int32_t m[2] = {p.lub_cutoff_mode, p.precision};
   v = fnv1a(v, m, sizeof(m));
@@ -1175,11 +1180,102 @@ int dss_autotune(dss_handle* h, int32_t trial_steps, int32_t ncand, const double
   return best < INFINITY ? DSS_OK : DSS_ERR_BOX;
 }
 
+// ------------------------------------------------------------------------
+// Adjoint of a rollout: forward with a checkpoint every ckpt_every steps,
+// then per segment (last first) a taped replay and the reverse sweep.
+// ------------------------------------------------------------------------
+int dss_adjoint(dss_handle* h, int64_t nsteps, int32_t ckpt_every, const double* weights,
+                int32_t initial_forces, double* J, double* dJ_dparams, double* dJ_dx0,
+                double* dJ_du0, double* dJ_dw0, double* dJ_dalpha0, double* dJ_dbeta0) {
+  if (!h || nsteps < 1 || ckpt_every < 1 || !weights) return DSS_ERR_ARG;
+  if (h->K != 1) return DSS_ERR_ARG;
+  if (!h->have_state) return DSS_ERR_STATE;
+  ENTER(h);
+  const int64_t nseg = (nsteps + ckpt_every - 1) / ckpt_every;
+  std::vector<std::vector<char>> ck((size_t)nseg);
+  int r;
+  auto save_to = [&](std::vector<char>& buf) -> int {
+    size_t len = 0;
+    int e = dss_save(h, nullptr, &len);
+    if (e) return e;
+    buf.resize(len);
+    return dss_save(h, buf.data(), &len);
+  };
+  // ---- forward, with checkpoints and the objective
+  std::vector<double> Wh(9 * (size_t)nsteps);
+  CK(cudaMemcpy(Wh.data(), weights, sizeof(double) * 9 * nsteps, cudaMemcpyDefault));
+  const bool from_forces = initial_forces != 0;
+  std::vector<double> Jsig(9);
+  double Jacc = 0.0;
+  for (int64_t s = 0; s < nseg; ++s) {
+    if ((r = save_to(ck[(size_t)s]))) return r;
+    const int64_t k1 = std::min<int64_t>(ckpt_every, nsteps - s * ckpt_every);
+    for (int64_t k = 0; k < k1; ++k) {
+      if ((r = dss_step(h, 1))) return r;
+      CK(cudaMemcpyAsync(Jsig.data(), h->sigma, 9 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+      const int64_t n1 = s * ckpt_every + k;
+      for (int q = 0; q < 9; ++q) Jacc += Wh[9 * n1 + q] * Jsig[q];
+    }
+  }
+  std::vector<char> ck_end;
+  if ((r = save_to(ck_end))) return r;
+  // ---- reverse
+  const int slots = (int)std::min<int64_t>(ckpt_every, nsteps);
+  if ((r = adj_alloc(h, slots, nsteps))) return r;
+  if ((r = adj_upload_weights(h, Wh.data(), nsteps))) return r;
+  adj_zero(h);
+  for (int64_t s = nseg - 1; s >= 0; --s) {
+    if ((r = dss_load(h, ck[(size_t)s].data(), ck[(size_t)s].size()))) return r;
+    const int64_t k1 = std::min<int64_t>(ckpt_every, nsteps - s * ckpt_every);
+    // taped replay (the same kernels as dss_step, without the graph)
+    for (int64_t k = 0; k < k1; ++k) {
+      const int w = 1 - h->cur;
+      launch_sort(h, true, h->cur, w);
+      launch_enumerate(h, w, 1 - h->hist, 1);
+      adj_tape(h, (int)k, w, 1 - h->hist, h->hist, false);
+      launch_forces(h, w, 1 - h->hist, h->hist, 1, G_STEP, nullptr, nullptr);
+      h->cur = w;
+      h->hist = 1 - h->hist;
+      h->last_list = h->hist;
+    }
+    CK(cudaGetLastError());
+    if ((r = sync_status(h))) return r;
+    if ((r = status_error(h))) { clear_err(h); return r; }
+    for (int64_t k = k1 - 1; k >= 0; --k) adj_reverse(h, (int)k, s * ckpt_every + k, false);
+    CK(cudaGetLastError());
+  }
+  if (from_forces) {
+    // alpha^0 came from a force evaluation at the initial state with an
+    // empty history: its reverse adds the dependence through alpha^0
+    if ((r = dss_load(h, ck[0].data(), ck[0].size()))) return r;
+    adj_tape(h, 0, h->cur, h->hist, h->hist, true);
+    CK(cudaStreamSynchronize(h->stream));   // the tape's pair count is read on the host
+    adj_reverse(h, 0, 0, true);
+  }
+  CK(cudaGetLastError());
+  if ((r = sync_status(h))) return r;
+  if ((r = status_error(h))) { clear_err(h); return r; }
+  // outputs, then back to the state after the rollout
+  AdjBuf* A = h->adj;
+  const size_t b3 = sizeof(double) * 3 * (size_t)h->n;
+  if (dJ_dx0) CK(cudaMemcpyAsync(dJ_dx0, A->xb, b3, cudaMemcpyDefault, h->stream));
+  if (dJ_du0) CK(cudaMemcpyAsync(dJ_du0, A->ub, b3, cudaMemcpyDefault, h->stream));
+  if (dJ_dw0) CK(cudaMemcpyAsync(dJ_dw0, A->wb, b3, cudaMemcpyDefault, h->stream));
+  if (dJ_dalpha0) CK(cudaMemcpyAsync(dJ_dalpha0, A->ab, b3, cudaMemcpyDefault, h->stream));
+  if (dJ_dbeta0) CK(cudaMemcpyAsync(dJ_dbeta0, A->bb, b3, cudaMemcpyDefault, h->stream));
+  if (dJ_dparams) CK(cudaMemcpyAsync(dJ_dparams, A->thb, 5 * sizeof(double), cudaMemcpyDefault, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (J) *J = Jacc;
+  return dss_load(h, ck_end.data(), ck_end.size());
+}
+
 int64_t dss_device_bytes(const dss_handle* h) { return h ? h->bytes : 0; }
 
 void dss_destroy(dss_handle* h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
+  adj_free(h);
   drop_graphs(h);
   free_buffers(h);
   if (h->status) cudaFree(h->status);

@@ -20,6 +20,7 @@
 #include <climits>
 
 #include "dss_internal.cuh"
+#include "dss_pair_model.cuh"
 
 namespace {
 constexpr int kPairThreads = 256;
@@ -55,95 +56,8 @@ __device__ __forceinline__ void history_lookup(const Geo& g, const ListBuf& H, i
   }
 }
 
-struct V3 {
-  double x, y, z;
-};
+using V3 = Vec3<double>;
 __device__ __forceinline__ V3 v3(double a, double b, double c) { return V3{a, b, c}; }
-__device__ __forceinline__ V3 operator+(V3 a, V3 b) { return v3(a.x + b.x, a.y + b.y, a.z + b.z); }
-__device__ __forceinline__ V3 operator-(V3 a, V3 b) { return v3(a.x - b.x, a.y - b.y, a.z - b.z); }
-__device__ __forceinline__ V3 operator*(double s, V3 a) { return v3(s * a.x, s * a.y, s * a.z); }
-__device__ __forceinline__ double dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
-__device__ __forceinline__ V3 cross(V3 a, V3 b) {
-  return v3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
-}
-__device__ __forceinline__ V3 tang(V3 n, V3 v) { return v - dot(n, v) * n; }
-
-// FP64 pair physics.  r = x_j(image) - x_i, n = r/|r|, d = |r| - (a_i+a_j).
-// Vi, Vj: velocities relative to U_inf at each centre; Wi, Wj: relative to
-// Omega_inf.  du: u_j(image) - u_i (absolute).  xo: stretch in i->j
-// orientation.  Outputs: force on i, torques on i and j, new stretch.
-struct PairOut {
-  V3 F, Ti, Tj, Fc, Fl, xi;
-  int contact;
-};
-
-__device__ __forceinline__ PairOut pair_fp64(const Geo& g, const InstGeo& I, V3 r, double rr, double ai,
-                                             double aj, V3 Vi, V3 Vj, V3 Wi, V3 Wj, V3 du, V3 wi, V3 wj,
-                                             const double xo[3]) {
-  PairOut o;
-  const double ir = 1.0 / rr;
-  const V3 n = ir * r;
-  const double S = ai + aj;
-  const double d = rr - S;
-  // ---- contact, Eq. 4-5
-  o.Fc = v3(0, 0, 0);
-  V3 Tci = v3(0, 0, 0), Tcj = v3(0, 0, 0);
-  o.xi = v3(0, 0, 0);
-  o.contact = 0;
-  if (d < 0.0) {
-    o.contact = 1;
-    const double fn = g.kn * d + I.gn * dot(n, du);
-    const V3 rel = du - cross(ai * wi + aj * wj, n);
-    const V3 ut = tang(n, rel);
-    V3 xs = tang(n, v3(xo[0], xo[1], xo[2])) + g.dt * ut;
-    const double cap = g.mu * fabs(fn) / g.kt;
-    const double xm = sqrt(dot(xs, xs));
-    if (xm > cap) xs = (cap / xm) * xs;
-    const V3 Ft = g.kt * xs;
-    o.Fc = fn * n + Ft;
-    const V3 nxf = cross(n, Ft);
-    Tci = ai * nxf;
-    Tcj = aj * nxf;
-    o.xi = xs;
-  }
-  // ---- lubrication, App. A
-  double ds = 2.0 * d / S;
-  ds = ds > 0.0 ? ds : 0.0;
-  const double dd = ds + g.eps;
-  const double X = 1.0 / dd;
-  const double Y = -log(dd);
-  const double A = ai, B = aj, AB = A * B;
-  const double iS = 1.0 / S, iS2 = iS * iS, iS3 = iS2 * iS;
-  const double xa = X * 2.0 * AB * AB * iS3;
-  const double ya = Y * (4.0 / 15.0) * AB * (2.0 * A * A + AB + 2.0 * B * B) * iS3;
-  const double ybi = -Y * (2.0 / 15.0) * A * AB * (4.0 * A + B) * iS2;
-  const double ybj = -Y * (2.0 / 15.0) * AB * B * (A + 4.0 * B) * iS2;
-  const double yci = Y * (8.0 / 15.0) * A * A * AB * iS;
-  const double ycj = Y * (8.0 / 15.0) * AB * B * B * iS;
-  const double ycx = Y * (2.0 / 15.0) * AB * AB * iS;
-  const double xg = X * 2.0 * AB * AB * iS2;
-  const double yg = Y * (1.0 / 15.0) * AB * (4.0 - 6.0 * AB * iS2);
-  const double yhi = Y * iS2 * ((2.0 / 15.0) * A * A * AB * (2.0 * A - B) + (1.0 / 15.0) * AB * AB * (7.0 * A + B));
-  const double yhj = Y * iS2 * ((1.0 / 15.0) * AB * AB * (A + 7.0 * B) + (2.0 / 15.0) * AB * B * B * (2.0 * B - A));
-  const V3 dV = Vi - Vj;
-  const double nV = dot(n, dV);
-  const V3 fr = (xa * nV) * n + ya * tang(n, dV) + ybi * cross(n, Wi) + ybj * cross(n, Wj);
-  // simple shear: 2 E n = gdot (n_y, n_x, 0), P = gdot n_x n_y, Q.n = 2 E n - 2 P n
-  const V3 twoEn = v3(I.gdot * n.y, I.gdot * n.x, 0.0);
-  const double P = I.gdot * n.x * n.y;
-  const V3 Qn = twoEn - (2.0 * P) * n;
-  const V3 nperp = cross(n, twoEn);
-  const V3 fe = (xg * P) * n + yg * Qn;
-  const V3 Fl = g.k6 * (fe - fr);
-  const V3 ndV = cross(n, dV);
-  const V3 Tli = g.k6 * (ybi * ndV - (yci * tang(n, Wi) + ycx * tang(n, Wj)) + yhi * nperp);
-  const V3 Tlj = g.k6 * (ybj * ndV - (ycx * tang(n, Wi) + ycj * tang(n, Wj)) + yhj * nperp);
-  o.Fl = Fl;
-  o.F = o.Fc + Fl;
-  o.Ti = Tci + Tli;
-  o.Tj = Tcj + Tlj;
-  return o;
-}
 
 struct F3 {
   float x, y, z;
@@ -196,7 +110,9 @@ __device__ __forceinline__ PairRes<double> pair_eval_fp64(const Geo& g, const In
   const V3 Wi = v3(wi.x, wi.y, wi.z - Om);
   const V3 Wj = v3(wj.x, wj.y, wj.z - Om);
   const V3 du = v3(uj.x + sy * I.gdot * I.L[1] - ui.x, uj.y - ui.y, uj.z - ui.z);
-  const PairOut o = pair_fp64(g, I, r, rr, ai, aj, Vi, Vj, Wi, Wj, du, wi, wj, xo);
+  const PairParams<double> pp{g.kn, g.kt, I.gn, g.mu, g.delta};
+  const PairModelOut<double> o =
+      pair_model<double>(g, I, pp, r, rr, ai, aj, Vi, Vj, Wi, Wj, du, wi, wj, v3(xo[0], xo[1], xo[2]));
   PairRes<double> q;
   q.F[0] = o.F.x; q.F[1] = o.F.y; q.F[2] = o.F.z;
   q.Ti[0] = o.Ti.x; q.Ti[1] = o.Ti.y; q.Ti[2] = o.Ti.z;
@@ -321,10 +237,21 @@ __device__ __forceinline__ PairRes<float> pair_eval_mixed(const Geo& g, const In
   const float Pn = gd * nn.x * nn.y;
   const F3 Qn = twoEn - (2.0f * Pn) * nn;
   const F3 nperp = crossf(nn, twoEn);
-  const F3 Fl = k6 * (((xg * Pn) * nn + yg * Qn) - fr);
+  F3 Fl = k6 * (((xg * Pn) * nn + yg * Qn) - fr);
   const F3 ndV = crossf(nn, dV);
-  const F3 Tli = k6 * (ybi * ndV - (yci * tangf(nn, Wi) + ycx * tangf(nn, Wj)) + yhi * nperp);
-  const F3 Tlj = k6 * (ybj * ndV - (ycx * tangf(nn, Wi) + ycj * tangf(nn, Wj)) + yhj * nperp);
+  F3 Tli = k6 * (ybi * ndV - (yci * tangf(nn, Wi) + ycx * tangf(nn, Wj)) + yhi * nperp);
+  F3 Tlj = k6 * (ybj * ndV - (ycx * tangf(nn, Wi) + ycj * tangf(nn, Wj)) + yhj * nperp);
+  if (g.f.taper > 0.0f) {
+    // differentiable cutoff: smoothstep over the last fraction w of the range
+    const float dl = g.mode == 1 ? g.f.delta_a0 : g.f.delta * 0.5f * S;
+    const float t = (dl - d) / (g.f.taper * dl);
+    if (t < 1.0f) {
+      const float s = t > 0.0f ? t * t * (3.0f - 2.0f * t) : 0.0f;
+      Fl = s * Fl;
+      Tli = s * Tli;
+      Tlj = s * Tlj;
+    }
+  }
   const F3 F = Fc + Fl;
   const F3 Ti = Ai * nxf + Tli;
   const F3 Tj = Bj * nxf + Tlj;

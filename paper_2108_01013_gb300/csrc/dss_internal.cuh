@@ -53,8 +53,10 @@ struct Geo {
   double dt;
   double k6;          // 6 pi eta0
   double k8;          // 8 pi eta0
+  double taper;       // lubrication taper width w (0: hard cutoff)
   struct {             // FP32 copies of the model constants (mixed precision)
     float kn, kt, mu_kt, dt, eps, k6, k8, mass_c;
+    float taper, delta, delta_a0;
   } f;
 };
 
@@ -302,6 +304,41 @@ struct ListBuf {
   int* id_of_slot;  // n: id of each sorted index of this list
 };
 
+// Buffers of the adjoint (reverse sweep over a rollout): per-step tapes of
+// the replayed forward and the adjoint state.  Owned by the handle.
+struct AdjTape {
+  double* x;        // 3n sorted positions at the step's force evaluation
+  double* u;        // 3n velocities u^{n+1/2} (or u^n for the initial evaluation)
+  double* w;        // 3n angular velocities
+  int* id;          // n ids of the sorted order
+  int* start;       // n+1 CSR row offsets of the step's pairs
+  int* op;          // pcap owner (sorted index) of each pair
+  int* pj;          // pcap partner (sorted index)
+  int* pold;        // pcap index of the pair in the previous step's list, -1 if none
+  double* xo;       // 3*pcap stretch carried in (i -> j orientation), 0 if none
+  StepGeo* sg;      // Lees-Edwards geometry of the step (instance 0)
+};
+
+struct AdjBuf {
+  int slots;
+  int64_t pcap;
+  AdjTape* tape;         // [slots] (host array of device pointers)
+  int* P_host;           // [slots] pairs per taped step (pinned)
+  double *xb, *ub, *wb, *ab, *bb;   // 3n adjoint state, id order
+  double* Fb;            // 3n force cotangent, sorted order of the step
+  double* Tb;            // 3n torque cotangent
+  double* pout;          // 18*pcap per-pair input adjoints (i side 9, j side 9)
+  int* bw_n;             // n partner records per particle
+  int* bw_p;             // n*M pair indices of the partner records
+  double* xib[2];        // 3*pcap stretch adjoints of the current / previous step's pairs
+  double* thb_part;      // 5 per pair block
+  double* thb;           // 5: kn, kt, gamma_n, mu, delta_lub
+  double* J;             // objective
+  double* W;             // [nsteps][9] stress weights
+  int64_t W_steps;
+  int cur;               // which xib is the current step's
+};
+
 struct dss_handle {
   dss_params p;
   int64_t n;                 // particles of all instances
@@ -378,6 +415,7 @@ struct dss_handle {
   bool graph_ok[4];
   int64_t bytes;
   int64_t host_steps_done;
+  AdjBuf* adj;               // adjoint buffers (allocated by dss_adjoint)
 };
 
 // Kernel launchers (defined in the .cu files).  adv = 1 inside a time step
@@ -397,3 +435,12 @@ int bw_slot_values();
 // Marks the start of kernel k of a step when profiling (event record node
 // when the step is being captured).
 void prof_mark(dss_handle* h, int k);
+
+// Adjoint (dss_adjoint.cu).
+int adj_alloc(dss_handle* h, int slots, int64_t nsteps);
+void adj_free(dss_handle* h);
+int adj_upload_weights(dss_handle* h, const double* W, int64_t nsteps);
+void adj_zero(dss_handle* h);
+void adj_accum_J(dss_handle* h, int64_t step);
+void adj_tape(dss_handle* h, int slot, int stbuf, int list, int hist_list, bool empty_history);
+void adj_reverse(dss_handle* h, int slot, int64_t step, bool initial);

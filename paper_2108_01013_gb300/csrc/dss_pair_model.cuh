@@ -1,0 +1,294 @@
+// The pair model of one listed pair (FP64 arithmetic), written once over a
+// scalar type T: T = double for the FP64 force pass, T = Dual<K> (forward-mode
+// derivatives in K directions) for the reverse sweep of the adjoint, which
+// builds each pair's vector-Jacobian product from K-column blocks of its
+// local Jacobian.  Branches (contact, Coulomb slip, gap clamp, taper ends)
+// are taken on the values, so derivatives are those of the branch taken.
+//
+// Contact: Eq. 4-5 (linear spring-dashpot normal force, tangential spring
+// with the stretch carried between steps, Coulomb rescale of the stretch).
+// Lubrication: App. A (Eq. A2, A3 with the coefficient functions of Eq. A6,
+// A7 and the 6 pi eta0 prefactor) in the simple shear of Sec. II; with a
+// taper width w > 0 the lubrication force and torques are scaled by
+// s = t^2 (3 - 2t), t = clamp((delta_ij - d) / (w delta_ij), 0, 1) (an
+// extension that makes the cutoff differentiable; w = 0 is the hard cutoff).
+#pragma once
+
+#include "dss_internal.cuh"
+
+// ---------------------------------------------------------------- scalars
+__device__ __forceinline__ double val(double x) { return x; }
+
+template <int K>
+struct Dual {
+  double v;
+  double d[K];
+};
+
+template <int K>
+__device__ __forceinline__ double val(const Dual<K>& x) { return x.v; }
+
+template <typename T>
+__device__ __forceinline__ T cst(double c);
+template <>
+__device__ __forceinline__ double cst<double>(double c) { return c; }
+
+template <int K>
+__device__ __forceinline__ Dual<K> dual_const(double c) {
+  Dual<K> r;
+  r.v = c;
+#pragma unroll
+  for (int k = 0; k < K; ++k) r.d[k] = 0.0;
+  return r;
+}
+
+#define DSS_DUAL_OPS(K)                                                              \
+  template <>                                                                        \
+  __device__ __forceinline__ Dual<K> cst<Dual<K>>(double c) { return dual_const<K>(c); }
+DSS_DUAL_OPS(1)
+DSS_DUAL_OPS(2)
+DSS_DUAL_OPS(3)
+DSS_DUAL_OPS(4)
+DSS_DUAL_OPS(5)
+DSS_DUAL_OPS(6)
+DSS_DUAL_OPS(7)
+DSS_DUAL_OPS(8)
+#undef DSS_DUAL_OPS
+
+template <int K>
+__device__ __forceinline__ Dual<K> operator+(const Dual<K>& a, const Dual<K>& b) {
+  Dual<K> r;
+  r.v = a.v + b.v;
+#pragma unroll
+  for (int k = 0; k < K; ++k) r.d[k] = a.d[k] + b.d[k];
+  return r;
+}
+template <int K>
+__device__ __forceinline__ Dual<K> operator-(const Dual<K>& a, const Dual<K>& b) {
+  Dual<K> r;
+  r.v = a.v - b.v;
+#pragma unroll
+  for (int k = 0; k < K; ++k) r.d[k] = a.d[k] - b.d[k];
+  return r;
+}
+template <int K>
+__device__ __forceinline__ Dual<K> operator-(const Dual<K>& a) {
+  Dual<K> r;
+  r.v = -a.v;
+#pragma unroll
+  for (int k = 0; k < K; ++k) r.d[k] = -a.d[k];
+  return r;
+}
+template <int K>
+__device__ __forceinline__ Dual<K> operator*(const Dual<K>& a, const Dual<K>& b) {
+  Dual<K> r;
+  r.v = a.v * b.v;
+#pragma unroll
+  for (int k = 0; k < K; ++k) r.d[k] = a.d[k] * b.v + a.v * b.d[k];
+  return r;
+}
+template <int K>
+__device__ __forceinline__ Dual<K> operator/(const Dual<K>& a, const Dual<K>& b) {
+  Dual<K> r;
+  const double ib = 1.0 / b.v;
+  r.v = a.v * ib;
+#pragma unroll
+  for (int k = 0; k < K; ++k) r.d[k] = (a.d[k] - r.v * b.d[k]) * ib;
+  return r;
+}
+template <int K>
+__device__ __forceinline__ Dual<K> operator+(const Dual<K>& a, double b) {
+  Dual<K> r = a;
+  r.v = a.v + b;
+  return r;
+}
+template <int K>
+__device__ __forceinline__ Dual<K> operator+(double a, const Dual<K>& b) { return b + a; }
+template <int K>
+__device__ __forceinline__ Dual<K> operator-(const Dual<K>& a, double b) {
+  Dual<K> r = a;
+  r.v = a.v - b;
+  return r;
+}
+template <int K>
+__device__ __forceinline__ Dual<K> operator-(double a, const Dual<K>& b) {
+  Dual<K> r;
+  r.v = a - b.v;
+#pragma unroll
+  for (int k = 0; k < K; ++k) r.d[k] = -b.d[k];
+  return r;
+}
+template <int K>
+__device__ __forceinline__ Dual<K> operator*(const Dual<K>& a, double b) {
+  Dual<K> r;
+  r.v = a.v * b;
+#pragma unroll
+  for (int k = 0; k < K; ++k) r.d[k] = a.d[k] * b;
+  return r;
+}
+template <int K>
+__device__ __forceinline__ Dual<K> operator*(double a, const Dual<K>& b) { return b * a; }
+template <int K>
+__device__ __forceinline__ Dual<K> operator/(const Dual<K>& a, double b) { return a * (1.0 / b); }
+template <int K>
+__device__ __forceinline__ Dual<K> operator/(double a, const Dual<K>& b) {
+  Dual<K> r;
+  const double ib = 1.0 / b.v;
+  r.v = a * ib;
+#pragma unroll
+  for (int k = 0; k < K; ++k) r.d[k] = -r.v * ib * b.d[k];
+  return r;
+}
+template <int K>
+__device__ __forceinline__ Dual<K> sqrt(const Dual<K>& a) {
+  Dual<K> r;
+  r.v = ::sqrt(a.v);
+  const double h = 0.5 / r.v;
+#pragma unroll
+  for (int k = 0; k < K; ++k) r.d[k] = h * a.d[k];
+  return r;
+}
+template <int K>
+__device__ __forceinline__ Dual<K> log(const Dual<K>& a) {
+  Dual<K> r;
+  r.v = ::log(a.v);
+  const double ia = 1.0 / a.v;
+#pragma unroll
+  for (int k = 0; k < K; ++k) r.d[k] = ia * a.d[k];
+  return r;
+}
+template <int K>
+__device__ __forceinline__ Dual<K> fabs(const Dual<K>& a) {
+  return a.v < 0.0 ? -a : a;
+}
+
+// ---------------------------------------------------------------- vectors
+template <typename T>
+struct Vec3 {
+  T x, y, z;
+};
+template <typename T>
+__device__ __forceinline__ Vec3<T> mk3(T a, T b, T c) { return Vec3<T>{a, b, c}; }
+template <typename T>
+__device__ __forceinline__ Vec3<T> operator+(const Vec3<T>& a, const Vec3<T>& b) {
+  return mk3<T>(a.x + b.x, a.y + b.y, a.z + b.z);
+}
+template <typename T>
+__device__ __forceinline__ Vec3<T> operator-(const Vec3<T>& a, const Vec3<T>& b) {
+  return mk3<T>(a.x - b.x, a.y - b.y, a.z - b.z);
+}
+template <typename T, typename S>
+__device__ __forceinline__ Vec3<T> operator*(const S& s, const Vec3<T>& a) {
+  return mk3<T>(s * a.x, s * a.y, s * a.z);
+}
+template <typename T>
+__device__ __forceinline__ T dot(const Vec3<T>& a, const Vec3<T>& b) {
+  return a.x * b.x + a.y * b.y + a.z * b.z;
+}
+template <typename T>
+__device__ __forceinline__ Vec3<T> cross(const Vec3<T>& a, const Vec3<T>& b) {
+  return mk3<T>(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+template <typename T>
+__device__ __forceinline__ Vec3<T> tang(const Vec3<T>& n, const Vec3<T>& v) {
+  return v - dot(n, v) * n;
+}
+
+// The model parameters a pair depends on (differentiable in the adjoint).
+template <typename T>
+struct PairParams {
+  T kn, kt, gn, mu, delta;
+};
+
+// Outputs: force on i (F = Fc + Fl), torques on i and j, the contact and
+// lubrication parts of the force, the new stretch (i -> j orientation).
+template <typename T>
+struct PairModelOut {
+  Vec3<T> F, Ti, Tj, Fc, Fl, xi;
+  int contact;
+};
+
+// r = x_j(image) - x_i, rr = |r|; Vi, Vj velocities relative to U_inf at each
+// centre; Wi, Wj angular velocities relative to Omega_inf; du = u_j(image) -
+// u_i (absolute); wi, wj absolute angular velocities; xo stretch (i -> j).
+template <typename T>
+__device__ __forceinline__ PairModelOut<T> pair_model(const Geo& g, const InstGeo& I,
+                                                      const PairParams<T>& q, Vec3<T> r, T rr,
+                                                      double ai, double aj, Vec3<T> Vi, Vec3<T> Vj,
+                                                      Vec3<T> Wi, Vec3<T> Wj, Vec3<T> du, Vec3<T> wi,
+                                                      Vec3<T> wj, Vec3<T> xo) {
+  PairModelOut<T> o;
+  const T zero = cst<T>(0.0);
+  const T ir = 1.0 / rr;
+  const Vec3<T> n = ir * r;
+  const double S = ai + aj;
+  const T d = rr - S;
+  // ---- contact, Eq. 4-5
+  o.Fc = mk3<T>(zero, zero, zero);
+  Vec3<T> Tci = o.Fc, Tcj = o.Fc;
+  o.xi = o.Fc;
+  o.contact = 0;
+  if (val(d) < 0.0) {
+    o.contact = 1;
+    const T fn = q.kn * d + q.gn * dot(n, du);
+    const Vec3<T> rel = du - cross(ai * wi + aj * wj, n);
+    const Vec3<T> ut = tang(n, rel);
+    Vec3<T> xs = tang(n, xo) + g.dt * ut;
+    const T cap = q.mu * fabs(fn) / q.kt;
+    const T xm = sqrt(dot(xs, xs));
+    if (val(xm) > val(cap)) xs = (cap / xm) * xs;
+    const Vec3<T> Ft = q.kt * xs;
+    o.Fc = fn * n + Ft;
+    const Vec3<T> nxf = cross(n, Ft);
+    Tci = ai * nxf;
+    Tcj = aj * nxf;
+    o.xi = xs;
+  }
+  // ---- lubrication, App. A
+  T ds = 2.0 * d / S;
+  if (!(val(ds) > 0.0)) ds = zero;
+  const T dd = ds + g.eps;
+  const T X = 1.0 / dd;
+  const T Y = -log(dd);
+  const double A = ai, B = aj, AB = A * B;
+  const double iS = 1.0 / S, iS2 = iS * iS, iS3 = iS2 * iS;
+  const T xa = X * (2.0 * AB * AB * iS3);
+  const T ya = Y * ((4.0 / 15.0) * AB * (2.0 * A * A + AB + 2.0 * B * B) * iS3);
+  const T ybi = -Y * ((2.0 / 15.0) * A * AB * (4.0 * A + B) * iS2);
+  const T ybj = -Y * ((2.0 / 15.0) * AB * B * (A + 4.0 * B) * iS2);
+  const T yci = Y * ((8.0 / 15.0) * A * A * AB * iS);
+  const T ycj = Y * ((8.0 / 15.0) * AB * B * B * iS);
+  const T ycx = Y * ((2.0 / 15.0) * AB * AB * iS);
+  const T xg = X * (2.0 * AB * AB * iS2);
+  const T yg = Y * ((1.0 / 15.0) * AB * (4.0 - 6.0 * AB * iS2));
+  const T yhi = Y * (iS2 * ((2.0 / 15.0) * A * A * AB * (2.0 * A - B) + (1.0 / 15.0) * AB * AB * (7.0 * A + B)));
+  const T yhj = Y * (iS2 * ((1.0 / 15.0) * AB * AB * (A + 7.0 * B) + (2.0 / 15.0) * AB * B * B * (2.0 * B - A)));
+  const Vec3<T> dV = Vi - Vj;
+  const T nV = dot(n, dV);
+  const Vec3<T> fr = (xa * nV) * n + ya * tang(n, dV) + ybi * cross(n, Wi) + ybj * cross(n, Wj);
+  // simple shear: 2 E n = gdot (n_y, n_x, 0), P = gdot n_x n_y, Q.n = 2 E n - 2 P n
+  const Vec3<T> twoEn = mk3<T>(I.gdot * n.y, I.gdot * n.x, zero);
+  const T P = I.gdot * n.x * n.y;
+  const Vec3<T> Qn = twoEn - (2.0 * P) * n;
+  const Vec3<T> nperp = cross(n, twoEn);
+  const Vec3<T> fe = (xg * P) * n + yg * Qn;
+  Vec3<T> Fl = g.k6 * (fe - fr);
+  const Vec3<T> ndV = cross(n, dV);
+  Vec3<T> Tli = g.k6 * (ybi * ndV - (yci * tang(n, Wi) + ycx * tang(n, Wj)) + yhi * nperp);
+  Vec3<T> Tlj = g.k6 * (ybj * ndV - (ycx * tang(n, Wi) + ycj * tang(n, Wj)) + yhj * nperp);
+  if (g.taper > 0.0) {
+    const T dl = g.mode == 1 ? q.delta * g.a0 : q.delta * (0.5 * S);
+    const T t = (dl - d) / (g.taper * dl);
+    if (val(t) < 1.0) {
+      const T s = val(t) > 0.0 ? t * t * (3.0 - 2.0 * t) : zero;
+      Fl = s * Fl;
+      Tli = s * Tli;
+      Tlj = s * Tlj;
+    }
+  }
+  o.Fl = Fl;
+  o.F = o.Fc + Fl;
+  o.Ti = Tci + Tli;
+  o.Tj = Tcj + Tlj;
+  return o;
+}

@@ -17,7 +17,8 @@ from . import _native as nat
 
 def default_params(box=None, *, kn=1e4, kt=None, gamma_n=None, mu=0.5, eta0=1.0, rho=1.0,
                    delta_lub=0.05, lub_eps=1e-3, a0=1.0, lub_cutoff_mode=0, precision="fp64",
-                   shear_rate=1.0, dt=1e-4, cell_size=0.0, capacity_M=0, pair_capacity=0):
+                   shear_rate=1.0, dt=1e-4, cell_size=0.0, capacity_M=0, pair_capacity=0,
+                   lub_taper=0.0):
     """Model parameters; kt defaults to kn/2 and gamma_n to 1e-7 kn / gdot."""
     p = nat.Params()
     p.kn = kn
@@ -31,6 +32,7 @@ def default_params(box=None, *, kn=1e4, kt=None, gamma_n=None, mu=0.5, eta0=1.0,
     p.precision = {"fp64": nat.FP64, "mixed": nat.MIXED}[precision] if isinstance(precision, str) else precision
     p.shear_rate, p.dt = shear_rate, dt
     p.cell_size, p.capacity_M, p.pair_capacity = cell_size, capacity_M, pair_capacity
+    p.lub_taper = lub_taper
     return p
 
 
@@ -200,6 +202,31 @@ class Suspension:
         nat.check(self.lib.dss_autotune(self._h, int(trial_steps), f.shape[0], f.ctypes.data_as(dp),
                                         ms.ctypes.data_as(dp), byref(cs)), "dss_autotune")
         return cs.value, dict(zip(f.tolist(), ms.tolist()))
+
+    def adjoint(self, nsteps: int, weights, *, ckpt_every: int = 20, initial_forces: bool = True):
+        """Reverse-mode gradient of J = sum_n sum_q weights[n, q] sigma^{n+1}_q
+        over nsteps steps from the current state (the handle ends after them).
+        Returns dict(J, params (k_n, k_t, gamma_n, mu, delta_lub), x0, u0, w0,
+        alpha0, beta0) with (3, n) arrays in id order."""
+        W = np.ascontiguousarray(weights, dtype=np.float64).reshape(int(nsteps), 9)
+        J = c_double(0.0)
+        gp = np.zeros(5)
+        outs = [np.zeros((3, self.n)) for _ in range(5)]
+        dp = ctypes.POINTER(c_double)
+        nat.check(self.lib.dss_adjoint(self._h, int(nsteps), int(ckpt_every), c_void_p(W.ctypes.data),
+                                       1 if initial_forces else 0, byref(J), gp.ctypes.data_as(dp),
+                                       *[c_void_p(o.ctypes.data) for o in outs]), "dss_adjoint")
+        return dict(J=J.value, params=gp, x0=outs[0], u0=outs[1], w0=outs[2], alpha0=outs[3],
+                    beta0=outs[4])
+
+    def rollout_objective(self, nsteps: int, weights) -> float:
+        """J of nsteps steps from the current state (forward only)."""
+        W = np.asarray(weights, dtype=np.float64).reshape(int(nsteps), 9)
+        J = 0.0
+        for k in range(int(nsteps)):
+            self.step(1)
+            J += float((W[k] * self.stress().reshape(9)).sum())
+        return J
 
     def device_bytes(self) -> int:
         return int(self.lib.dss_device_bytes(self._h))

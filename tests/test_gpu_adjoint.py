@@ -1,0 +1,184 @@
+"""Reverse-mode gradients of a rollout (dss_adjoint) against the FP64 adjoint
+oracle (plain PyTorch autograd over the oracle's model), against central
+finite differences of the GPU forward, and for independence of the
+checkpoint interval (the replayed segments repeat the forward bit for bit)."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import oracle
+    from oracle import adjoint as oadj
+    import paper_2108_01013_gb300 as dss
+    from paper_2108_01013_gb300 import synth
+    oracle.build()
+    dss.build()
+    synth.build()
+    return dict(oracle=oracle, oadj=oadj, dss=dss, synth=synth, torch=torch)
+
+
+def relerr(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _case(env, taper, n=260, seed=61):
+    g = env["synth"].small(n, 0.52, seed)
+    rng = np.random.default_rng(5)
+    u0 = np.zeros((3, n))
+    u0[0] = 5.0 * g["x"][1]
+    u0 += 0.5 * rng.normal(size=(3, n))
+    w0 = 0.5 * rng.normal(size=(3, n))
+    kw = dict(shear_rate=5.0, dt=1e-4, lub_taper=taper)
+    th = dict(kn=1e4, kt=6e3, gamma_n=0.5, mu=0.4, delta_lub=0.2 if taper else 0.05)
+    return g, u0, w0, kw, th
+
+
+def _weights(T, gd):
+    W = np.zeros((T, 9))
+    W[:, 1] = 1.0 / (T * gd)
+    W[:, 3] = 0.25 / (T * gd)
+    W[:, 0] = 0.1 / T
+    return W
+
+
+def _gpu(env, g, u0, w0, kw, th, T, W, precision="fp64", ckpt=5, nstep0=3):
+    p = env["dss"].default_params(g["box"], precision=precision, **th, **kw)
+    s = env["dss"].Suspension(g["x"], g["a"], g["box"], p, ids=g["ids"], u=u0, w=w0, nstep=nstep0)
+    r = s.adjoint(T, W, ckpt_every=ckpt)
+    st = s.state()
+    s.close()
+    return r, st
+
+
+@pytest.mark.parametrize("taper", [0.0, 0.3])
+def test_adjoint_matches_oracle_fp64(env, taper):
+    g, u0, w0, kw, th = _case(env, taper)
+    T = 12
+    W = _weights(T, kw["shear_rate"])
+    o = env["oadj"].gradients(g["box"], g["x"], g["a"], u0, w0, T, W, **th, **kw, nstep0=3)
+    r, st = _gpu(env, g, u0, w0, kw, th, T, W)
+    assert r["J"] == pytest.approx(o["J"], rel=1e-11)
+    assert relerr(r["params"], o["params"]) < 1e-8
+    for k in range(5):
+        assert r["params"][k] == pytest.approx(o["params"][k], rel=1e-7, abs=1e-12 * abs(o["J"]))
+    assert relerr(r["x0"], o["x0"]) < 1e-8
+    assert relerr(r["u0"], o["u0"]) < 1e-8
+    assert relerr(r["w0"], o["w0"]) < 1e-8
+    assert np.abs(r["alpha0"]).max() == 0.0
+    # the handle ends after the rollout
+    box = g["box"]
+    d = np.abs(st["x"].cpu().numpy() - o["final"]["x"])
+    d = np.minimum(d, box[:, None] - d)
+    assert d.max() < 1e-12
+
+
+def test_adjoint_independent_of_checkpoint_interval(env):
+    g, u0, w0, kw, th = _case(env, 0.3)
+    T = 12
+    W = _weights(T, kw["shear_rate"])
+    a, _ = _gpu(env, g, u0, w0, kw, th, T, W, ckpt=12)
+    b, _ = _gpu(env, g, u0, w0, kw, th, T, W, ckpt=5)
+    c, _ = _gpu(env, g, u0, w0, kw, th, T, W, ckpt=1)
+    for k in ("params", "x0", "u0", "w0"):
+        assert np.array_equal(a[k], b[k]) and np.array_equal(a[k], c[k]), k
+    assert a["J"] == b["J"] == c["J"]
+
+
+def test_adjoint_mixed_precision_vs_oracle(env):
+    g, u0, w0, kw, th = _case(env, 0.3)
+    T = 12
+    W = _weights(T, kw["shear_rate"])
+    o = env["oadj"].gradients(g["box"], g["x"], g["a"], u0, w0, T, W, **th, **kw, nstep0=3)
+    r, _ = _gpu(env, g, u0, w0, kw, th, T, W, precision="mixed")
+    assert r["J"] == pytest.approx(o["J"], rel=1e-6)
+    for k in range(5):
+        assert r["params"][k] == pytest.approx(o["params"][k], rel=1e-4, abs=1e-9 * abs(o["J"]))
+    assert relerr(r["x0"], o["x0"]) < 1e-4
+
+
+def test_autograd_function_and_tied_parameters(env):
+    torch = env["torch"]
+    dss = env["dss"]
+    g, u0, w0, kw, th = _case(env, 0.3)
+    T = 8
+    W = dss.viscosity_weights(T, shear_rate=kw["shear_rate"])
+    x0 = torch.tensor(g["x"], requires_grad=True)
+    kn = torch.tensor(th["kn"], dtype=torch.float64, requires_grad=True)
+    mu = torch.tensor(th["mu"], dtype=torch.float64, requires_grad=True)
+    # k_t = k_n / 2 tied: the total derivative flows through both slots
+    theta = torch.stack([kn, 0.5 * kn, torch.tensor(th["gamma_n"], dtype=torch.float64), mu,
+                         torch.tensor(th["delta_lub"], dtype=torch.float64)])
+    J = dss.rollout_stress(x0, theta, g["a"], g["box"], u0, w0, T, W, ckpt_every=4, **kw)
+    J.backward()
+    th2 = dict(th, kt=0.5 * th["kn"])
+    o = env["oadj"].gradients(g["box"], g["x"], g["a"], u0, w0, T, W, **th2, **kw)
+    assert J.item() == pytest.approx(o["J"], rel=1e-11)
+    assert float(kn.grad) == pytest.approx(o["params"][0] + 0.5 * o["params"][1], rel=1e-7)
+    assert float(mu.grad) == pytest.approx(o["params"][3], rel=1e-7)
+    assert relerr(x0.grad.numpy(), o["x0"]) < 1e-8
+
+
+def test_adjoint_20k_rollout_vs_central_differences(env):
+    """The differentiable-rollout workload: 20,000 bidisperse spheres at
+    volume fraction 0.54, mu = 0.5, 200 steps with a checkpoint every 20;
+    time-averaged relative viscosity.  FP64 gradients against central
+    differences of the GPU forward (FP64) for mu, k_n and delta_lub (taper on),
+    and along random directions of the initial positions."""
+    dss = env["dss"]
+    synth = env["synth"]
+    g = synth.generate(synth.SPECS["c5"])
+    box = g["box"]
+    T = 200
+    kw = dict(shear_rate=1.0, dt=1e-4, lub_taper=0.2)
+    th = dict(kn=1e4, kt=5e3, gamma_n=1e-3, mu=0.5, delta_lub=0.1)
+    W = dss.viscosity_weights(T, shear_rate=1.0)
+    n = g["a"].shape[0]
+    u0 = np.zeros((3, n))
+    u0[0] = g["x"][1]
+    w0 = np.zeros((3, n))
+    w0[2] = -0.5
+
+    def make(th_, x=None):
+        p = dss.default_params(box, precision="fp64", **th_, **kw)
+        return dss.Suspension(g["x"] if x is None else x, g["a"], box, p, ids=g["ids"], u=u0, w=w0)
+
+    s = make(th)
+    r = s.adjoint(T, W, ckpt_every=20)
+    s.close()
+
+    def J(th_, x=None):
+        s2 = make(th_, x)
+        v = s2.rollout_objective(T, W)
+        s2.close()
+        return v
+
+    for k, name, rel in ((3, "mu", 1e-3), (0, "kn", 1e-3), (4, "delta_lub", 1e-3)):
+        h = rel * th[name]
+        fd = (J(dict(th, **{name: th[name] + h})) - J(dict(th, **{name: th[name] - h}))) / (2 * h)
+        assert r["params"][k] == pytest.approx(fd, rel=1e-4, abs=1e-6 * abs(fd) + 1e-12), name
+    # initial positions: directions that move 20 particles.  A perturbed
+    # trajectory can cross a cell boundary a step earlier or later, which
+    # reorders force sums; the dense packing amplifies those last-bit changes
+    # over 200 steps into FD noise.  The noise is estimated from the spread of
+    # the difference quotient over two steps and allowed for on top of 1e-4.
+    for seed in (3, 4):
+        rng = np.random.default_rng(seed)
+        v = np.zeros((3, n))
+        idx = rng.choice(n, 20, replace=False)
+        v[:, idx] = rng.normal(size=(3, 20))
+        fds = []
+        for h in (1e-7, 2e-7):
+            fds.append((J(th, np.mod(g["x"] + h * v, box[:, None]))
+                        - J(th, np.mod(g["x"] - h * v, box[:, None]))) / (2 * h))
+        noise = abs(fds[0] - fds[1])
+        ad = float((r["x0"] * v).sum())
+        assert noise < 1e-2 * abs(fds[0])
+        assert abs(ad - fds[0]) <= 1e-4 * abs(fds[0]) + 2.0 * noise

@@ -147,6 +147,36 @@ def test_forces_and_stress_fp64(env, seed, nstep, mu):
     s.close()
 
 
+@pytest.mark.parametrize("precision,tol,mode", [("fp64", FP64_TOL, 0), ("mixed", 1e-5, 0),
+                                                ("fp64", FP64_TOL, 1)])
+def test_forces_with_lubrication_taper(env, precision, tol, mode):
+    """The differentiable cutoff (lubrication scaled down over the last 30% of
+    the range) against the oracle, with a wide range so that many pairs sit in
+    the band."""
+    g = env["synth"].small(1200, 0.50, 7)
+    box = g["box"]
+    kw = dict(mu=0.5, lub_taper=0.3, delta_lub=0.3, lub_cutoff_mode=mode)
+    p = env["dss"].default_params(box, precision=precision, **kw)
+    po = env["oracle"].make_params(box, **kw)
+    rng = np.random.default_rng(3)
+    n = g["a"].shape[0]
+    u = 0.3 * rng.normal(size=(3, n))
+    w = 0.3 * rng.normal(size=(3, n))
+    s = env["dss"].Suspension(g["x"], g["a"], box, p, ids=g["ids"], u=u, w=w,
+                              alpha_lin=np.zeros((3, n)), alpha_ang=np.zeros((3, n)))
+    F, T = s.forces()
+    o = env["oracle"].System(po, g["x"], g["a"], ids=g["ids"], u=u, w=w)
+    Fo, To, So = o.forces()
+    assert relerr(F.cpu().numpy(), Fo) < tol
+    assert relerr(T.cpu().numpy(), To) < tol
+    assert relerr(s.stress(), So) < tol
+    # the taper changes the answer: the untapered oracle differs
+    po0 = env["oracle"].make_params(box, **dict(kw, lub_taper=0.0))
+    Fu = env["oracle"].System(po0, g["x"], g["a"], ids=g["ids"], u=u, w=w).forces()[0]
+    assert relerr(Fu, Fo) > 1e-3
+    s.close()
+
+
 def test_forces_with_carried_history(env):
     """History handed over from the oracle gives the same tangential forces."""
     g = env["synth"].small(800, 0.52, 7)
