@@ -117,7 +117,7 @@ SPECS = {
     "c1": Spec("c1_fp64_bidisperse_1k", 1000, 0.50, mu=0.5, steps=1000, seed=1),
     "c2": Spec("c2_mixed_bidisperse_100k", 100_000, 0.55, mu=1.0, steps=10_000, seed=2),
     "c3": Spec("c3_polydisperse_1m", 1_000_000, 0.50, radii="loguniform", mu=0.5,
-               steps=1000, seed=3, max_iter=400),
+               steps=1000, seed=3, max_iter=20),
     "c5": Spec("c5_rollout_20k", 20_000, 0.54, mu=0.5, steps=200, seed=5),
 }
 
