@@ -40,7 +40,8 @@ void free_buffers(dss_handle* h) {
     dfree(L.id_of_slot);
     memset(&L, 0, sizeof(L));
   }
-  dfree(h->posf); dfree(h->cellid); dfree(h->perm); dfree(h->key); dfree(h->offs);
+  dfree(h->posf); dfree(h->cellid); dfree(h->perm); dfree(h->key); dfree(h->offs); dfree(h->pred);
+  h->pred = nullptr;
   dfree(h->cell_count); dfree(h->cell_start); dfree(h->tmp); dfree(h->spart);
   dfree(h->own); dfree(h->bw_count); dfree(h->bw_rec);
   h->own = nullptr; h->bw_count = nullptr; h->bw_rec = nullptr;
@@ -129,6 +130,7 @@ int alloc_buffers(dss_handle* h) {
       return r;
   }
   if ((r = dalloc(h, &h->posf, n)) || (r = dalloc(h, &h->cellid, n)) || (r = dalloc(h, &h->perm, n)) ||
+      (r = dalloc(h, &h->pred, 6 * n)) ||
       (r = dalloc(h, &h->key, n)) || (r = dalloc(h, &h->offs, n)) ||
       (r = dalloc(h, &h->cell_count, (size_t)h->g.ncell)) ||
       (r = dalloc(h, &h->cell_start, (size_t)h->g.ncell + 1)) || (r = dalloc(h, &h->tmp, n)) ||

@@ -375,6 +375,7 @@ struct dss_handle {
   float4* posf;      // n: cell-local FP32 position + radius
   int* cellid;       // n
   int* perm;         // n: new sorted index -> previous index
+  double* pred;      // 6n: predicted position and velocity of a step, source order
   // counting sort scratch
   int* key;          // n
   int* offs;         // n

@@ -4,8 +4,9 @@
 //      and a warp-aggregated histogram (one atomic per distinct key per warp);
 //   2. exclusive scan of the histogram (single-pass decoupled look-back);
 //   3. scatter to the cell's slot range;
-//   4. deterministic in-cell order (by previous index) and the gather of the
-//      state into the new sorted order, recomputing the predictor.
+//   4. deterministic in-cell order (by id) and the gather of the state into
+//      the new sorted order; the predicted position and velocity are stored by
+//      step 1 (SoA, source order) and gathered, not recomputed.
 #include "dss_internal.cuh"
 
 namespace {
@@ -82,7 +83,7 @@ __global__ void __launch_bounds__(kThreads)
 k_key_hist(Geo g, const InstGeo* __restrict__ ig, StepGeo* __restrict__ sg, StateBuf s,
            int* __restrict__ key, int* __restrict__ offs, int* __restrict__ cell_count,
            DevStatus* st, bool predict, unsigned long long* scan_status, int* scan_ticket,
-           int scan_tiles) {
+           int scan_tiles, double* __restrict__ pred) {
   if (dev_err(st)) return;
   // reset the look-back state of both scans of this operation, the
   // counters, and set every instance's Lees-Edwards geometry for its time
@@ -111,6 +112,15 @@ k_key_hist(Geo g, const InstGeo* __restrict__ ig, StepGeo* __restrict__ sg, Stat
   if (i >= g.n) return;
   const InstGeo& I = ig[s.inst[i]];
   Pred p = predict_one(g, I, st, predict ? 1 : 0, s, i, predict);
+  if (predict) {
+    const int n = g.n;
+    pred[i] = p.x;
+    pred[n + i] = p.y;
+    pred[2 * n + i] = p.z;
+    pred[3 * n + i] = p.ux;
+    pred[4 * n + i] = p.uy;
+    pred[5 * n + i] = p.uz;
+  }
   int k = cell_key(I, p.x, p.y, p.z);
   unsigned act = __activemask();
   unsigned peers = __match_any_sync(act, k);
@@ -141,7 +151,8 @@ __global__ void __launch_bounds__(kThreads)
 k_rank_gather(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ sgk, StateBuf src,
               StateBuf dst, const int* __restrict__ key, const int* __restrict__ cell_start,
               const int* __restrict__ tmp, int* __restrict__ perm, int* __restrict__ cellid,
-              float4* __restrict__ posf, DevStatus* st, bool predict) {
+              float4* __restrict__ posf, DevStatus* st, bool predict,
+              const double* __restrict__ pred) {
   if (dev_err(st)) return;
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = g.n;
@@ -157,7 +168,14 @@ k_rank_gather(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__
   cellid[f] = k;
   const int inst = src.inst[o];
   const InstGeo& I = ig[inst];
-  Pred p = predict_one(g, I, st, predict ? 1 : 0, src, o, predict);
+  Pred p;
+  if (predict) {
+    p.x = pred[o]; p.y = pred[n + o]; p.z = pred[2 * n + o];
+    p.ux = pred[3 * n + o]; p.uy = pred[4 * n + o]; p.uz = pred[5 * n + o];
+  } else {
+    p.x = src.x[o]; p.y = src.x[n + o]; p.z = src.x[2 * n + o];
+    p.ux = src.u[o]; p.uy = src.u[n + o]; p.uz = src.u[2 * n + o];
+  }
   dst.x[f] = p.x; dst.x[n + f] = p.y; dst.x[2 * n + f] = p.z;
   dst.u[f] = p.ux; dst.u[n + f] = p.uy; dst.u[2 * n + f] = p.uz;
   if (predict) {
@@ -292,7 +310,7 @@ void launch_sort(dss_handle* h, bool predict, int src, int dst) {
   prof_mark(h, 0);
   k_key_hist<<<blocks, kThreads, 0, h->stream>>>(h->g, h->ig, h->sg, h->st[src], h->key, h->offs,
                                                  h->cell_count, h->status, predict, h->scan_status,
-                                                 h->scan_ticket, h->scan_tiles_max);
+                                                 h->scan_ticket, h->scan_tiles_max, h->pred);
   prof_mark(h, 1);
   launch_scan(h, h->cell_count, h->cell_start, h->g.ncell, 0, true);
   prof_mark(h, 2);
@@ -300,5 +318,5 @@ void launch_sort(dss_handle* h, bool predict, int src, int dst) {
   prof_mark(h, 3);
   k_rank_gather<<<blocks, kThreads, 0, h->stream>>>(h->g, h->ig, h->sg, h->st[src], h->st[dst], h->key,
                                                     h->cell_start, h->tmp, h->perm, h->cellid,
-                                                    h->posf, h->status, predict);
+                                                    h->posf, h->status, predict, h->pred);
 }
