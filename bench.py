@@ -14,15 +14,18 @@ step is timed on its own with CUDA events recorded inside the step's CUDA
 graph (per-kernel events; the step time runs from the first kernel's start to
 the last kernel's end).
 
-Two more modes are measured in the same run and reported under "modes":
-"fp64", the same workload with the FP64 pair arithmetic, and "batched", a
+More modes are measured in the same run and reported under "modes":
+"fp64", the same workload with the FP64 pair arithmetic; "batched", a
 flow-curve sweep of 256 independent bidisperse suspensions (N uniform in
 [500, 20000], volume fraction uniform in [0.40, 0.58], shear rate log-uniform
 in [1e-2, 1e2], mixed precision) advanced together in one handle after the
-cell edge is autotuned; its working set (~1.5 GB) exceeds the L2.
+cell edge is autotuned (working set ~1.5 GB, beyond the L2); "poly1m",
+1,000,000 spheres with radii log-uniform in [1, 10] in mixed precision and
+FP64; "adjoint", the gradient of the 200-step time-averaged viscosity of
+20,000 spheres (checkpoint every 20 steps) against the forward alone.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
-                       [--modes fp64,batched|none]
+                       [--modes fp64,batched,poly1m,adjoint|none]
 Under torchrun each rank runs an independent replica (replicas only: the
 single-instance path has no data-parallel exchange); value = total particle
 steps of all ranks / max over ranks of the timed GPU time.
@@ -100,9 +103,11 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--modes", default="fp64,batched",
+    ap.add_argument("--modes", default="fp64,batched,poly1m,adjoint",
                     help="extra modes measured in the same run: fp64 (the headline workload in "
-                         "FP64), batched (256-instance flow-curve sweep, mixed); 'none' for neither")
+                         "FP64), batched (256-instance flow-curve sweep, mixed), poly1m (1M "
+                         "polydisperse, mixed and FP64), adjoint (gradient of the 200-step "
+                         "viscosity of 20k spheres); 'none' for none")
     ap.add_argument("--mode-steps", type=int, default=400)
     return ap.parse_args()
 
@@ -266,6 +271,59 @@ def mode_batched(dss, b, bspec, args, stream):
     return out
 
 
+def mode_poly1m(dss, g, spec, args):
+    """1,000,000 spheres, radii log-uniform in [1, 10] (M = 728), in mixed
+    precision and in FP64; its working set exceeds L2."""
+    n = g["a"].shape[0]
+    out = {"config": {"workload": spec.name, "n": n, "phi": spec.phi, "radii": "log-uniform [1, 10]",
+                      "mu": spec.mu, "l2": "working set > L2 (no flush)",
+                      "packing": "random insertion + %d relaxation sweeps" % spec.max_iter}}
+    for prec, steps in (("mixed", args.mode_steps // 2), ("fp64", args.mode_steps // 8)):
+        p = dss.default_params(g["box"], precision=prec, mu=spec.mu, kn=spec.kn,
+                               shear_rate=spec.shear_rate, dt=spec.dt)
+        s = dss.Suspension(g["x"], g["a"], g["box"], p, ids=g["ids"])
+        time_steps(s, 3)
+        t = time_steps(s, steps)
+        c = s.counters()
+        out[prec] = {"value": n * steps / (t * 1e-3), "unit": "particle-steps/s", "ms_per_step": t / steps,
+                     "steps": steps, "device_gb": round(s.device_bytes() / 1e9, 1), "pairs": c["npairs"],
+                     "M": c["M"], "kernels_ms": profile_pass(s, 5)}
+        s.close()
+    return out
+
+
+def mode_adjoint(dss, g, spec, args):
+    """Gradient of the time-averaged relative viscosity of a 200-step rollout
+    of 20,000 spheres with respect to the model constants and the initial
+    positions (checkpoint every 20 steps, mixed-precision forward)."""
+    n = g["a"].shape[0]
+    T = spec.steps
+    p = dss.default_params(g["box"], precision="mixed", mu=spec.mu, kn=spec.kn,
+                           shear_rate=spec.shear_rate, dt=spec.dt, lub_taper=0.2)
+    W = dss.viscosity_weights(T, shear_rate=spec.shear_rate)
+    s = dss.Suspension(g["x"], g["a"], g["box"], p, ids=g["ids"])
+    ck = s.save()
+    s.adjoint(T, W, ckpt_every=20)                    # warm-up (allocations, graphs)
+    s.load(ck)
+    time_steps(s, T)                                   # forward alone, same steps
+    s.load(ck)
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = s.adjoint(T, W, ckpt_every=20)
+    t_adj = time.perf_counter() - t0
+    s.load(ck)
+    t_fwd = time_steps(s, T) * 1e-3
+    s.close()
+    return {"value": n * T / t_adj, "unit": "particle-steps/s (forward + reverse)",
+            "seconds": t_adj, "forward_seconds": t_fwd, "reverse_over_forward": t_adj / t_fwd,
+            "config": {"workload": spec.name, "n": n, "steps": T, "checkpoint_every": 20,
+                       "precision": "mixed forward, FP64 reverse", "lub_taper": 0.2,
+                       "objective": "time-averaged relative viscosity"},
+            "J": r["J"], "dJ": dict(zip(("kn", "kt", "gamma_n", "mu", "delta_lub"), r["params"].tolist())),
+            "dJ_dx0_norm": float(np.linalg.norm(r["x0"]))}
+
+
 def run_reference(args, rank, world):
     spec, g = workload(args.workload, 0)
     if rank != 0:
@@ -316,6 +374,12 @@ def main():
 
     modes = [] if args.modes in ("", "none") else args.modes.split(",")
     batch = None
+    extra_inputs = {}
+    if "poly1m" in modes:
+        from paper_2108_01013_gb300 import synth
+        extra_inputs["poly1m"] = workload("c3", rank)
+    if "adjoint" in modes:
+        extra_inputs["adjoint"] = workload("c5", rank)
     if "batched" in modes:
         # packed by spawned worker processes before the first CUDA call
         from paper_2108_01013_gb300 import synth
@@ -400,8 +464,16 @@ def main():
         del flush
         if batch is not None:
             extra["batched"] = mode_batched(dss, batch, bspec, args, stream)
+        if "poly1m" in extra_inputs:
+            sp, gp = extra_inputs.pop("poly1m")
+            extra["poly1m"] = mode_poly1m(dss, gp, sp, args)
+        if "adjoint" in extra_inputs:
+            sp, gp = extra_inputs.pop("adjoint")
+            extra["adjoint"] = mode_adjoint(dss, gp, sp, args)
         if world > 1:
             for m in extra.values():
+                if "ms_per_step" not in m:
+                    continue
                 tt = torch.tensor([m["ms_per_step"]], device=dev, dtype=torch.float64)
                 dist.all_reduce(tt, op=dist.ReduceOp.MAX)
                 m["value"] = m["value"] * m["ms_per_step"] / float(tt.item()) * world
