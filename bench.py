@@ -109,6 +109,8 @@ def parse():
                          "polydisperse, mixed and FP64), adjoint (gradient of the 200-step "
                          "viscosity of 20k spheres); 'none' for none")
     ap.add_argument("--mode-steps", type=int, default=400)
+    ap.add_argument("--batch-instances", type=int, default=256,
+                    help="instances of the batched mode (the first K of the 256-instance sweep)")
     return ap.parse_args()
 
 
@@ -384,6 +386,9 @@ def main():
         # packed by spawned worker processes before the first CUDA call
         from paper_2108_01013_gb300 import synth
         bspec = synth.BATCH_SPECS["c4"]
+        if args.batch_instances != bspec.K:
+            from dataclasses import replace
+            bspec = replace(bspec, K=args.batch_instances)
         if rank:
             from dataclasses import replace
             bspec = replace(bspec, seed=bspec.seed + 1000 * rank)
@@ -416,10 +421,11 @@ def main():
         clocks.start()
         t_wall = time.perf_counter()
         t_gpu_ms = 0.0
-        for _ in range(args.steps):
-            flush.fill_(1.0)                       # L2 flush between timed steps
-            s.step(1)
-            t_gpu_ms += s.last_step_ms()           # events around the step graph
+        with torch.cuda.nvtx.range("headline"):
+            for _ in range(args.steps):
+                flush.fill_(1.0)                   # L2 flush between timed steps
+                s.step(1)
+                t_gpu_ms += s.last_step_ms()       # events around the step graph
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
@@ -460,16 +466,20 @@ def main():
         s.close()
         extra = {}
         if "fp64" in modes:
-            extra["fp64"] = mode_fp64(dss, g, spec, kw, args, flush, stream)
+            with torch.cuda.nvtx.range("fp64"):
+                extra["fp64"] = mode_fp64(dss, g, spec, kw, args, flush, stream)
         del flush
         if batch is not None:
-            extra["batched"] = mode_batched(dss, batch, bspec, args, stream)
+            with torch.cuda.nvtx.range("batched"):
+                extra["batched"] = mode_batched(dss, batch, bspec, args, stream)
         if "poly1m" in extra_inputs:
             sp, gp = extra_inputs.pop("poly1m")
-            extra["poly1m"] = mode_poly1m(dss, gp, sp, args)
+            with torch.cuda.nvtx.range("poly1m"):
+                extra["poly1m"] = mode_poly1m(dss, gp, sp, args)
         if "adjoint" in extra_inputs:
             sp, gp = extra_inputs.pop("adjoint")
-            extra["adjoint"] = mode_adjoint(dss, gp, sp, args)
+            with torch.cuda.nvtx.range("adjoint"):
+                extra["adjoint"] = mode_adjoint(dss, gp, sp, args)
         if world > 1:
             for m in extra.values():
                 if "ms_per_step" not in m:
