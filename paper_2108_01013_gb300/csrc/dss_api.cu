@@ -413,6 +413,8 @@ int create_handle(dss_handle** out, const dss_params* p, int K, const int64_t* n
   h->n = total;
   h->user_stream = (cudaStream_t)cuda_stream;
   if (cudaGetDevice(&h->device) != cudaSuccess) { dss_destroy(h); return DSS_ERR_CUDA; }
+  if (cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess || h->sms < 1)
+    h->sms = 1;
   // work runs on the caller's stream; for the legacy default stream (NULL),
   // where graph capture is not allowed, on a stream of our own ordered after it
   if (cuda_stream) {

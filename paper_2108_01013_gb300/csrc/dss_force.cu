@@ -273,8 +273,11 @@ __device__ __forceinline__ double owner_bits<double>(int o) { return __longlong_
 __device__ __forceinline__ int bits_owner(float v) { return __float_as_int(v); }
 __device__ __forceinline__ int bits_owner(double v) { return (int)__double_as_longlong(v); }
 
-template <bool MIXED>
-__global__ void __launch_bounds__(kPairThreads, MIXED ? 3 : 2)
+// MINB: resident blocks per SM the register budget is cut for (a grid that
+// fills more than three blocks per SM gains from the fourth; smaller grids
+// run faster with the larger budget).
+template <bool MIXED, int MINB>
+__global__ void __launch_bounds__(kPairThreads, MINB)
 k_pairs(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ sgk, StateBuf s, ListBuf W,
         ListBuf H, const float4* __restrict__ posf, void* __restrict__ own_v, int* __restrict__ bw_count,
         void* __restrict__ bw_v, double* __restrict__ spart, DevStatus* st, int adv) {
@@ -622,14 +625,19 @@ void launch_forces(dss_handle* h, int stbuf, int work_list, int hist_list, int a
   const int pb = pair_grid_blocks(h);
   const bool mixed = h->g.precision == DSS_MIXED;
   prof_mark(h, 5);
-  if (mixed)
-    k_pairs<true><<<pb, kPairThreads, 0, h->stream>>>(h->g, h->ig, h->sg, h->st[stbuf], h->lb[work_list],
-                                                      h->lb[hist_list], h->posf, h->own, h->bw_count,
-                                                      h->bw_rec, h->spart, h->status, adv);
+  const bool big = pb > 3 * h->sms;
+  if (mixed && big)
+    k_pairs<true, 4><<<pb, kPairThreads, 0, h->stream>>>(h->g, h->ig, h->sg, h->st[stbuf], h->lb[work_list],
+                                                         h->lb[hist_list], h->posf, h->own, h->bw_count,
+                                                         h->bw_rec, h->spart, h->status, adv);
+  else if (mixed)
+    k_pairs<true, 3><<<pb, kPairThreads, 0, h->stream>>>(h->g, h->ig, h->sg, h->st[stbuf], h->lb[work_list],
+                                                         h->lb[hist_list], h->posf, h->own, h->bw_count,
+                                                         h->bw_rec, h->spart, h->status, adv);
   else
-    k_pairs<false><<<pb, kPairThreads, 0, h->stream>>>(h->g, h->ig, h->sg, h->st[stbuf], h->lb[work_list],
-                                                       h->lb[hist_list], h->posf, h->own, h->bw_count,
-                                                       h->bw_rec, h->spart, h->status, adv);
+    k_pairs<false, 2><<<pb, kPairThreads, 0, h->stream>>>(h->g, h->ig, h->sg, h->st[stbuf], h->lb[work_list],
+                                                          h->lb[hist_list], h->posf, h->own, h->bw_count,
+                                                          h->bw_rec, h->spart, h->status, adv);
   prof_mark(h, 6);
   const int gb = (n + kThreads - 1) / kThreads;
   if (mixed)

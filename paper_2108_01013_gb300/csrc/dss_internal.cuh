@@ -364,6 +364,7 @@ struct dss_handle {
   int64_t prof_count;
   double* a_by_id;           // n radii in id order (dss_load_state)
   int device;
+  int sms;                   // streaming multiprocessors of the device
   bool have_state;
   bool sized;
   double a_min, a_max;
