@@ -144,12 +144,13 @@ k_adj_tape_pairs(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restric
       if (q < 0)
         for (int m = 0; m < H.count[oj]; ++m)
           if (H.list[(int64_t)oj * g.M + m] == oi) { q = H.start[oj] + m; break; }
-      if (q >= 0 && H.cflag[q]) {
+      const Xi4 hv = q >= 0 ? H.xi[q] : Xi4{0.0, 0.0, 0.0, 0.0};
+      if (hv.w != 0.0) {
         const double sgn = idi < idj ? 1.0 : -1.0;
         pold = q;
-        xo[0] = sgn * H.xi[q];
-        xo[1] = sgn * H.xi[g.pcap + q];
-        xo[2] = sgn * H.xi[2 * g.pcap + q];
+        xo[0] = sgn * hv.x;
+        xo[1] = sgn * hv.y;
+        xo[2] = sgn * hv.z;
       }
     }
     t.pold[p] = pold;

@@ -36,7 +36,7 @@ void free_buffers(dss_handle* h) {
     dfree(s.vf); dfree(s.wf); dfree(s.posl); dfree(s.cellc);
     memset(&s, 0, sizeof(s));
     ListBuf& L = h->lb[b];
-    dfree(L.count); dfree(L.list); dfree(L.start); dfree(L.xi); dfree(L.cflag); dfree(L.slot_of_id);
+    dfree(L.count); dfree(L.list); dfree(L.start); dfree(L.xi); dfree(L.slot_of_id);
     dfree(L.id_of_slot);
     memset(&L, 0, sizeof(L));
   }
@@ -82,21 +82,14 @@ int alloc_pair_buffers(dss_handle* h, int64_t pcap, bool keep_hist) {
   int r;
   for (int b = 0; b < 2; ++b) {
     ListBuf& L = h->lb[b];
-    double* xi = nullptr;
-    unsigned char* cf = nullptr;
-    if ((r = dalloc(h, &xi, 3 * (size_t)pcap))) return r;
-    if ((r = dalloc(h, &cf, (size_t)pcap))) return r;
+    Xi4* xi = nullptr;
+    if ((r = dalloc(h, &xi, (size_t)pcap))) return r;
     if (keep_hist && b == h->hist && L.xi && old > 0) {
-      for (int c = 0; c < 3; ++c)
-        CK(cudaMemcpyAsync(xi + c * pcap, L.xi + c * old, sizeof(double) * old,
-                           cudaMemcpyDeviceToDevice, h->stream));
-      CK(cudaMemcpyAsync(cf, L.cflag, old, cudaMemcpyDeviceToDevice, h->stream));
+      CK(cudaMemcpyAsync(xi, L.xi, sizeof(Xi4) * old, cudaMemcpyDeviceToDevice, h->stream));
       CK(cudaStreamSynchronize(h->stream));
     }
     dfree(L.xi);
-    dfree(L.cflag);
     L.xi = xi;
-    L.cflag = cf;
   }
   h->pcap = pcap;
   h->g.pcap = pcap;
@@ -202,6 +195,7 @@ __global__ void k_scatter_by_id(int n, const double* __restrict__ src, const int
 }
 
 __global__ void k_set_nstep(DevStatus* st, long long nstep) {
+  st->w[ST_IDORDER] = 0;
   st->w[ST_NSTEP_LO] = (int)(unsigned)(nstep & 0xffffffffll);
   st->w[ST_NSTEP_HI] = (int)(nstep >> 32);
   st->w[ST_STEPS] = 0;
@@ -243,15 +237,16 @@ __global__ void k_attach_history(Geo g, StateBuf s, ListBuf L, const long long* 
       if (keys[m] == key) { f = m; break; }
       if (keys[m] < key) l = m + 1; else r = m - 1;
     }
+    Xi4 v;
     if (f >= 0) {
-      L.xi[p] = xi[3 * (int64_t)f];
-      L.xi[g.pcap + p] = xi[3 * (int64_t)f + 1];
-      L.xi[2 * g.pcap + p] = xi[3 * (int64_t)f + 2];
-      L.cflag[p] = 1;
+      v.x = xi[3 * (int64_t)f];
+      v.y = xi[3 * (int64_t)f + 1];
+      v.z = xi[3 * (int64_t)f + 2];
+      v.w = 1.0;
     } else {
-      L.xi[p] = 0.0; L.xi[g.pcap + p] = 0.0; L.xi[2 * g.pcap + p] = 0.0;
-      L.cflag[p] = 0;
+      v.x = v.y = v.z = v.w = 0.0;
     }
+    L.xi[p] = v;
   }
 }
 
@@ -260,7 +255,8 @@ __global__ void k_history_out(Geo g, ListBuf L, long long* __restrict__ keys,
   const int n = g.n;
   const int P = L.start[n];
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
-    if (!L.cflag[p]) continue;
+    const Xi4 v = L.xi[p];
+    if (v.w == 0.0) continue;
     int lo = 0, hi = n;
     while (hi - lo > 1) {
       int mid = (lo + hi) >> 1;
@@ -271,9 +267,9 @@ __global__ void k_history_out(Geo g, ListBuf L, long long* __restrict__ keys,
     int q = atomicAdd(counter, 1);
     if (q < cap) {
       keys[q] = a < b ? (a << 32) | b : (b << 32) | a;
-      xi[3 * (int64_t)q] = L.xi[p];
-      xi[3 * (int64_t)q + 1] = L.xi[g.pcap + p];
-      xi[3 * (int64_t)q + 2] = L.xi[2 * g.pcap + p];
+      xi[3 * (int64_t)q] = v.x;
+      xi[3 * (int64_t)q + 1] = v.y;
+      xi[3 * (int64_t)q + 2] = v.z;
     }
   }
 }
@@ -889,6 +885,8 @@ int dss_set_history(dss_handle* h, int64_t k, const int64_t* keys, const double*
   if (r) return r;
   if ((r = status_error(h))) { clear_err(h); return r; }
   h->hist = L;
+  // the new history's rows follow the committed (sorted) order
+  CK(cudaMemsetAsync(&h->status->w[ST_IDORDER], 0, sizeof(int), h->stream));
   return DSS_OK;
 }
 
@@ -942,6 +940,8 @@ int dss_load_state(dss_handle* h, const double* x, const double* u, const double
   CK(cudaMemcpyAsync(s.a, h->a_by_id, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, h->stream));
   CK(cudaMemcpyAsync(s.inst, h->inst_map, sizeof(int32_t) * h->n, cudaMemcpyDeviceToDevice, h->stream));
   k_iota_int<<<(int)((h->n + 255) / 256), 256, 0, h->stream>>>((int)h->n, s.id);
+  // the committed state is now in id order, not in the history's row order
+  CK(cudaMemsetAsync(&h->status->w[ST_IDORDER], 1, sizeof(int), h->stream));
   CK(cudaGetLastError());
   return DSS_OK;
 }

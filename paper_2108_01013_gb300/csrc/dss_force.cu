@@ -35,12 +35,21 @@ __device__ __forceinline__ int row_find(const int* row, int cnt, int target) {
   return -1;
 }
 
-// Tangential stretch of pair (idi, idj) at the last committed step, in the
-// lo -> hi orientation; zero when the pair was not in contact then.
-__device__ __forceinline__ void history_lookup(const Geo& g, const ListBuf& H, int idi, int idj,
-                                               double xo[3]) {
+// Where the particles of the current sorted order sit in the rows of the
+// committed history: perm (the sort's new -> previous index) when the sort's
+// source was in the history's row order, else the history's id -> row map.
+struct HistRef {
+  const int* perm;
+  int idorder;
+};
+
+// Tangential stretch of pair (i, j) (ids idi, idj) at the last committed
+// step, in the lo -> hi orientation; zero when the pair was not in contact.
+__device__ __forceinline__ void history_lookup(const Geo& g, const ListBuf& H, const HistRef& hr, int i,
+                                               int j, int idi, int idj, double xo[3]) {
   xo[0] = xo[1] = xo[2] = 0.0;
-  const int oi = H.slot_of_id[idi], oj = H.slot_of_id[idj];
+  const int oi = hr.idorder ? H.slot_of_id[idi] : hr.perm[i];
+  const int oj = hr.idorder ? H.slot_of_id[idj] : hr.perm[j];
   int64_t pold = -1;
   int k = row_find(H.list + (int64_t)oi * g.M, H.count[oi], oj);
   if (k >= 0) {
@@ -49,10 +58,13 @@ __device__ __forceinline__ void history_lookup(const Geo& g, const ListBuf& H, i
     k = row_find(H.list + (int64_t)oj * g.M, H.count[oj], oi);
     if (k >= 0) pold = (int64_t)H.start[oj] + k;
   }
-  if (pold >= 0 && H.cflag[pold]) {
-    xo[0] = H.xi[pold];
-    xo[1] = H.xi[g.pcap + pold];
-    xo[2] = H.xi[2 * g.pcap + pold];
+  if (pold >= 0) {
+    const Xi4 v = H.xi[pold];
+    if (v.w != 0.0) {
+      xo[0] = v.x;
+      xo[1] = v.y;
+      xo[2] = v.z;
+    }
   }
 }
 
@@ -83,7 +95,8 @@ struct PairRes {
 
 // FP64 pair from the state (exact FP64 throughout).
 __device__ __forceinline__ PairRes<double> pair_eval_fp64(const Geo& g, const InstGeo& I, const StateBuf& s,
-                                                         const ListBuf& H, double off, int i, int j) {
+                                                         const ListBuf& H, const HistRef& hr, double off,
+                                                         int i, int j) {
   const int n = g.n;
   const double xi = s.x[i], yi = s.x[n + i], zi = s.x[2 * n + i];
   const double xj = s.x[j], yj = s.x[n + j], zj = s.x[2 * n + j];
@@ -101,7 +114,7 @@ __device__ __forceinline__ PairRes<double> pair_eval_fp64(const Geo& g, const In
   double xo[3] = {0.0, 0.0, 0.0};
   const double rr = sqrt(dot(r, r));
   if (rr - (ai + aj) < 0.0) {
-    history_lookup(g, H, idi, idj, xo);
+    history_lookup(g, H, hr, i, j, idi, idj, xo);
     xo[0] *= sgn; xo[1] *= sgn; xo[2] *= sgn;
   }
   const double Om = -0.5 * I.gdot;
@@ -132,7 +145,8 @@ __device__ __forceinline__ PairRes<double> pair_eval_fp64(const Geo& g, const In
 // stretch is carried and updated in FP64; the rest of the pair arithmetic is
 // FP32, on velocities taken relative to the ambient flow.
 __device__ __forceinline__ PairRes<float> pair_eval_mixed(const Geo& g, const InstGeo& I, const StateBuf& s,
-                                                         const ListBuf& H, const StepGeo& sg,
+                                                         const ListBuf& H, const HistRef& hr,
+                                                         const StepGeo& sg,
                                                          const float4* __restrict__ posf, int i, int j) {
   const float gd = I.gdot_f;
   const float k6 = g.f.k6;
@@ -182,7 +196,7 @@ __device__ __forceinline__ PairRes<float> pair_eval_mixed(const Geo& g, const In
     const int idi = s.id[i], idj = s.id[j];
     const float sg = idi < idj ? 1.0f : -1.0f;   // stored (lo -> hi) vs i -> j orientation
     double xo[3];
-    history_lookup(g, H, idi, idj, xo);
+    history_lookup(g, H, hr, i, j, idi, idj, xo);
     // u_j(image) - u_i = (V_j - V_i) + gdot dy x
     const F3 du = (Vj - Vi) + f3(gd * r.y, 0.f, 0.f);
     const F3 wi = f3(Wi.x, Wi.y, Wi.z - 0.5f * gd), wj = f3(Wj.x, Wj.y, Wj.z - 0.5f * gd);
@@ -273,6 +287,34 @@ __device__ __forceinline__ double owner_bits<double>(int o) { return __longlong_
 __device__ __forceinline__ int bits_owner(float v) { return __float_as_int(v); }
 __device__ __forceinline__ int bits_owner(double v) { return (int)__double_as_longlong(v); }
 
+__device__ __forceinline__ void load_record(const float* b, float* v) {
+  const float4 p = reinterpret_cast<const float4*>(b)[0], q = reinterpret_cast<const float4*>(b)[1];
+  v[0] = p.x; v[1] = p.y; v[2] = p.z; v[3] = p.w; v[4] = q.x; v[5] = q.y; v[6] = q.z; v[7] = q.w;
+}
+__device__ __forceinline__ void load_record(const double* b, double* v) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const double2 p = reinterpret_cast<const double2*>(b)[k];
+    v[2 * k] = p.x;
+    v[2 * k + 1] = p.y;
+  }
+}
+
+// A partner record (8 values, 32 B in FP32 / 64 B in FP64, slot-aligned) in
+// wide stores.
+__device__ __forceinline__ void store_record(float* b, float a0, float a1, float a2, float a3, float a4,
+                                             float a5, float a6) {
+  reinterpret_cast<float4*>(b)[0] = make_float4(a0, a1, a2, a3);
+  reinterpret_cast<float4*>(b)[1] = make_float4(a4, a5, a6, 0.f);
+}
+__device__ __forceinline__ void store_record(double* b, double a0, double a1, double a2, double a3,
+                                             double a4, double a5, double a6) {
+  reinterpret_cast<double2*>(b)[0] = make_double2(a0, a1);
+  reinterpret_cast<double2*>(b)[1] = make_double2(a2, a3);
+  reinterpret_cast<double2*>(b)[2] = make_double2(a4, a5);
+  reinterpret_cast<double2*>(b)[3] = make_double2(a6, 0.0);
+}
+
 // MINB: resident blocks per SM the register budget is cut for (a grid that
 // fills more than three blocks per SM gains from the fourth; smaller grids
 // run faster with the larger budget).
@@ -280,13 +322,15 @@ template <bool MIXED, int MINB>
 __global__ void __launch_bounds__(kPairThreads, MINB)
 k_pairs(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ sgk, StateBuf s, ListBuf W,
         ListBuf H, const float4* __restrict__ posf, void* __restrict__ own_v, int* __restrict__ bw_count,
-        void* __restrict__ bw_v, double* __restrict__ spart, DevStatus* st, int adv) {
+        void* __restrict__ bw_v, double* __restrict__ spart, DevStatus* st, int adv,
+        const int* __restrict__ perm) {
   using R = typename std::conditional<MIXED, float, double>::type;
   if (dev_err(st)) return;
   R* __restrict__ own = static_cast<R*>(own_v);
   R* __restrict__ bw = static_cast<R*>(bw_v);
   const int n = g.n;
   const int P = W.start[n];
+  const HistRef hr{perm, *((volatile const int*)&st->w[ST_IDORDER])};
   if (P > g.pcap) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       st->w[ST_NPAIRS] = P;
@@ -340,24 +384,19 @@ k_pairs(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ sgk, 
         const InstGeo& I = ig[inst];
         const StepGeo sg = sgk[inst];
         PairRes<R> q;
-        if constexpr (MIXED) q = pair_eval_mixed(g, I, s, H, sg, posf, i, j);
-        else q = pair_eval_fp64(g, I, s, H, sg.off, i, j);
+        if constexpr (MIXED) q = pair_eval_mixed(g, I, s, H, hr, sg, posf, i, j);
+        else q = pair_eval_fp64(g, I, s, H, hr, sg.off, i, j);
         v[0] = q.F[0]; v[1] = q.F[1]; v[2] = q.F[2];
         v[3] = q.Ti[0]; v[4] = q.Ti[1]; v[5] = q.Ti[2];
         // partner's share, appended to its row with the owner's index
         const int slot = atomicAdd(&bw_count[j], 1);
         if (slot < g.M) {
           R* b = bw + ((int64_t)j * g.M + slot) * kSlot;
-          b[0] = -q.F[0]; b[1] = -q.F[1]; b[2] = -q.F[2];
-          b[3] = q.Tj[0]; b[4] = q.Tj[1]; b[5] = q.Tj[2];
-          b[6] = owner_bits<R>(i);
+          store_record(b, -q.F[0], -q.F[1], -q.F[2], q.Tj[0], q.Tj[1], q.Tj[2], owner_bits<R>(i));
         } else {
           set_err(st, DSS_ERR_CAPACITY);
         }
-        W.xi[p] = q.xi[0];
-        W.xi[g.pcap + p] = q.xi[1];
-        W.xi[2 * g.pcap + p] = q.xi[2];
-        W.cflag[p] = (unsigned char)q.contact;
+        W.xi[p] = Xi4{q.xi[0], q.xi[1], q.xi[2], q.contact ? 1.0 : 0.0};
         ncont += q.contact;
         // Eq. 9: S^C = r (x) F^C, S^L = sym(r (x) F^L), F on the owner
         if (inst != cur_inst) {
@@ -460,6 +499,7 @@ __device__ void commit_step(const Geo& g, DevStatus* st, const int* __restrict__
   if (dev_err(st)) return;
   st->w[ST_NPAIRS] = start[g.n];
   if (step) {
+    st->w[ST_IDORDER] = 0;   // the new history rows follow the committed order
     st->w[ST_STEPS] += 1;
     int64_t ns = dev_nstep(st) + 1;
     st->w[ST_NSTEP_LO] = (int)(uint32_t)(ns & 0xffffffffll);
@@ -496,7 +536,8 @@ __device__ __forceinline__ void gather_one(const Geo& g, const InstGeo* __restri
       const int o = bits_owner(row[q * kSlot + 6]);
       if (o > prev && o < best) { best = o; bs = q; }
     }
-    const R* b = row + bs * kSlot;
+    R b[8];
+    load_record(row + bs * kSlot, b);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       F[c] += b[c];
@@ -629,15 +670,15 @@ void launch_forces(dss_handle* h, int stbuf, int work_list, int hist_list, int a
   if (mixed && big)
     k_pairs<true, 4><<<pb, kPairThreads, 0, h->stream>>>(h->g, h->ig, h->sg, h->st[stbuf], h->lb[work_list],
                                                          h->lb[hist_list], h->posf, h->own, h->bw_count,
-                                                         h->bw_rec, h->spart, h->status, adv);
+                                                         h->bw_rec, h->spart, h->status, adv, h->perm);
   else if (mixed)
     k_pairs<true, 3><<<pb, kPairThreads, 0, h->stream>>>(h->g, h->ig, h->sg, h->st[stbuf], h->lb[work_list],
                                                          h->lb[hist_list], h->posf, h->own, h->bw_count,
-                                                         h->bw_rec, h->spart, h->status, adv);
+                                                         h->bw_rec, h->spart, h->status, adv, h->perm);
   else
     k_pairs<false, 2><<<pb, kPairThreads, 0, h->stream>>>(h->g, h->ig, h->sg, h->st[stbuf], h->lb[work_list],
                                                           h->lb[hist_list], h->posf, h->own, h->bw_count,
-                                                          h->bw_rec, h->spart, h->status, adv);
+                                                          h->bw_rec, h->spart, h->status, adv, h->perm);
   prof_mark(h, 6);
   const int gb = (n + kThreads - 1) / kThreads;
   if (mixed)

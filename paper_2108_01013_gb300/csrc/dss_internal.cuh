@@ -22,6 +22,7 @@ enum {
   ST_NSTEP_LO = 6,   // time step counter (64 bit, lo/hi)
   ST_NSTEP_HI = 7,
   ST_BADPOS = 8,     // set_state: positions outside the box
+  ST_IDORDER = 9,    // 1 after dss_load_state: the committed state is not in the history's row order
   ST_WORDS = 16
 };
 
@@ -294,12 +295,18 @@ struct StateBuf {
   int* cellc;   // n, mixed precision: cell coordinates packed cx | cy << 10 | cz << 20
 };
 
+// Tangential stretch of one listed pair and its contact flag (one 32-byte
+// load or store).
+struct __align__(32) Xi4 {
+  double x, y, z, w;
+};
+
 struct ListBuf {
   int* count;       // n half-list row lengths
   int* list;        // n*M partner sorted indices
   int* start;       // n+1 row offsets into the pair arrays (exclusive scan of count)
-  double* xi;       // 3*pcap tangential stretch (lo->hi orientation), per pair slot
-  unsigned char* cflag;  // pcap: 1 when the pair was in contact (d < 0)
+  Xi4* xi;          // pcap: tangential stretch (lo->hi orientation) per pair slot; w = 1
+                    // when the pair was in contact (d < 0), else 0
   int* slot_of_id;  // n: sorted index of each id in this list's index space
   int* id_of_slot;  // n: id of each sorted index of this list
 };

@@ -268,3 +268,31 @@ def test_error_reporting(env):
     with pytest.raises(dss.DssError) as e:
         dss.Suspension(g["x"], g["a"], box, dss.default_params(box), ids=ids)
     assert e.value.code == -1
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_load_state_keeps_history(env, precision):
+    """dss_load_state (the per-step upload of a caller that keeps its own
+    state) with the same values must leave the trajectory unchanged, bit for
+    bit: the contact history is then found through the id map rather than
+    the sort permutation."""
+    g = env["synth"].small(1500, 0.54, 8)
+    box = g["box"]
+    p = env["dss"].default_params(box, mu=1.0, shear_rate=3.0, precision=precision)
+    a = env["dss"].Suspension(g["x"], g["a"], box, p, ids=g["ids"])
+    b = env["dss"].Suspension(g["x"], g["a"], box, p, ids=g["ids"])
+    a.step(20)
+    b.step(20)
+    st = a.state()
+    a.load_state(st["x"], st["u"], st["w"], st["al"], st["aw"])
+    a.step(15)
+    b.step(15)
+    assert a.counters()["ncontacts"] > 50
+    sa, sb = a.state(), b.state()
+    for k in sa:
+        assert env["torch"].equal(sa[k], sb[k]), k
+    ka, xa = a.history()
+    kb, xb = b.history()
+    assert np.array_equal(ka, kb) and np.array_equal(xa, xb)
+    a.close()
+    b.close()
