@@ -126,7 +126,7 @@ k_adj_tape_pairs(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restric
   const int idi = s.id[i];
   for (int k = 0; k < cnt; ++k) {
     const int p = p0 + k;
-    const int j = W.list[(int64_t)i * g.M + k];
+    const int j = W.list[(int64_t)i * g.Ms + k];
     t.op[p] = i;
     t.pj[p] = j;
     double dx, dy, dz;
@@ -140,10 +140,10 @@ k_adj_tape_pairs(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restric
       const int oi = H.slot_of_id[idi], oj = H.slot_of_id[idj];
       int q = -1;
       for (int m = 0; m < H.count[oi]; ++m)
-        if (H.list[(int64_t)oi * g.M + m] == oj) { q = H.start[oi] + m; break; }
+        if (H.list[(int64_t)oi * g.Ms + m] == oj) { q = H.start[oi] + m; break; }
       if (q < 0)
         for (int m = 0; m < H.count[oj]; ++m)
-          if (H.list[(int64_t)oj * g.M + m] == oi) { q = H.start[oj] + m; break; }
+          if (H.list[(int64_t)oj * g.Ms + m] == oi) { q = H.start[oj] + m; break; }
       const Xi4 hv = q >= 0 ? H.xi[q] : Xi4{0.0, 0.0, 0.0, 0.0};
       if (hv.w != 0.0) {
         const double sgn = idi < idj ? 1.0 : -1.0;

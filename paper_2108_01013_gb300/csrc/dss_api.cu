@@ -117,7 +117,7 @@ int alloc_buffers(dss_handle* h) {
          (r = dalloc(h, &s.cellc, n))))
       return r;
     ListBuf& L = h->lb[b];
-    if ((r = dalloc(h, &L.count, n)) || (r = dalloc(h, &L.list, n * (size_t)h->g.M)) ||
+    if ((r = dalloc(h, &L.count, n)) || (r = dalloc(h, &L.list, n * (size_t)h->g.Ms)) ||
         (r = dalloc(h, &L.start, n + 1)) || (r = dalloc(h, &L.slot_of_id, n)) ||
         (r = dalloc(h, &L.id_of_slot, n)))
       return r;
@@ -228,7 +228,7 @@ __global__ void k_attach_history(Geo g, StateBuf s, ListBuf L, const long long* 
       int mid = (lo + hi) >> 1;
       if (L.start[mid] <= p) lo = mid; else hi = mid;
     }
-    const int j = L.list[(int64_t)lo * g.M + (p - L.start[lo])];
+    const int j = L.list[(int64_t)lo * g.Ms + (p - L.start[lo])];
     const long long a = s.id[lo], b = s.id[j];
     const long long key = a < b ? (a << 32) | b : (b << 32) | a;
     int l = 0, r = k - 1, f = -1;
@@ -262,7 +262,7 @@ __global__ void k_history_out(Geo g, ListBuf L, long long* __restrict__ keys,
       int mid = (lo + hi) >> 1;
       if (L.start[mid] <= p) lo = mid; else hi = mid;
     }
-    const int j = L.list[(int64_t)lo * g.M + (p - L.start[lo])];
+    const int j = L.list[(int64_t)lo * g.Ms + (p - L.start[lo])];
     const long long a = L.id_of_slot[lo], b = L.id_of_slot[j];
     int q = atomicAdd(counter, 1);
     if (q < cap) {
@@ -373,6 +373,7 @@ int geometry(dss_handle* h) {
   int M = p.capacity_M > 0 ? p.capacity_M : dss_capacity_estimate(h->a_min, h->a_max, p.a0);
   if (M <= 0) return DSS_ERR_ARG;
   g.M = M;
+  g.Ms = (M + 3) & ~3;   // row stride: rows start on 16-byte boundaries
   return DSS_OK;
 }
 

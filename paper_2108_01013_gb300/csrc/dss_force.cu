@@ -28,10 +28,17 @@ constexpr int kWarps = kPairThreads / 32;
 constexpr int kThreads = 128;
 constexpr int kSlot = 8;   // partner-row slot: F (3), T (3), owner index, pad
 
-// Position of `target` in a row (rows are in stencil visiting order); -1 if absent.
+// Position of `target` in a row (rows are in stencil visiting order and
+// start on 16-byte boundaries, so four entries come per load); -1 if absent.
 __device__ __forceinline__ int row_find(const int* row, int cnt, int target) {
-  for (int k = 0; k < cnt; ++k)
-    if (row[k] == target) return k;
+  const int4* r4 = reinterpret_cast<const int4*>(row);
+  for (int k = 0; k < cnt; k += 4) {
+    const int4 v = r4[k >> 2];
+    if (v.x == target) return k;
+    if (k + 1 < cnt && v.y == target) return k + 1;
+    if (k + 2 < cnt && v.z == target) return k + 2;
+    if (k + 3 < cnt && v.w == target) return k + 3;
+  }
   return -1;
 }
 
@@ -51,11 +58,11 @@ __device__ __forceinline__ void history_lookup(const Geo& g, const ListBuf& H, c
   const int oi = hr.idorder ? H.slot_of_id[idi] : hr.perm[i];
   const int oj = hr.idorder ? H.slot_of_id[idj] : hr.perm[j];
   int64_t pold = -1;
-  int k = row_find(H.list + (int64_t)oi * g.M, H.count[oi], oj);
+  int k = row_find(H.list + (int64_t)oi * g.Ms, H.count[oi], oj);
   if (k >= 0) {
     pold = (int64_t)H.start[oi] + k;
   } else {
-    k = row_find(H.list + (int64_t)oj * g.M, H.count[oj], oi);
+    k = row_find(H.list + (int64_t)oj * g.Ms, H.count[oj], oi);
     if (k >= 0) pold = (int64_t)H.start[oj] + k;
   }
   if (pold >= 0) {
@@ -379,7 +386,7 @@ k_pairs(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ sgk, 
       if (valid) {
         const int i = w0 + Lw;
         const int p = base + t;
-        const int j = W.list[(int64_t)i * g.M + kk];
+        const int j = W.list[(int64_t)i * g.Ms + kk];
         const int inst = s.inst[i];
         const InstGeo& I = ig[inst];
         const StepGeo sg = sgk[inst];
@@ -643,7 +650,7 @@ __global__ void k_pairs_out(Geo g, ListBuf W, long long* __restrict__ out) {
       int mid = (lo + hi) >> 1;
       if (W.start[mid] <= p) lo = mid; else hi = mid;
     }
-    const int j = W.list[(int64_t)lo * g.M + (p - W.start[lo])];
+    const int j = W.list[(int64_t)lo * g.Ms + (p - W.start[lo])];
     const int a = W.id_of_slot[lo], b = W.id_of_slot[j];
     out[2 * (int64_t)p] = a < b ? a : b;
     out[2 * (int64_t)p + 1] = a < b ? b : a;

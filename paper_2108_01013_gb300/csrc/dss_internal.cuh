@@ -45,6 +45,7 @@ struct Geo {
   int K;              // instances
   int ncell;          // cells of all instances
   int M;              // half-list capacity per particle
+  int Ms;             // row stride of the half lists (M rounded up to 4)
   int64_t pcap;       // pair capacity
   double kn, kt, mu;
   double eta0, rho;

@@ -78,7 +78,7 @@ k_enumerate(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ s
     e.i = i;
     e.off = sg.off;
     e.pi = posf[i];
-    e.row = L.list + (int64_t)i * g.M;
+    e.row = L.list + (int64_t)i * g.Ms;
     const int fsh = sg.fsh;
     const float offr = sg.offr_hi;
     const int nx = I.nc[0], ny = I.nc[1], nz = I.nc[2];
