@@ -45,7 +45,8 @@ void free_buffers(dss_handle* h) {
   dfree(h->cell_count); dfree(h->cell_start); dfree(h->tmp); dfree(h->spart);
   dfree(h->own); dfree(h->bw_count); dfree(h->bw_rec);
   h->own = nullptr; h->bw_count = nullptr; h->bw_rec = nullptr;
-  dfree(h->io3); dfree(h->io3b); dfree(h->io_id); dfree(h->scan_status); dfree(h->scan_ticket);
+  dfree(h->io3); dfree(h->io3b); dfree(h->io_id); dfree(h->stage);
+  h->stage = nullptr; dfree(h->scan_status); dfree(h->scan_ticket);
   dfree(h->sigma);
   dfree(h->sigma_sum);
   dfree(h->a_by_id);
@@ -128,6 +129,7 @@ int alloc_buffers(dss_handle* h) {
       (r = dalloc(h, &h->cell_count, (size_t)h->g.ncell)) ||
       (r = dalloc(h, &h->cell_start, (size_t)h->g.ncell + 1)) || (r = dalloc(h, &h->tmp, n)) ||
       (r = dalloc(h, &h->io3, 3 * n)) || (r = dalloc(h, &h->io3b, 3 * n)) ||
+      (r = dalloc(h, &h->stage, 15 * n)) ||
       (r = dalloc(h, &h->io_id, n)) || (r = dalloc(h, &h->sigma, 9 * (size_t)h->K)) ||
       (r = dalloc(h, &h->sigma_sum, 9 * (size_t)h->K)) || (r = dalloc(h, &h->a_by_id, n)) ||
       (r = dalloc(h, &h->inst_map, n)) || (r = dalloc(h, &h->ig, (size_t)h->K)) ||
@@ -184,14 +186,69 @@ int clear_err(dss_handle* h) {
   return DSS_OK;
 }
 
-__global__ void k_scatter_by_id(int n, const double* __restrict__ src, const int* __restrict__ id,
-                                double* __restrict__ dst) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
+// The committed state (sorted order) into id order, all five vectors in one
+// pass: dst[k] is device-accessible (device memory, mapped pinned host memory)
+// or the staging area; a null dst[k] is skipped.
+struct Dst5 {
+  double* d[5];
+};
+__global__ void k_state_out(int n, StateBuf s, Dst5 dst) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  int k = id[i];
-  dst[k] = src[i];
-  dst[n + k] = src[n + i];
-  dst[2 * n + k] = src[2 * n + i];
+  const int k = s.id[i];
+  const double* src[5] = {s.x, s.u, s.w, s.al, s.aw};
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    double* d = dst.d[q];
+    if (!d) continue;
+    d[k] = src[q][i];
+    d[n + k] = src[q][n + i];
+    d[2 * n + k] = src[q][2 * n + i];
+  }
+}
+
+// Coalesced copy of up to five 3n-vectors (staging -> device-accessible views).
+__global__ void k_copy5(int64_t m, Dst5 src, Dst5 dst) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m; t += (int64_t)gridDim.x * blockDim.x)
+#pragma unroll
+    for (int q = 0; q < 5; ++q)
+      if (dst.d[q]) dst.d[q][t] = src.d[q][t];
+}
+
+// dss_load_state in one pass: the five vectors from device-accessible views,
+// radii and instances in id order, ids = indices.
+struct Src5 {
+  const double* d[5];
+};
+__global__ void k_state_in(int n, Src5 src, StateBuf s, const double* __restrict__ a_by_id,
+                           const int* __restrict__ inst_map) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double* dst[5] = {s.x, s.u, s.w, s.al, s.aw};
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    dst[q][i] = src.d[q][i];
+    dst[q][n + i] = src.d[q][n + i];
+    dst[q][2 * n + i] = src.d[q][2 * n + i];
+  }
+  s.a[i] = a_by_id[i];
+  s.inst[i] = inst_map[i];
+  s.id[i] = i;
+}
+
+// Address through which a kernel may access a caller's buffer: device and
+// managed memory as is, pinned host memory through its mapped device
+// pointer; nullptr for pageable host memory (copy engines only).
+const void* device_view(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (at.type == cudaMemoryTypeDevice) return p;
+  if ((at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeManaged) && at.devicePointer)
+    return at.devicePointer;
+  return nullptr;
 }
 
 __global__ void k_set_nstep(DevStatus* st, long long nstep) {
@@ -312,11 +369,6 @@ int accumulate_profile(dss_handle* h) {
   }
   h->prof_count += 1;
   return DSS_OK;
-}
-
-__global__ void k_iota_int(int n, int* __restrict__ v) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) v[i] = i;
 }
 
 int status_error(dss_handle* h) {
@@ -654,13 +706,43 @@ int dss_get_state(dss_handle* h, double* x, double* u, double* w, double* alpha_
   ENTER(h);
   const int n = (int)h->n;
   const StateBuf& s = h->st[h->cur];
-  const double* src[5] = {s.x, s.u, s.w, s.al, s.aw};
-  double* dst[5] = {x, u, w, alpha_lin, alpha_ang};
+  double* out[5] = {x, u, w, alpha_lin, alpha_ang};
+  // device outputs are written in place by the scatter; host outputs go
+  // through the staging area, then out by a coalesced copy kernel (mapped
+  // pinned memory) or the copy engine (pageable memory)
+  Dst5 direct, staged, views;
   for (int k = 0; k < 5; ++k) {
-    if (!dst[k]) continue;
-    k_scatter_by_id<<<(n + 255) / 256, 256, 0, h->stream>>>(n, src[k], s.id, h->io3);
-    CK(cudaMemcpyAsync(dst[k], h->io3, sizeof(double) * 3 * n, cudaMemcpyDefault, h->stream));
+    direct.d[k] = staged.d[k] = views.d[k] = nullptr;
+    if (!out[k]) continue;
+    cudaPointerAttributes at;
+    const bool is_dev = cudaPointerGetAttributes(&at, out[k]) == cudaSuccess && at.type == cudaMemoryTypeDevice;
+    cudaGetLastError();
+    if (is_dev) {
+      direct.d[k] = out[k];
+    } else {
+      staged.d[k] = h->stage + (size_t)k * 3 * n;
+      views.d[k] = static_cast<double*>(const_cast<void*>(device_view(out[k])));
+    }
   }
+  Dst5 all = direct;
+  for (int k = 0; k < 5; ++k)
+    if (staged.d[k]) all.d[k] = staged.d[k];
+  k_state_out<<<(n + 255) / 256, 256, 0, h->stream>>>(n, s, all);
+  Dst5 src_c, dst_c;
+  bool any_view = false;
+  for (int k = 0; k < 5; ++k) {
+    src_c.d[k] = dst_c.d[k] = nullptr;
+    if (!staged.d[k]) continue;
+    if (views.d[k]) {
+      src_c.d[k] = staged.d[k];
+      dst_c.d[k] = views.d[k];
+      any_view = true;
+    } else {
+      CK(cudaMemcpyAsync(out[k], staged.d[k], sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, h->stream));
+    }
+  }
+  if (any_view) k_copy5<<<std::min((3 * n + 255) / 256, 8 * h->sms), 256, 0, h->stream>>>(3 * (int64_t)n, src_c, dst_c);
+  CK(cudaGetLastError());
   CK(cudaStreamSynchronize(h->stream));
   return DSS_OK;
 }
@@ -933,14 +1015,19 @@ int dss_load_state(dss_handle* h, const double* x, const double* u, const double
   ENTER(h);
   const size_t b = sizeof(double) * 3 * (size_t)h->n;
   StateBuf& s = h->st[h->cur];
-  CK(cudaMemcpyAsync(s.x, x, b, cudaMemcpyDefault, h->stream));
-  CK(cudaMemcpyAsync(s.u, u, b, cudaMemcpyDefault, h->stream));
-  CK(cudaMemcpyAsync(s.w, w, b, cudaMemcpyDefault, h->stream));
-  CK(cudaMemcpyAsync(s.al, alpha_lin, b, cudaMemcpyDefault, h->stream));
-  CK(cudaMemcpyAsync(s.aw, alpha_ang, b, cudaMemcpyDefault, h->stream));
-  CK(cudaMemcpyAsync(s.a, h->a_by_id, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, h->stream));
-  CK(cudaMemcpyAsync(s.inst, h->inst_map, sizeof(int32_t) * h->n, cudaMemcpyDeviceToDevice, h->stream));
-  k_iota_int<<<(int)((h->n + 255) / 256), 256, 0, h->stream>>>((int)h->n, s.id);
+  const double* in[5] = {x, u, w, alpha_lin, alpha_ang};
+  // device and mapped pinned host buffers are read by one kernel; pageable
+  // host buffers go through the staging area with the copy engine first
+  Src5 src;
+  for (int k = 0; k < 5; ++k) {
+    src.d[k] = static_cast<const double*>(device_view(in[k]));
+    if (!src.d[k]) {
+      double* st = h->stage + (size_t)k * 3 * h->n;
+      CK(cudaMemcpyAsync(st, in[k], b, cudaMemcpyHostToDevice, h->stream));
+      src.d[k] = st;
+    }
+  }
+  k_state_in<<<(int)((h->n + 255) / 256), 256, 0, h->stream>>>((int)h->n, src, s, h->a_by_id, h->inst_map);
   // the committed state is now in id order, not in the history's row order
   CK(cudaMemsetAsync(&h->status->w[ST_IDORDER], 1, sizeof(int), h->stream));
   CK(cudaGetLastError());

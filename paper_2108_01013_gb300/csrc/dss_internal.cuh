@@ -418,6 +418,7 @@ struct dss_handle {
   // user-order io scratch
   double* io3;       // 3n
   double* io3b;      // 3n
+  double* stage;     // 15n: staging of the five state vectors for host transfers
   int* io_id;        // n
   int last_list;     // list written by the last enumeration
   // graphs: one per (cur, hist) combination
