@@ -72,7 +72,7 @@ KERNELS_PER_STEP = len(ALG_BYTES)
 # unchanged (profiles/ncu_full_c2_mixed_100k.md).
 NCU_TRAFFIC = {
     ("k_pairs", "mixed"): (21_715_968, ("dss_force.cu", "dss_internal.cuh", "dss_pair_model.cuh"),
-                           "8ccae4d4e3877b20"),
+                           "206cb468ed859283"),
 }
 
 

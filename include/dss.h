@@ -283,6 +283,14 @@ int dss_adjoint(dss_handle *h, int64_t nsteps, int32_t ckpt_every, const double 
                 int32_t initial_forces, double *J, double *dJ_dparams, double *dJ_dx0,
                 double *dJ_du0, double *dJ_dw0, double *dJ_dalpha0, double *dJ_dbeta0);
 
+/* Self-test of the bounded device waits (failure detection without a GPU
+ * fault): runs one warp of the decoupled look-back used by the scans on a
+ * predecessor that never publishes.  The wait gives up after its time limit
+ * (0.5 s) and records DSS_ERR_TIMEOUT, which this call returns (DSS_OK would
+ * mean the wait did not notice).  The context stays usable.  cuda_stream:
+ * stream to run on (NULL: legacy default stream); synchronises it. */
+int dss_selftest_bounded_wait(void *cuda_stream);
+
 /* Bytes of device memory the handle holds. */
 int64_t dss_device_bytes(const dss_handle *h);
 

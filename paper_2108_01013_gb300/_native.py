@@ -104,6 +104,7 @@ SIGNATURES = {
     "dss_save": (c_int, [c_void_p, _vp, POINTER(c_size_t)]),
     "dss_load": (c_int, [c_void_p, _vp, c_size_t]),
     "dss_autotune": (c_int, [c_void_p, c_int32, c_int32, _dp, _dp, _dp]),
+    "dss_selftest_bounded_wait": (c_int, [c_void_p]),
     "dss_adjoint": (c_int, [c_void_p, c_int64, c_int32, _vp, c_int32, _dp, _dp, _vp, _vp, _vp, _vp, _vp]),
     "dss_set_state": (c_int, [c_void_p, _vp, _vp, _vp, _vp, _vp, _vp, _vp, c_int64]),
     "dss_get_state": (c_int, [c_void_p, _vp, _vp, _vp, _vp, _vp]),

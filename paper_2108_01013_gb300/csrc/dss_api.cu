@@ -251,6 +251,11 @@ const void* device_view(const void* p) {
   return nullptr;
 }
 
+// Tile 1 of a look-back whose tile 0 never publishes: the wait must give up.
+__global__ void k_selftest_wait(unsigned long long* status, DevStatus* st) {
+  lookback_warp(status, 1, 0, st);
+}
+
 __global__ void k_set_nstep(DevStatus* st, long long nstep) {
   st->w[ST_IDORDER] = 0;
   st->w[ST_NSTEP_LO] = (int)(unsigned)(nstep & 0xffffffffll);
@@ -1360,6 +1365,34 @@ int dss_adjoint(dss_handle* h, int64_t nsteps, int32_t ckpt_every, const double*
   CK(cudaStreamSynchronize(h->stream));
   if (J) *J = Jacc;
   return dss_load(h, ck_end.data(), ck_end.size());
+}
+
+int dss_selftest_bounded_wait(void* cuda_stream) {
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  unsigned long long* status = nullptr;
+  DevStatus* st = nullptr;
+  if (cudaMalloc((void**)&status, 2 * sizeof(unsigned long long)) != cudaSuccess) return DSS_ERR_CUDA;
+  if (cudaMalloc((void**)&st, sizeof(DevStatus)) != cudaSuccess) {
+    cudaFree(status);
+    return DSS_ERR_CUDA;
+  }
+  DevStatus host;
+  int r = DSS_OK;
+  if (cudaMemsetAsync(status, 0, 2 * sizeof(unsigned long long), s) != cudaSuccess ||
+      cudaMemsetAsync(st, 0, sizeof(DevStatus), s) != cudaSuccess) {
+    r = DSS_ERR_CUDA;
+  } else {
+    k_selftest_wait<<<1, 32, 0, s>>>(status, st);
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(&host, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      r = DSS_ERR_CUDA;
+    else
+      r = host.w[ST_ERR];
+  }
+  cudaFree(status);
+  cudaFree(st);
+  return r;
 }
 
 int64_t dss_device_bytes(const dss_handle* h) { return h ? h->bytes : 0; }

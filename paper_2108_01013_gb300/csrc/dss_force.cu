@@ -615,12 +615,20 @@ k_gather(Geo g, const InstGeo* __restrict__ ig, StateBuf s, const void* __restri
          const int* __restrict__ bw_count, const void* __restrict__ bw_v, double* __restrict__ Fout,
          double* __restrict__ Tout, DevStatus* st, int mode, const double* __restrict__ spart,
          double* sigma, double* sigma_sum, const int* __restrict__ start, unsigned int* done_blocks) {
-  // block k < K also reduces the stress of instance k (the grid has at least
-  // two blocks per instance)
-  if (blockIdx.x < (unsigned)g.K) inst_stress(g, ig[blockIdx.x], spart, sigma + 9 * blockIdx.x);
-  // no early exit on an earlier error: every block must reach the counter;
-  // the step is committed only when no error is set
-  gather_one<MIXED>(g, ig, s, own_v, bw_count, bw_v, Fout, Tout, st, mode);
+  // An error set before this kernel (an earlier kernel of the step, or an
+  // earlier step of the same dss_step call, whose successors still replay)
+  // means this step is void: touch no state, since the buffer this step
+  // would write can be the committed one.  Every block still reaches the
+  // counter below.
+  __shared__ int s_err0;
+  if (threadIdx.x == 0) s_err0 = dev_err(st);
+  __syncthreads();
+  if (!s_err0) {
+    // block k < K also reduces the stress of instance k (the grid has at
+    // least two blocks per instance)
+    if (blockIdx.x < (unsigned)g.K) inst_stress(g, ig[blockIdx.x], spart, sigma + 9 * blockIdx.x);
+    gather_one<MIXED>(g, ig, s, own_v, bw_count, bw_v, Fout, Tout, st, mode);
+  }
   // the last block to finish commits the step
   __shared__ bool last;
   __threadfence();

@@ -206,6 +206,14 @@ __device__ __forceinline__ float pair_delta_f(const Geo& g, float ai, float aj) 
 // ------------------------------------------------------------------------
 constexpr unsigned long long kLbAgg = 1ull << 32;
 constexpr unsigned long long kLbPre = 2ull << 32;
+constexpr unsigned long long kWaitLimitNs = 500000000ull;   // a device wait gives up after 0.5 s
+
+// Global nanosecond timer (the %globaltimer special register).
+__device__ __forceinline__ unsigned long long dev_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 __device__ __forceinline__ int lookback_warp(unsigned long long* status, int tile, int agg,
                                              DevStatus* st) {
@@ -217,6 +225,7 @@ __device__ __forceinline__ int lookback_warp(unsigned long long* status, int til
   if (lane == 0) atomicExch(&status[tile], kLbAgg | (unsigned)agg);
   int prefix = 0;
   int t = tile - 1;
+  const unsigned long long t0 = dev_ns();
   long long spins = 0;
   while (true) {
     const int idx = t - lane;                 // lane 0: nearest predecessor
@@ -227,7 +236,11 @@ __device__ __forceinline__ int lookback_warp(unsigned long long* status, int til
     const int p = pre ? __ffs(pre) - 1 : 32;
     const unsigned need = p == 32 ? 0xffffffffu : (p == 31 ? 0xffffffffu : ((2u << p) - 1u));
     if (not_ready & need) {
-      if (++spins > (1ll << 22)) {
+      // bounded: a predecessor that never publishes (an earlier failure)
+      // ends the wait with DSS_ERR_TIMEOUT instead of a hang
+      ++spins;
+      const bool late = (spins & 63) == 0 && dev_ns() - t0 > kWaitLimitNs;
+      if (__any_sync(0xffffffffu, late) || spins > (1ll << 24)) {
         if (lane == 0) set_err(st, DSS_ERR_TIMEOUT);
         break;
       }
