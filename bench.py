@@ -281,16 +281,23 @@ def mode_poly1m(dss, g, spec, args):
     out = {"config": {"workload": spec.name, "n": n, "phi": spec.phi, "radii": "log-uniform [1, 10]",
                       "mu": spec.mu, "l2": "working set > L2 (no flush)",
                       "packing": "random insertion + %d relaxation sweeps" % spec.max_iter}}
-    for prec, steps in (("mixed", args.mode_steps // 2), ("fp64", args.mode_steps // 8)):
-        p = dss.default_params(g["box"], precision=prec, mu=spec.mu, kn=spec.kn,
-                               shear_rate=spec.shear_rate, dt=spec.dt)
+    cmin = (2.0 + 0.05) * float(g["a"].max()) * (1 + 1e-9)
+    for prec, steps in (("mixed", args.mode_steps // 2), ("fp64", args.mode_steps // 8),
+                        ("mixed_size_classes", args.mode_steps // 4)):
+        # one cell list (cells >= 2 a_max + delta); for comparison the size
+        # classes of Sec. II A (cells of half that edge, larger stencils for the
+        # larger particles)
+        classes = prec.endswith("size_classes")
+        p = dss.default_params(g["box"], precision=prec.split("_")[0], mu=spec.mu, kn=spec.kn,
+                               shear_rate=spec.shear_rate, dt=spec.dt, cell_mode=1 if classes else 0,
+                               cell_size=0.5 * cmin if classes else 0.0)
         s = dss.Suspension(g["x"], g["a"], g["box"], p, ids=g["ids"])
         time_steps(s, 3)
         t = time_steps(s, steps)
         c = s.counters()
         out[prec] = {"value": n * steps / (t * 1e-3), "unit": "particle-steps/s", "ms_per_step": t / steps,
                      "steps": steps, "device_gb": round(s.device_bytes() / 1e9, 1), "pairs": c["npairs"],
-                     "M": c["M"], "kernels_ms": profile_pass(s, 5)}
+                     "M": c["M"], "cells": list(c["ncell"]), "kernels_ms": profile_pass(s, 5)}
         s.close()
     return out
 

@@ -79,6 +79,11 @@ typedef struct dss_params {
                                    t = clamp((delta_ij - d) / (w delta_ij), 0, 1), so it
                                    vanishes continuously at the cutoff (an extension for
                                    differentiation, not in the paper); 0: hard cutoff */
+  int32_t cell_mode;            /* 0: cells >= 2 a_max + delta_max, one list (Sec. II A);
+                                   1: smaller cells, particles binned by size class, larger
+                                   classes search larger stencils (Sec. II A, for highly
+                                   polydisperse suspensions); cell_size 0: auto */
+  int32_t reserved_;
 } dss_params;
 
 typedef struct dss_handle dss_handle;

@@ -33,6 +33,7 @@ void free_buffers(dss_handle* h) {
   for (int b = 0; b < 2; ++b) {
     StateBuf& s = h->st[b];
     dfree(s.x); dfree(s.u); dfree(s.w); dfree(s.al); dfree(s.aw); dfree(s.a); dfree(s.id); dfree(s.inst);
+    dfree(s.cls);
     dfree(s.vf); dfree(s.wf); dfree(s.posl); dfree(s.cellc);
     memset(&s, 0, sizeof(s));
     ListBuf& L = h->lb[b];
@@ -51,6 +52,8 @@ void free_buffers(dss_handle* h) {
   dfree(h->sigma_sum);
   dfree(h->a_by_id);
   dfree(h->inst_map);
+  dfree(h->cls_map);
+  h->cls_map = nullptr;
   dfree(h->ig);
   dfree(h->sg);
   h->sigma_sum = nullptr;
@@ -111,7 +114,7 @@ int alloc_buffers(dss_handle* h) {
     StateBuf& s = h->st[b];
     if ((r = dalloc(h, &s.x, 3 * n)) || (r = dalloc(h, &s.u, 3 * n)) || (r = dalloc(h, &s.w, 3 * n)) ||
         (r = dalloc(h, &s.al, 3 * n)) || (r = dalloc(h, &s.aw, 3 * n)) || (r = dalloc(h, &s.a, n)) ||
-        (r = dalloc(h, &s.id, n)) || (r = dalloc(h, &s.inst, n)))
+        (r = dalloc(h, &s.id, n)) || (r = dalloc(h, &s.inst, n)) || (r = dalloc(h, &s.cls, n)))
       return r;
     if (h->p.precision == DSS_MIXED &&
         ((r = dalloc(h, &s.vf, n)) || (r = dalloc(h, &s.wf, n)) || (r = dalloc(h, &s.posl, n)) ||
@@ -132,7 +135,8 @@ int alloc_buffers(dss_handle* h) {
       (r = dalloc(h, &h->stage, 15 * n)) ||
       (r = dalloc(h, &h->io_id, n)) || (r = dalloc(h, &h->sigma, 9 * (size_t)h->K)) ||
       (r = dalloc(h, &h->sigma_sum, 9 * (size_t)h->K)) || (r = dalloc(h, &h->a_by_id, n)) ||
-      (r = dalloc(h, &h->inst_map, n)) || (r = dalloc(h, &h->ig, (size_t)h->K)) ||
+      (r = dalloc(h, &h->inst_map, n)) || (r = dalloc(h, &h->cls_map, n)) ||
+      (r = dalloc(h, &h->ig, (size_t)h->K)) ||
       (r = dalloc(h, &h->sg, (size_t)h->K)) || (r = dalloc(h, &h->done_blocks, 1)))
     return r;
   CK(cudaMemsetAsync(h->sigma, 0, 9 * sizeof(double) * h->K, h->stream));
@@ -221,7 +225,7 @@ struct Src5 {
   const double* d[5];
 };
 __global__ void k_state_in(int n, Src5 src, StateBuf s, const double* __restrict__ a_by_id,
-                           const int* __restrict__ inst_map) {
+                           const int* __restrict__ inst_map, const unsigned char* __restrict__ cls_map) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double* dst[5] = {s.x, s.u, s.w, s.al, s.aw};
@@ -233,6 +237,7 @@ __global__ void k_state_in(int n, Src5 src, StateBuf s, const double* __restrict
   }
   s.a[i] = a_by_id[i];
   s.inst[i] = inst_map[i];
+  s.cls[i] = cls_map[i];
   s.id[i] = i;
 }
 
@@ -383,16 +388,67 @@ int status_error(dss_handle* h) {
 
 // Cell grid of every instance (Sec. II A: cells of edge >= the largest
 // interaction range, 2 a_max + delta_max); cells are numbered instance-major.
+// Interaction range beyond contact of the largest pair a particle of radius a
+// can own (partners no larger than itself).
+double dmax_of(const dss_params& p, double a) {
+  return p.lub_cutoff_mode == 1 ? p.delta_lub * p.a0 : p.delta_lub * a;
+}
+
+// Size class of a particle of radius a on cells of edge cs: the particle's own
+// pairs reach at most (class + 1) cells.  Rounded up by a relative 1e-9 so
+// that rounding never shortens a reach.
+int class_of(const dss_params& p, double a, double cs) {
+  const double need = (2.0 * a + dmax_of(p, a)) * (1.0 + 1e-9) / cs;
+  int c = (int)std::ceil(need) - 1;
+  return c < 0 ? 0 : c;
+}
+
+// Cell grid of every instance (Sec. II A).  Mode 0: cells of edge >= the
+// largest interaction range, 2 a_max + delta_max, one cell list, the 27-cell
+// (half: 14-cell) stencil.  Mode 1 (highly polydisperse suspensions): smaller
+// cells, particles binned by size class; a class-c particle searches its own
+// class in the half stencil of reach rtab[c][c] and each smaller class in the
+// full stencil of reach rtab[c][c2].  Bins are numbered instance-major, then
+// class, then cell.
 int geometry(dss_handle* h) {
   Geo& g = h->g;
   const dss_params& p = h->p;
-  double dmax = p.lub_cutoff_mode == 1 ? p.delta_lub * p.a0 : p.delta_lub * h->a_max;
-  double range = 2.0 * h->a_max + dmax;
+  double range = 2.0 * h->a_max + dmax_of(p, h->a_max);
   double cmin = range * (1.0 + 1e-9) + 1e-12;
-  if (p.cell_size > 0.0) {
+  double cs = cmin;
+  int C = 1;
+  if (p.cell_mode == 1) {
+    const double rmin = (2.0 * h->a_min + dmax_of(p, h->a_min)) * (1.0 + 1e-9) + 1e-12;
+    cs = p.cell_size > 0.0 ? p.cell_size : std::max(rmin, cmin / 4.0);
+    if (cs < rmin) return DSS_ERR_ARG;
+    C = class_of(p, h->a_max, cs) + 1;
+    if (C > 8) return DSS_ERR_ARG;
+  } else if (p.cell_size > 0.0) {
     if (p.cell_size < cmin) return DSS_ERR_ARG;
-    cmin = p.cell_size;
+    cs = p.cell_size;
   }
+  // reach table from the largest radius of each class
+  double A[8];
+  for (int c = 0; c < C; ++c)
+    A[c] = p.lub_cutoff_mode == 1 ? ((c + 1) * cs / (1.0 + 1e-9) - p.delta_lub * p.a0) * 0.5
+                                  : (c + 1) * cs / ((1.0 + 1e-9) * (2.0 + p.delta_lub));
+  if (C == 1) A[0] = h->a_max;
+  int reach = 1;
+  memset(g.rtab, 0, sizeof(g.rtab));
+  for (int c = 0; c < C; ++c)
+    for (int c2 = 0; c2 <= c; ++c2) {
+      const double dpair = p.lub_cutoff_mode == 1 ? p.delta_lub * p.a0 : p.delta_lub * 0.5 * (A[c] + A[c2]);
+      // A[] already carries the 1e-9 margin of class_of: the ranges of the
+      // class pair stay below (A + A2 + dpair), so no further margin
+      int R = (int)std::ceil((A[c] + A[c2] + dpair) / cs);
+      if (c2 == c) R = std::min(R, c + 1);
+      if (C == 1) R = 1;
+      if (R < 1) R = 1;
+      g.rtab[c][c2] = (unsigned char)R;
+      reach = std::max(reach, R);
+    }
+  g.nclass = C;
+  g.reach = reach;
   int64_t cells = 0, pos = 0;
   for (int k = 0; k < h->K; ++k) {
     InstGeo& I = h->ig_host[k];
@@ -400,7 +456,7 @@ int geometry(dss_handle* h) {
     for (int d = 0; d < 3; ++d) {
       I.L[d] = L[d];
       I.halfL[d] = 0.5 * L[d];
-      I.nc[d] = (int)std::floor(L[d] / cmin);
+      I.nc[d] = (int)std::floor(L[d] / cs);
       if (I.nc[d] < 1) I.nc[d] = 1;
       I.cs[d] = L[d] / I.nc[d];
       I.inv_cs[d] = 1.0 / I.cs[d];
@@ -409,13 +465,15 @@ int geometry(dss_handle* h) {
       I.cs_lo[d] = (float)(I.cs[d] - (double)I.csf[d]);
       I.invL[d] = 1.0 / L[d];
     }
-    if (I.nc[0] < 4 || I.nc[1] < 3 || I.nc[2] < 3) return DSS_ERR_BOX;
+    // the stencil may not meet itself across the periodic box
+    if (I.nc[0] < 2 * reach + 2 || I.nc[1] < 2 * reach + 1 || I.nc[2] < 2 * reach + 1) return DSS_ERR_BOX;
     if (I.nc[0] > 1023 || I.nc[1] > 1023 || I.nc[2] > 1023) return DSS_ERR_ARG;   // packed coords
     const int64_t nck = (int64_t)I.nc[0] * I.nc[1] * I.nc[2];
-    if (cells + nck > (int64_t)2000000000) return DSS_ERR_ARG;
+    if (cells + C * nck > (int64_t)2000000000) return DSS_ERR_ARG;
     I.cell_base = (int)cells;
-    I.ncell = (int)nck;
-    cells += nck;
+    I.ncell_layer = (int)nck;
+    I.ncell = (int)(C * nck);
+    cells += C * nck;
     const double csmax = std::max(I.cs[0], std::max(I.cs[1], I.cs[2]));
     I.r2_margin = (float)(1e-4 * csmax * csmax);
     I.p_begin = (int)pos;
@@ -427,6 +485,7 @@ int geometry(dss_handle* h) {
     I.gn_f = (float)I.gn;
   }
   g.ncell = (int)cells;
+  h->cell_edge = cs;
   int M = p.capacity_M > 0 ? p.capacity_M : dss_capacity_estimate(h->a_min, h->a_max, p.a0);
   if (M <= 0) return DSS_ERR_ARG;
   g.M = M;
@@ -439,7 +498,7 @@ bool valid_params(const dss_params* p) {
          (p->rho > 0) && (p->delta_lub >= 0) && (p->lub_eps > 0) && (p->a0 > 0) && (p->dt > 0) &&
          std::isfinite(p->shear_rate) && (p->lub_cutoff_mode == 0 || p->lub_cutoff_mode == 1) &&
          (p->precision == DSS_FP64 || p->precision == DSS_MIXED) &&
-         (p->lub_taper >= 0.0 && p->lub_taper < 1.0);
+         (p->lub_taper >= 0.0 && p->lub_taper < 1.0) && (p->cell_mode == 0 || p->cell_mode == 1);
 }
 
 // Common constructor: K instances of n[k] particles in boxes box[3k..3k+2]
@@ -659,6 +718,19 @@ int dss_set_state(dss_handle* h, const double* x, const double* a, const int32_t
   CK(cudaMemcpyAsync(h->ig, h->ig_host, sizeof(InstGeo) * h->K, cudaMemcpyHostToDevice, h->stream));
   CK(cudaMemcpyAsync(h->inst_map, imap.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, h->stream));
   CK(cudaMemcpyAsync(s.inst, h->inst_map, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, h->stream));
+  {
+    // size classes (all 0 with one cell list), by index and by id
+    std::vector<unsigned char> cu(n), cid(n);
+    for (int64_t i = 0; i < n; ++i) {
+      int c = h->g.nclass > 1 ? class_of(h->p, ha[i], h->cell_edge) : 0;
+      if (c > h->g.nclass - 1) c = h->g.nclass - 1;
+      cu[i] = (unsigned char)c;
+      cid[hid[i]] = (unsigned char)c;
+    }
+    CK(cudaMemcpyAsync(s.cls, cu.data(), n, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->cls_map, cid.data(), n, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+  }
   CK(cudaMemsetAsync(h->sigma_sum, 0, 9 * sizeof(double) * h->K, h->stream));
   CK(cudaMemcpyAsync(s.x, hx.data(), sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->stream));
   CK(cudaMemcpyAsync(s.a, ha.data(), sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
@@ -1032,7 +1104,8 @@ int dss_load_state(dss_handle* h, const double* x, const double* u, const double
       src.d[k] = st;
     }
   }
-  k_state_in<<<(int)((h->n + 255) / 256), 256, 0, h->stream>>>((int)h->n, src, s, h->a_by_id, h->inst_map);
+  k_state_in<<<(int)((h->n + 255) / 256), 256, 0, h->stream>>>((int)h->n, src, s, h->a_by_id, h->inst_map,
+                                                               h->cls_map);
   // the committed state is now in id order, not in the history's row order
   CK(cudaMemsetAsync(&h->status->w[ST_IDORDER], 1, sizeof(int), h->stream));
   CK(cudaGetLastError());

@@ -158,22 +158,25 @@ __device__ __forceinline__ PairRes<float> pair_eval_mixed(const Geo& g, const In
   const float gd = I.gdot_f;
   const float k6 = g.f.k6;
   // double-float separation from cell-local hi/lo words and the cell offset
-  // (listed pairs are one cell apart at most; a pair across y = L_y has its
-  // owner in the top row and its partner in row 0, image shifted by off)
+  // (listed pairs are at most `reach` cells apart along y and z; a pair whose
+  // rows differ by more crosses y = L_y, its image shifted by +-off along x)
   const float4 pi = posf[i], pj = posf[j], li = s.posl[i], lj = s.posl[j];
   const int ci = s.cellc[i], cj = s.cellc[j];
   const int nx = I.nc[0], ny = I.nc[1], nz = I.nc[2];
-  const int cyi = (ci >> 10) & 1023, cyj = (cj >> 10) & 1023;
-  const bool le = cyi == ny - 1 && cyj == 0;
-  int wx = (cj & 1023) - (ci & 1023) + (le ? sg.fsh : 0);
+  const int R = g.reach;
+  int wy = ((cj >> 10) & 1023) - ((ci >> 10) & 1023);
+  const int le = wy < -R ? 1 : (wy > R ? -1 : 0);
+  wy += le * ny;
+  int wx = (cj & 1023) - (ci & 1023) + le * sg.fsh;
   wx %= nx;
   if (wx < 0) wx += nx;
-  if (wx >= nx - (le ? 2 : 1)) wx -= nx;
-  const int wy = le ? 1 : cyj - cyi;
+  // the image row spans x offsets -R-1..R (above) or -R..R+1 (below)
+  if (le == -1 ? 2 * wx > nx : 2 * wx >= nx) wx -= nx;
   int wz = (cj >> 20) - (ci >> 20);
-  if (wz > 1) wz -= nz; else if (wz < -1) wz += nz;
+  if (wz > R) wz -= nz; else if (wz < -R) wz += nz;
   FF cx = FF{(float)wx * I.csf[0], (float)wx * I.cs_lo[0]};
-  if (le) cx = ff_add(cx, FF{sg.offr_hi, sg.offr_lo});
+  if (le == 1) cx = ff_add(cx, FF{sg.offr_hi, sg.offr_lo});
+  else if (le == -1) cx = ff_add(cx, FF{-sg.offr_hi, -sg.offr_lo});
   const FF dxf = ff_add(two_sum(pj.x, -pi.x), ff_add(cx, FF{lj.x - li.x, 0.f}));
   const FF dyf = ff_add(two_sum(pj.y, -pi.y),
                         ff_add(FF{(float)wy * I.csf[1], (float)wy * I.cs_lo[1]}, FF{lj.y - li.y, 0.f}));

@@ -43,7 +43,10 @@ struct DevStatus {
 struct Geo {
   int n;              // particles of all instances
   int K;              // instances
-  int ncell;          // cells of all instances
+  int ncell;          // cell bins of all instances (classes x cells)
+  int nclass;         // particle size classes (1: one cell list, cells >= 2 a_max + delta)
+  int reach;          // largest stencil reach in cells of any class pair
+  unsigned char rtab[8][8];   // rtab[c][c2], c2 <= c: reach of class c searching class c2
   int M;              // half-list capacity per particle
   int Ms;             // row stride of the half lists (M rounded up to 4)
   int64_t pcap;       // pair capacity
@@ -73,7 +76,8 @@ struct InstGeo {
   float halfLf[3];
   float r2_margin;              // FP32 prefilter margin on r^2 (absolute)
   int nc[3];
-  int cell_base, ncell;
+  int cell_base, ncell;        // first bin and bins (= classes x ncell_layer)
+  int ncell_layer;             // cells of one class layer (nc[0] nc[1] nc[2])
   int p_begin, p_end;
   double gdot, gn;              // shear rate, normal dashpot
   float gdot_f, gn_f;
@@ -186,7 +190,9 @@ __device__ __forceinline__ int prefilter(const InstGeo& g, float4 pi, float4 pj,
 __device__ __forceinline__ void stencil_shift(const InstGeo& g, int ox, int oy, int oz, int le,
                                               int fsh, float offr, float& cx, float& cy,
                                               float& cz) {
-  cx = le == 1 ? (float)(ox + fsh) * g.csf[0] + offr : (float)ox * g.csf[0];
+  // le = 1: image one box above (shifted by +off), -1: one box below (-off)
+  cx = le == 1 ? (float)(ox + fsh) * g.csf[0] + offr
+               : (le == -1 ? (float)(ox - fsh) * g.csf[0] - offr : (float)ox * g.csf[0]);
   cy = (float)oy * g.csf[1];
   cz = (float)oz * g.csf[2];
 }
@@ -303,6 +309,7 @@ struct StateBuf {
   double* a;    // n radius
   int* id;      // n persistent id
   int* inst;    // n instance index
+  unsigned char* cls;  // n size class (stencil reach), see Geo::rtab
   float4* vf;   // n, mixed precision: FP32 velocity relative to U_inf (xyz)
   float4* wf;   // n, mixed precision: FP32 angular velocity relative to Omega_inf (xyz)
   float4* posl; // n, mixed precision: low words of the cell-local position and radius
@@ -389,6 +396,7 @@ struct dss_handle {
   bool have_state;
   bool sized;
   double a_min, a_max;
+  double cell_edge;          // cell edge the grid was built for
   Geo g;
   // state: cur holds the committed state; the other buffer is scratch
   StateBuf st[2];
@@ -420,6 +428,7 @@ struct dss_handle {
   double* sigma_sum; // 9K: sum over committed steps since the last reset
   int64_t mean_steps;         // steps summed in sigma_sum
   int* inst_map;     // n: instance of each index in instance-major (id) order
+  unsigned char* cls_map;   // n: size class of each id
   unsigned int* done_blocks;  // last-block counter of the gather (reset by that block)
   // scans
   unsigned long long* scan_status;  // tile status words (2 scans)

@@ -159,6 +159,151 @@ k_enumerate(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ s
   __syncthreads();
   if (i < n) L.start[i] = s_prefix + s_warp[wid] + incl - v;
 }
+
+// Size classes (Sec. II A: cells smaller than 2 a_max, a larger stencil for
+// the larger particles).  Owner i of class c takes the partners of its own
+// class from the half stencil of reach R = rtab[c][c] (own bin after i; the
+// rest of the own row in +x; the rows z+1..z+R of its y layer; the layers
+// y+1..y+R), and the partners of every smaller class c2 from the full stencil
+// of reach rtab[c][c2] in that class's layer of bins: each pair is found
+// once, by its larger member (or by the half stencil within a class).  Rows
+// crossing y = L_y (either way) cover the x range shifted by the
+// Lees-Edwards offset.
+__global__ void __launch_bounds__(kThreads, 8)
+k_enumerate_classes(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ sgk, StateBuf s,
+                    const float4* __restrict__ posf, const int* __restrict__ cellid,
+                    const int* __restrict__ cell_start, ListBuf L, int* __restrict__ bw_count,
+                    unsigned long long* scan_status, int* scan_ticket, DevStatus* st) {
+  if (dev_err(st)) return;
+  __shared__ int s_tile;
+  __shared__ int s_warp[kThreads / 32];
+  __shared__ int s_prefix;
+  if (threadIdx.x == 0) s_tile = atomicAdd(scan_ticket, 1);
+  __syncthreads();
+  const int tile = s_tile;
+  const int i = tile * kThreads + threadIdx.x;
+  const int n = g.n;
+  EnumCtx e;
+  e.cnt = 0;
+  e.band = 0;
+  if (i < n) {
+    const int inst = s.inst[i];
+    const InstGeo& I = ig[inst];
+    const StepGeo sg = sgk[inst];
+    e.g = &g;
+    e.I = &I;
+    e.s = &s;
+    e.posf = posf;
+    e.i = i;
+    e.off = sg.off;
+    e.pi = posf[i];
+    e.row = L.list + (int64_t)i * g.Ms;
+    const int fsh = sg.fsh;
+    const float offr = sg.offr_hi;
+    const int nx = I.nc[0], ny = I.nc[1], nz = I.nc[2];
+    const int layer = I.ncell_layer;
+    const int cls = s.cls[i];
+    const int c = (cellid[i] - I.cell_base) % layer;
+    const int cx = c % nx, cy = (c / nx) % ny, cz = c / (nx * ny);
+    // own bin, partners after i
+    scan_range(e, i + 1, cell_start[cellid[i] + 1], 0.f, 0.f, 0.f);
+    for (int c2 = cls; c2 >= 0; --c2) {
+      const int R = g.rtab[cls][c2];
+      const bool half = c2 == cls;
+      const int lb = I.cell_base + c2 * layer;
+      for (int oy = half ? 0 : -R; oy <= R; ++oy) {
+        const int yy = cy + oy;
+        const int le = yy >= ny ? 1 : (yy < 0 ? -1 : 0);
+        const int qy = le == 1 ? yy - ny : (le == -1 ? yy + ny : yy);
+        for (int oz = (half && oy == 0) ? 0 : -R; oz <= R; ++oz) {
+          const int qz = wrapi(cz + oz, nz);
+          int xa, xb;
+          if (half && oy == 0 && oz == 0) {
+            xa = 1;
+            xb = R;
+          } else if (le == 1) {
+            xa = -R - 1 - fsh;
+            xb = R - fsh;
+          } else if (le == -1) {
+            xa = -R + fsh;
+            xb = R + 1 + fsh;
+          } else {
+            xa = -R;
+            xb = R;
+          }
+          // the row's cells are adjacent bins (split where x wraps): one
+          // candidate range per piece, most of them empty on small cells
+          const int rowq = lb + (qz * ny + qy) * nx;
+          int ox = xa;
+          while (ox <= xb) {
+            const int x0 = wrapi(cx + ox, nx);
+            const int m = min(xb - ox + 1, nx - x0);
+            const int q0 = rowq + x0;
+            const int lo = cell_start[q0], hi = cell_start[q0 + m];
+            if (lo < hi) {
+              int k = 0, kend = cell_start[q0 + 1];
+              float cxo, cyo, czo;
+              stencil_shift(I, ox, oy, oz, le, fsh, offr, cxo, cyo, czo);
+              for (int j = lo; j < hi; ++j) {
+                if (j >= kend) {
+                  do {
+                    ++k;
+                    kend = cell_start[q0 + k + 1];
+                  } while (j >= kend);
+                  stencil_shift(I, ox + k, oy, oz, le, fsh, offr, cxo, cyo, czo);
+                }
+                scan_range(e, j, j + 1, cxo, cyo, czo);
+              }
+            }
+            ox += m;
+          }
+        }
+      }
+    }
+    L.count[i] = e.cnt < g.M ? e.cnt : g.M;
+    if (e.cnt > g.M) set_err(st, DSS_ERR_CAPACITY);
+    bw_count[i] = 0;
+    const int id = s.id[i];
+    L.slot_of_id[id] = i;
+    L.id_of_slot[i] = id;
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int m = e.cnt, b = e.band;
+  for (int d = 16; d > 0; d >>= 1) {
+    m = max(m, __shfl_xor_sync(0xffffffffu, m, d));
+    b += __shfl_xor_sync(0xffffffffu, b, d);
+  }
+  if (lane == 0) {
+    atomicMax(&st->w[ST_MAXROW], m);
+    if (b) atomicAdd(&st->w[ST_BAND], b);
+  }
+  const int v = i < n ? (e.cnt < g.M ? e.cnt : g.M) : 0;
+  int incl = v;
+  for (int d = 1; d < 32; d <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += t;
+  }
+  if (lane == 31) s_warp[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    int run = 0;
+    if (lane == 0) {
+      for (int w = 0; w < kThreads / 32; ++w) {
+        const int t = s_warp[w];
+        s_warp[w] = run;
+        run += t;
+      }
+    }
+    const int agg = __shfl_sync(0xffffffffu, run, 0);
+    const int prefix = lookback_warp(scan_status, tile, agg, st);
+    if (lane == 0) {
+      s_prefix = prefix;
+      if ((tile + 1) * kThreads >= n) L.start[n] = prefix + agg;
+    }
+  }
+  __syncthreads();
+  if (i < n) L.start[i] = s_prefix + s_warp[wid] + incl - v;
+}
 }  // namespace
 
 int enum_tiles_for(int n) { return (n + kThreads - 1) / kThreads; }
@@ -167,8 +312,13 @@ void launch_enumerate(dss_handle* h, int stbuf, int dst_list, int adv) {
   const int n = (int)h->n;
   ListBuf& L = h->lb[dst_list];
   prof_mark(h, 4);
-  k_enumerate<<<enum_tiles_for(n), kThreads, 0, h->stream>>>(
-      h->g, h->ig, h->sg, h->st[stbuf], h->posf, h->cellid, h->cell_start, L, h->bw_count,
-      h->scan_status + h->scan_tiles_max, h->scan_ticket + 1, h->status, adv);
+  if (h->g.nclass > 1)
+    k_enumerate_classes<<<enum_tiles_for(n), kThreads, 0, h->stream>>>(
+        h->g, h->ig, h->sg, h->st[stbuf], h->posf, h->cellid, h->cell_start, L, h->bw_count,
+        h->scan_status + h->scan_tiles_max, h->scan_ticket + 1, h->status);
+  else
+    k_enumerate<<<enum_tiles_for(n), kThreads, 0, h->stream>>>(
+        h->g, h->ig, h->sg, h->st[stbuf], h->posf, h->cellid, h->cell_start, L, h->bw_count,
+        h->scan_status + h->scan_tiles_max, h->scan_ticket + 1, h->status, adv);
   h->last_list = dst_list;
 }

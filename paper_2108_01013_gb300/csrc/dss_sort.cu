@@ -71,11 +71,12 @@ __device__ __forceinline__ Pred predict_one(const Geo& g, const InstGeo& I, cons
   return r;
 }
 
-__device__ __forceinline__ int cell_key(const InstGeo& I, double x, double y, double z) {
+// Bin of a particle: its instance's bins, its size class's layer, its cell.
+__device__ __forceinline__ int cell_key(const InstGeo& I, int cls, double x, double y, double z) {
   int cx = cell_coord(x, I.inv_cs[0], I.nc[0]);
   int cy = cell_coord(y, I.inv_cs[1], I.nc[1]);
   int cz = cell_coord(z, I.inv_cs[2], I.nc[2]);
-  return I.cell_base + (cz * I.nc[1] + cy) * I.nc[0] + cx;
+  return I.cell_base + cls * I.ncell_layer + (cz * I.nc[1] + cy) * I.nc[0] + cx;
 }
 
 // 1. key + warp-aggregated histogram
@@ -121,7 +122,7 @@ k_key_hist(Geo g, const InstGeo* __restrict__ ig, StepGeo* __restrict__ sg, Stat
     pred[4 * n + i] = p.uy;
     pred[5 * n + i] = p.uz;
   }
-  int k = cell_key(I, p.x, p.y, p.z);
+  int k = cell_key(I, s.cls[i], p.x, p.y, p.z);
   unsigned act = __activemask();
   unsigned peers = __match_any_sync(act, k);
   int lane = threadIdx.x & 31;
@@ -193,6 +194,7 @@ k_rank_gather(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__
   dst.a[f] = a;
   dst.id[f] = id;
   dst.inst[f] = inst;
+  dst.cls[f] = src.cls[o];
   if (g.precision == DSS_MIXED) {
     // FP32 copies relative to the ambient flow for the FP32 pair arithmetic:
     // u - U_inf(x) and w - Omega_inf are O(gdot a), free of O(gdot L) terms
@@ -202,7 +204,7 @@ k_rank_gather(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__
   }
   // cell-local position (FP32 for the enumeration prefilter; in mixed
   // precision also the low words, for double-float pair geometry)
-  const int kl = k - I.cell_base;
+  const int kl = (k - I.cell_base) % I.ncell_layer;
   int cx = kl % I.nc[0];
   int cy = (kl / I.nc[0]) % I.nc[1];
   int cz = kl / (I.nc[0] * I.nc[1]);

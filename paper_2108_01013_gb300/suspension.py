@@ -18,7 +18,7 @@ from . import _native as nat
 def default_params(box=None, *, kn=1e4, kt=None, gamma_n=None, mu=0.5, eta0=1.0, rho=1.0,
                    delta_lub=0.05, lub_eps=1e-3, a0=1.0, lub_cutoff_mode=0, precision="fp64",
                    shear_rate=1.0, dt=1e-4, cell_size=0.0, capacity_M=0, pair_capacity=0,
-                   lub_taper=0.0):
+                   lub_taper=0.0, cell_mode=0):
     """Model parameters; kt defaults to kn/2 and gamma_n to 1e-7 kn / gdot."""
     p = nat.Params()
     p.kn = kn
@@ -33,6 +33,7 @@ def default_params(box=None, *, kn=1e4, kt=None, gamma_n=None, mu=0.5, eta0=1.0,
     p.shear_rate, p.dt = shear_rate, dt
     p.cell_size, p.capacity_M, p.pair_capacity = cell_size, capacity_M, pair_capacity
     p.lub_taper = lub_taper
+    p.cell_mode = cell_mode
     return p
 
 

@@ -5,7 +5,7 @@ full O(N^2) problem, so it checks sampled outputs it computes one by one: the
 complete neighbour set of sampled particles (bit-exact; the largest and the
 smallest particles are always sampled) and the force and torque on them, at
 the initial state and after steps with contact history, in FP64 and mixed
-precision."""
+precision, with one cell list and with size classes."""
 import numpy as np
 import pytest
 
@@ -39,11 +39,12 @@ def relerr(a, b):
     return np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b))
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-5)])
-def test_c3_sampled_neighbours_and_forces(env, precision, tol):
+@pytest.mark.parametrize("precision,tol,cell_mode", [("fp64", 1e-10, 0), ("mixed", 1e-5, 0),
+                                                    ("fp64", 1e-10, 1), ("mixed", 1e-5, 1)])
+def test_c3_sampled_neighbours_and_forces(env, precision, tol, cell_mode):
     g, dss, oracle = env["g"], env["dss"], env["oracle"]
     box = g["box"]
-    p = dss.default_params(box, precision=precision, mu=0.5)
+    p = dss.default_params(box, precision=precision, mu=0.5, cell_mode=cell_mode)
     s = dss.Suspension(g["x"], g["a"], box, p, ids=g["ids"])
     assert s.counters()["M"] == 728
     s.step(5)
