@@ -14,9 +14,9 @@
 // k_gather<MIXED>: one thread per particle: its own sum plus the partner
 //   records of its row taken in increasing owner index (a fixed order, so the
 //   result is bitwise reproducible), Stokes drag (Eq. A1) and the corrector
-//   of Eq. 15d.
-//   The last block of the gather to finish computes the bulk stress of Eq. 8
-//   from the per-block partials and commits the step.
+//   of Eq. 15d.  K leading blocks reduce each instance's bulk stress of
+//   Eq. 8 from the pair blocks' partials; the last block of the gather to
+//   finish adds them to the running sums and commits the step.
 #include <climits>
 
 #include "dss_internal.cuh"
@@ -517,28 +517,40 @@ __device__ void commit_step(const Geo& g, DevStatus* st, const int* __restrict__
   }
 }
 
-template <bool MIXED>
-__device__ __forceinline__ void gather_one(const Geo& g, const InstGeo* __restrict__ ig, const StateBuf& s,
-                                           const void* __restrict__ own_v,
-                                           const int* __restrict__ bw_count, const void* __restrict__ bw_v,
-                                           double* __restrict__ Fout, double* __restrict__ Tout,
-                                           DevStatus* st, int mode) {
-  using R = typename std::conditional<MIXED, float, double>::type;
-  const R* __restrict__ own = static_cast<const R*>(own_v);
-  const R* __restrict__ bw = static_cast<const R*>(bw_v);
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  const int n = g.n;
-  if (j >= n) return;
-  R F[3], T[3];
+// Sums one particle's partner records in increasing owner index.  Owners are
+// distinct within a row; the rank of each record is counted in registers
+// for rows of up to 8 records, otherwise by repeated minimum search.
+template <typename R>
+__device__ __forceinline__ void sum_records(const R* __restrict__ row, int cnt, R* F, R* T) {
+  if (cnt <= 8) {
+    int ow[8];
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    F[c] = own[(int64_t)c * n + j];
-    T[c] = own[(int64_t)(3 + c) * n + j];
+    for (int q = 0; q < 8; ++q) ow[q] = q < cnt ? bits_owner(row[q * kSlot + 6]) : INT_MAX;
+    int rk[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      int r0 = 0;
+#pragma unroll
+      for (int r = 0; r < 8; ++r) r0 += (ow[r] < ow[q]) || (ow[r] == ow[q] && r < q);
+      rk[q] = r0;
+    }
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      if (t < cnt) {
+        int sel = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) sel = rk[q] == t ? q : sel;
+        R b[8];
+        load_record(row + sel * kSlot, b);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          F[c] += b[c];
+          T[c] += b[3 + c];
+        }
+      }
+    }
+    return;
   }
-  // partner records in increasing owner index
-  int cnt = bw_count[j];
-  cnt = cnt < g.M ? cnt : g.M;
-  const R* row = bw + (int64_t)j * g.M * kSlot;
   int prev = -1;
   for (int t = 0; t < cnt; ++t) {
     int best = INT_MAX, bs = 0;
@@ -555,33 +567,80 @@ __device__ __forceinline__ void gather_one(const Geo& g, const InstGeo* __restri
     }
     prev = best;
   }
-  const double a = s.a[j];
-  const int id = s.id[j];
+}
+
+// Total force and torque on particle j (its own pair sum, its partner
+// records, Stokes drag), then the accelerations and, in a step, the velocity
+// half-kick of Eq. 15d.  Returns true when the sums are not finite (the
+// error is then set).  Every load that does not depend on the partner rows
+// is issued first.
+template <bool MIXED>
+__device__ __forceinline__ bool gather_one(const Geo& g, const InstGeo* __restrict__ ig, const StateBuf& s,
+                                           const void* __restrict__ own_v,
+                                           const int* __restrict__ bw_count, const void* __restrict__ bw_v,
+                                           double* __restrict__ Fout, double* __restrict__ Tout,
+                                           DevStatus* st, int mode, int j) {
+  using R = typename std::conditional<MIXED, float, double>::type;
+  const R* __restrict__ own = static_cast<const R*>(own_v);
+  const R* __restrict__ bw = static_cast<const R*>(bw_v);
+  const int n = g.n;
+  if (j >= n) return false;
+  int cnt = __ldg(bw_count + j);
+  R F[3], T[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    F[c] = own[(int64_t)c * n + j];
+    T[c] = own[(int64_t)(3 + c) * n + j];
+  }
+  const double a = __ldg(s.a + j);
+  const int id = __ldg(s.id + j);
+  const bool stepm = mode == G_STEP;
+  const double* __restrict__ su = s.u;
+  const double* __restrict__ sw = s.w;
+  double u[3] = {0.0, 0.0, 0.0}, w[3] = {0.0, 0.0, 0.0};
+  float4 v4 = make_float4(0.f, 0.f, 0.f, 0.f), w4 = v4;
+  double yj = 0.0, gd = 0.0;
+  if constexpr (MIXED) {
+    v4 = __ldg(s.vf + j);
+    w4 = __ldg(s.wf + j);
+  } else {
+    yj = __ldg(s.x + n + j);
+    gd = __ldg(&ig[__ldg(s.inst + j)].gdot);
+  }
+  if (!MIXED || stepm) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      u[c] = su[c * n + j];
+      w[c] = sw[c * n + j];
+    }
+  }
+  cnt = cnt < g.M ? cnt : g.M;
+  sum_records<R>(bw + (int64_t)j * g.M * kSlot, cnt, F, T);
   if constexpr (MIXED) {
     // Stokes drag on the FP32 velocities relative to the ambient flow
     const float af = (float)a;
-    const float4 v4 = s.vf[j], w4 = s.wf[j];
     const float kd = -g.f.k6 * af, kr = -g.f.k8 * af * af * af;
     F[0] += kd * v4.x; F[1] += kd * v4.y; F[2] += kd * v4.z;
     T[0] += kr * w4.x; T[1] += kr * w4.y; T[2] += kr * w4.z;
   } else {
-    const double yj = s.x[n + j];
     const double kd = -g.k6 * a, kr = -g.k8 * a * a * a;
-    const double gd = ig[s.inst[j]].gdot;
-    F[0] += kd * (s.u[j] - gd * yj);
-    F[1] += kd * s.u[n + j];
-    F[2] += kd * s.u[2 * n + j];
-    T[0] += kr * s.w[j];
-    T[1] += kr * s.w[n + j];
-    T[2] += kr * (s.w[2 * n + j] + 0.5 * gd);
+    F[0] += kd * (u[0] - gd * yj);
+    F[1] += kd * u[1];
+    F[2] += kd * u[2];
+    T[0] += kr * w[0];
+    T[1] += kr * w[1];
+    T[2] += kr * (w[2] + 0.5 * gd);
   }
+  bool bad = false;
   if (!(isfinite(F[0]) && isfinite(F[1]) && isfinite(F[2]) && isfinite(T[0]) && isfinite(T[1]) &&
-        isfinite(T[2])))
+        isfinite(T[2]))) {
     set_err(st, DSS_ERR_NONFINITE);
+    bad = true;
+  }
   if (mode == G_EVAL) {
     if (Fout) { Fout[id] = F[0]; Fout[n + id] = F[1]; Fout[2 * n + id] = F[2]; }
     if (Tout) { Tout[id] = T[0]; Tout[n + id] = T[1]; Tout[2 * n + id] = T[2]; }
-    return;
+    return bad;
   }
   // accelerations: m = 4/3 pi rho a^3, I = 2/5 m a^2
   R imr, iIr;
@@ -601,17 +660,22 @@ __device__ __forceinline__ void gather_one(const Geo& g, const InstGeo* __restri
     s.al[c * n + j] = al[c];
     s.aw[c * n + j] = aw[c];
   }
-  if (mode == G_STEP) {
+  if (stepm) {
     // Eq. 15d from u^{n+1/2}: u^{n+1} = u^{n+1/2} + dt/2 alpha^{n+1}
     const double hdt = __dmul_rn(0.5, g.dt);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      s.u[c * n + j] = __dadd_rn(s.u[c * n + j], __dmul_rn(hdt, (double)al[c]));
-      s.w[c * n + j] = __dadd_rn(s.w[c * n + j], __dmul_rn(hdt, (double)aw[c]));
+      s.u[c * n + j] = __dadd_rn(u[c], __dmul_rn(hdt, (double)al[c]));
+      s.w[c * n + j] = __dadd_rn(w[c], __dmul_rn(hdt, (double)aw[c]));
     }
   }
+  return bad;
 }
 
+// Blocks 0..K-1 reduce the bulk stress of instance k (scheduled first, off
+// the particles' critical path); the blocks after them take one particle per
+// thread.  The last block to finish commits the step; only the writes that
+// block reads (the stresses, an error code) are fenced before the count.
 template <bool MIXED>
 __global__ void __launch_bounds__(kThreads)
 k_gather(Geo g, const InstGeo* __restrict__ ig, StateBuf s, const void* __restrict__ own_v,
@@ -626,15 +690,18 @@ k_gather(Geo g, const InstGeo* __restrict__ ig, StateBuf s, const void* __restri
   __shared__ int s_err0;
   if (threadIdx.x == 0) s_err0 = dev_err(st);
   __syncthreads();
+  bool fence = false;
   if (!s_err0) {
-    // block k < K also reduces the stress of instance k (the grid has at
-    // least two blocks per instance)
-    if (blockIdx.x < (unsigned)g.K) inst_stress(g, ig[blockIdx.x], spart, sigma + 9 * blockIdx.x);
-    gather_one<MIXED>(g, ig, s, own_v, bw_count, bw_v, Fout, Tout, st, mode);
+    if (blockIdx.x < (unsigned)g.K) {
+      inst_stress(g, ig[blockIdx.x], spart, sigma + 9 * blockIdx.x);
+      fence = threadIdx.x < 9;
+    } else {
+      const int j = (int)(blockIdx.x - g.K) * blockDim.x + threadIdx.x;
+      fence = gather_one<MIXED>(g, ig, s, own_v, bw_count, bw_v, Fout, Tout, st, mode, j);
+    }
   }
-  // the last block to finish commits the step
   __shared__ bool last;
-  __threadfence();
+  if (fence) __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) last = atomicAdd(done_blocks, 1u) == gridDim.x - 1;
   __syncthreads();
@@ -698,7 +765,7 @@ void launch_forces(dss_handle* h, int stbuf, int work_list, int hist_list, int a
                                                           h->lb[hist_list], h->posf, h->own, h->bw_count,
                                                           h->bw_rec, h->spart, h->status, adv, h->perm);
   prof_mark(h, 6);
-  const int gb = (n + kThreads - 1) / kThreads;
+  const int gb = (n + kThreads - 1) / kThreads + h->g.K;
   if (mixed)
     k_gather<true><<<gb, kThreads, 0, h->stream>>>(h->g, h->ig, h->st[stbuf], h->own, h->bw_count, h->bw_rec,
                                                    F_out, T_out, h->status, mode, h->spart, h->sigma,
