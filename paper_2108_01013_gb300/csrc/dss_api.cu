@@ -152,7 +152,7 @@ int alloc_buffers(dss_handle* h) {
     h->own = own;
     h->bw_rec = bwr;
   }
-  int tiles = std::max(scan_tiles_for(h->g.ncell), enum_tiles_for((int)n));
+  int tiles = std::max(scan_tiles_for(h->g.ncell), enum_scan_tiles_for((int)n));
   h->scan_tiles_max = std::max(tiles, 1);
   if ((r = dalloc(h, &h->scan_status, 2 * (size_t)h->scan_tiles_max)) ||
       (r = dalloc(h, &h->scan_ticket, 2)))

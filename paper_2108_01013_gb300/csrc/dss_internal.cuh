@@ -464,6 +464,7 @@ int pair_grid_blocks(const dss_handle* h);
 void launch_scan(dss_handle* h, const int* in, int* out, int count, int which, bool zero_in);
 int scan_tiles_for(int count);
 int enum_tiles_for(int n);
+int enum_scan_tiles_for(int n);
 int bw_slot_values();
 // Marks the start of kernel k of a step when profiling (event record node
 // when the step is being captured).

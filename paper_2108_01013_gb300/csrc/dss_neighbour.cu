@@ -9,45 +9,134 @@
 //
 // The exclusive scan of the row lengths (the pair offsets of each owner) is
 // fused into the same kernel with a single-pass decoupled look-back over
-// blocks taken in launch order.
+// warps (32 owners each) of blocks taken in launch order.
 #include "dss_internal.cuh"
 
 namespace {
 constexpr int kThreads = 128;
 
-// Visits the candidates of one stencil cell and appends the pairs.
+// Per-owner state of the enumeration; everything the candidate loop reads is
+// held in registers.
 struct EnumCtx {
-  const Geo* g;
-  const InstGeo* I;
-  const StateBuf* s;
-  const float4* posf;
+  const float4* __restrict__ posf;
   float4 pi;
-  double off;
-  int i;
+  float sc, sa;     // cutoff of pair (i, j): s = a_j sc + sa (a_i + a_j + delta)
+  float m2;         // r^2 margin of the FP32 decision
+  float hx, hy, hz; // half box: a separation beyond it is decided exactly
+  bool img;         // the stencil reaches past half the box along some axis
+  int M;
   int cnt;
   int band;
   int* row;
+  // exact FP64 decision
+  const Geo* g;
+  const InstGeo* I;
+  const StateBuf* s;
+  double off;
+  int i;
 };
 
+__device__ __forceinline__ void enum_init(EnumCtx& e, const Geo& g, const InstGeo& I, const StateBuf& s,
+                                          const float4* __restrict__ posf, int i, double off, int* row,
+                                          int reach) {
+  e.posf = posf;
+  e.pi = posf[i];
+  // delta of Sec. II A: a fixed multiple of a0 (mode 1) or of the mean
+  // radius (mode 0); the FP32 cutoff is within a few ulp of the exact one,
+  // far inside the margin
+  if (g.mode == 1) {
+    e.sc = 1.0f;
+    e.sa = e.pi.w + (float)(g.delta * g.a0);
+  } else {
+    e.sc = 1.0f + 0.5f * (float)g.delta;
+    e.sa = e.pi.w * e.sc;
+  }
+  e.m2 = I.r2_margin;
+  e.hx = I.halfLf[0];
+  e.hy = I.halfLf[1];
+  e.hz = I.halfLf[2];
+  // a stencil cell is at most reach+1 cells away along y and z and, across
+  // y = L_y, reach+2 along x: separations stay below half the box when the
+  // box is wider than twice that (plus one cell of slack)
+  e.img = I.nc[0] < 2 * reach + 5 || I.nc[1] < 2 * reach + 3 || I.nc[2] < 2 * reach + 3;
+  e.M = g.M;
+  e.cnt = 0;
+  e.band = 0;
+  e.row = row;
+  e.g = &g;
+  e.I = &I;
+  e.s = &s;
+  e.off = off;
+  e.i = i;
+}
+
+// Visits the candidates [jb, je) of one stencil cell (origin displaced by
+// (cxo, cyo, czo) from the owner's cell) and appends the pairs in order.
+// FP32 decision on cell-local coordinates: certainly a pair, certainly not,
+// or (within the margin of the cutoff, or past half the box) the exact FP64
+// predicate.
 __device__ __forceinline__ void scan_range(EnumCtx& e, int jb, int je, float cxo, float cyo, float czo) {
-  const Geo& g = *e.g;
-  const InstGeo& I = *e.I;
-  const int n = g.n;
+  const float px = e.pi.x - cxo, py = e.pi.y - cyo, pz = e.pi.z - czo;
   for (int j = jb; j < je; ++j) {
-    const float4 pj = e.posf[j];
-    const float sf = e.pi.w + pj.w + pair_delta_f(g, e.pi.w, pj.w);
-    int dec = prefilter(I, e.pi, pj, cxo, cyo, czo, sf);
+    const float4 pj = __ldg(e.posf + j);
+    const float dx = pj.x - px, dy = pj.y - py, dz = pj.z - pz;
+    int dec;
+    if (e.img && (fabsf(dx) > e.hx || fabsf(dy) > e.hy || fabsf(dz) > e.hz)) {
+      dec = -1;
+    } else {
+      const float sv = fmaf(pj.w, e.sc, e.sa);
+      const float t = fmaf(-sv, sv, fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
+      dec = t < -e.m2 ? 1 : (t > e.m2 ? 0 : -1);
+    }
     if (dec < 0) {
       ++e.band;
       const StateBuf& s = *e.s;
-      dec = exact_is_pair(g, I, e.off, s.x[e.i], s.x[n + e.i], s.x[2 * n + e.i], s.a[e.i], s.x[j],
+      const int n = e.g->n, i = e.i;
+      dec = exact_is_pair(*e.g, *e.I, e.off, s.x[i], s.x[n + i], s.x[2 * n + i], s.a[i], s.x[j],
                           s.x[n + j], s.x[2 * n + j], s.a[j]) ? 1 : 0;
     }
     if (dec) {
-      if (e.cnt < g.M) e.row[e.cnt] = j;
+      if (e.cnt < e.M) e.row[e.cnt] = j;
       ++e.cnt;
     }
   }
+}
+
+// Row lengths, counters and the fused exclusive scan of the row lengths:
+// each warp is one scan tile (32 owners) with its own decoupled look-back,
+// so no warp waits for the others of its block.
+__device__ __forceinline__ void finish_rows(const Geo& g, const StateBuf& s, ListBuf& L,
+                                            int* __restrict__ bw_count, unsigned long long* scan_status,
+                                            DevStatus* st, const EnumCtx& e, int i, int wtile) {
+  const int n = g.n;
+  const int lane = threadIdx.x & 31;
+  const int v = i < n ? (e.cnt < g.M ? e.cnt : g.M) : 0;
+  if (i < n) {
+    L.count[i] = v;
+    if (e.cnt > g.M) set_err(st, DSS_ERR_CAPACITY);
+    bw_count[i] = 0;
+    const int id = s.id[i];
+    L.slot_of_id[id] = i;
+    L.id_of_slot[i] = id;
+  }
+  int m = i < n ? e.cnt : 0, b = i < n ? e.band : 0;
+  int incl = v;
+  for (int d = 1; d < 32; d <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += t;
+  }
+  for (int d = 16; d > 0; d >>= 1) {
+    m = max(m, __shfl_xor_sync(0xffffffffu, m, d));
+    b += __shfl_xor_sync(0xffffffffu, b, d);
+  }
+  if (lane == 0) {
+    atomicMax(&st->w[ST_MAXROW], m);
+    if (b) atomicAdd(&st->w[ST_BAND], b);
+  }
+  const int agg = __shfl_sync(0xffffffffu, incl, 31);
+  const int prefix = lookback_warp(scan_status, wtile, agg, st);
+  if (i < n) L.start[i] = prefix + incl - v;
+  if (lane == 0 && (wtile + 1) * 32 >= n) L.start[n] = prefix + agg;
 }
 
 __global__ void __launch_bounds__(kThreads, 8)
@@ -57,8 +146,6 @@ k_enumerate(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ s
             unsigned long long* scan_status, int* scan_ticket, DevStatus* st, int adv) {
   if (dev_err(st)) return;
   __shared__ int s_tile;
-  __shared__ int s_warp[kThreads / 32];
-  __shared__ int s_prefix;
   if (threadIdx.x == 0) s_tile = atomicAdd(scan_ticket, 1);
   __syncthreads();
   const int tile = s_tile;
@@ -71,14 +158,7 @@ k_enumerate(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ s
     const int inst = s.inst[i];
     const InstGeo& I = ig[inst];
     const StepGeo sg = sgk[inst];
-    e.g = &g;
-    e.I = &I;
-    e.s = &s;
-    e.posf = posf;
-    e.i = i;
-    e.off = sg.off;
-    e.pi = posf[i];
-    e.row = L.list + (int64_t)i * g.Ms;
+    enum_init(e, g, I, s, posf, i, sg.off, L.list + (int64_t)i * g.Ms, 1);
     const int fsh = sg.fsh;
     const float offr = sg.offr_hi;
     const int nx = I.nc[0], ny = I.nc[1], nz = I.nc[2];
@@ -113,51 +193,8 @@ k_enumerate(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ s
         scan_range(e, cell_start[q], cell_start[q + 1], cxo, cyo, czo);
       }
     }
-    L.count[i] = e.cnt < g.M ? e.cnt : g.M;
-    if (e.cnt > g.M) set_err(st, DSS_ERR_CAPACITY);
-    bw_count[i] = 0;
-    const int id = s.id[i];
-    L.slot_of_id[id] = i;
-    L.id_of_slot[i] = id;
   }
-  // counters
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  int m = e.cnt, b = e.band;
-  for (int d = 16; d > 0; d >>= 1) {
-    m = max(m, __shfl_xor_sync(0xffffffffu, m, d));
-    b += __shfl_xor_sync(0xffffffffu, b, d);
-  }
-  if (lane == 0) {
-    atomicMax(&st->w[ST_MAXROW], m);
-    if (b) atomicAdd(&st->w[ST_BAND], b);
-  }
-  // fused exclusive scan of the row lengths: block scan + decoupled look-back
-  const int v = i < n ? (e.cnt < g.M ? e.cnt : g.M) : 0;
-  int incl = v;
-  for (int d = 1; d < 32; d <<= 1) {
-    const int t = __shfl_up_sync(0xffffffffu, incl, d);
-    if (lane >= d) incl += t;
-  }
-  if (lane == 31) s_warp[wid] = incl;
-  __syncthreads();
-  if (wid == 0) {
-    int run = 0;
-    if (lane == 0) {
-      for (int w = 0; w < kThreads / 32; ++w) {
-        const int t = s_warp[w];
-        s_warp[w] = run;
-        run += t;
-      }
-    }
-    const int agg = __shfl_sync(0xffffffffu, run, 0);
-    const int prefix = lookback_warp(scan_status, tile, agg, st);
-    if (lane == 0) {
-      s_prefix = prefix;
-      if ((tile + 1) * kThreads >= n) L.start[n] = prefix + agg;
-    }
-  }
-  __syncthreads();
-  if (i < n) L.start[i] = s_prefix + s_warp[wid] + incl - v;
+  finish_rows(g, s, L, bw_count, scan_status, st, e, i, tile * (kThreads / 32) + (threadIdx.x >> 5));
 }
 
 // Size classes (Sec. II A: cells smaller than 2 a_max, a larger stencil for
@@ -176,8 +213,6 @@ k_enumerate_classes(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __rest
                     unsigned long long* scan_status, int* scan_ticket, DevStatus* st) {
   if (dev_err(st)) return;
   __shared__ int s_tile;
-  __shared__ int s_warp[kThreads / 32];
-  __shared__ int s_prefix;
   if (threadIdx.x == 0) s_tile = atomicAdd(scan_ticket, 1);
   __syncthreads();
   const int tile = s_tile;
@@ -190,14 +225,7 @@ k_enumerate_classes(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __rest
     const int inst = s.inst[i];
     const InstGeo& I = ig[inst];
     const StepGeo sg = sgk[inst];
-    e.g = &g;
-    e.I = &I;
-    e.s = &s;
-    e.posf = posf;
-    e.i = i;
-    e.off = sg.off;
-    e.pi = posf[i];
-    e.row = L.list + (int64_t)i * g.Ms;
+    enum_init(e, g, I, s, posf, i, sg.off, L.list + (int64_t)i * g.Ms, g.reach);
     const int fsh = sg.fsh;
     const float offr = sg.offr_hi;
     const int nx = I.nc[0], ny = I.nc[1], nz = I.nc[2];
@@ -260,53 +288,13 @@ k_enumerate_classes(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __rest
         }
       }
     }
-    L.count[i] = e.cnt < g.M ? e.cnt : g.M;
-    if (e.cnt > g.M) set_err(st, DSS_ERR_CAPACITY);
-    bw_count[i] = 0;
-    const int id = s.id[i];
-    L.slot_of_id[id] = i;
-    L.id_of_slot[i] = id;
   }
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  int m = e.cnt, b = e.band;
-  for (int d = 16; d > 0; d >>= 1) {
-    m = max(m, __shfl_xor_sync(0xffffffffu, m, d));
-    b += __shfl_xor_sync(0xffffffffu, b, d);
-  }
-  if (lane == 0) {
-    atomicMax(&st->w[ST_MAXROW], m);
-    if (b) atomicAdd(&st->w[ST_BAND], b);
-  }
-  const int v = i < n ? (e.cnt < g.M ? e.cnt : g.M) : 0;
-  int incl = v;
-  for (int d = 1; d < 32; d <<= 1) {
-    const int t = __shfl_up_sync(0xffffffffu, incl, d);
-    if (lane >= d) incl += t;
-  }
-  if (lane == 31) s_warp[wid] = incl;
-  __syncthreads();
-  if (wid == 0) {
-    int run = 0;
-    if (lane == 0) {
-      for (int w = 0; w < kThreads / 32; ++w) {
-        const int t = s_warp[w];
-        s_warp[w] = run;
-        run += t;
-      }
-    }
-    const int agg = __shfl_sync(0xffffffffu, run, 0);
-    const int prefix = lookback_warp(scan_status, tile, agg, st);
-    if (lane == 0) {
-      s_prefix = prefix;
-      if ((tile + 1) * kThreads >= n) L.start[n] = prefix + agg;
-    }
-  }
-  __syncthreads();
-  if (i < n) L.start[i] = s_prefix + s_warp[wid] + incl - v;
+  finish_rows(g, s, L, bw_count, scan_status, st, e, i, tile * (kThreads / 32) + (threadIdx.x >> 5));
 }
 }  // namespace
 
 int enum_tiles_for(int n) { return (n + kThreads - 1) / kThreads; }
+int enum_scan_tiles_for(int n) { return enum_tiles_for(n) * (kThreads / 32); }
 
 void launch_enumerate(dss_handle* h, int stbuf, int dst_list, int adv) {
   const int n = (int)h->n;
