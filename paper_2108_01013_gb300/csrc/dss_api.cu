@@ -561,6 +561,8 @@ int create_handle(dss_handle** out, const dss_params* p, int K, const int64_t* n
   g.delta = p->delta_lub; g.eps = p->lub_eps; g.a0 = p->a0;
   g.mode = p->lub_cutoff_mode; g.precision = p->precision;
   g.dt = p->dt;
+  g.hdt = 0.5 * p->dt;
+  g.hdt2 = g.hdt * p->dt;
   g.k6 = 6.0 * DSS_PI * p->eta0;
   g.k8 = 8.0 * DSS_PI * p->eta0;
   g.f.kn = (float)p->kn;

@@ -662,7 +662,7 @@ __device__ __forceinline__ bool gather_one(const Geo& g, const InstGeo* __restri
   }
   if (stepm) {
     // Eq. 15d from u^{n+1/2}: u^{n+1} = u^{n+1/2} + dt/2 alpha^{n+1}
-    const double hdt = __dmul_rn(0.5, g.dt);
+    const double hdt = g.hdt;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       s.u[c * n + j] = __dadd_rn(u[c], __dmul_rn(hdt, (double)al[c]));

@@ -56,6 +56,7 @@ struct Geo {
   int mode;           // cutoff mode
   int precision;
   double dt;
+  double hdt, hdt2;   // dt/2 and (dt/2) dt, each rounded once
   double k6;          // 6 pi eta0
   double k8;          // 8 pi eta0
   double taper;       // lubrication taper width w (0: hard cutoff)
@@ -151,7 +152,7 @@ __device__ __forceinline__ bool exact_is_pair(const Geo& g, const InstGeo& I, do
 }
 
 __device__ __forceinline__ int cell_coord(double v, double inv, int nc) {
-  int k = (int)floor(v * inv);
+  int k = __double2int_rd(v * inv);   // floor, one conversion
   return k < 0 ? 0 : (k >= nc ? nc - 1 : k);
 }
 

@@ -13,9 +13,10 @@ namespace {
 
 constexpr int kThreads = 256;
 
-// Predictor of Eq. 15a-b and the wrap of Eq. 16 for one particle, with the
-// rounding of every operation fixed so that both sort kernels obtain the
-// same bits.  Returns the y crossing (-1 out through the top, +1 bottom).
+// Predictor of Eq. 15a-b (as fused multiply-adds: GB300's FP64 pipe bounds
+// this kernel) and the wrap of Eq. 16 for one particle; computed once per
+// step and stored for the gather.  Returns the y crossing (-1 out through
+// the top, +1 bottom).
 struct Pred {
   double x, y, z, ux, uy, uz;
   int cross;
@@ -30,15 +31,15 @@ __device__ __forceinline__ Pred predict_one(const Geo& g, const InstGeo& I, cons
   r.cross = 0;
   if (predict) {
     const double dt = g.dt;
-    const double hdt2 = __dmul_rn(__dmul_rn(0.5, dt), dt);
-    const double hdt = __dmul_rn(0.5, dt);
+    const double hdt2 = g.hdt2;
+    const double hdt = g.hdt;
     double ax = s.al[i], ay = s.al[n + i], az = s.al[2 * n + i];
-    x = __dadd_rn(__dadd_rn(x, __dmul_rn(dt, ux)), __dmul_rn(hdt2, ax));
-    y = __dadd_rn(__dadd_rn(y, __dmul_rn(dt, uy)), __dmul_rn(hdt2, ay));
-    z = __dadd_rn(__dadd_rn(z, __dmul_rn(dt, uz)), __dmul_rn(hdt2, az));
-    ux = __dadd_rn(ux, __dmul_rn(hdt, ax));
-    uy = __dadd_rn(uy, __dmul_rn(hdt, ay));
-    uz = __dadd_rn(uz, __dmul_rn(hdt, az));
+    x = __fma_rn(hdt2, ax, __fma_rn(dt, ux, x));
+    y = __fma_rn(hdt2, ay, __fma_rn(dt, uy, y));
+    z = __fma_rn(hdt2, az, __fma_rn(dt, uz, z));
+    ux = __fma_rn(hdt, ax, ux);
+    uy = __fma_rn(hdt, ay, uy);
+    uz = __fma_rn(hdt, az, uz);
     // Lees-Edwards wrap: leaving through y >= L_y re-enters at the bottom
     // shifted by -off along x with u_x - gdot L_y, and vice versa
     const double Ly = I.L[1];
@@ -180,9 +181,9 @@ k_rank_gather(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__
   dst.x[f] = p.x; dst.x[n + f] = p.y; dst.x[2 * n + f] = p.z;
   dst.u[f] = p.ux; dst.u[n + f] = p.uy; dst.u[2 * n + f] = p.uz;
   if (predict) {
-    const double hdt = __dmul_rn(0.5, g.dt);
+    const double hdt = g.hdt;
     for (int c = 0; c < 3; ++c)
-      dst.w[c * n + f] = __dadd_rn(src.w[c * n + o], __dmul_rn(hdt, src.aw[c * n + o]));
+      dst.w[c * n + f] = __fma_rn(hdt, src.aw[c * n + o], src.w[c * n + o]);
   } else {
     for (int c = 0; c < 3; ++c) {
       dst.w[c * n + f] = src.w[c * n + o];
@@ -208,7 +209,8 @@ k_rank_gather(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__
   int cx = kl % I.nc[0];
   int cy = (kl / I.nc[0]) % I.nc[1];
   int cz = kl / (I.nc[0] * I.nc[1]);
-  const double lx = p.x - cx * I.cs[0], ly = p.y - cy * I.cs[1], lz = p.z - cz * I.cs[2];
+  const double lx = __fma_rn(-(double)cx, I.cs[0], p.x), ly = __fma_rn(-(double)cy, I.cs[1], p.y),
+               lz = __fma_rn(-(double)cz, I.cs[2], p.z);
   float4 pf;
   pf.x = (float)lx;
   pf.y = (float)ly;
