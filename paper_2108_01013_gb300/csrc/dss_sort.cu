@@ -231,52 +231,68 @@ k_rank_gather(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__
 // launch order through an atomic ticket, so every predecessor a tile waits
 // on is already running; each wait is bounded and reports DSS_ERR_TIMEOUT.
 namespace {
-constexpr int kScanThreads = 512;
+constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanThreads * kScanItems;
 
+__host__ __device__ constexpr int scan_pad(int q) { return q + (q >> 5); }   // no bank conflicts
+
+// A tile is loaded and stored coalesced through shared memory; each thread
+// scans 8 consecutive items of it.  The input is cleared as soon as it is
+// read when zero_in is set (the histogram of the next operation).
 __global__ void __launch_bounds__(kScanThreads)
 k_scan(const int* __restrict__ in, int* __restrict__ out, int count,
        unsigned long long* status, int* ticket, DevStatus* st, int zero_in) {
-  if (dev_err(st)) return;
-  __shared__ int s_tile;
+  __shared__ int s_tile, s_err, s_prefix, s_agg;
   __shared__ int s_warp[kScanThreads / 32];
-  __shared__ int s_prefix;
+  __shared__ int s_v[scan_pad(kScanTile)];
   if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1);
+  if (threadIdx.x == 32) s_err = dev_err(st);
   __syncthreads();
+  if (s_err) return;
   const int tile = s_tile;
   const int base = tile * kScanTile;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    const int q = k * kScanThreads + threadIdx.x;
+    const int idx = base + q;
+    int x = 0;
+    if (idx < count) {
+      x = in[idx];
+      if (zero_in) const_cast<int*>(in)[idx] = 0;
+    }
+    s_v[scan_pad(q)] = x;
+  }
+  __syncthreads();
   int v[kScanItems];
   int local = 0;
+#pragma unroll
   for (int k = 0; k < kScanItems; ++k) {
-    int idx = base + threadIdx.x * kScanItems + k;
-    v[k] = idx < count ? in[idx] : 0;
+    v[k] = s_v[scan_pad(threadIdx.x * kScanItems + k)];
     local += v[k];
   }
   // block exclusive scan of the per-thread sums
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   int incl = local;
   for (int d = 1; d < 32; d <<= 1) {
-    int t = __shfl_up_sync(0xffffffffu, incl, d);
+    const int t = __shfl_up_sync(0xffffffffu, incl, d);
     if (lane >= d) incl += t;
   }
   if (lane == 31) s_warp[wid] = incl;
   __syncthreads();
   if (wid == 0) {
-    int w = lane < kScanThreads / 32 ? s_warp[lane] : 0;
+    const int w = lane < kScanThreads / 32 ? s_warp[lane] : 0;
     int wi = w;
     for (int d = 1; d < 32; d <<= 1) {
-      int t = __shfl_up_sync(0xffffffffu, wi, d);
+      const int t = __shfl_up_sync(0xffffffffu, wi, d);
       if (lane >= d) wi += t;
     }
     if (lane < kScanThreads / 32) s_warp[lane] = wi - w;   // exclusive warp offsets
+    if (lane == kScanThreads / 32 - 1) s_agg = wi;
   }
   __syncthreads();
-  int excl = incl - local + s_warp[wid];
-  // tile aggregate and look-back
-  __shared__ int s_agg;
-  if (threadIdx.x == kScanThreads - 1) s_agg = excl + local;
-  __syncthreads();
+  // tile prefix by look-back (warp 0) while every thread stores its
+  // tile-local exclusive values
   if (wid == 0) {
     const int agg = s_agg;
     const int prefix = lookback_warp(status, tile, agg, st);
@@ -285,15 +301,19 @@ k_scan(const int* __restrict__ in, int* __restrict__ out, int count,
       if (base + kScanTile >= count) out[count] = prefix + agg;   // total
     }
   }
-  __syncthreads();
-  int run = s_prefix + excl;
+  int run = incl - local + s_warp[wid];
+#pragma unroll
   for (int k = 0; k < kScanItems; ++k) {
-    int idx = base + threadIdx.x * kScanItems + k;
-    if (idx < count) {
-      out[idx] = run;
-      run += v[k];
-      if (zero_in) const_cast<int*>(in)[idx] = 0;
-    }
+    s_v[scan_pad(threadIdx.x * kScanItems + k)] = run;
+    run += v[k];
+  }
+  __syncthreads();
+  const int pre = s_prefix;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    const int q = k * kScanThreads + threadIdx.x;
+    const int idx = base + q;
+    if (idx < count) out[idx] = s_v[scan_pad(q)] + pre;
   }
 }
 }  // namespace
