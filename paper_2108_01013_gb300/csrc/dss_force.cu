@@ -218,10 +218,13 @@ __device__ __forceinline__ PairRes<float> pair_eval_mixed(const Geo& g, const In
     const F3 xf = f3((float)xo[0], (float)xo[1], (float)xo[2]);
     const float pn = dotf(nn, xf);
     const float sdt = sg * g.f.dt;
-    double xs0 = xo[0] + (double)(sdt * ut.x - pn * nn.x);
-    double xs1 = xo[1] + (double)(sdt * ut.y - pn * nn.y);
-    double xs2 = xo[2] + (double)(sdt * ut.z - pn * nn.z);
-    F3 xsf = f3((float)xs0, (float)xs1, (float)xs2);
+    const F3 dxs = f3(sdt * ut.x - pn * nn.x, sdt * ut.y - pn * nn.y, sdt * ut.z - pn * nn.z);
+    double xs0 = xo[0] + (double)dxs.x;
+    double xs1 = xo[1] + (double)dxs.y;
+    double xs2 = xo[2] + (double)dxs.z;
+    // the FP32 copy for the force is formed in FP32 (within an ulp of the
+    // rounded FP64 sum; no conversions back from FP64)
+    F3 xsf = xf + dxs;
     const float cap = g.f.mu_kt * fabsf(fn);
     const float xm2 = dotf(xsf, xsf);
     if (xm2 > cap * cap) {
@@ -665,8 +668,8 @@ __device__ __forceinline__ bool gather_one(const Geo& g, const InstGeo* __restri
     const double hdt = g.hdt;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      s.u[c * n + j] = __dadd_rn(u[c], __dmul_rn(hdt, (double)al[c]));
-      s.w[c * n + j] = __dadd_rn(w[c], __dmul_rn(hdt, (double)aw[c]));
+      s.u[c * n + j] = __fma_rn(hdt, (double)al[c], u[c]);
+      s.w[c * n + j] = __fma_rn(hdt, (double)aw[c], w[c]);
     }
   }
   return bad;
