@@ -1,13 +1,17 @@
 """The 1,000,000-particle polydisperse workload (radii log-uniform in [1, 10],
 volume fraction 0.50, mu = 0.5; list capacity M = 728 from the shell bound),
 in the launch configuration the benchmark uses.  The oracle cannot do the
-full O(N^2) problem, so it checks sampled outputs it computes one by one: the
-complete neighbour set of sampled particles (bit-exact; the largest and the
-smallest particles are always sampled) and the force and torque on them, at
-the initial state and after steps with contact history, in FP64 and mixed
-precision, with one cell list and with size classes."""
+full O(N^2) problem, so it checks sampled outputs it computes one by one, on
+inputs made without the CUDA path (the seeded packing, seeded velocities, a
+seeded stretch on the contacts the oracle finds): the complete neighbour set
+of sampled particles (bit-exact; the largest and the smallest particles are
+always sampled) at two Lees-Edwards offsets, and the force and torque on them
+with that contact history, in FP64 and mixed precision, with one cell list
+and with size classes."""
 import numpy as np
 import pytest
+
+from fullsize_cases import contact_history, partners, relerr, sample, velocities
 
 pytestmark = pytest.mark.gpu
 
@@ -24,53 +28,44 @@ def env():
     dss.build()
     synth.build()
     g = synth.generate(synth.SPECS["c3"])
-    return dict(oracle=oracle, dss=dss, synth=synth, g=g)
-
-
-def _sample(g, m=48, seed=0):
-    a = g["a"]
-    order = np.argsort(a)
-    rng = np.random.default_rng(seed)
-    pick = np.concatenate([order[-8:], order[:8], rng.choice(a.shape[0], m - 16, replace=False)])
-    return np.unique(pick)
-
-
-def relerr(a, b):
-    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b))
+    box = g["box"]
+    po = oracle.make_params(box, mu=0.5)
+    u, w = velocities(g["x"], g["a"], 1.0, seed=31)
+    idx = sample(g["a"])
+    cases = {}
+    for nstep in (0, 7_654_321):
+        off = oracle.le_offset(po, nstep)
+        keys, xi = contact_history(oracle, po, off, g["x"], g["a"], g["ids"], u, w, idx, seed=nstep % 97)
+        o = oracle.System(po, g["x"], g["a"], ids=g["ids"], u=u, w=w, nstep=nstep)
+        o.set_history(keys, xi)
+        Fo, To = o.forces_sampled(idx)
+        want = {int(k): oracle.neighbours_of(g["x"], g["a"], g["ids"], po, off, int(k)) for k in idx}
+        cases[nstep] = dict(keys=keys, xi=xi, Fo=Fo, To=To, want=want)
+    return dict(oracle=oracle, dss=dss, g=g, u=u, w=w, idx=idx, cases=cases)
 
 
 @pytest.mark.parametrize("precision,tol,cell_mode", [("fp64", 1e-10, 0), ("mixed", 1e-5, 0),
                                                     ("fp64", 1e-10, 1), ("mixed", 1e-5, 1)])
 def test_c3_sampled_neighbours_and_forces(env, precision, tol, cell_mode):
-    g, dss, oracle = env["g"], env["dss"], env["oracle"]
-    box = g["box"]
+    g, dss = env["g"], env["dss"]
+    box, idx = g["box"], env["idx"]
+    n = g["a"].shape[0]
     p = dss.default_params(box, precision=precision, mu=0.5, cell_mode=cell_mode)
-    s = dss.Suspension(g["x"], g["a"], box, p, ids=g["ids"])
-    assert s.counters()["M"] == 728
-    s.step(5)
-    st = {k: v.cpu().numpy() for k, v in s.state().items()}
-    nstep = s.counters()["nstep"]
-    keys, xi = s.history()
-    assert len(keys) > 100_000
-    # neighbour sets at the current state
-    s.neighbour_build()
-    pairs = s.pairs()
-    po = oracle.make_params(box, mu=0.5)
-    off = oracle.le_offset(po, nstep)
-    idx = _sample(g)
-    for k in idx:
-        want = oracle.neighbours_of(st["x"], g["a"], g["ids"], po, off, int(k))
-        got = np.sort(np.concatenate([pairs[pairs[:, 0] == k, 1], pairs[pairs[:, 1] == k, 0]]))
-        np.testing.assert_array_equal(got, want)
-    # forces and torques on the sample, with the carried history
-    F, T = s.forces()
-    F, T = F.cpu().numpy(), T.cpu().numpy()
-    o = oracle.System(po, st["x"], g["a"], ids=g["ids"], u=st["u"], w=st["w"], nstep=nstep)
-    o.set_history(keys, xi)
-    Fo, To = o.forces_sampled(idx)
-    assert relerr(F[:, idx], Fo) < tol
-    assert relerr(T[:, idx], To) < tol
-    big = idx[np.argsort(g["a"][idx])[-8:]]
-    j = np.searchsorted(idx, big)
-    assert relerr(F[:, big], Fo[:, j]) < tol
-    s.close()
+    for nstep, c in env["cases"].items():
+        s = dss.Suspension(g["x"], g["a"], box, p, ids=g["ids"], u=env["u"], w=env["w"], nstep=nstep,
+                           alpha_lin=np.zeros((3, n)), alpha_ang=np.zeros((3, n)))
+        assert s.counters()["M"] == 728
+        s.neighbour_build()
+        pairs = s.pairs()
+        for k in idx:
+            np.testing.assert_array_equal(partners(pairs, int(g["ids"][k])), c["want"][int(k)])
+        assert len(c["keys"]) > 100
+        s.set_history(c["keys"], c["xi"])
+        F, T = s.forces()
+        F, T = F.cpu().numpy(), T.cpu().numpy()
+        assert relerr(F[:, idx], c["Fo"]) < tol
+        assert relerr(T[:, idx], c["To"]) < tol
+        big = idx[np.argsort(g["a"][idx])[-8:]]
+        j = np.searchsorted(idx, big)
+        assert relerr(F[:, big], c["Fo"][:, j]) < tol
+        s.close()
