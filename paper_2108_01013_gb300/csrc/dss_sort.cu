@@ -17,6 +17,18 @@ constexpr int kThreads = 256;
 // this kernel) and the wrap of Eq. 16 for one particle; computed once per
 // step and stored for the gather.  Returns the y crossing (-1 out through
 // the top, +1 bottom).
+// Comparisons for the wrap on the IEEE bit patterns (integer instructions
+// instead of GB300's narrow FP64 pipe).  For L > 0 and any finite v the
+// signed 64-bit order of the patterns is the order of the values on the
+// non-negative side, and every negative v sorts below; -0.0 is not below 0.
+__device__ __forceinline__ bool ge_pos(double v, double L) {
+  return __double_as_longlong(v) >= __double_as_longlong(L);
+}
+__device__ __forceinline__ bool lt_zero(double v) {
+  const long long b = __double_as_longlong(v);
+  return b < 0 && b != (long long)0x8000000000000000ull;
+}
+
 struct Pred {
   double x, y, z, ux, uy, uz;
   int cross;
@@ -43,26 +55,26 @@ __device__ __forceinline__ Pred predict_one(const Geo& g, const InstGeo& I, cons
     // Lees-Edwards wrap: leaving through y >= L_y re-enters at the bottom
     // shifted by -off along x with u_x - gdot L_y, and vice versa
     const double Ly = I.L[1];
-    if (y >= Ly) {
+    if (ge_pos(y, Ly)) {
       y = __dsub_rn(y, Ly);
       x = __dsub_rn(x, le_offset(g, I, dev_nstep(st) + adv));
       r.cross = -1;
-    } else if (y < 0.0) {
+    } else if (lt_zero(y)) {
       y = __dadd_rn(y, Ly);
       x = __dadd_rn(x, le_offset(g, I, dev_nstep(st) + adv));
       r.cross = 1;
-      if (y >= Ly) y = 0.0;
+      if (ge_pos(y, Ly)) y = 0.0;
     }
     // x back into [0, L_x): two conditional shifts give the same bits as
     // fmod followed by the two corrections, for |x| < 2 L_x
     const double Lx = I.L[0];
-    if (x < 0.0) x = __dadd_rn(x, Lx); else if (x >= Lx) x = __dsub_rn(x, Lx);
-    if (x < 0.0) x = __dadd_rn(x, Lx); else if (x >= Lx) x = __dsub_rn(x, Lx);
-    if (z >= I.L[2]) {
+    if (lt_zero(x)) x = __dadd_rn(x, Lx); else if (ge_pos(x, Lx)) x = __dsub_rn(x, Lx);
+    if (lt_zero(x)) x = __dadd_rn(x, Lx); else if (ge_pos(x, Lx)) x = __dsub_rn(x, Lx);
+    if (ge_pos(z, I.L[2])) {
       z = __dsub_rn(z, I.L[2]);
-    } else if (z < 0.0) {
+    } else if (lt_zero(z)) {
       z = __dadd_rn(z, I.L[2]);
-      if (z >= I.L[2]) z = 0.0;
+      if (ge_pos(z, I.L[2])) z = 0.0;
     }
     if (r.cross != 0)
       ux = __dadd_rn(ux, __dmul_rn(__dmul_rn((double)r.cross, I.gdot), Ly));
