@@ -99,10 +99,12 @@ k_key_hist(Geo g, const InstGeo* __restrict__ ig, StepGeo* __restrict__ sg, Stat
            DevStatus* st, bool predict, unsigned long long* scan_status, int* scan_ticket,
            int scan_tiles, double* __restrict__ pred) {
   if (dev_err(st)) return;
-  // reset the look-back state of both scans of this operation, the
-  // counters, and set every instance's Lees-Edwards geometry for its time
+  // reset the look-back state of both scans of this operation (spread over
+  // the grid), the counters, and set every instance's Lees-Edwards geometry
+  // for its time
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < 2 * scan_tiles; t += gridDim.x * blockDim.x)
+    scan_status[t] = 0ull;
   if (blockIdx.x == 0) {
-    for (int t = threadIdx.x; t < 2 * scan_tiles; t += blockDim.x) scan_status[t] = 0ull;
     if (threadIdx.x < 2) scan_ticket[threadIdx.x] = 0;
     if (threadIdx.x == 0) {
       st->w[ST_MAXROW] = 0;
