@@ -14,6 +14,11 @@ Parity status of each function (see the pins in ``tests/test_oracle_*.py``):
                                     placed geometry, Lees-Edwards images)
   contact                           pinned (head-on spring-dashpot closed
                                     form, Coulomb-capped tangential loading)
+  echem / echem_range               pinned (integrates to the closed-form
+                                    potentials of Eq. 6, Debye decay,
+                                    harmonic-radius scaling, flat and
+                                    continuous at contact, exact ranges,
+                                    central and balanced in pair_eval)
   lubrication                       pinned by physics invariants (Reynolds
                                     squeeze law for equal spheres, zero
                                     force/torque for rigid motion of the pair
@@ -61,12 +66,14 @@ class Params(ctypes.Structure):
                 ("delta_lub", c_double), ("lub_eps", c_double), ("a0", c_double),
                 ("lub_cutoff_mode", c_int32), ("pad_", c_int32),
                 ("shear_rate", c_double), ("dt", c_double), ("L", c_double * 3),
-                ("lub_taper", c_double)]
+                ("lub_taper", c_double), ("f_er", c_double), ("lambda_d", c_double),
+                ("hamaker", c_double), ("vdw_eps", c_double)]
 
 
 def make_params(box, kn=1e4, kt=None, gamma_n=None, mu=0.5, eta0=1.0, rho=1.0,
                 delta_lub=0.05, lub_eps=1e-3, a0=1.0, lub_cutoff_mode=0,
-                shear_rate=1.0, dt=1e-4, lub_taper=0.0) -> Params:
+                shear_rate=1.0, dt=1e-4, lub_taper=0.0, f_er=0.0, lambda_d=0.05,
+                hamaker=0.0, vdw_eps=0.01) -> Params:
     """Oracle parameters; kt defaults to kn/2 and gamma_n to 1e-7 kn/gdot."""
     if kt is None:
         kt = 0.5 * kn
@@ -78,6 +85,7 @@ def make_params(box, kn=1e4, kt=None, gamma_n=None, mu=0.5, eta0=1.0, rho=1.0,
     p.lub_cutoff_mode = lub_cutoff_mode
     p.shear_rate, p.dt = shear_rate, dt
     p.lub_taper = lub_taper
+    p.f_er, p.lambda_d, p.hamaker, p.vdw_eps = f_er, lambda_d, hamaker, vdw_eps
     for k in range(3):
         p.L[k] = float(box[k])
     return p
@@ -105,6 +113,10 @@ def lib():
         L.orc_contact.argtypes = [pp, dp, c_double, c_double] + [dp] * 5 + [dp] * 4
         L.orc_lubrication.restype = None
         L.orc_lubrication.argtypes = [pp, dp, c_double, c_double] + [dp] * 4 + [dp] * 4
+        L.orc_echem.restype = None
+        L.orc_echem.argtypes = [pp, c_double, c_double, c_double, dp, dp]
+        L.orc_echem_range.restype = c_double
+        L.orc_echem_range.argtypes = [pp]
         L.orc_pair_eval.restype = c_int
         L.orc_pair_eval.argtypes = [pp, c_double] + [dp] * 6 + [c_double, c_double, dp] + [dp] * 6
         L.orc_create.restype = c_void_p
@@ -195,6 +207,18 @@ def lubrication(p: Params, r, ai, aj, Vi, Vj, Wi, Wj):
     lib().orc_lubrication(ctypes.byref(p), _ptr(_d(r)), float(ai), float(aj),
                           *[_ptr(v) for v in args], *[_ptr(o) for o in outs])
     return tuple(outs)
+
+
+def echem(p: Params, d, ai, aj, n):
+    """Eq. 6 electro-chemical force on i from j at surface distance d along n."""
+    F = np.zeros(3)
+    lib().orc_echem(ctypes.byref(p), float(d), float(ai), float(aj), _ptr(_d(n)), _ptr(F))
+    return F
+
+
+def echem_range(p: Params) -> float:
+    """Surface distance below which the electro-chemical forces act (0: off)."""
+    return lib().orc_echem_range(ctypes.byref(p))
 
 
 def pair_eval(p: Params, off, xi, xj, ui, uj, wi, wj, ai, aj, xi_old=(0, 0, 0)):

@@ -61,6 +61,8 @@ typedef struct orc_params {
   double shear_rate, dt;        /* gdot, time step */
   double L[3];                  /* box edges */
   double lub_taper;             /* w of the lubrication taper; 0: hard cutoff */
+  double f_er, lambda_d;        /* Eq. 6a (repulsion): magnitude F_ER, Debye length */
+  double hamaker, vdw_eps;      /* Eq. 6b (attraction): Hamaker constant A, eps / abar */
 } orc_params;
 
 typedef struct orc_sys {
@@ -113,17 +115,42 @@ static void min_image(const orc_params *p, double off, const double xi[3],
   *sy = s;
 }
 
-/* Interaction range beyond contact: the lubrication cutoff delta_lub of
- * Sec. II (Fig. 1) expressed as a surface distance for the pair. */
-static double pair_delta(const orc_params *p, double ai, double aj) {
+/* The lubrication cutoff delta_lub of Sec. II (Fig. 1) expressed as a
+ * surface distance for the pair. */
+static double lub_delta(const orc_params *p, double ai, double aj) {
   if (p->lub_cutoff_mode == 1) return p->delta_lub * p->a0;
   return p->delta_lub * (ai + aj) * 0.5;
+}
+
+/* Range of the electro-chemical forces (Fig. 3): the repulsion acts below a
+ * surface distance of 20 lambda_D, the attraction below 4 a0; 0 when both
+ * are off. */
+double orc_echem_range(const orc_params *p) {
+  double r = 0.0;
+  if (p->f_er > 0.0 && 20.0 * p->lambda_d > r) r = 20.0 * p->lambda_d;
+  if (p->hamaker > 0.0 && 4.0 * p->a0 > r) r = 4.0 * p->a0;
+  return r;
+}
+
+/* Interaction range beyond contact: the larger of the lubrication cutoff and
+ * the electro-chemical range. */
+static double pair_delta(const orc_params *p, double ai, double aj) {
+  double dl = lub_delta(p, ai, aj), de = orc_echem_range(p);
+  return de > dl ? de : dl;
 }
 
 /* Neighbour predicate: r^2 < (a_i + a_j + delta_ij)^2 (strict). */
 static int is_pair(const orc_params *p, const double r[3], double ai, double aj) {
   double r2 = (r[0] * r[0] + r[1] * r[1]) + r[2] * r[2];
   double s = (ai + aj) + pair_delta(p, ai, aj);
+  return r2 < s * s;
+}
+
+/* Lubrication acts on a listed pair iff it is within the lubrication cutoff
+ * (the same strict test with the lubrication range alone). */
+static int in_lub_range(const orc_params *p, const double r[3], double ai, double aj) {
+  double r2 = (r[0] * r[0] + r[1] * r[1]) + r[2] * r[2];
+  double s = (ai + aj) + lub_delta(p, ai, aj);
   return r2 < s * s;
 }
 
@@ -404,11 +431,33 @@ void orc_lubrication(const orc_params *p, const double r[3], double ai, double a
 /* Lubrication taper factor of a listed pair at gap d (1 for w = 0). */
 static double lub_taper_factor(const orc_params *p, double d, double ai, double aj) {
   if (!(p->lub_taper > 0.0)) return 1.0;
-  double dl = pair_delta(p, ai, aj);
+  double dl = lub_delta(p, ai, aj);
   double t = (dl - d) / (p->lub_taper * dl);
   if (t >= 1.0) return 1.0;
   if (t <= 0.0) return 0.0;
   return t * t * (3.0 - 2.0 * t);
+}
+
+/* Electro-chemical force on i from j at surface distance d, along the unit
+ * vector n from i to j (Eq. 6): the double-layer repulsion
+ * -F_ER (abar/a0) exp(-d/lambda_D) n (its contact value for d < 0), acting
+ * below d = 20 lambda_D, plus the van der Waals attraction
+ * A abar / (12 (d^2 + eps^2)) n (its contact value for d < 0), acting below
+ * d = 4 a0, with abar = 2 a_i a_j / (a_i + a_j) and eps = vdw_eps abar.  The
+ * force on j is the opposite. */
+void orc_echem(const orc_params *p, double d, double ai, double aj, const double n[3], double F[3]) {
+  double abar = 2.0 * ai * aj / (ai + aj);
+  double m = 0.0;
+  if (p->f_er > 0.0 && d < 20.0 * p->lambda_d) {
+    double e = d >= 0.0 ? exp(-d / p->lambda_d) : 1.0;
+    m -= p->f_er * (abar / p->a0) * e;
+  }
+  if (p->hamaker > 0.0 && d < 4.0 * p->a0) {
+    double eps = p->vdw_eps * abar;
+    double dd = d >= 0.0 ? d : 0.0;
+    m += p->hamaker * abar / (12.0 * (dd * dd + eps * eps));
+  }
+  for (int q = 0; q < 3; ++q) F[q] = m * n[q];
 }
 
 /* ------------------------------------------------------------------------ */
@@ -448,22 +497,31 @@ int orc_pair_eval(const orc_params *p, double off, const double xi[3], const dou
   double Vj[3] = {ujm[0] - p->shear_rate * yjm, ujm[1], ujm[2]};
   double Wi[3] = {wi[0] - Om[0], wi[1] - Om[1], wi[2] - Om[2]};
   double Wj[3] = {wj[0] - Om[0], wj[1] - Om[1], wj[2] - Om[2]};
-  double Fli[3], Flj[3], Tli[3], Tlj[3];
-  orc_lubrication(p, r, ai, aj, Vi, Vj, Wi, Wj, Fli, Flj, Tli, Tlj);
-  double tap = lub_taper_factor(p, d, ai, aj);
-  for (int q = 0; q < 3; ++q) {
-    Fli[q] *= tap; Flj[q] *= tap; Tli[q] *= tap; Tlj[q] *= tap;
+  double Fli[3] = {0, 0, 0}, Flj[3] = {0, 0, 0}, Tli[3] = {0, 0, 0}, Tlj[3] = {0, 0, 0};
+  if (in_lub_range(p, r, ai, aj)) {
+    orc_lubrication(p, r, ai, aj, Vi, Vj, Wi, Wj, Fli, Flj, Tli, Tlj);
+    double tap = lub_taper_factor(p, d, ai, aj);
+    for (int q = 0; q < 3; ++q) {
+      Fli[q] *= tap; Flj[q] *= tap; Tli[q] *= tap; Tlj[q] *= tap;
+    }
+  }
+  /* electro-chemical force (Eq. 6), central */
+  double Fe[3] = {0, 0, 0};
+  if (orc_echem_range(p) > 0.0) {
+    double n[3] = {r[0] / dist, r[1] / dist, r[2] / dist};
+    orc_echem(p, d, ai, aj, n, Fe);
   }
   for (int q = 0; q < 3; ++q) {
-    Fi[q] = Fc[q] + Fli[q];
-    Fj[q] = -Fc[q] + Flj[q];
+    Fi[q] = Fc[q] + Fli[q] + Fe[q];
+    Fj[q] = -Fc[q] + Flj[q] - Fe[q];
     Ti[q] = Tci[q] + Tli[q];
     Tj[q] = Tcj[q] + Tlj[q];
   }
-  /* Eq. 9: S^C = r (x) F^C_ij, S^L = sym(r (x) F^L_ij), r = x_j - x_i */
+  /* Eq. 9: S^C = r (x) F^C_ij, S^L = sym(r (x) F^L_ij), S^E = r (x) F^E_ij,
+   * r = x_j - x_i */
   for (int a = 0; a < 3; ++a)
     for (int b = 0; b < 3; ++b)
-      S[3 * a + b] = r[a] * Fc[b] + 0.5 * (r[a] * Fli[b] + r[b] * Fli[a]);
+      S[3 * a + b] = r[a] * Fc[b] + 0.5 * (r[a] * Fli[b] + r[b] * Fli[a]) + r[a] * Fe[b];
   return flags;
 }
 
