@@ -74,7 +74,9 @@ class Params(Structure):
                 ("lub_eps", c_double), ("a0", c_double), ("lub_cutoff_mode", c_int32),
                 ("precision", c_int32), ("shear_rate", c_double), ("dt", c_double),
                 ("cell_size", c_double), ("capacity_M", c_int32), ("pair_capacity", c_int32),
-                ("lub_taper", c_double), ("cell_mode", c_int32), ("reserved_", c_int32)]
+                ("lub_taper", c_double), ("cell_mode", c_int32), ("reserved_", c_int32),
+                ("f_er", c_double), ("lambda_d", c_double), ("hamaker", c_double),
+                ("vdw_eps", c_double)]
 
 
 class Counters(Structure):

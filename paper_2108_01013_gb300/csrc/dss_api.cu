@@ -288,7 +288,7 @@ __global__ void k_default_vel(int n, const double* __restrict__ x, const InstGeo
 __global__ void k_attach_history(Geo g, StateBuf s, ListBuf L, const long long* __restrict__ keys,
                                  const double* __restrict__ xi, int k) {
   const int n = g.n;
-  const int P = L.start[n];
+  const int P = (int)min((int64_t)L.start[n], g.pcap);   // the host grew pcap to the list first
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
     int lo = 0, hi = n;
     while (hi - lo > 1) {
@@ -320,7 +320,7 @@ __global__ void k_attach_history(Geo g, StateBuf s, ListBuf L, const long long* 
 __global__ void k_history_out(Geo g, ListBuf L, long long* __restrict__ keys,
                               double* __restrict__ xi, int* __restrict__ counter, int cap) {
   const int n = g.n;
-  const int P = L.start[n];
+  const int P = (int)min((int64_t)L.start[n], g.pcap);
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
     const Xi4 v = L.xi[p];
     if (v.w == 0.0) continue;
@@ -386,12 +386,30 @@ int status_error(dss_handle* h) {
   return e ? e : DSS_OK;
 }
 
+// Outside a step (where the pair kernel reports an overflow and the step is
+// replayed), a list just built may hold more pairs than the pair buffers fit:
+// grow them before anything writes per-pair data.  Waits for the list and
+// returns the status of the kernels before it.
+int ensure_pair_capacity(dss_handle* h, int list) {
+  int r = sync_status(h);
+  if (r) return r;
+  if ((r = status_error(h))) { clear_err(h); return r; }
+  int P = 0;
+  CK(cudaMemcpyAsync(&P, h->lb[list].start + h->n, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (P > h->pcap) return alloc_pair_buffers(h, (int64_t)(P * 1.25) + 1024, true);
+  return DSS_OK;
+}
+
+
 // Cell grid of every instance (Sec. II A: cells of edge >= the largest
 // interaction range, 2 a_max + delta_max); cells are numbered instance-major.
 // Interaction range beyond contact of the largest pair a particle of radius a
 // can own (partners no larger than itself).
 double dmax_of(const dss_params& p, double a) {
-  return p.lub_cutoff_mode == 1 ? p.delta_lub * p.a0 : p.delta_lub * a;
+  const double dl = p.lub_cutoff_mode == 1 ? p.delta_lub * p.a0 : p.delta_lub * a;
+  const double de = echem_range(&p);
+  return de > dl ? de : dl;
 }
 
 // Size class of a particle of radius a on cells of edge cs: the particle's own
@@ -429,15 +447,20 @@ int geometry(dss_handle* h) {
   }
   // reach table from the largest radius of each class
   double A[8];
-  for (int c = 0; c < C; ++c)
-    A[c] = p.lub_cutoff_mode == 1 ? ((c + 1) * cs / (1.0 + 1e-9) - p.delta_lub * p.a0) * 0.5
-                                  : (c + 1) * cs / ((1.0 + 1e-9) * (2.0 + p.delta_lub));
+  const double de = echem_range(&p);
+  for (int c = 0; c < C; ++c) {
+    // the largest radius a with 2 a + dmax(a) <= (c + 1) cs / (1 + 1e-9)
+    const double X = (c + 1) * cs / (1.0 + 1e-9);
+    A[c] = p.lub_cutoff_mode == 1 ? (X - std::max(p.delta_lub * p.a0, de)) * 0.5
+                                  : std::min(X / (2.0 + p.delta_lub), (X - de) * 0.5);
+  }
   if (C == 1) A[0] = h->a_max;
   int reach = 1;
   memset(g.rtab, 0, sizeof(g.rtab));
   for (int c = 0; c < C; ++c)
     for (int c2 = 0; c2 <= c; ++c2) {
-      const double dpair = p.lub_cutoff_mode == 1 ? p.delta_lub * p.a0 : p.delta_lub * 0.5 * (A[c] + A[c2]);
+      const double dpair = std::max(de, p.lub_cutoff_mode == 1 ? p.delta_lub * p.a0
+                                                                 : p.delta_lub * 0.5 * (A[c] + A[c2]));
       // A[] already carries the 1e-9 margin of class_of: the ranges of the
       // class pair stay below (A + A2 + dpair), so no further margin
       int R = (int)std::ceil((A[c] + A[c2] + dpair) / cs);
@@ -487,6 +510,14 @@ int geometry(dss_handle* h) {
   g.ncell = (int)cells;
   h->cell_edge = cs;
   int M = p.capacity_M > 0 ? p.capacity_M : dss_capacity_estimate(h->a_min, h->a_max, p.a0);
+  if (p.capacity_M <= 0 && de > 0.0) {
+    // with electro-chemical forces pairs reach beyond the 2 a0 shell of
+    // Sec. II A: the shell then spans every partner within the range
+    const double outer = h->a_max + std::max(2.0 * p.a0, 2.0 * h->a_min + de);
+    const double v = (outer * outer * outer - h->a_max * h->a_max * h->a_max) /
+                     (h->a_min * h->a_min * h->a_min);
+    M = v < 2e9 ? std::max(M, (int)std::ceil(v)) : -1;
+  }
   if (M <= 0) return DSS_ERR_ARG;
   g.M = M;
   g.Ms = (M + 3) & ~3;   // row stride: rows start on 16-byte boundaries
@@ -498,7 +529,10 @@ bool valid_params(const dss_params* p) {
          (p->rho > 0) && (p->delta_lub >= 0) && (p->lub_eps > 0) && (p->a0 > 0) && (p->dt > 0) &&
          std::isfinite(p->shear_rate) && (p->lub_cutoff_mode == 0 || p->lub_cutoff_mode == 1) &&
          (p->precision == DSS_FP64 || p->precision == DSS_MIXED) &&
-         (p->lub_taper >= 0.0 && p->lub_taper < 1.0) && (p->cell_mode == 0 || p->cell_mode == 1);
+         (p->lub_taper >= 0.0 && p->lub_taper < 1.0) && (p->cell_mode == 0 || p->cell_mode == 1) &&
+         (p->f_er >= 0.0 && std::isfinite(p->f_er)) && (p->hamaker >= 0.0 && std::isfinite(p->hamaker)) &&
+         (!(p->f_er > 0.0) || (p->lambda_d > 0.0 && std::isfinite(p->lambda_d))) &&
+         (!(p->hamaker > 0.0) || (p->vdw_eps > 0.0 && std::isfinite(p->vdw_eps)));
 }
 
 // Common constructor: K instances of n[k] particles in boxes box[3k..3k+2]
@@ -577,11 +611,32 @@ int create_handle(dss_handle** out, const dss_params* p, int K, const int64_t* n
   g.f.taper = (float)p->lub_taper;
   g.f.delta = (float)p->delta_lub;
   g.f.delta_a0 = (float)(p->delta_lub * p->a0);
+  g.f_er = p->f_er;
+  g.lambda_d = p->lambda_d;
+  g.hamaker = p->hamaker;
+  g.vdw_eps = p->vdw_eps;
+  g.de = echem_range(p);
+  g.f.f_er = (float)(p->f_er / p->a0);   // F_ER / a0
+  g.f.inv_lambda = p->f_er > 0.0 ? (float)(1.0 / p->lambda_d) : 0.0f;
+  g.f.range_r = (float)(20.0 * p->lambda_d);
+  g.f.hamaker12 = (float)(p->hamaker / 12.0);
+  g.f.vdw_eps = (float)p->vdw_eps;
+  g.f.range_a = (float)(4.0 * p->a0);
   *out = h;
   return DSS_OK;
 }
 
 }  // namespace
+
+// Surface-distance range of the electro-chemical forces (Fig. 3): 20 lambda_D
+// for the repulsion, 4 a0 for the attraction, the larger of the active ones;
+// 0 when both are off.
+double echem_range(const dss_params* p) {
+  double r = 0.0;
+  if (p->f_er > 0.0 && 20.0 * p->lambda_d > r) r = 20.0 * p->lambda_d;
+  if (p->hamaker > 0.0 && 4.0 * p->a0 > r) r = 4.0 * p->a0;
+  return r;
+}
 
 void prof_mark(dss_handle* h, int k) {
   if (!h->profiling) return;
@@ -769,6 +824,8 @@ int dss_set_state(dss_handle* h, const double* x, const double* a, const int32_t
     // alpha^0 from one force evaluation at the initial state (empty history)
     seq_sort_enum(h, false, 0);
     h->cur = 1 - h->cur;
+    int rc = ensure_pair_capacity(h, 1 - h->hist);
+    if (rc) return rc;
     launch_forces(h, h->cur, 1 - h->hist, h->hist, 0, G_ACCEL, nullptr, nullptr);
     CK(cudaGetLastError());
     int r = sync_status(h);
@@ -849,7 +906,6 @@ int dss_get_pairs(dss_handle* h, int64_t* lohi, int64_t cap, int64_t* count) {
   CK(cudaStreamSynchronize(h->stream));
   *count = P;
   if (P == 0 || cap == 0) return DSS_OK;
-  if (P > h->pcap) return DSS_ERR_CAPACITY;
   // scratch: the partner-row buffer (n*M slots of >= 32 bytes >= 16 bytes per pair)
   long long* dev = (long long*)h->bw_rec;
   launch_pairs_out(h, list, dev);
@@ -874,6 +930,8 @@ int dss_force_eval(dss_handle* h, double* F, double* T) {
   const int n = (int)h->n;
   seq_sort_enum(h, false, 0);
   h->cur = 1 - h->cur;
+  int rc = ensure_pair_capacity(h, 1 - h->hist);
+  if (rc) return rc;
   launch_forces(h, h->cur, 1 - h->hist, h->hist, 0, G_EVAL, F ? h->io3 : nullptr,
                 T ? h->io3b : nullptr);
   CK(cudaGetLastError());
@@ -1039,6 +1097,10 @@ int dss_set_history(dss_handle* h, int64_t k, const int64_t* keys, const double*
   seq_sort_enum(h, false, 0);
   h->cur = 1 - h->cur;
   const int L = 1 - h->hist;
+  {
+    const int rc = ensure_pair_capacity(h, L);
+    if (rc) { cudaFree(dk); cudaFree(dx); return rc; }
+  }
   k_attach_history<<<pair_grid_blocks(h), 256, 0, h->stream>>>(h->g, h->st[h->cur], h->lb[L], dk, dx, (int)k);
   CK(cudaGetLastError());
   int r = sync_status(h);
@@ -1191,6 +1253,10 @@ uint64_t config_hash(const dss_handle* h) {
   v = fnv1a(v, c, sizeof(c));
   const int32_t m[2] = {p.lub_cutoff_mode, p.precision};
   v = fnv1a(v, m, sizeof(m));
+  if (echem_range(&p) > 0.0) {
+    const double e[4] = {p.f_er, p.lambda_d, p.hamaker, p.vdw_eps};
+    v = fnv1a(v, e, sizeof(e));
+  }
   return v;
 }
 
@@ -1311,7 +1377,7 @@ int dss_autotune(dss_handle* h, int32_t trial_steps, int32_t ncand, const double
   std::vector<char> ck(len);
   if ((r = dss_save(h, ck.data(), &len))) return r;
   const dss_params& p = h->p;
-  const double dmax = p.lub_cutoff_mode == 1 ? p.delta_lub * p.a0 : p.delta_lub * h->a_max;
+  const double dmax = dmax_of(p, h->a_max);
   const double cmin = (2.0 * h->a_max + dmax) * (1.0 + 1e-9) + 1e-12;
   const double base = p.cell_size > 0.0 ? p.cell_size : cmin;
   const bool prof_was = h->profiling;

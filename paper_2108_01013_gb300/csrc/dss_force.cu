@@ -238,6 +238,39 @@ __device__ __forceinline__ PairRes<float> pair_eval_mixed(const Geo& g, const In
     nxf = crossf(nn, Ft);
     q.xi[0] = xs0; q.xi[1] = xs1; q.xi[2] = xs2;
   }
+  // ---- electro-chemical forces, Eq. 6 (FP32; central, stresslet r (x) F).
+  // The range decisions (lubrication cutoff, 20 lambda_D, 4 a0) are taken on
+  // the FP32 gap unless it lies within 1e-5 of a threshold; there the FP64
+  // state decides, in the operations of the neighbour test.
+  bool lub_on = true;
+  if (g.de > 0.0) {
+    const float dl = g.mode == 1 ? g.f.delta_a0 : g.f.delta * 0.5f * S;
+    const float tol = 1e-5f * (S + dl);
+    const bool rep = g.f.f_er > 0.0f, att = g.f.hamaker12 > 0.0f;
+    bool in_r = d < g.f.range_r, in_a = d < g.f.range_a;
+    lub_on = d < dl;
+    if (fabsf(d - dl) < tol || (rep && fabsf(d - g.f.range_r) < tol) || (att && fabsf(d - g.f.range_a) < tol)) {
+      const int n = g.n;
+      double ex, ey, ez;
+      int sy;
+      min_image(I, sg.off, s.x[i], s.x[n + i], s.x[2 * n + i], s.x[j], s.x[n + j], s.x[2 * n + j], ex, ey, ez, sy);
+      const double ai = s.a[i], aj = s.a[j];
+      const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
+      const double sl = __dadd_rn(__dadd_rn(ai, aj), lub_delta(g, ai, aj));
+      lub_on = r2 < __dmul_rn(sl, sl);
+      const double d64 = sqrt(r2) - (ai + aj);
+      in_r = d64 < 20.0 * g.lambda_d;
+      in_a = d64 < 4.0 * g.a0;
+    }
+    const float abar = 2.0f * Ai * Bj / (Ai + Bj);
+    float m = 0.0f;
+    if (rep && in_r) m -= g.f.f_er * abar * (d >= 0.0f ? __expf(-d * g.f.inv_lambda) : 1.0f);
+    if (att && in_a) {
+      const float eps = g.f.vdw_eps * abar, dp = fmaxf(d, 0.0f);
+      m += __fdividef(g.f.hamaker12 * abar, fmaf(dp, dp, eps * eps));
+    }
+    Fc = Fc + m * nn;
+  }
   // ---- lubrication, App. A (FP32)
   const float iS = __fdividef(1.0f, S), iS2 = iS * iS, iS3 = iS2 * iS;
   float ds = 2.0f * d * iS;
@@ -268,6 +301,11 @@ __device__ __forceinline__ PairRes<float> pair_eval_mixed(const Geo& g, const In
   const F3 ndV = crossf(nn, dV);
   F3 Tli = k6 * (ybi * ndV - (yci * tangf(nn, Wi) + ycx * tangf(nn, Wj)) + yhi * nperp);
   F3 Tlj = k6 * (ybj * ndV - (ycx * tangf(nn, Wi) + ycj * tangf(nn, Wj)) + yhj * nperp);
+  if (!lub_on) {
+    Fl = f3(0.0f, 0.0f, 0.0f);
+    Tli = Fl;
+    Tlj = Fl;
+  }
   if (g.f.taper > 0.0f) {
     // differentiable cutoff: smoothstep over the last fraction w of the range
     const float dl = g.mode == 1 ? g.f.delta_a0 : g.f.delta * 0.5f * S;

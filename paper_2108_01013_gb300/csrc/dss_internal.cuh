@@ -60,9 +60,12 @@ struct Geo {
   double k6;          // 6 pi eta0
   double k8;          // 8 pi eta0
   double taper;       // lubrication taper width w (0: hard cutoff)
+  double f_er, lambda_d, hamaker, vdw_eps;   // electro-chemical forces (Eq. 6)
+  double de;          // their range as a surface distance (0: off)
   struct {             // FP32 copies of the model constants (mixed precision)
     float kn, kt, mu_kt, dt, eps, k6, k8, mass_c;
     float taper, delta, delta_a0;
+    float f_er, inv_lambda, range_r, hamaker12, vdw_eps, range_a;   // f_er: F_ER / a0
   } f;
 };
 
@@ -107,9 +110,16 @@ __device__ __forceinline__ double le_offset(const Geo& g, const InstGeo& I, int6
 }
 
 // Interaction range beyond contact for the pair.
-__device__ __forceinline__ double pair_delta(const Geo& g, double ai, double aj) {
+__device__ __forceinline__ double lub_delta(const Geo& g, double ai, double aj) {
   if (g.mode == 1) return __dmul_rn(g.delta, g.a0);
   return __dmul_rn(__dmul_rn(g.delta, __dadd_rn(ai, aj)), 0.5);
+}
+
+// Listing range of a pair: the larger of the lubrication cutoff and the
+// electro-chemical range.
+__device__ __forceinline__ double pair_delta(const Geo& g, double ai, double aj) {
+  const double dl = lub_delta(g, ai, aj);
+  return g.de > dl ? g.de : dl;
 }
 
 // Minimum-image separation r = x_j - x_i under Lees-Edwards conditions,
@@ -465,6 +475,7 @@ int pair_grid_blocks(const dss_handle* h);
 void launch_scan(dss_handle* h, const int* in, int* out, int count, int which, bool zero_in);
 int scan_tiles_for(int count);
 int enum_tiles_for(int n);
+double echem_range(const dss_params* p);
 int enum_scan_tiles_for(int n);
 int bw_slot_values();
 // Marks the start of kernel k of a step when profiling (event record node

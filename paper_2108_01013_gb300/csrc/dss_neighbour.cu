@@ -21,6 +21,7 @@ struct EnumCtx {
   const float4* __restrict__ posf;
   float4 pi;
   float sc, sa;     // cutoff of pair (i, j): s = a_j sc + sa (a_i + a_j + delta)
+  float sa2;        // with electro-chemical forces the cutoff is max(s, a_j + sa2)
   float m2;         // r^2 margin of the FP32 decision
   float hx, hy, hz; // half box: a separation beyond it is decided exactly
   bool img;         // the stencil reaches past half the box along some axis
@@ -46,11 +47,13 @@ __device__ __forceinline__ void enum_init(EnumCtx& e, const Geo& g, const InstGe
   // far inside the margin
   if (g.mode == 1) {
     e.sc = 1.0f;
-    e.sa = e.pi.w + (float)(g.delta * g.a0);
+    e.sa = e.pi.w + (float)(g.delta * g.a0 > g.de ? g.delta * g.a0 : g.de);
   } else {
     e.sc = 1.0f + 0.5f * (float)g.delta;
     e.sa = e.pi.w * e.sc;
   }
+  // the electro-chemical range (a surface distance): a_i + a_j + de
+  e.sa2 = e.pi.w + (float)g.de;
   e.m2 = I.r2_margin;
   e.hx = I.halfLf[0];
   e.hy = I.halfLf[1];
@@ -75,6 +78,7 @@ __device__ __forceinline__ void enum_init(EnumCtx& e, const Geo& g, const InstGe
 // FP32 decision on cell-local coordinates: certainly a pair, certainly not,
 // or (within the margin of the cutoff, or past half the box) the exact FP64
 // predicate.
+template <bool ECH>
 __device__ __forceinline__ void scan_range(EnumCtx& e, int jb, int je, float cxo, float cyo, float czo) {
   const float px = e.pi.x - cxo, py = e.pi.y - cyo, pz = e.pi.z - czo;
   for (int j = jb; j < je; ++j) {
@@ -84,7 +88,8 @@ __device__ __forceinline__ void scan_range(EnumCtx& e, int jb, int je, float cxo
     if (e.img && (fabsf(dx) > e.hx || fabsf(dy) > e.hy || fabsf(dz) > e.hz)) {
       dec = -1;
     } else {
-      const float sv = fmaf(pj.w, e.sc, e.sa);
+      float sv = fmaf(pj.w, e.sc, e.sa);
+      if (ECH) sv = fmaxf(sv, pj.w + e.sa2);
       const float t = fmaf(-sv, sv, fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
       dec = t < -e.m2 ? 1 : (t > e.m2 ? 0 : -1);
     }
@@ -139,6 +144,7 @@ __device__ __forceinline__ void finish_rows(const Geo& g, const StateBuf& s, Lis
   if (lane == 0 && (wtile + 1) * 32 >= n) L.start[n] = prefix + agg;
 }
 
+template <bool ECH>
 __global__ void __launch_bounds__(kThreads, 8)
 k_enumerate(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ sgk, StateBuf s,
             const float4* __restrict__ posf, const int* __restrict__ cellid,
@@ -166,17 +172,17 @@ k_enumerate(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ s
     const int c = cellid[i] - cb;
     const int cx = c % nx, cy = (c / nx) % ny, cz = c / (nx * ny);
     // own cell (partners after i) and the cell x+1
-    scan_range(e, i + 1, cell_start[cb + c + 1], 0.f, 0.f, 0.f);
+    scan_range<ECH>(e, i + 1, cell_start[cb + c + 1], 0.f, 0.f, 0.f);
     {
       const int q = cb + (cz * ny + cy) * nx + wrapi(cx + 1, nx);
-      scan_range(e, cell_start[q], cell_start[q + 1], I.csf[0], 0.f, 0.f);
+      scan_range<ECH>(e, cell_start[q], cell_start[q + 1], I.csf[0], 0.f, 0.f);
     }
     // layer y, z+1: three x cells
     {
       const int qz = wrapi(cz + 1, nz);
       for (int ox = -1; ox <= 1; ++ox) {
         const int q = cb + (qz * ny + cy) * nx + wrapi(cx + ox, nx);
-        scan_range(e, cell_start[q], cell_start[q + 1], (float)ox * I.csf[0], 0.f, I.csf[2]);
+        scan_range<ECH>(e, cell_start[q], cell_start[q + 1], (float)ox * I.csf[0], 0.f, I.csf[2]);
       }
     }
     // layer y+1: 3x3 cells, or across y = L_y the 4 x cells covering the
@@ -190,7 +196,7 @@ k_enumerate(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ s
         const int q = cb + (qz * ny + qy) * nx + wrapi(cx + ox, nx);
         float cxo, cyo, czo;
         stencil_shift(I, ox, 1, oz, le ? 1 : 0, fsh, offr, cxo, cyo, czo);
-        scan_range(e, cell_start[q], cell_start[q + 1], cxo, cyo, czo);
+        scan_range<ECH>(e, cell_start[q], cell_start[q + 1], cxo, cyo, czo);
       }
     }
   }
@@ -206,6 +212,7 @@ k_enumerate(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ s
 // once, by its larger member (or by the half stencil within a class).  Rows
 // crossing y = L_y (either way) cover the x range shifted by the
 // Lees-Edwards offset.
+template <bool ECH>
 __global__ void __launch_bounds__(kThreads, 8)
 k_enumerate_classes(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ sgk, StateBuf s,
                     const float4* __restrict__ posf, const int* __restrict__ cellid,
@@ -234,7 +241,7 @@ k_enumerate_classes(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __rest
     const int c = (cellid[i] - I.cell_base) % layer;
     const int cx = c % nx, cy = (c / nx) % ny, cz = c / (nx * ny);
     // own bin, partners after i
-    scan_range(e, i + 1, cell_start[cellid[i] + 1], 0.f, 0.f, 0.f);
+    scan_range<ECH>(e, i + 1, cell_start[cellid[i] + 1], 0.f, 0.f, 0.f);
     for (int c2 = cls; c2 >= 0; --c2) {
       const int R = g.rtab[cls][c2];
       const bool half = c2 == cls;
@@ -280,7 +287,7 @@ k_enumerate_classes(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __rest
                   } while (j >= kend);
                   stencil_shift(I, ox + k, oy, oz, le, fsh, offr, cxo, cyo, czo);
                 }
-                scan_range(e, j, j + 1, cxo, cyo, czo);
+                scan_range<ECH>(e, j, j + 1, cxo, cyo, czo);
               }
             }
             ox += m;
@@ -300,12 +307,17 @@ void launch_enumerate(dss_handle* h, int stbuf, int dst_list, int adv) {
   const int n = (int)h->n;
   ListBuf& L = h->lb[dst_list];
   prof_mark(h, 4);
+  // the pair-mean lubrication cutoff and the electro-chemical range combine
+  // by a maximum, which only that case needs in the candidate test
+  const bool ech = h->g.de > 0.0 && h->g.mode == 0;
+  auto kc = ech ? k_enumerate_classes<true> : k_enumerate_classes<false>;
+  auto k1 = ech ? k_enumerate<true> : k_enumerate<false>;
   if (h->g.nclass > 1)
-    k_enumerate_classes<<<enum_tiles_for(n), kThreads, 0, h->stream>>>(
+    kc<<<enum_tiles_for(n), kThreads, 0, h->stream>>>(
         h->g, h->ig, h->sg, h->st[stbuf], h->posf, h->cellid, h->cell_start, L, h->bw_count,
         h->scan_status + h->scan_tiles_max, h->scan_ticket + 1, h->status);
   else
-    k_enumerate<<<enum_tiles_for(n), kThreads, 0, h->stream>>>(
+    k1<<<enum_tiles_for(n), kThreads, 0, h->stream>>>(
         h->g, h->ig, h->sg, h->st[stbuf], h->posf, h->cellid, h->cell_start, L, h->bw_count,
         h->scan_status + h->scan_tiles_max, h->scan_ticket + 1, h->status, adv);
   h->last_list = dst_list;

@@ -161,7 +161,9 @@ extern "C" int dss_pairs_noalloc(const double* x, const double* a, const int32_t
       !(a_max > 0.0) || nstep < 0 || (p->lub_cutoff_mode != 0 && p->lub_cutoff_mode != 1))
     return DSS_ERR_ARG;
   // cell grid: edge >= the largest interaction range, as in the main path
-  const double dmax = p->lub_cutoff_mode == 1 ? p->delta_lub * p->a0 : p->delta_lub * a_max;
+  const double dl = p->lub_cutoff_mode == 1 ? p->delta_lub * p->a0 : p->delta_lub * a_max;
+  const double de = echem_range(p);
+  const double dmax = de > dl ? de : dl;
   const double cmin = (2.0 * a_max + dmax) * (1.0 + 1e-9) + 1e-12;
   NoAllocGrid q;
   for (int d = 0; d < 3; ++d) {
@@ -198,6 +200,7 @@ extern "C" int dss_pairs_noalloc(const double* x, const double* a, const int32_t
   g.delta = p->delta_lub;
   g.a0 = p->a0;
   g.mode = p->lub_cutoff_mode;
+  g.de = de;
   I.gdot = p->shear_rate;
   g.dt = p->dt;
   // Lees-Edwards offset at time nstep*dt, with the same operations as the main path

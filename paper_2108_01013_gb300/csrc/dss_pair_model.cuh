@@ -158,6 +158,14 @@ __device__ __forceinline__ Dual<K> log(const Dual<K>& a) {
   return r;
 }
 template <int K>
+__device__ __forceinline__ Dual<K> exp(const Dual<K>& a) {
+  Dual<K> r;
+  r.v = ::exp(a.v);
+#pragma unroll
+  for (int k = 0; k < K; ++k) r.d[k] = r.v * a.d[k];
+  return r;
+}
+template <int K>
 __device__ __forceinline__ Dual<K> fabs(const Dual<K>& a) {
   return a.v < 0.0 ? -a : a;
 }
@@ -200,8 +208,9 @@ struct PairParams {
   T kn, kt, gn, mu, delta;
 };
 
-// Outputs: force on i (F = Fc + Fl), torques on i and j, the contact and
-// lubrication parts of the force, the new stretch (i -> j orientation).
+// Outputs: force on i (F = Fc + Fl), torques on i and j, the parts of the
+// force whose stresslet is r (x) F (contact and electro-chemical, Fc) and
+// sym(r (x) F) (lubrication, Fl), the new stretch (i -> j orientation).
 template <typename T>
 struct PairModelOut {
   Vec3<T> F, Ti, Tj, Fc, Fl, xi;
@@ -244,6 +253,28 @@ __device__ __forceinline__ PairModelOut<T> pair_model(const Geo& g, const InstGe
     Tcj = aj * nxf;
     o.xi = xs;
   }
+  // ---- electro-chemical forces, Eq. 6 (central; stresslet r (x) F like contact)
+  bool lub_on = true;
+  if (g.de > 0.0) {
+    const double abar = 2.0 * ai * aj / (ai + aj);
+    T m = zero;
+    if (g.f_er > 0.0 && val(d) < 20.0 * g.lambda_d)
+      m = m - (g.f_er * (abar / g.a0)) * (val(d) >= 0.0 ? exp(-d / g.lambda_d) : cst<T>(1.0));
+    if (g.hamaker > 0.0 && val(d) < 4.0 * g.a0) {
+      const double eps = g.vdw_eps * abar;
+      const T dp = val(d) >= 0.0 ? d : zero;
+      m = m + (g.hamaker * abar) / (12.0 * (dp * dp + eps * eps));
+    }
+    o.Fc = o.Fc + m * n;
+    // lubrication only within its own cutoff: the listing predicate with the
+    // lubrication range, in the same operations as the neighbour test
+    const double rx = val(r.x), ry = val(r.y), rz = val(r.z);
+    const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(rx, rx), __dmul_rn(ry, ry)), __dmul_rn(rz, rz));
+    const double dl = g.mode == 1 ? __dmul_rn(val(q.delta), g.a0)
+                                  : __dmul_rn(__dmul_rn(val(q.delta), __dadd_rn(ai, aj)), 0.5);
+    const double sl = __dadd_rn(__dadd_rn(ai, aj), dl);
+    lub_on = r2 < __dmul_rn(sl, sl);
+  }
   // ---- lubrication, App. A
   T ds = 2.0 * d / S;
   if (!(val(ds) > 0.0)) ds = zero;
@@ -285,6 +316,11 @@ __device__ __forceinline__ PairModelOut<T> pair_model(const Geo& g, const InstGe
       Tli = s * Tli;
       Tlj = s * Tlj;
     }
+  }
+  if (!lub_on) {
+    Fl = mk3<T>(zero, zero, zero);
+    Tli = Fl;
+    Tlj = Fl;
   }
   o.Fl = Fl;
   o.F = o.Fc + Fl;

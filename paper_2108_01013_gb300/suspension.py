@@ -18,7 +18,7 @@ from . import _native as nat
 def default_params(box=None, *, kn=1e4, kt=None, gamma_n=None, mu=0.5, eta0=1.0, rho=1.0,
                    delta_lub=0.05, lub_eps=1e-3, a0=1.0, lub_cutoff_mode=0, precision="fp64",
                    shear_rate=1.0, dt=1e-4, cell_size=0.0, capacity_M=0, pair_capacity=0,
-                   lub_taper=0.0, cell_mode=0):
+                   lub_taper=0.0, cell_mode=0, f_er=0.0, lambda_d=0.05, hamaker=0.0, vdw_eps=0.01):
     """Model parameters; kt defaults to kn/2 and gamma_n to 1e-7 kn / gdot."""
     p = nat.Params()
     p.kn = kn
@@ -34,6 +34,7 @@ def default_params(box=None, *, kn=1e4, kt=None, gamma_n=None, mu=0.5, eta0=1.0,
     p.cell_size, p.capacity_M, p.pair_capacity = cell_size, capacity_M, pair_capacity
     p.lub_taper = lub_taper
     p.cell_mode = cell_mode
+    p.f_er, p.lambda_d, p.hamaker, p.vdw_eps = f_er, lambda_d, hamaker, vdw_eps
     return p
 
 
