@@ -104,9 +104,10 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--modes", default="fp64,batched,poly1m,adjoint",
+    ap.add_argument("--modes", default="fp64,echem,batched,poly1m,adjoint",
                     help="extra modes measured in the same run: fp64 (the headline workload in "
-                         "FP64), batched (256-instance flow-curve sweep, mixed), poly1m (1M "
+                         "FP64), echem (the headline packing with the electro-chemical forces, "
+                         "mixed), batched (256-instance flow-curve sweep, mixed), poly1m (1M "
                          "polydisperse, mixed and FP64), adjoint (gradient of the 200-step "
                          "viscosity of 20k spheres); 'none' for none")
     ap.add_argument("--mode-steps", type=int, default=400)
@@ -240,6 +241,41 @@ def mode_fp64(dss, g, spec, kw, args, flush, stream):
                                                       "l2": "flushed before every timed step"},
            "kernels_ms": profile_pass(s, 20, flush)}
     s.close()
+    return out
+
+
+# The electro-chemical settings of the paper's shear-rate studies (Table 2:
+# lambda_D = 0.05 a0, repulsion only, delta_lub = 0.10 a0; Table 4 (SI):
+# lambda_D = 0.0225 a0, F^R/F^A = 19 at contact, delta_lub = 0.25 a0, mu = 0.5),
+# at gdot/gdot_0 = 0.1 (F_ER = 10 eta0 a0^2 gdot with gdot = 1).  The van der
+# Waals constant follows from the contact ratio: F^A(0) = A / (12 eps^2) for
+# abar = a0 and eps = 0.01 abar.
+ECHEM_SETTINGS = {
+    "repulsion": dict(f_er=10.0, lambda_d=0.05, hamaker=0.0, vdw_eps=0.01, delta_lub=0.10),
+    "repulsion_attraction": dict(f_er=10.0, lambda_d=0.0225, hamaker=10.0 / 19.0 * 12.0 * 1e-4,
+                                 vdw_eps=0.01, delta_lub=0.25, mu=0.5),
+}
+
+
+def mode_echem(dss, g, spec, kw, args, flush, stream):
+    """The headline packing with the electro-chemical forces of Eq. 6 (mixed
+    precision): pairs are listed out to their range."""
+    n = g["a"].shape[0]
+    out = {"config": {"workload": spec.name + "_echem", "n": n, "precision": "mixed",
+                      "l2": "flushed before every timed step"}}
+    for name, e in ECHEM_SETTINGS.items():
+        kk = dict(kw)
+        kk.update(e)
+        p = dss.default_params(g["box"], precision="mixed", **kk)
+        s = dss.Suspension(g["x"], g["a"], g["box"], p, ids=g["ids"], stream=stream)
+        time_steps(s, 5, flush)
+        steps = max(args.mode_steps // 2, 1)
+        t = time_steps(s, steps, flush)
+        c = s.counters()
+        out[name] = {"value": n * steps / (t * 1e-3), "unit": "particle-steps/s", "ms_per_step": t / steps,
+                     "steps": steps, "params": e, "pairs": c["npairs"], "contacts": c["ncontacts"], "M": c["M"],
+                     "cells": list(c["ncell"]), "kernels_ms": profile_pass(s, 10, flush)}
+        s.close()
     return out
 
 
@@ -476,6 +512,9 @@ def main():
         if "fp64" in modes:
             with torch.cuda.nvtx.range("fp64"):
                 extra["fp64"] = mode_fp64(dss, g, spec, kw, args, flush, stream)
+        if "echem" in modes:
+            with torch.cuda.nvtx.range("echem"):
+                extra["echem"] = mode_echem(dss, g, spec, kw, args, flush, stream)
         del flush
         if batch is not None:
             with torch.cuda.nvtx.range("batched"):

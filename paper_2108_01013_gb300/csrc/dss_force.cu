@@ -13,7 +13,9 @@
 //   atomic.
 // k_gather<MIXED>: one thread per particle: its own sum plus the partner
 //   records of its row taken in increasing owner index (a fixed order, so the
-//   result is bitwise reproducible), Stokes drag (Eq. A1) and the corrector
+//   result is bitwise reproducible; rows of more than 8 records are summed by
+//   the whole warp, ranks counted and placed, then a fixed reduction), Stokes
+//   drag (Eq. A1) and the corrector
 //   of Eq. 15d.  K leading blocks reduce each instance's bulk stress of
 //   Eq. 8 from the pair blocks' partials; the last block of the gather to
 //   finish adds them to the running sums and commits the step.
@@ -592,21 +594,45 @@ __device__ __forceinline__ void sum_records(const R* __restrict__ row, int cnt, 
     }
     return;
   }
-  int prev = -1;
-  for (int t = 0; t < cnt; ++t) {
-    int best = INT_MAX, bs = 0;
-    for (int q = 0; q < cnt; ++q) {
-      const int o = bits_owner(row[q * kSlot + 6]);
-      if (o > prev && o < best) { best = o; bs = q; }
+}
+
+constexpr int kHeavyWin = 256;   // ranks placed per pass of a heavy row
+
+// A row of more than 8 records, summed by the whole warp: each record's rank
+// in owner order is counted (the lanes read the owner words together), the
+// ranks are placed in a per-warp table, and the records are added in rank
+// order, lane k taking ranks k, k + 32, ..., then a fixed butterfly.  The
+// result is a function of the set of records alone.  Every lane returns the
+// total.
+template <typename R>
+__device__ __forceinline__ void warp_sum_row(const R* __restrict__ row, int cc, int* slots, R tot[6]) {
+  const int lane = threadIdx.x & 31;
+  R part[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
+  for (int base = 0; base < cc; base += kHeavyWin) {
+    for (int q = lane; q < cc; q += 32) {
+      const int oq = bits_owner(row[q * kSlot + 6]);
+      int rk = 0;
+      for (int r = 0; r < cc; ++r) {
+        const int o = bits_owner(row[r * kSlot + 6]);
+        rk += (o < oq) || (o == oq && r < q);
+      }
+      if (rk >= base && rk < base + kHeavyWin) slots[rk - base] = q;
     }
-    R b[8];
-    load_record(row + bs * kSlot, b);
+    __syncwarp();
+    const int we = min(cc - base, kHeavyWin);
+    for (int k = lane; k < we; k += 32) {
+      R b[8];
+      load_record(row + slots[k] * kSlot, b);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      F[c] += b[c];
-      T[c] += b[3 + c];
+      for (int c = 0; c < 6; ++c) part[c] += b[c];
     }
-    prev = best;
+    __syncwarp();
+  }
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) part[c] += __shfl_xor_sync(0xffffffffu, part[c], d);
+    tot[c] = part[c];
   }
 }
 
@@ -620,13 +646,16 @@ __device__ __forceinline__ bool gather_one(const Geo& g, const InstGeo* __restri
                                            const void* __restrict__ own_v,
                                            const int* __restrict__ bw_count, const void* __restrict__ bw_v,
                                            double* __restrict__ Fout, double* __restrict__ Tout,
-                                           DevStatus* st, int mode, int j) {
+                                           DevStatus* st, int mode, int j0, int* slots) {
   using R = typename std::conditional<MIXED, float, double>::type;
   const R* __restrict__ own = static_cast<const R*>(own_v);
   const R* __restrict__ bw = static_cast<const R*>(bw_v);
   const int n = g.n;
-  if (j >= n) return false;
-  int cnt = __ldg(bw_count + j);
+  // every lane of the warp takes part in the heavy rows below; lanes past
+  // the last particle work on particle 0 and write nothing
+  const bool valid = j0 < n;
+  const int j = valid ? j0 : 0;
+  int cnt = valid ? __ldg(bw_count + j) : 0;
   R F[3], T[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -656,7 +685,23 @@ __device__ __forceinline__ bool gather_one(const Geo& g, const InstGeo* __restri
     }
   }
   cnt = cnt < g.M ? cnt : g.M;
-  sum_records<R>(bw + (int64_t)j * g.M * kSlot, cnt, F, T);
+  if (cnt <= 8) sum_records<R>(bw + (int64_t)j * g.M * kSlot, cnt, F, T);
+  unsigned heavy = __ballot_sync(0xffffffffu, cnt > 8);
+  while (heavy) {
+    const int src = __ffs(heavy) - 1;
+    heavy &= heavy - 1u;
+    const int jj = __shfl_sync(0xffffffffu, j, src), cc = __shfl_sync(0xffffffffu, cnt, src);
+    R tot[6];
+    warp_sum_row<R>(bw + (int64_t)jj * g.M * kSlot, cc, slots, tot);
+    if ((int)(threadIdx.x & 31) == src) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        F[c] += tot[c];
+        T[c] += tot[3 + c];
+      }
+    }
+  }
+  if (!valid) return false;
   if constexpr (MIXED) {
     // Stokes drag on the FP32 velocities relative to the ambient flow
     const float af = (float)a;
@@ -729,6 +774,7 @@ k_gather(Geo g, const InstGeo* __restrict__ ig, StateBuf s, const void* __restri
   // would write can be the committed one.  Every block still reaches the
   // counter below.
   __shared__ int s_err0;
+  __shared__ int s_slot[kThreads / 32][kHeavyWin];
   if (threadIdx.x == 0) s_err0 = dev_err(st);
   __syncthreads();
   bool fence = false;
@@ -738,7 +784,8 @@ k_gather(Geo g, const InstGeo* __restrict__ ig, StateBuf s, const void* __restri
       fence = threadIdx.x < 9;
     } else {
       const int j = (int)(blockIdx.x - g.K) * blockDim.x + threadIdx.x;
-      fence = gather_one<MIXED>(g, ig, s, own_v, bw_count, bw_v, Fout, Tout, st, mode, j);
+      fence = gather_one<MIXED>(g, ig, s, own_v, bw_count, bw_v, Fout, Tout, st, mode, j,
+                                s_slot[threadIdx.x >> 5]);
     }
   }
   __shared__ bool last;
