@@ -244,7 +244,7 @@ def mode_fp64(dss, g, spec, kw, args, flush, stream):
     return out
 
 
-# The electro-chemical settings of the paper's shear-rate studies (Table 2:
+# The electro-chemical settings of the paper's shear-rate studies (Table 3:
 # lambda_D = 0.05 a0, repulsion only, delta_lub = 0.10 a0; Table 4 (SI):
 # lambda_D = 0.0225 a0, F^R/F^A = 19 at contact, delta_lub = 0.25 a0, mu = 0.5),
 # at gdot/gdot_0 = 0.1 (F_ER = 10 eta0 a0^2 gdot with gdot = 1).  The van der
@@ -258,7 +258,7 @@ ECHEM_SETTINGS = {
 
 
 def mode_echem(dss, g, spec, kw, args, flush, stream):
-    """The headline packing with the electro-chemical forces of Eq. 6 (mixed
+    """The headline packing with the electro-chemical forces of Eq. 6-7 (mixed
     precision): pairs are listed out to their range."""
     n = g["a"].shape[0]
     out = {"config": {"workload": spec.name + "_echem", "n": n, "precision": "mixed",

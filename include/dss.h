@@ -84,12 +84,12 @@ typedef struct dss_params {
                                    classes search larger stencils (Sec. II A, for highly
                                    polydisperse suspensions); cell_size 0: auto */
   int32_t reserved_;
-  double f_er;                  /* Eq. 6a: double-layer repulsion -F_ER (abar/a0) exp(-d/lambda_D) n,
+  double f_er;                  /* Eq. 6: double-layer repulsion -F_ER (abar/a0) exp(-d/lambda_D) n,
                                    acting below d = 20 lambda_D (Fig. 3); 0: off */
   double lambda_d;              /* Debye length lambda_D (> 0 when f_er > 0) */
-  double hamaker;               /* Eq. 6b: van der Waals attraction A abar / (12 (d^2 + eps^2)) n,
+  double hamaker;               /* Eq. 7: van der Waals attraction A abar / (12 (d^2 + eps^2)) n,
                                    acting below d = 4 a0 (Fig. 3); 0: off */
-  double vdw_eps;               /* eps / abar of Eq. 6b (> 0 when hamaker > 0).  Pairs are
+  double vdw_eps;               /* eps / abar of Eq. 7 (> 0 when hamaker > 0).  Pairs are
                                    listed out to the larger of the lubrication and
                                    electro-chemical ranges; lubrication acts within its own
                                    range only.  abar = 2 a_i a_j / (a_i + a_j) */

@@ -15,7 +15,7 @@ Parity status of each function (see the pins in ``tests/test_oracle_*.py``):
   contact                           pinned (head-on spring-dashpot closed
                                     form, Coulomb-capped tangential loading)
   echem / echem_range               pinned (integrates to the closed-form
-                                    potentials of Eq. 6, Debye decay,
+                                    potentials of Eq. 6-7, Debye decay,
                                     harmonic-radius scaling, flat and
                                     continuous at contact, exact ranges,
                                     central and balanced in pair_eval)
@@ -210,7 +210,7 @@ def lubrication(p: Params, r, ai, aj, Vi, Vj, Wi, Wj):
 
 
 def echem(p: Params, d, ai, aj, n):
-    """Eq. 6 electro-chemical force on i from j at surface distance d along n."""
+    """Eq. 6-7 electro-chemical force on i from j at surface distance d along n."""
     F = np.zeros(3)
     lib().orc_echem(ctypes.byref(p), float(d), float(ai), float(aj), _ptr(_d(n)), _ptr(F))
     return F

@@ -61,8 +61,8 @@ typedef struct orc_params {
   double shear_rate, dt;        /* gdot, time step */
   double L[3];                  /* box edges */
   double lub_taper;             /* w of the lubrication taper; 0: hard cutoff */
-  double f_er, lambda_d;        /* Eq. 6a (repulsion): magnitude F_ER, Debye length */
-  double hamaker, vdw_eps;      /* Eq. 6b (attraction): Hamaker constant A, eps / abar */
+  double f_er, lambda_d;        /* Eq. 6 (repulsion): magnitude F_ER, Debye length */
+  double hamaker, vdw_eps;      /* Eq. 7 (attraction): Hamaker constant A, eps / abar */
 } orc_params;
 
 typedef struct orc_sys {
@@ -439,7 +439,7 @@ static double lub_taper_factor(const orc_params *p, double d, double ai, double 
 }
 
 /* Electro-chemical force on i from j at surface distance d, along the unit
- * vector n from i to j (Eq. 6): the double-layer repulsion
+ * vector n from i to j (Eq. 6-7): the double-layer repulsion
  * -F_ER (abar/a0) exp(-d/lambda_D) n (its contact value for d < 0), acting
  * below d = 20 lambda_D, plus the van der Waals attraction
  * A abar / (12 (d^2 + eps^2)) n (its contact value for d < 0), acting below
@@ -505,7 +505,7 @@ int orc_pair_eval(const orc_params *p, double off, const double xi[3], const dou
       Fli[q] *= tap; Flj[q] *= tap; Tli[q] *= tap; Tlj[q] *= tap;
     }
   }
-  /* electro-chemical force (Eq. 6), central */
+  /* electro-chemical force (Eq. 6-7), central */
   double Fe[3] = {0, 0, 0};
   if (orc_echem_range(p) > 0.0) {
     double n[3] = {r[0] / dist, r[1] / dist, r[2] / dist};

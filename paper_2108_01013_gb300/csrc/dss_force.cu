@@ -240,7 +240,7 @@ __device__ __forceinline__ PairRes<float> pair_eval_mixed(const Geo& g, const In
     nxf = crossf(nn, Ft);
     q.xi[0] = xs0; q.xi[1] = xs1; q.xi[2] = xs2;
   }
-  // ---- electro-chemical forces, Eq. 6 (FP32; central, stresslet r (x) F).
+  // ---- electro-chemical forces, Eq. 6-7 (FP32; central, stresslet r (x) F).
   // The range decisions (lubrication cutoff, 20 lambda_D, 4 a0) are taken on
   // the FP32 gap unless it lies within 1e-5 of a threshold; there the FP64
   // state decides, in the operations of the neighbour test.

@@ -60,7 +60,7 @@ struct Geo {
   double k6;          // 6 pi eta0
   double k8;          // 8 pi eta0
   double taper;       // lubrication taper width w (0: hard cutoff)
-  double f_er, lambda_d, hamaker, vdw_eps;   // electro-chemical forces (Eq. 6)
+  double f_er, lambda_d, hamaker, vdw_eps;   // electro-chemical forces (Eq. 6-7)
   double de;          // their range as a surface distance (0: off)
   struct {             // FP32 copies of the model constants (mixed precision)
     float kn, kt, mu_kt, dt, eps, k6, k8, mass_c;

@@ -253,7 +253,7 @@ __device__ __forceinline__ PairModelOut<T> pair_model(const Geo& g, const InstGe
     Tcj = aj * nxf;
     o.xi = xs;
   }
-  // ---- electro-chemical forces, Eq. 6 (central; stresslet r (x) F like contact)
+  // ---- electro-chemical forces, Eq. 6-7 (central; stresslet r (x) F like contact)
   bool lub_on = true;
   if (g.de > 0.0) {
     const double abar = 2.0 * ai * aj / (ai + aj);

@@ -1,4 +1,4 @@
-"""Electro-chemical forces (Eq. 6; Fig. 3): Debye-screened double-layer
+"""Electro-chemical forces (Eq. 6-7; Fig. 3): Debye-screened double-layer
 repulsion below a surface distance of 20 lambda_D and regularised van der
 Waals attraction below 4 a0, with their stresslet in the bulk stress.  GPU
 against the FP64 oracle: pair sets listed out to the enlarged range bit for

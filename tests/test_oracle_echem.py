@@ -1,4 +1,4 @@
-"""Pins of the oracle's electro-chemical forces (Eq. 6, Fig. 3): checks
+"""Pins of the oracle's electro-chemical forces (Eq. 6-7, Fig. 3): checks
 against what the mathematics fixes, not a retyped formula.
 
 - The force derives from a closed-form pair potential U(d): its component
@@ -7,7 +7,7 @@ against what the mathematics fixes, not a retyped formula.
   U_R = F_ER (abar/a0) lambda_D exp(-d/lambda_D) (repulsion) and
   U_A = (A abar / (12 eps)) atan(d/eps) (regularised van der Waals).
 - The repulsion decays by e over one Debye length; at a fixed gap both terms
-  scale with the harmonic radius abar = 2 a_i a_j/(a_i + a_j) as Eq. 6 states.
+  scale with the harmonic radius abar = 2 a_i a_j/(a_i + a_j) as Eq. 6-7 state.
 - Both terms are flat for overlapping pairs and continuous at contact; they
   vanish at and beyond 20 lambda_D and 4 a0 and not just below.
 - A pair at rest beyond the lubrication range feels only the central force:
