@@ -5,7 +5,7 @@
  * Monti, Rathee, Shen & Rosti, "A fast and efficient tool to study the
  * rheology of dense suspensions" (arXiv:2108.01013):
  *   - fixed-radius near-neighbour search by counting sort into cells with the
- *     symmetric half-stencil (Sec. II A, Fig. 5 and 6) and the per-particle
+ *     symmetric half-stencil (Sec. II A, Fig. 4 and 5) and the per-particle
  *     list capacity estimated from the shell around the largest particle
  *     (Sec. II A, last paragraphs);
  *   - pair forces: lubrication (Eq. 3, App. A Eq. A2-A7) and stick-and-slide

@@ -1,5 +1,5 @@
 // Symmetric (half-stencil) fixed-radius near-neighbour enumeration
-// (Sec. II A, Fig. 6): each pair is found exactly once, by its owner, and
+// (Sec. II A, Fig. 5): each pair is found exactly once, by its owner, and
 // written into the owner's fixed-capacity row (capacity M, the shell
 // estimate of Sec. II A), in a fixed visiting order.
 //
