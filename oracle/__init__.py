@@ -14,6 +14,10 @@ Parity status of each function (see the pins in ``tests/test_oracle_*.py``):
                                     placed geometry, Lees-Edwards images)
   contact                           pinned (head-on spring-dashpot closed
                                     form, Coulomb-capped tangential loading)
+  analysis (rheology, clusters,     pinned in tests/test_oracle_analysis.py
+    dispersion, image count)        (Einstein viscosity, compressional
+                                    contact, hand-built and scipy graphs,
+                                    ballistic dispersion, wrap continuity)
   echem / echem_range               pinned (integrates to the closed-form
                                     potentials of Eq. 6-7, Debye decay,
                                     harmonic-radius scaling, flat and
@@ -139,6 +143,8 @@ def lib():
         L.orc_get_state.argtypes = [c_void_p, dp, dp, dp, dp, dp]
         L.orc_get_forces.restype = None
         L.orc_get_forces.argtypes = [c_void_p, dp, dp, dp]
+        L.orc_get_images.restype = None
+        L.orc_get_images.argtypes = [c_void_p, i64p]
         L.orc_forces_sampled.restype = None
         L.orc_forces_sampled.argtypes = [c_void_p, i64p, c_int64, dp, dp]
         for nm in ("orc_get_nstep", "orc_get_npairs", "orc_get_ncontacts"):
@@ -287,6 +293,13 @@ class System:
         s = np.zeros(9)
         lib().orc_get_forces(self._h, _ptr(F), _ptr(T), _ptr(s))
         return F, T, s.reshape(3, 3)
+
+    def get_images(self):
+        """Lees-Edwards image count along y of each particle since set_state
+        (the unwrapped gradient coordinate is y + images * L_y)."""
+        iy = np.zeros(self.n, dtype=np.int64)
+        lib().orc_get_images(self._h, _ptr(iy, c_int64))
+        return iy
 
     def set_history(self, keys, xi):
         keys = np.ascontiguousarray(keys, dtype=np.int64)

@@ -76,6 +76,7 @@ typedef struct orc_sys {
   int64_t nstep;                /* time t = nstep*dt */
   int64_t hk, hcap;             /* contact history: sorted keys lo<<32|hi */
   int64_t *hkey;
+  int64_t *iy;                  /* Lees-Edwards image count along y (unwrapped y = y + iy L_y) */
   double *hxi;                  /* [hk][3], orientation lo -> hi */
   int64_t npairs_last, ncontacts_last;
 } orc_sys;
@@ -543,13 +544,14 @@ orc_sys *orc_create(int64_t n, const orc_params *p) {
   s->hcap = 16;
   s->hkey = (int64_t *)malloc(sizeof(int64_t) * (size_t)s->hcap);
   s->hxi = (double *)malloc(sizeof(double) * 3 * (size_t)s->hcap);
+  s->iy = (int64_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int64_t));
   return s;
 }
 
 void orc_destroy(orc_sys *s) {
   if (!s) return;
   free(s->x); free(s->u); free(s->w); free(s->al); free(s->aw);
-  free(s->F); free(s->T); free(s->a); free(s->id); free(s->hkey); free(s->hxi);
+  free(s->F); free(s->T); free(s->a); free(s->id); free(s->hkey); free(s->hxi); free(s->iy);
   free(s);
 }
 
@@ -574,6 +576,7 @@ void orc_set_state(orc_sys *s, const double *x, const double *a, const int32_t *
   }
   s->nstep = nstep;
   s->hk = 0;
+  memset(s->iy, 0, sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
 }
 
 /* Contact history as (key, xi) arrays; key = lo_id << 32 | hi_id. */
@@ -819,6 +822,7 @@ void orc_step(orc_sys *s, int64_t nsteps) {
       }
       int cr = le_wrap(p, off, X, Y, Z);
       s->u[i] = s->u[i] + cr * p->shear_rate * p->L[1];
+      s->iy[i] -= cr;   /* left through the top: one image up */
     }
     /* Eq. 15c at (x^{n+1}, u^{n+1/2}) */
     orc_forces(s, 1);
@@ -833,6 +837,10 @@ void orc_step(orc_sys *s, int64_t nsteps) {
 }
 
 /* Accessors for the ctypes wrapper. */
+void orc_get_images(const orc_sys *s, int64_t *iy) {
+  memcpy(iy, s->iy, sizeof(int64_t) * (size_t)s->n);
+}
+
 void orc_get_state(const orc_sys *s, double *x, double *u, double *w, double *al, double *aw) {
   size_t b = sizeof(double) * 3 * (size_t)s->n;
   if (x) memcpy(x, s->x, b);
