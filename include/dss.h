@@ -305,6 +305,42 @@ int dss_adjoint(dss_handle *h, int64_t nsteps, int32_t ckpt_every, const double 
  * stream to run on (NULL: legacy default stream); synchronises it. */
 int dss_selftest_bounded_wait(void *cuda_stream);
 
+/* ---- Analysis pass (not part of the time step; each call synchronises) ---- */
+
+/* Rheology of every instance from its bulk stress (Sec. II, after Eq. 9):
+ * out[6k .. 6k+5] = {sigma = S_xy, N1 = S_xx - S_yy, N2 = S_yy - S_zz,
+ * Pi = -tr(S)/3, eta_r = sigma / (eta0 gdot_k), eta_n = Pi / (eta0 gdot_k)},
+ * from the running mean of the committed steps (mean != 0, as dss_batch_stress
+ * returns it) or from the last force evaluation (mean == 0).  out: 6K doubles,
+ * host or device.  DSS_ERR_ARG for a zero shear rate or eta0. */
+int dss_rheology(dss_handle *h, int mean, double *out);
+
+/* Lees-Edwards image count along y of every particle, by id: how many times
+ * it left through y = L_y minus how many times through y = 0 since the state
+ * was set (dss_set_state, dss_load_state and dss_load restart it at 0); the
+ * unwrapped shear-wise coordinate is y + count L_y.  iy: n int32, host or
+ * device. */
+int dss_get_images(dss_handle *h, int32_t *iy);
+
+/* Shear-wise dispersion (Sec. III B, Eq. 18-19).  dss_dispersion_mark records
+ * the current time t0, and the unwrapped y and the shear-wise velocity
+ * fluctuation v' = u_y of every particle.  dss_dispersion then returns, per
+ * instance k, out[3k .. 3k+2] = {D_y = <(y(t) - y(t0))^2> / (2 (t - t0)) /
+ * (a0^2 gdot_k), C_v = <v'(t) v'(t0)> / <v'(t)^2>, t - t0}, the averages over
+ * the instance's particles (D_y = 0 at t = t0).  out: 3K doubles, host or
+ * device.  DSS_ERR_STATE before a mark, or after the state was set again. */
+int dss_dispersion_mark(dss_handle *h);
+int dss_dispersion(dss_handle *h, double *out);
+
+/* Clusters of contacting particles (Sec. III A, Fig. 10-11): the connected
+ * components of the graph whose edges are the pairs in contact (d < 0) at
+ * the last committed step (or the history set by dss_set_history).  label:
+ * n int32 by id (host or device, may be NULL), the smallest id in the
+ * particle's cluster; *nclusters: the number of clusters (a particle without
+ * contact is a cluster of one).  The result is unique (no dependence on
+ * thread order). */
+int dss_contact_clusters(dss_handle *h, int32_t *label, int64_t *nclusters);
+
 /* Bytes of device memory the handle holds. */
 int64_t dss_device_bytes(const dss_handle *h);
 

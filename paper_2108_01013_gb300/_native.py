@@ -19,7 +19,7 @@ _BUILD = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(_BUILD, "libdss.so")
 INCLUDE = os.path.join(os.path.dirname(_HERE), "include")
 SOURCES = ["dss_sort.cu", "dss_neighbour.cu", "dss_force.cu", "dss_api.cu", "dss_noalloc.cu",
-           "dss_adjoint.cu"]
+           "dss_adjoint.cu", "dss_analysis.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v"]
 
@@ -107,6 +107,11 @@ SIGNATURES = {
     "dss_load": (c_int, [c_void_p, _vp, c_size_t]),
     "dss_autotune": (c_int, [c_void_p, c_int32, c_int32, _dp, _dp, _dp]),
     "dss_selftest_bounded_wait": (c_int, [c_void_p]),
+    "dss_rheology": (c_int, [c_void_p, c_int, _vp]),
+    "dss_get_images": (c_int, [c_void_p, _vp]),
+    "dss_dispersion_mark": (c_int, [c_void_p]),
+    "dss_dispersion": (c_int, [c_void_p, _vp]),
+    "dss_contact_clusters": (c_int, [c_void_p, _vp, _lp]),
     "dss_adjoint": (c_int, [c_void_p, c_int64, c_int32, _vp, c_int32, _dp, _dp, _vp, _vp, _vp, _vp, _vp]),
     "dss_set_state": (c_int, [c_void_p, _vp, _vp, _vp, _vp, _vp, _vp, _vp, c_int64]),
     "dss_get_state": (c_int, [c_void_p, _vp, _vp, _vp, _vp, _vp]),

@@ -34,6 +34,7 @@ void free_buffers(dss_handle* h) {
     StateBuf& s = h->st[b];
     dfree(s.x); dfree(s.u); dfree(s.w); dfree(s.al); dfree(s.aw); dfree(s.a); dfree(s.id); dfree(s.inst);
     dfree(s.cls);
+    dfree(s.iy);
     dfree(s.vf); dfree(s.wf); dfree(s.posl); dfree(s.cellc);
     memset(&s, 0, sizeof(s));
     ListBuf& L = h->lb[b];
@@ -43,6 +44,8 @@ void free_buffers(dss_handle* h) {
   }
   dfree(h->posf); dfree(h->cellid); dfree(h->perm); dfree(h->key); dfree(h->offs); dfree(h->pred);
   h->pred = nullptr;
+  dfree(h->xc); dfree(h->mark);
+  h->xc = nullptr; h->mark = nullptr; h->marked = false;
   dfree(h->cell_count); dfree(h->cell_start); dfree(h->tmp); dfree(h->spart);
   dfree(h->own); dfree(h->bw_count); dfree(h->bw_rec);
   h->own = nullptr; h->bw_count = nullptr; h->bw_rec = nullptr;
@@ -114,7 +117,8 @@ int alloc_buffers(dss_handle* h) {
     StateBuf& s = h->st[b];
     if ((r = dalloc(h, &s.x, 3 * n)) || (r = dalloc(h, &s.u, 3 * n)) || (r = dalloc(h, &s.w, 3 * n)) ||
         (r = dalloc(h, &s.al, 3 * n)) || (r = dalloc(h, &s.aw, 3 * n)) || (r = dalloc(h, &s.a, n)) ||
-        (r = dalloc(h, &s.id, n)) || (r = dalloc(h, &s.inst, n)) || (r = dalloc(h, &s.cls, n)))
+        (r = dalloc(h, &s.id, n)) || (r = dalloc(h, &s.inst, n)) || (r = dalloc(h, &s.cls, n)) ||
+        (r = dalloc(h, &s.iy, n)))
       return r;
     if (h->p.precision == DSS_MIXED &&
         ((r = dalloc(h, &s.vf, n)) || (r = dalloc(h, &s.wf, n)) || (r = dalloc(h, &s.posl, n)) ||
@@ -127,7 +131,7 @@ int alloc_buffers(dss_handle* h) {
       return r;
   }
   if ((r = dalloc(h, &h->posf, n)) || (r = dalloc(h, &h->cellid, n)) || (r = dalloc(h, &h->perm, n)) ||
-      (r = dalloc(h, &h->pred, 6 * n)) ||
+      (r = dalloc(h, &h->pred, 6 * n)) || (r = dalloc(h, &h->xc, n)) ||
       (r = dalloc(h, &h->key, n)) || (r = dalloc(h, &h->offs, n)) ||
       (r = dalloc(h, &h->cell_count, (size_t)h->g.ncell)) ||
       (r = dalloc(h, &h->cell_start, (size_t)h->g.ncell + 1)) || (r = dalloc(h, &h->tmp, n)) ||
@@ -238,6 +242,7 @@ __global__ void k_state_in(int n, Src5 src, StateBuf s, const double* __restrict
   s.a[i] = a_by_id[i];
   s.inst[i] = inst_map[i];
   s.cls[i] = cls_map[i];
+  s.iy[i] = 0;
   s.id[i] = i;
 }
 
@@ -792,6 +797,8 @@ int dss_set_state(dss_handle* h, const double* x, const double* a, const int32_t
   CK(cudaMemcpyAsync(s.x, hx.data(), sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->stream));
   CK(cudaMemcpyAsync(s.a, ha.data(), sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
   CK(cudaMemcpyAsync(s.id, hid.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemsetAsync(s.iy, 0, sizeof(int) * n, h->stream));
+  h->marked = false;
   {
     std::vector<double> aid(n);
     for (int64_t i = 0; i < n; ++i) aid[hid[i]] = ha[i];
@@ -811,6 +818,7 @@ int dss_set_state(dss_handle* h, const double* x, const double* a, const int32_t
     CK(cudaMemsetAsync(h->lb[b].count, 0, sizeof(int) * n, h->stream));
     CK(cudaMemsetAsync(h->lb[b].start, 0, sizeof(int) * (n + 1), h->stream));
     k_iota<<<nb, 256, 0, h->stream>>>((int)n, h->lb[b].slot_of_id);
+    k_iota<<<nb, 256, 0, h->stream>>>((int)n, h->lb[b].id_of_slot);
   }
   k_set_nstep<<<1, 1, 0, h->stream>>>(h->status, (long long)nstep);
   CK(cudaGetLastError());
@@ -1048,6 +1056,106 @@ int dss_batch_stress(dss_handle* h, double* sigma, double* sigma_mean, int64_t* 
 }
 
 int32_t dss_batch_size(const dss_handle* h) { return h ? h->K : 0; }
+
+int dss_rheology(dss_handle* h, int mean, double* out) {
+  if (!h || !out) return DSS_ERR_ARG;
+  if (!h->have_state) return DSS_ERR_STATE;
+  const int K = h->K;
+  std::vector<double> S(9 * (size_t)K), r(6 * (size_t)K);
+  int rc = mean ? dss_batch_stress(h, nullptr, S.data(), nullptr, 0) : dss_batch_stress(h, S.data(), nullptr, nullptr, 0);
+  if (rc) return rc;
+  for (int k = 0; k < K; ++k) {
+    const double* s = &S[9 * (size_t)k];
+    const double g = h->p.eta0 * h->inst_gdot[k];
+    if (!(g != 0.0)) return DSS_ERR_ARG;
+    const double pi = -(s[0] + s[4] + s[8]) / 3.0;
+    double* o = &r[6 * (size_t)k];
+    o[0] = s[1];
+    o[1] = s[0] - s[4];
+    o[2] = s[4] - s[8];
+    o[3] = pi;
+    o[4] = s[1] / g;
+    o[5] = pi / g;
+  }
+  CK(cudaMemcpy(out, r.data(), sizeof(double) * r.size(), cudaMemcpyDefault));
+  return DSS_OK;
+}
+
+int dss_get_images(dss_handle* h, int32_t* iy) {
+  if (!h || !iy) return DSS_ERR_ARG;
+  if (!h->have_state) return DSS_ERR_STATE;
+  ENTER(h);
+  launch_images_out(h, h->io_id);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(iy, h->io_id, sizeof(int32_t) * h->n, cudaMemcpyDefault, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return DSS_OK;
+}
+
+int dss_dispersion_mark(dss_handle* h) {
+  if (!h) return DSS_ERR_ARG;
+  if (!h->have_state) return DSS_ERR_STATE;
+  ENTER(h);
+  if (!h->mark) {
+    int r = dalloc(h, &h->mark, 2 * (size_t)h->n);
+    if (r) return r;
+  }
+  launch_mark(h);
+  CK(cudaGetLastError());
+  int r = sync_status(h);
+  if (r) return r;
+  h->mark_nstep = (int64_t)(uint32_t)h->status_host->w[ST_NSTEP_LO] |
+                  ((int64_t)h->status_host->w[ST_NSTEP_HI] << 32);
+  h->marked = true;
+  return DSS_OK;
+}
+
+int dss_dispersion(dss_handle* h, double* out) {
+  if (!h || !out) return DSS_ERR_ARG;
+  if (!h->have_state || !h->marked || !h->mark) return DSS_ERR_STATE;
+  ENTER(h);
+  const int K = h->K;
+  launch_dispersion(h, h->io3);
+  CK(cudaGetLastError());
+  std::vector<double> sums(3 * (size_t)K), r(3 * (size_t)K);
+  CK(cudaMemcpyAsync(sums.data(), h->io3, sizeof(double) * sums.size(), cudaMemcpyDeviceToHost, h->stream));
+  int rc = sync_status(h);
+  if (rc) return rc;
+  const int64_t ns = (int64_t)(uint32_t)h->status_host->w[ST_NSTEP_LO] |
+                     ((int64_t)h->status_host->w[ST_NSTEP_HI] << 32);
+  const double t = (double)(ns - h->mark_nstep) * h->p.dt;
+  for (int k = 0; k < K; ++k) {
+    const double nk = (double)h->inst_n[k];
+    const double g = h->inst_gdot[k] * h->p.a0 * h->p.a0;
+    r[3 * k] = t > 0.0 && g != 0.0 ? sums[3 * k] / nk / (2.0 * t) / g : 0.0;
+    r[3 * k + 1] = sums[3 * k + 2] != 0.0 ? sums[3 * k + 1] / sums[3 * k + 2] : 0.0;
+    r[3 * k + 2] = t;
+  }
+  CK(cudaMemcpy(out, r.data(), sizeof(double) * r.size(), cudaMemcpyDefault));
+  return DSS_OK;
+}
+
+int dss_contact_clusters(dss_handle* h, int32_t* label, int64_t* nclusters) {
+  if (!h || !nclusters) return DSS_ERR_ARG;
+  if (!h->have_state) return DSS_ERR_STATE;
+  ENTER(h);
+  // scratch, free between steps: the sort's key, offset and slot arrays hold
+  // the parents, the smallest ids and the labels; the id staging array the
+  // count
+  int* count = h->io_id;
+  launch_clusters(h, h->key, h->offs, count, h->tmp);
+  CK(cudaGetLastError());
+  int c = 0;
+  CK(cudaMemcpyAsync(&c, count, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  int r = sync_status(h);
+  if (r) return r;
+  if ((r = status_error(h))) { clear_err(h); return r; }
+  if (label) {
+    CK(cudaMemcpy(label, h->tmp, sizeof(int32_t) * h->n, cudaMemcpyDefault));
+  }
+  *nclusters = c;
+  return DSS_OK;
+}
 
 int dss_get_counters(dss_handle* h, dss_counters* c) {
   if (!h || !c) return DSS_ERR_ARG;

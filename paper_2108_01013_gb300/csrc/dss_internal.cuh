@@ -321,6 +321,7 @@ struct StateBuf {
   int* id;      // n persistent id
   int* inst;    // n instance index
   unsigned char* cls;  // n size class (stencil reach), see Geo::rtab
+  int* iy;      // n Lees-Edwards image count along y since the state was set (unwrapped y = y + iy L_y)
   float4* vf;   // n, mixed precision: FP32 velocity relative to U_inf (xyz)
   float4* wf;   // n, mixed precision: FP32 angular velocity relative to Omega_inf (xyz)
   float4* posl; // n, mixed precision: low words of the cell-local position and radius
@@ -417,6 +418,11 @@ struct dss_handle {
   int* cellid;       // n
   int* perm;         // n: new sorted index -> previous index
   double* pred;      // 6n: predicted position and velocity of a step, source order
+  signed char* xc;   // n: the step's y crossing of each particle (source order): -1 out through
+                     // the top, +1 through the bottom
+  double* mark;      // 2n (analysis): unwrapped y and v_y of each id at the marked time
+  int64_t mark_nstep;
+  bool marked;
   // counting sort scratch
   int* key;          // n
   int* offs;         // n
@@ -471,6 +477,10 @@ enum GatherMode { G_STEP = 0, G_EVAL = 1, G_ACCEL = 2 };
 void launch_forces(dss_handle* h, int stbuf, int work_list, int hist_list, int adv, int mode,
                    double* F_out, double* T_out);
 void launch_pairs_out(dss_handle* h, int list, long long* out);
+void launch_images_out(dss_handle* h, int* out);
+void launch_mark(dss_handle* h);
+void launch_dispersion(dss_handle* h, double* sums);
+void launch_clusters(dss_handle* h, int* parent, int* minid, int* count, int* label);
 int pair_grid_blocks(const dss_handle* h);
 void launch_scan(dss_handle* h, const int* in, int* out, int count, int which, bool zero_in);
 int scan_tiles_for(int count);

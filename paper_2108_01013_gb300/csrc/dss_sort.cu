@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(kThreads)
 k_key_hist(Geo g, const InstGeo* __restrict__ ig, StepGeo* __restrict__ sg, StateBuf s,
            int* __restrict__ key, int* __restrict__ offs, int* __restrict__ cell_count,
            DevStatus* st, bool predict, unsigned long long* scan_status, int* scan_ticket,
-           int scan_tiles, double* __restrict__ pred) {
+           int scan_tiles, double* __restrict__ pred, signed char* __restrict__ xc) {
   if (dev_err(st)) return;
   // reset the look-back state of both scans of this operation (spread over
   // the grid), the counters, and set every instance's Lees-Edwards geometry
@@ -136,6 +136,7 @@ k_key_hist(Geo g, const InstGeo* __restrict__ ig, StepGeo* __restrict__ sg, Stat
     pred[3 * n + i] = p.ux;
     pred[4 * n + i] = p.uy;
     pred[5 * n + i] = p.uz;
+    xc[i] = (signed char)p.cross;
   }
   int k = cell_key(I, s.cls[i], p.x, p.y, p.z);
   unsigned act = __activemask();
@@ -168,7 +169,7 @@ k_rank_gather(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__
               StateBuf dst, const int* __restrict__ key, const int* __restrict__ cell_start,
               const int* __restrict__ tmp, int* __restrict__ perm, int* __restrict__ cellid,
               float4* __restrict__ posf, DevStatus* st, bool predict,
-              const double* __restrict__ pred) {
+              const double* __restrict__ pred, const signed char* __restrict__ xc) {
   if (dev_err(st)) return;
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = g.n;
@@ -210,6 +211,8 @@ k_rank_gather(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__
   dst.id[f] = id;
   dst.inst[f] = inst;
   dst.cls[f] = src.cls[o];
+  // image count: leaving through the top is one image up
+  dst.iy[f] = src.iy[o] - (predict ? (int)xc[o] : 0);
   if (g.precision == DSS_MIXED) {
     // FP32 copies relative to the ambient flow for the FP32 pair arithmetic:
     // u - U_inf(x) and w - Omega_inf are O(gdot a), free of O(gdot L) terms
@@ -348,7 +351,7 @@ void launch_sort(dss_handle* h, bool predict, int src, int dst) {
   prof_mark(h, 0);
   k_key_hist<<<blocks, kThreads, 0, h->stream>>>(h->g, h->ig, h->sg, h->st[src], h->key, h->offs,
                                                  h->cell_count, h->status, predict, h->scan_status,
-                                                 h->scan_ticket, h->scan_tiles_max, h->pred);
+                                                 h->scan_ticket, h->scan_tiles_max, h->pred, h->xc);
   prof_mark(h, 1);
   launch_scan(h, h->cell_count, h->cell_start, h->g.ncell, 0, true);
   prof_mark(h, 2);
@@ -356,5 +359,5 @@ void launch_sort(dss_handle* h, bool predict, int src, int dst) {
   prof_mark(h, 3);
   k_rank_gather<<<blocks, kThreads, 0, h->stream>>>(h->g, h->ig, h->sg, h->st[src], h->st[dst], h->key,
                                                     h->cell_start, h->tmp, h->perm, h->cellid,
-                                                    h->posf, h->status, predict, h->pred);
+                                                    h->posf, h->status, predict, h->pred, h->xc);
 }

@@ -175,6 +175,40 @@ class Suspension:
                                            k, byref(cnt)), "dss_get_history")
         return keys[:k], xi[:k]
 
+    # ---- analysis pass (dss_rheology, dss_get_images, dss_dispersion*,
+    # dss_contact_clusters); per instance rows for a batch
+    def _instances(self) -> int:
+        return int(self.lib.dss_batch_size(self._h))
+
+    def rheology(self, mean: bool = True) -> np.ndarray:
+        """(K, 6): sigma, N1, N2, Pi, eta_r, eta_n per instance."""
+        out = np.zeros((self._instances(), 6))
+        nat.check(self.lib.dss_rheology(self._h, 1 if mean else 0, c_void_p(out.ctypes.data)), "dss_rheology")
+        return out
+
+    def images(self) -> np.ndarray:
+        """Lees-Edwards image count along y of each id since the state was set."""
+        iy = np.zeros(self.n, dtype=np.int32)
+        nat.check(self.lib.dss_get_images(self._h, c_void_p(iy.ctypes.data)), "dss_get_images")
+        return iy
+
+    def dispersion_mark(self):
+        nat.check(self.lib.dss_dispersion_mark(self._h), "dss_dispersion_mark")
+
+    def dispersion(self) -> np.ndarray:
+        """(K, 3): D_y, C_v, t - t0 per instance (Eq. 18-19)."""
+        out = np.zeros((self._instances(), 3))
+        nat.check(self.lib.dss_dispersion(self._h, c_void_p(out.ctypes.data)), "dss_dispersion")
+        return out
+
+    def contact_clusters(self):
+        """(label by id: smallest id of its cluster, number of clusters)."""
+        label = np.zeros(self.n, dtype=np.int32)
+        cnt = c_int64(0)
+        nat.check(self.lib.dss_contact_clusters(self._h, c_void_p(label.ctypes.data), byref(cnt)),
+                  "dss_contact_clusters")
+        return label, int(cnt.value)
+
     def set_history(self, keys, xi):
         keys = np.ascontiguousarray(keys, dtype=np.int64)
         xi = np.ascontiguousarray(xi, dtype=np.float64).reshape(-1, 3)
