@@ -8,7 +8,8 @@ following oracle.c step for step: the brute-force pair set (taken from the C
 oracle; it is discrete and carries no derivative), the stick-and-slide
 contact of Eq. 4-5, the lubrication blocks of Eq. A2/A3 with the g functions
 of Eq. A7 (6 pi eta0 prefactor) and the optional taper of the cutoff, the
-Stokes drag of Eq. A1, the modified velocity-Verlet step of Eq. 15 in the
+optional electro-chemical forces of Eq. 6-7 (central, with their stresslet),
+the Stokes drag of Eq. A1, the modified velocity-Verlet step of Eq. 15 in the
 Lees-Edwards box of Eq. 16, and the bulk stress of Eq. 8.  The objective is a
 weighted sum of the stress over the steps,
 
@@ -101,13 +102,16 @@ class Model:
     differentiated inputs)."""
 
     def __init__(self, box, a, *, eta0=1.0, rho=1.0, lub_eps=1e-3, a0=1.0, lub_cutoff_mode=0,
-                 shear_rate=1.0, dt=1e-4, lub_taper=0.0, nstep0=0):
+                 shear_rate=1.0, dt=1e-4, lub_taper=0.0, nstep0=0, f_er=0.0, lambda_d=0.05,
+                 hamaker=0.0, vdw_eps=0.01):
         self.box = np.asarray(box, dtype=np.float64)
         self.a = np.asarray(a, dtype=np.float64)
         self.n = self.a.shape[0]
         self.eta0, self.rho, self.eps, self.a0 = eta0, rho, lub_eps, a0
         self.mode, self.gdot, self.dt, self.taper = lub_cutoff_mode, shear_rate, dt, lub_taper
         self.nstep0 = nstep0
+        # electro-chemical forces, Eq. 6-7 (constants, not differentiated)
+        self.f_er, self.lambda_d, self.hamaker, self.vdw_eps = f_er, lambda_d, hamaker, vdw_eps
         at = torch.as_tensor(self.a, dtype=TD)
         self.at = at
         self.mass = 4.0 / 3.0 * math.pi * rho * at ** 3
@@ -130,7 +134,8 @@ class Model:
         p = make_params(L, kn=th["kn"].item(), kt=th["kt"].item(), gamma_n=th["gn"].item(),
                         mu=th["mu"].item(), eta0=self.eta0, rho=self.rho,
                         delta_lub=th["delta"].item(), lub_eps=self.eps, a0=self.a0,
-                        lub_cutoff_mode=self.mode, shear_rate=gd, dt=self.dt, lub_taper=self.taper)
+                        lub_cutoff_mode=self.mode, shear_rate=gd, dt=self.dt, lub_taper=self.taper,
+                        f_er=self.f_er, lambda_d=self.lambda_d, hamaker=self.hamaker, vdw_eps=self.vdw_eps)
         xn = x.detach().numpy()
         pr = pairs_bruteforce(xn, self.a, np.arange(n, dtype=np.int32), p, off)
         i = torch.as_tensor(pr[:, 0])
@@ -240,6 +245,28 @@ class Model:
             s = torch.where(tv >= 1.0, torch.ones_like(t),
                             torch.where(tv <= 0.0, torch.zeros_like(t), t * t * (3.0 - 2.0 * t)))
             Fli, Flj, Tli, Tlj = (s[:, None] * v for v in (Fli, Flj, Tli, Tlj))
+        # lubrication only within its own cutoff (the listing test with the
+        # lubrication range; the list may reach further for Eq. 6-7)
+        dlub = th["delta"].item() * self.a0 if self.mode == 1 else th["delta"].item() * S.numpy() * 0.5
+        r2v = ((dx * dx).detach().numpy() + (dy * dy).detach().numpy()) + (dz * dz).detach().numpy()
+        lub_on = r2v < (S.numpy() + dlub) ** 2
+        lm = torch.as_tensor(lub_on.astype(np.float64), dtype=TD)[:, None]
+        Fli, Flj, Tli, Tlj = (lm * v for v in (Fli, Flj, Tli, Tlj))
+        # electro-chemical forces, Eq. 6-7: central, stresslet r (x) F like contact
+        if self.f_er > 0.0 or self.hamaker > 0.0:
+            abar = 2.0 * ai * aj / S
+            dv = d.detach()
+            mE = torch.zeros_like(d)
+            if self.f_er > 0.0:
+                rep_ = torch.where(dv >= 0.0, torch.exp(-d / self.lambda_d), torch.ones_like(d))
+                mE = mE - torch.where(dv < 20.0 * self.lambda_d, self.f_er * (abar / self.a0) * rep_,
+                                      torch.zeros_like(d))
+            if self.hamaker > 0.0:
+                eps = self.vdw_eps * abar
+                dp = torch.where(dv >= 0.0, d, torch.zeros_like(d))
+                mE = mE + torch.where(dv < 4.0 * self.a0, self.hamaker * abar / (12.0 * (dp * dp + eps * eps)),
+                                      torch.zeros_like(d))
+            Fc = Fc + mE[:, None] * nv
         Fi = Fc + Fli
         Fj = -Fc + Flj
         Ti = Tci + Tli
@@ -269,7 +296,8 @@ class Model:
             band = (d.detach().numpy() > (1.0 - self.taper) * dlv)
         sl = slip.numpy()
         ev = (P, int(cm_np.sum()), int(sl.sum()), hash(keys[cm_np].tobytes()),
-              hash(keys[sl].tobytes()), hash(keys[band].tobytes()), hash(keys.tobytes()))
+              hash(keys[sl].tobytes()), hash(keys[band].tobytes()), hash(keys.tobytes()),
+              hash(keys[lub_on].tobytes()))
         return F.T, Tq.T, sigma, new_hist, ev
 
     # -- the rollout -----------------------------------------------------------

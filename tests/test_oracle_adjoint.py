@@ -2,7 +2,9 @@
 repeat oracle.c step for step, and its reverse-mode gradient must match
 central finite differences of oracle.c, with the event set (pair set,
 contacts, Coulomb slips) checked unchanged between the two sides of each
-difference."""
+difference.  One case adds the electro-chemical forces of Eq. 6-7 (the
+list then reaches their range and lubrication keeps its own).
+"""
 import numpy as np
 import pytest
 
@@ -13,7 +15,10 @@ from oracle import adjoint
 from paper_2108_01013_gb300 import synth
 
 
-def _case(taper):
+ECHEM = dict(f_er=30.0, lambda_d=0.05, hamaker=0.01, vdw_eps=0.05)
+
+
+def _case(taper, echem=False):
     g = synth.small(260, 0.52, 61)
     n = g["a"].shape[0]
     rng = np.random.default_rng(5)
@@ -22,6 +27,8 @@ def _case(taper):
     u0 += 0.5 * rng.normal(size=(3, n))
     w0 = 0.5 * rng.normal(size=(3, n))
     kw = dict(shear_rate=5.0, dt=1e-4, lub_taper=taper, nstep0=3)
+    if echem:
+        kw.update(ECHEM)
     th = dict(kn=1e4, kt=6e3, gamma_n=0.5, mu=0.4, delta_lub=0.2 if taper else 0.05)
     return g, u0, w0, kw, th
 
@@ -29,7 +36,7 @@ def _case(taper):
 def _c_oracle(g, u0, w0, kw, th, nsteps, weights, x0=None):
     p = oracle.make_params(g["box"], kn=th["kn"], kt=th["kt"], gamma_n=th["gamma_n"], mu=th["mu"],
                            delta_lub=th["delta_lub"], shear_rate=kw["shear_rate"], dt=kw["dt"],
-                           lub_taper=kw["lub_taper"])
+                           lub_taper=kw["lub_taper"], **{k: kw[k] for k in ECHEM if k in kw})
     o = oracle.System(p, g["x"] if x0 is None else x0, g["a"], u=u0, w=w0, nstep=kw["nstep0"])
     o.init_accel()
     J, sig, ev = 0.0, [], []
@@ -50,9 +57,9 @@ def _weights(nsteps, gd):
     return W
 
 
-@pytest.mark.parametrize("taper", [0.0, 0.3])
-def test_torch_rollout_repeats_c_oracle(taper):
-    g, u0, w0, kw, th = _case(taper)
+@pytest.mark.parametrize("taper,echem", [(0.0, False), (0.3, False), (0.3, True)])
+def test_torch_rollout_repeats_c_oracle(taper, echem):
+    g, u0, w0, kw, th = _case(taper, echem)
     T = 15
     W = _weights(T, kw["shear_rate"])
     r = adjoint.gradients(g["box"], g["x"], g["a"], u0, w0, T, W, **th, **kw)
@@ -97,9 +104,9 @@ def _fd(g, u0, w0, kw, th, T, W, key, h, x0=None, du=None, dw=None):
     return (Jp - Jm) / (2 * h)
 
 
-@pytest.mark.parametrize("taper", [0.0, 0.3])
-def test_gradient_matches_central_differences(taper):
-    g, u0, w0, kw, th = _case(taper)
+@pytest.mark.parametrize("taper,echem", [(0.0, False), (0.3, False), (0.3, True)])
+def test_gradient_matches_central_differences(taper, echem):
+    g, u0, w0, kw, th = _case(taper, echem)
     T = 12
     W = _weights(T, kw["shear_rate"])
     r = adjoint.gradients(g["box"], g["x"], g["a"], u0, w0, T, W, **th, **kw)
@@ -108,8 +115,15 @@ def test_gradient_matches_central_differences(taper):
         if name == "delta_lub" and taper == 0.0:
             assert r["params"][k] == 0.0        # hard cutoff: no pathwise dependence
             continue
-        h = 1e-4 * th[name]
-        fd = _fd(g, u0, w0, kw, th, T, W, name, h)
+        # the largest relative step that leaves the event set unchanged
+        for rel in (1e-4, 3e-5, 1e-5, 3e-6):
+            try:
+                fd = _fd(g, u0, w0, kw, th, T, W, name, rel * th[name])
+                break
+            except AssertionError:
+                continue
+        else:
+            pytest.fail("no step keeps the event set: " + name)
         assert r["params"][k] == pytest.approx(fd, rel=2e-5, abs=1e-9 * abs(r["J"])), name
     rng = np.random.default_rng(9)
     for _ in range(2):
