@@ -277,7 +277,9 @@ __device__ __forceinline__ PairModelOut<T> pair_model(const Geo& g, const InstGe
   }
   // ---- lubrication, App. A
   T ds = 2.0 * d / S;
-  if (!(val(ds) > 0.0)) ds = zero;
+  // the clamp's branch: overlapping pairs only (a pair exactly touching keeps
+  // the gap's derivative, the branch its values share with d > 0)
+  if (!(val(ds) >= 0.0)) ds = zero;
   const T dd = ds + g.eps;
   const T X = 1.0 / dd;
   const T Y = -log(dd);
