@@ -56,10 +56,10 @@ L2_FLUSH_BYTES = 256 << 20
 # and mixed precision (FP32 records).  The derivation is in the design notes.
 ALG_BYTES = {
     #                  fp64 (n, c, p, k)      mixed (n, c, p, k)
-    "k_key_hist":    ((84, 0, 0, 0),        (84, 0, 0, 0)),
+    "k_key_hist":    ((133, 0, 0, 0),       (133, 0, 0, 0)),
     "k_scan_cells":  ((0, 12, 0, 0),        (0, 12, 0, 0)),
     "k_scatter":     ((16, 0, 0, 0),        (16, 0, 0, 0)),
-    "k_rank_gather": ((260, 0, 0, 0),       (292, 0, 0, 0)),
+    "k_rank_gather": ((269, 0, 0, 0),       (301, 0, 0, 0)),
     "k_enumerate":   ((52, 8, 4, 0),        (52, 8, 4, 0)),
     "k_pairs":       ((148, 0, 108, 56),    (112, 0, 76, 56)),
     "k_gather":      ((216, 0, 64, 0),      (216, 0, 32, 0)),
@@ -104,10 +104,10 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--modes", default="fp64,echem,batched,poly1m,adjoint",
+    ap.add_argument("--modes", default="fp64,echem,analysis,batched,poly1m,adjoint",
                     help="extra modes measured in the same run: fp64 (the headline workload in "
                          "FP64), echem (the headline packing with the electro-chemical forces, "
-                         "mixed), batched (256-instance flow-curve sweep, mixed), poly1m (1M "
+                         "mixed), analysis (clusters, dispersion, rheology calls on it), batched (256-instance flow-curve sweep, mixed), poly1m (1M "
                          "polydisperse, mixed and FP64), adjoint (gradient of the 200-step "
                          "viscosity of 20k spheres); 'none' for none")
     ap.add_argument("--mode-steps", type=int, default=400)
@@ -276,6 +276,40 @@ def mode_echem(dss, g, spec, kw, args, flush, stream):
                      "steps": steps, "params": e, "pairs": c["npairs"], "contacts": c["ncontacts"], "M": c["M"],
                      "cells": list(c["ncell"]), "kernels_ms": profile_pass(s, 10, flush)}
         s.close()
+    return out
+
+
+def mode_analysis(dss, g, spec, kw, args, stream):
+    """The analysis pass on the headline workload (mixed): after 50 steps the
+    dispersion is marked, after 50 more every analysis call is timed (host
+    clock around calls that synchronise, mean of 10)."""
+    import time as _t
+    import numpy as _np
+    n = g["a"].shape[0]
+    p = dss.default_params(g["box"], precision="mixed", **kw)
+    s = dss.Suspension(g["x"], g["a"], g["box"], p, ids=g["ids"], stream=stream)
+    s.step(50)
+    s.dispersion_mark()
+    s.step(50)
+
+    def timed(f):
+        f()
+        t0 = _t.perf_counter()
+        for _ in range(10):
+            r = f()
+        return (_t.perf_counter() - t0) / 10 * 1e3, r
+
+    t_cl, (label, ncl) = timed(s.contact_clusters)
+    t_di, disp = timed(s.dispersion)
+    t_rh, rh = timed(lambda: s.rheology(mean=True))
+    sizes = _np.unique(label, return_counts=True)[1]
+    out = {"config": {"workload": spec.name, "n": n, "precision": "mixed", "steps_before": 100},
+           "contact_clusters": {"ms": t_cl, "clusters": ncl, "largest": int(sizes.max()),
+                                "contacts": s.counters()["ncontacts"]},
+           "dispersion": {"ms": t_di, "D_y": float(disp[0, 0]), "C_v": float(disp[0, 1]),
+                          "t_minus_t0": float(disp[0, 2])},
+           "rheology": {"ms": t_rh, "sigma_N1_N2_Pi_eta_r_eta_n": [float(v) for v in rh[0]]}}
+    s.close()
     return out
 
 
@@ -515,6 +549,9 @@ def main():
         if "echem" in modes:
             with torch.cuda.nvtx.range("echem"):
                 extra["echem"] = mode_echem(dss, g, spec, kw, args, flush, stream)
+        if "analysis" in modes:
+            with torch.cuda.nvtx.range("analysis"):
+                extra["analysis"] = mode_analysis(dss, g, spec, kw, args, stream)
         del flush
         if batch is not None:
             with torch.cuda.nvtx.range("batched"):
