@@ -31,6 +31,18 @@ Parity status of each function (see the pins in ``tests/test_oracle_*.py``):
                                     The absolute values of the log-order
                                     coefficients for unequal radii beyond
                                     these invariants are parity unpinned.
+  flow_ux / flow_rate / faxen_ux,    pinned in tests/test_oracle_wavy.py (Faxen
+    the wavy flow of Eq. 17         drag = surface mean of the flow up to
+                                    (ka)^4, relaxation to it and to the local
+                                    spin, pairs equal simple-shear pairs at
+                                    the mean rate, local stresslets, wrap
+                                    continuity, no wave = simple shear)
+  rolling (App. B)                  pinned in tests/test_oracle_rolling.py
+                                    (oscillation of the relative spin of a
+                                    row of spheres at the closed-form
+                                    frequency with its angular momentum
+                                    conserved, Coulomb limit, no force, no
+                                    stresslet, orientation independence)
   System.step / forces / stress     pinned (Stokes relaxation closed form,
                                     Lees-Edwards wrap invariants, momentum
                                     balance, stress sign checks)
@@ -71,14 +83,18 @@ class Params(ctypes.Structure):
                 ("lub_cutoff_mode", c_int32), ("pad_", c_int32),
                 ("shear_rate", c_double), ("dt", c_double), ("L", c_double * 3),
                 ("lub_taper", c_double), ("f_er", c_double), ("lambda_d", c_double),
-                ("hamaker", c_double), ("vdw_eps", c_double)]
+                ("hamaker", c_double), ("vdw_eps", c_double),
+                ("wave_amp", c_double), ("k_r", c_double), ("wave_n", c_int32),
+                ("pad2_", c_int32)]
 
 
 def make_params(box, kn=1e4, kt=None, gamma_n=None, mu=0.5, eta0=1.0, rho=1.0,
                 delta_lub=0.05, lub_eps=1e-3, a0=1.0, lub_cutoff_mode=0,
                 shear_rate=1.0, dt=1e-4, lub_taper=0.0, f_er=0.0, lambda_d=0.05,
-                hamaker=0.0, vdw_eps=0.01) -> Params:
-    """Oracle parameters; kt defaults to kn/2 and gamma_n to 1e-7 kn/gdot."""
+                hamaker=0.0, vdw_eps=0.01, wave_amp=0.0, wave_n=0, k_r=0.0) -> Params:
+    """Oracle parameters; kt defaults to kn/2 and gamma_n to 1e-7 kn/gdot.
+    wave_amp, wave_n: the wavy shear flow of Eq. 17; k_r: the rolling spring
+    of App. B (0: off)."""
     if kt is None:
         kt = 0.5 * kn
     if gamma_n is None:
@@ -90,6 +106,7 @@ def make_params(box, kn=1e4, kt=None, gamma_n=None, mu=0.5, eta0=1.0, rho=1.0,
     p.shear_rate, p.dt = shear_rate, dt
     p.lub_taper = lub_taper
     p.f_er, p.lambda_d, p.hamaker, p.vdw_eps = f_er, lambda_d, hamaker, vdw_eps
+    p.wave_amp, p.wave_n, p.k_r = wave_amp, int(wave_n), k_r
     for k in range(3):
         p.L[k] = float(box[k])
     return p
@@ -117,6 +134,22 @@ def lib():
         L.orc_contact.argtypes = [pp, dp, c_double, c_double] + [dp] * 5 + [dp] * 4
         L.orc_lubrication.restype = None
         L.orc_lubrication.argtypes = [pp, dp, c_double, c_double] + [dp] * 4 + [dp] * 4
+        L.orc_lubrication_rate.restype = None
+        L.orc_lubrication_rate.argtypes = [pp, c_double, dp, c_double, c_double] + [dp] * 8
+        L.orc_rolling.restype = None
+        L.orc_rolling.argtypes = [pp, dp, c_double, c_double] + [dp] * 5 + [dp] * 3
+        for nm in ("orc_flow_ux", "orc_flow_rate"):
+            getattr(L, nm).restype = c_double
+            getattr(L, nm).argtypes = [pp, c_double]
+        L.orc_faxen_ux.restype = c_double
+        L.orc_faxen_ux.argtypes = [pp, c_double, c_double]
+        L.orc_pair_eval_full.restype = c_int
+        L.orc_pair_eval_full.argtypes = ([pp, c_double] + [dp] * 6 + [c_double, c_double, dp, dp]
+                                         + [dp] * 7)
+        L.orc_set_history_r.restype = None
+        L.orc_set_history_r.argtypes = [c_void_p, c_int64, i64p, dp, dp]
+        L.orc_get_history_r.restype = c_int64
+        L.orc_get_history_r.argtypes = [c_void_p, c_int64, i64p, dp, dp]
         L.orc_echem.restype = None
         L.orc_echem.argtypes = [pp, c_double, c_double, c_double, dp, dp]
         L.orc_echem_range.restype = c_double
@@ -206,13 +239,42 @@ def contact(p: Params, r, ai, aj, ui, uj, wi, wj, xi_old):
     return tuple(outs)
 
 
-def lubrication(p: Params, r, ai, aj, Vi, Vj, Wi, Wj):
-    """App. A lubrication: returns (F_i, F_j, T_i, T_j)."""
+def lubrication(p: Params, r, ai, aj, Vi, Vj, Wi, Wj, rate=None):
+    """App. A lubrication: returns (F_i, F_j, T_i, T_j); the strain is that of
+    a shear of rate ``rate`` along x (default: gdot)."""
     args = [_d(v) for v in (Vi, Vj, Wi, Wj)]
     outs = [np.zeros(3) for _ in range(4)]
-    lib().orc_lubrication(ctypes.byref(p), _ptr(_d(r)), float(ai), float(aj),
-                          *[_ptr(v) for v in args], *[_ptr(o) for o in outs])
+    if rate is None:
+        lib().orc_lubrication(ctypes.byref(p), _ptr(_d(r)), float(ai), float(aj),
+                              *[_ptr(v) for v in args], *[_ptr(o) for o in outs])
+    else:
+        lib().orc_lubrication_rate(ctypes.byref(p), float(rate), _ptr(_d(r)), float(ai),
+                                   float(aj), *[_ptr(v) for v in args], *[_ptr(o) for o in outs])
     return tuple(outs)
+
+
+def rolling(p: Params, r, ai, aj, ui, uj, wi, wj, xr_old=(0, 0, 0)):
+    """App. B rolling resistance of a contact: returns (T_i, T_j, xr_new)."""
+    args = [_d(v) for v in (r, ui, uj, wi, wj, xr_old)]
+    outs = [np.zeros(3) for _ in range(3)]
+    lib().orc_rolling(ctypes.byref(p), _ptr(args[0]), float(ai), float(aj),
+                      *[_ptr(v) for v in args[1:]], *[_ptr(o) for o in outs])
+    return tuple(outs)
+
+
+def flow_ux(p: Params, y):
+    """U_inf,x at height y (Eq. 17)."""
+    return lib().orc_flow_ux(ctypes.byref(p), float(y))
+
+
+def flow_rate(p: Params, y):
+    """Local shear rate dU_inf,x/dy at height y."""
+    return lib().orc_flow_rate(ctypes.byref(p), float(y))
+
+
+def faxen_ux(p: Params, y, a):
+    """(1 + a^2/6 Laplacian) U_inf,x at height y (the Faxen velocity of Eq. A1)."""
+    return lib().orc_faxen_ux(ctypes.byref(p), float(y), float(a))
 
 
 def echem(p: Params, d, ai, aj, n):
@@ -227,16 +289,24 @@ def echem_range(p: Params) -> float:
     return lib().orc_echem_range(ctypes.byref(p))
 
 
-def pair_eval(p: Params, off, xi, xj, ui, uj, wi, wj, ai, aj, xi_old=(0, 0, 0)):
-    """Whole pair from absolute state: (flags, F_i, F_j, T_i, T_j, S(3x3), xi_new)."""
+def pair_eval(p: Params, off, xi, xj, ui, uj, wi, wj, ai, aj, xi_old=(0, 0, 0),
+              xr_old=None):
+    """Whole pair from absolute state: (flags, F_i, F_j, T_i, T_j, S(3x3), xi_new),
+    plus xr_new (the rolling stretch) at the end when xr_old is given."""
     ins = [_d(v) for v in (xi, xj, ui, uj, wi, wj)]
     xo = _d(xi_old)
-    Fi, Fj, Ti, Tj, xn = (np.zeros(3) for _ in range(5))
+    Fi, Fj, Ti, Tj, xn, rn = (np.zeros(3) for _ in range(6))
     S = np.zeros(9)
-    fl = lib().orc_pair_eval(ctypes.byref(p), float(off), *[_ptr(v) for v in ins],
-                             float(ai), float(aj), _ptr(xo), _ptr(Fi), _ptr(Fj),
-                             _ptr(Ti), _ptr(Tj), _ptr(S), _ptr(xn))
-    return fl, Fi, Fj, Ti, Tj, S.reshape(3, 3), xn
+    if xr_old is None:
+        fl = lib().orc_pair_eval(ctypes.byref(p), float(off), *[_ptr(v) for v in ins],
+                                 float(ai), float(aj), _ptr(xo), _ptr(Fi), _ptr(Fj),
+                                 _ptr(Ti), _ptr(Tj), _ptr(S), _ptr(xn))
+        return fl, Fi, Fj, Ti, Tj, S.reshape(3, 3), xn
+    ro = _d(xr_old)
+    fl = lib().orc_pair_eval_full(ctypes.byref(p), float(off), *[_ptr(v) for v in ins],
+                                  float(ai), float(aj), _ptr(xo), _ptr(ro), _ptr(Fi), _ptr(Fj),
+                                  _ptr(Ti), _ptr(Tj), _ptr(S), _ptr(xn), _ptr(rn))
+    return fl, Fi, Fj, Ti, Tj, S.reshape(3, 3), xn, rn
 
 
 class System:
@@ -301,16 +371,23 @@ class System:
         lib().orc_get_images(self._h, _ptr(iy, c_int64))
         return iy
 
-    def set_history(self, keys, xi):
+    def set_history(self, keys, xi, xr=None):
+        """Contact history: sorted keys lo_id << 32 | hi_id, sliding stretch
+        (lo -> hi) and, optionally, the rolling stretch of each contact."""
         keys = np.ascontiguousarray(keys, dtype=np.int64)
         xi = _d(xi).reshape(-1, 3)
-        lib().orc_set_history(self._h, keys.shape[0], _ptr(keys, c_int64), _ptr(xi))
+        xr = None if xr is None else _d(xr).reshape(-1, 3)
+        lib().orc_set_history_r(self._h, keys.shape[0], _ptr(keys, c_int64), _ptr(xi), _opt(xr))
 
-    def get_history(self):
+    def get_history(self, rolling: bool = False):
+        """(keys, xi), or (keys, xi, xr) with the rolling stretch."""
         k = lib().orc_get_history(self._h, 0, None, None)
         keys = np.zeros(max(k, 1), dtype=np.int64)
         xi = np.zeros((max(k, 1), 3))
-        lib().orc_get_history(self._h, k, _ptr(keys, c_int64), _ptr(xi))
+        xr = np.zeros((max(k, 1), 3))
+        lib().orc_get_history_r(self._h, k, _ptr(keys, c_int64), _ptr(xi), _ptr(xr))
+        if rolling:
+            return keys[:k], xi[:k], xr[:k]
         return keys[:k], xi[:k]
 
     @property

@@ -11,7 +11,9 @@
  *
  * Conventions (Sec. II): flow along x, gradient along y, vorticity along z;
  * U_inf = (gdot*y, 0, 0), E_inf_xy = E_inf_yx = gdot/2, Omega_inf =
- * (0, 0, -gdot/2).  Arrays are SoA: v[0*n+i], v[1*n+i], v[2*n+i].
+ * (0, 0, -gdot/2); in the wavy shear flow of Eq. 17 U_inf,x gains
+ * U sin(2 pi n y / L_y) and E_inf, Omega_inf follow the local rate
+ * dU_inf,x/dy.  Arrays are SoA: v[0*n+i], v[1*n+i], v[2*n+i].
  * Neighbour pairs come from an O(N^2) brute-force scan (the plain definition
  * of the fixed-radius near-neighbour set); nothing is blocked or reordered.
  *
@@ -36,6 +38,17 @@
  *  - u^{n+1} = u^{n+1/2} + dt/2 alpha^{n+1}, algebraically Eq. 15d, so that a
  *    Lees-Edwards velocity jump applied to u^{n+1/2} carries over;
  *  - each pair's stresslet is counted once in Eq. 8;
+ *  - wavy flow (Eq. 17): n a whole number (the wave is L_y-periodic); the
+ *    Stokes drag takes the Faxen velocity (1 + a^2/6 Laplacian) U_inf and
+ *    the local Omega_inf at the centre (Eq. A1: no Laplacian on rotation);
+ *    lubrication takes V and W at each centre and the strain of the mean of
+ *    the two centres' local rates; the single-particle stresslet takes
+ *    E_inf at the centre (no Laplacian), the fluid term 2 eta0 E_inf the box
+ *    mean gdot; default velocities are U_inf and Omega_inf at the centre;
+ *  - rolling resistance (App. B): u_r = abar (n x w_i - n x w_j), the
+ *    Coulomb limit mu |F_nor| / k_r with the sliding contact's mu and normal
+ *    force, torques only (no force, no stresslet), the stretch lives with
+ *    the contact like the sliding one;
  *  - optional lubrication taper (an extension for differentiation, not in
  *    the paper): with w = lub_taper > 0 the lubrication force, torques and
  *    stresslet of a listed pair are scaled by s = t^2 (3 - 2t),
@@ -63,6 +76,10 @@ typedef struct orc_params {
   double lub_taper;             /* w of the lubrication taper; 0: hard cutoff */
   double f_er, lambda_d;        /* Eq. 6 (repulsion): magnitude F_ER, Debye length */
   double hamaker, vdw_eps;      /* Eq. 7 (attraction): Hamaker constant A, eps / abar */
+  double wave_amp;              /* Eq. 17: amplitude U of the wavy part of U_inf; 0: simple shear */
+  double k_r;                   /* App. B: rolling spring stiffness; 0: no rolling resistance */
+  int32_t wave_n;               /* Eq. 17: number n of periods of the wave along L_y */
+  int32_t pad2_;
 } orc_params;
 
 typedef struct orc_sys {
@@ -78,6 +95,7 @@ typedef struct orc_sys {
   int64_t *hkey;
   int64_t *iy;                  /* Lees-Edwards image count along y (unwrapped y = y + iy L_y) */
   double *hxi;                  /* [hk][3], orientation lo -> hi */
+  double *hxr;                  /* [hk][3], rolling stretch (the same in both orientations) */
   int64_t npairs_last, ncontacts_last;
 } orc_sys;
 
@@ -240,12 +258,43 @@ static void nproj(const double n[3], const double v[3], double o[3]) {
   o[0] = n[0] * s; o[1] = n[1] * s; o[2] = n[2] * s;
 }
 
-/* Ambient simple shear of Sec. II: E_inf (3x3, row major) and Omega_inf. */
-static void ambient(const orc_params *p, double E[9], double Om[3]) {
+/* A shear along x with local rate g = dU_x/dy: E_inf (3x3, row major) with
+ * E_xy = E_yx = g/2 and Omega_inf = curl(U_inf)/2 = (0, 0, -g/2). */
+static void ambient_rate(double g, double E[9], double Om[3]) {
   memset(E, 0, 9 * sizeof(double));
-  E[0 * 3 + 1] = 0.5 * p->shear_rate;
-  E[1 * 3 + 0] = 0.5 * p->shear_rate;
-  Om[0] = 0.0; Om[1] = 0.0; Om[2] = -0.5 * p->shear_rate;
+  E[0 * 3 + 1] = 0.5 * g;
+  E[1 * 3 + 0] = 0.5 * g;
+  Om[0] = 0.0; Om[1] = 0.0; Om[2] = -0.5 * g;
+}
+
+/* Ambient simple shear of Sec. II (the box mean of the flow of Eq. 17). */
+static void ambient(const orc_params *p, double E[9], double Om[3]) {
+  ambient_rate(p->shear_rate, E, Om);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Wavy shear flow, Eq. 17: U_inf = (gdot y + U sin(k y), 0, 0) with         */
+/* k = 2 pi n / L_y (n = 0 or U = 0: the simple shear).  The wave is         */
+/* L_y-periodic, so the Lees-Edwards velocity jump stays gdot L_y.           */
+/* ------------------------------------------------------------------------ */
+static double wave_k(const orc_params *p) { return 2.0 * M_PI * (double)p->wave_n / p->L[1]; }
+
+/* U_inf,x at height y. */
+double orc_flow_ux(const orc_params *p, double y) {
+  return p->shear_rate * y + p->wave_amp * sin(wave_k(p) * y);
+}
+
+/* Local shear rate dU_inf,x/dy at height y (E_xy = rate/2, Omega_z = -rate/2). */
+double orc_flow_rate(const orc_params *p, double y) {
+  double k = wave_k(p);
+  return p->shear_rate + p->wave_amp * k * cos(k * y);
+}
+
+/* The Faxen velocity of Eq. A1: (1 + a^2/6 Laplacian) U_inf,x at height y
+ * for a sphere of radius a; the Laplacian of sin(k y) is -k^2 sin(k y). */
+double orc_faxen_ux(const orc_params *p, double y, double a) {
+  double k = wave_k(p);
+  return p->shear_rate * y + p->wave_amp * (1.0 - a * a * k * k / 6.0) * sin(k * y);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -295,6 +344,52 @@ void orc_contact(const orc_params *p, const double r[3], double ai, double aj,
     Ti[c] = ai * nxf[c];
     Tj[c] = (aj / ai) * Ti[c];
     xi_new[c] = xs[c];
+  }
+}
+
+/* Rolling resistance, App. B (Eq. B1), after Luding: a rolling spring of
+ * stiffness k_r whose stretch integrates the rolling velocity
+ * u_r = abar (n x w_i - n x w_j), abar = 2 a_i a_j / (a_i + a_j), by the
+ * procedure of Eq. 5 with u_r and k_r in place of u_t and k_t: the old
+ * stretch projected on the current tangent plane plus u_r dt, rescaled so
+ * that |k_r xi_r| <= mu |F_nor| (the Coulomb coefficient and the normal
+ * force, dashpot included, of the sliding contact).  The pseudo-force
+ * k_r xi_r acts through torques only: T_i = abar n x (k_r xi_r), T_j = -T_i.
+ * u_r, and with it xi_r, is unchanged when i and j swap (n and w_i - w_j
+ * both change sign). */
+void orc_rolling(const orc_params *p, const double r[3], double ai, double aj,
+                 const double ui[3], const double uj[3], const double wi[3],
+                 const double wj[3], const double xr_old[3], double Ti[3], double Tj[3],
+                 double xr_new[3]) {
+  double dist = sqrt(dot3(r, r));
+  double n[3] = {r[0] / dist, r[1] / dist, r[2] / dist};
+  double d = dist - (ai + aj);
+  double abar = 2.0 * ai * aj / (ai + aj);
+  double du[3] = {uj[0] - ui[0], uj[1] - ui[1], uj[2] - ui[2]};
+  double un[3];
+  nproj(n, du, un);
+  double Fnor[3];
+  for (int c = 0; c < 3; ++c) Fnor[c] = p->kn * d * n[c] + p->gamma_n * un[c];
+  double dw[3] = {wi[0] - wj[0], wi[1] - wj[1], wi[2] - wj[2]};
+  double nxdw[3];
+  cross3(n, dw, nxdw);
+  double xp[3];
+  tproj(n, xr_old, xp);
+  double xs[3];
+  for (int c = 0; c < 3; ++c) xs[c] = xp[c] + abar * nxdw[c] * p->dt;
+  double cap = p->mu * sqrt(dot3(Fnor, Fnor)) / p->k_r;
+  double xm = sqrt(dot3(xs, xs));
+  if (xm > cap) {
+    double f = cap / xm;
+    xs[0] *= f; xs[1] *= f; xs[2] *= f;
+  }
+  double Fr[3] = {p->k_r * xs[0], p->k_r * xs[1], p->k_r * xs[2]};
+  double nxf[3];
+  cross3(n, Fr, nxf);
+  for (int c = 0; c < 3; ++c) {
+    Ti[c] = abar * nxf[c];
+    Tj[c] = -Ti[c];
+    xr_new[c] = xs[c];
   }
 }
 
@@ -368,19 +463,20 @@ static void lub_coefficients(const orc_params *p, double d, double ai, double aj
 
 /* Lubrication forces and torques on i and j (Eq. 3 without the Stokes part):
  *   (F_i,F_j,T_i,T_j) = -6 pi eta0 R_Lub.(V_i,V_j,W_i,W_j) + 6 pi eta0 R'_Lub.(n,n,n_perp,n_perp)
- * with V = u - U_inf(x), W = omega - Omega_inf (particle-by-particle) and
- * r = x_j - x_i.  Each block of Eq. A2/A3 is applied as written. */
-void orc_lubrication(const orc_params *p, const double r[3], double ai, double aj,
-                     const double Vi[3], const double Vj[3], const double Wi[3],
-                     const double Wj[3], double Fi[3], double Fj[3], double Ti[3],
-                     double Tj[3]) {
+ * with V = u - U_inf(x), W = omega - Omega_inf (particle-by-particle),
+ * r = x_j - x_i and the strain E_inf of a shear of local rate `rate` along x.
+ * Each block of Eq. A2/A3 is applied as written. */
+void orc_lubrication_rate(const orc_params *p, double rate, const double r[3], double ai,
+                          double aj, const double Vi[3], const double Vj[3],
+                          const double Wi[3], const double Wj[3], double Fi[3], double Fj[3],
+                          double Ti[3], double Tj[3]) {
   double dist = sqrt(dot3(r, r));
   double n[3] = {r[0] / dist, r[1] / dist, r[2] / dist};
   double d = dist - (ai + aj);
   lub_coef c;
   lub_coefficients(p, d, ai, aj, &c);
   double E[9], Om[3];
-  ambient(p, E, Om);
+  ambient_rate(rate, E, Om);
   (void)Om;
   /* projections of each velocity */
   double NVi[3], TVi[3], NVj[3], TVj[3], TWi[3], TWj[3], nxVi[3], nxVj[3], nxWi[3], nxWj[3];
@@ -429,6 +525,14 @@ void orc_lubrication(const orc_params *p, const double r[3], double ai, double a
   }
 }
 
+/* The same in the simple shear of rate gdot. */
+void orc_lubrication(const orc_params *p, const double r[3], double ai, double aj,
+                     const double Vi[3], const double Vj[3], const double Wi[3],
+                     const double Wj[3], double Fi[3], double Fj[3], double Ti[3],
+                     double Tj[3]) {
+  orc_lubrication_rate(p, p->shear_rate, r, ai, aj, Vi, Vj, Wi, Wj, Fi, Fj, Ti, Tj);
+}
+
 /* Lubrication taper factor of a listed pair at gap d (1 for w = 0). */
 static double lub_taper_factor(const orc_params *p, double d, double ai, double aj) {
   if (!(p->lub_taper > 0.0)) return 1.0;
@@ -467,40 +571,53 @@ void orc_echem(const orc_params *p, double d, double ai, double aj, const double
 
 /* Evaluates pair (i, j) from absolute state.  Returns bit 0 set when the
  * pair is listed (within the interaction range), bit 1 when in contact.
- * xi_old/xi_new are in the i -> j orientation.  S is the pair stresslet
- * S^C + S^L of Eq. 9 (row major).  Outputs are zero for unlisted pairs. */
-int orc_pair_eval(const orc_params *p, double off, const double xi[3], const double xj[3],
-                  const double ui[3], const double uj[3], const double wi[3],
-                  const double wj[3], double ai, double aj, const double xi_old[3],
-                  double Fi[3], double Fj[3], double Ti[3], double Tj[3], double S[9],
-                  double xi_new[3]) {
+ * xi_old/xi_new (sliding stretch) are in the i -> j orientation; xr_old and
+ * xr_new (rolling stretch, App. B) do not depend on it and may be NULL when
+ * k_r = 0.  S is the pair stresslet S^C + S^L + S^E of Eq. 9 (row major).
+ * Outputs are zero for unlisted pairs.
+ * In the wavy flow of Eq. 17, V = u - U_inf and W = w - Omega_inf are taken
+ * at each centre and the strain acting on the pair is that of the mean of
+ * the two centres' local shear rates. */
+int orc_pair_eval_full(const orc_params *p, double off, const double xi[3], const double xj[3],
+                       const double ui[3], const double uj[3], const double wi[3],
+                       const double wj[3], double ai, double aj, const double xi_old[3],
+                       const double xr_old[3], double Fi[3], double Fj[3], double Ti[3],
+                       double Tj[3], double S[9], double xi_new[3], double xr_new[3]) {
   double r[3];
   int sy;
   memset(Fi, 0, 3 * sizeof(double)); memset(Fj, 0, 3 * sizeof(double));
   memset(Ti, 0, 3 * sizeof(double)); memset(Tj, 0, 3 * sizeof(double));
   memset(S, 0, 9 * sizeof(double)); memset(xi_new, 0, 3 * sizeof(double));
+  if (xr_new) memset(xr_new, 0, 3 * sizeof(double));
   min_image(p, off, xi, xj, r, &sy);
   if (!is_pair(p, r, ai, aj)) return 0;
   int flags = 1;
-  double E[9], Om[3];
-  ambient(p, E, Om);
   /* image of j: shifted by sy boxes along y, moving with sy*gdot*L_y along x */
   double ujm[3] = {uj[0] + sy * p->shear_rate * p->L[1], uj[1], uj[2]};
   double yjm = xj[1] + sy * p->L[1];
   double dist = sqrt(dot3(r, r));
   double d = dist - (ai + aj);
   double Fc[3] = {0, 0, 0}, Tci[3] = {0, 0, 0}, Tcj[3] = {0, 0, 0};
+  double Tri[3] = {0, 0, 0}, Trj[3] = {0, 0, 0};
   if (d < 0.0) {
     flags |= 2;
     orc_contact(p, r, ai, aj, ui, ujm, wi, wj, xi_old, Fc, Tci, Tcj, xi_new);
+    if (p->k_r > 0.0) {
+      double zero[3] = {0, 0, 0}, xr_tmp[3];
+      orc_rolling(p, r, ai, aj, ui, ujm, wi, wj, xr_old ? xr_old : zero, Tri, Trj,
+                  xr_new ? xr_new : xr_tmp);
+    }
   }
-  double Vi[3] = {ui[0] - p->shear_rate * xi[1], ui[1], ui[2]};
-  double Vj[3] = {ujm[0] - p->shear_rate * yjm, ujm[1], ujm[2]};
-  double Wi[3] = {wi[0] - Om[0], wi[1] - Om[1], wi[2] - Om[2]};
-  double Wj[3] = {wj[0] - Om[0], wj[1] - Om[1], wj[2] - Om[2]};
+  /* velocities relative to the ambient flow at each centre */
+  double rate_i = orc_flow_rate(p, xi[1]), rate_j = orc_flow_rate(p, yjm);
+  double Vi[3] = {ui[0] - orc_flow_ux(p, xi[1]), ui[1], ui[2]};
+  double Vj[3] = {ujm[0] - orc_flow_ux(p, yjm), ujm[1], ujm[2]};
+  double Wi[3] = {wi[0], wi[1], wi[2] + 0.5 * rate_i};
+  double Wj[3] = {wj[0], wj[1], wj[2] + 0.5 * rate_j};
   double Fli[3] = {0, 0, 0}, Flj[3] = {0, 0, 0}, Tli[3] = {0, 0, 0}, Tlj[3] = {0, 0, 0};
   if (in_lub_range(p, r, ai, aj)) {
-    orc_lubrication(p, r, ai, aj, Vi, Vj, Wi, Wj, Fli, Flj, Tli, Tlj);
+    orc_lubrication_rate(p, 0.5 * (rate_i + rate_j), r, ai, aj, Vi, Vj, Wi, Wj, Fli, Flj, Tli,
+                         Tlj);
     double tap = lub_taper_factor(p, d, ai, aj);
     for (int q = 0; q < 3; ++q) {
       Fli[q] *= tap; Flj[q] *= tap; Tli[q] *= tap; Tlj[q] *= tap;
@@ -515,15 +632,25 @@ int orc_pair_eval(const orc_params *p, double off, const double xi[3], const dou
   for (int q = 0; q < 3; ++q) {
     Fi[q] = Fc[q] + Fli[q] + Fe[q];
     Fj[q] = -Fc[q] + Flj[q] - Fe[q];
-    Ti[q] = Tci[q] + Tli[q];
-    Tj[q] = Tcj[q] + Tlj[q];
+    Ti[q] = Tci[q] + Tli[q] + Tri[q];
+    Tj[q] = Tcj[q] + Tlj[q] + Trj[q];
   }
   /* Eq. 9: S^C = r (x) F^C_ij, S^L = sym(r (x) F^L_ij), S^E = r (x) F^E_ij,
-   * r = x_j - x_i */
+   * r = x_j - x_i (the rolling pseudo-force exerts no force: no stresslet) */
   for (int a = 0; a < 3; ++a)
     for (int b = 0; b < 3; ++b)
       S[3 * a + b] = r[a] * Fc[b] + 0.5 * (r[a] * Fli[b] + r[b] * Fli[a]) + r[a] * Fe[b];
   return flags;
+}
+
+/* The pair without rolling history (a new rolling spring when k_r > 0). */
+int orc_pair_eval(const orc_params *p, double off, const double xi[3], const double xj[3],
+                  const double ui[3], const double uj[3], const double wi[3],
+                  const double wj[3], double ai, double aj, const double xi_old[3],
+                  double Fi[3], double Fj[3], double Ti[3], double Tj[3], double S[9],
+                  double xi_new[3]) {
+  return orc_pair_eval_full(p, off, xi, xj, ui, uj, wi, wj, ai, aj, xi_old, NULL, Fi, Fj, Ti,
+                            Tj, S, xi_new, NULL);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -544,6 +671,7 @@ orc_sys *orc_create(int64_t n, const orc_params *p) {
   s->hcap = 16;
   s->hkey = (int64_t *)malloc(sizeof(int64_t) * (size_t)s->hcap);
   s->hxi = (double *)malloc(sizeof(double) * 3 * (size_t)s->hcap);
+  s->hxr = (double *)calloc(3 * (size_t)s->hcap, sizeof(double));
   s->iy = (int64_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int64_t));
   return s;
 }
@@ -551,25 +679,23 @@ orc_sys *orc_create(int64_t n, const orc_params *p) {
 void orc_destroy(orc_sys *s) {
   if (!s) return;
   free(s->x); free(s->u); free(s->w); free(s->al); free(s->aw);
-  free(s->F); free(s->T); free(s->a); free(s->id); free(s->hkey); free(s->hxi); free(s->iy);
+  free(s->F); free(s->T); free(s->a); free(s->id); free(s->hkey); free(s->hxi); free(s->hxr); free(s->iy);
   free(s);
 }
 
 /* Copies state in.  Any of u, w, al, aw may be NULL: u defaults to
- * U_inf(x), w to Omega_inf, al/aw to zero. */
+ * U_inf(x), w to Omega_inf(x), al/aw to zero. */
 void orc_set_state(orc_sys *s, const double *x, const double *a, const int32_t *id,
                    const double *u, const double *w, const double *al,
                    const double *aw, int64_t nstep) {
   int64_t n = s->n;
-  double E[9], Om[3];
-  ambient(&s->p, E, Om);
   memcpy(s->x, x, sizeof(double) * 3 * (size_t)n);
   memcpy(s->a, a, sizeof(double) * (size_t)n);
   memcpy(s->id, id, sizeof(int32_t) * (size_t)n);
   for (int64_t i = 0; i < n; ++i) {
     for (int c = 0; c < 3; ++c) {
-      s->u[c * n + i] = u ? u[c * n + i] : (c == 0 ? s->p.shear_rate * x[n + i] : 0.0);
-      s->w[c * n + i] = w ? w[c * n + i] : Om[c];
+      s->u[c * n + i] = u ? u[c * n + i] : (c == 0 ? orc_flow_ux(&s->p, x[n + i]) : 0.0);
+      s->w[c * n + i] = w ? w[c * n + i] : (c == 2 ? -0.5 * orc_flow_rate(&s->p, x[n + i]) : 0.0);
       s->al[c * n + i] = al ? al[c * n + i] : 0.0;
       s->aw[c * n + i] = aw ? aw[c * n + i] : 0.0;
     }
@@ -579,25 +705,44 @@ void orc_set_state(orc_sys *s, const double *x, const double *a, const int32_t *
   memset(s->iy, 0, sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
 }
 
-/* Contact history as (key, xi) arrays; key = lo_id << 32 | hi_id. */
-void orc_set_history(orc_sys *s, int64_t k, const int64_t *key, const double *xi) {
+static void hist_reserve(orc_sys *s, int64_t k) {
   if (k > s->hcap) {
     s->hcap = k;
     s->hkey = (int64_t *)realloc(s->hkey, sizeof(int64_t) * (size_t)k);
     s->hxi = (double *)realloc(s->hxi, sizeof(double) * 3 * (size_t)k);
+    s->hxr = (double *)realloc(s->hxr, sizeof(double) * 3 * (size_t)k);
   }
+}
+
+/* Contact history as (key, xi, xr) arrays sorted by key = lo_id << 32 |
+ * hi_id: the sliding stretch (lo -> hi orientation) and the rolling stretch
+ * of each contact; xr may be NULL (zero rolling stretch). */
+void orc_set_history_r(orc_sys *s, int64_t k, const int64_t *key, const double *xi,
+                       const double *xr) {
+  hist_reserve(s, k);
   memcpy(s->hkey, key, sizeof(int64_t) * (size_t)k);
   memcpy(s->hxi, xi, sizeof(double) * 3 * (size_t)k);
+  if (xr) memcpy(s->hxr, xr, sizeof(double) * 3 * (size_t)k);
+  else memset(s->hxr, 0, sizeof(double) * 3 * (size_t)k);
   s->hk = k;
 }
 
-int64_t orc_get_history(const orc_sys *s, int64_t cap, int64_t *key, double *xi) {
+void orc_set_history(orc_sys *s, int64_t k, const int64_t *key, const double *xi) {
+  orc_set_history_r(s, k, key, xi, NULL);
+}
+
+int64_t orc_get_history_r(const orc_sys *s, int64_t cap, int64_t *key, double *xi, double *xr) {
   int64_t m = s->hk < cap ? s->hk : cap;
   if (m > 0) {
     memcpy(key, s->hkey, sizeof(int64_t) * (size_t)m);
     memcpy(xi, s->hxi, sizeof(double) * 3 * (size_t)m);
+    if (xr) memcpy(xr, s->hxr, sizeof(double) * 3 * (size_t)m);
   }
   return s->hk;
+}
+
+int64_t orc_get_history(const orc_sys *s, int64_t cap, int64_t *key, double *xi) {
+  return orc_get_history_r(s, cap, key, xi, NULL);
 }
 
 static int64_t hist_find(const orc_sys *s, int64_t key) {
@@ -610,16 +755,32 @@ static int64_t hist_find(const orc_sys *s, int64_t key) {
   return -1;
 }
 
-typedef struct hrec { int64_t key; double xi[3]; } hrec;
+typedef struct hrec { int64_t key; double xi[3], xr[3]; } hrec;
 static int cmp_hrec(const void *A, const void *B) {
   const hrec *a = (const hrec *)A, *b = (const hrec *)B;
   return a->key < b->key ? -1 : (a->key > b->key ? 1 : 0);
 }
 
+/* Stokes drag of Eq. A1 on particle k with the Faxen term:
+ * F = -6 pi eta0 a (u - (1 + a^2/6 Laplacian) U_inf), T = -8 pi eta0 a^3
+ * (w - Omega_inf), both at the centre (the Laplacian vanishes in the simple
+ * shear). */
+static void stokes_drag(const orc_sys *s, int64_t k, double f[3], double t[3]) {
+  const orc_params *p = &s->p;
+  int64_t n = s->n;
+  double a = s->a[k], y = s->x[n + k];
+  double V[3] = {s->u[k] - orc_faxen_ux(p, y, a), s->u[n + k], s->u[2 * n + k]};
+  double W[3] = {s->w[k], s->w[n + k], s->w[2 * n + k] + 0.5 * orc_flow_rate(p, y)};
+  for (int c = 0; c < 3; ++c) {
+    f[c] = -6.0 * M_PI * p->eta0 * a * V[c];
+    t[c] = -8.0 * M_PI * p->eta0 * a * a * a * W[c];
+  }
+}
+
 /* Force evaluation at the current state (x, u, w) and time nstep*dt:
- * all pair interactions (brute force), Stokes drag (Eq. A1, no Faxen term
- * in simple shear), per-particle totals F and T, the bulk stress of Eq. 8,
- * and, when commit != 0, the new contact history. */
+ * all pair interactions (brute force), Stokes drag (Eq. A1), per-particle
+ * totals F and T, the bulk stress of Eq. 8, and, when commit != 0, the new
+ * contact history. */
 void orc_forces(orc_sys *s, int commit) {
   const orc_params *p = &s->p;
   int64_t n = s->n;
@@ -648,12 +809,16 @@ void orc_forces(orc_sys *s, int commit) {
       int64_t hi = s->id[i] < s->id[j] ? s->id[j] : s->id[i];
       int64_t key = (lo << 32) | hi;
       double sgn = s->id[i] < s->id[j] ? 1.0 : -1.0;   /* i->j vs lo->hi */
-      double xo[3] = {0, 0, 0};
+      double xo[3] = {0, 0, 0}, ro[3] = {0, 0, 0};
       int64_t h = hist_find(s, key);
-      if (h >= 0) for (int c = 0; c < 3; ++c) xo[c] = sgn * s->hxi[3 * h + c];
-      double Fi[3], Fj[3], Ti[3], Tj[3], S[9], xn[3];
-      int fl = orc_pair_eval(p, off, xi, xj, ui, uj, wi, wj, s->a[i], s->a[j], xo,
-                             Fi, Fj, Ti, Tj, S, xn);
+      if (h >= 0)
+        for (int c = 0; c < 3; ++c) {
+          xo[c] = sgn * s->hxi[3 * h + c];
+          ro[c] = s->hxr[3 * h + c];
+        }
+      double Fi[3], Fj[3], Ti[3], Tj[3], S[9], xn[3], rn[3];
+      int fl = orc_pair_eval_full(p, off, xi, xj, ui, uj, wi, wj, s->a[i], s->a[j], xo, ro,
+                                  Fi, Fj, Ti, Tj, S, xn, rn);
       ++npairs;
       for (int c = 0; c < 3; ++c) {
         s->F[c * n + i] += Fi[c]; s->F[c * n + j] += Fj[c];
@@ -664,39 +829,43 @@ void orc_forces(orc_sys *s, int commit) {
         ++ncont;
         if (hn == hc) { hc *= 2; hnew = (hrec *)realloc(hnew, sizeof(hrec) * (size_t)hc); }
         hnew[hn].key = key;
-        for (int c = 0; c < 3; ++c) hnew[hn].xi[c] = sgn * xn[c];
+        for (int c = 0; c < 3; ++c) {
+          hnew[hn].xi[c] = sgn * xn[c];
+          hnew[hn].xr[c] = rn[c];
+        }
         ++hn;
       }
     }
   }
-  /* Stokes drag, Eq. A1: F = -6 pi eta0 a (u - U_inf), T = -8 pi eta0 a^3 (w - Omega_inf) */
-  double sumA3 = 0.0;
+  /* Stokes drag, Eq. A1, and the single-particle stresslets
+   * S^S_i = 20/3 pi eta0 a_i^3 E_inf(x_i) (E_inf at the centre, no Laplacian) */
+  double Sein[9] = {0};
   for (int64_t i = 0; i < n; ++i) {
-    double a = s->a[i];
-    double V[3] = {s->u[i] - p->shear_rate * s->x[n + i], s->u[n + i], s->u[2 * n + i]};
+    double f[3], t[3];
+    stokes_drag(s, i, f, t);
     for (int c = 0; c < 3; ++c) {
-      s->F[c * n + i] += -6.0 * M_PI * p->eta0 * a * V[c];
-      s->T[c * n + i] += -8.0 * M_PI * p->eta0 * a * a * a * (s->w[c * n + i] - Om[c]);
+      s->F[c * n + i] += f[c];
+      s->T[c * n + i] += t[c];
     }
-    sumA3 += a * a * a;
+    double a = s->a[i], Ei[9], Oi[3];
+    ambient_rate(orc_flow_rate(p, s->x[n + i]), Ei, Oi);
+    for (int q = 0; q < 9; ++q) Sein[q] += 20.0 / 3.0 * M_PI * p->eta0 * a * a * a * Ei[q];
   }
-  /* Eq. 8 with S^S_i = 20/3 pi eta0 a_i^3 E_inf (uniform E, no Laplacian) */
+  /* Eq. 8; the fluid's own term with the box mean of E_inf (the wave of
+   * Eq. 17 averages to zero over L_y) */
   double V = p->L[0] * p->L[1] * p->L[2];
-  for (int q = 0; q < 9; ++q)
-    s->sigma[q] = 2.0 * p->eta0 * E[q] +
-                  (20.0 / 3.0 * M_PI * p->eta0 * sumA3 * E[q] + Spair[q]) / V;
+  for (int q = 0; q < 9; ++q) s->sigma[q] = 2.0 * p->eta0 * E[q] + (Sein[q] + Spair[q]) / V;
   s->npairs_last = npairs;
   s->ncontacts_last = ncont;
   if (commit) {
     qsort(hnew, (size_t)hn, sizeof(hrec), cmp_hrec);
-    if (hn > s->hcap) {
-      s->hcap = hn;
-      s->hkey = (int64_t *)realloc(s->hkey, sizeof(int64_t) * (size_t)hn);
-      s->hxi = (double *)realloc(s->hxi, sizeof(double) * 3 * (size_t)hn);
-    }
+    hist_reserve(s, hn);
     for (int64_t h = 0; h < hn; ++h) {
       s->hkey[h] = hnew[h].key;
-      for (int c = 0; c < 3; ++c) s->hxi[3 * h + c] = hnew[h].xi[c];
+      for (int c = 0; c < 3; ++c) {
+        s->hxi[3 * h + c] = hnew[h].xi[c];
+        s->hxr[3 * h + c] = hnew[h].xr[c];
+      }
     }
     s->hk = hn;
   }
@@ -711,8 +880,6 @@ void orc_forces_sampled(orc_sys *s, const int64_t *idx, int64_t m, double *F, do
   const orc_params *p = &s->p;
   int64_t n = s->n;
   double off = orc_le_offset(p, s->nstep);
-  double E[9], Om[3];
-  ambient(p, E, Om);
   for (int64_t q = 0; q < m; ++q) {
     int64_t k = idx[q];
     double f[3] = {0, 0, 0}, t[3] = {0, 0, 0};
@@ -732,21 +899,26 @@ void orc_forces_sampled(orc_sys *s, const int64_t *idx, int64_t m, double *F, do
       int64_t lo = s->id[i] < s->id[j] ? s->id[i] : s->id[j];
       int64_t hi = s->id[i] < s->id[j] ? s->id[j] : s->id[i];
       double sgn = s->id[i] < s->id[j] ? 1.0 : -1.0;
-      double xo[3] = {0, 0, 0};
+      double xo[3] = {0, 0, 0}, ro[3] = {0, 0, 0};
       int64_t h = hist_find(s, (lo << 32) | hi);
-      if (h >= 0) for (int c = 0; c < 3; ++c) xo[c] = sgn * s->hxi[3 * h + c];
-      double Fi[3], Fj[3], Ti[3], Tj[3], S[9], xn[3];
-      orc_pair_eval(p, off, xi, xj, ui, uj, wi, wj, s->a[i], s->a[j], xo, Fi, Fj, Ti, Tj, S, xn);
+      if (h >= 0)
+        for (int c = 0; c < 3; ++c) {
+          xo[c] = sgn * s->hxi[3 * h + c];
+          ro[c] = s->hxr[3 * h + c];
+        }
+      double Fi[3], Fj[3], Ti[3], Tj[3], S[9], xn[3], rn[3];
+      orc_pair_eval_full(p, off, xi, xj, ui, uj, wi, wj, s->a[i], s->a[j], xo, ro, Fi, Fj, Ti,
+                         Tj, S, xn, rn);
       for (int c = 0; c < 3; ++c) {
         f[c] += (k == i) ? Fi[c] : Fj[c];
         t[c] += (k == i) ? Ti[c] : Tj[c];
       }
     }
-    double a = s->a[k];
-    double V[3] = {s->u[k] - p->shear_rate * s->x[n + k], s->u[n + k], s->u[2 * n + k]};
+    double fd[3], td[3];
+    stokes_drag(s, k, fd, td);
     for (int c = 0; c < 3; ++c) {
-      f[c] += -6.0 * M_PI * p->eta0 * a * V[c];
-      t[c] += -8.0 * M_PI * p->eta0 * a * a * a * (s->w[c * n + k] - Om[c]);
+      f[c] += fd[c];
+      t[c] += td[c];
       F[c * m + q] = f[c];
       T[c * m + q] = t[c];
     }
