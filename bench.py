@@ -22,10 +22,14 @@ in [1e-2, 1e2], mixed precision) advanced together in one handle after the
 cell edge is autotuned (working set ~1.5 GB, beyond the L2); "poly1m",
 1,000,000 spheres with radii log-uniform in [1, 10] in mixed precision and
 FP64; "adjoint", the gradient of the 200-step time-averaged viscosity of
-20,000 spheres (checkpoint every 20 steps) against the forward alone.
+20,000 spheres (checkpoint every 20 steps) against the forward alone;
+"echem", the headline packing with the electro-chemical forces of Eq. 6-7;
+"analysis", the analysis pass; "wavy", the Table 5 suspension (2^16 spheres,
+radius ratio 3) in the uniform and the wavy shear flow of Eq. 17, with and
+without rolling resistance.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
-                       [--modes fp64,batched,poly1m,adjoint|none]
+                       [--modes fp64,echem,analysis,wavy,batched,poly1m,adjoint|none]
 Under torchrun each rank runs an independent replica (replicas only: the
 single-instance path has no data-parallel exchange); value = total particle
 steps of all ranks / max over ranks of the timed GPU time.
@@ -104,7 +108,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--modes", default="fp64,echem,analysis,batched,poly1m,adjoint",
+    ap.add_argument("--modes", default="fp64,echem,analysis,wavy,batched,poly1m,adjoint",
                     help="extra modes measured in the same run: fp64 (the headline workload in "
                          "FP64), echem (the headline packing with the electro-chemical forces, "
                          "mixed), analysis (clusters, dispersion, rheology calls on it), batched (256-instance flow-curve sweep, mixed), poly1m (1M "
@@ -275,6 +279,36 @@ def mode_echem(dss, g, spec, kw, args, flush, stream):
         out[name] = {"value": n * steps / (t * 1e-3), "unit": "particle-steps/s", "ms_per_step": t / steps,
                      "steps": steps, "params": e, "pairs": c["npairs"], "contacts": c["ncontacts"], "M": c["M"],
                      "cells": list(c["ncell"]), "kernels_ms": profile_pass(s, 10, flush)}
+        s.close()
+    return out
+
+
+def mode_wavy(dss, g, spec, args, flush, stream):
+    """Table 5: 2^16 spheres of radius ratio 3 (V2/V1 = 0.25, phi = 0.5) with
+    the electro-chemical forces, in the uniform shear (NW) and in the wavy
+    shear flow of Eq. 17 (YW, U = 20 gdot a0, n = 1, Faxen drag), and YW with
+    the rolling resistance of App. B (k_r = 0.05 k_n)."""
+    n = g["a"].shape[0]
+    base = dict(mu=spec.mu, kn=spec.kn, shear_rate=spec.shear_rate, dt=spec.dt, **spec.extra)
+    cases = {
+        "NW_mixed": (dict(base, wave_amp=0.0, wave_n=0), "mixed"),
+        "YW_mixed": (base, "mixed"),
+        "YW_fp64": (base, "fp64"),
+        "YW_rolling_mixed": (dict(base, k_r=0.05 * spec.kn), "mixed"),
+        "YW_rolling_fp64": (dict(base, k_r=0.05 * spec.kn), "fp64"),
+    }
+    out = {"config": {"workload": spec.name, "n": n, "a2_a1": spec.a_large / spec.a_small,
+                      "l2": "flushed before every timed step"}}
+    for name, (k, prec) in cases.items():
+        p = dss.default_params(g["box"], precision=prec, **k)
+        s = dss.Suspension(g["x"], g["a"], g["box"], p, ids=g["ids"], stream=stream)
+        time_steps(s, 5, flush)
+        steps = max(args.mode_steps // 2, 1)
+        t = time_steps(s, steps, flush)
+        c = s.counters()
+        out[name] = {"value": n * steps / (t * 1e-3), "unit": "particle-steps/s", "ms_per_step": t / steps,
+                     "steps": steps, "precision": prec, "pairs": c["npairs"], "contacts": c["ncontacts"],
+                     "M": c["M"], "cells": list(c["ncell"]), "kernels_ms": profile_pass(s, 10, flush)}
         s.close()
     return out
 
@@ -460,6 +494,8 @@ def main():
         extra_inputs["poly1m"] = workload("c3", rank)
     if "adjoint" in modes:
         extra_inputs["adjoint"] = workload("c5", rank)
+    if "wavy" in modes:
+        extra_inputs["wavy"] = workload("c6", rank)
     if "batched" in modes:
         # packed by spawned worker processes before the first CUDA call
         from paper_2108_01013_gb300 import synth
@@ -552,6 +588,10 @@ def main():
         if "analysis" in modes:
             with torch.cuda.nvtx.range("analysis"):
                 extra["analysis"] = mode_analysis(dss, g, spec, kw, args, stream)
+        if "wavy" in extra_inputs:
+            sp, gp = extra_inputs.pop("wavy")
+            with torch.cuda.nvtx.range("wavy"):
+                extra["wavy"] = mode_wavy(dss, gp, sp, args, flush, stream)
         del flush
         if batch is not None:
             with torch.cuda.nvtx.range("batched"):

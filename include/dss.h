@@ -12,10 +12,15 @@
  *     frictional contact with tangential-spring history (Eq. 4, 5);
  *   - Stokes drag (Eq. A1) and the modified velocity-Verlet update (Eq. 15)
  *     in the Lees-Edwards box (Eq. 16);
- *   - bulk stress from stresslets (Eq. 8, 9).
+ *   - bulk stress from stresslets (Eq. 8, 9);
+ *   - optionally: electro-chemical forces (Eq. 6, 7), the wavy shear flow of
+ *     Eq. 17 with the Faxen term of the Stokes drag (Eq. A1), and rolling
+ *     resistance between contacting particles (App. B, Eq. B1).
  *
  * Conventions: flow along x, gradient along y, vorticity along z;
- * U_inf = (gdot y, 0, 0), Omega_inf = (0, 0, -gdot/2).  Vector arrays are
+ * U_inf = (gdot y, 0, 0), Omega_inf = (0, 0, -gdot/2); with the wave of
+ * Eq. 17, U_inf,x = gdot y + U sin(2 pi n y / L_y) and Omega_inf, E_inf follow
+ * the local rate dU_inf,x/dy.  Vector arrays are
  * SoA with three planes: v[0*n + k], v[1*n + k], v[2*n + k].
  *
  * Pointers: every array argument may be host memory (pageable or pinned) or
@@ -93,6 +98,23 @@ typedef struct dss_params {
                                    listed out to the larger of the lubrication and
                                    electro-chemical ranges; lubrication acts within its own
                                    range only.  abar = 2 a_i a_j / (a_i + a_j) */
+  double wave_amp;              /* Eq. 17: amplitude U of the wave added to U_inf,x,
+                                   U sin(2 pi wave_n y / L_y) (L_y of each instance).  The
+                                   Stokes drag then takes the Faxen velocity
+                                   (1 + a^2/6 Laplacian) U_inf and the local Omega_inf at the
+                                   centre (Eq. A1); lubrication takes the velocities relative
+                                   to the flow at each centre and the strain of the mean of
+                                   the two centres' local rates; a particle's stresslet takes
+                                   the strain at its centre.  0: simple shear */
+  double k_r;                   /* App. B: rolling spring stiffness (k_r << k_n).  A contact
+                                   then also carries a rolling stretch xi_r integrating
+                                   u_r = abar (n x w_i - n x w_j) under the Coulomb limit
+                                   |k_r xi_r| <= mu |F_nor| (Eq. 5 with k_r for k_t); it adds
+                                   the torques abar n x (k_r xi_r) on i and its opposite on j,
+                                   no force and no stresslet.  0: off */
+  int32_t wave_n;               /* Eq. 17: whole number n >= 0 of wave periods along L_y
+                                   (the wave stays periodic under Lees-Edwards); 0: no wave */
+  int32_t reserved2_;           /* 0 */
 } dss_params;
 
 typedef struct dss_handle dss_handle;
@@ -184,12 +206,21 @@ int dss_get_state(dss_handle *h, double *x, double *u, double *w, double *alpha_
 
 /* Replaces the contact history: k entries with keys (lo_id << 32 | hi_id)
  * and tangential stretch xi (3 per entry, row-major [k][3], orientation
- * lo -> hi).  Used to resume from a checkpoint. */
+ * lo -> hi).  Used to resume from a checkpoint.  The rolling stretch of
+ * every entry (App. B) is set to zero. */
 int dss_set_history(dss_handle *h, int64_t k, const int64_t *keys, const double *xi);
 
 /* Copies the committed contact history out, sorted by key.  Writes up to
  * cap entries; *count receives the number of entries. */
 int dss_get_history(dss_handle *h, int64_t *keys, double *xi, int64_t cap, int64_t *count);
+
+/* The same with the rolling stretch of App. B: xr (row-major [k][3]; it does
+ * not depend on the orientation of the pair) may be NULL (zero), and is kept
+ * only when k_r > 0; dss_get_history_rolling writes zeros when k_r = 0. */
+int dss_set_history_rolling(dss_handle *h, int64_t k, const int64_t *keys, const double *xi,
+                            const double *xr);
+int dss_get_history_rolling(dss_handle *h, int64_t *keys, double *xi, double *xr, int64_t cap,
+                            int64_t *count);
 
 /* Counting sort and half-stencil enumeration at the current state (no time
  * advance).  The pairs can then be read with dss_get_pairs. */
@@ -244,7 +275,7 @@ int dss_last_step_ms(dss_handle *h, double *ms);
 
 /* Checkpoint of the whole dynamic state: positions, velocities, angular
  * velocities and both accelerations (id order), radii, the contact history
- * (keys and tangential stretch), the step count, the last stress and the
+ * (keys, tangential stretch and, when k_r > 0, rolling stretch), the step count, the last stress and the
  * running stress sums of every instance.  With buf == NULL, *len receives the
  * size needed; otherwise buf (host memory, *len bytes) receives the
  * checkpoint and *len its size (DSS_ERR_ARG, with *len set, when too small).
@@ -290,7 +321,8 @@ int dss_autotune(dss_handle *h, int32_t trial_steps, int32_t ncand, const double
  * Derivatives are pathwise: the pair set, contacts, Coulomb slips and the
  * taper ends of each step are those of the forward run and held fixed; with
  * the hard cutoff (lub_taper = 0) J has no pathwise dependence on delta_lub.
- * Single-instance handles only (DSS_ERR_ARG for a batch).  The handle is left
+ * Single-instance handles without the wave of Eq. 17 or rolling resistance
+ * only (DSS_ERR_ARG otherwise).  The handle is left
  * in the state after the rollout.  Output pointers are host or device
  * memory and may be NULL.  Synchronises the stream. */
 int dss_adjoint(dss_handle *h, int64_t nsteps, int32_t ckpt_every, const double *weights,

@@ -76,7 +76,8 @@ class Params(Structure):
                 ("cell_size", c_double), ("capacity_M", c_int32), ("pair_capacity", c_int32),
                 ("lub_taper", c_double), ("cell_mode", c_int32), ("reserved_", c_int32),
                 ("f_er", c_double), ("lambda_d", c_double), ("hamaker", c_double),
-                ("vdw_eps", c_double)]
+                ("vdw_eps", c_double), ("wave_amp", c_double), ("k_r", c_double),
+                ("wave_n", c_int32), ("reserved2_", c_int32)]
 
 
 class Counters(Structure):
@@ -117,6 +118,8 @@ SIGNATURES = {
     "dss_get_state": (c_int, [c_void_p, _vp, _vp, _vp, _vp, _vp]),
     "dss_set_history": (c_int, [c_void_p, c_int64, _vp, _vp]),
     "dss_get_history": (c_int, [c_void_p, _vp, _vp, c_int64, _lp]),
+    "dss_set_history_rolling": (c_int, [c_void_p, c_int64, _vp, _vp, _vp]),
+    "dss_get_history_rolling": (c_int, [c_void_p, _vp, _vp, _vp, c_int64, _lp]),
     "dss_neighbour_build": (c_int, [c_void_p]),
     "dss_get_pairs": (c_int, [c_void_p, _vp, c_int64, _lp]),
     "dss_force_eval": (c_int, [c_void_p, _vp, _vp]),

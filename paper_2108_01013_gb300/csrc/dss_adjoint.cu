@@ -88,7 +88,10 @@ __device__ __noinline__ void vjp_pass(const Geo& g, const InstGeo& I, const Pair
   const Vec3<D> Wi = mk3<D>(wi.x, wi.y, wi.z - Om);
   const Vec3<D> Wj = mk3<D>(wj.x, wj.y, wj.z - Om);
   const Vec3<D> du = mk3<D>(uj.x + in.sy * I.gdot * I.L[1] - ui.x, uj.y - ui.y, uj.z - ui.z);
-  const PairModelOut<D> o = pair_model<D>(g, I, q, r, rr, in.ai, in.aj, Vi, Vj, Wi, Wj, du, wi, wj, xo);
+  // simple shear without rolling springs (dss_adjoint refuses the others)
+  const Vec3<D> ro = mk3<D>(cst<D>(0.0), cst<D>(0.0), cst<D>(0.0));
+  const PairModelOut<D> o =
+      pair_model<D>(g, I, q, r, rr, in.ai, in.aj, Vi, Vj, Wi, Wj, du, wi, wj, xo, ro, I.gdot);
   D v = c.F[0] * o.F.x + c.F[1] * o.F.y + c.F[2] * o.F.z;
   v = v + c.Ti[0] * o.Ti.x + c.Ti[1] * o.Ti.y + c.Ti[2] * o.Ti.z;
   v = v + c.Tj[0] * o.Tj.x + c.Tj[1] * o.Tj.y + c.Tj[2] * o.Tj.z;

@@ -35,10 +35,10 @@ void free_buffers(dss_handle* h) {
     dfree(s.x); dfree(s.u); dfree(s.w); dfree(s.al); dfree(s.aw); dfree(s.a); dfree(s.id); dfree(s.inst);
     dfree(s.cls);
     dfree(s.iy);
-    dfree(s.vf); dfree(s.wf); dfree(s.posl); dfree(s.cellc);
+    dfree(s.vf); dfree(s.wf); dfree(s.posl); dfree(s.cellc); dfree(s.wv);
     memset(&s, 0, sizeof(s));
     ListBuf& L = h->lb[b];
-    dfree(L.count); dfree(L.list); dfree(L.start); dfree(L.xi); dfree(L.slot_of_id);
+    dfree(L.count); dfree(L.list); dfree(L.start); dfree(L.xi); dfree(L.xr); dfree(L.slot_of_id);
     dfree(L.id_of_slot);
     memset(&L, 0, sizeof(L));
   }
@@ -89,14 +89,21 @@ int alloc_pair_buffers(dss_handle* h, int64_t pcap, bool keep_hist) {
   int r;
   for (int b = 0; b < 2; ++b) {
     ListBuf& L = h->lb[b];
-    Xi4* xi = nullptr;
+    Xi4 *xi = nullptr, *xr = nullptr;
     if ((r = dalloc(h, &xi, (size_t)pcap))) return r;
+    if (h->g.k_r > 0.0 && (r = dalloc(h, &xr, (size_t)pcap))) {
+      dfree(xi);
+      return r;
+    }
     if (keep_hist && b == h->hist && L.xi && old > 0) {
       CK(cudaMemcpyAsync(xi, L.xi, sizeof(Xi4) * old, cudaMemcpyDeviceToDevice, h->stream));
+      if (xr && L.xr) CK(cudaMemcpyAsync(xr, L.xr, sizeof(Xi4) * old, cudaMemcpyDeviceToDevice, h->stream));
       CK(cudaStreamSynchronize(h->stream));
     }
     dfree(L.xi);
+    dfree(L.xr);
     L.xi = xi;
+    L.xr = xr;
   }
   h->pcap = pcap;
   h->g.pcap = pcap;
@@ -124,6 +131,7 @@ int alloc_buffers(dss_handle* h) {
         ((r = dalloc(h, &s.vf, n)) || (r = dalloc(h, &s.wf, n)) || (r = dalloc(h, &s.posl, n)) ||
          (r = dalloc(h, &s.cellc, n))))
       return r;
+    if (h->g.wave && (r = dalloc(h, &s.wv, n))) return r;
     ListBuf& L = h->lb[b];
     if ((r = dalloc(h, &L.count, n)) || (r = dalloc(h, &L.list, n * (size_t)h->g.Ms)) ||
         (r = dalloc(h, &L.start, n + 1)) || (r = dalloc(h, &L.slot_of_id, n)) ||
@@ -279,19 +287,30 @@ __global__ void k_iota(int n, int* __restrict__ v) {
   if (i < n) v[i] = i;
 }
 
-__global__ void k_default_vel(int n, const double* __restrict__ x, const InstGeo* __restrict__ ig,
+__global__ void k_default_vel(Geo g, int n, const double* __restrict__ x, const InstGeo* __restrict__ ig,
                               const int* __restrict__ inst, double* __restrict__ u,
                               double* __restrict__ w, bool du, bool dw) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const double gdot = ig[inst[i]].gdot;
-  if (du) { u[i] = gdot * x[n + i]; u[n + i] = 0.0; u[2 * n + i] = 0.0; }
+  const InstGeo& I = ig[inst[i]];
+  const double gdot = I.gdot;
+  const double y = x[n + i];
+  if (g.wave) {
+    // U_inf and Omega_inf of the wave of Eq. 17 at the centre
+    double sn, cs;
+    sincos(I.wave_k * y, &sn, &cs);
+    if (du) { u[i] = gdot * y + g.wave_amp * sn; u[n + i] = 0.0; u[2 * n + i] = 0.0; }
+    if (dw) { w[i] = 0.0; w[n + i] = 0.0; w[2 * n + i] = -0.5 * (gdot + g.wave_amp * I.wave_k * cs); }
+    return;
+  }
+  if (du) { u[i] = gdot * y; u[n + i] = 0.0; u[2 * n + i] = 0.0; }
   if (dw) { w[i] = 0.0; w[n + i] = 0.0; w[2 * n + i] = -0.5 * gdot; }
 }
 
-// Attach the stretch of a given history (sorted keys) to a freshly built list.
+// Attach the stretch of a given history (sorted keys) to a freshly built list
+// (and the rolling stretch, xr, when the list keeps one; NULL: zero).
 __global__ void k_attach_history(Geo g, StateBuf s, ListBuf L, const long long* __restrict__ keys,
-                                 const double* __restrict__ xi, int k) {
+                                 const double* __restrict__ xi, const double* __restrict__ xr, int k) {
   const int n = g.n;
   const int P = (int)min((int64_t)L.start[n], g.pcap);   // the host grew pcap to the list first
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
@@ -309,21 +328,29 @@ __global__ void k_attach_history(Geo g, StateBuf s, ListBuf L, const long long* 
       if (keys[m] == key) { f = m; break; }
       if (keys[m] < key) l = m + 1; else r = m - 1;
     }
-    Xi4 v;
+    Xi4 v, vr;
+    vr.x = vr.y = vr.z = vr.w = 0.0;
     if (f >= 0) {
       v.x = xi[3 * (int64_t)f];
       v.y = xi[3 * (int64_t)f + 1];
       v.z = xi[3 * (int64_t)f + 2];
       v.w = 1.0;
+      if (xr) {
+        vr.x = xr[3 * (int64_t)f];
+        vr.y = xr[3 * (int64_t)f + 1];
+        vr.z = xr[3 * (int64_t)f + 2];
+      }
     } else {
       v.x = v.y = v.z = v.w = 0.0;
     }
     L.xi[p] = v;
+    if (L.xr) L.xr[p] = vr;
   }
 }
 
 __global__ void k_history_out(Geo g, ListBuf L, long long* __restrict__ keys,
-                              double* __restrict__ xi, int* __restrict__ counter, int cap) {
+                              double* __restrict__ xi, double* __restrict__ xr, int* __restrict__ counter,
+                              int cap) {
   const int n = g.n;
   const int P = (int)min((int64_t)L.start[n], g.pcap);
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
@@ -342,6 +369,10 @@ __global__ void k_history_out(Geo g, ListBuf L, long long* __restrict__ keys,
       xi[3 * (int64_t)q] = v.x;
       xi[3 * (int64_t)q + 1] = v.y;
       xi[3 * (int64_t)q + 2] = v.z;
+      const Xi4 vr = L.xr ? L.xr[p] : Xi4{0.0, 0.0, 0.0, 0.0};
+      xr[3 * (int64_t)q] = vr.x;
+      xr[3 * (int64_t)q + 1] = vr.y;
+      xr[3 * (int64_t)q + 2] = vr.z;
     }
   }
 }
@@ -511,6 +542,9 @@ int geometry(dss_handle* h) {
     I.gn = h->inst_gn[k];
     I.gdot_f = (float)I.gdot;
     I.gn_f = (float)I.gn;
+    // the wave of Eq. 17 spans wave_n periods of this instance's L_y
+    I.wave_k = g.wave ? 2.0 * DSS_PI * (double)p.wave_n / I.L[1] : 0.0;
+    I.faxen_c = I.wave_k * I.wave_k / 6.0;
   }
   g.ncell = (int)cells;
   h->cell_edge = cs;
@@ -537,7 +571,8 @@ bool valid_params(const dss_params* p) {
          (p->lub_taper >= 0.0 && p->lub_taper < 1.0) && (p->cell_mode == 0 || p->cell_mode == 1) &&
          (p->f_er >= 0.0 && std::isfinite(p->f_er)) && (p->hamaker >= 0.0 && std::isfinite(p->hamaker)) &&
          (!(p->f_er > 0.0) || (p->lambda_d > 0.0 && std::isfinite(p->lambda_d))) &&
-         (!(p->hamaker > 0.0) || (p->vdw_eps > 0.0 && std::isfinite(p->vdw_eps)));
+         (!(p->hamaker > 0.0) || (p->vdw_eps > 0.0 && std::isfinite(p->vdw_eps))) &&
+         std::isfinite(p->wave_amp) && (p->wave_n >= 0) && (p->k_r >= 0.0 && std::isfinite(p->k_r));
 }
 
 // Common constructor: K instances of n[k] particles in boxes box[3k..3k+2]
@@ -627,6 +662,11 @@ int create_handle(dss_handle** out, const dss_params* p, int K, const int64_t* n
   g.f.hamaker12 = (float)(p->hamaker / 12.0);
   g.f.vdw_eps = (float)p->vdw_eps;
   g.f.range_a = (float)(4.0 * p->a0);
+  g.wave = (p->wave_amp != 0.0 && p->wave_n > 0) ? 1 : 0;
+  g.wave_amp = g.wave ? p->wave_amp : 0.0;
+  g.k_r = p->k_r;
+  g.f.k_r = (float)p->k_r;
+  g.f.mu_kr = p->k_r > 0.0 ? (float)(p->mu / p->k_r) : 0.0f;
   *out = h;
   return DSS_OK;
 }
@@ -808,7 +848,7 @@ int dss_set_state(dss_handle* h, const double* x, const double* a, const int32_t
   if (u) CK(cudaMemcpyAsync(s.u, u, sizeof(double) * 3 * n, cudaMemcpyDefault, h->stream));
   if (w) CK(cudaMemcpyAsync(s.w, w, sizeof(double) * 3 * n, cudaMemcpyDefault, h->stream));
   const int nb = (int)((n + 255) / 256);
-  if (!u || !w) k_default_vel<<<nb, 256, 0, h->stream>>>((int)n, s.x, h->ig, s.inst, s.u, s.w, !u, !w);
+  if (!u || !w) k_default_vel<<<nb, 256, 0, h->stream>>>(h->g, (int)n, s.x, h->ig, s.inst, s.u, s.w, !u, !w);
   if (alpha_lin) {
     CK(cudaMemcpyAsync(s.al, alpha_lin, sizeof(double) * 3 * n, cudaMemcpyDefault, h->stream));
     CK(cudaMemcpyAsync(s.aw, alpha_ang, sizeof(double) * 3 * n, cudaMemcpyDefault, h->stream));
@@ -1176,24 +1216,30 @@ int dss_get_counters(dss_handle* h, dss_counters* c) {
   return DSS_OK;
 }
 
-int dss_set_history(dss_handle* h, int64_t k, const int64_t* keys, const double* xi) {
+int dss_set_history_rolling(dss_handle* h, int64_t k, const int64_t* keys, const double* xi,
+                            const double* xr) {
   if (!h || k < 0 || (k > 0 && (!keys || !xi))) return DSS_ERR_ARG;
   if (!h->have_state) return DSS_ERR_STATE;
   ENTER(h);
   std::vector<std::pair<int64_t, int64_t>> order(k);
   std::vector<int64_t> hk(k);
-  std::vector<double> hx(3 * k);
+  std::vector<double> hx(3 * k), hr(3 * k, 0.0);
   if (k) {
     CK(cudaMemcpy(hk.data(), keys, sizeof(int64_t) * k, cudaMemcpyDefault));
     CK(cudaMemcpy(hx.data(), xi, sizeof(double) * 3 * k, cudaMemcpyDefault));
+    if (xr) CK(cudaMemcpy(hr.data(), xr, sizeof(double) * 3 * k, cudaMemcpyDefault));
   }
   for (int64_t q = 0; q < k; ++q) order[q] = {hk[q], q};
   std::sort(order.begin(), order.end());
-  std::vector<long long> sk(std::max<int64_t>(k, 1));
-  std::vector<double> sx(3 * std::max<int64_t>(k, 1));
+  const size_t m = (size_t)std::max<int64_t>(k, 1);
+  std::vector<long long> sk(m);
+  std::vector<double> sx(6 * m, 0.0);   // sliding then rolling stretch
   for (int64_t q = 0; q < k; ++q) {
     sk[q] = order[q].first;
-    for (int c = 0; c < 3; ++c) sx[3 * q + c] = hx[3 * order[q].second + c];
+    for (int c = 0; c < 3; ++c) {
+      sx[3 * q + c] = hx[3 * order[q].second + c];
+      sx[3 * m + 3 * q + c] = hr[3 * order[q].second + c];
+    }
   }
   long long* dk = nullptr;
   double* dx = nullptr;
@@ -1209,7 +1255,8 @@ int dss_set_history(dss_handle* h, int64_t k, const int64_t* keys, const double*
     const int rc = ensure_pair_capacity(h, L);
     if (rc) { cudaFree(dk); cudaFree(dx); return rc; }
   }
-  k_attach_history<<<pair_grid_blocks(h), 256, 0, h->stream>>>(h->g, h->st[h->cur], h->lb[L], dk, dx, (int)k);
+  k_attach_history<<<pair_grid_blocks(h), 256, 0, h->stream>>>(h->g, h->st[h->cur], h->lb[L], dk, dx,
+                                                                 dx + 3 * m, (int)k);
   CK(cudaGetLastError());
   int r = sync_status(h);
   cudaFree(dk);
@@ -1222,7 +1269,12 @@ int dss_set_history(dss_handle* h, int64_t k, const int64_t* keys, const double*
   return DSS_OK;
 }
 
-int dss_get_history(dss_handle* h, int64_t* keys, double* xi, int64_t cap, int64_t* count) {
+int dss_set_history(dss_handle* h, int64_t k, const int64_t* keys, const double* xi) {
+  return dss_set_history_rolling(h, k, keys, xi, nullptr);
+}
+
+int dss_get_history_rolling(dss_handle* h, int64_t* keys, double* xi, double* xr, int64_t cap,
+                            int64_t* count) {
   if (!h || !count || cap < 0 || (cap > 0 && (!keys || !xi))) return DSS_ERR_ARG;
   if (!h->have_state) return DSS_ERR_STATE;
   ENTER(h);
@@ -1233,17 +1285,19 @@ int dss_get_history(dss_handle* h, int64_t* keys, double* xi, int64_t cap, int64
   int* cnt = nullptr;
   size_t m = std::max(P, 1);
   CK(cudaMalloc((void**)&dk, sizeof(long long) * m));
-  CK(cudaMalloc((void**)&dx, sizeof(double) * 3 * m));
+  CK(cudaMalloc((void**)&dx, sizeof(double) * 6 * m));
   CK(cudaMalloc((void**)&cnt, sizeof(int)));
   CK(cudaMemsetAsync(cnt, 0, sizeof(int), h->stream));
-  k_history_out<<<pair_grid_blocks(h), 256, 0, h->stream>>>(h->g, h->lb[h->hist], dk, dx, cnt, (int)m);
+  k_history_out<<<pair_grid_blocks(h), 256, 0, h->stream>>>(h->g, h->lb[h->hist], dk, dx, dx + 3 * m, cnt,
+                                                              (int)m);
   int K = 0;
   CK(cudaMemcpyAsync(&K, cnt, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   std::vector<long long> hk(std::max(K, 1));
-  std::vector<double> hx(3 * (size_t)std::max(K, 1));
+  std::vector<double> hx(3 * (size_t)std::max(K, 1)), hr(3 * (size_t)std::max(K, 1));
   CK(cudaMemcpy(hk.data(), dk, sizeof(long long) * K, cudaMemcpyDeviceToHost));
   CK(cudaMemcpy(hx.data(), dx, sizeof(double) * 3 * K, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(hr.data(), dx + 3 * m, sizeof(double) * 3 * K, cudaMemcpyDeviceToHost));
   cudaFree(dk); cudaFree(dx); cudaFree(cnt);
   std::vector<std::pair<long long, int>> order(K);
   for (int q = 0; q < K; ++q) order[q] = {hk[q], q};
@@ -1252,9 +1306,16 @@ int dss_get_history(dss_handle* h, int64_t* keys, double* xi, int64_t cap, int64
   int64_t mm = std::min<int64_t>(cap, K);
   for (int64_t q = 0; q < mm; ++q) {
     keys[q] = order[q].first;
-    for (int c = 0; c < 3; ++c) xi[3 * q + c] = hx[3 * order[q].second + c];
+    for (int c = 0; c < 3; ++c) {
+      xi[3 * q + c] = hx[3 * order[q].second + c];
+      if (xr) xr[3 * q + c] = hr[3 * order[q].second + c];
+    }
   }
   return DSS_OK;
+}
+
+int dss_get_history(dss_handle* h, int64_t* keys, double* xi, int64_t cap, int64_t* count) {
+  return dss_get_history_rolling(h, keys, xi, nullptr, cap, count);
 }
 
 int dss_load_state(dss_handle* h, const double* x, const double* u, const double* w,
@@ -1320,6 +1381,7 @@ int dss_last_step_ms(dss_handle* h, double* ms) {
 // Checkpoint / resume.  Layout (host byte order):
 //   CkptHeader, then x, u, w, alpha_lin, alpha_ang (3n doubles each, id
 //   order), a (n doubles, id order), history keys (nhist int64), stretch
+//   (3*nhist doubles), with rolling resistance (k_r > 0) the rolling stretch
 //   (3*nhist doubles), sigma and sigma_sum (9K doubles each).
 // The sorted order inside the library is a function of positions and ids
 // alone, so a run resumed from a checkpoint repeats the uninterrupted run bit
@@ -1365,12 +1427,17 @@ uint64_t config_hash(const dss_handle* h) {
     const double e[4] = {p.f_er, p.lambda_d, p.hamaker, p.vdw_eps};
     v = fnv1a(v, e, sizeof(e));
   }
+  if (h->g.wave) {
+    const double wv[2] = {p.wave_amp, (double)p.wave_n};
+    v = fnv1a(v, wv, sizeof(wv));
+  }
+  if (p.k_r > 0.0) v = fnv1a(v, &p.k_r, sizeof(p.k_r));
   return v;
 }
 
-size_t ckpt_bytes(int64_t n, int64_t nhist, int K) {
-  return sizeof(CkptHeader) + sizeof(double) * 16 * (size_t)n + (sizeof(int64_t) + 3 * sizeof(double)) * nhist +
-         sizeof(double) * 18 * (size_t)K;
+size_t ckpt_bytes(int64_t n, int64_t nhist, int K, bool rolling) {
+  return sizeof(CkptHeader) + sizeof(double) * 16 * (size_t)n +
+         (sizeof(int64_t) + (rolling ? 6 : 3) * sizeof(double)) * nhist + sizeof(double) * 18 * (size_t)K;
 }
 
 // Forces the next dss_set_state to rebuild the cell grid and buffers.
@@ -1390,7 +1457,8 @@ int dss_save(dss_handle* h, void* buf, size_t* len) {
   int r = dss_get_history(h, nullptr, nullptr, 0, &nh);
   if (r) return r;
   const int64_t n = h->n;
-  const size_t need = ckpt_bytes(n, nh, h->K);
+  const bool rolling = h->g.k_r > 0.0;
+  const size_t need = ckpt_bytes(n, nh, h->K, rolling);
   if (!buf) {
     *len = need;
     return DSS_OK;
@@ -1413,14 +1481,15 @@ int dss_save(dss_handle* h, void* buf, size_t* len) {
   double* a = x + 15 * n;
   int64_t* keys = reinterpret_cast<int64_t*>(a + n);
   double* xi = reinterpret_cast<double*>(keys + nh);
-  double* sig = xi + 3 * nh;
+  double* xr = xi + 3 * nh;
+  double* sig = xr + (rolling ? 3 * nh : 0);
   std::vector<double> st(15 * (size_t)n);
   if ((r = dss_get_state(h, st.data(), st.data() + 3 * n, st.data() + 6 * n, st.data() + 9 * n,
                          st.data() + 12 * n)))
     return r;
   memcpy(x, st.data(), sizeof(double) * 15 * n);
   int64_t nh2 = 0;
-  if (nh > 0 && (r = dss_get_history(h, keys, xi, nh, &nh2))) return r;
+  if (nh > 0 && (r = dss_get_history_rolling(h, keys, xi, rolling ? xr : nullptr, nh, &nh2))) return r;
   if (nh2 != nh && nh > 0) return DSS_ERR_INTERNAL;
   CK(cudaMemcpyAsync(a, h->a_by_id, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
   CK(cudaMemcpyAsync(sig, h->sigma, sizeof(double) * 9 * h->K, cudaMemcpyDeviceToHost, h->stream));
@@ -1442,7 +1511,8 @@ int dss_load(dss_handle* h, const void* buf, size_t len) {
       hd.nhist < 0 || hd.nstep < 0 || hd.mean_steps < 0 || hd.config != config_hash(h))
     return DSS_ERR_ARG;
   const int64_t n = hd.n, nh = hd.nhist;
-  if (len < ckpt_bytes(n, nh, h->K)) return DSS_ERR_ARG;
+  const bool rolling = h->g.k_r > 0.0;
+  if (len < ckpt_bytes(n, nh, h->K, rolling)) return DSS_ERR_ARG;
   // copies keep the arrays aligned whatever the caller's buffer alignment
   const char* in = static_cast<const char*>(buf) + sizeof(CkptHeader);
   std::vector<double> st(16 * (size_t)n);
@@ -1454,12 +1524,17 @@ int dss_load(dss_handle* h, const void* buf, size_t len) {
   in += sizeof(int64_t) * nh;
   memcpy(xi.data(), in, sizeof(double) * 3 * nh);
   in += sizeof(double) * 3 * nh;
+  std::vector<double> xr(3 * (size_t)std::max<int64_t>(nh, 1), 0.0);
+  if (rolling) {
+    memcpy(xr.data(), in, sizeof(double) * 3 * nh);
+    in += sizeof(double) * 3 * nh;
+  }
   std::vector<double> sig(18 * (size_t)h->K);
   memcpy(sig.data(), in, sizeof(double) * 18 * h->K);
   const double* x = st.data();
   int r = dss_set_state(h, x, x + 15 * n, nullptr, x + 3 * n, x + 6 * n, x + 9 * n, x + 12 * n, hd.nstep);
   if (r) return r;
-  if ((r = dss_set_history(h, nh, keys.data(), xi.data()))) return r;
+  if ((r = dss_set_history_rolling(h, nh, keys.data(), xi.data(), rolling ? xr.data() : nullptr))) return r;
   CK(cudaMemcpyAsync(h->sigma, sig.data(), sizeof(double) * 9 * h->K, cudaMemcpyHostToDevice, h->stream));
   CK(cudaMemcpyAsync(h->sigma_sum, sig.data() + 9 * h->K, sizeof(double) * 9 * h->K,
                      cudaMemcpyHostToDevice, h->stream));
@@ -1534,7 +1609,8 @@ int dss_adjoint(dss_handle* h, int64_t nsteps, int32_t ckpt_every, const double*
                 int32_t initial_forces, double* J, double* dJ_dparams, double* dJ_dx0,
                 double* dJ_du0, double* dJ_dw0, double* dJ_dalpha0, double* dJ_dbeta0) {
   if (!h || nsteps < 1 || ckpt_every < 1 || !weights) return DSS_ERR_ARG;
-  if (h->K != 1) return DSS_ERR_ARG;
+  // single instance, simple shear, no rolling springs (the taped model)
+  if (h->K != 1 || h->g.wave || h->g.k_r > 0.0) return DSS_ERR_ARG;
   if (!h->have_state) return DSS_ERR_STATE;
   ENTER(h);
   const int64_t nseg = (nsteps + ckpt_every - 1) / ckpt_every;

@@ -1,6 +1,6 @@
 // Pair forces and their deterministic symmetric accumulation.
 //
-// k_pairs<MIXED>: a warp takes 32 consecutive owners and deals out their
+// k_pairs<MIXED, MINB, EXT>: a warp takes 32 consecutive owners and deals out their
 //   listed pairs (owner-sorted) 32 at a time.  Per pair: lubrication of
 //   App. A (Eq. A2, A3 with the coefficients of Eq. A6, A7 and the
 //   6 pi eta0 prefactor), stick-and-slide contact of Eq. 4-5 with the
@@ -11,7 +11,7 @@
 //   (-F and its torque) is appended to the partner's fixed-capacity row
 //   together with the owner's index.  No float is ever accumulated with an
 //   atomic.
-// k_gather<MIXED>: one thread per particle: its own sum plus the partner
+// k_gather<MIXED, EXT>: one thread per particle: its own sum plus the partner
 //   records of its row taken in increasing owner index (a fixed order, so the
 //   result is bitwise reproducible; rows of more than 8 records are summed by
 //   the whole warp, ranks counted and placed, then a fixed reduction), Stokes
@@ -53,10 +53,13 @@ struct HistRef {
 };
 
 // Tangential stretch of pair (i, j) (ids idi, idj) at the last committed
-// step, in the lo -> hi orientation; zero when the pair was not in contact.
+// step, in the lo -> hi orientation, and (when k_r > 0) its rolling stretch;
+// zero when the pair was not in contact.
+template <bool EXT>
 __device__ __forceinline__ void history_lookup(const Geo& g, const ListBuf& H, const HistRef& hr, int i,
-                                               int j, int idi, int idj, double xo[3]) {
+                                               int j, int idi, int idj, double xo[3], double ro[3]) {
   xo[0] = xo[1] = xo[2] = 0.0;
+  ro[0] = ro[1] = ro[2] = 0.0;
   const int oi = hr.idorder ? H.slot_of_id[idi] : hr.perm[i];
   const int oj = hr.idorder ? H.slot_of_id[idj] : hr.perm[j];
   int64_t pold = -1;
@@ -73,6 +76,12 @@ __device__ __forceinline__ void history_lookup(const Geo& g, const ListBuf& H, c
       xo[0] = v.x;
       xo[1] = v.y;
       xo[2] = v.z;
+      if (EXT && g.k_r > 0.0) {
+        const Xi4 vr = H.xr[pold];
+        ro[0] = vr.x;
+        ro[1] = vr.y;
+        ro[2] = vr.z;
+      }
     }
   }
 }
@@ -98,11 +107,13 @@ __device__ __forceinline__ F3 tangf(F3 n, F3 v) { return v - dotf(n, v) * n; }
 template <typename R>
 struct PairRes {
   R F[3], Ti[3], Tj[3], Fc[3], Fl[3], r[3];
-  double xi[3];
+  double xi[3], xr[3];
   int contact;
 };
 
-// FP64 pair from the state (exact FP64 throughout).
+// FP64 pair from the state (exact FP64 throughout).  EXT: the wave of
+// Eq. 17 or rolling resistance may be on (compiled out otherwise).
+template <bool EXT>
 __device__ __forceinline__ PairRes<double> pair_eval_fp64(const Geo& g, const InstGeo& I, const StateBuf& s,
                                                          const ListBuf& H, const HistRef& hr, double off,
                                                          int i, int j) {
@@ -120,21 +131,32 @@ __device__ __forceinline__ PairRes<double> pair_eval_fp64(const Geo& g, const In
   const V3 wj = v3(s.w[j], s.w[n + j], s.w[2 * n + j]);
   const int idi = s.id[i], idj = s.id[j];
   const double sgn = idi < idj ? 1.0 : -1.0;
-  double xo[3] = {0.0, 0.0, 0.0};
+  double xo[3] = {0.0, 0.0, 0.0}, ro[3] = {0.0, 0.0, 0.0};
   const double rr = sqrt(dot(r, r));
   if (rr - (ai + aj) < 0.0) {
-    history_lookup(g, H, hr, i, j, idi, idj, xo);
+    history_lookup<EXT>(g, H, hr, i, j, idi, idj, xo, ro);
     xo[0] *= sgn; xo[1] *= sgn; xo[2] *= sgn;
   }
   const double Om = -0.5 * I.gdot;
-  const V3 Vi = v3(ui.x - I.gdot * yi, ui.y, ui.z);
-  const V3 Vj = v3(uj.x - I.gdot * yj, uj.y, uj.z);
-  const V3 Wi = v3(wi.x, wi.y, wi.z - Om);
-  const V3 Wj = v3(wj.x, wj.y, wj.z - Om);
+  V3 Vi = v3(ui.x - I.gdot * yi, ui.y, ui.z);
+  V3 Vj = v3(uj.x - I.gdot * yj, uj.y, uj.z);
+  V3 Wi = v3(wi.x, wi.y, wi.z - Om);
+  V3 Wj = v3(wj.x, wj.y, wj.z - Om);
+  double rate = I.gdot;
+  if (EXT && g.wave) {
+    // the wave of Eq. 17 at each centre: V and W relative to the local flow,
+    // the pair's strain from the mean of the two local rates
+    const double2 qi = s.wv[i], qj = s.wv[j];
+    Vi.x -= qi.x;
+    Vj.x -= qj.x;
+    Wi.z += 0.5 * qi.y;
+    Wj.z += 0.5 * qj.y;
+    rate = I.gdot + 0.5 * (qi.y + qj.y);
+  }
   const V3 du = v3(uj.x + sy * I.gdot * I.L[1] - ui.x, uj.y - ui.y, uj.z - ui.z);
   const PairParams<double> pp{g.kn, g.kt, I.gn, g.mu, g.delta};
-  const PairModelOut<double> o =
-      pair_model<double>(g, I, pp, r, rr, ai, aj, Vi, Vj, Wi, Wj, du, wi, wj, v3(xo[0], xo[1], xo[2]));
+  const PairModelOut<double> o = pair_model<double, EXT>(g, I, pp, r, rr, ai, aj, Vi, Vj, Wi, Wj, du, wi, wj,
+                                                    v3(xo[0], xo[1], xo[2]), v3(ro[0], ro[1], ro[2]), rate);
   PairRes<double> q;
   q.F[0] = o.F.x; q.F[1] = o.F.y; q.F[2] = o.F.z;
   q.Ti[0] = o.Ti.x; q.Ti[1] = o.Ti.y; q.Ti[2] = o.Ti.z;
@@ -143,6 +165,7 @@ __device__ __forceinline__ PairRes<double> pair_eval_fp64(const Geo& g, const In
   q.Fl[0] = o.Fl.x; q.Fl[1] = o.Fl.y; q.Fl[2] = o.Fl.z;
   q.r[0] = dx; q.r[1] = dy; q.r[2] = dz;
   q.xi[0] = sgn * o.xi.x; q.xi[1] = sgn * o.xi.y; q.xi[2] = sgn * o.xi.z;
+  q.xr[0] = o.xr.x; q.xr[1] = o.xr.y; q.xr[2] = o.xr.z;
   q.contact = o.contact;
   return q;
 }
@@ -153,6 +176,7 @@ __device__ __forceinline__ PairRes<double> pair_eval_fp64(const Geo& g, const In
 // then d = (r^2 - S^2)/(r + S) with the division in FP32.  The tangential
 // stretch is carried and updated in FP64; the rest of the pair arithmetic is
 // FP32, on velocities taken relative to the ambient flow.
+template <bool EXT>
 __device__ __forceinline__ PairRes<float> pair_eval_mixed(const Geo& g, const InstGeo& I, const StateBuf& s,
                                                          const ListBuf& H, const HistRef& hr,
                                                          const StepGeo& sg,
@@ -201,17 +225,24 @@ __device__ __forceinline__ PairRes<float> pair_eval_mixed(const Geo& g, const In
   const float Ai = pi.w + li.w, Bj = pj.w + lj.w;
   PairRes<float> q;
   // ---- contact, Eq. 4-5; the stretch stays in FP64
-  F3 Fc = f3(0, 0, 0), nxf = f3(0, 0, 0);
+  F3 Fc = f3(0, 0, 0), nxf = f3(0, 0, 0), Tr = f3(0, 0, 0);
   q.xi[0] = q.xi[1] = q.xi[2] = 0.0;
+  q.xr[0] = q.xr[1] = q.xr[2] = 0.0;
   q.contact = num < 0.0f;
   if (q.contact) {
     const int idi = s.id[i], idj = s.id[j];
     const float sg = idi < idj ? 1.0f : -1.0f;   // stored (lo -> hi) vs i -> j orientation
-    double xo[3];
-    history_lookup(g, H, hr, i, j, idi, idj, xo);
-    // u_j(image) - u_i = (V_j - V_i) + gdot dy x
-    const F3 du = (Vj - Vi) + f3(gd * r.y, 0.f, 0.f);
-    const F3 wi = f3(Wi.x, Wi.y, Wi.z - 0.5f * gd), wj = f3(Wj.x, Wj.y, Wj.z - 0.5f * gd);
+    double xo[3], ro[3];
+    history_lookup<EXT>(g, H, hr, i, j, idi, idj, xo, ro);
+    // u_j(image) - u_i = (V_j - V_i) + gdot dy x (+ the wave's U_inf,x
+    // difference); absolute w = W + Omega_inf (local with the wave)
+    F3 du = (Vj - Vi) + f3(gd * r.y, 0.f, 0.f);
+    F3 wi = f3(Wi.x, Wi.y, Wi.z - 0.5f * gd), wj = f3(Wj.x, Wj.y, Wj.z - 0.5f * gd);
+    if (EXT && g.wave) {
+      du.x += wj4.w - wi4.w;
+      wi.z -= 0.5f * vi4.w;
+      wj.z -= 0.5f * vj4.w;
+    }
     const float fn = g.f.kn * d + I.gn_f * dotf(nn, du);
     const F3 ut = tangf(nn, du - crossf(Ai * wi + Bj * wj, nn));
     // stretch (stored orientation) in FP64: xi + delta, with the small change
@@ -239,6 +270,27 @@ __device__ __forceinline__ PairRes<float> pair_eval_mixed(const Geo& g, const In
     Fc = fn * nn + Ft;
     nxf = crossf(nn, Ft);
     q.xi[0] = xs0; q.xi[1] = xs1; q.xi[2] = xs2;
+    if (EXT && g.k_r > 0.0) {
+      // rolling resistance, App. B: the rolling stretch (orientation-free)
+      // carried in FP64 with its FP32 increment, like the sliding one
+      const float abar = 2.0f * Ai * Bj / (Ai + Bj);
+      const F3 rf = f3((float)ro[0], (float)ro[1], (float)ro[2]);
+      const float rn = dotf(nn, rf);
+      const F3 ur = (abar * g.f.dt) * crossf(nn, wi - wj);
+      const F3 dr = f3(ur.x - rn * nn.x, ur.y - rn * nn.y, ur.z - rn * nn.z);
+      double r0 = ro[0] + (double)dr.x, r1 = ro[1] + (double)dr.y, r2 = ro[2] + (double)dr.z;
+      F3 xrf = rf + dr;
+      const float capr = g.f.mu_kr * fabsf(fn);
+      const float xrm2 = dotf(xrf, xrf);
+      if (xrm2 > capr * capr) {
+        const float fs = capr * rsqrtf(xrm2);
+        const double fd = (double)fs;
+        r0 *= fd; r1 *= fd; r2 *= fd;
+        xrf = fs * xrf;
+      }
+      Tr = abar * crossf(nn, g.f.k_r * xrf);
+      q.xr[0] = r0; q.xr[1] = r1; q.xr[2] = r2;
+    }
   }
   // ---- electro-chemical forces, Eq. 6-7 (FP32; central, stresslet r (x) F).
   // The range decisions (lubrication cutoff, 20 lambda_D, 4 a0) are taken on
@@ -295,8 +347,11 @@ __device__ __forceinline__ PairRes<float> pair_eval_mixed(const Geo& g, const In
   const F3 dV = Vi - Vj;
   const float nV = dotf(nn, dV);
   const F3 fr = (xa * nV) * nn + ya * tangf(nn, dV) + ybi * crossf(nn, Wi) + ybj * crossf(nn, Wj);
-  const F3 twoEn = f3(gd * nn.y, gd * nn.x, 0.0f);
-  const float Pn = gd * nn.x * nn.y;
+  // strain of the shear rate acting on the pair (the wave of Eq. 17: the
+  // mean of the two centres' local rates)
+  const float rate = (EXT && g.wave) ? gd + 0.5f * (vi4.w + vj4.w) : gd;
+  const F3 twoEn = f3(rate * nn.y, rate * nn.x, 0.0f);
+  const float Pn = rate * nn.x * nn.y;
   const F3 Qn = twoEn - (2.0f * Pn) * nn;
   const F3 nperp = crossf(nn, twoEn);
   F3 Fl = k6 * (((xg * Pn) * nn + yg * Qn) - fr);
@@ -320,8 +375,12 @@ __device__ __forceinline__ PairRes<float> pair_eval_mixed(const Geo& g, const In
     }
   }
   const F3 F = Fc + Fl;
-  const F3 Ti = Ai * nxf + Tli;
-  const F3 Tj = Bj * nxf + Tlj;
+  F3 Ti = Ai * nxf + Tli;
+  F3 Tj = Bj * nxf + Tlj;
+  if (EXT && g.k_r > 0.0) {
+    Ti = Ti + Tr;
+    Tj = Tj - Tr;
+  }
   q.F[0] = F.x; q.F[1] = F.y; q.F[2] = F.z;
   q.Ti[0] = Ti.x; q.Ti[1] = Ti.y; q.Ti[2] = Ti.z;
   q.Tj[0] = Tj.x; q.Tj[1] = Tj.y; q.Tj[2] = Tj.z;
@@ -371,7 +430,7 @@ __device__ __forceinline__ void store_record(double* b, double a0, double a1, do
 // MINB: resident blocks per SM the register budget is cut for (a grid that
 // fills more than three blocks per SM gains from the fourth; smaller grids
 // run faster with the larger budget).
-template <bool MIXED, int MINB>
+template <bool MIXED, int MINB, bool EXT>
 __global__ void __launch_bounds__(kPairThreads, MINB)
 k_pairs(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ sgk, StateBuf s, ListBuf W,
         ListBuf H, const float4* __restrict__ posf, void* __restrict__ own_v, int* __restrict__ bw_count,
@@ -437,8 +496,8 @@ k_pairs(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ sgk, 
         const InstGeo& I = ig[inst];
         const StepGeo sg = sgk[inst];
         PairRes<R> q;
-        if constexpr (MIXED) q = pair_eval_mixed(g, I, s, H, hr, sg, posf, i, j);
-        else q = pair_eval_fp64(g, I, s, H, hr, sg.off, i, j);
+        if constexpr (MIXED) q = pair_eval_mixed<EXT>(g, I, s, H, hr, sg, posf, i, j);
+        else q = pair_eval_fp64<EXT>(g, I, s, H, hr, sg.off, i, j);
         v[0] = q.F[0]; v[1] = q.F[1]; v[2] = q.F[2];
         v[3] = q.Ti[0]; v[4] = q.Ti[1]; v[5] = q.Ti[2];
         // partner's share, appended to its row with the owner's index
@@ -450,6 +509,7 @@ k_pairs(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ sgk, 
           set_err(st, DSS_ERR_CAPACITY);
         }
         W.xi[p] = Xi4{q.xi[0], q.xi[1], q.xi[2], q.contact ? 1.0 : 0.0};
+        if (EXT && g.k_r > 0.0) W.xr[p] = Xi4{q.xr[0], q.xr[1], q.xr[2], 0.0};
         ncont += q.contact;
         // Eq. 9: S^C = r (x) F^C, S^L = sym(r (x) F^L), F on the owner
         if (inst != cur_inst) {
@@ -497,9 +557,24 @@ k_pairs(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ sgk, 
   // warps and blocks in FP64)
   __shared__ double red[kWarps][18];
   const bool moved = cur_inst != inst0;
+  // With the wave of Eq. 17 the single-particle stresslets 20/3 pi eta0 a^3
+  // E_inf(x) carry a local part, (10/3) pi eta0 a^3 U k cos(k y) on xy and
+  // yx: one owner per thread (the grid covers each owner once), added to its
+  // instance's slot.
+  R ew0 = R(0), ew1 = R(0);
+  if (EXT && g.wave) {
+    const int il0 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (il0 < n) {
+      const double a = s.a[il0];
+      const R e = (R)((10.0 / 3.0) * DSS_PI * g.eta0 * a * a * a * s.wv[il0].y);
+      if (s.inst[il0] == inst0) ew0 = e; else ew1 = e;
+    }
+  }
 #pragma unroll
   for (int q = 0; q < 18; ++q) {
     R v = q < 9 ? (moved ? park[threadIdx.x][q] : Sx[q]) : (moved ? Sx[q - 9] : R(0));
+    if (q == 1 || q == 3) v += ew0;
+    if (q == 10 || q == 12) v += ew1;
     for (int dlt = 16; dlt > 0; dlt >>= 1) v += __shfl_down_sync(0xffffffffu, v, dlt);
     if (lane == 0) red[wid][q] = (double)v;
   }
@@ -641,7 +716,7 @@ __device__ __forceinline__ void warp_sum_row(const R* __restrict__ row, int cc, 
 // half-kick of Eq. 15d.  Returns true when the sums are not finite (the
 // error is then set).  Every load that does not depend on the partner rows
 // is issued first.
-template <bool MIXED>
+template <bool MIXED, bool EXT>
 __device__ __forceinline__ bool gather_one(const Geo& g, const InstGeo* __restrict__ ig, const StateBuf& s,
                                            const void* __restrict__ own_v,
                                            const int* __restrict__ bw_count, const void* __restrict__ bw_v,
@@ -669,13 +744,18 @@ __device__ __forceinline__ bool gather_one(const Geo& g, const InstGeo* __restri
   const double* __restrict__ sw = s.w;
   double u[3] = {0.0, 0.0, 0.0}, w[3] = {0.0, 0.0, 0.0};
   float4 v4 = make_float4(0.f, 0.f, 0.f, 0.f), w4 = v4;
-  double yj = 0.0, gd = 0.0;
+  double yj = 0.0, gd = 0.0, fx = 0.0;
+  double2 wq = make_double2(0.0, 0.0);
   if constexpr (MIXED) {
     v4 = __ldg(s.vf + j);
     w4 = __ldg(s.wf + j);
   } else {
     yj = __ldg(s.x + n + j);
     gd = __ldg(&ig[__ldg(s.inst + j)].gdot);
+  }
+  if (EXT && g.wave) {
+    fx = __ldg(&ig[__ldg(s.inst + j)].faxen_c);
+    if constexpr (!MIXED) wq = s.wv[j];
   }
   if (!MIXED || stepm) {
 #pragma unroll
@@ -703,19 +783,28 @@ __device__ __forceinline__ bool gather_one(const Geo& g, const InstGeo* __restri
   }
   if (!valid) return false;
   if constexpr (MIXED) {
-    // Stokes drag on the FP32 velocities relative to the ambient flow
+    // Stokes drag on the FP32 velocities relative to the ambient flow (with
+    // the wave of Eq. 17, relative to the Faxen velocity of Eq. A1:
+    // u - (1 + a^2/6 Laplacian) U_inf = (u - U_inf) + a^2 k^2/6 U sin(k y))
     const float af = (float)a;
     const float kd = -g.f.k6 * af, kr = -g.f.k8 * af * af * af;
-    F[0] += kd * v4.x; F[1] += kd * v4.y; F[2] += kd * v4.z;
+    const float vx = (EXT && g.wave) ? v4.x + (float)(a * a * fx) * w4.w : v4.x;
+    F[0] += kd * vx; F[1] += kd * v4.y; F[2] += kd * v4.z;
     T[0] += kr * w4.x; T[1] += kr * w4.y; T[2] += kr * w4.z;
   } else {
     const double kd = -g.k6 * a, kr = -g.k8 * a * a * a;
-    F[0] += kd * (u[0] - gd * yj);
+    if (EXT && g.wave) {
+      // Faxen velocity (1 + a^2/6 Laplacian) U_inf,x and local Omega_inf
+      F[0] += kd * (u[0] - gd * yj - (1.0 - a * a * fx) * wq.x);
+      T[2] += kr * (w[2] + 0.5 * (gd + wq.y));
+    } else {
+      F[0] += kd * (u[0] - gd * yj);
+      T[2] += kr * (w[2] + 0.5 * gd);
+    }
     F[1] += kd * u[1];
     F[2] += kd * u[2];
     T[0] += kr * w[0];
     T[1] += kr * w[1];
-    T[2] += kr * (w[2] + 0.5 * gd);
   }
   bool bad = false;
   if (!(isfinite(F[0]) && isfinite(F[1]) && isfinite(F[2]) && isfinite(T[0]) && isfinite(T[1]) &&
@@ -762,7 +851,7 @@ __device__ __forceinline__ bool gather_one(const Geo& g, const InstGeo* __restri
 // the particles' critical path); the blocks after them take one particle per
 // thread.  The last block to finish commits the step; only the writes that
 // block reads (the stresses, an error code) are fenced before the count.
-template <bool MIXED>
+template <bool MIXED, bool EXT>
 __global__ void __launch_bounds__(kThreads)
 k_gather(Geo g, const InstGeo* __restrict__ ig, StateBuf s, const void* __restrict__ own_v,
          const int* __restrict__ bw_count, const void* __restrict__ bw_v, double* __restrict__ Fout,
@@ -784,7 +873,7 @@ k_gather(Geo g, const InstGeo* __restrict__ ig, StateBuf s, const void* __restri
       fence = threadIdx.x < 9;
     } else {
       const int j = (int)(blockIdx.x - g.K) * blockDim.x + threadIdx.x;
-      fence = gather_one<MIXED>(g, ig, s, own_v, bw_count, bw_v, Fout, Tout, st, mode, j,
+      fence = gather_one<MIXED, EXT>(g, ig, s, own_v, bw_count, bw_v, Fout, Tout, st, mode, j,
                                 s_slot[threadIdx.x >> 5]);
     }
   }
@@ -833,38 +922,51 @@ int pair_grid_blocks(const dss_handle* h) {
 
 int bw_slot_values() { return kSlot; }
 
-void launch_forces(dss_handle* h, int stbuf, int work_list, int hist_list, int adv, int mode,
-                   double* F_out, double* T_out) {
+namespace {
+// The pair and gather kernels of one configuration (EXT: the wave of Eq. 17
+// or rolling resistance is on; the plain kernels carry none of its code).
+template <bool EXT>
+void launch_forces_t(dss_handle* h, int stbuf, int work_list, int hist_list, int adv, int mode,
+                     double* F_out, double* T_out) {
   const int n = (int)h->n;
   const int pb = pair_grid_blocks(h);
   const bool mixed = h->g.precision == DSS_MIXED;
   prof_mark(h, 5);
   const bool big = pb > 3 * h->sms;
   if (mixed && big)
-    k_pairs<true, 4><<<pb, kPairThreads, 0, h->stream>>>(h->g, h->ig, h->sg, h->st[stbuf], h->lb[work_list],
-                                                         h->lb[hist_list], h->posf, h->own, h->bw_count,
-                                                         h->bw_rec, h->spart, h->status, adv, h->perm);
+    k_pairs<true, 4, EXT><<<pb, kPairThreads, 0, h->stream>>>(
+        h->g, h->ig, h->sg, h->st[stbuf], h->lb[work_list], h->lb[hist_list], h->posf, h->own, h->bw_count,
+        h->bw_rec, h->spart, h->status, adv, h->perm);
   else if (mixed)
-    k_pairs<true, 3><<<pb, kPairThreads, 0, h->stream>>>(h->g, h->ig, h->sg, h->st[stbuf], h->lb[work_list],
-                                                         h->lb[hist_list], h->posf, h->own, h->bw_count,
-                                                         h->bw_rec, h->spart, h->status, adv, h->perm);
+    k_pairs<true, 3, EXT><<<pb, kPairThreads, 0, h->stream>>>(
+        h->g, h->ig, h->sg, h->st[stbuf], h->lb[work_list], h->lb[hist_list], h->posf, h->own, h->bw_count,
+        h->bw_rec, h->spart, h->status, adv, h->perm);
   else
-    k_pairs<false, 2><<<pb, kPairThreads, 0, h->stream>>>(h->g, h->ig, h->sg, h->st[stbuf], h->lb[work_list],
-                                                          h->lb[hist_list], h->posf, h->own, h->bw_count,
-                                                          h->bw_rec, h->spart, h->status, adv, h->perm);
+    k_pairs<false, 2, EXT><<<pb, kPairThreads, 0, h->stream>>>(
+        h->g, h->ig, h->sg, h->st[stbuf], h->lb[work_list], h->lb[hist_list], h->posf, h->own, h->bw_count,
+        h->bw_rec, h->spart, h->status, adv, h->perm);
   prof_mark(h, 6);
   const int gb = (n + kThreads - 1) / kThreads + h->g.K;
   if (mixed)
-    k_gather<true><<<gb, kThreads, 0, h->stream>>>(h->g, h->ig, h->st[stbuf], h->own, h->bw_count, h->bw_rec,
-                                                   F_out, T_out, h->status, mode, h->spart, h->sigma,
-                                                   h->sigma_sum,
-                                                   h->lb[work_list].start, h->done_blocks);
+    k_gather<true, EXT><<<gb, kThreads, 0, h->stream>>>(h->g, h->ig, h->st[stbuf], h->own, h->bw_count,
+                                                        h->bw_rec, F_out, T_out, h->status, mode, h->spart,
+                                                        h->sigma, h->sigma_sum, h->lb[work_list].start,
+                                                        h->done_blocks);
   else
-    k_gather<false><<<gb, kThreads, 0, h->stream>>>(h->g, h->ig, h->st[stbuf], h->own, h->bw_count,
-                                                    h->bw_rec, F_out, T_out, h->status, mode, h->spart, h->sigma,
-                                                    h->sigma_sum,
-                                                    h->lb[work_list].start, h->done_blocks);
+    k_gather<false, EXT><<<gb, kThreads, 0, h->stream>>>(h->g, h->ig, h->st[stbuf], h->own, h->bw_count,
+                                                         h->bw_rec, F_out, T_out, h->status, mode, h->spart,
+                                                         h->sigma, h->sigma_sum, h->lb[work_list].start,
+                                                         h->done_blocks);
   prof_mark(h, 7);
+}
+}  // namespace
+
+void launch_forces(dss_handle* h, int stbuf, int work_list, int hist_list, int adv, int mode,
+                   double* F_out, double* T_out) {
+  if (h->g.wave || h->g.k_r > 0.0)
+    launch_forces_t<true>(h, stbuf, work_list, hist_list, adv, mode, F_out, T_out);
+  else
+    launch_forces_t<false>(h, stbuf, work_list, hist_list, adv, mode, F_out, T_out);
 }
 
 void launch_pairs_out(dss_handle* h, int list, long long* out) {

@@ -62,10 +62,14 @@ struct Geo {
   double taper;       // lubrication taper width w (0: hard cutoff)
   double f_er, lambda_d, hamaker, vdw_eps;   // electro-chemical forces (Eq. 6-7)
   double de;          // their range as a surface distance (0: off)
+  int wave;           // the wavy shear flow of Eq. 17 is on (wave_amp != 0, wave_n > 0)
+  double wave_amp;    // its amplitude U (wave number per instance: InstGeo::wave_k)
+  double k_r;         // rolling spring stiffness of App. B (0: off)
   struct {             // FP32 copies of the model constants (mixed precision)
     float kn, kt, mu_kt, dt, eps, k6, k8, mass_c;
     float taper, delta, delta_a0;
     float f_er, inv_lambda, range_r, hamaker12, vdw_eps, range_a;   // f_er: F_ER / a0
+    float k_r, mu_kr;  // rolling: k_r, mu / k_r
   } f;
 };
 
@@ -86,6 +90,8 @@ struct InstGeo {
   double gdot, gn;              // shear rate, normal dashpot
   float gdot_f, gn_f;
   double sumA3;                 // sum of a^3 (Einstein stresslet of Eq. 9)
+  double wave_k;                // 2 pi n / L_y of the wave of Eq. 17 (0: no wave)
+  double faxen_c;               // wave_k^2 / 6: the Faxen factor is 1 - a^2 faxen_c
 };
 
 // ------------------------------------------------------------------------
@@ -322,8 +328,11 @@ struct StateBuf {
   int* inst;    // n instance index
   unsigned char* cls;  // n size class (stencil reach), see Geo::rtab
   int* iy;      // n Lees-Edwards image count along y since the state was set (unwrapped y = y + iy L_y)
-  float4* vf;   // n, mixed precision: FP32 velocity relative to U_inf (xyz)
-  float4* wf;   // n, mixed precision: FP32 angular velocity relative to Omega_inf (xyz)
+  float4* vf;   // n, mixed precision: FP32 velocity relative to U_inf (xyz); with the wave
+                //    of Eq. 17, w = U k cos(k y) (the wave's part of the local rate)
+  float4* wf;   // n, mixed precision: FP32 angular velocity relative to Omega_inf (xyz); with
+                //    the wave, w = U sin(k y) (the wave's part of U_inf,x)
+  double2* wv;  // n, wave of Eq. 17 on: (U sin(k y), U k cos(k y)) at the centre
   float4* posl; // n, mixed precision: low words of the cell-local position and radius
   int* cellc;   // n, mixed precision: cell coordinates packed cx | cy << 10 | cz << 20
 };
@@ -340,6 +349,7 @@ struct ListBuf {
   int* start;       // n+1 row offsets into the pair arrays (exclusive scan of count)
   Xi4* xi;          // pcap: tangential stretch (lo->hi orientation) per pair slot; w = 1
                     // when the pair was in contact (d < 0), else 0
+  Xi4* xr;          // pcap when k_r > 0: rolling stretch (App. B) per pair slot (w unused)
   int* slot_of_id;  // n: sorted index of each id in this list's index space
   int* id_of_slot;  // n: id of each sorted index of this list
 };

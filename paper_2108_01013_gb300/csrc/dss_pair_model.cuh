@@ -210,22 +210,27 @@ struct PairParams {
 
 // Outputs: force on i (F = Fc + Fl), torques on i and j, the parts of the
 // force whose stresslet is r (x) F (contact and electro-chemical, Fc) and
-// sym(r (x) F) (lubrication, Fl), the new stretch (i -> j orientation).
+// sym(r (x) F) (lubrication, Fl), the new stretch (i -> j orientation) and
+// the new rolling stretch (App. B; orientation-free).
 template <typename T>
 struct PairModelOut {
-  Vec3<T> F, Ti, Tj, Fc, Fl, xi;
+  Vec3<T> F, Ti, Tj, Fc, Fl, xi, xr;
   int contact;
 };
 
 // r = x_j(image) - x_i, rr = |r|; Vi, Vj velocities relative to U_inf at each
-// centre; Wi, Wj angular velocities relative to Omega_inf; du = u_j(image) -
-// u_i (absolute); wi, wj absolute angular velocities; xo stretch (i -> j).
-template <typename T>
+// centre; Wi, Wj angular velocities relative to Omega_inf at each centre;
+// du = u_j(image) - u_i (absolute); wi, wj absolute angular velocities; xo
+// stretch (i -> j); ro rolling stretch (used when k_r > 0); rate the shear
+// rate whose strain acts on the pair's lubrication (gdot, or in the wave of
+// Eq. 17 the mean of the two centres' local rates).
+template <typename T, bool EXT = false>
 __device__ __forceinline__ PairModelOut<T> pair_model(const Geo& g, const InstGeo& I,
                                                       const PairParams<T>& q, Vec3<T> r, T rr,
                                                       double ai, double aj, Vec3<T> Vi, Vec3<T> Vj,
                                                       Vec3<T> Wi, Vec3<T> Wj, Vec3<T> du, Vec3<T> wi,
-                                                      Vec3<T> wj, Vec3<T> xo) {
+                                                      Vec3<T> wj, Vec3<T> xo, Vec3<T> ro, double rate) {
+  (void)I;
   PairModelOut<T> o;
   const T zero = cst<T>(0.0);
   const T ir = 1.0 / rr;
@@ -236,6 +241,7 @@ __device__ __forceinline__ PairModelOut<T> pair_model(const Geo& g, const InstGe
   o.Fc = mk3<T>(zero, zero, zero);
   Vec3<T> Tci = o.Fc, Tcj = o.Fc;
   o.xi = o.Fc;
+  o.xr = o.Fc;
   o.contact = 0;
   if (val(d) < 0.0) {
     o.contact = 1;
@@ -252,6 +258,19 @@ __device__ __forceinline__ PairModelOut<T> pair_model(const Geo& g, const InstGe
     Tci = ai * nxf;
     Tcj = aj * nxf;
     o.xi = xs;
+    // rolling resistance, App. B: the procedure of Eq. 5 on the rolling
+    // velocity abar (n x w_i - n x w_j) with k_r; torques only
+    if (EXT && g.k_r > 0.0) {
+      const double abar = 2.0 * ai * aj / (ai + aj);
+      Vec3<T> xr = tang(n, ro) + g.dt * (abar * cross(n, wi - wj));
+      const T capr = q.mu * fabs(fn) / g.k_r;
+      const T xrm = sqrt(dot(xr, xr));
+      if (val(xrm) > val(capr)) xr = (capr / xrm) * xr;
+      const Vec3<T> Tr = abar * cross(n, g.k_r * xr);
+      Tci = Tci + Tr;
+      Tcj = Tcj - Tr;
+      o.xr = xr;
+    }
   }
   // ---- electro-chemical forces, Eq. 6-7 (central; stresslet r (x) F like contact)
   bool lub_on = true;
@@ -299,9 +318,10 @@ __device__ __forceinline__ PairModelOut<T> pair_model(const Geo& g, const InstGe
   const Vec3<T> dV = Vi - Vj;
   const T nV = dot(n, dV);
   const Vec3<T> fr = (xa * nV) * n + ya * tang(n, dV) + ybi * cross(n, Wi) + ybj * cross(n, Wj);
-  // simple shear: 2 E n = gdot (n_y, n_x, 0), P = gdot n_x n_y, Q.n = 2 E n - 2 P n
-  const Vec3<T> twoEn = mk3<T>(I.gdot * n.y, I.gdot * n.x, zero);
-  const T P = I.gdot * n.x * n.y;
+  // shear along x of rate `rate`: 2 E n = rate (n_y, n_x, 0), P = rate n_x n_y,
+  // Q.n = 2 E n - 2 P n
+  const Vec3<T> twoEn = mk3<T>(rate * n.y, rate * n.x, zero);
+  const T P = rate * n.x * n.y;
   const Vec3<T> Qn = twoEn - (2.0 * P) * n;
   const Vec3<T> nperp = cross(n, twoEn);
   const Vec3<T> fe = (xg * P) * n + yg * Qn;

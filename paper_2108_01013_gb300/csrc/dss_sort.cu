@@ -163,7 +163,8 @@ k_scatter(int n, const int* __restrict__ key, const int* __restrict__ offs,
 
 // 4. order inside each cell by id (so the sorted order, and with it every
 // summation order downstream, is a function of positions and ids alone) and
-// state gather
+// state gather (WAVE: the wave of Eq. 17 is on, compiled out otherwise)
+template <bool WAVE>
 __global__ void __launch_bounds__(kThreads)
 k_rank_gather(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ sgk, StateBuf src,
               StateBuf dst, const int* __restrict__ key, const int* __restrict__ cell_start,
@@ -213,7 +214,19 @@ k_rank_gather(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__
   dst.cls[f] = src.cls[o];
   // image count: leaving through the top is one image up
   dst.iy[f] = src.iy[o] - (predict ? (int)xc[o] : 0);
-  if (g.precision == DSS_MIXED) {
+  if (WAVE) {
+    // the wave of Eq. 17 at the centre, once per evaluation: its part of
+    // U_inf,x and of the local rate dU_inf,x/dy
+    double sn, cs;
+    sincos(I.wave_k * p.y, &sn, &cs);
+    const double ws = g.wave_amp * sn, wc = g.wave_amp * I.wave_k * cs;
+    dst.wv[f] = make_double2(ws, wc);
+    if (g.precision == DSS_MIXED) {
+      dst.vf[f] = make_float4((float)(p.ux - I.gdot * p.y - ws), (float)p.uy, (float)p.uz, (float)wc);
+      dst.wf[f] = make_float4((float)dst.w[f], (float)dst.w[n + f],
+                              (float)(dst.w[2 * n + f] + 0.5 * (I.gdot + wc)), (float)ws);
+    }
+  } else if (g.precision == DSS_MIXED) {
     // FP32 copies relative to the ambient flow for the FP32 pair arithmetic:
     // u - U_inf(x) and w - Omega_inf are O(gdot a), free of O(gdot L) terms
     dst.vf[f] = make_float4((float)(p.ux - I.gdot * p.y), (float)p.uy, (float)p.uz, 0.f);
@@ -357,7 +370,12 @@ void launch_sort(dss_handle* h, bool predict, int src, int dst) {
   prof_mark(h, 2);
   k_scatter<<<blocks, kThreads, 0, h->stream>>>(n, h->key, h->offs, h->cell_start, h->tmp, h->status);
   prof_mark(h, 3);
-  k_rank_gather<<<blocks, kThreads, 0, h->stream>>>(h->g, h->ig, h->sg, h->st[src], h->st[dst], h->key,
-                                                    h->cell_start, h->tmp, h->perm, h->cellid,
-                                                    h->posf, h->status, predict, h->pred, h->xc);
+  if (h->g.wave)
+    k_rank_gather<true><<<blocks, kThreads, 0, h->stream>>>(h->g, h->ig, h->sg, h->st[src], h->st[dst], h->key,
+                                                            h->cell_start, h->tmp, h->perm, h->cellid,
+                                                            h->posf, h->status, predict, h->pred, h->xc);
+  else
+    k_rank_gather<false><<<blocks, kThreads, 0, h->stream>>>(h->g, h->ig, h->sg, h->st[src], h->st[dst], h->key,
+                                                             h->cell_start, h->tmp, h->perm, h->cellid,
+                                                             h->posf, h->status, predict, h->pred, h->xc);
 }

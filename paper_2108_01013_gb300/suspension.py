@@ -18,8 +18,11 @@ from . import _native as nat
 def default_params(box=None, *, kn=1e4, kt=None, gamma_n=None, mu=0.5, eta0=1.0, rho=1.0,
                    delta_lub=0.05, lub_eps=1e-3, a0=1.0, lub_cutoff_mode=0, precision="fp64",
                    shear_rate=1.0, dt=1e-4, cell_size=0.0, capacity_M=0, pair_capacity=0,
-                   lub_taper=0.0, cell_mode=0, f_er=0.0, lambda_d=0.05, hamaker=0.0, vdw_eps=0.01):
-    """Model parameters; kt defaults to kn/2 and gamma_n to 1e-7 kn / gdot."""
+                   lub_taper=0.0, cell_mode=0, f_er=0.0, lambda_d=0.05, hamaker=0.0, vdw_eps=0.01,
+                   wave_amp=0.0, wave_n=0, k_r=0.0):
+    """Model parameters; kt defaults to kn/2 and gamma_n to 1e-7 kn / gdot.
+    wave_amp, wave_n: the wavy shear flow of Eq. 17; k_r: the rolling spring of
+    App. B (0: off)."""
     p = nat.Params()
     p.kn = kn
     p.kt = 0.5 * kn if kt is None else kt
@@ -35,6 +38,7 @@ def default_params(box=None, *, kn=1e4, kt=None, gamma_n=None, mu=0.5, eta0=1.0,
     p.lub_taper = lub_taper
     p.cell_mode = cell_mode
     p.f_er, p.lambda_d, p.hamaker, p.vdw_eps = f_er, lambda_d, hamaker, vdw_eps
+    p.wave_amp, p.wave_n, p.k_r = wave_amp, int(wave_n), k_r
     return p
 
 
@@ -165,14 +169,20 @@ class Suspension:
         return dict(steps_done=c.steps_done, nstep=c.nstep, npairs=c.npairs, ncontacts=c.ncontacts,
                     max_row=c.max_row, band_checks=c.band_checks, M=c.M, ncell=tuple(c.ncell))
 
-    def history(self):
+    def history(self, rolling: bool = False):
+        """Committed contact history sorted by key: (keys, xi), or (keys, xi, xr)
+        with the rolling stretch of App. B."""
         cnt = c_int64(0)
         nat.check(self.lib.dss_get_history(self._h, None, None, 0, byref(cnt)), "dss_get_history")
         k = cnt.value
         keys = np.zeros(max(k, 1), dtype=np.int64)
         xi = np.zeros((max(k, 1), 3))
-        nat.check(self.lib.dss_get_history(self._h, c_void_p(keys.ctypes.data), c_void_p(xi.ctypes.data),
-                                           k, byref(cnt)), "dss_get_history")
+        xr = np.zeros((max(k, 1), 3))
+        nat.check(self.lib.dss_get_history_rolling(self._h, c_void_p(keys.ctypes.data),
+                                                   c_void_p(xi.ctypes.data), c_void_p(xr.ctypes.data),
+                                                   k, byref(cnt)), "dss_get_history_rolling")
+        if rolling:
+            return keys[:k], xi[:k], xr[:k]
         return keys[:k], xi[:k]
 
     # ---- analysis pass (dss_rheology, dss_get_images, dss_dispersion*,
@@ -209,11 +219,19 @@ class Suspension:
                   "dss_contact_clusters")
         return label, int(cnt.value)
 
-    def set_history(self, keys, xi):
+    def set_history(self, keys, xi, xr=None):
+        """Replace the contact history (keys lo_id << 32 | hi_id, sliding stretch
+        lo -> hi, optional rolling stretch)."""
         keys = np.ascontiguousarray(keys, dtype=np.int64)
         xi = np.ascontiguousarray(xi, dtype=np.float64).reshape(-1, 3)
-        nat.check(self.lib.dss_set_history(self._h, keys.shape[0], c_void_p(keys.ctypes.data),
-                                           c_void_p(xi.ctypes.data)), "dss_set_history")
+        if xr is None:
+            nat.check(self.lib.dss_set_history(self._h, keys.shape[0], c_void_p(keys.ctypes.data),
+                                               c_void_p(xi.ctypes.data)), "dss_set_history")
+            return
+        xr = np.ascontiguousarray(xr, dtype=np.float64).reshape(-1, 3)
+        nat.check(self.lib.dss_set_history_rolling(self._h, keys.shape[0], c_void_p(keys.ctypes.data),
+                                                   c_void_p(xi.ctypes.data), c_void_p(xr.ctypes.data)),
+                  "dss_set_history_rolling")
 
     def save(self) -> bytes:
         """Checkpoint of the dynamic state, history, step count and stress sums."""

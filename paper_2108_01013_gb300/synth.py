@@ -119,6 +119,19 @@ SPECS = {
     "c3": Spec("c3_polydisperse_1m", 1_000_000, 0.50, radii="loguniform", mu=0.5,
                steps=1000, seed=3, max_iter=20),
     "c5": Spec("c5_rollout_20k", 20_000, 0.54, mu=0.5, steps=200, seed=5),
+    # Table 5 (case YW): 2^16 particles, radius ratio a2/a1 = 3 with the large
+    # spheres holding a quarter of the small ones' volume (V2/V1 = 0.25),
+    # phi = 0.5; k_n = 4e5 eta0 a0 gdot, k_t/k_n = 2/7, gamma_n gdot/k_n = 1e-7,
+    # St = rho a0^2 gdot/eta0 = 1e-3, mu = 1, delta_lub = 0.25 a0,
+    # lambda_D = 0.02 a0, F^R/F^A = 19 at contact with the repulsion at
+    # gdot/gdot_0 = 1 (F_ER = eta0 a0^2 gdot), the wave U = 20 gdot a0 with
+    # n = 1; time step gamma_n/k_n (Sec. II A).
+    "c6": Spec("c6_wavy_bidisperse_65k", 65_536, 0.50, a_small=1.0, a_large=3.0,
+               frac_large=(0.25 / 27.0) / (1.0 + 0.25 / 27.0), mu=1.0, kn=4e5, dt=1e-7,
+               steps=1000, seed=6,
+               extra=dict(kt=4e5 * 2.0 / 7.0, rho=1e-3, eta0=1.0, delta_lub=0.25,
+                          lub_cutoff_mode=1, f_er=1.0, lambda_d=0.02,
+                          hamaker=12.0 * 1e-4 / 19.0, vdw_eps=0.01, wave_amp=20.0, wave_n=1)),
 }
 
 
