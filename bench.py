@@ -287,7 +287,9 @@ def mode_wavy(dss, g, spec, args, flush, stream):
     """Table 5: 2^16 spheres of radius ratio 3 (V2/V1 = 0.25, phi = 0.5) with
     the electro-chemical forces, in the uniform shear (NW) and in the wavy
     shear flow of Eq. 17 (YW, U = 20 gdot a0, n = 1, Faxen drag), and YW with
-    the rolling resistance of App. B (k_r = 0.05 k_n)."""
+    the rolling resistance of App. B (k_r = 0.05 k_n); YW also on the
+    size-class grid (cell_mode 1: the small spheres search cells sized for
+    their own range, Sec. II A)."""
     n = g["a"].shape[0]
     base = dict(mu=spec.mu, kn=spec.kn, shear_rate=spec.shear_rate, dt=spec.dt, **spec.extra)
     cases = {
@@ -296,6 +298,7 @@ def mode_wavy(dss, g, spec, args, flush, stream):
         "YW_fp64": (base, "fp64"),
         "YW_rolling_mixed": (dict(base, k_r=0.05 * spec.kn), "mixed"),
         "YW_rolling_fp64": (dict(base, k_r=0.05 * spec.kn), "fp64"),
+        "YW_mixed_size_classes": (dict(base, cell_mode=1), "mixed"),
     }
     out = {"config": {"workload": spec.name, "n": n, "a2_a1": spec.a_large / spec.a_small,
                       "l2": "flushed before every timed step"}}

@@ -13,9 +13,11 @@
 //   atomic.
 // k_gather<MIXED, EXT>: one thread per particle: its own sum plus the partner
 //   records of its row taken in increasing owner index (a fixed order, so the
-//   result is bitwise reproducible; rows of more than 8 records are summed by
-//   the whole warp, ranks counted and placed, then a fixed reduction), Stokes
-//   drag (Eq. A1) and the corrector
+//   result is bitwise reproducible; rows of 9 to 24 FP32 records and longer
+//   FP64 rows are summed by the whole warp, ranks counted and placed, then a
+//   fixed reduction; longer FP32 rows by their own thread in 64-bit fixed
+//   point, whose sum does not depend on the order), Stokes drag (Eq. A1) and
+//   the corrector
 //   of Eq. 15d.  K leading blocks reduce each instance's bulk stress of
 //   Eq. 8 from the pair blocks' partials; the last block of the gather to
 //   finish adds them to the running sums and commits the step.
@@ -672,6 +674,83 @@ __device__ __forceinline__ void sum_records(const R* __restrict__ row, int cnt, 
 }
 
 constexpr int kHeavyWin = 256;   // ranks placed per pass of a heavy row
+constexpr int kRankedMax = 24;   // FP32 rows up to this length are summed in owner order
+
+// FP32 value as a fixed-point integer in units of 2^(e - 126 - bits), e the
+// largest biased exponent of its row: the 24-bit significand shifted left by
+// bits - 24 - (e - e_v) (at most bits - 24), or right with the low bits
+// dropped.  Zero and denormals give 0.  Integer operations only, so the
+// value is the same on every path.
+__device__ __forceinline__ long long fx_of(float v, int e, int bits) {
+  const int u = __float_as_int(v);
+  const int ev = (u >> 23) & 0xff;
+  if (ev == 0) return 0;
+  long long m = (long long)((u & 0x7fffff) | 0x800000);
+  const int sh = bits - 24 - (e - ev);
+  m = sh >= 0 ? (m << sh) : (sh > -25 ? (m >> -sh) : 0);
+  return u < 0 ? -m : m;
+}
+
+// A row of more than 8 FP32 records (mixed precision), summed by its own
+// thread in 64-bit fixed point.  Per component the largest exponent e of the
+// row fixes the unit 2^(e - 126 - bits), bits = 62 - ceil(log2(cc + 1)), so
+// that every record is an integer below 2^bits and the row's sum stays below
+// 2^62 (a first pass finds e, a second adds; four records in flight per
+// thread).  Integer addition is
+// associative: the total is a function of the set of records alone, whatever
+// their order in the row, so no ranking and no help from the other lanes is
+// needed.  It is exact up to the dropped bits below 2^-(bits - 24) of each
+// record relative to the row's largest (more accurate than an FP32 running
+// sum).  A non-finite record makes the total NaN.
+__device__ __forceinline__ void row_sum_fixed(const float* __restrict__ row, int cc, float tot[6]) {
+  int e[6] = {0, 0, 0, 0, 0, 0};
+  bool bad = false;
+  int k = 0;
+  for (; k + 4 <= cc; k += 4) {
+    float b[4][8];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) load_record(row + (k + t) * kSlot, b[t]);
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        const int ev = (__float_as_int(b[t][c]) >> 23) & 0xff;
+        e[c] = max(e[c], ev);
+        bad |= ev == 0xff;
+      }
+  }
+  for (; k < cc; ++k) {
+    float b[8];
+    load_record(row + k * kSlot, b);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      const int ev = (__float_as_int(b[c]) >> 23) & 0xff;
+      e[c] = max(e[c], ev);
+      bad |= ev == 0xff;
+    }
+  }
+  const int bits = 62 - (32 - __clz(cc));
+  long long acc[6] = {0, 0, 0, 0, 0, 0};
+  k = 0;
+  for (; k + 4 <= cc; k += 4) {
+    float b[4][8];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) load_record(row + (k + t) * kSlot, b[t]);
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+#pragma unroll
+      for (int c = 0; c < 6; ++c) acc[c] += fx_of(b[t][c], e[c], bits);
+  }
+  for (; k < cc; ++k) {
+    float b[8];
+    load_record(row + k * kSlot, b);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) acc[c] += fx_of(b[c], e[c], bits);
+  }
+#pragma unroll
+  for (int c = 0; c < 6; ++c)
+    tot[c] = bad ? __int_as_float(0x7fc00000) : (float)ldexp((double)acc[c], e[c] - 126 - bits);
+}
 
 // A row of more than 8 records, summed by the whole warp: each record's rank
 // in owner order is counted (the lanes read the owner words together), the
@@ -726,8 +805,8 @@ __device__ __forceinline__ bool gather_one(const Geo& g, const InstGeo* __restri
   const R* __restrict__ own = static_cast<const R*>(own_v);
   const R* __restrict__ bw = static_cast<const R*>(bw_v);
   const int n = g.n;
-  // every lane of the warp takes part in the heavy rows below; lanes past
-  // the last particle work on particle 0 and write nothing
+  // every lane of the warp takes part in the long FP64 rows below; lanes
+  // past the last particle work on particle 0 and write nothing
   const bool valid = j0 < n;
   const int j = valid ? j0 : 0;
   int cnt = valid ? __ldg(bw_count + j) : 0;
@@ -765,19 +844,36 @@ __device__ __forceinline__ bool gather_one(const Geo& g, const InstGeo* __restri
     }
   }
   cnt = cnt < g.M ? cnt : g.M;
-  if (cnt <= 8) sum_records<R>(bw + (int64_t)j * g.M * kSlot, cnt, F, T);
-  unsigned heavy = __ballot_sync(0xffffffffu, cnt > 8);
-  while (heavy) {
-    const int src = __ffs(heavy) - 1;
-    heavy &= heavy - 1u;
-    const int jj = __shfl_sync(0xffffffffu, j, src), cc = __shfl_sync(0xffffffffu, cnt, src);
-    R tot[6];
-    warp_sum_row<R>(bw + (int64_t)jj * g.M * kSlot, cc, slots, tot);
-    if ((int)(threadIdx.x & 31) == src) {
+  if (cnt <= 8) {
+    sum_records<R>(bw + (int64_t)j * g.M * kSlot, cnt, F, T);
+  } else if constexpr (MIXED) {
+    if (cnt > kRankedMax) {
+      // long FP32 rows: each thread its own, in fixed point
+      float tot[6];
+      row_sum_fixed(bw + (int64_t)j * g.M * kSlot, cnt, tot);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         F[c] += tot[c];
         T[c] += tot[3 + c];
+      }
+    }
+  }
+  {
+    // rows of 9..kRankedMax FP32 records, and every longer FP64 row: the
+    // whole warp, one row after another, in owner order
+    unsigned heavy = __ballot_sync(0xffffffffu, cnt > 8 && (!MIXED || cnt <= kRankedMax));
+    while (heavy) {
+      const int src = __ffs(heavy) - 1;
+      heavy &= heavy - 1u;
+      const int jj = __shfl_sync(0xffffffffu, j, src), cc = __shfl_sync(0xffffffffu, cnt, src);
+      R tot[6];
+      warp_sum_row<R>(bw + (int64_t)jj * g.M * kSlot, cc, slots, tot);
+      if ((int)(threadIdx.x & 31) == src) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          F[c] += tot[c];
+          T[c] += tot[3 + c];
+        }
       }
     }
   }
@@ -849,10 +945,11 @@ __device__ __forceinline__ bool gather_one(const Geo& g, const InstGeo* __restri
 
 // Blocks 0..K-1 reduce the bulk stress of instance k (scheduled first, off
 // the particles' critical path); the blocks after them take one particle per
-// thread.  The last block to finish commits the step; only the writes that
+// thread.  At most 80 registers, so that six blocks fit on an SM and a
+// 100k-particle grid runs in one wave.  The last block to finish commits the step; only the writes that
 // block reads (the stresses, an error code) are fenced before the count.
 template <bool MIXED, bool EXT>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 6)
 k_gather(Geo g, const InstGeo* __restrict__ ig, StateBuf s, const void* __restrict__ own_v,
          const int* __restrict__ bw_count, const void* __restrict__ bw_v, double* __restrict__ Fout,
          double* __restrict__ Tout, DevStatus* st, int mode, const double* __restrict__ spart,

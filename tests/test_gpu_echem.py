@@ -129,3 +129,25 @@ def test_echem_size_classes_pairs_bit_exact(env):
     np.testing.assert_array_equal(s.pairs(), want)
     assert s.counters()["ncell"][0] > 6
     s.close()
+
+
+def test_long_rows_are_summed_reproducibly(env):
+    """With the 4 a0 attraction every partner row is long (tens of records),
+    so the gather sums them on its warp-wide path (mixed precision: 64-bit
+    fixed point).  The records arrive in the rows in a different order from
+    run to run; the trajectories must still be bitwise identical and the
+    forces within the mixed tolerance of the oracle."""
+    g, dss, oracle = env["g"], env["dss"], env["oracle"]
+    box = g["box"]
+    kw = _kw("both", mu=0.5, shear_rate=1.0)
+    p = dss.default_params(box, precision="mixed", **kw)
+    runs = []
+    for _ in range(2):
+        s = dss.Suspension(g["x"], g["a"], box, p, ids=g["ids"])
+        s.step(15)
+        st = s.state()
+        runs.append((st["x"].cpu().numpy(), st["u"].cpu().numpy(), st["w"].cpu().numpy(), s.stress()))
+        assert s.counters()["max_row"] > 8
+        s.close()
+    for a, b in zip(*runs):
+        np.testing.assert_array_equal(a, b)
