@@ -73,38 +73,53 @@ __device__ __forceinline__ void enum_init(EnumCtx& e, const Geo& g, const InstGe
   e.i = i;
 }
 
-// Visits the candidates [jb, je) of one stencil cell (origin displaced by
-// (cxo, cyo, czo) from the owner's cell) and appends the pairs in order.
-// FP32 decision on cell-local coordinates: certainly a pair, certainly not,
-// or (within the margin of the cutoff, or past half the box) the exact FP64
-// predicate.
+// One candidate j of owner i (positions relative to the candidate cell's
+// origin): FP32 decision on cell-local coordinates, certainly a pair,
+// certainly not, or (within the margin of the cutoff, or past half the box)
+// the exact FP64 predicate; a pair is appended to the row.
 template <bool ECH>
+__device__ __forceinline__ void take_candidate(EnumCtx& e, float4 pj, int j, float px, float py, float pz) {
+  const float dx = pj.x - px, dy = pj.y - py, dz = pj.z - pz;
+  int dec;
+  if (e.img && (fabsf(dx) > e.hx || fabsf(dy) > e.hy || fabsf(dz) > e.hz)) {
+    dec = -1;
+  } else {
+    float sv = fmaf(pj.w, e.sc, e.sa);
+    if (ECH) sv = fmaxf(sv, pj.w + e.sa2);
+    const float t = fmaf(-sv, sv, fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
+    dec = t < -e.m2 ? 1 : (t > e.m2 ? 0 : -1);
+  }
+  if (dec < 0) {
+    ++e.band;
+    const StateBuf& s = *e.s;
+    const int n = e.g->n, i = e.i;
+    dec = exact_is_pair(*e.g, *e.I, e.off, s.x[i], s.x[n + i], s.x[2 * n + i], s.a[i], s.x[j],
+                        s.x[n + j], s.x[2 * n + j], s.a[j]) ? 1 : 0;
+  }
+  if (dec) {
+    if (e.cnt < e.M) e.row[e.cnt] = j;
+    ++e.cnt;
+  }
+}
+
+// Visits the candidates [jb, je) of one stencil cell (origin displaced by
+// (cxo, cyo, czo) from the owner's cell) in order.  UNR > 1 loads UNR positions before
+// testing them (more loads in flight; pays when cells hold many particles),
+// with the same decisions in the same order, so the rows are identical.
+template <bool ECH, int UNR>
 __device__ __forceinline__ void scan_range(EnumCtx& e, int jb, int je, float cxo, float cyo, float czo) {
   const float px = e.pi.x - cxo, py = e.pi.y - cyo, pz = e.pi.z - czo;
-  for (int j = jb; j < je; ++j) {
-    const float4 pj = __ldg(e.posf + j);
-    const float dx = pj.x - px, dy = pj.y - py, dz = pj.z - pz;
-    int dec;
-    if (e.img && (fabsf(dx) > e.hx || fabsf(dy) > e.hy || fabsf(dz) > e.hz)) {
-      dec = -1;
-    } else {
-      float sv = fmaf(pj.w, e.sc, e.sa);
-      if (ECH) sv = fmaxf(sv, pj.w + e.sa2);
-      const float t = fmaf(-sv, sv, fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
-      dec = t < -e.m2 ? 1 : (t > e.m2 ? 0 : -1);
-    }
-    if (dec < 0) {
-      ++e.band;
-      const StateBuf& s = *e.s;
-      const int n = e.g->n, i = e.i;
-      dec = exact_is_pair(*e.g, *e.I, e.off, s.x[i], s.x[n + i], s.x[2 * n + i], s.a[i], s.x[j],
-                          s.x[n + j], s.x[2 * n + j], s.a[j]) ? 1 : 0;
-    }
-    if (dec) {
-      if (e.cnt < e.M) e.row[e.cnt] = j;
-      ++e.cnt;
+  int j = jb;
+  if (UNR > 1) {
+    for (; j + UNR <= je; j += UNR) {
+      float4 q[UNR];
+#pragma unroll
+      for (int t = 0; t < UNR; ++t) q[t] = __ldg(e.posf + j + t);
+#pragma unroll
+      for (int t = 0; t < UNR; ++t) take_candidate<ECH>(e, q[t], j + t, px, py, pz);
     }
   }
+  for (; j < je; ++j) take_candidate<ECH>(e, __ldg(e.posf + j), j, px, py, pz);
 }
 
 // Row lengths, counters and the fused exclusive scan of the row lengths:
@@ -144,7 +159,7 @@ __device__ __forceinline__ void finish_rows(const Geo& g, const StateBuf& s, Lis
   if (lane == 0 && (wtile + 1) * 32 >= n) L.start[n] = prefix + agg;
 }
 
-template <bool ECH>
+template <bool ECH, int UNR>
 __global__ void __launch_bounds__(kThreads, 8)
 k_enumerate(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ sgk, StateBuf s,
             const float4* __restrict__ posf, const int* __restrict__ cellid,
@@ -172,17 +187,17 @@ k_enumerate(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ s
     const int c = cellid[i] - cb;
     const int cx = c % nx, cy = (c / nx) % ny, cz = c / (nx * ny);
     // own cell (partners after i) and the cell x+1
-    scan_range<ECH>(e, i + 1, cell_start[cb + c + 1], 0.f, 0.f, 0.f);
+    scan_range<ECH, UNR>(e, i + 1, cell_start[cb + c + 1], 0.f, 0.f, 0.f);
     {
       const int q = cb + (cz * ny + cy) * nx + wrapi(cx + 1, nx);
-      scan_range<ECH>(e, cell_start[q], cell_start[q + 1], I.csf[0], 0.f, 0.f);
+      scan_range<ECH, UNR>(e, cell_start[q], cell_start[q + 1], I.csf[0], 0.f, 0.f);
     }
     // layer y, z+1: three x cells
     {
       const int qz = wrapi(cz + 1, nz);
       for (int ox = -1; ox <= 1; ++ox) {
         const int q = cb + (qz * ny + cy) * nx + wrapi(cx + ox, nx);
-        scan_range<ECH>(e, cell_start[q], cell_start[q + 1], (float)ox * I.csf[0], 0.f, I.csf[2]);
+        scan_range<ECH, UNR>(e, cell_start[q], cell_start[q + 1], (float)ox * I.csf[0], 0.f, I.csf[2]);
       }
     }
     // layer y+1: 3x3 cells, or across y = L_y the 4 x cells covering the
@@ -196,7 +211,7 @@ k_enumerate(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ s
         const int q = cb + (qz * ny + qy) * nx + wrapi(cx + ox, nx);
         float cxo, cyo, czo;
         stencil_shift(I, ox, 1, oz, le ? 1 : 0, fsh, offr, cxo, cyo, czo);
-        scan_range<ECH>(e, cell_start[q], cell_start[q + 1], cxo, cyo, czo);
+        scan_range<ECH, UNR>(e, cell_start[q], cell_start[q + 1], cxo, cyo, czo);
       }
     }
   }
@@ -241,7 +256,7 @@ k_enumerate_classes(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __rest
     const int c = (cellid[i] - I.cell_base) % layer;
     const int cx = c % nx, cy = (c / nx) % ny, cz = c / (nx * ny);
     // own bin, partners after i
-    scan_range<ECH>(e, i + 1, cell_start[cellid[i] + 1], 0.f, 0.f, 0.f);
+    scan_range<ECH, 1>(e, i + 1, cell_start[cellid[i] + 1], 0.f, 0.f, 0.f);
     for (int c2 = cls; c2 >= 0; --c2) {
       const int R = g.rtab[cls][c2];
       const bool half = c2 == cls;
@@ -287,7 +302,7 @@ k_enumerate_classes(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __rest
                   } while (j >= kend);
                   stencil_shift(I, ox + k, oy, oz, le, fsh, offr, cxo, cyo, czo);
                 }
-                scan_range<ECH>(e, j, j + 1, cxo, cyo, czo);
+                scan_range<ECH, 1>(e, j, j + 1, cxo, cyo, czo);
               }
             }
             ox += m;
@@ -311,7 +326,11 @@ void launch_enumerate(dss_handle* h, int stbuf, int dst_list, int adv) {
   // by a maximum, which only that case needs in the candidate test
   const bool ech = h->g.de > 0.0 && h->g.mode == 0;
   auto kc = ech ? k_enumerate_classes<true> : k_enumerate_classes<false>;
-  auto k1 = ech ? k_enumerate<true> : k_enumerate<false>;
+  // cells holding many particles (long ranges, large radius ratios) take
+  // the candidate loop with four loads in flight
+  const bool crowded = h->n >= 8 * (int64_t)h->g.ncell;
+  auto k1 = ech ? (crowded ? k_enumerate<true, 4> : k_enumerate<true, 1>)
+                : (crowded ? k_enumerate<false, 4> : k_enumerate<false, 1>);
   if (h->g.nclass > 1)
     kc<<<enum_tiles_for(n), kThreads, 0, h->stream>>>(
         h->g, h->ig, h->sg, h->st[stbuf], h->posf, h->cellid, h->cell_start, L, h->bw_count,
