@@ -299,6 +299,10 @@ def mode_wavy(dss, g, spec, args, flush, stream):
         "YW_rolling_mixed": (dict(base, k_r=0.05 * spec.kn), "mixed"),
         "YW_rolling_fp64": (dict(base, k_r=0.05 * spec.kn), "fp64"),
         "YW_mixed_size_classes": (dict(base, cell_mode=1), "mixed"),
+        # the same packing with lubrication and contact only (the paper's
+        # timing workload shape without the electro-chemical forces)
+        "context_no_echem_fp64": (dict(base, wave_amp=0.0, wave_n=0, f_er=0.0, hamaker=0.0), "fp64"),
+        "context_no_echem_mixed": (dict(base, wave_amp=0.0, wave_n=0, f_er=0.0, hamaker=0.0), "mixed"),
     }
     out = {"config": {"workload": spec.name, "n": n, "a2_a1": spec.a_large / spec.a_small,
                       "l2": "flushed before every timed step"}}
