@@ -327,53 +327,53 @@ __device__ __forceinline__ PairRes<float> pair_eval_mixed(const Geo& g, const In
     }
     Fc = Fc + m * nn;
   }
-  // ---- lubrication, App. A (FP32)
-  const float iS = __fdividef(1.0f, S), iS2 = iS * iS, iS3 = iS2 * iS;
-  float ds = 2.0f * d * iS;
-  ds = ds > 0.0f ? ds : 0.0f;
-  const float dd = ds + g.f.eps;
-  const float X = __fdividef(1.0f, dd);
-  const float Y = -__logf(dd);
-  const float A = Ai, B = Bj, AB = A * B;
-  const float xa = X * 2.0f * AB * AB * iS3;
-  const float ya = Y * (4.0f / 15.0f) * AB * (2.0f * A * A + AB + 2.0f * B * B) * iS3;
-  const float ybi = -Y * (2.0f / 15.0f) * A * AB * (4.0f * A + B) * iS2;
-  const float ybj = -Y * (2.0f / 15.0f) * AB * B * (A + 4.0f * B) * iS2;
-  const float yci = Y * (8.0f / 15.0f) * A * A * AB * iS;
-  const float ycj = Y * (8.0f / 15.0f) * AB * B * B * iS;
-  const float ycx = Y * (2.0f / 15.0f) * AB * AB * iS;
-  const float xg = X * 2.0f * AB * AB * iS2;
-  const float yg = Y * (1.0f / 15.0f) * AB * (4.0f - 6.0f * AB * iS2);
-  const float yhi = Y * iS2 * ((2.0f / 15.0f) * A * A * AB * (2.0f * A - B) + (1.0f / 15.0f) * AB * AB * (7.0f * A + B));
-  const float yhj = Y * iS2 * ((1.0f / 15.0f) * AB * AB * (A + 7.0f * B) + (2.0f / 15.0f) * AB * B * B * (2.0f * B - A));
-  const F3 dV = Vi - Vj;
-  const float nV = dotf(nn, dV);
-  const F3 fr = (xa * nV) * nn + ya * tangf(nn, dV) + ybi * crossf(nn, Wi) + ybj * crossf(nn, Wj);
-  // strain of the shear rate acting on the pair (the wave of Eq. 17: the
-  // mean of the two centres' local rates)
-  const float rate = (EXT && g.wave) ? gd + 0.5f * (vi4.w + vj4.w) : gd;
-  const F3 twoEn = f3(rate * nn.y, rate * nn.x, 0.0f);
-  const float Pn = rate * nn.x * nn.y;
-  const F3 Qn = twoEn - (2.0f * Pn) * nn;
-  const F3 nperp = crossf(nn, twoEn);
-  F3 Fl = k6 * (((xg * Pn) * nn + yg * Qn) - fr);
-  const F3 ndV = crossf(nn, dV);
-  F3 Tli = k6 * (ybi * ndV - (yci * tangf(nn, Wi) + ycx * tangf(nn, Wj)) + yhi * nperp);
-  F3 Tlj = k6 * (ybj * ndV - (ycx * tangf(nn, Wi) + ycj * tangf(nn, Wj)) + yhj * nperp);
-  if (!lub_on) {
-    Fl = f3(0.0f, 0.0f, 0.0f);
-    Tli = Fl;
-    Tlj = Fl;
-  }
-  if (g.f.taper > 0.0f) {
-    // differentiable cutoff: smoothstep over the last fraction w of the range
-    const float dl = g.mode == 1 ? g.f.delta_a0 : g.f.delta * 0.5f * S;
-    const float t = (dl - d) / (g.f.taper * dl);
-    if (t < 1.0f) {
-      const float s = t > 0.0f ? t * t * (3.0f - 2.0f * t) : 0.0f;
-      Fl = s * Fl;
-      Tli = s * Tli;
-      Tlj = s * Tlj;
+  // ---- lubrication, App. A (FP32), for the pairs within its range (every
+  // listed pair unless electro-chemical forces widen the list; a warp whose
+  // pairs are all beyond it skips the block)
+  F3 Fl = f3(0.0f, 0.0f, 0.0f), Tli = Fl, Tlj = Fl;
+  if (lub_on) {
+    const float iS = __fdividef(1.0f, S), iS2 = iS * iS, iS3 = iS2 * iS;
+    float ds = 2.0f * d * iS;
+    ds = ds > 0.0f ? ds : 0.0f;
+    const float dd = ds + g.f.eps;
+    const float X = __fdividef(1.0f, dd);
+    const float Y = -__logf(dd);
+    const float A = Ai, B = Bj, AB = A * B;
+    const float xa = X * 2.0f * AB * AB * iS3;
+    const float ya = Y * (4.0f / 15.0f) * AB * (2.0f * A * A + AB + 2.0f * B * B) * iS3;
+    const float ybi = -Y * (2.0f / 15.0f) * A * AB * (4.0f * A + B) * iS2;
+    const float ybj = -Y * (2.0f / 15.0f) * AB * B * (A + 4.0f * B) * iS2;
+    const float yci = Y * (8.0f / 15.0f) * A * A * AB * iS;
+    const float ycj = Y * (8.0f / 15.0f) * AB * B * B * iS;
+    const float ycx = Y * (2.0f / 15.0f) * AB * AB * iS;
+    const float xg = X * 2.0f * AB * AB * iS2;
+    const float yg = Y * (1.0f / 15.0f) * AB * (4.0f - 6.0f * AB * iS2);
+    const float yhi = Y * iS2 * ((2.0f / 15.0f) * A * A * AB * (2.0f * A - B) + (1.0f / 15.0f) * AB * AB * (7.0f * A + B));
+    const float yhj = Y * iS2 * ((1.0f / 15.0f) * AB * AB * (A + 7.0f * B) + (2.0f / 15.0f) * AB * B * B * (2.0f * B - A));
+    const F3 dV = Vi - Vj;
+    const float nV = dotf(nn, dV);
+    const F3 fr = (xa * nV) * nn + ya * tangf(nn, dV) + ybi * crossf(nn, Wi) + ybj * crossf(nn, Wj);
+    // strain of the shear rate acting on the pair (the wave of Eq. 17: the
+    // mean of the two centres' local rates)
+    const float rate = (EXT && g.wave) ? gd + 0.5f * (vi4.w + vj4.w) : gd;
+    const F3 twoEn = f3(rate * nn.y, rate * nn.x, 0.0f);
+    const float Pn = rate * nn.x * nn.y;
+    const F3 Qn = twoEn - (2.0f * Pn) * nn;
+    const F3 nperp = crossf(nn, twoEn);
+    Fl = k6 * (((xg * Pn) * nn + yg * Qn) - fr);
+    const F3 ndV = crossf(nn, dV);
+    Tli = k6 * (ybi * ndV - (yci * tangf(nn, Wi) + ycx * tangf(nn, Wj)) + yhi * nperp);
+    Tlj = k6 * (ybj * ndV - (ycx * tangf(nn, Wi) + ycj * tangf(nn, Wj)) + yhj * nperp);
+    if (g.f.taper > 0.0f) {
+      // differentiable cutoff: smoothstep over the last fraction w of the range
+      const float dl = g.mode == 1 ? g.f.delta_a0 : g.f.delta * 0.5f * S;
+      const float t = (dl - d) / (g.f.taper * dl);
+      if (t < 1.0f) {
+        const float s = t > 0.0f ? t * t * (3.0f - 2.0f * t) : 0.0f;
+        Fl = s * Fl;
+        Tli = s * Tli;
+        Tlj = s * Tlj;
+      }
     }
   }
   const F3 F = Fc + Fl;

@@ -23,10 +23,12 @@ struct EnumCtx {
   float sc, sa;     // cutoff of pair (i, j): s = a_j sc + sa (a_i + a_j + delta)
   float sa2;        // with electro-chemical forces the cutoff is max(s, a_j + sa2)
   float m2;         // r^2 margin of the FP32 decision
+  float lc, la;     // lubrication cutoff of pair (i, j): a_j lc + la (row order only)
   float hx, hy, hz; // half box: a separation beyond it is decided exactly
   bool img;         // the stencil reaches past half the box along some axis
   int M;
   int cnt;
+  int nnear;        // SPLIT rows: pairs within the lubrication range, at the row's front
   int band;
   int* row;
   // exact FP64 decision
@@ -54,6 +56,14 @@ __device__ __forceinline__ void enum_init(EnumCtx& e, const Geo& g, const InstGe
   }
   // the electro-chemical range (a surface distance): a_i + a_j + de
   e.sa2 = e.pi.w + (float)g.de;
+  if (g.mode == 1) {
+    e.lc = 1.0f;
+    e.la = e.pi.w + (float)(g.delta * g.a0);
+  } else {
+    e.lc = 1.0f + 0.5f * (float)g.delta;
+    e.la = e.pi.w * e.lc;
+  }
+  e.nnear = 0;
   e.m2 = I.r2_margin;
   e.hx = I.halfLf[0];
   e.hy = I.halfLf[1];
@@ -76,8 +86,12 @@ __device__ __forceinline__ void enum_init(EnumCtx& e, const Geo& g, const InstGe
 // One candidate j of owner i (positions relative to the candidate cell's
 // origin): FP32 decision on cell-local coordinates, certainly a pair,
 // certainly not, or (within the margin of the cutoff, or past half the box)
-// the exact FP64 predicate; a pair is appended to the row.
-template <bool ECH>
+// the exact FP64 predicate; a pair is appended to the row.  SPLIT (pairs
+// listed beyond the lubrication range, i.e. with electro-chemical forces):
+// pairs within the lubrication range by an FP32 test go to the row's front
+// in visiting order, the others to its back from the end; the row is closed
+// up afterwards (close_row).  Only the order within the row changes.
+template <bool ECH, bool SPLIT>
 __device__ __forceinline__ void take_candidate(EnumCtx& e, float4 pj, int j, float px, float py, float pz) {
   const float dx = pj.x - px, dy = pj.y - py, dz = pj.z - pz;
   int dec;
@@ -97,16 +111,35 @@ __device__ __forceinline__ void take_candidate(EnumCtx& e, float4 pj, int j, flo
                         s.x[n + j], s.x[2 * n + j], s.a[j]) ? 1 : 0;
   }
   if (dec) {
-    if (e.cnt < e.M) e.row[e.cnt] = j;
+    if (SPLIT) {
+      const float sl = fmaf(pj.w, e.lc, e.la);
+      const bool near = fmaf(dz, dz, fmaf(dy, dy, dx * dx)) < sl * sl;
+      if (e.cnt < e.M) e.row[near ? e.nnear : e.M - 1 - (e.cnt - e.nnear)] = j;
+      e.nnear += near;
+    } else {
+      if (e.cnt < e.M) e.row[e.cnt] = j;
+    }
     ++e.cnt;
   }
+}
+
+// SPLIT rows: the far block [M - nf, M) moves down to follow the near block
+// (ascending, each entry read before any write reaches it: the source index
+// exceeds the destination by the gap).  Overflowing rows are left as they
+// are (the step is not committed).
+__device__ __forceinline__ void close_row(EnumCtx& e) {
+  if (e.cnt > e.M) return;
+  const int nf = e.cnt - e.nnear;
+  const int gap = e.M - e.cnt;
+  if (nf > 0 && gap > 0)
+    for (int k = 0; k < nf; ++k) e.row[e.nnear + k] = e.row[e.nnear + gap + k];
 }
 
 // Visits the candidates [jb, je) of one stencil cell (origin displaced by
 // (cxo, cyo, czo) from the owner's cell) in order.  UNR > 1 loads UNR positions before
 // testing them (more loads in flight; pays when cells hold many particles),
 // with the same decisions in the same order, so the rows are identical.
-template <bool ECH, int UNR>
+template <bool ECH, int UNR, bool SPLIT = false>
 __device__ __forceinline__ void scan_range(EnumCtx& e, int jb, int je, float cxo, float cyo, float czo) {
   const float px = e.pi.x - cxo, py = e.pi.y - cyo, pz = e.pi.z - czo;
   int j = jb;
@@ -116,10 +149,10 @@ __device__ __forceinline__ void scan_range(EnumCtx& e, int jb, int je, float cxo
 #pragma unroll
       for (int t = 0; t < UNR; ++t) q[t] = __ldg(e.posf + j + t);
 #pragma unroll
-      for (int t = 0; t < UNR; ++t) take_candidate<ECH>(e, q[t], j + t, px, py, pz);
+      for (int t = 0; t < UNR; ++t) take_candidate<ECH, SPLIT>(e, q[t], j + t, px, py, pz);
     }
   }
-  for (; j < je; ++j) take_candidate<ECH>(e, __ldg(e.posf + j), j, px, py, pz);
+  for (; j < je; ++j) take_candidate<ECH, SPLIT>(e, __ldg(e.posf + j), j, px, py, pz);
 }
 
 // Row lengths, counters and the fused exclusive scan of the row lengths:
@@ -159,7 +192,7 @@ __device__ __forceinline__ void finish_rows(const Geo& g, const StateBuf& s, Lis
   if (lane == 0 && (wtile + 1) * 32 >= n) L.start[n] = prefix + agg;
 }
 
-template <bool ECH, int UNR>
+template <bool ECH, int UNR, bool SPLIT>
 __global__ void __launch_bounds__(kThreads, 8)
 k_enumerate(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ sgk, StateBuf s,
             const float4* __restrict__ posf, const int* __restrict__ cellid,
@@ -187,17 +220,17 @@ k_enumerate(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ s
     const int c = cellid[i] - cb;
     const int cx = c % nx, cy = (c / nx) % ny, cz = c / (nx * ny);
     // own cell (partners after i) and the cell x+1
-    scan_range<ECH, UNR>(e, i + 1, cell_start[cb + c + 1], 0.f, 0.f, 0.f);
+    scan_range<ECH, UNR, SPLIT>(e, i + 1, cell_start[cb + c + 1], 0.f, 0.f, 0.f);
     {
       const int q = cb + (cz * ny + cy) * nx + wrapi(cx + 1, nx);
-      scan_range<ECH, UNR>(e, cell_start[q], cell_start[q + 1], I.csf[0], 0.f, 0.f);
+      scan_range<ECH, UNR, SPLIT>(e, cell_start[q], cell_start[q + 1], I.csf[0], 0.f, 0.f);
     }
     // layer y, z+1: three x cells
     {
       const int qz = wrapi(cz + 1, nz);
       for (int ox = -1; ox <= 1; ++ox) {
         const int q = cb + (qz * ny + cy) * nx + wrapi(cx + ox, nx);
-        scan_range<ECH, UNR>(e, cell_start[q], cell_start[q + 1], (float)ox * I.csf[0], 0.f, I.csf[2]);
+        scan_range<ECH, UNR, SPLIT>(e, cell_start[q], cell_start[q + 1], (float)ox * I.csf[0], 0.f, I.csf[2]);
       }
     }
     // layer y+1: 3x3 cells, or across y = L_y the 4 x cells covering the
@@ -211,10 +244,11 @@ k_enumerate(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ s
         const int q = cb + (qz * ny + qy) * nx + wrapi(cx + ox, nx);
         float cxo, cyo, czo;
         stencil_shift(I, ox, 1, oz, le ? 1 : 0, fsh, offr, cxo, cyo, czo);
-        scan_range<ECH, UNR>(e, cell_start[q], cell_start[q + 1], cxo, cyo, czo);
+        scan_range<ECH, UNR, SPLIT>(e, cell_start[q], cell_start[q + 1], cxo, cyo, czo);
       }
     }
   }
+  if (SPLIT && i < n) close_row(e);
   finish_rows(g, s, L, bw_count, scan_status, st, e, i, tile * (kThreads / 32) + (threadIdx.x >> 5));
 }
 
@@ -329,8 +363,14 @@ void launch_enumerate(dss_handle* h, int stbuf, int dst_list, int adv) {
   // cells holding many particles (long ranges, large radius ratios) take
   // the candidate loop with four loads in flight
   const bool crowded = h->n >= 8 * (int64_t)h->g.ncell;
-  auto k1 = ech ? (crowded ? k_enumerate<true, 4> : k_enumerate<true, 1>)
-                : (crowded ? k_enumerate<false, 4> : k_enumerate<false, 1>);
+  // with electro-chemical forces over crowded cells (long ranges) most
+  // listed pairs lie beyond the lubrication range: rows put the others
+  // first, so that the pair kernel's warps meet runs of pairs without
+  // lubrication (short rows gain less than the reordering costs)
+  const bool split = h->g.de > 0.0 && crowded;
+  auto k1 = ech ? (split ? k_enumerate<true, 4, true> : k_enumerate<true, 1, false>)
+                : split ? k_enumerate<false, 4, true>
+                        : (crowded ? k_enumerate<false, 4, false> : k_enumerate<false, 1, false>);
   if (h->g.nclass > 1)
     kc<<<enum_tiles_for(n), kThreads, 0, h->stream>>>(
         h->g, h->ig, h->sg, h->st[stbuf], h->posf, h->cellid, h->cell_start, L, h->bw_count,

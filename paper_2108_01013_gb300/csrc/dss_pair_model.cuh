@@ -294,55 +294,54 @@ __device__ __forceinline__ PairModelOut<T> pair_model(const Geo& g, const InstGe
     const double sl = __dadd_rn(__dadd_rn(ai, aj), dl);
     lub_on = r2 < __dmul_rn(sl, sl);
   }
-  // ---- lubrication, App. A
-  T ds = 2.0 * d / S;
-  // the clamp's branch: overlapping pairs only (a pair exactly touching keeps
-  // the gap's derivative, the branch its values share with d > 0)
-  if (!(val(ds) >= 0.0)) ds = zero;
-  const T dd = ds + g.eps;
-  const T X = 1.0 / dd;
-  const T Y = -log(dd);
-  const double A = ai, B = aj, AB = A * B;
-  const double iS = 1.0 / S, iS2 = iS * iS, iS3 = iS2 * iS;
-  const T xa = X * (2.0 * AB * AB * iS3);
-  const T ya = Y * ((4.0 / 15.0) * AB * (2.0 * A * A + AB + 2.0 * B * B) * iS3);
-  const T ybi = -Y * ((2.0 / 15.0) * A * AB * (4.0 * A + B) * iS2);
-  const T ybj = -Y * ((2.0 / 15.0) * AB * B * (A + 4.0 * B) * iS2);
-  const T yci = Y * ((8.0 / 15.0) * A * A * AB * iS);
-  const T ycj = Y * ((8.0 / 15.0) * AB * B * B * iS);
-  const T ycx = Y * ((2.0 / 15.0) * AB * AB * iS);
-  const T xg = X * (2.0 * AB * AB * iS2);
-  const T yg = Y * ((1.0 / 15.0) * AB * (4.0 - 6.0 * AB * iS2));
-  const T yhi = Y * (iS2 * ((2.0 / 15.0) * A * A * AB * (2.0 * A - B) + (1.0 / 15.0) * AB * AB * (7.0 * A + B)));
-  const T yhj = Y * (iS2 * ((1.0 / 15.0) * AB * AB * (A + 7.0 * B) + (2.0 / 15.0) * AB * B * B * (2.0 * B - A)));
-  const Vec3<T> dV = Vi - Vj;
-  const T nV = dot(n, dV);
-  const Vec3<T> fr = (xa * nV) * n + ya * tang(n, dV) + ybi * cross(n, Wi) + ybj * cross(n, Wj);
-  // shear along x of rate `rate`: 2 E n = rate (n_y, n_x, 0), P = rate n_x n_y,
-  // Q.n = 2 E n - 2 P n
-  const Vec3<T> twoEn = mk3<T>(rate * n.y, rate * n.x, zero);
-  const T P = rate * n.x * n.y;
-  const Vec3<T> Qn = twoEn - (2.0 * P) * n;
-  const Vec3<T> nperp = cross(n, twoEn);
-  const Vec3<T> fe = (xg * P) * n + yg * Qn;
-  Vec3<T> Fl = g.k6 * (fe - fr);
-  const Vec3<T> ndV = cross(n, dV);
-  Vec3<T> Tli = g.k6 * (ybi * ndV - (yci * tang(n, Wi) + ycx * tang(n, Wj)) + yhi * nperp);
-  Vec3<T> Tlj = g.k6 * (ybj * ndV - (ycx * tang(n, Wi) + ycj * tang(n, Wj)) + yhj * nperp);
-  if (g.taper > 0.0) {
-    const T dl = g.mode == 1 ? q.delta * g.a0 : q.delta * (0.5 * S);
-    const T t = (dl - d) / (g.taper * dl);
-    if (val(t) < 1.0) {
-      const T s = val(t) > 0.0 ? t * t * (3.0 - 2.0 * t) : zero;
-      Fl = s * Fl;
-      Tli = s * Tli;
-      Tlj = s * Tlj;
+  // ---- lubrication, App. A, for the pairs within its range (every listed
+  // pair unless electro-chemical forces widen the list)
+  Vec3<T> Fl = mk3<T>(zero, zero, zero), Tli = Fl, Tlj = Fl;
+  if (lub_on) {
+    T ds = 2.0 * d / S;
+    // the clamp's branch: overlapping pairs only (a pair exactly touching keeps
+    // the gap's derivative, the branch its values share with d > 0)
+    if (!(val(ds) >= 0.0)) ds = zero;
+    const T dd = ds + g.eps;
+    const T X = 1.0 / dd;
+    const T Y = -log(dd);
+    const double A = ai, B = aj, AB = A * B;
+    const double iS = 1.0 / S, iS2 = iS * iS, iS3 = iS2 * iS;
+    const T xa = X * (2.0 * AB * AB * iS3);
+    const T ya = Y * ((4.0 / 15.0) * AB * (2.0 * A * A + AB + 2.0 * B * B) * iS3);
+    const T ybi = -Y * ((2.0 / 15.0) * A * AB * (4.0 * A + B) * iS2);
+    const T ybj = -Y * ((2.0 / 15.0) * AB * B * (A + 4.0 * B) * iS2);
+    const T yci = Y * ((8.0 / 15.0) * A * A * AB * iS);
+    const T ycj = Y * ((8.0 / 15.0) * AB * B * B * iS);
+    const T ycx = Y * ((2.0 / 15.0) * AB * AB * iS);
+    const T xg = X * (2.0 * AB * AB * iS2);
+    const T yg = Y * ((1.0 / 15.0) * AB * (4.0 - 6.0 * AB * iS2));
+    const T yhi = Y * (iS2 * ((2.0 / 15.0) * A * A * AB * (2.0 * A - B) + (1.0 / 15.0) * AB * AB * (7.0 * A + B)));
+    const T yhj = Y * (iS2 * ((1.0 / 15.0) * AB * AB * (A + 7.0 * B) + (2.0 / 15.0) * AB * B * B * (2.0 * B - A)));
+    const Vec3<T> dV = Vi - Vj;
+    const T nV = dot(n, dV);
+    const Vec3<T> fr = (xa * nV) * n + ya * tang(n, dV) + ybi * cross(n, Wi) + ybj * cross(n, Wj);
+    // shear along x of rate `rate`: 2 E n = rate (n_y, n_x, 0), P = rate n_x n_y,
+    // Q.n = 2 E n - 2 P n
+    const Vec3<T> twoEn = mk3<T>(rate * n.y, rate * n.x, zero);
+    const T P = rate * n.x * n.y;
+    const Vec3<T> Qn = twoEn - (2.0 * P) * n;
+    const Vec3<T> nperp = cross(n, twoEn);
+    const Vec3<T> fe = (xg * P) * n + yg * Qn;
+    Fl = g.k6 * (fe - fr);
+    const Vec3<T> ndV = cross(n, dV);
+    Tli = g.k6 * (ybi * ndV - (yci * tang(n, Wi) + ycx * tang(n, Wj)) + yhi * nperp);
+    Tlj = g.k6 * (ybj * ndV - (ycx * tang(n, Wi) + ycj * tang(n, Wj)) + yhj * nperp);
+    if (g.taper > 0.0) {
+      const T dl = g.mode == 1 ? q.delta * g.a0 : q.delta * (0.5 * S);
+      const T t = (dl - d) / (g.taper * dl);
+      if (val(t) < 1.0) {
+        const T s = val(t) > 0.0 ? t * t * (3.0 - 2.0 * t) : zero;
+        Fl = s * Fl;
+        Tli = s * Tli;
+        Tlj = s * Tlj;
+      }
     }
-  }
-  if (!lub_on) {
-    Fl = mk3<T>(zero, zero, zero);
-    Tli = Fl;
-    Tlj = Fl;
   }
   o.Fl = Fl;
   o.F = o.Fc + Fl;
