@@ -200,6 +200,41 @@ def cpu_baseline(g, params_kw, seconds: float, nstep: int = 0):
                       "thread) in %.1f s; full-step rate = 2 m / t" % (m, n, dt)}
 
 
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """Largest value of x over the ranks (x itself on one rank); device is
+    where the reduction's tensor lives (a GPU under NCCL, the CPU under gloo)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units: float, seconds: float, world: int, device=None) -> float:
+    """Whole-job rate of N independent replicas (weak scaling): the units all
+    ranks processed (each rank the same count) over the slowest rank's time."""
+    return world * units / max_over_ranks(seconds, world, device)
+
+
+def reduce_modes(extra: dict, world: int, device=None) -> None:
+    """Every measured mode (an entry, or an entry of a mode's sub-table,
+    carrying ms_per_step and value) becomes a whole-job figure: the slowest
+    rank's ms per step and the rate of all ranks over it.  Every rank walks
+    the same modes in the same order, so the reductions pair up."""
+    if world <= 1:
+        return
+    for m in extra.values():
+        if not isinstance(m, dict):
+            continue
+        subs = [m] if "ms_per_step" in m else [v for v in m.values() if isinstance(v, dict) and "ms_per_step" in v]
+        for e in subs:
+            slowest = max_over_ranks(e["ms_per_step"], world, device)
+            e["value"] = world * e["value"] * e["ms_per_step"] / slowest
+            e["ms_per_step"] = slowest
+
+
 def workload(name: str, rank: int):
     from paper_2108_01013_gb300 import synth
     spec = synth.SPECS[name]
@@ -554,11 +589,7 @@ def main():
         clk = clocks.stop()
         c = s.counters()
         step_ms = t_gpu_ms / args.steps
-        t_gpu = t_gpu_ms * 1e-3
-        if world > 1:
-            tt = torch.tensor([t_gpu], device=dev, dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t_gpu = float(tt.item())
+        t_gpu = max_over_ranks(t_gpu_ms * 1e-3, world, dev)
         value = world * n * args.steps / t_gpu
         # per-kernel shares: a separate pass with events between the kernels
         s.set_profiling(True)
@@ -582,7 +613,7 @@ def main():
             sig = s.stress()
         torch.cuda.synchronize()
         t_e2e = time.perf_counter() - t0
-        e2e_value = n * args.e2e_steps / t_e2e * world
+        e2e_value = job_rate(n * args.e2e_steps, t_e2e, world, dev)
         bytes_state = 5 * 3 * n * 8
         s.close()
         extra = {}
@@ -611,14 +642,7 @@ def main():
             sp, gp = extra_inputs.pop("adjoint")
             with torch.cuda.nvtx.range("adjoint"):
                 extra["adjoint"] = mode_adjoint(dss, gp, sp, args)
-        if world > 1:
-            for m in extra.values():
-                if "ms_per_step" not in m:
-                    continue
-                tt = torch.tensor([m["ms_per_step"]], device=dev, dtype=torch.float64)
-                dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-                m["value"] = m["value"] * m["ms_per_step"] / float(tt.item()) * world
-                m["ms_per_step"] = float(tt.item())
+        reduce_modes(extra, world, dev)
         if "fp64" in extra:
             extra["mixed_vs_fp64"] = value / extra["fp64"]["value"]
             if "batched" in extra:
