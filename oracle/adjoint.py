@@ -9,7 +9,11 @@ oracle; it is discrete and carries no derivative), the stick-and-slide
 contact of Eq. 4-5, the lubrication blocks of Eq. A2/A3 with the g functions
 of Eq. A7 (6 pi eta0 prefactor) and the optional taper of the cutoff, the
 optional electro-chemical forces of Eq. 6-7 (central, with their stresslet),
-the Stokes drag of Eq. A1, the modified velocity-Verlet step of Eq. 15 in the
+the optional wavy shear flow of Eq. 17 (velocities relative to the local
+flow, the strain of the mean local rate, the Faxen drag, local stresslets)
+and rolling resistance of App. B (a rolling stretch carried with the
+contact, torques only), the Stokes drag of Eq. A1, the modified
+velocity-Verlet step of Eq. 15 in the
 Lees-Edwards box of Eq. 16, and the bulk stress of Eq. 8.  The objective is a
 weighted sum of the stress over the steps,
 
@@ -17,7 +21,8 @@ weighted sum of the stress over the steps,
 
 so W[n-1] = e_xy / (T eta0 gdot) gives the time-averaged relative viscosity.
 Derivatives come from torch.autograd (a library primitive).  Branch decisions
-(pair set, contact, Coulomb slip, gap clamp, taper ends, box wraps) are taken
+(pair set, contact, Coulomb slips of both springs, gap clamp, taper ends,
+box wraps) are taken
 on the values and held fixed, so these are the derivatives of the branch
 taken (pathwise derivatives).
 
@@ -103,7 +108,7 @@ class Model:
 
     def __init__(self, box, a, *, eta0=1.0, rho=1.0, lub_eps=1e-3, a0=1.0, lub_cutoff_mode=0,
                  shear_rate=1.0, dt=1e-4, lub_taper=0.0, nstep0=0, f_er=0.0, lambda_d=0.05,
-                 hamaker=0.0, vdw_eps=0.01):
+                 hamaker=0.0, vdw_eps=0.01, wave_amp=0.0, wave_n=0, k_r=0.0):
         self.box = np.asarray(box, dtype=np.float64)
         self.a = np.asarray(a, dtype=np.float64)
         self.n = self.a.shape[0]
@@ -112,12 +117,26 @@ class Model:
         self.nstep0 = nstep0
         # electro-chemical forces, Eq. 6-7 (constants, not differentiated)
         self.f_er, self.lambda_d, self.hamaker, self.vdw_eps = f_er, lambda_d, hamaker, vdw_eps
+        # the wavy shear flow of Eq. 17 and the rolling spring of App. B
+        self.wave_amp, self.wave_n, self.k_r = wave_amp, int(wave_n), k_r
+        self.wk = 2.0 * math.pi * float(wave_n) / float(self.box[1])
         at = torch.as_tensor(self.a, dtype=TD)
         self.at = at
         self.mass = 4.0 / 3.0 * math.pi * rho * at ** 3
         self.inertia = 0.4 * self.mass * at ** 2
         self.k6 = 6.0 * math.pi * eta0
         self.k8 = 8.0 * math.pi * eta0
+
+    # U_inf,x, the local rate dU_inf,x/dy and the Faxen velocity of Eq. A1
+    # (1 + a^2/6 Laplacian) U_inf,x at heights y (Eq. 17)
+    def ux_inf(self, y):
+        return self.gdot * y + self.wave_amp * torch.sin(self.wk * y)
+
+    def rate(self, y):
+        return self.gdot + self.wave_amp * self.wk * torch.cos(self.wk * y)
+
+    def faxen_ux(self, y, a):
+        return self.gdot * y + self.wave_amp * (1.0 - a * a * self.wk * self.wk / 6.0) * torch.sin(self.wk * y)
 
     def offset(self, nstep):
         t = float(nstep) * self.dt
@@ -127,15 +146,17 @@ class Model:
     def forces(self, x, u, w, th, hist, nstep):
         """Forces, torques, stress and the new history at time nstep*dt.
         x, u, w: (3, n) tensors; th: dict of scalar tensors kn, kt, gn, mu,
-        delta; hist: (keys ndarray sorted, xi (k, 3) tensor) in lo -> hi
-        orientation.  Returns F, T (3, n), sigma (9,), new hist, counts."""
+        delta; hist: (keys ndarray sorted, xi (k, 3) tensor in lo -> hi
+        orientation, xr (k, 3) tensor: the rolling stretch).  Returns F, T
+        (3, n), sigma (9,), new hist, counts."""
         n, L, gd = self.n, self.box, self.gdot
         off = self.offset(nstep)
         p = make_params(L, kn=th["kn"].item(), kt=th["kt"].item(), gamma_n=th["gn"].item(),
                         mu=th["mu"].item(), eta0=self.eta0, rho=self.rho,
                         delta_lub=th["delta"].item(), lub_eps=self.eps, a0=self.a0,
                         lub_cutoff_mode=self.mode, shear_rate=gd, dt=self.dt, lub_taper=self.taper,
-                        f_er=self.f_er, lambda_d=self.lambda_d, hamaker=self.hamaker, vdw_eps=self.vdw_eps)
+                        f_er=self.f_er, lambda_d=self.lambda_d, hamaker=self.hamaker, vdw_eps=self.vdw_eps,
+                        wave_amp=self.wave_amp, wave_n=self.wave_n, k_r=self.k_r)
         xn = x.detach().numpy()
         pr = pairs_bruteforce(xn, self.a, np.arange(n, dtype=np.int32), p, off)
         i = torch.as_tensor(pr[:, 0])
@@ -166,8 +187,9 @@ class Model:
         # ---- contact, Eq. 4-5
         cmask = (d.detach() < 0.0)
         keys = (pr[:, 0].astype(np.int64) << 32) | pr[:, 1].astype(np.int64)
-        hk, hxi = hist
+        hk, hxi, hxr = hist
         xo = torch.zeros((P, 3), dtype=TD)
+        ro = torch.zeros((P, 3), dtype=TD)
         if len(hk):
             pos = np.searchsorted(hk, keys)
             pos = np.minimum(pos, len(hk) - 1)
@@ -175,6 +197,7 @@ class Model:
             if found.any():
                 idx = torch.as_tensor(np.nonzero(found)[0])
                 xo = xo.index_copy(0, idx, hxi[torch.as_tensor(pos[found])])
+                ro = ro.index_copy(0, idx, hxr[torch.as_tensor(pos[found])])
         du = ujm - ui
         un = _dot(nv, du) * nv
         Fnor = th["kn"] * d[:, None] * nv + th["gn"] * un
@@ -195,6 +218,24 @@ class Model:
         Tci = ai[:, None] * nxf * cm
         Tcj = aj[:, None] * nxf * cm
         xinew = xs * cm
+        # ---- rolling resistance, App. B: Eq. 5 on u_r = abar n x (w_i - w_j)
+        # with k_r, under the sliding contact's Coulomb limit; torques only
+        rslip = np.zeros(P, bool)
+        xrnew = torch.zeros((P, 3), dtype=TD)
+        if self.k_r > 0.0:
+            abar_r = (2.0 * ai * aj / S)[:, None]
+            xrp = ro - _dot(nv, ro) * nv
+            xrs = xrp + (abar_r * _cross(nv, wi - wj)) * self.dt
+            capr = th["mu"] * torch.sqrt((Fnor * Fnor).sum(1)) / self.k_r
+            xrm = torch.sqrt((xrs * xrs).sum(1))
+            rs = (xrm.detach() > capr.detach()) & cmask
+            rscale = torch.where(rs, capr / torch.where(rs, xrm, torch.ones_like(xrm)), torch.ones_like(xrm))
+            xrs = xrs * rscale[:, None]
+            Tr = abar_r * _cross(nv, self.k_r * xrs) * cm
+            Tci = Tci + Tr
+            Tcj = Tcj - Tr
+            xrnew = xrs * cm
+            rslip = rs.numpy()
         # ---- lubrication, App. A (block form of Eq. A2/A3)
         ds = 2.0 * d / S
         ds = torch.where(ds.detach() < 0.0, torch.zeros_like(ds), ds)
@@ -203,11 +244,15 @@ class Model:
         c = _coefficients(ai.numpy(), aj.numpy())
         XY = {"XA": X, "YA": Y, "YB": Y, "YC": Y, "XG": X, "YG": Y, "YH": Y}
         cc = {k: (XY[k[:2]] * v)[:, None] for k, v in c.items()}
-        Vi = ui - torch.stack([gd * x[1, i], torch.zeros(P, dtype=TD), torch.zeros(P, dtype=TD)], 1)
-        Vj = ujm - torch.stack([gd * yjm, torch.zeros(P, dtype=TD), torch.zeros(P, dtype=TD)], 1)
-        Om = torch.tensor([0.0, 0.0, -0.5 * gd], dtype=TD)
-        Wi = wi - Om
-        Wj = wj - Om
+        # velocities relative to the flow at each centre (Eq. 17), the
+        # strain of the mean of the two centres' local rates
+        zP = torch.zeros(P, dtype=TD)
+        Vi = ui - torch.stack([self.ux_inf(x[1, i]), zP, zP], 1)
+        Vj = ujm - torch.stack([self.ux_inf(yjm), zP, zP], 1)
+        rate_i, rate_j = self.rate(x[1, i]), self.rate(yjm)
+        Wi = wi + torch.stack([zP, zP, 0.5 * rate_i], 1)
+        Wj = wj + torch.stack([zP, zP, 0.5 * rate_j], 1)
+        gp = (0.5 * (rate_i + rate_j))[:, None]
 
         def N(v):
             return _dot(nv, v) * nv
@@ -219,12 +264,12 @@ class Model:
         nxVi, nxVj = _cross(nv, Vi), _cross(nv, Vj)
         E = torch.zeros((3, 3), dtype=TD)
         E[0, 1] = E[1, 0] = 0.5 * gd
-        En = nv @ E.T
-        EnT = nv @ E
+        # E_inf of the pair: E_xy = E_yx = gp/2 (traceless, symmetric)
+        En = 0.5 * gp * torch.stack([nv[:, 1], nv[:, 0], torch.zeros_like(nv[:, 0])], 1)
         Enn = _dot(nv, En)
-        Pq = Enn - (E[0, 0] + E[1, 1] + E[2, 2]) / 3.0
+        Pq = Enn
         Qn = 2.0 * En - 2.0 * Enn * nv
-        nperp = _cross(nv, En + EnT)
+        nperp = _cross(nv, 2.0 * En)
         fi = (cc["XA_ii"] * N(Vi) + cc["YA_ii"] * T(Vi) + cc["XA_ij"] * N(Vj) + cc["YA_ij"] * T(Vj)
               + cc["YB_ii"] * nxWi + cc["YB_ji"] * nxWj)
         fj = (cc["XA_ji"] * N(Vi) + cc["YA_ji"] * T(Vi) + cc["XA_jj"] * N(Vj) + cc["YA_jj"] * T(Vj)
@@ -273,21 +318,28 @@ class Model:
         Tj = Tcj + Tlj
         F = torch.zeros((n, 3), dtype=TD).index_add(0, i, Fi).index_add(0, j, Fj)
         Tq = torch.zeros((n, 3), dtype=TD).index_add(0, i, Ti).index_add(0, j, Tj)
-        # Stokes drag, Eq. A1
-        V = torch.stack([u[0] - gd * x[1], u[1], u[2]], 1)
+        # Stokes drag, Eq. A1 (Faxen velocity and local Omega_inf at the centre)
+        V = torch.stack([u[0] - self.faxen_ux(x[1], self.at), u[1], u[2]], 1)
         F = F - self.k6 * self.at[:, None] * V
-        Tq = Tq - self.k8 * (self.at ** 3)[:, None] * (w.T - Om)
+        zn = torch.zeros(n, dtype=TD)
+        Wp = w.T + torch.stack([zn, zn, 0.5 * self.rate(x[1])], 1)
+        Tq = Tq - self.k8 * (self.at ** 3)[:, None] * Wp
         # stress, Eq. 8 and 9
         Sp = (r[:, :, None] * Fc[:, None, :] + 0.5 * (r[:, :, None] * Fli[:, None, :]
                                                      + Fli[:, :, None] * r[:, None, :])).sum(0)
         Vol = float(L[0] * L[1] * L[2])
-        sumA3 = float((self.a ** 3).sum())
-        sigma = (2.0 * self.eta0 * E + (20.0 / 3.0 * math.pi * self.eta0 * sumA3 * E + Sp) / Vol).reshape(9)
+        # single-particle stresslets 20/3 pi eta0 a^3 E_inf(x_i); the fluid
+        # term with the box mean of E_inf
+        ein = 20.0 / 3.0 * math.pi * self.eta0 * (self.at ** 3 * 0.5 * self.rate(x[1])).sum()
+        Sein = torch.zeros((3, 3), dtype=TD)
+        Sein = Sein.index_put((torch.tensor([0, 1]), torch.tensor([1, 0])), ein.expand(2))
+        sigma = (2.0 * self.eta0 * E + (Sein + Sp) / Vol).reshape(9)
         # new history: the pairs in contact, sorted by key (ids are indices, lo = i)
         cm_np = cmask.numpy()
         nk = keys[cm_np]
         order = np.argsort(nk, kind="stable")
-        new_hist = (nk[order], xinew[torch.as_tensor(np.nonzero(cm_np)[0][order])])
+        sel = torch.as_tensor(np.nonzero(cm_np)[0][order])
+        new_hist = (nk[order], xinew[sel], xrnew[sel])
         # event signature: pair count, contact count, slip count, and the
         # identities of the contacts, slips and pairs in the taper band
         band = np.zeros(P, bool)
@@ -297,7 +349,7 @@ class Model:
         sl = slip.numpy()
         ev = (P, int(cm_np.sum()), int(sl.sum()), hash(keys[cm_np].tobytes()),
               hash(keys[sl].tobytes()), hash(keys[band].tobytes()), hash(keys.tobytes()),
-              hash(keys[lub_on].tobytes()))
+              hash(keys[lub_on].tobytes()), hash(keys[rslip].tobytes()))
         return F.T, Tq.T, sigma, new_hist, ev
 
     # -- the rollout -----------------------------------------------------------
@@ -307,11 +359,11 @@ class Model:
         Returns (J, sigma list, event counts per step, final state dict)."""
         dt, L, gd = self.dt, self.box, self.gdot
         nstep = self.nstep0
-        F, Tq, _, _, ev0 = self.forces(x0, u0, w0, th, (np.zeros(0, np.int64), None), nstep)
+        F, Tq, _, _, ev0 = self.forces(x0, u0, w0, th, (np.zeros(0, np.int64), None, None), nstep)
         al = F / self.mass
         aw = Tq / self.inertia
         x, u, w = x0, u0, w0
-        hist = (np.zeros(0, np.int64), None)
+        hist = (np.zeros(0, np.int64), None, None)
         J = torch.zeros((), dtype=TD)
         sig, events = [], [ev0]
         for k in range(nsteps):

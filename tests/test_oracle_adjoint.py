@@ -3,7 +3,8 @@ repeat oracle.c step for step, and its reverse-mode gradient must match
 central finite differences of oracle.c, with the event set (pair set,
 contacts, Coulomb slips) checked unchanged between the two sides of each
 difference.  One case adds the electro-chemical forces of Eq. 6-7 (the
-list then reaches their range and lubrication keeps its own).
+list then reaches their range and lubrication keeps its own), one the wavy
+shear flow of Eq. 17 with rolling resistance (App. B).
 """
 import numpy as np
 import pytest
@@ -16,6 +17,8 @@ from paper_2108_01013_gb300 import synth
 
 
 ECHEM = dict(f_er=30.0, lambda_d=0.05, hamaker=0.01, vdw_eps=0.05)
+WAVE_ROLL = dict(wave_amp=4.0, wave_n=1, k_r=1e3)
+EXTRA = tuple(ECHEM) + tuple(WAVE_ROLL)
 
 
 def _case(taper, echem=False):
@@ -27,7 +30,9 @@ def _case(taper, echem=False):
     u0 += 0.5 * rng.normal(size=(3, n))
     w0 = 0.5 * rng.normal(size=(3, n))
     kw = dict(shear_rate=5.0, dt=1e-4, lub_taper=taper, nstep0=3)
-    if echem:
+    if echem == "wave_roll":
+        kw.update(WAVE_ROLL)
+    elif echem:
         kw.update(ECHEM)
     th = dict(kn=1e4, kt=6e3, gamma_n=0.5, mu=0.4, delta_lub=0.2 if taper else 0.05)
     return g, u0, w0, kw, th
@@ -36,7 +41,7 @@ def _case(taper, echem=False):
 def _c_oracle(g, u0, w0, kw, th, nsteps, weights, x0=None):
     p = oracle.make_params(g["box"], kn=th["kn"], kt=th["kt"], gamma_n=th["gamma_n"], mu=th["mu"],
                            delta_lub=th["delta_lub"], shear_rate=kw["shear_rate"], dt=kw["dt"],
-                           lub_taper=kw["lub_taper"], **{k: kw[k] for k in ECHEM if k in kw})
+                           lub_taper=kw["lub_taper"], **{k: kw[k] for k in EXTRA if k in kw})
     o = oracle.System(p, g["x"] if x0 is None else x0, g["a"], u=u0, w=w0, nstep=kw["nstep0"])
     o.init_accel()
     J, sig, ev = 0.0, [], []
@@ -57,7 +62,7 @@ def _weights(nsteps, gd):
     return W
 
 
-@pytest.mark.parametrize("taper,echem", [(0.0, False), (0.3, False), (0.3, True)])
+@pytest.mark.parametrize("taper,echem", [(0.0, False), (0.3, False), (0.3, True), (0.3, "wave_roll")])
 def test_torch_rollout_repeats_c_oracle(taper, echem):
     g, u0, w0, kw, th = _case(taper, echem)
     T = 15
@@ -104,7 +109,7 @@ def _fd(g, u0, w0, kw, th, T, W, key, h, x0=None, du=None, dw=None):
     return (Jp - Jm) / (2 * h)
 
 
-@pytest.mark.parametrize("taper,echem", [(0.0, False), (0.3, False), (0.3, True)])
+@pytest.mark.parametrize("taper,echem", [(0.0, False), (0.3, False), (0.3, True), (0.3, "wave_roll")])
 def test_gradient_matches_central_differences(taper, echem):
     g, u0, w0, kw, th = _case(taper, echem)
     T = 12
