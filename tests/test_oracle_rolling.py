@@ -120,3 +120,36 @@ def test_rolling_exerts_no_force_and_ignores_co_rotation():
         # rigid co-rotation: a fresh rolling spring stays unloaded
         d = oracle.pair_eval(p1, 0.0, xi, xj, ui, uj, wi, wi, ai, aj, xo, (0, 0, 0))
         np.testing.assert_allclose(d[7], 0.0, atol=1e-15)
+
+
+def test_rolling_stretch_lives_with_the_contact():
+    """Two spheres pushed together, held, then pulled apart and back: the
+    rolling stretch appears with the contact, is dropped with it, and starts
+    again from zero (one step of u_r dt) on the next contact."""
+    L = 20.0
+    p = oracle.make_params([L] * 3, kn=1e4, mu=0.8, eta0=0.0, shear_rate=0.0, dt=1e-3, k_r=200.0)
+    a = [1.0, 1.0]
+    def run(gap, steps, xr_seed=None):
+        x = np.array([[8.0, 8.0 + 2.0 + gap], [10.0, 10.0], [10.0, 10.0]])
+        u = np.zeros((3, 2))
+        w = np.zeros((3, 2))
+        w[2] = [3.0, -1.0]
+        s = oracle.System(p, x, a, u=u, w=w)
+        s.init_accel()
+        if xr_seed is not None:
+            keys, xi = np.array([1], dtype=np.int64), np.zeros((1, 3))
+            s.set_history(keys, xi, xr_seed)
+        s.step(steps)
+        return s
+    s = run(-0.01, 5)
+    keys, xi, xr = s.get_history(rolling=True)
+    assert list(keys) == [1] and np.abs(xr).max() > 0
+    # separated pair: no entry, whatever stretch it carried before
+    s = run(+0.05, 1, xr_seed=np.array([[0.0, 0.3, 0.0]]))
+    keys, xi, xr = s.get_history(rolling=True)
+    assert len(keys) == 0
+    # a fresh contact starts from zero: one step adds abar (n x (w_i - w_j)) dt
+    s = run(-0.01, 1)
+    keys, xi, xr = s.get_history(rolling=True)
+    wrel = 4.0                                     # w_i - w_j about z, at the half step
+    assert abs(np.linalg.norm(xr[0]) - 1.0 * wrel * p.dt) < 1e-2 * wrel * p.dt
