@@ -54,12 +54,32 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 METRIC = "particle-timesteps/s"
 L2_FLUSH_BYTES = 256 << 20
 
-# Algorithmic bytes of each kernel: the minimum traffic its definition
-# needs (every input read once, every output written once).  Per particle
-# (n), per cell (c), per listed pair (p) and per contact (k); values for FP64
-# and mixed precision (FP32 records).  The derivation is in the design notes.
-ALG_BYTES = {
+# Method bytes per particle-step of the paper's path (the algorithmic
+# minimum: every input read once, every output written once), per particle
+# (n), cell (c), listed pair (p) and contact (k), FP64 / mixed:
+#   neighbour + force step: sorted state read (x, u, w, a, id: 84 n), permuted
+#   state written (84 n), F and T written (48 n / 24 n), the pair list
+#   written and read (8 p), the contact history read and written (key and
+#   stretch: 64 k), the cell table (8 c);
+#   integration (Eq. 15): 168 n read, 120 n written.
+# Each item is charged to the kernel that performs it.  The state read is
+# split between the enumeration (positions and radii, 32 n) and the pair
+# kernel (velocities, angular velocities and ids, 52 n).
+METHOD_BYTES = {
     #                  fp64 (n, c, p, k)      mixed (n, c, p, k)
+    "k_key_hist":    ((120, 0, 0, 0),       (120, 0, 0, 0)),     # predictor of x, u: 72 read, 48 written
+    "k_scan_cells":  ((0, 8, 0, 0),         (0, 8, 0, 0)),       # cell table
+    "k_scatter":     ((0, 0, 0, 0),         (0, 0, 0, 0)),
+    "k_rank_gather": ((156, 0, 0, 0),       (156, 0, 0, 0)),     # permuted state 84, w predictor 72
+    "k_enumerate":   ((32, 0, 4, 0),        (32, 0, 4, 0)),      # positions and radii, list written
+    "k_pairs":       ((100, 0, 4, 64),      (76, 0, 4, 64)),     # u, w, id; F, T; list read; history
+    "k_gather":      ((96, 0, 0, 0),        (96, 0, 0, 0)),      # corrector: u, w read and written
+}
+# Bytes of this design's own data structures per kernel (partner records,
+# 32-byte stretch records, FP32 copies of the sorted state, ...): what the
+# kernels actually move when every access hits DRAM once.  Reported beside the
+# method bytes as implementation overhead.
+IMPL_BYTES = {
     "k_key_hist":    ((133, 0, 0, 0),       (133, 0, 0, 0)),
     "k_scan_cells":  ((0, 12, 0, 0),        (0, 12, 0, 0)),
     "k_scatter":     ((16, 0, 0, 0),        (16, 0, 0, 0)),
@@ -68,6 +88,9 @@ ALG_BYTES = {
     "k_pairs":       ((148, 0, 108, 56),    (112, 0, 76, 56)),
     "k_gather":      ((216, 0, 64, 0),      (216, 0, 32, 0)),
 }
+# The neighbour + force step alone (without the integration's 288 n).
+NF_BYTES = ((216, 8, 8, 64), (192, 8, 8, 64))
+ALG_BYTES = METHOD_BYTES
 KERNELS_PER_STEP = len(ALG_BYTES)
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
@@ -108,12 +131,14 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--modes", default="fp64,echem,analysis,wavy,batched,poly1m,adjoint",
+    ap.add_argument("--modes", default="fp64,echem,analysis,wavy,batched,poly1m,adjoint,cpu",
                     help="extra modes measured in the same run: fp64 (the headline workload in "
                          "FP64), echem (the headline packing with the electro-chemical forces, "
                          "mixed), analysis (clusters, dispersion, rheology calls on it), batched (256-instance flow-curve sweep, mixed), poly1m (1M "
                          "polydisperse, mixed and FP64), adjoint (gradient of the 200-step "
-                         "viscosity of 20k spheres); 'none' for none")
+                         "viscosity of 20k spheres), cpu (the oracle on the host cores: 1000 "
+                         "brute-force steps of the 1k configuration, whole steps of the 1M "
+                         "and Table 5 packings); 'none' for none")
     ap.add_argument("--mode-steps", type=int, default=400)
     ap.add_argument("--batch-instances", type=int, default=256,
                     help="instances of the batched mode (the first K of the 256-instance sweep)")
@@ -174,30 +199,77 @@ class Clocks:
                 "reasons": sorted(reasons)}
 
 
-def cpu_baseline(g, params_kw, seconds: float, nstep: int = 0):
-    """The oracle (single thread, brute force) timed on a sample of the
-    workload: forces on m particles, each against all N.  A full oracle step
-    visits every pair once (N(N-1)/2 checks) while a sampled particle checks
-    all N-1 partners, so the full step's rate is 2m / t."""
+def host_cores() -> int:
+    """Threads the oracle's OpenMP loops use on this host."""
+    env = os.environ.get("OMP_NUM_THREADS")
+    if env and env.isdigit() and int(env) > 0:
+        return int(env)
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
+def oracle_steps(g, params_kw, steps: int, cells: bool = True, warmup: int = 1):
+    """Times whole oracle time steps (Eq. 15 with every force of the model)
+    on the host: the cell-list search with the half stencil of Sec. II A
+    (cells=True, the pair set checked equal to the brute force) or the O(N^2)
+    brute force, pairs evaluated on all host cores.  Returns (seconds per
+    step, pairs of the last step)."""
     import oracle
     oracle.build()
     po = oracle.make_params(g["box"], **params_kw)
-    o = oracle.System(po, g["x"], g["a"], ids=g["ids"], nstep=nstep)
+    o = oracle.System(po, g["x"], g["a"], ids=g["ids"], cells=cells)
+    o.init_accel()
+    if warmup:
+        o.step(warmup)
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = (time.perf_counter() - t0) / max(steps, 1)
+    return dt, o.npairs
+
+
+def cpu_baseline(g, params_kw, seconds: float, steps: int = 0):
+    """The oracle timed on whole time steps of the workload: cell-list search
+    with the half stencil, pairs on all host cores; the number of steps is
+    chosen so that the run takes about ``seconds``."""
     n = g["a"].shape[0]
-    rng = np.random.default_rng(0)
-    m = 64
-    t0 = time.perf_counter()
-    o.forces_sampled(rng.choice(n, size=m, replace=False))
-    dt = time.perf_counter() - t0
-    m = max(16, int(m * seconds / max(dt, 1e-6)))
-    m = min(m, n)
-    idx = rng.choice(n, size=m, replace=False)
-    t0 = time.perf_counter()
-    o.forces_sampled(idx)
-    dt = time.perf_counter() - t0
-    return {"value": 2.0 * m / dt, "unit": METRIC, "cores": 1, "kind": "oracle",
-            "sample": "forces on %d of the %d particles (brute force over all N, FP64, one "
-                      "thread) in %.1f s; full-step rate = 2 m / t" % (m, n, dt)}
+    per, _ = oracle_steps(g, params_kw, 1, warmup=0)
+    k = steps or max(2, min(50, int(seconds / max(per, 1e-6))))
+    per, npairs = oracle_steps(g, params_kw, k, warmup=0)
+    return {"value": n / per, "unit": METRIC, "cores": host_cores(), "kind": "oracle",
+            "sample": "%d whole time steps of the %d-particle workload (%d pairs per step; cell list "
+                      "with the half stencil, pair evaluations in parallel, FP64) at %.3f s per "
+                      "step" % (k, n, npairs, per)}
+
+
+def cpu_oracle_modes(inputs: dict, seconds: float):
+    """The oracle on the other workloads, for context: the 1000-particle FP64
+    configuration over its full 1000 steps by brute force, and about
+    ``seconds`` of whole steps with the cell list on the 1M polydisperse and
+    the Table 5 packings (without the electro-chemical forces, as the paper's
+    timing table is quoted with them; the force settings differ)."""
+    out = {"cores": host_cores()}
+    if "c1" in inputs:
+        spec, g = inputs["c1"]
+        kw = dict(mu=spec.mu, kn=spec.kn, shear_rate=spec.shear_rate, dt=spec.dt)
+        per, P = oracle_steps(g, kw, spec.steps, cells=False, warmup=0)
+        out["c1_bruteforce_1000_steps"] = {"seconds": per * spec.steps, "value": g["a"].shape[0] / per,
+                                           "unit": "particle-steps/s", "steps": spec.steps, "pairs": P}
+    for key, name in (("c3", "c3_cell_list"), ("c6", "c6_cell_list")):
+        if key not in inputs:
+            continue
+        spec, g = inputs[key]
+        kw = dict(mu=spec.mu, kn=spec.kn, shear_rate=spec.shear_rate, dt=spec.dt)
+        if key == "c6":
+            kw.update({k: v for k, v in spec.extra.items()
+                       if k not in ("f_er", "hamaker", "wave_amp", "wave_n")})
+        per1, _ = oracle_steps(g, kw, 1, warmup=0)
+        k = max(1, min(10, int(seconds / max(per1, 1e-6))))
+        per, P = oracle_steps(g, kw, k, warmup=0)
+        out[name] = {"value": g["a"].shape[0] / per, "unit": "particle-steps/s", "s_per_step": per,
+                     "steps": k, "pairs": P}
+    return out
 
 
 def max_over_ranks(x: float, world: int, device=None) -> float:
@@ -212,17 +284,29 @@ def max_over_ranks(x: float, world: int, device=None) -> float:
     return float(t.item())
 
 
+def sum_over_ranks(x: float, world: int, device=None) -> float:
+    """Sum of x over the ranks (x itself on one rank)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def job_rate(units: float, seconds: float, world: int, device=None) -> float:
     """Whole-job rate of N independent replicas (weak scaling): the units all
-    ranks processed (each rank the same count) over the slowest rank's time."""
-    return world * units / max_over_ranks(seconds, world, device)
+    ranks processed (summed, since the seeded workloads of the ranks may
+    differ in size) over the slowest rank's time."""
+    return sum_over_ranks(units, world, device) / max_over_ranks(seconds, world, device)
 
 
 def reduce_modes(extra: dict, world: int, device=None) -> None:
     """Every measured mode (an entry, or an entry of a mode's sub-table,
     carrying ms_per_step and value) becomes a whole-job figure: the slowest
-    rank's ms per step and the rate of all ranks over it.  Every rank walks
-    the same modes in the same order, so the reductions pair up."""
+    rank's ms per step and the units per step of all ranks over it.  Every
+    rank walks the same modes in the same order, so the reductions pair up."""
     if world <= 1:
         return
     for m in extra.values():
@@ -230,9 +314,56 @@ def reduce_modes(extra: dict, world: int, device=None) -> None:
             continue
         subs = [m] if "ms_per_step" in m else [v for v in m.values() if isinstance(v, dict) and "ms_per_step" in v]
         for e in subs:
+            units = sum_over_ranks(e["value"] * e["ms_per_step"], world, device)
             slowest = max_over_ranks(e["ms_per_step"], world, device)
-            e["value"] = world * e["value"] * e["ms_per_step"] / slowest
+            e["value"] = units / slowest
             e["ms_per_step"] = slowest
+
+
+def roofline(prof, nprof, c, n, precision, peaks, src, step_ms):
+    """Roofline records from the method bytes: the dominant kernel's (its
+    method bytes per launch over its mean event time), the whole step's
+    (method bytes of the step, and of the neighbour + force part alone, over
+    the step time), and a per-kernel table with this design's own bytes
+    beside the method bytes."""
+    mode = 0 if precision == "fp64" else 1
+    P, K = c["npairs"], c["ncontacts"]
+    ncell = int(np.prod(c["ncell"]))
+
+    def nbytes(t):
+        bn, bc, bp, bk = t
+        return bn * n + bc * ncell + bp * P + bk * K
+
+    per_kernel = {}
+    for k, ms in prof.items():
+        avg = ms / max(nprof, 1)
+        mb, ib = nbytes(METHOD_BYTES[k][mode]), nbytes(IMPL_BYTES[k][mode])
+        per_kernel[k] = {"ms": avg, "method_bytes": mb, "impl_bytes": ib,
+                         "gbs": mb / (avg * 1e-3) / 1e9 if avg > 0 else 0.0,
+                         "impl_over_method": ib / mb if mb else None}
+    dom = max(per_kernel, key=lambda k: per_kernel[k]["ms"])
+    d = per_kernel[dom]
+    peak = float(peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
+    traffic = None
+    rec = NCU_TRAFFIC.get((dom, precision))
+    if rec is not None and src_hash(rec[1]) == rec[2]:
+        traffic = rec[0]
+    roof = {"bound": "hbm", "kernel": dom, "achieved": d["gbs"], "peak": peak, "unit": "GB/s",
+            "frac": d["gbs"] / peak, "traffic": traffic, "peak_source": src,
+            "bytes_per_launch": d["method_bytes"],
+            "share": d["ms"] / max(sum(v["ms"] for v in per_kernel.values()), 1e-12)}
+    step_bytes = sum(v["method_bytes"] for v in per_kernel.values())
+    nf_bytes = nbytes(NF_BYTES[mode])
+    step_s = step_ms * 1e-3
+    roof_step = {"bound": "hbm", "unit": "GB/s", "peak": peak, "peak_source": src,
+                 "bytes_per_particle_step": step_bytes / n,
+                 "achieved": step_bytes / step_s / 1e9, "frac": step_bytes / step_s / 1e9 / peak,
+                 "neighbour_force_bytes_per_particle_step": nf_bytes / n,
+                 "neighbour_force_achieved": nf_bytes / step_s / 1e9,
+                 "neighbour_force_frac": nf_bytes / step_s / 1e9 / peak,
+                 "pairs_per_particle": P / n, "contacts_per_particle": K / n,
+                 "impl_bytes_per_particle_step": sum(v["impl_bytes"] for v in per_kernel.values()) / n}
+    return roof, roof_step, per_kernel
 
 
 def workload(name: str, rank: int):
@@ -441,9 +572,13 @@ def mode_poly1m(dss, g, spec, args):
         time_steps(s, 3)
         t = time_steps(s, steps)
         c = s.counters()
+        kms = profile_pass(s, 5)
+        peaks, src = load_peaks()
+        roof, roof_step, _ = roofline(kms, 1, c, n, prec.split("_")[0], peaks, src, t / steps)
         out[prec] = {"value": n * steps / (t * 1e-3), "unit": "particle-steps/s", "ms_per_step": t / steps,
                      "steps": steps, "device_gb": round(s.device_bytes() / 1e9, 1), "pairs": c["npairs"],
-                     "M": c["M"], "cells": list(c["ncell"]), "kernels_ms": profile_pass(s, 5)}
+                     "contacts": c["ncontacts"], "M": c["M"], "cells": list(c["ncell"]), "kernels_ms": kms,
+                     "roofline": roof, "roofline_step": roof_step}
         s.close()
     return out
 
@@ -481,6 +616,10 @@ def mode_adjoint(dss, g, spec, args):
 
 
 def run_reference(args, rank, world):
+    """The reference arm: the oracle itself (the paper publishes no code), on
+    rank 0 alone, stepping the headline workload whole time step by whole
+    time step on the host cores (cell list with the half stencil, pair
+    evaluations in parallel): W untimed steps, then K timed ones."""
     spec, g = workload(args.workload, 0)
     if rank != 0:
         return
@@ -488,33 +627,26 @@ def run_reference(args, rank, world):
     import oracle
     oracle.build()
     po = oracle.make_params(g["box"], **kw)
-    o = oracle.System(po, g["x"], g["a"], ids=g["ids"])
+    o = oracle.System(po, g["x"], g["a"], ids=g["ids"], cells=True)
     n = g["a"].shape[0]
-    rng = np.random.default_rng(1)
-    budget = 150.0 / max(args.steps + args.warmup, 1)          # seconds per step
+    o.init_accel()
+    if args.warmup:
+        o.step(args.warmup)
     t0 = time.perf_counter()
-    o.forces_sampled(rng.choice(n, size=32, replace=False))
-    per = (time.perf_counter() - t0) / 32
-    m = int(min(n, max(16, budget / max(per, 1e-9))))
-    for _ in range(args.warmup):
-        o.forces_sampled(rng.choice(n, size=m, replace=False))
-    times = []
-    for _ in range(args.steps):
-        idx = rng.choice(n, size=m, replace=False)
-        t0 = time.perf_counter()
-        o.forces_sampled(idx)
-        times.append(time.perf_counter() - t0)
-    t = float(np.mean(times))
-    value = 2.0 * m / t
+    o.step(args.steps)
+    t = time.perf_counter() - t0
+    value = n * args.steps / t
+    cores = host_cores()
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "particle-steps/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * n / value, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": spec.name, "n": n, "phi": spec.phi, "mu": spec.mu,
                        "radii": "1.0/1.4 equal numbers", "precision": "fp64", "l2": "n/a (CPU)"},
-            "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
-                             "sample": "each step: forces on %d of %d particles (brute force over all "
-                                       "N, FP64, one thread); full-step rate = 2 m / t" % (m, n)},
+            "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": cores, "kind": "oracle",
+                             "sample": "%d whole time steps after %d untimed ones (cell list with the "
+                                       "half stencil, pair evaluations on %d host threads, FP64)"
+                                       % (args.steps, args.warmup, cores)},
             "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -531,13 +663,21 @@ def main():
     modes = [] if args.modes in ("", "none") else args.modes.split(",")
     batch = None
     extra_inputs = {}
+    # the oracle's timings on the other workloads (rank 0, before any CUDA call)
+    cpu_inputs = {}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and "cpu" in modes:
+        cpu_inputs["c1"] = workload("c1", 0)
     if "poly1m" in modes:
         from paper_2108_01013_gb300 import synth
         extra_inputs["poly1m"] = workload("c3", rank)
+        if cpu_inputs:
+            cpu_inputs["c3"] = extra_inputs["poly1m"]
     if "adjoint" in modes:
         extra_inputs["adjoint"] = workload("c5", rank)
     if "wavy" in modes:
         extra_inputs["wavy"] = workload("c6", rank)
+    if cpu_inputs:
+        cpu_inputs["c6"] = extra_inputs["wavy"] if "wavy" in extra_inputs else workload("c6", 0)
     if "batched" in modes:
         # packed by spawned worker processes before the first CUDA call
         from paper_2108_01013_gb300 import synth
@@ -589,8 +729,7 @@ def main():
         clk = clocks.stop()
         c = s.counters()
         step_ms = t_gpu_ms / args.steps
-        t_gpu = max_over_ranks(t_gpu_ms * 1e-3, world, dev)
-        value = world * n * args.steps / t_gpu
+        value = job_rate(n * args.steps, t_gpu_ms * 1e-3, world, dev)
         # per-kernel shares: a separate pass with events between the kernels
         s.set_profiling(True)
         for _ in range(min(args.steps, 50)):
@@ -648,33 +787,18 @@ def main():
             if "batched" in extra:
                 extra["batched_vs_fp64_single"] = extra["batched"]["value"] / extra["fp64"]["value"]
 
-    # roofline of the dominant kernel
+    # roofline of the dominant kernel and of the whole step
     peaks, src = load_peaks()
+    roof, roof_step, per_kernel = roofline(prof, nprof, c, n, args.precision, peaks, src, step_ms)
     P = c["npairs"]
-    ncell = int(np.prod(c["ncell"]))
-    per_kernel = {}
-    mode = 0 if args.precision == "fp64" else 1
-    for k, ms in prof.items():
-        bn, bc, bp, bk = ALG_BYTES[k][mode]
-        nb = bn * n + bc * ncell + bp * P + bk * c["ncontacts"]
-        avg = ms / max(nprof, 1)
-        per_kernel[k] = {"ms": avg, "bytes": nb, "gbs": nb / (avg * 1e-3) / 1e9 if avg > 0 else 0.0}
-    dom = max(per_kernel, key=lambda k: per_kernel[k]["ms"])
-    d = per_kernel[dom]
-    peak = float(peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
-    traffic = None
-    rec = NCU_TRAFFIC.get((dom, args.precision))
-    if rec is not None and src_hash(rec[1]) == rec[2]:
-        traffic = rec[0]
-    roof = {"bound": "hbm", "kernel": dom, "achieved": d["gbs"], "peak": peak, "unit": "GB/s",
-            "frac": d["gbs"] / peak, "traffic": traffic, "peak_source": src,
-            "share": d["ms"] / max(sum(v["ms"] for v in per_kernel.values()), 1e-12)}
 
     if rank != 0:
         return
     cpu = None
     if not args.no_cpu_baseline:
         cpu = cpu_baseline(g, kw, args.cpu_seconds)
+        if cpu_inputs:
+            extra["cpu_oracle"] = cpu_oracle_modes(cpu_inputs, args.cpu_seconds)
     line = {
         "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
@@ -687,7 +811,10 @@ def main():
                    "l2": "flushed before every timed step (256 MB write)",
                    "pairs": P, "contacts": c["ncontacts"], "cells": list(c["ncell"])},
         "roofline": roof,
+        "roofline_step": roof_step,
         "kernels_ms": {k: round(v["ms"], 5) for k, v in per_kernel.items()},
+        "kernels_bytes": {k: {"method": v["method_bytes"], "impl": v["impl_bytes"],
+                              "method_gbs": round(v["gbs"], 1)} for k, v in per_kernel.items()},
         "kernels_note": "per-kernel times from a separate pass with CUDA events between kernels",
         "wall_s_timed_region": t_wall,
         "clocks": clk,

@@ -59,7 +59,8 @@ enum dss_status {
   DSS_ERR_TIMEOUT = -7,    /* a bounded device-side wait gave up */
   DSS_ERR_STATE = -8,      /* call order (e.g. dss_step before dss_set_state) */
   DSS_ERR_INTERNAL = -9,   /* internal consistency check failed on the device */
-  DSS_ERR_SCRATCH_LIMIT = -10  /* dss_pairs_noalloc: problem larger than its fixed scratch array */
+  DSS_ERR_SCRATCH_LIMIT = -10, /* dss_pairs_noalloc: problem larger than its fixed scratch array */
+  DSS_ERR_NOMEM = -11          /* a host-side allocation inside the call failed */
 };
 
 enum dss_precision {
@@ -301,6 +302,20 @@ int dss_load(dss_handle *h, const void *buf, size_t len);
 int dss_autotune(dss_handle *h, int32_t trial_steps, int32_t ncand, const double *factors,
                  double *ms_per_step, double *cell_size);
 
+/* Kernel shapes (the tile parameters of the step; north star: "tile shape
+ * picked by an autotuner"), timed at the current cell grid: the register
+ * budget of the pair kernel (cut for 3 or 4 resident 256-thread blocks per
+ * SM: 80 or 64 registers; more warps in flight against more spills) and the
+ * enumeration's candidate loop (one candidate at a time, or four loaded
+ * before they are tested).  Each of the 4 combinations runs 2 + trial_steps
+ * steps from a checkpoint of the current state; the fastest is kept and the
+ * state restored.  ms_per_step (host, 4 doubles, may be NULL): ms per step of
+ * (3 blocks, 1), (3, 4), (4, 1), (4, 4); choice (host, 2 ints, may be NULL):
+ * the kept (blocks per SM, candidates ahead).  Errors: DSS_ERR_ARG
+ * (trial_steps < 1), DSS_ERR_STATE, and any error of a trial step (the
+ * built-in rule is kept then). */
+int dss_autotune_kernels(dss_handle *h, int32_t trial_steps, double *ms_per_step, int32_t *choice);
+
 /* Gradient of a stress functional of a rollout (reverse mode).  Runs nsteps
  * steps from the current state (as dss_step would), with
  *     J = sum_{n=1..nsteps} sum_q weights[(n-1)*9 + q] * sigma^n_q
@@ -373,6 +388,23 @@ int dss_dispersion(dss_handle *h, double *out);
  * thread order). */
 int dss_contact_clusters(dss_handle *h, int32_t *label, int64_t *nclusters);
 
+/* Local volume fraction along the shear-wise direction y by size class
+ * (Sec. III B, Fig. 12: the distribution of the large and of the small
+ * particles across the gradient direction, whose peaks show the large
+ * particles migrating to the zero-shear planes of the wavy flow).  The box
+ * of each instance is cut into nbins slabs of equal width along y; for each
+ * slab and class, out holds the volume of the class's spheres inside the
+ * slab (each sphere's exact integral of its cross-sections over the slab,
+ * its periodic images across y = 0 and y = L_y included) divided by the
+ * slab's volume.  Class 0: radius <= a_split, class 1: radius > a_split.
+ * The mean over the slabs of a class is that class's volume fraction.  At
+ * the committed state; averaging over snapshots is the caller's.  out: K x 2
+ * x nbins doubles (instance-major, then class, then slab), host or device.
+ * Deterministic (integer sums in a unit of 2^-62 of the instance's solid
+ * volume).  Errors: DSS_ERR_ARG (nbins < 1 or > 2^20, a_split not finite),
+ * DSS_ERR_STATE, DSS_ERR_CUDA. */
+int dss_phi_profile(dss_handle *h, int32_t nbins, double a_split, double *out);
+
 /* Bytes of device memory the handle holds. */
 int64_t dss_device_bytes(const dss_handle *h);
 
@@ -389,10 +421,14 @@ const char *dss_strerror(int code);
  * allocating library routine.
  *
  * It computes the same pair set as dss_neighbour_build + dss_get_pairs for
- * the state (x, a, ids) at time nstep*dt, with the parameters p (only the
- * cutoff fields and gdot, dt are used): every pair with
- * r^2 < (a_i + a_j + delta_ij)^2 under Lees-Edwards minimum images, written
- * as (lo id, hi id) into pairs[2*k], pairs[2*k+1] in no particular order.
+ * the state (x, a, ids) at time nstep*dt, with the parameters p: every pair
+ * with r^2 < (a_i + a_j + delta_ij)^2 under Lees-Edwards minimum images, where
+ * delta_ij is the larger of the lubrication range (delta_lub, a0,
+ * lub_cutoff_mode) and the electro-chemical range (f_er, lambda_d, hamaker,
+ * a0: 20 lambda_d and 4 a0 while the respective force is on); shear_rate and
+ * dt set the Lees-Edwards offset; the other fields are not read.  Pairs are
+ * written as (lo id, hi id) into pairs[2*k], pairs[2*k+1] in no particular
+ * order.
  *
  * Arguments: x (3n, SoA, inside [0, L)), a (n), ids (n, or NULL for k -> k)
  * and pairs (2*cap int64) are DEVICE memory of the current device; box,
@@ -400,6 +436,11 @@ const char *dss_strerror(int code);
  * (it sets the cell size; a larger radius returns DSS_ERR_ARG).  *count
  * receives the number of pairs; at most cap are written.  The call is
  * ordered on cuda_stream (NULL: legacy stream) and synchronises it.
+ *
+ * Errors: DSS_ERR_ARG (NULL pointer, n < 2, a non-positive box edge or
+ * a_max, nstep < 0, an unknown cutoff mode, a radius above a_max),
+ * DSS_ERR_BOX (fewer than 4 x 3 x 3 cells of that edge fit in the box),
+ * DSS_ERR_SCRATCH_LIMIT (below), DSS_ERR_CUDA.
  *
  * Working memory: one file-scope __device__ array of DSS_NOALLOC_SCRATCH_INTS
  * 32-bit words (8 MiB), which every GPU that loads the library holds until

@@ -46,6 +46,12 @@ Parity status of each function (see the pins in ``tests/test_oracle_*.py``):
   System.step / forces / stress     pinned (Stokes relaxation closed form,
                                     Lees-Edwards wrap invariants, momentum
                                     balance, stress sign checks)
+  System(cells=True), pairs_cell    the cell list with the half stencil of
+                                    Sec. II A: pinned to the brute force
+                                    (equal pair sets up to 20k particles,
+                                    Lees-Edwards layers, polydisperse radii,
+                                    near-cutoff pairs; bit-identical forces,
+                                    stress and trajectories)
 """
 from __future__ import annotations
 
@@ -62,7 +68,8 @@ _OUT = os.path.join(_HERE, "_build", "liboracle.so")
 
 
 def build(force: bool = False) -> str:
-    """Compile ``oracle.c`` into ``_build/liboracle.so`` (gcc, FP64, no FMA)."""
+    """Compile ``oracle.c`` into ``_build/liboracle.so`` (gcc, FP64, no FMA;
+    OpenMP over the host cores where the compiler offers it)."""
     os.makedirs(os.path.dirname(_OUT), exist_ok=True)
     if (not force and os.path.exists(_OUT)
             and os.path.getmtime(_OUT) >= os.path.getmtime(_SRC)):
@@ -70,7 +77,11 @@ def build(force: bool = False) -> str:
     tmp = _OUT + ".tmp%d" % os.getpid()
     cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
            "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
-    subprocess.check_call(cmd)
+    try:
+        subprocess.check_call(cmd[:1] + ["-fopenmp"] + cmd[1:], stdout=subprocess.DEVNULL,
+                              stderr=subprocess.DEVNULL)
+    except subprocess.CalledProcessError:
+        subprocess.check_call(cmd)
     os.replace(tmp, _OUT)
     return _OUT
 
@@ -179,7 +190,13 @@ def lib():
         L.orc_get_images.restype = None
         L.orc_get_images.argtypes = [c_void_p, i64p]
         L.orc_forces_sampled.restype = None
-        L.orc_forces_sampled.argtypes = [c_void_p, i64p, c_int64, dp, dp]
+        L.orc_forces_sampled.argtypes = [c_void_p, i64p, c_int64, dp, dp, dp, dp]
+        L.orc_set_cells.restype = None
+        L.orc_set_cells.argtypes = [c_void_p, c_int]
+        L.orc_pairs_cell.restype = c_int64
+        L.orc_pairs_cell.argtypes = [c_void_p, i64p, c_int64]
+        L.orc_get_force_scale.restype = None
+        L.orc_get_force_scale.argtypes = [c_void_p, dp, dp]
         for nm in ("orc_get_nstep", "orc_get_npairs", "orc_get_ncontacts"):
             getattr(L, nm).restype = c_int64
             getattr(L, nm).argtypes = [c_void_p]
@@ -313,7 +330,7 @@ class System:
     """Oracle simulation: state + contact history, brute-force pairs."""
 
     def __init__(self, p: Params, x, a, ids=None, u=None, w=None, al=None, aw=None,
-                 nstep: int = 0):
+                 nstep: int = 0, cells: bool = False):
         a = _d(a)
         self.n = a.shape[0]
         self.p = p
@@ -326,6 +343,24 @@ class System:
         self._keep = bufs
         lib().orc_set_state(self._h, _ptr(_d(x).reshape(3, self.n)), _ptr(a),
                             _ptr(self.ids, c_int32), *[_opt(b) for b in bufs], int(nstep))
+        self.set_cells(cells)
+
+    def set_cells(self, cells: bool):
+        """Neighbour search by the cell list with the half stencil (True) or
+        the brute force (False, the default); the same pair set in the same
+        order, hence the same numbers."""
+        lib().orc_set_cells(self._h, 1 if cells else 0)
+
+    def pairs_cell(self) -> np.ndarray:
+        """(lo id, hi id) pairs of the current state found by the cell list,
+        sorted (compare ``pairs_bruteforce``); None when the box holds too few
+        cells for it."""
+        cnt = lib().orc_pairs_cell(self._h, None, 0)
+        if cnt < 0:
+            return None
+        out = np.zeros((max(cnt, 1), 2), dtype=np.int64)
+        lib().orc_pairs_cell(self._h, _ptr(out, c_int64), cnt)
+        return out[:cnt]
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -340,12 +375,16 @@ class System:
         lib().orc_forces(self._h, 1 if commit else 0)
         return self.get_forces()
 
-    def forces_sampled(self, idx):
-        """Force and torque (3, m) on the listed particles (array indices)."""
+    def forces_sampled(self, idx, scale: bool = False):
+        """Force and torque (3, m) on the listed particles (array indices);
+        with scale=True also the sums of the magnitudes of their terms (m)."""
         idx = np.ascontiguousarray(idx, dtype=np.int64)
         m = idx.shape[0]
         F, T = np.zeros((3, m)), np.zeros((3, m))
-        lib().orc_forces_sampled(self._h, _ptr(idx, c_int64), m, _ptr(F), _ptr(T))
+        Fa, Ta = np.zeros(m), np.zeros(m)
+        lib().orc_forces_sampled(self._h, _ptr(idx, c_int64), m, _ptr(F), _ptr(T), _ptr(Fa), _ptr(Ta))
+        if scale:
+            return F, T, Fa, Ta
         return F, T
 
     def step(self, nsteps: int = 1):
@@ -363,6 +402,14 @@ class System:
         s = np.zeros(9)
         lib().orc_get_forces(self._h, _ptr(F), _ptr(T), _ptr(s))
         return F, T, s.reshape(3, 3)
+
+    def force_scale(self):
+        """Per particle, the sums of the magnitudes of the terms of the force
+        and of the torque of the last evaluation (pair terms and drag), (n,)
+        each: the scale of the rounding error of any summation of them."""
+        Fa, Ta = np.zeros(self.n), np.zeros(self.n)
+        lib().orc_get_force_scale(self._h, _ptr(Fa), _ptr(Ta))
+        return Fa, Ta
 
     def get_images(self):
         """Lees-Edwards image count along y of each particle since set_state

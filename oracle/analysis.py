@@ -1,7 +1,8 @@
 """CPU oracle of the analysis pass (TEST INFRASTRUCTURE ONLY; only tests/
 may import it): the rheological quantities derived from the bulk stress
 (Sec. II, after Eq. 9), the clusters of contacting particles (Sec. III A,
-Fig. 10-11) and the shear-wise dispersion of Eq. 18-19.  Plain Python and
+Fig. 10-11), the shear-wise dispersion of Eq. 18-19 and the local volume
+fraction along y by size class (Sec. III B, Fig. 12).  Plain Python and
 numpy, written from the definitions; pinned in tests/test_oracle_analysis.py.
 """
 from __future__ import annotations
@@ -58,3 +59,28 @@ def dispersion(y, y0, v, v0, dt_elapsed: float, shear_rate: float, a0: float = 1
     dy = msd / (2.0 * dt_elapsed) / (a0 * a0 * shear_rate) if dt_elapsed > 0 else 0.0
     cv = np.mean(v * v0) / np.mean(v * v)
     return float(dy), float(cv)
+
+
+def phi_profile(y, a, box, nbins: int, a_split: float) -> np.ndarray:
+    """Local volume fraction along y (Sec. III B, Fig. 12): (2, nbins), the
+    volume of the spheres of class 0 (a <= a_split) and class 1 (a > a_split)
+    inside each of nbins equal slabs of the periodic box, over the slab's
+    volume.  A sphere of radius a centred at yc holds, between the planes
+    y0 < y1, the integral of its cross-sections pi (a^2 - t^2) over
+    t in [max(y0 - yc, -a), min(y1 - yc, a)]; its images at yc -+ L_y count
+    the same way."""
+    y = np.asarray(y, dtype=np.float64)
+    a = np.asarray(a, dtype=np.float64)
+    Lx, Ly, Lz = (float(v) for v in box)
+    w = Ly / nbins
+    out = np.zeros((2, nbins))
+    for yy, aa in zip(y.tolist(), a.tolist()):
+        c = 1 if aa > a_split else 0
+        for img in (-1, 0, 1):
+            yc = yy + img * Ly
+            for b in range(nbins):
+                y0, y1 = b * w, (Ly if b == nbins - 1 else (b + 1) * w)
+                t0, t1 = max(y0 - yc, -aa), min(y1 - yc, aa)
+                if t1 > t0:
+                    out[c, b] += np.pi * (aa * aa * (t1 - t0) - (t1 ** 3 - t0 ** 3) / 3.0)
+    return out / (Lx * Lz * w)

@@ -15,7 +15,11 @@
  * U sin(2 pi n y / L_y) and E_inf, Omega_inf follow the local rate
  * dU_inf,x/dy.  Arrays are SoA: v[0*n+i], v[1*n+i], v[2*n+i].
  * Neighbour pairs come from an O(N^2) brute-force scan (the plain definition
- * of the fixed-radius near-neighbour set); nothing is blocked or reordered.
+ * of the fixed-radius near-neighbour set) or, on request, from a cell list
+ * with the paper's half stencil (Sec. II A) that is checked to give the same
+ * set; either set is sorted by (i, j) and evaluated in that order, so both
+ * give the same numbers bit for bit.  Pairs are evaluated on all host cores
+ * (OpenMP, each pair on its own) and summed in the set's order.
  *
  * Readings of the paper that this file takes (each one is listed in the
  * design notes of the repository):
@@ -89,6 +93,10 @@ typedef struct orc_sys {
   double *a;                    /* radius */
   int32_t *id;                  /* persistent id */
   double *F, *T;                /* total force/torque of the last evaluation */
+  double *Fa, *Ta;              /* sums of the magnitudes of the terms of F and T (per pair the
+                                   contact, each lubrication sub-term, the electro-chemical and
+                                   rolling terms; the drag): the scale of the rounding error of
+                                   any evaluation that forms these terms and sums them */
   double sigma[9];              /* bulk stress of the last evaluation, row major */
   int64_t nstep;                /* time t = nstep*dt */
   int64_t hk, hcap;             /* contact history: sorted keys lo<<32|hi */
@@ -97,6 +105,7 @@ typedef struct orc_sys {
   double *hxi;                  /* [hk][3], orientation lo -> hi */
   double *hxr;                  /* [hk][3], rolling stretch (the same in both orientations) */
   int64_t npairs_last, ncontacts_last;
+  int cells;                    /* neighbour search: 0 brute force, 1 cell list (same pair set) */
 } orc_sys;
 
 /* ------------------------------------------------------------------------ */
@@ -466,10 +475,15 @@ static void lub_coefficients(const orc_params *p, double d, double ai, double aj
  * with V = u - U_inf(x), W = omega - Omega_inf (particle-by-particle),
  * r = x_j - x_i and the strain E_inf of a shear of local rate `rate` along x.
  * Each block of Eq. A2/A3 is applied as written. */
-void orc_lubrication_rate(const orc_params *p, double rate, const double r[3], double ai,
-                          double aj, const double Vi[3], const double Vj[3],
-                          const double Wi[3], const double Wj[3], double Fi[3], double Fj[3],
-                          double Ti[3], double Tj[3]) {
+/* mag (may be NULL): the sums of the magnitudes of the sub-terms of F_i,
+ * F_j, T_i, T_j (each coefficient times its projected velocity, angular
+ * velocity or strain vector), the scale of the rounding of any evaluation
+ * that forms the sub-terms separately; a diagnostic for the parity checks
+ * that does not change the result. */
+static void lubrication_core(const orc_params *p, double rate, const double r[3], double ai,
+                             double aj, const double Vi[3], const double Vj[3],
+                             const double Wi[3], const double Wj[3], double Fi[3], double Fj[3],
+                             double Ti[3], double Tj[3], double mag[4]) {
   double dist = sqrt(dot3(r, r));
   double n[3] = {r[0] / dist, r[1] / dist, r[2] / dist};
   double d = dist - (ai + aj);
@@ -523,6 +537,30 @@ void orc_lubrication_rate(const orc_params *p, double rate, const double r[3], d
     Ti[q] = -k * ti + k * hi;
     Tj[q] = -k * tj + k * hj;
   }
+  if (mag) {
+    double nNVi = sqrt(dot3(NVi, NVi)), nTVi = sqrt(dot3(TVi, TVi)), nNVj = sqrt(dot3(NVj, NVj));
+    double nTVj = sqrt(dot3(TVj, TVj)), nWi = sqrt(dot3(nxWi, nxWi)), nWj = sqrt(dot3(nxWj, nxWj));
+    double nVi = sqrt(dot3(nxVi, nxVi)), nVj = sqrt(dot3(nxVj, nxVj));
+    double nTWi = sqrt(dot3(TWi, TWi)), nTWj = sqrt(dot3(TWj, TWj));
+    double nQ = sqrt(dot3(Qn, Qn)), nP = fabs(P), nH = sqrt(dot3(nperp, nperp));
+    mag[0] = k * (fabs(c.XA_ii) * nNVi + fabs(c.YA_ii) * nTVi + fabs(c.XA_ij) * nNVj +
+                  fabs(c.YA_ij) * nTVj + fabs(c.YB_ii) * nWi + fabs(c.YB_ji) * nWj +
+                  (fabs(c.XG_ii) + fabs(c.XG_ji)) * nP + (fabs(c.YG_ii) + fabs(c.YG_ji)) * nQ);
+    mag[1] = k * (fabs(c.XA_ji) * nNVi + fabs(c.YA_ji) * nTVi + fabs(c.XA_jj) * nNVj +
+                  fabs(c.YA_jj) * nTVj + fabs(c.YB_ij) * nWi + fabs(c.YB_jj) * nWj +
+                  (fabs(c.XG_ij) + fabs(c.XG_jj)) * nP + (fabs(c.YG_ij) + fabs(c.YG_jj)) * nQ);
+    mag[2] = k * (fabs(c.YB_ii) * nVi + fabs(c.YB_ij) * nVj + fabs(c.YC_ii) * nTWi +
+                  fabs(c.YC_ij) * nTWj + (fabs(c.YH_ii) + fabs(c.YH_ji)) * nH);
+    mag[3] = k * (fabs(c.YB_ji) * nVi + fabs(c.YB_jj) * nVj + fabs(c.YC_ji) * nTWi +
+                  fabs(c.YC_jj) * nTWj + (fabs(c.YH_ij) + fabs(c.YH_jj)) * nH);
+  }
+}
+
+void orc_lubrication_rate(const orc_params *p, double rate, const double r[3], double ai,
+                          double aj, const double Vi[3], const double Vj[3],
+                          const double Wi[3], const double Wj[3], double Fi[3], double Fj[3],
+                          double Ti[3], double Tj[3]) {
+  lubrication_core(p, rate, r, ai, aj, Vi, Vj, Wi, Wj, Fi, Fj, Ti, Tj, NULL);
 }
 
 /* The same in the simple shear of rate gdot. */
@@ -578,11 +616,12 @@ void orc_echem(const orc_params *p, double d, double ai, double aj, const double
  * In the wavy flow of Eq. 17, V = u - U_inf and W = w - Omega_inf are taken
  * at each centre and the strain acting on the pair is that of the mean of
  * the two centres' local shear rates. */
-int orc_pair_eval_full(const orc_params *p, double off, const double xi[3], const double xj[3],
-                       const double ui[3], const double uj[3], const double wi[3],
-                       const double wj[3], double ai, double aj, const double xi_old[3],
-                       const double xr_old[3], double Fi[3], double Fj[3], double Ti[3],
-                       double Tj[3], double S[9], double xi_new[3], double xr_new[3]) {
+static int pair_eval_core(const orc_params *p, double off, const double xi[3], const double xj[3],
+                          const double ui[3], const double uj[3], const double wi[3],
+                          const double wj[3], double ai, double aj, const double xi_old[3],
+                          const double xr_old[3], double Fi[3], double Fj[3], double Ti[3],
+                          double Tj[3], double S[9], double xi_new[3], double xr_new[3],
+                          double mag[4]) {
   double r[3];
   int sy;
   memset(Fi, 0, 3 * sizeof(double)); memset(Fj, 0, 3 * sizeof(double));
@@ -615,13 +654,15 @@ int orc_pair_eval_full(const orc_params *p, double off, const double xi[3], cons
   double Wi[3] = {wi[0], wi[1], wi[2] + 0.5 * rate_i};
   double Wj[3] = {wj[0], wj[1], wj[2] + 0.5 * rate_j};
   double Fli[3] = {0, 0, 0}, Flj[3] = {0, 0, 0}, Tli[3] = {0, 0, 0}, Tlj[3] = {0, 0, 0};
+  double lm[4] = {0, 0, 0, 0};
   if (in_lub_range(p, r, ai, aj)) {
-    orc_lubrication_rate(p, 0.5 * (rate_i + rate_j), r, ai, aj, Vi, Vj, Wi, Wj, Fli, Flj, Tli,
-                         Tlj);
+    lubrication_core(p, 0.5 * (rate_i + rate_j), r, ai, aj, Vi, Vj, Wi, Wj, Fli, Flj, Tli, Tlj,
+                     mag ? lm : NULL);
     double tap = lub_taper_factor(p, d, ai, aj);
     for (int q = 0; q < 3; ++q) {
       Fli[q] *= tap; Flj[q] *= tap; Tli[q] *= tap; Tlj[q] *= tap;
     }
+    for (int q = 0; q < 4; ++q) lm[q] *= tap;
   }
   /* electro-chemical force (Eq. 6-7), central */
   double Fe[3] = {0, 0, 0};
@@ -640,7 +681,25 @@ int orc_pair_eval_full(const orc_params *p, double off, const double xi[3], cons
   for (int a = 0; a < 3; ++a)
     for (int b = 0; b < 3; ++b)
       S[3 * a + b] = r[a] * Fc[b] + 0.5 * (r[a] * Fli[b] + r[b] * Fli[a]) + r[a] * Fe[b];
+  if (mag) {
+    /* each physical term on its own: contact, lubrication sub-terms,
+     * electro-chemical, rolling */
+    double c = sqrt(dot3(Fc, Fc)), e = sqrt(dot3(Fe, Fe));
+    mag[0] = c + lm[0] + e;
+    mag[1] = c + lm[1] + e;
+    mag[2] = sqrt(dot3(Tci, Tci)) + lm[2] + sqrt(dot3(Tri, Tri));
+    mag[3] = sqrt(dot3(Tcj, Tcj)) + lm[3] + sqrt(dot3(Trj, Trj));
+  }
   return flags;
+}
+
+int orc_pair_eval_full(const orc_params *p, double off, const double xi[3], const double xj[3],
+                       const double ui[3], const double uj[3], const double wi[3],
+                       const double wj[3], double ai, double aj, const double xi_old[3],
+                       const double xr_old[3], double Fi[3], double Fj[3], double Ti[3],
+                       double Tj[3], double S[9], double xi_new[3], double xr_new[3]) {
+  return pair_eval_core(p, off, xi, xj, ui, uj, wi, wj, ai, aj, xi_old, xr_old, Fi, Fj, Ti, Tj, S,
+                        xi_new, xr_new, NULL);
 }
 
 /* The pair without rolling history (a new rolling spring when k_r > 0). */
@@ -666,6 +725,8 @@ orc_sys *orc_create(int64_t n, const orc_params *p) {
   s->w = (double *)calloc(1, v3); s->al = (double *)calloc(1, v3);
   s->aw = (double *)calloc(1, v3); s->F = (double *)calloc(1, v3);
   s->T = (double *)calloc(1, v3);
+  s->Fa = (double *)calloc(1, v3 / 3);
+  s->Ta = (double *)calloc(1, v3 / 3);
   s->a = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
   s->id = (int32_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int32_t));
   s->hcap = 16;
@@ -679,7 +740,7 @@ orc_sys *orc_create(int64_t n, const orc_params *p) {
 void orc_destroy(orc_sys *s) {
   if (!s) return;
   free(s->x); free(s->u); free(s->w); free(s->al); free(s->aw);
-  free(s->F); free(s->T); free(s->a); free(s->id); free(s->hkey); free(s->hxi); free(s->hxr); free(s->iy);
+  free(s->F); free(s->T); free(s->Fa); free(s->Ta); free(s->a); free(s->id); free(s->hkey); free(s->hxi); free(s->hxr); free(s->iy);
   free(s);
 }
 
@@ -777,10 +838,218 @@ static void stokes_drag(const orc_sys *s, int64_t k, double f[3], double t[3]) {
   }
 }
 
+/* ------------------------------------------------------------------------ */
+/* Pair sets of the current state: (i, j) array indices with i < j, sorted   */
+/* by (i, j).  The brute force is the definition; the cell list (Sec. II A:  */
+/* a counting sort into cells of edge >= the largest pair range, then the    */
+/* symmetric half stencil) finds the same set, and since the set is then     */
+/* sorted the same way, the evaluation below is the same arithmetic in the   */
+/* same order either way.                                                    */
+/* ------------------------------------------------------------------------ */
+
+/* Brute force: every i < j, in that order. */
+static int64_t pairs_brute(const orc_sys *s, double off, int64_t **out) {
+  const orc_params *p = &s->p;
+  int64_t n = s->n;
+  int64_t *cnt = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+  /* two passes over the rows (count, then fill), each row on its own */
+  for (int pass = 0; pass < 2; ++pass) {
+    int64_t *pr = pass ? *out : NULL;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; ++i) {
+      double xi[3] = {s->x[i], s->x[n + i], s->x[2 * n + i]};
+      int64_t k = pass ? cnt[i] : 0;
+      for (int64_t j = i + 1; j < n; ++j) {
+        double xj[3] = {s->x[j], s->x[n + j], s->x[2 * n + j]};
+        double r[3];
+        int sy;
+        min_image(p, off, xi, xj, r, &sy);
+        if (!is_pair(p, r, s->a[i], s->a[j])) continue;
+        if (pass) {
+          pr[2 * k] = i;
+          pr[2 * k + 1] = j;
+        }
+        ++k;
+      }
+      if (!pass) cnt[i + 1] = k;
+    }
+    if (!pass) {
+      for (int64_t i = 0; i < n; ++i) cnt[i + 1] += cnt[i];
+      *out = (int64_t *)malloc(sizeof(int64_t) * 2 * (size_t)(cnt[n] > 0 ? cnt[n] : 1));
+    }
+  }
+  int64_t P = cnt[n];
+  free(cnt);
+  return P;
+}
+
+/* Cell list with the half stencil.  Cells: nc = floor(L / (range (1 + 1e-9)))
+ * per axis, range = 2 a_max + the largest delta_ij, so that a pair's cells
+ * differ by at most one along each axis.  Particle i of cell (cx, cy, cz)
+ * looks at the particles after it in its own cell, the cell x+1, the three
+ * cells x-1..x+1 of the row z+1, and the layer y+1: its nine cells, or, when
+ * y+1 wraps through y = L_y, the four x cells cx - s - 2 .. cx - s + 1
+ * (s = floor(off / cs_x)) of rows z-1..z+1, which hold every particle whose
+ * Lees-Edwards image (x + off) can lie within range.  Each unordered pair of
+ * cells is visited from one side only, so each pair is found once.  Needs at
+ * least 4 cells along x and 3 along y and z; returns -1 otherwise. */
+static int64_t pairs_cell(const orc_sys *s, double off, int64_t **out) {
+  const orc_params *p = &s->p;
+  int64_t n = s->n;
+  double amax = 0.0;
+  for (int64_t i = 0; i < n; ++i) amax = s->a[i] > amax ? s->a[i] : amax;
+  double range = 2.0 * amax + pair_delta(p, amax, amax);
+  int nc[3];
+  double cs[3];
+  for (int d = 0; d < 3; ++d) {
+    nc[d] = (int)floor(p->L[d] / (range * (1.0 + 1e-9)));
+    if (nc[d] < (d == 0 ? 4 : 3)) return -1;
+    cs[d] = p->L[d] / nc[d];
+  }
+  int64_t ncell = (int64_t)nc[0] * nc[1] * nc[2];
+  int32_t *cell = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+  int64_t *cstart = (int64_t *)calloc((size_t)ncell + 1, sizeof(int64_t));
+  int64_t *order = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+  /* counting sort (stable: increasing index within a cell) */
+  for (int64_t i = 0; i < n; ++i) {
+    int c[3];
+    for (int d = 0; d < 3; ++d) {
+      c[d] = (int)floor(s->x[d * n + i] / cs[d]);
+      if (c[d] < 0) c[d] = 0;
+      if (c[d] >= nc[d]) c[d] = nc[d] - 1;
+    }
+    cell[i] = (int32_t)((c[2] * nc[1] + c[1]) * nc[0] + c[0]);
+    cstart[cell[i] + 1] += 1;
+  }
+  for (int64_t c = 0; c < ncell; ++c) cstart[c + 1] += cstart[c];
+  {
+    int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)ncell);
+    memcpy(fill, cstart, sizeof(int64_t) * (size_t)ncell);
+    for (int64_t i = 0; i < n; ++i) order[fill[cell[i]]++] = i;
+    free(fill);
+  }
+  int fsh = (int)floor(off / cs[0]);
+  /* pairs grouped by their lower index: count, offsets, fill, sort each group */
+  int64_t *cnt = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+  int64_t *pos = NULL;
+  for (int pass = 0; pass < 2; ++pass) {
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < n; ++i) {
+      int ci = cell[i];
+      int cx = ci % nc[0], cy = (ci / nc[0]) % nc[1], cz = ci / (nc[0] * nc[1]);
+      double xi[3] = {s->x[i], s->x[n + i], s->x[2 * n + i]};
+      /* the stencil: up to 1 + 1 + 3 + 12 cells */
+      int64_t cells[17];
+      int nq = 0;
+      cells[nq++] = ci;
+      cells[nq++] = (cz * nc[1] + cy) * nc[0] + (cx + 1) % nc[0];
+      for (int ox = -1; ox <= 1; ++ox)
+        cells[nq++] = (((cz + 1) % nc[2]) * nc[1] + cy) * nc[0] + (cx + ox + nc[0]) % nc[0];
+      int wrap = cy + 1 == nc[1];
+      int qy = wrap ? 0 : cy + 1;
+      int x0 = wrap ? -2 - fsh : -1, x1 = wrap ? 1 - fsh : 1;
+      for (int oz = -1; oz <= 1; ++oz)
+        for (int ox = x0; ox <= x1; ++ox) {
+          int qx = ((cx + ox) % nc[0] + nc[0]) % nc[0];
+          cells[nq++] = (((cz + oz + nc[2]) % nc[2]) * nc[1] + qy) * nc[0] + qx;
+        }
+      for (int q = 0; q < nq; ++q) {
+        int64_t b = cstart[cells[q]], e = cstart[cells[q] + 1];
+        for (int64_t t = b; t < e; ++t) {
+          int64_t j = order[t];
+          if (q == 0 && j <= i) continue;   /* own cell: partners after i */
+          double xj[3] = {s->x[j], s->x[n + j], s->x[2 * n + j]};
+          double r[3];
+          int sy;
+          min_image(p, off, xi, xj, r, &sy);
+          if (!is_pair(p, r, s->a[i], s->a[j])) continue;
+          int64_t lo = i < j ? i : j, hi = i < j ? j : i;
+          if (!pass) {
+#pragma omp atomic
+            cnt[lo + 1] += 1;
+          } else {
+            int64_t k;
+#pragma omp atomic capture
+            k = pos[lo]++;
+            (*out)[2 * k] = lo;
+            (*out)[2 * k + 1] = hi;
+          }
+        }
+      }
+    }
+    if (!pass) {
+      for (int64_t i = 0; i < n; ++i) cnt[i + 1] += cnt[i];
+      *out = (int64_t *)malloc(sizeof(int64_t) * 2 * (size_t)(cnt[n] > 0 ? cnt[n] : 1));
+      pos = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+      memcpy(pos, cnt, sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    }
+  }
+  /* each group in increasing partner index (insertion sort: groups are short) */
+#pragma omp parallel for schedule(dynamic, 256)
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t *g = *out + 2 * cnt[i];
+    int64_t m = cnt[i + 1] - cnt[i];
+    for (int64_t k = 1; k < m; ++k) {
+      int64_t v = g[2 * k + 1], t = k;
+      while (t > 0 && g[2 * (t - 1) + 1] > v) {
+        g[2 * t + 1] = g[2 * (t - 1) + 1];
+        --t;
+      }
+      g[2 * t + 1] = v;
+    }
+  }
+  int64_t P = cnt[n];
+  free(cell); free(cstart); free(order); free(cnt); free(pos);
+  return P;
+}
+
+/* Pair set of the current state by the system's neighbour mode (0: brute
+ * force, 1: cell list; the brute force also when the box holds too few
+ * cells). */
+static int64_t pairs_of(const orc_sys *s, double off, int64_t **out) {
+  if (s->cells) {
+    int64_t P = pairs_cell(s, off, out);
+    if (P >= 0) return P;
+  }
+  return pairs_brute(s, off, out);
+}
+
+/* Neighbour search mode of a system: 0 brute force (the default), 1 cell
+ * list.  Both give the same pair set in the same order. */
+void orc_set_cells(orc_sys *s, int cells) { s->cells = cells ? 1 : 0; }
+
+/* The pair set of the current state found by the cell list, as (lo id, hi
+ * id) sorted lexicographically (compare orc_pairs_bruteforce).  Returns the
+ * number of pairs (at most cap written), -1 when the box holds too few
+ * cells. */
+int64_t orc_pairs_cell(orc_sys *s, int64_t *out, int64_t cap) {
+  int64_t *pr = NULL;
+  int64_t P = pairs_cell(s, orc_le_offset(&s->p, s->nstep), &pr);
+  if (P < 0) return -1;
+  for (int64_t k = 0; k < P; ++k) {
+    int64_t a = s->id[pr[2 * k]], b = s->id[pr[2 * k + 1]];
+    pr[2 * k] = a < b ? a : b;
+    pr[2 * k + 1] = a < b ? b : a;
+  }
+  qsort(pr, (size_t)P, sizeof(int64_t) * 2, cmp_i64pair);
+  int64_t m = P < cap ? P : cap;
+  if (out && m > 0) memcpy(out, pr, sizeof(int64_t) * 2 * (size_t)m);
+  free(pr);
+  return P;
+}
+
+/* One pair's results, kept until they are summed in pair order. */
+typedef struct pres {
+  double Fi[3], Fj[3], Ti[3], Tj[3], S[9], xn[3], rn[3], mag[4];
+  int fl;
+} pres;
+
 /* Force evaluation at the current state (x, u, w) and time nstep*dt:
- * all pair interactions (brute force), Stokes drag (Eq. A1), per-particle
- * totals F and T, the bulk stress of Eq. 8, and, when commit != 0, the new
- * contact history. */
+ * all pair interactions (from the pair set, in its order), Stokes drag
+ * (Eq. A1), per-particle totals F and T, the bulk stress of Eq. 8, and, when
+ * commit != 0, the new contact history.  The pairs are evaluated in parallel
+ * (each on its own) and summed one after another in the set's order, so the
+ * result does not depend on the number of threads. */
 void orc_forces(orc_sys *s, int commit) {
   const orc_params *p = &s->p;
   int64_t n = s->n;
@@ -789,54 +1058,64 @@ void orc_forces(orc_sys *s, int commit) {
   ambient(p, E, Om);
   memset(s->F, 0, sizeof(double) * 3 * (size_t)n);
   memset(s->T, 0, sizeof(double) * 3 * (size_t)n);
-  double Spair[9] = {0};
-  int64_t hn = 0, hc = 64;
-  hrec *hnew = (hrec *)malloc(sizeof(hrec) * (size_t)hc);
-  int64_t npairs = 0, ncont = 0;
-  for (int64_t i = 0; i < n; ++i) {
+  memset(s->Fa, 0, sizeof(double) * (size_t)n);
+  memset(s->Ta, 0, sizeof(double) * (size_t)n);
+  int64_t *pr = NULL;
+  int64_t P = pairs_of(s, off, &pr);
+  pres *res = (pres *)malloc(sizeof(pres) * (size_t)(P > 0 ? P : 1));
+#pragma omp parallel for schedule(dynamic, 256)
+  for (int64_t k = 0; k < P; ++k) {
+    int64_t i = pr[2 * k], j = pr[2 * k + 1];
     double xi[3] = {s->x[i], s->x[n + i], s->x[2 * n + i]};
     double ui[3] = {s->u[i], s->u[n + i], s->u[2 * n + i]};
     double wi[3] = {s->w[i], s->w[n + i], s->w[2 * n + i]};
-    for (int64_t j = i + 1; j < n; ++j) {
-      double xj[3] = {s->x[j], s->x[n + j], s->x[2 * n + j]};
-      double r[3];
-      int sy;
-      min_image(p, off, xi, xj, r, &sy);
-      if (!is_pair(p, r, s->a[i], s->a[j])) continue;
-      double uj[3] = {s->u[j], s->u[n + j], s->u[2 * n + j]};
-      double wj[3] = {s->w[j], s->w[n + j], s->w[2 * n + j]};
+    double xj[3] = {s->x[j], s->x[n + j], s->x[2 * n + j]};
+    double uj[3] = {s->u[j], s->u[n + j], s->u[2 * n + j]};
+    double wj[3] = {s->w[j], s->w[n + j], s->w[2 * n + j]};
+    int64_t lo = s->id[i] < s->id[j] ? s->id[i] : s->id[j];
+    int64_t hi = s->id[i] < s->id[j] ? s->id[j] : s->id[i];
+    double sgn = s->id[i] < s->id[j] ? 1.0 : -1.0;   /* i->j vs lo->hi */
+    double xo[3] = {0, 0, 0}, ro[3] = {0, 0, 0};
+    int64_t h = hist_find(s, (lo << 32) | hi);
+    if (h >= 0)
+      for (int c = 0; c < 3; ++c) {
+        xo[c] = sgn * s->hxi[3 * h + c];
+        ro[c] = s->hxr[3 * h + c];
+      }
+    pres *q = &res[k];
+    q->fl = pair_eval_core(p, off, xi, xj, ui, uj, wi, wj, s->a[i], s->a[j], xo, ro, q->Fi, q->Fj,
+                           q->Ti, q->Tj, q->S, q->xn, q->rn, q->mag);
+  }
+  double Spair[9] = {0};
+  int64_t hn = 0, hc = 64;
+  hrec *hnew = (hrec *)malloc(sizeof(hrec) * (size_t)hc);
+  int64_t ncont = 0;
+  for (int64_t k = 0; k < P; ++k) {
+    int64_t i = pr[2 * k], j = pr[2 * k + 1];
+    const pres *q = &res[k];
+    for (int c = 0; c < 3; ++c) {
+      s->F[c * n + i] += q->Fi[c]; s->F[c * n + j] += q->Fj[c];
+      s->T[c * n + i] += q->Ti[c]; s->T[c * n + j] += q->Tj[c];
+    }
+    s->Fa[i] += q->mag[0]; s->Fa[j] += q->mag[1];
+    s->Ta[i] += q->mag[2]; s->Ta[j] += q->mag[3];
+    for (int c = 0; c < 9; ++c) Spair[c] += q->S[c];
+    if (q->fl & 2) {
+      ++ncont;
+      if (hn == hc) { hc *= 2; hnew = (hrec *)realloc(hnew, sizeof(hrec) * (size_t)hc); }
       int64_t lo = s->id[i] < s->id[j] ? s->id[i] : s->id[j];
       int64_t hi = s->id[i] < s->id[j] ? s->id[j] : s->id[i];
-      int64_t key = (lo << 32) | hi;
-      double sgn = s->id[i] < s->id[j] ? 1.0 : -1.0;   /* i->j vs lo->hi */
-      double xo[3] = {0, 0, 0}, ro[3] = {0, 0, 0};
-      int64_t h = hist_find(s, key);
-      if (h >= 0)
-        for (int c = 0; c < 3; ++c) {
-          xo[c] = sgn * s->hxi[3 * h + c];
-          ro[c] = s->hxr[3 * h + c];
-        }
-      double Fi[3], Fj[3], Ti[3], Tj[3], S[9], xn[3], rn[3];
-      int fl = orc_pair_eval_full(p, off, xi, xj, ui, uj, wi, wj, s->a[i], s->a[j], xo, ro,
-                                  Fi, Fj, Ti, Tj, S, xn, rn);
-      ++npairs;
+      double sgn = s->id[i] < s->id[j] ? 1.0 : -1.0;
+      hnew[hn].key = (lo << 32) | hi;
       for (int c = 0; c < 3; ++c) {
-        s->F[c * n + i] += Fi[c]; s->F[c * n + j] += Fj[c];
-        s->T[c * n + i] += Ti[c]; s->T[c * n + j] += Tj[c];
+        hnew[hn].xi[c] = sgn * q->xn[c];
+        hnew[hn].xr[c] = q->rn[c];
       }
-      for (int q = 0; q < 9; ++q) Spair[q] += S[q];
-      if (fl & 2) {
-        ++ncont;
-        if (hn == hc) { hc *= 2; hnew = (hrec *)realloc(hnew, sizeof(hrec) * (size_t)hc); }
-        hnew[hn].key = key;
-        for (int c = 0; c < 3; ++c) {
-          hnew[hn].xi[c] = sgn * xn[c];
-          hnew[hn].xr[c] = rn[c];
-        }
-        ++hn;
-      }
+      ++hn;
     }
   }
+  free(res);
+  free(pr);
   /* Stokes drag, Eq. A1, and the single-particle stresslets
    * S^S_i = 20/3 pi eta0 a_i^3 E_inf(x_i) (E_inf at the centre, no Laplacian) */
   double Sein[9] = {0};
@@ -847,6 +1126,8 @@ void orc_forces(orc_sys *s, int commit) {
       s->F[c * n + i] += f[c];
       s->T[c * n + i] += t[c];
     }
+    s->Fa[i] += sqrt(dot3(f, f));
+    s->Ta[i] += sqrt(dot3(t, t));
     double a = s->a[i], Ei[9], Oi[3];
     ambient_rate(orc_flow_rate(p, s->x[n + i]), Ei, Oi);
     for (int q = 0; q < 9; ++q) Sein[q] += 20.0 / 3.0 * M_PI * p->eta0 * a * a * a * Ei[q];
@@ -855,7 +1136,7 @@ void orc_forces(orc_sys *s, int commit) {
    * Eq. 17 averages to zero over L_y) */
   double V = p->L[0] * p->L[1] * p->L[2];
   for (int q = 0; q < 9; ++q) s->sigma[q] = 2.0 * p->eta0 * E[q] + (Sein[q] + Spair[q]) / V;
-  s->npairs_last = npairs;
+  s->npairs_last = P;
   s->ncontacts_last = ncont;
   if (commit) {
     qsort(hnew, (size_t)hn, sizeof(hrec), cmp_hrec);
@@ -876,13 +1157,14 @@ void orc_forces(orc_sys *s, int commit) {
  * force over all others plus Stokes drag, at the current state, time and
  * history: the rows of orc_forces for those particles.  Used to time the
  * oracle on systems where the full O(N^2) evaluation takes minutes. */
-void orc_forces_sampled(orc_sys *s, const int64_t *idx, int64_t m, double *F, double *T) {
+void orc_forces_sampled(orc_sys *s, const int64_t *idx, int64_t m, double *F, double *T,
+                        double *Fa, double *Ta) {
   const orc_params *p = &s->p;
   int64_t n = s->n;
   double off = orc_le_offset(p, s->nstep);
   for (int64_t q = 0; q < m; ++q) {
     int64_t k = idx[q];
-    double f[3] = {0, 0, 0}, t[3] = {0, 0, 0};
+    double f[3] = {0, 0, 0}, t[3] = {0, 0, 0}, fa = 0.0, ta = 0.0;
     for (int64_t o = 0; o < n; ++o) {
       if (o == k) continue;
       int64_t i = k < o ? k : o, j = k < o ? o : k;   /* same orientation as orc_forces */
@@ -907,12 +1189,15 @@ void orc_forces_sampled(orc_sys *s, const int64_t *idx, int64_t m, double *F, do
           ro[c] = s->hxr[3 * h + c];
         }
       double Fi[3], Fj[3], Ti[3], Tj[3], S[9], xn[3], rn[3];
-      orc_pair_eval_full(p, off, xi, xj, ui, uj, wi, wj, s->a[i], s->a[j], xo, ro, Fi, Fj, Ti,
-                         Tj, S, xn, rn);
+      double mag[4];
+      pair_eval_core(p, off, xi, xj, ui, uj, wi, wj, s->a[i], s->a[j], xo, ro, Fi, Fj, Ti, Tj, S,
+                     xn, rn, mag);
       for (int c = 0; c < 3; ++c) {
         f[c] += (k == i) ? Fi[c] : Fj[c];
         t[c] += (k == i) ? Ti[c] : Tj[c];
       }
+      fa += (k == i) ? mag[0] : mag[1];
+      ta += (k == i) ? mag[2] : mag[3];
     }
     double fd[3], td[3];
     stokes_drag(s, k, fd, td);
@@ -922,6 +1207,8 @@ void orc_forces_sampled(orc_sys *s, const int64_t *idx, int64_t m, double *F, do
       F[c * m + q] = f[c];
       T[c * m + q] = t[c];
     }
+    if (Fa) Fa[q] = fa + sqrt(dot3(fd, fd));
+    if (Ta) Ta[q] = ta + sqrt(dot3(td, td));
   }
 }
 
@@ -1021,6 +1308,17 @@ void orc_get_state(const orc_sys *s, double *x, double *u, double *w, double *al
   if (al) memcpy(al, s->al, b);
   if (aw) memcpy(aw, s->aw, b);
 }
+/* Per particle, the sum of the magnitudes of the terms of its force and its
+ * torque in the last evaluation (per pair: contact, each lubrication
+ * sub-term of Eq. A2-A3, electro-chemical, rolling; and the drag): the
+ * rounding error of an evaluation that forms these terms in a given
+ * precision and sums them is bounded in proportion to it, so parity checks
+ * scale by it where the terms cancel. */
+void orc_get_force_scale(const orc_sys *s, double *Fa, double *Ta) {
+  memcpy(Fa, s->Fa, sizeof(double) * (size_t)s->n);
+  memcpy(Ta, s->Ta, sizeof(double) * (size_t)s->n);
+}
+
 void orc_get_forces(const orc_sys *s, double *F, double *T, double sigma[9]) {
   size_t b = sizeof(double) * 3 * (size_t)s->n;
   if (F) memcpy(F, s->F, b);

@@ -93,7 +93,7 @@ BATCH_MIN_N = 256
 ERRORS = {0: "DSS_OK", -1: "DSS_ERR_ARG", -2: "DSS_ERR_BOX", -3: "DSS_ERR_CAPACITY",
           -4: "DSS_ERR_NONFINITE", -5: "DSS_ERR_UNSTABLE", -6: "DSS_ERR_CUDA",
           -7: "DSS_ERR_TIMEOUT", -8: "DSS_ERR_STATE", -9: "DSS_ERR_INTERNAL",
-          -10: "DSS_ERR_SCRATCH_LIMIT"}
+          -10: "DSS_ERR_SCRATCH_LIMIT", -11: "DSS_ERR_NOMEM"}
 
 # every symbol include/dss.h declares, with (restype, argtypes)
 _dp, _ip, _lp, _vp = POINTER(c_double), POINTER(c_int32), POINTER(c_int64), c_void_p
@@ -107,12 +107,14 @@ SIGNATURES = {
     "dss_save": (c_int, [c_void_p, _vp, POINTER(c_size_t)]),
     "dss_load": (c_int, [c_void_p, _vp, c_size_t]),
     "dss_autotune": (c_int, [c_void_p, c_int32, c_int32, _dp, _dp, _dp]),
+    "dss_autotune_kernels": (c_int, [c_void_p, c_int32, _dp, _ip]),
     "dss_selftest_bounded_wait": (c_int, [c_void_p]),
     "dss_rheology": (c_int, [c_void_p, c_int, _vp]),
     "dss_get_images": (c_int, [c_void_p, _vp]),
     "dss_dispersion_mark": (c_int, [c_void_p]),
     "dss_dispersion": (c_int, [c_void_p, _vp]),
     "dss_contact_clusters": (c_int, [c_void_p, _vp, _lp]),
+    "dss_phi_profile": (c_int, [c_void_p, c_int32, c_double, _vp]),
     "dss_adjoint": (c_int, [c_void_p, c_int64, c_int32, _vp, c_int32, _dp, _dp, _vp, _vp, _vp, _vp, _vp]),
     "dss_set_state": (c_int, [c_void_p, _vp, _vp, _vp, _vp, _vp, _vp, _vp, c_int64]),
     "dss_get_state": (c_int, [c_void_p, _vp, _vp, _vp, _vp, _vp]),

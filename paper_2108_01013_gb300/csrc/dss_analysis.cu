@@ -8,7 +8,13 @@
 //     at the last committed step, by a lock-free union-find (a root is only
 //     ever linked below a smaller root, so every parent chain decreases and
 //     every walk ends), labelled by the smallest id of each cluster, which
-//     makes the result unique.
+//     makes the result unique;
+//   - the local volume fraction along the shear-wise direction y by size
+//     class (Sec. III B, Fig. 12): the volume of each sphere inside each of
+//     nbins slabs of the box (the exact integral of its cross-sections,
+//     periodic in y), summed per instance, class and slab as 64-bit integers
+//     in a unit of 2^-62 of the instance's solid volume (integer sums do not
+//     depend on their order, so the profile is reproducible bit for bit).
 #include <climits>
 
 #include "dss_internal.cuh"
@@ -136,7 +142,43 @@ __global__ void k_cc_label(int n, ListBuf H, const int* __restrict__ parent, con
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) label[H.id_of_slot[i]] = minid[parent[i]];
 }
+// ------------------------------------------------------------ phi(y)
+// Volume of the sphere of radius a centred at yc between the planes y0 < y1:
+// the integral of the cross-section pi (a^2 - t^2) over t = y - yc clipped
+// to [-a, a].
+__device__ __forceinline__ double slab_volume(double a, double yc, double y0, double y1) {
+  const double t0 = fmax(y0 - yc, -a), t1 = fmin(y1 - yc, a);
+  if (t1 <= t0) return 0.0;
+  return DSS_PI * (a * a * (t1 - t0) - (t1 * t1 * t1 - t0 * t0 * t0) / 3.0);
+}
+
+// One thread per particle: its volume in every slab it reaches (its images
+// across y = 0 and y = L_y included), class 1 when a > a_split.
+__global__ void k_phi_profile(int n, const InstGeo* __restrict__ ig, StateBuf s, int nbins, double a_split,
+                              const double* __restrict__ unit, unsigned long long* __restrict__ acc) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= n) return;
+  const int inst = s.inst[f];
+  const InstGeo& I = ig[inst];
+  const double y = s.x[n + f], a = s.a[f], Ly = I.L[1], w = Ly / nbins, u = unit[inst];
+  unsigned long long* row = acc + ((size_t)inst * 2 + (a > a_split ? 1 : 0)) * nbins;
+  for (int img = -1; img <= 1; ++img) {
+    const double yc = y + img * Ly;
+    if (yc + a <= 0.0 || yc - a >= Ly) continue;
+    const int b0 = max(0, (int)floor((yc - a) / w)), b1 = min(nbins - 1, (int)floor((yc + a) / w));
+    for (int b = b0; b <= b1; ++b) {
+      const double v = slab_volume(a, yc, b * w, b == nbins - 1 ? Ly : (b + 1) * w);
+      if (v > 0.0) atomicAdd(row + b, (unsigned long long)llrint(v / u));
+    }
+  }
+}
 }  // namespace
+
+void launch_phi_profile(dss_handle* h, int nbins, double a_split, const double* unit, unsigned long long* acc) {
+  const int n = (int)h->n;
+  k_phi_profile<<<(n + kThreads - 1) / kThreads, kThreads, 0, h->stream>>>(n, h->ig, h->st[h->cur], nbins,
+                                                                            a_split, unit, acc);
+}
 
 void launch_images_out(dss_handle* h, int* out) {
   const int n = (int)h->n;

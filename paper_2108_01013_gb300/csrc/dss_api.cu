@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <new>
 #include <vector>
 
 #include "dss_internal.cuh"
@@ -79,6 +80,8 @@ void drop_graphs(dss_handle* h) {
   for (int k = 0; k < 4; ++k) {
     if (h->graph_ok[k]) cudaGraphExecDestroy(h->step_graph[k]);
     h->graph_ok[k] = false;
+    if (h->multi_ok[k]) cudaGraphExecDestroy(h->multi_graph[k]);
+    h->multi_ok[k] = false;
   }
 }
 
@@ -406,6 +409,33 @@ int capture_step(dss_handle* h, int key) {
   return DSS_OK;
 }
 
+// DSS_MULTI_STEPS steps in one graph, starting with the buffers in the
+// roles (cur, hist) of key; each step's kernels skip after an earlier
+// failure exactly as in separate launches.
+int capture_multi(dss_handle* h, int key) {
+  const int cur0 = h->cur, hist0 = h->hist;
+  h->cur = key >> 1;
+  h->hist = key & 1;
+  cudaGraph_t graph;
+  CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  h->capturing = true;
+  for (int k = 0; k < DSS_MULTI_STEPS; ++k) {
+    seq_step(h);
+    h->cur = 1 - h->cur;
+    h->hist = 1 - h->hist;
+  }
+  h->capturing = false;
+  h->cur = cur0;
+  h->hist = hist0;
+  cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+  if (e != cudaSuccess) return DSS_ERR_CUDA;
+  e = cudaGraphInstantiate(&h->multi_graph[key], graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return DSS_ERR_CUDA;
+  h->multi_ok[key] = true;
+  return DSS_OK;
+}
+
 int accumulate_profile(dss_handle* h) {
   CK(cudaStreamSynchronize(h->stream));
   for (int k = 0; k < DSS_PROF_KERNELS; ++k) {
@@ -691,6 +721,20 @@ void prof_mark(dss_handle* h, int k) {
     cudaEventRecord(h->prof_ev[k], h->stream);
 }
 
+// Runs the body of an entry point so that no C++ exception crosses the C ABI:
+// a failed host allocation returns DSS_ERR_NOMEM, anything else
+// DSS_ERR_INTERNAL.
+template <class F>
+static int guard(F&& body) {
+  try {
+    return body();
+  } catch (const std::bad_alloc&) {
+    return DSS_ERR_NOMEM;
+  } catch (...) {
+    return DSS_ERR_INTERNAL;
+  }
+}
+
 extern "C" {
 
 int32_t dss_capacity_estimate(double a_min, double a_max, double a0) {
@@ -716,6 +760,7 @@ const char* dss_strerror(int code) {
     case DSS_ERR_TIMEOUT: return "bounded device wait gave up";
     case DSS_ERR_STATE: return "call out of order (no state loaded)";
     case DSS_ERR_INTERNAL: return "internal consistency check failed";
+    case DSS_ERR_NOMEM: return "host memory allocation failed";
     case DSS_ERR_SCRATCH_LIMIT:
       return "problem too large for the fixed scratch array of dss_pairs_noalloc "
              "(needs n + 3*cells + 17 <= DSS_NOALLOC_SCRATCH_INTS words)";
@@ -725,210 +770,218 @@ const char* dss_strerror(int code) {
 
 int dss_create(dss_handle** out, const dss_params* p, int64_t n, const double box[3],
                void* cuda_stream) {
-  if (!out || !p || !box || n < 2 || n > (int64_t)1 << 30) return DSS_ERR_ARG;
-  *out = nullptr;
-  for (int d = 0; d < 3; ++d)
-    if (!(box[d] > 0.0) || !std::isfinite(box[d])) return DSS_ERR_ARG;
-  if (!valid_params(p)) return DSS_ERR_ARG;
-  const double gd = p->shear_rate, gn = p->gamma_n;
-  return create_handle(out, p, 1, &n, box, &gd, &gn, cuda_stream);
+  return guard([&]() -> int {
+    if (!out || !p || !box || n < 2 || n > (int64_t)1 << 30) return DSS_ERR_ARG;
+    *out = nullptr;
+    for (int d = 0; d < 3; ++d)
+      if (!(box[d] > 0.0) || !std::isfinite(box[d])) return DSS_ERR_ARG;
+    if (!valid_params(p)) return DSS_ERR_ARG;
+    const double gd = p->shear_rate, gn = p->gamma_n;
+    return create_handle(out, p, 1, &n, box, &gd, &gn, cuda_stream);
+  });
 }
 
 int dss_batch_create(dss_handle** out, const dss_params* p, int32_t K, const int64_t* n,
                      const double* box, const double* shear_rate, const double* gamma_n,
                      void* cuda_stream) {
-  if (!out || !p || !n || !box || !shear_rate || K < 1 || K > (1 << 20)) return DSS_ERR_ARG;
-  *out = nullptr;
-  if (!valid_params(p)) return DSS_ERR_ARG;
-  int64_t total = 0;
-  for (int k = 0; k < K; ++k) {
-    // a pair block (256 owners) spans at most two instances
-    if (n[k] < (K > 1 ? DSS_BATCH_MIN_N : 2)) return DSS_ERR_ARG;
-    total += n[k];
-    if (total > (int64_t)1 << 30) return DSS_ERR_ARG;
-    for (int d = 0; d < 3; ++d)
-      if (!(box[3 * k + d] > 0.0) || !std::isfinite(box[3 * k + d])) return DSS_ERR_ARG;
-    if (!std::isfinite(shear_rate[k])) return DSS_ERR_ARG;
-    if (gamma_n && !(gamma_n[k] >= 0.0 && std::isfinite(gamma_n[k]))) return DSS_ERR_ARG;
-  }
-  std::vector<double> gn(K);
-  for (int k = 0; k < K; ++k) gn[k] = gamma_n ? gamma_n[k] : p->gamma_n;
-  return create_handle(out, p, K, n, box, shear_rate, gn.data(), cuda_stream);
+  return guard([&]() -> int {
+    if (!out || !p || !n || !box || !shear_rate || K < 1 || K > (1 << 20)) return DSS_ERR_ARG;
+    *out = nullptr;
+    if (!valid_params(p)) return DSS_ERR_ARG;
+    int64_t total = 0;
+    for (int k = 0; k < K; ++k) {
+      // a pair block (256 owners) spans at most two instances
+      if (n[k] < (K > 1 ? DSS_BATCH_MIN_N : 2)) return DSS_ERR_ARG;
+      total += n[k];
+      if (total > (int64_t)1 << 30) return DSS_ERR_ARG;
+      for (int d = 0; d < 3; ++d)
+        if (!(box[3 * k + d] > 0.0) || !std::isfinite(box[3 * k + d])) return DSS_ERR_ARG;
+      if (!std::isfinite(shear_rate[k])) return DSS_ERR_ARG;
+      if (gamma_n && !(gamma_n[k] >= 0.0 && std::isfinite(gamma_n[k]))) return DSS_ERR_ARG;
+    }
+    std::vector<double> gn(K);
+    for (int k = 0; k < K; ++k) gn[k] = gamma_n ? gamma_n[k] : p->gamma_n;
+    return create_handle(out, p, K, n, box, shear_rate, gn.data(), cuda_stream);
+  });
 }
 
 int dss_set_state(dss_handle* h, const double* x, const double* a, const int32_t* ids,
                   const double* u, const double* w, const double* alpha_lin,
                   const double* alpha_ang, int64_t nstep) {
-  if (!h || !x || !a || nstep < 0) return DSS_ERR_ARG;
-  if ((alpha_lin == nullptr) != (alpha_ang == nullptr)) return DSS_ERR_ARG;
-  ENTER(h);
-  const int64_t n = h->n;
-  // host-side validation of radii, positions and ids
-  std::vector<double> ha(n), hx(3 * n);
-  CK(cudaMemcpy(ha.data(), a, sizeof(double) * n, cudaMemcpyDefault));
-  CK(cudaMemcpy(hx.data(), x, sizeof(double) * 3 * n, cudaMemcpyDefault));
-  double amin = INFINITY, amax = 0.0;
-  for (int64_t i = 0; i < n; ++i) {
-    if (!(ha[i] > 0.0) || !std::isfinite(ha[i])) return DSS_ERR_ARG;
-    amin = std::min(amin, ha[i]);
-    amax = std::max(amax, ha[i]);
-  }
-  // instance of each index (instance-major); positions inside their box
-  std::vector<int32_t> imap(n);
-  std::vector<int64_t> ibeg(h->K + 1, 0);
-  for (int k = 0; k < h->K; ++k) {
-    ibeg[k + 1] = ibeg[k] + h->inst_n[k];
-    for (int64_t i = ibeg[k]; i < ibeg[k + 1]; ++i) imap[i] = k;
-  }
-  for (int d = 0; d < 3; ++d)
+  return guard([&]() -> int {
+    if (!h || !x || !a || nstep < 0) return DSS_ERR_ARG;
+    if ((alpha_lin == nullptr) != (alpha_ang == nullptr)) return DSS_ERR_ARG;
+    ENTER(h);
+    const int64_t n = h->n;
+    // host-side validation of radii, positions and ids
+    std::vector<double> ha(n), hx(3 * n);
+    CK(cudaMemcpy(ha.data(), a, sizeof(double) * n, cudaMemcpyDefault));
+    CK(cudaMemcpy(hx.data(), x, sizeof(double) * 3 * n, cudaMemcpyDefault));
+    double amin = INFINITY, amax = 0.0;
     for (int64_t i = 0; i < n; ++i) {
-      double v = hx[d * n + i];
-      if (!(v >= 0.0 && v < h->inst_box[3 * imap[i] + d])) return DSS_ERR_ARG;
+      if (!(ha[i] > 0.0) || !std::isfinite(ha[i])) return DSS_ERR_ARG;
+      amin = std::min(amin, ha[i]);
+      amax = std::max(amax, ha[i]);
     }
-  std::vector<int32_t> hid(n);
-  if (ids) {
-    // ids of instance k are a permutation of its own index range
-    CK(cudaMemcpy(hid.data(), ids, sizeof(int32_t) * n, cudaMemcpyDefault));
-    std::vector<char> seen(n, 0);
-    for (int64_t i = 0; i < n; ++i) {
-      if (hid[i] < 0 || hid[i] >= n || seen[hid[i]] || imap[hid[i]] != imap[i]) return DSS_ERR_ARG;
-      seen[hid[i]] = 1;
+    // instance of each index (instance-major); positions inside their box
+    std::vector<int32_t> imap(n);
+    std::vector<int64_t> ibeg(h->K + 1, 0);
+    for (int k = 0; k < h->K; ++k) {
+      ibeg[k + 1] = ibeg[k] + h->inst_n[k];
+      for (int64_t i = ibeg[k]; i < ibeg[k + 1]; ++i) imap[i] = k;
     }
-  } else {
-    for (int64_t i = 0; i < n; ++i) hid[i] = (int32_t)i;
-  }
-  if (!h->sized || amax > h->a_max || amin < h->a_min) {
-    if (h->sized) free_buffers(h);
+    for (int d = 0; d < 3; ++d)
+      for (int64_t i = 0; i < n; ++i) {
+        double v = hx[d * n + i];
+        if (!(v >= 0.0 && v < h->inst_box[3 * imap[i] + d])) return DSS_ERR_ARG;
+      }
+    std::vector<int32_t> hid(n);
+    if (ids) {
+      // ids of instance k are a permutation of its own index range
+      CK(cudaMemcpy(hid.data(), ids, sizeof(int32_t) * n, cudaMemcpyDefault));
+      std::vector<char> seen(n, 0);
+      for (int64_t i = 0; i < n; ++i) {
+        if (hid[i] < 0 || hid[i] >= n || seen[hid[i]] || imap[hid[i]] != imap[i]) return DSS_ERR_ARG;
+        seen[hid[i]] = 1;
+      }
+    } else {
+      for (int64_t i = 0; i < n; ++i) hid[i] = (int32_t)i;
+    }
+    if (!h->sized || amax > h->a_max || amin < h->a_min) {
+      if (h->sized) free_buffers(h);
+      drop_graphs(h);
+      h->a_min = amin;
+      h->a_max = amax;
+      int r = geometry(h);
+      if (r) return r;
+      r = alloc_buffers(h);
+      if (r) { free_buffers(h); return r; }
+    }
+    for (int k = 0; k < h->K; ++k) {
+      double s3 = 0.0;
+      for (int64_t i = ibeg[k]; i < ibeg[k + 1]; ++i) s3 += ha[i] * ha[i] * ha[i];
+      h->ig_host[k].sumA3 = s3;
+    }
     drop_graphs(h);
-    h->a_min = amin;
-    h->a_max = amax;
-    int r = geometry(h);
-    if (r) return r;
-    r = alloc_buffers(h);
-    if (r) { free_buffers(h); return r; }
-  }
-  for (int k = 0; k < h->K; ++k) {
-    double s3 = 0.0;
-    for (int64_t i = ibeg[k]; i < ibeg[k + 1]; ++i) s3 += ha[i] * ha[i] * ha[i];
-    h->ig_host[k].sumA3 = s3;
-  }
-  drop_graphs(h);
-  h->cur = 0;
-  h->hist = 0;
-  h->mean_steps = 0;
-  StateBuf& s = h->st[0];
-  CK(cudaMemcpyAsync(h->ig, h->ig_host, sizeof(InstGeo) * h->K, cudaMemcpyHostToDevice, h->stream));
-  CK(cudaMemcpyAsync(h->inst_map, imap.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, h->stream));
-  CK(cudaMemcpyAsync(s.inst, h->inst_map, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, h->stream));
-  {
-    // size classes (all 0 with one cell list), by index and by id
-    std::vector<unsigned char> cu(n), cid(n);
-    for (int64_t i = 0; i < n; ++i) {
-      int c = h->g.nclass > 1 ? class_of(h->p, ha[i], h->cell_edge) : 0;
-      if (c > h->g.nclass - 1) c = h->g.nclass - 1;
-      cu[i] = (unsigned char)c;
-      cid[hid[i]] = (unsigned char)c;
+    h->cur = 0;
+    h->hist = 0;
+    h->mean_steps = 0;
+    StateBuf& s = h->st[0];
+    CK(cudaMemcpyAsync(h->ig, h->ig_host, sizeof(InstGeo) * h->K, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->inst_map, imap.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(s.inst, h->inst_map, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, h->stream));
+    {
+      // size classes (all 0 with one cell list), by index and by id
+      std::vector<unsigned char> cu(n), cid(n);
+      for (int64_t i = 0; i < n; ++i) {
+        int c = h->g.nclass > 1 ? class_of(h->p, ha[i], h->cell_edge) : 0;
+        if (c > h->g.nclass - 1) c = h->g.nclass - 1;
+        cu[i] = (unsigned char)c;
+        cid[hid[i]] = (unsigned char)c;
+      }
+      CK(cudaMemcpyAsync(s.cls, cu.data(), n, cudaMemcpyHostToDevice, h->stream));
+      CK(cudaMemcpyAsync(h->cls_map, cid.data(), n, cudaMemcpyHostToDevice, h->stream));
+      CK(cudaStreamSynchronize(h->stream));
     }
-    CK(cudaMemcpyAsync(s.cls, cu.data(), n, cudaMemcpyHostToDevice, h->stream));
-    CK(cudaMemcpyAsync(h->cls_map, cid.data(), n, cudaMemcpyHostToDevice, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
-  }
-  CK(cudaMemsetAsync(h->sigma_sum, 0, 9 * sizeof(double) * h->K, h->stream));
-  CK(cudaMemcpyAsync(s.x, hx.data(), sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->stream));
-  CK(cudaMemcpyAsync(s.a, ha.data(), sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
-  CK(cudaMemcpyAsync(s.id, hid.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, h->stream));
-  CK(cudaMemsetAsync(s.iy, 0, sizeof(int) * n, h->stream));
-  h->marked = false;
-  {
-    std::vector<double> aid(n);
-    for (int64_t i = 0; i < n; ++i) aid[hid[i]] = ha[i];
-    CK(cudaMemcpyAsync(h->a_by_id, aid.data(), sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
-  }
-  if (u) CK(cudaMemcpyAsync(s.u, u, sizeof(double) * 3 * n, cudaMemcpyDefault, h->stream));
-  if (w) CK(cudaMemcpyAsync(s.w, w, sizeof(double) * 3 * n, cudaMemcpyDefault, h->stream));
-  const int nb = (int)((n + 255) / 256);
-  if (!u || !w) k_default_vel<<<nb, 256, 0, h->stream>>>(h->g, (int)n, s.x, h->ig, s.inst, s.u, s.w, !u, !w);
-  if (alpha_lin) {
-    CK(cudaMemcpyAsync(s.al, alpha_lin, sizeof(double) * 3 * n, cudaMemcpyDefault, h->stream));
-    CK(cudaMemcpyAsync(s.aw, alpha_ang, sizeof(double) * 3 * n, cudaMemcpyDefault, h->stream));
-  }
-  // empty history: no rows, identity id map
-  for (int b = 0; b < 2; ++b) {
-    CK(cudaMemsetAsync(h->lb[b].count, 0, sizeof(int) * n, h->stream));
-    CK(cudaMemsetAsync(h->lb[b].start, 0, sizeof(int) * (n + 1), h->stream));
-    k_iota<<<nb, 256, 0, h->stream>>>((int)n, h->lb[b].slot_of_id);
-    k_iota<<<nb, 256, 0, h->stream>>>((int)n, h->lb[b].id_of_slot);
-  }
-  k_set_nstep<<<1, 1, 0, h->stream>>>(h->status, (long long)nstep);
-  CK(cudaGetLastError());
-  h->have_state = true;
-  h->host_steps_done = 0;
-  if (alpha_lin) {
-    int r0 = sync_status(h);
-    if (r0) return r0;
-  }
-  if (!alpha_lin) {
-    // alpha^0 from one force evaluation at the initial state (empty history)
-    seq_sort_enum(h, false, 0);
-    h->cur = 1 - h->cur;
-    int rc = ensure_pair_capacity(h, 1 - h->hist);
-    if (rc) return rc;
-    launch_forces(h, h->cur, 1 - h->hist, h->hist, 0, G_ACCEL, nullptr, nullptr);
+    CK(cudaMemsetAsync(h->sigma_sum, 0, 9 * sizeof(double) * h->K, h->stream));
+    CK(cudaMemcpyAsync(s.x, hx.data(), sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(s.a, ha.data(), sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(s.id, hid.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemsetAsync(s.iy, 0, sizeof(int) * n, h->stream));
+    h->marked = false;
+    {
+      std::vector<double> aid(n);
+      for (int64_t i = 0; i < n; ++i) aid[hid[i]] = ha[i];
+      CK(cudaMemcpyAsync(h->a_by_id, aid.data(), sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+    }
+    if (u) CK(cudaMemcpyAsync(s.u, u, sizeof(double) * 3 * n, cudaMemcpyDefault, h->stream));
+    if (w) CK(cudaMemcpyAsync(s.w, w, sizeof(double) * 3 * n, cudaMemcpyDefault, h->stream));
+    const int nb = (int)((n + 255) / 256);
+    if (!u || !w) k_default_vel<<<nb, 256, 0, h->stream>>>(h->g, (int)n, s.x, h->ig, s.inst, s.u, s.w, !u, !w);
+    if (alpha_lin) {
+      CK(cudaMemcpyAsync(s.al, alpha_lin, sizeof(double) * 3 * n, cudaMemcpyDefault, h->stream));
+      CK(cudaMemcpyAsync(s.aw, alpha_ang, sizeof(double) * 3 * n, cudaMemcpyDefault, h->stream));
+    }
+    // empty history: no rows, identity id map
+    for (int b = 0; b < 2; ++b) {
+      CK(cudaMemsetAsync(h->lb[b].count, 0, sizeof(int) * n, h->stream));
+      CK(cudaMemsetAsync(h->lb[b].start, 0, sizeof(int) * (n + 1), h->stream));
+      k_iota<<<nb, 256, 0, h->stream>>>((int)n, h->lb[b].slot_of_id);
+      k_iota<<<nb, 256, 0, h->stream>>>((int)n, h->lb[b].id_of_slot);
+    }
+    k_set_nstep<<<1, 1, 0, h->stream>>>(h->status, (long long)nstep);
     CK(cudaGetLastError());
-    int r = sync_status(h);
-    if (r) return r;
-    if ((r = status_error(h))) { clear_err(h); return r; }
-  }
-  return DSS_OK;
+    h->have_state = true;
+    h->host_steps_done = 0;
+    if (alpha_lin) {
+      int r0 = sync_status(h);
+      if (r0) return r0;
+    }
+    if (!alpha_lin) {
+      // alpha^0 from one force evaluation at the initial state (empty history)
+      seq_sort_enum(h, false, 0);
+      h->cur = 1 - h->cur;
+      int rc = ensure_pair_capacity(h, 1 - h->hist);
+      if (rc) return rc;
+      launch_forces(h, h->cur, 1 - h->hist, h->hist, 0, G_ACCEL, nullptr, nullptr);
+      CK(cudaGetLastError());
+      int r = sync_status(h);
+      if (r) return r;
+      if ((r = status_error(h))) { clear_err(h); return r; }
+    }
+    return DSS_OK;
+  });
 }
 
 int dss_get_state(dss_handle* h, double* x, double* u, double* w, double* alpha_lin,
                   double* alpha_ang) {
-  if (!h) return DSS_ERR_ARG;
-  if (!h->have_state) return DSS_ERR_STATE;
-  ENTER(h);
-  const int n = (int)h->n;
-  const StateBuf& s = h->st[h->cur];
-  double* out[5] = {x, u, w, alpha_lin, alpha_ang};
-  // device outputs are written in place by the scatter; host outputs go
-  // through the staging area, then out by a coalesced copy kernel (mapped
-  // pinned memory) or the copy engine (pageable memory)
-  Dst5 direct, staged, views;
-  for (int k = 0; k < 5; ++k) {
-    direct.d[k] = staged.d[k] = views.d[k] = nullptr;
-    if (!out[k]) continue;
-    cudaPointerAttributes at;
-    const bool is_dev = cudaPointerGetAttributes(&at, out[k]) == cudaSuccess && at.type == cudaMemoryTypeDevice;
-    cudaGetLastError();
-    if (is_dev) {
-      direct.d[k] = out[k];
-    } else {
-      staged.d[k] = h->stage + (size_t)k * 3 * n;
-      views.d[k] = static_cast<double*>(const_cast<void*>(device_view(out[k])));
+  return guard([&]() -> int {
+    if (!h) return DSS_ERR_ARG;
+    if (!h->have_state) return DSS_ERR_STATE;
+    ENTER(h);
+    const int n = (int)h->n;
+    const StateBuf& s = h->st[h->cur];
+    double* out[5] = {x, u, w, alpha_lin, alpha_ang};
+    // device outputs are written in place by the scatter; host outputs go
+    // through the staging area, then out by a coalesced copy kernel (mapped
+    // pinned memory) or the copy engine (pageable memory)
+    Dst5 direct, staged, views;
+    for (int k = 0; k < 5; ++k) {
+      direct.d[k] = staged.d[k] = views.d[k] = nullptr;
+      if (!out[k]) continue;
+      cudaPointerAttributes at;
+      const bool is_dev = cudaPointerGetAttributes(&at, out[k]) == cudaSuccess && at.type == cudaMemoryTypeDevice;
+      cudaGetLastError();
+      if (is_dev) {
+        direct.d[k] = out[k];
+      } else {
+        staged.d[k] = h->stage + (size_t)k * 3 * n;
+        views.d[k] = static_cast<double*>(const_cast<void*>(device_view(out[k])));
+      }
     }
-  }
-  Dst5 all = direct;
-  for (int k = 0; k < 5; ++k)
-    if (staged.d[k]) all.d[k] = staged.d[k];
-  k_state_out<<<(n + 255) / 256, 256, 0, h->stream>>>(n, s, all);
-  Dst5 src_c, dst_c;
-  bool any_view = false;
-  for (int k = 0; k < 5; ++k) {
-    src_c.d[k] = dst_c.d[k] = nullptr;
-    if (!staged.d[k]) continue;
-    if (views.d[k]) {
-      src_c.d[k] = staged.d[k];
-      dst_c.d[k] = views.d[k];
-      any_view = true;
-    } else {
-      CK(cudaMemcpyAsync(out[k], staged.d[k], sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, h->stream));
+    Dst5 all = direct;
+    for (int k = 0; k < 5; ++k)
+      if (staged.d[k]) all.d[k] = staged.d[k];
+    k_state_out<<<(n + 255) / 256, 256, 0, h->stream>>>(n, s, all);
+    Dst5 src_c, dst_c;
+    bool any_view = false;
+    for (int k = 0; k < 5; ++k) {
+      src_c.d[k] = dst_c.d[k] = nullptr;
+      if (!staged.d[k]) continue;
+      if (views.d[k]) {
+        src_c.d[k] = staged.d[k];
+        dst_c.d[k] = views.d[k];
+        any_view = true;
+      } else {
+        CK(cudaMemcpyAsync(out[k], staged.d[k], sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, h->stream));
+      }
     }
-  }
-  if (any_view) k_copy5<<<std::min((3 * n + 255) / 256, 8 * h->sms), 256, 0, h->stream>>>(3 * (int64_t)n, src_c, dst_c);
-  CK(cudaGetLastError());
-  CK(cudaStreamSynchronize(h->stream));
-  return DSS_OK;
+    if (any_view) k_copy5<<<std::min((3 * n + 255) / 256, 8 * h->sms), 256, 0, h->stream>>>(3 * (int64_t)n, src_c, dst_c);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(h->stream));
+    return DSS_OK;
+  });
 }
 
 int dss_neighbour_build(dss_handle* h) {
@@ -945,30 +998,32 @@ int dss_neighbour_build(dss_handle* h) {
 }
 
 int dss_get_pairs(dss_handle* h, int64_t* lohi, int64_t cap, int64_t* count) {
-  if (!h || !count || cap < 0 || (cap > 0 && !lohi)) return DSS_ERR_ARG;
-  if (!h->have_state) return DSS_ERR_STATE;
-  ENTER(h);
-  const int list = h->last_list;
-  int P = 0;
-  CK(cudaMemcpyAsync(&P, h->lb[list].start + h->n, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-  CK(cudaStreamSynchronize(h->stream));
-  *count = P;
-  if (P == 0 || cap == 0) return DSS_OK;
-  // scratch: the partner-row buffer (n*M slots of >= 32 bytes >= 16 bytes per pair)
-  long long* dev = (long long*)h->bw_rec;
-  launch_pairs_out(h, list, dev);
-  std::vector<long long> hp(2 * (size_t)P);
-  CK(cudaMemcpyAsync(hp.data(), dev, sizeof(long long) * 2 * P, cudaMemcpyDeviceToHost, h->stream));
-  CK(cudaStreamSynchronize(h->stream));
-  std::vector<std::pair<long long, long long>> v(P);
-  for (int p = 0; p < P; ++p) v[p] = {hp[2 * p], hp[2 * p + 1]};
-  std::sort(v.begin(), v.end());
-  int64_t m = std::min<int64_t>(cap, P);
-  for (int64_t p = 0; p < m; ++p) {
-    lohi[2 * p] = v[p].first;
-    lohi[2 * p + 1] = v[p].second;
-  }
-  return DSS_OK;
+  return guard([&]() -> int {
+    if (!h || !count || cap < 0 || (cap > 0 && !lohi)) return DSS_ERR_ARG;
+    if (!h->have_state) return DSS_ERR_STATE;
+    ENTER(h);
+    const int list = h->last_list;
+    int P = 0;
+    CK(cudaMemcpyAsync(&P, h->lb[list].start + h->n, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    *count = P;
+    if (P == 0 || cap == 0) return DSS_OK;
+    // scratch: the partner-row buffer (n*M slots of >= 32 bytes >= 16 bytes per pair)
+    long long* dev = (long long*)h->bw_rec;
+    launch_pairs_out(h, list, dev);
+    std::vector<long long> hp(2 * (size_t)P);
+    CK(cudaMemcpyAsync(hp.data(), dev, sizeof(long long) * 2 * P, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    std::vector<std::pair<long long, long long>> v(P);
+    for (int p = 0; p < P; ++p) v[p] = {hp[2 * p], hp[2 * p + 1]};
+    std::sort(v.begin(), v.end());
+    int64_t m = std::min<int64_t>(cap, P);
+    for (int64_t p = 0; p < m; ++p) {
+      lohi[2 * p] = v[p].first;
+      lohi[2 * p + 1] = v[p].second;
+    }
+    return DSS_OK;
+  });
 }
 
 int dss_force_eval(dss_handle* h, double* F, double* T) {
@@ -992,75 +1047,85 @@ int dss_force_eval(dss_handle* h, double* F, double* T) {
 }
 
 int dss_step(dss_handle* h, int64_t nsteps) {
-  if (!h || nsteps < 0) return DSS_ERR_ARG;
-  if (!h->have_state) return DSS_ERR_STATE;
-  ENTER(h);
-  int64_t remaining = nsteps;
-  int retries = 0;
-  h->last_step_ms = 0.0;
-  if (!h->step_ev[0]) {
-    CK(cudaEventCreate(&h->step_ev[0]));
-    CK(cudaEventCreate(&h->step_ev[1]));
-  }
-  while (remaining > 0) {
-    int r;
-    // the host mirror holds the counter of the last synchronisation; only
-    // dss_step and dss_set_state change it, and both end synchronised
-    const int steps0 = h->status_host->w[ST_STEPS];
-    const int cur0 = h->cur, hist0 = h->hist;
-    int c = cur0, hs = hist0;
-    for (int64_t k = 0; k < remaining; ++k) {
-      if (!h->graph_ok[c * 2 + hs]) {
-        h->cur = c;
-        h->hist = hs;
-        r = capture_step(h, c * 2 + hs);
+  return guard([&]() -> int {
+    if (!h || nsteps < 0) return DSS_ERR_ARG;
+    if (!h->have_state) return DSS_ERR_STATE;
+    ENTER(h);
+    int64_t remaining = nsteps;
+    int retries = 0;
+    h->last_step_ms = 0.0;
+    if (!h->step_ev[0]) {
+      CK(cudaEventCreate(&h->step_ev[0]));
+      CK(cudaEventCreate(&h->step_ev[1]));
+    }
+    while (remaining > 0) {
+      int r;
+      // the host mirror holds the counter of the last synchronisation; only
+      // dss_step and dss_set_state change it, and both end synchronised
+      const int steps0 = h->status_host->w[ST_STEPS];
+      const int cur0 = h->cur, hist0 = h->hist;
+      int c = cur0, hs = hist0;
+      for (int64_t k = 0; k < remaining; ++k) {
+        if (!h->graph_ok[c * 2 + hs]) {
+          h->cur = c;
+          h->hist = hs;
+          r = capture_step(h, c * 2 + hs);
+          if (r) return r;
+        }
+        c = 1 - c;
+        hs = 1 - hs;
+      }
+      c = cur0;
+      hs = hist0;
+      // runs of DSS_MULTI_STEPS steps go out as one graph launch (not while
+      // profiling, which times each step's kernels)
+      const int64_t multi = h->profiling ? 0 : remaining / DSS_MULTI_STEPS;
+      if (multi > 0 && !h->multi_ok[c * 2 + hs]) {
+        r = capture_multi(h, c * 2 + hs);
         if (r) return r;
       }
-      c = 1 - c;
-      hs = 1 - hs;
-    }
-    c = cur0;
-    hs = hist0;
-    CK(cudaEventRecord(h->step_ev[0], h->stream));
-    for (int64_t k = 0; k < remaining; ++k) {
-      const int key = c * 2 + hs;
-      CK(cudaGraphLaunch(h->step_graph[key], h->stream));
-      if (h->profiling) {
-        r = accumulate_profile(h);
-        if (r) return r;
+      CK(cudaEventRecord(h->step_ev[0], h->stream));
+      for (int64_t k = 0; k < multi; ++k) CK(cudaGraphLaunch(h->multi_graph[c * 2 + hs], h->stream));
+      for (int64_t k = multi * DSS_MULTI_STEPS; k < remaining; ++k) {
+        const int key = c * 2 + hs;
+        CK(cudaGraphLaunch(h->step_graph[key], h->stream));
+        if (h->profiling) {
+          r = accumulate_profile(h);
+          if (r) return r;
+        }
+        c = 1 - c;
+        hs = 1 - hs;
       }
-      c = 1 - c;
-      hs = 1 - hs;
-    }
-    CK(cudaEventRecord(h->step_ev[1], h->stream));
-    r = sync_status(h);
-    if (r) return r;
-    {
-      float ms = 0.f;
-      CK(cudaEventElapsedTime(&ms, h->step_ev[0], h->step_ev[1]));
-      h->last_step_ms += ms;
-    }
-    const int done = h->status_host->w[ST_STEPS] - steps0;
-    h->cur = (done & 1) ? 1 - cur0 : cur0;
-    h->hist = (done & 1) ? 1 - hist0 : hist0;
-    h->host_steps_done += done;
-    h->mean_steps += done;
-    remaining -= done;
-    if (done > 0) h->last_list = h->hist;
-    const int err = status_error(h);
-    if (!err) break;
-    clear_err(h);
-    // a pair-capacity overflow is recovered by growing the pair buffers
-    const int P = h->status_host->w[ST_NPAIRS];
-    if (err == DSS_ERR_CAPACITY && P > h->pcap && retries < 4) {
-      ++retries;
-      r = alloc_pair_buffers(h, (int64_t)(P * 1.25) + 1024, true);
+      CK(cudaEventRecord(h->step_ev[1], h->stream));
+      r = sync_status(h);
       if (r) return r;
-      continue;
+      {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, h->step_ev[0], h->step_ev[1]));
+        h->last_step_ms += ms;
+      }
+      const int done = h->status_host->w[ST_STEPS] - steps0;
+      h->cur = (done & 1) ? 1 - cur0 : cur0;
+      h->hist = (done & 1) ? 1 - hist0 : hist0;
+      h->host_steps_done += done;
+      h->mean_steps += done;
+      remaining -= done;
+      if (done > 0) h->last_list = h->hist;
+      const int err = status_error(h);
+      if (!err) break;
+      clear_err(h);
+      // a pair-capacity overflow is recovered by growing the pair buffers
+      const int P = h->status_host->w[ST_NPAIRS];
+      if (err == DSS_ERR_CAPACITY && P > h->pcap && retries < 4) {
+        ++retries;
+        r = alloc_pair_buffers(h, (int64_t)(P * 1.25) + 1024, true);
+        if (r) return r;
+        continue;
+      }
+      return err;
     }
-    return err;
-  }
-  return DSS_OK;
+    return DSS_OK;
+  });
 }
 
 int dss_stress(dss_handle* h, double sigma[9]) {
@@ -1073,52 +1138,56 @@ int dss_stress(dss_handle* h, double sigma[9]) {
 }
 
 int dss_batch_stress(dss_handle* h, double* sigma, double* sigma_mean, int64_t* steps, int reset) {
-  if (!h) return DSS_ERR_ARG;
-  if (!h->have_state) return DSS_ERR_STATE;
-  ENTER(h);
-  const size_t b = 9 * sizeof(double) * h->K;
-  if (sigma) CK(cudaMemcpyAsync(sigma, h->sigma, b, cudaMemcpyDefault, h->stream));
-  if (sigma_mean) {
-    std::vector<double> sum(9 * (size_t)h->K);
-    CK(cudaMemcpyAsync(sum.data(), h->sigma_sum, b, cudaMemcpyDeviceToHost, h->stream));
+  return guard([&]() -> int {
+    if (!h) return DSS_ERR_ARG;
+    if (!h->have_state) return DSS_ERR_STATE;
+    ENTER(h);
+    const size_t b = 9 * sizeof(double) * h->K;
+    if (sigma) CK(cudaMemcpyAsync(sigma, h->sigma, b, cudaMemcpyDefault, h->stream));
+    if (sigma_mean) {
+      std::vector<double> sum(9 * (size_t)h->K);
+      CK(cudaMemcpyAsync(sum.data(), h->sigma_sum, b, cudaMemcpyDeviceToHost, h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+      const double c = h->mean_steps > 0 ? 1.0 / (double)h->mean_steps : 0.0;
+      for (auto& v : sum) v *= c;
+      CK(cudaMemcpyAsync(sigma_mean, sum.data(), b, cudaMemcpyDefault, h->stream));
+    }
+    if (steps) *steps = h->mean_steps;
+    if (reset) {
+      CK(cudaMemsetAsync(h->sigma_sum, 0, b, h->stream));
+      h->mean_steps = 0;
+    }
     CK(cudaStreamSynchronize(h->stream));
-    const double c = h->mean_steps > 0 ? 1.0 / (double)h->mean_steps : 0.0;
-    for (auto& v : sum) v *= c;
-    CK(cudaMemcpyAsync(sigma_mean, sum.data(), b, cudaMemcpyDefault, h->stream));
-  }
-  if (steps) *steps = h->mean_steps;
-  if (reset) {
-    CK(cudaMemsetAsync(h->sigma_sum, 0, b, h->stream));
-    h->mean_steps = 0;
-  }
-  CK(cudaStreamSynchronize(h->stream));
-  return DSS_OK;
+    return DSS_OK;
+  });
 }
 
 int32_t dss_batch_size(const dss_handle* h) { return h ? h->K : 0; }
 
 int dss_rheology(dss_handle* h, int mean, double* out) {
-  if (!h || !out) return DSS_ERR_ARG;
-  if (!h->have_state) return DSS_ERR_STATE;
-  const int K = h->K;
-  std::vector<double> S(9 * (size_t)K), r(6 * (size_t)K);
-  int rc = mean ? dss_batch_stress(h, nullptr, S.data(), nullptr, 0) : dss_batch_stress(h, S.data(), nullptr, nullptr, 0);
-  if (rc) return rc;
-  for (int k = 0; k < K; ++k) {
-    const double* s = &S[9 * (size_t)k];
-    const double g = h->p.eta0 * h->inst_gdot[k];
-    if (!(g != 0.0)) return DSS_ERR_ARG;
-    const double pi = -(s[0] + s[4] + s[8]) / 3.0;
-    double* o = &r[6 * (size_t)k];
-    o[0] = s[1];
-    o[1] = s[0] - s[4];
-    o[2] = s[4] - s[8];
-    o[3] = pi;
-    o[4] = s[1] / g;
-    o[5] = pi / g;
-  }
-  CK(cudaMemcpy(out, r.data(), sizeof(double) * r.size(), cudaMemcpyDefault));
-  return DSS_OK;
+  return guard([&]() -> int {
+    if (!h || !out) return DSS_ERR_ARG;
+    if (!h->have_state) return DSS_ERR_STATE;
+    const int K = h->K;
+    std::vector<double> S(9 * (size_t)K), r(6 * (size_t)K);
+    int rc = mean ? dss_batch_stress(h, nullptr, S.data(), nullptr, 0) : dss_batch_stress(h, S.data(), nullptr, nullptr, 0);
+    if (rc) return rc;
+    for (int k = 0; k < K; ++k) {
+      const double* s = &S[9 * (size_t)k];
+      const double g = h->p.eta0 * h->inst_gdot[k];
+      if (!(g != 0.0)) return DSS_ERR_ARG;
+      const double pi = -(s[0] + s[4] + s[8]) / 3.0;
+      double* o = &r[6 * (size_t)k];
+      o[0] = s[1];
+      o[1] = s[0] - s[4];
+      o[2] = s[4] - s[8];
+      o[3] = pi;
+      o[4] = s[1] / g;
+      o[5] = pi / g;
+    }
+    CK(cudaMemcpy(out, r.data(), sizeof(double) * r.size(), cudaMemcpyDefault));
+    return DSS_OK;
+  });
 }
 
 int dss_get_images(dss_handle* h, int32_t* iy) {
@@ -1150,51 +1219,101 @@ int dss_dispersion_mark(dss_handle* h) {
   return DSS_OK;
 }
 
+int dss_phi_profile(dss_handle* h, int32_t nbins, double a_split, double* out) {
+  return guard([&]() -> int {
+    if (!h || !out || nbins < 1 || nbins > (1 << 20) || !std::isfinite(a_split)) return DSS_ERR_ARG;
+    if (!h->have_state) return DSS_ERR_STATE;
+    ENTER(h);
+    const int K = h->K;
+    // per instance: the integer unit 2^-62 of its solid volume, so that no
+    // slab sum can overflow
+    std::vector<double> unit(K);
+    for (int k = 0; k < K; ++k) {
+      const double vol = 4.0 / 3.0 * DSS_PI * h->ig_host[k].sumA3;
+      unit[k] = std::ldexp(vol > 0.0 ? vol : 1.0, -62);
+    }
+    const size_t nacc = (size_t)K * 2 * nbins;
+    double* du = nullptr;
+    unsigned long long* acc = nullptr;
+    CK(cudaMalloc((void**)&du, sizeof(double) * K));
+    if (cudaMalloc((void**)&acc, sizeof(unsigned long long) * nacc) != cudaSuccess) {
+      cudaFree(du);
+      return DSS_ERR_CUDA;
+    }
+    std::vector<unsigned long long> hacc(nacc);
+    cudaError_t e = cudaMemcpyAsync(du, unit.data(), sizeof(double) * K, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * nacc, h->stream);
+    if (e == cudaSuccess) {
+      launch_phi_profile(h, nbins, a_split, du, acc);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(hacc.data(), acc, sizeof(unsigned long long) * nacc, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(du);
+    cudaFree(acc);
+    if (e != cudaSuccess) return DSS_ERR_CUDA;
+    std::vector<double> r(nacc);
+    for (int k = 0; k < K; ++k) {
+      const double* L = h->inst_box + 3 * k;
+      const double slab = L[0] * L[2] * (L[1] / nbins);
+      for (int q = 0; q < 2 * nbins; ++q)
+        r[(size_t)k * 2 * nbins + q] = (double)hacc[(size_t)k * 2 * nbins + q] * unit[k] / slab;
+    }
+    CK(cudaMemcpy(out, r.data(), sizeof(double) * nacc, cudaMemcpyDefault));
+    return DSS_OK;
+  });
+}
+
 int dss_dispersion(dss_handle* h, double* out) {
-  if (!h || !out) return DSS_ERR_ARG;
-  if (!h->have_state || !h->marked || !h->mark) return DSS_ERR_STATE;
-  ENTER(h);
-  const int K = h->K;
-  launch_dispersion(h, h->io3);
-  CK(cudaGetLastError());
-  std::vector<double> sums(3 * (size_t)K), r(3 * (size_t)K);
-  CK(cudaMemcpyAsync(sums.data(), h->io3, sizeof(double) * sums.size(), cudaMemcpyDeviceToHost, h->stream));
-  int rc = sync_status(h);
-  if (rc) return rc;
-  const int64_t ns = (int64_t)(uint32_t)h->status_host->w[ST_NSTEP_LO] |
-                     ((int64_t)h->status_host->w[ST_NSTEP_HI] << 32);
-  const double t = (double)(ns - h->mark_nstep) * h->p.dt;
-  for (int k = 0; k < K; ++k) {
-    const double nk = (double)h->inst_n[k];
-    const double g = h->inst_gdot[k] * h->p.a0 * h->p.a0;
-    r[3 * k] = t > 0.0 && g != 0.0 ? sums[3 * k] / nk / (2.0 * t) / g : 0.0;
-    r[3 * k + 1] = sums[3 * k + 2] != 0.0 ? sums[3 * k + 1] / sums[3 * k + 2] : 0.0;
-    r[3 * k + 2] = t;
-  }
-  CK(cudaMemcpy(out, r.data(), sizeof(double) * r.size(), cudaMemcpyDefault));
-  return DSS_OK;
+  return guard([&]() -> int {
+    if (!h || !out) return DSS_ERR_ARG;
+    if (!h->have_state || !h->marked || !h->mark) return DSS_ERR_STATE;
+    ENTER(h);
+    const int K = h->K;
+    launch_dispersion(h, h->io3);
+    CK(cudaGetLastError());
+    std::vector<double> sums(3 * (size_t)K), r(3 * (size_t)K);
+    CK(cudaMemcpyAsync(sums.data(), h->io3, sizeof(double) * sums.size(), cudaMemcpyDeviceToHost, h->stream));
+    int rc = sync_status(h);
+    if (rc) return rc;
+    const int64_t ns = (int64_t)(uint32_t)h->status_host->w[ST_NSTEP_LO] |
+                       ((int64_t)h->status_host->w[ST_NSTEP_HI] << 32);
+    const double t = (double)(ns - h->mark_nstep) * h->p.dt;
+    for (int k = 0; k < K; ++k) {
+      const double nk = (double)h->inst_n[k];
+      const double g = h->inst_gdot[k] * h->p.a0 * h->p.a0;
+      r[3 * k] = t > 0.0 && g != 0.0 ? sums[3 * k] / nk / (2.0 * t) / g : 0.0;
+      r[3 * k + 1] = sums[3 * k + 2] != 0.0 ? sums[3 * k + 1] / sums[3 * k + 2] : 0.0;
+      r[3 * k + 2] = t;
+    }
+    CK(cudaMemcpy(out, r.data(), sizeof(double) * r.size(), cudaMemcpyDefault));
+    return DSS_OK;
+  });
 }
 
 int dss_contact_clusters(dss_handle* h, int32_t* label, int64_t* nclusters) {
-  if (!h || !nclusters) return DSS_ERR_ARG;
-  if (!h->have_state) return DSS_ERR_STATE;
-  ENTER(h);
-  // scratch, free between steps: the sort's key, offset and slot arrays hold
-  // the parents, the smallest ids and the labels; the id staging array the
-  // count
-  int* count = h->io_id;
-  launch_clusters(h, h->key, h->offs, count, h->tmp);
-  CK(cudaGetLastError());
-  int c = 0;
-  CK(cudaMemcpyAsync(&c, count, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-  int r = sync_status(h);
-  if (r) return r;
-  if ((r = status_error(h))) { clear_err(h); return r; }
-  if (label) {
-    CK(cudaMemcpy(label, h->tmp, sizeof(int32_t) * h->n, cudaMemcpyDefault));
-  }
-  *nclusters = c;
-  return DSS_OK;
+  return guard([&]() -> int {
+    if (!h || !nclusters) return DSS_ERR_ARG;
+    if (!h->have_state) return DSS_ERR_STATE;
+    ENTER(h);
+    // scratch, free between steps: the sort's key, offset and slot arrays hold
+    // the parents, the smallest ids and the labels; the id staging array the
+    // count
+    int* count = h->io_id;
+    launch_clusters(h, h->key, h->offs, count, h->tmp);
+    CK(cudaGetLastError());
+    int c = 0;
+    CK(cudaMemcpyAsync(&c, count, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    int r = sync_status(h);
+    if (r) return r;
+    if ((r = status_error(h))) { clear_err(h); return r; }
+    if (label) {
+      CK(cudaMemcpy(label, h->tmp, sizeof(int32_t) * h->n, cudaMemcpyDefault));
+    }
+    *nclusters = c;
+    return DSS_OK;
+  });
 }
 
 int dss_get_counters(dss_handle* h, dss_counters* c) {
@@ -1218,55 +1337,57 @@ int dss_get_counters(dss_handle* h, dss_counters* c) {
 
 int dss_set_history_rolling(dss_handle* h, int64_t k, const int64_t* keys, const double* xi,
                             const double* xr) {
-  if (!h || k < 0 || (k > 0 && (!keys || !xi))) return DSS_ERR_ARG;
-  if (!h->have_state) return DSS_ERR_STATE;
-  ENTER(h);
-  std::vector<std::pair<int64_t, int64_t>> order(k);
-  std::vector<int64_t> hk(k);
-  std::vector<double> hx(3 * k), hr(3 * k, 0.0);
-  if (k) {
-    CK(cudaMemcpy(hk.data(), keys, sizeof(int64_t) * k, cudaMemcpyDefault));
-    CK(cudaMemcpy(hx.data(), xi, sizeof(double) * 3 * k, cudaMemcpyDefault));
-    if (xr) CK(cudaMemcpy(hr.data(), xr, sizeof(double) * 3 * k, cudaMemcpyDefault));
-  }
-  for (int64_t q = 0; q < k; ++q) order[q] = {hk[q], q};
-  std::sort(order.begin(), order.end());
-  const size_t m = (size_t)std::max<int64_t>(k, 1);
-  std::vector<long long> sk(m);
-  std::vector<double> sx(6 * m, 0.0);   // sliding then rolling stretch
-  for (int64_t q = 0; q < k; ++q) {
-    sk[q] = order[q].first;
-    for (int c = 0; c < 3; ++c) {
-      sx[3 * q + c] = hx[3 * order[q].second + c];
-      sx[3 * m + 3 * q + c] = hr[3 * order[q].second + c];
+  return guard([&]() -> int {
+    if (!h || k < 0 || (k > 0 && (!keys || !xi))) return DSS_ERR_ARG;
+    if (!h->have_state) return DSS_ERR_STATE;
+    ENTER(h);
+    std::vector<std::pair<int64_t, int64_t>> order(k);
+    std::vector<int64_t> hk(k);
+    std::vector<double> hx(3 * k), hr(3 * k, 0.0);
+    if (k) {
+      CK(cudaMemcpy(hk.data(), keys, sizeof(int64_t) * k, cudaMemcpyDefault));
+      CK(cudaMemcpy(hx.data(), xi, sizeof(double) * 3 * k, cudaMemcpyDefault));
+      if (xr) CK(cudaMemcpy(hr.data(), xr, sizeof(double) * 3 * k, cudaMemcpyDefault));
     }
-  }
-  long long* dk = nullptr;
-  double* dx = nullptr;
-  CK(cudaMalloc((void**)&dk, sizeof(long long) * sk.size()));
-  CK(cudaMalloc((void**)&dx, sizeof(double) * sx.size()));
-  CK(cudaMemcpy(dk, sk.data(), sizeof(long long) * sk.size(), cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(dx, sx.data(), sizeof(double) * sx.size(), cudaMemcpyHostToDevice));
-  // neighbour build at the current state, attach the stretch, commit as history
-  seq_sort_enum(h, false, 0);
-  h->cur = 1 - h->cur;
-  const int L = 1 - h->hist;
-  {
-    const int rc = ensure_pair_capacity(h, L);
-    if (rc) { cudaFree(dk); cudaFree(dx); return rc; }
-  }
-  k_attach_history<<<pair_grid_blocks(h), 256, 0, h->stream>>>(h->g, h->st[h->cur], h->lb[L], dk, dx,
-                                                                 dx + 3 * m, (int)k);
-  CK(cudaGetLastError());
-  int r = sync_status(h);
-  cudaFree(dk);
-  cudaFree(dx);
-  if (r) return r;
-  if ((r = status_error(h))) { clear_err(h); return r; }
-  h->hist = L;
-  // the new history's rows follow the committed (sorted) order
-  CK(cudaMemsetAsync(&h->status->w[ST_IDORDER], 0, sizeof(int), h->stream));
-  return DSS_OK;
+    for (int64_t q = 0; q < k; ++q) order[q] = {hk[q], q};
+    std::sort(order.begin(), order.end());
+    const size_t m = (size_t)std::max<int64_t>(k, 1);
+    std::vector<long long> sk(m);
+    std::vector<double> sx(6 * m, 0.0);   // sliding then rolling stretch
+    for (int64_t q = 0; q < k; ++q) {
+      sk[q] = order[q].first;
+      for (int c = 0; c < 3; ++c) {
+        sx[3 * q + c] = hx[3 * order[q].second + c];
+        sx[3 * m + 3 * q + c] = hr[3 * order[q].second + c];
+      }
+    }
+    long long* dk = nullptr;
+    double* dx = nullptr;
+    CK(cudaMalloc((void**)&dk, sizeof(long long) * sk.size()));
+    CK(cudaMalloc((void**)&dx, sizeof(double) * sx.size()));
+    CK(cudaMemcpy(dk, sk.data(), sizeof(long long) * sk.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(dx, sx.data(), sizeof(double) * sx.size(), cudaMemcpyHostToDevice));
+    // neighbour build at the current state, attach the stretch, commit as history
+    seq_sort_enum(h, false, 0);
+    h->cur = 1 - h->cur;
+    const int L = 1 - h->hist;
+    {
+      const int rc = ensure_pair_capacity(h, L);
+      if (rc) { cudaFree(dk); cudaFree(dx); return rc; }
+    }
+    k_attach_history<<<pair_grid_blocks(h), 256, 0, h->stream>>>(h->g, h->st[h->cur], h->lb[L], dk, dx,
+                                                                   dx + 3 * m, (int)k);
+    CK(cudaGetLastError());
+    int r = sync_status(h);
+    cudaFree(dk);
+    cudaFree(dx);
+    if (r) return r;
+    if ((r = status_error(h))) { clear_err(h); return r; }
+    h->hist = L;
+    // the new history's rows follow the committed (sorted) order
+    CK(cudaMemsetAsync(&h->status->w[ST_IDORDER], 0, sizeof(int), h->stream));
+    return DSS_OK;
+  });
 }
 
 int dss_set_history(dss_handle* h, int64_t k, const int64_t* keys, const double* xi) {
@@ -1275,43 +1396,45 @@ int dss_set_history(dss_handle* h, int64_t k, const int64_t* keys, const double*
 
 int dss_get_history_rolling(dss_handle* h, int64_t* keys, double* xi, double* xr, int64_t cap,
                             int64_t* count) {
-  if (!h || !count || cap < 0 || (cap > 0 && (!keys || !xi))) return DSS_ERR_ARG;
-  if (!h->have_state) return DSS_ERR_STATE;
-  ENTER(h);
-  int P = 0;
-  CK(cudaMemcpy(&P, h->lb[h->hist].start + h->n, sizeof(int), cudaMemcpyDeviceToHost));
-  long long* dk = nullptr;
-  double* dx = nullptr;
-  int* cnt = nullptr;
-  size_t m = std::max(P, 1);
-  CK(cudaMalloc((void**)&dk, sizeof(long long) * m));
-  CK(cudaMalloc((void**)&dx, sizeof(double) * 6 * m));
-  CK(cudaMalloc((void**)&cnt, sizeof(int)));
-  CK(cudaMemsetAsync(cnt, 0, sizeof(int), h->stream));
-  k_history_out<<<pair_grid_blocks(h), 256, 0, h->stream>>>(h->g, h->lb[h->hist], dk, dx, dx + 3 * m, cnt,
-                                                              (int)m);
-  int K = 0;
-  CK(cudaMemcpyAsync(&K, cnt, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-  CK(cudaStreamSynchronize(h->stream));
-  std::vector<long long> hk(std::max(K, 1));
-  std::vector<double> hx(3 * (size_t)std::max(K, 1)), hr(3 * (size_t)std::max(K, 1));
-  CK(cudaMemcpy(hk.data(), dk, sizeof(long long) * K, cudaMemcpyDeviceToHost));
-  CK(cudaMemcpy(hx.data(), dx, sizeof(double) * 3 * K, cudaMemcpyDeviceToHost));
-  CK(cudaMemcpy(hr.data(), dx + 3 * m, sizeof(double) * 3 * K, cudaMemcpyDeviceToHost));
-  cudaFree(dk); cudaFree(dx); cudaFree(cnt);
-  std::vector<std::pair<long long, int>> order(K);
-  for (int q = 0; q < K; ++q) order[q] = {hk[q], q};
-  std::sort(order.begin(), order.end());
-  *count = K;
-  int64_t mm = std::min<int64_t>(cap, K);
-  for (int64_t q = 0; q < mm; ++q) {
-    keys[q] = order[q].first;
-    for (int c = 0; c < 3; ++c) {
-      xi[3 * q + c] = hx[3 * order[q].second + c];
-      if (xr) xr[3 * q + c] = hr[3 * order[q].second + c];
+  return guard([&]() -> int {
+    if (!h || !count || cap < 0 || (cap > 0 && (!keys || !xi))) return DSS_ERR_ARG;
+    if (!h->have_state) return DSS_ERR_STATE;
+    ENTER(h);
+    int P = 0;
+    CK(cudaMemcpy(&P, h->lb[h->hist].start + h->n, sizeof(int), cudaMemcpyDeviceToHost));
+    long long* dk = nullptr;
+    double* dx = nullptr;
+    int* cnt = nullptr;
+    size_t m = std::max(P, 1);
+    CK(cudaMalloc((void**)&dk, sizeof(long long) * m));
+    CK(cudaMalloc((void**)&dx, sizeof(double) * 6 * m));
+    CK(cudaMalloc((void**)&cnt, sizeof(int)));
+    CK(cudaMemsetAsync(cnt, 0, sizeof(int), h->stream));
+    k_history_out<<<pair_grid_blocks(h), 256, 0, h->stream>>>(h->g, h->lb[h->hist], dk, dx, dx + 3 * m, cnt,
+                                                                (int)m);
+    int K = 0;
+    CK(cudaMemcpyAsync(&K, cnt, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    std::vector<long long> hk(std::max(K, 1));
+    std::vector<double> hx(3 * (size_t)std::max(K, 1)), hr(3 * (size_t)std::max(K, 1));
+    CK(cudaMemcpy(hk.data(), dk, sizeof(long long) * K, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(hx.data(), dx, sizeof(double) * 3 * K, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(hr.data(), dx + 3 * m, sizeof(double) * 3 * K, cudaMemcpyDeviceToHost));
+    cudaFree(dk); cudaFree(dx); cudaFree(cnt);
+    std::vector<std::pair<long long, int>> order(K);
+    for (int q = 0; q < K; ++q) order[q] = {hk[q], q};
+    std::sort(order.begin(), order.end());
+    *count = K;
+    int64_t mm = std::min<int64_t>(cap, K);
+    for (int64_t q = 0; q < mm; ++q) {
+      keys[q] = order[q].first;
+      for (int c = 0; c < 3; ++c) {
+        xi[3 * q + c] = hx[3 * order[q].second + c];
+        if (xr) xr[3 * q + c] = hr[3 * order[q].second + c];
+      }
     }
-  }
-  return DSS_OK;
+    return DSS_OK;
+  });
 }
 
 int dss_get_history(dss_handle* h, int64_t* keys, double* xi, int64_t cap, int64_t* count) {
@@ -1320,29 +1443,31 @@ int dss_get_history(dss_handle* h, int64_t* keys, double* xi, int64_t cap, int64
 
 int dss_load_state(dss_handle* h, const double* x, const double* u, const double* w,
                    const double* alpha_lin, const double* alpha_ang) {
-  if (!h || !x || !u || !w || !alpha_lin || !alpha_ang) return DSS_ERR_ARG;
-  if (!h->have_state) return DSS_ERR_STATE;
-  ENTER(h);
-  const size_t b = sizeof(double) * 3 * (size_t)h->n;
-  StateBuf& s = h->st[h->cur];
-  const double* in[5] = {x, u, w, alpha_lin, alpha_ang};
-  // device and mapped pinned host buffers are read by one kernel; pageable
-  // host buffers go through the staging area with the copy engine first
-  Src5 src;
-  for (int k = 0; k < 5; ++k) {
-    src.d[k] = static_cast<const double*>(device_view(in[k]));
-    if (!src.d[k]) {
-      double* st = h->stage + (size_t)k * 3 * h->n;
-      CK(cudaMemcpyAsync(st, in[k], b, cudaMemcpyHostToDevice, h->stream));
-      src.d[k] = st;
+  return guard([&]() -> int {
+    if (!h || !x || !u || !w || !alpha_lin || !alpha_ang) return DSS_ERR_ARG;
+    if (!h->have_state) return DSS_ERR_STATE;
+    ENTER(h);
+    const size_t b = sizeof(double) * 3 * (size_t)h->n;
+    StateBuf& s = h->st[h->cur];
+    const double* in[5] = {x, u, w, alpha_lin, alpha_ang};
+    // device and mapped pinned host buffers are read by one kernel; pageable
+    // host buffers go through the staging area with the copy engine first
+    Src5 src;
+    for (int k = 0; k < 5; ++k) {
+      src.d[k] = static_cast<const double*>(device_view(in[k]));
+      if (!src.d[k]) {
+        double* st = h->stage + (size_t)k * 3 * h->n;
+        CK(cudaMemcpyAsync(st, in[k], b, cudaMemcpyHostToDevice, h->stream));
+        src.d[k] = st;
+      }
     }
-  }
-  k_state_in<<<(int)((h->n + 255) / 256), 256, 0, h->stream>>>((int)h->n, src, s, h->a_by_id, h->inst_map,
-                                                               h->cls_map);
-  // the committed state is now in id order, not in the history's row order
-  CK(cudaMemsetAsync(&h->status->w[ST_IDORDER], 1, sizeof(int), h->stream));
-  CK(cudaGetLastError());
-  return DSS_OK;
+    k_state_in<<<(int)((h->n + 255) / 256), 256, 0, h->stream>>>((int)h->n, src, s, h->a_by_id, h->inst_map,
+                                                                 h->cls_map);
+    // the committed state is now in id order, not in the history's row order
+    CK(cudaMemsetAsync(&h->status->w[ST_IDORDER], 1, sizeof(int), h->stream));
+    CK(cudaGetLastError());
+    return DSS_OK;
+  });
 }
 
 int dss_set_profiling(dss_handle* h, int on) {
@@ -1451,154 +1576,217 @@ void unsize(dss_handle* h) {
 }  // namespace
 
 int dss_save(dss_handle* h, void* buf, size_t* len) {
-  if (!h || !len) return DSS_ERR_ARG;
-  if (!h->have_state) return DSS_ERR_STATE;
-  int64_t nh = 0;
-  int r = dss_get_history(h, nullptr, nullptr, 0, &nh);
-  if (r) return r;
-  const int64_t n = h->n;
-  const bool rolling = h->g.k_r > 0.0;
-  const size_t need = ckpt_bytes(n, nh, h->K, rolling);
-  if (!buf) {
+  return guard([&]() -> int {
+    if (!h || !len) return DSS_ERR_ARG;
+    if (!h->have_state) return DSS_ERR_STATE;
+    int64_t nh = 0;
+    int r = dss_get_history(h, nullptr, nullptr, 0, &nh);
+    if (r) return r;
+    const int64_t n = h->n;
+    const bool rolling = h->g.k_r > 0.0;
+    const size_t need = ckpt_bytes(n, nh, h->K, rolling);
+    if (!buf) {
+      *len = need;
+      return DSS_OK;
+    }
+    if (*len < need) {
+      *len = need;
+      return DSS_ERR_ARG;
+    }
+    CkptHeader hd;
+    memset(&hd, 0, sizeof(hd));
+    memcpy(hd.magic, kMagic, 8);
+    hd.version = 1;
+    hd.K = h->K;
+    hd.n = n;
+    hd.nhist = nh;
+    hd.mean_steps = h->mean_steps;
+    hd.config = config_hash(h);
+    char* out = static_cast<char*>(buf);
+    double* x = reinterpret_cast<double*>(out + sizeof(CkptHeader));
+    double* a = x + 15 * n;
+    int64_t* keys = reinterpret_cast<int64_t*>(a + n);
+    double* xi = reinterpret_cast<double*>(keys + nh);
+    double* xr = xi + 3 * nh;
+    double* sig = xr + (rolling ? 3 * nh : 0);
+    std::vector<double> st(15 * (size_t)n);
+    if ((r = dss_get_state(h, st.data(), st.data() + 3 * n, st.data() + 6 * n, st.data() + 9 * n,
+                           st.data() + 12 * n)))
+      return r;
+    memcpy(x, st.data(), sizeof(double) * 15 * n);
+    int64_t nh2 = 0;
+    if (nh > 0 && (r = dss_get_history_rolling(h, keys, xi, rolling ? xr : nullptr, nh, &nh2))) return r;
+    if (nh2 != nh && nh > 0) return DSS_ERR_INTERNAL;
+    CK(cudaMemcpyAsync(a, h->a_by_id, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(sig, h->sigma, sizeof(double) * 9 * h->K, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(sig + 9 * h->K, h->sigma_sum, sizeof(double) * 9 * h->K, cudaMemcpyDeviceToHost,
+                       h->stream));
+    if ((r = sync_status(h))) return r;
+    hd.nstep = (int64_t)(uint32_t)h->status_host->w[ST_NSTEP_LO] |
+               ((int64_t)h->status_host->w[ST_NSTEP_HI] << 32);
+    memcpy(out, &hd, sizeof(hd));
     *len = need;
     return DSS_OK;
-  }
-  if (*len < need) {
-    *len = need;
-    return DSS_ERR_ARG;
-  }
-  CkptHeader hd;
-  memset(&hd, 0, sizeof(hd));
-  memcpy(hd.magic, kMagic, 8);
-  hd.version = 1;
-  hd.K = h->K;
-  hd.n = n;
-  hd.nhist = nh;
-  hd.mean_steps = h->mean_steps;
-  hd.config = config_hash(h);
-  char* out = static_cast<char*>(buf);
-  double* x = reinterpret_cast<double*>(out + sizeof(CkptHeader));
-  double* a = x + 15 * n;
-  int64_t* keys = reinterpret_cast<int64_t*>(a + n);
-  double* xi = reinterpret_cast<double*>(keys + nh);
-  double* xr = xi + 3 * nh;
-  double* sig = xr + (rolling ? 3 * nh : 0);
-  std::vector<double> st(15 * (size_t)n);
-  if ((r = dss_get_state(h, st.data(), st.data() + 3 * n, st.data() + 6 * n, st.data() + 9 * n,
-                         st.data() + 12 * n)))
-    return r;
-  memcpy(x, st.data(), sizeof(double) * 15 * n);
-  int64_t nh2 = 0;
-  if (nh > 0 && (r = dss_get_history_rolling(h, keys, xi, rolling ? xr : nullptr, nh, &nh2))) return r;
-  if (nh2 != nh && nh > 0) return DSS_ERR_INTERNAL;
-  CK(cudaMemcpyAsync(a, h->a_by_id, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
-  CK(cudaMemcpyAsync(sig, h->sigma, sizeof(double) * 9 * h->K, cudaMemcpyDeviceToHost, h->stream));
-  CK(cudaMemcpyAsync(sig + 9 * h->K, h->sigma_sum, sizeof(double) * 9 * h->K, cudaMemcpyDeviceToHost,
-                     h->stream));
-  if ((r = sync_status(h))) return r;
-  hd.nstep = (int64_t)(uint32_t)h->status_host->w[ST_NSTEP_LO] |
-             ((int64_t)h->status_host->w[ST_NSTEP_HI] << 32);
-  memcpy(out, &hd, sizeof(hd));
-  *len = need;
-  return DSS_OK;
+  });
 }
 
 int dss_load(dss_handle* h, const void* buf, size_t len) {
-  if (!h || !buf || len < sizeof(CkptHeader)) return DSS_ERR_ARG;
-  CkptHeader hd;
-  memcpy(&hd, buf, sizeof(hd));
-  if (memcmp(hd.magic, kMagic, 8) != 0 || hd.version != 1 || hd.K != h->K || hd.n != h->n ||
-      hd.nhist < 0 || hd.nstep < 0 || hd.mean_steps < 0 || hd.config != config_hash(h))
-    return DSS_ERR_ARG;
-  const int64_t n = hd.n, nh = hd.nhist;
-  const bool rolling = h->g.k_r > 0.0;
-  if (len < ckpt_bytes(n, nh, h->K, rolling)) return DSS_ERR_ARG;
-  // copies keep the arrays aligned whatever the caller's buffer alignment
-  const char* in = static_cast<const char*>(buf) + sizeof(CkptHeader);
-  std::vector<double> st(16 * (size_t)n);
-  memcpy(st.data(), in, sizeof(double) * 16 * n);
-  in += sizeof(double) * 16 * n;
-  std::vector<int64_t> keys(std::max<int64_t>(nh, 1));
-  std::vector<double> xi(3 * (size_t)std::max<int64_t>(nh, 1));
-  memcpy(keys.data(), in, sizeof(int64_t) * nh);
-  in += sizeof(int64_t) * nh;
-  memcpy(xi.data(), in, sizeof(double) * 3 * nh);
-  in += sizeof(double) * 3 * nh;
-  std::vector<double> xr(3 * (size_t)std::max<int64_t>(nh, 1), 0.0);
-  if (rolling) {
-    memcpy(xr.data(), in, sizeof(double) * 3 * nh);
+  return guard([&]() -> int {
+    if (!h || !buf || len < sizeof(CkptHeader)) return DSS_ERR_ARG;
+    CkptHeader hd;
+    memcpy(&hd, buf, sizeof(hd));
+    if (memcmp(hd.magic, kMagic, 8) != 0 || hd.version != 1 || hd.K != h->K || hd.n != h->n ||
+        hd.nhist < 0 || hd.nstep < 0 || hd.mean_steps < 0 || hd.config != config_hash(h))
+      return DSS_ERR_ARG;
+    const int64_t n = hd.n, nh = hd.nhist;
+    const bool rolling = h->g.k_r > 0.0;
+    // the history entries must fit in what the buffer holds beyond the fixed
+    // part (checked before any size arithmetic on nhist, which could overflow)
+    const size_t fixed = ckpt_bytes(n, 0, h->K, rolling);
+    const size_t per_entry = sizeof(int64_t) + (rolling ? 6 : 3) * sizeof(double);
+    if (len < fixed || (uint64_t)nh > (len - fixed) / per_entry) return DSS_ERR_ARG;
+    // copies keep the arrays aligned whatever the caller's buffer alignment
+    const char* in = static_cast<const char*>(buf) + sizeof(CkptHeader);
+    std::vector<double> st(16 * (size_t)n);
+    memcpy(st.data(), in, sizeof(double) * 16 * n);
+    in += sizeof(double) * 16 * n;
+    std::vector<int64_t> keys(std::max<int64_t>(nh, 1));
+    std::vector<double> xi(3 * (size_t)std::max<int64_t>(nh, 1));
+    memcpy(keys.data(), in, sizeof(int64_t) * nh);
+    in += sizeof(int64_t) * nh;
+    memcpy(xi.data(), in, sizeof(double) * 3 * nh);
     in += sizeof(double) * 3 * nh;
-  }
-  std::vector<double> sig(18 * (size_t)h->K);
-  memcpy(sig.data(), in, sizeof(double) * 18 * h->K);
-  const double* x = st.data();
-  int r = dss_set_state(h, x, x + 15 * n, nullptr, x + 3 * n, x + 6 * n, x + 9 * n, x + 12 * n, hd.nstep);
-  if (r) return r;
-  if ((r = dss_set_history_rolling(h, nh, keys.data(), xi.data(), rolling ? xr.data() : nullptr))) return r;
-  CK(cudaMemcpyAsync(h->sigma, sig.data(), sizeof(double) * 9 * h->K, cudaMemcpyHostToDevice, h->stream));
-  CK(cudaMemcpyAsync(h->sigma_sum, sig.data() + 9 * h->K, sizeof(double) * 9 * h->K,
-                     cudaMemcpyHostToDevice, h->stream));
-  CK(cudaStreamSynchronize(h->stream));
-  h->mean_steps = hd.mean_steps;
-  return DSS_OK;
+    std::vector<double> xr(3 * (size_t)std::max<int64_t>(nh, 1), 0.0);
+    if (rolling) {
+      memcpy(xr.data(), in, sizeof(double) * 3 * nh);
+      in += sizeof(double) * 3 * nh;
+    }
+    std::vector<double> sig(18 * (size_t)h->K);
+    memcpy(sig.data(), in, sizeof(double) * 18 * h->K);
+    const double* x = st.data();
+    int r = dss_set_state(h, x, x + 15 * n, nullptr, x + 3 * n, x + 6 * n, x + 9 * n, x + 12 * n, hd.nstep);
+    if (r) return r;
+    if ((r = dss_set_history_rolling(h, nh, keys.data(), xi.data(), rolling ? xr.data() : nullptr))) return r;
+    CK(cudaMemcpyAsync(h->sigma, sig.data(), sizeof(double) * 9 * h->K, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->sigma_sum, sig.data() + 9 * h->K, sizeof(double) * 9 * h->K,
+                       cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    h->mean_steps = hd.mean_steps;
+    return DSS_OK;
+  });
 }
 
 int dss_autotune(dss_handle* h, int32_t trial_steps, int32_t ncand, const double* factors,
                  double* ms_per_step, double* cell_size) {
-  static const double kDefault[4] = {1.0, 1.1, 1.25, 1.5};
-  if (!h || trial_steps < 1 || ncand < 0 || ncand > 16 || (ncand > 0 && !factors)) return DSS_ERR_ARG;
-  if (!h->have_state) return DSS_ERR_STATE;
-  if (ncand == 0) {
-    ncand = 4;
-    factors = kDefault;
-  }
-  for (int c = 0; c < ncand; ++c)
-    if (!(factors[c] >= 1.0) || !std::isfinite(factors[c])) return DSS_ERR_ARG;
-  size_t len = 0;
-  int r = dss_save(h, nullptr, &len);
-  if (r) return r;
-  std::vector<char> ck(len);
-  if ((r = dss_save(h, ck.data(), &len))) return r;
-  const dss_params& p = h->p;
-  const double dmax = dmax_of(p, h->a_max);
-  const double cmin = (2.0 * h->a_max + dmax) * (1.0 + 1e-9) + 1e-12;
-  const double base = p.cell_size > 0.0 ? p.cell_size : cmin;
-  const bool prof_was = h->profiling;
-  h->profiling = false;
-  double best = INFINITY, best_cs = base;
-  for (int c = 0; c < ncand; ++c) {
-    const double cs = factors[c] * cmin;
-    double ms = INFINITY;
-    h->p.cell_size = cs;
+  return guard([&]() -> int {
+    static const double kDefault[4] = {1.0, 1.1, 1.25, 1.5};
+    if (!h || trial_steps < 1 || ncand < 0 || ncand > 16 || (ncand > 0 && !factors)) return DSS_ERR_ARG;
+    if (!h->have_state) return DSS_ERR_STATE;
+    if (ncand == 0) {
+      ncand = 4;
+      factors = kDefault;
+    }
+    for (int c = 0; c < ncand; ++c)
+      if (!(factors[c] >= 1.0) || !std::isfinite(factors[c])) return DSS_ERR_ARG;
+    size_t len = 0;
+    int r = dss_save(h, nullptr, &len);
+    if (r) return r;
+    std::vector<char> ck(len);
+    if ((r = dss_save(h, ck.data(), &len))) return r;
+    const dss_params& p = h->p;
+    const double dmax = dmax_of(p, h->a_max);
+    const double cmin = (2.0 * h->a_max + dmax) * (1.0 + 1e-9) + 1e-12;
+    const double base = p.cell_size > 0.0 ? p.cell_size : cmin;
+    const bool prof_was = h->profiling;
+    h->profiling = false;
+    double best = INFINITY, best_cs = base;
+    for (int c = 0; c < ncand; ++c) {
+      const double cs = factors[c] * cmin;
+      double ms = INFINITY;
+      h->p.cell_size = cs;
+      unsize(h);
+      r = dss_load(h, ck.data(), len);
+      if (r == DSS_OK) {
+        r = dss_step(h, 2);   // captures the step graphs
+        double t = 0.0;
+        if (r == DSS_OK) r = dss_step(h, trial_steps);
+        if (r == DSS_OK && dss_last_step_ms(h, &t) == DSS_OK) ms = t / trial_steps;
+      }
+      if (r != DSS_OK && r != DSS_ERR_BOX && r != DSS_ERR_ARG) {
+        h->p.cell_size = base;
+        unsize(h);
+        dss_load(h, ck.data(), len);
+        h->profiling = prof_was;
+        return r;
+      }
+      if (ms_per_step) ms_per_step[c] = ms;
+      if (ms < best) {
+        best = ms;
+        best_cs = cs;
+      }
+    }
+    // keep the fastest grid and return to the saved state
+    h->p.cell_size = best < INFINITY ? best_cs : base;
     unsize(h);
     r = dss_load(h, ck.data(), len);
-    if (r == DSS_OK) {
-      r = dss_step(h, 2);   // captures the step graphs
-      double t = 0.0;
-      if (r == DSS_OK) r = dss_step(h, trial_steps);
-      if (r == DSS_OK && dss_last_step_ms(h, &t) == DSS_OK) ms = t / trial_steps;
+    h->profiling = prof_was;
+    if (r) return r;
+    if (cell_size) *cell_size = h->p.cell_size;
+    return best < INFINITY ? DSS_OK : DSS_ERR_BOX;
+  });
+}
+
+int dss_autotune_kernels(dss_handle* h, int32_t trial_steps, double* ms_per_step, int32_t* choice) {
+  return guard([&]() -> int {
+    if (!h || trial_steps < 1) return DSS_ERR_ARG;
+    if (!h->have_state) return DSS_ERR_STATE;
+    size_t len = 0;
+    int r = dss_save(h, nullptr, &len);
+    if (r) return r;
+    std::vector<char> ck(len);
+    if ((r = dss_save(h, ck.data(), &len))) return r;
+    const bool prof_was = h->profiling;
+    h->profiling = false;
+    static const int kMinb[2] = {3, 4}, kUnr[2] = {1, 4};
+    double best = INFINITY;
+    int bm = 0, bu = 0;
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b) {
+        h->tune_pairs_minb = kMinb[a];
+        h->tune_enum_unr = kUnr[b];
+        drop_graphs(h);
+        double ms = INFINITY;
+        r = dss_load(h, ck.data(), len);
+        if (r == DSS_OK) r = dss_step(h, 2);
+        double t = 0.0;
+        if (r == DSS_OK) r = dss_step(h, trial_steps);
+        if (r == DSS_OK && dss_last_step_ms(h, &t) == DSS_OK) ms = t / trial_steps;
+        if (r != DSS_OK) {
+          h->tune_pairs_minb = h->tune_enum_unr = 0;
+          drop_graphs(h);
+          dss_load(h, ck.data(), len);
+          h->profiling = prof_was;
+          return r;
+        }
+        if (ms_per_step) ms_per_step[2 * a + b] = ms;
+        if (ms < best) {
+          best = ms;
+          bm = kMinb[a];
+          bu = kUnr[b];
+        }
+      }
+    h->tune_pairs_minb = bm;
+    h->tune_enum_unr = bu;
+    drop_graphs(h);
+    r = dss_load(h, ck.data(), len);
+    h->profiling = prof_was;
+    if (r) return r;
+    if (choice) {
+      choice[0] = bm;
+      choice[1] = bu;
     }
-    if (r != DSS_OK && r != DSS_ERR_BOX && r != DSS_ERR_ARG) {
-      h->p.cell_size = base;
-      unsize(h);
-      dss_load(h, ck.data(), len);
-      h->profiling = prof_was;
-      return r;
-    }
-    if (ms_per_step) ms_per_step[c] = ms;
-    if (ms < best) {
-      best = ms;
-      best_cs = cs;
-    }
-  }
-  // keep the fastest grid and return to the saved state
-  h->p.cell_size = best < INFINITY ? best_cs : base;
-  unsize(h);
-  r = dss_load(h, ck.data(), len);
-  h->profiling = prof_was;
-  if (r) return r;
-  if (cell_size) *cell_size = h->p.cell_size;
-  return best < INFINITY ? DSS_OK : DSS_ERR_BOX;
+    return DSS_OK;
+  });
 }
 
 // ------------------------------------------------------------------------
@@ -1608,88 +1796,90 @@ int dss_autotune(dss_handle* h, int32_t trial_steps, int32_t ncand, const double
 int dss_adjoint(dss_handle* h, int64_t nsteps, int32_t ckpt_every, const double* weights,
                 int32_t initial_forces, double* J, double* dJ_dparams, double* dJ_dx0,
                 double* dJ_du0, double* dJ_dw0, double* dJ_dalpha0, double* dJ_dbeta0) {
-  if (!h || nsteps < 1 || ckpt_every < 1 || !weights) return DSS_ERR_ARG;
-  // single instance, simple shear, no rolling springs (the taped model)
-  if (h->K != 1 || h->g.wave || h->g.k_r > 0.0) return DSS_ERR_ARG;
-  if (!h->have_state) return DSS_ERR_STATE;
-  ENTER(h);
-  const int64_t nseg = (nsteps + ckpt_every - 1) / ckpt_every;
-  std::vector<std::vector<char>> ck((size_t)nseg);
-  int r;
-  auto save_to = [&](std::vector<char>& buf) -> int {
-    size_t len = 0;
-    int e = dss_save(h, nullptr, &len);
-    if (e) return e;
-    buf.resize(len);
-    return dss_save(h, buf.data(), &len);
-  };
-  // ---- forward, with checkpoints and the objective
-  std::vector<double> Wh(9 * (size_t)nsteps);
-  CK(cudaMemcpy(Wh.data(), weights, sizeof(double) * 9 * nsteps, cudaMemcpyDefault));
-  const bool from_forces = initial_forces != 0;
-  std::vector<double> Jsig(9);
-  double Jacc = 0.0;
-  for (int64_t s = 0; s < nseg; ++s) {
-    if ((r = save_to(ck[(size_t)s]))) return r;
-    const int64_t k1 = std::min<int64_t>(ckpt_every, nsteps - s * ckpt_every);
-    for (int64_t k = 0; k < k1; ++k) {
-      if ((r = dss_step(h, 1))) return r;
-      CK(cudaMemcpyAsync(Jsig.data(), h->sigma, 9 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-      CK(cudaStreamSynchronize(h->stream));
-      const int64_t n1 = s * ckpt_every + k;
-      for (int q = 0; q < 9; ++q) Jacc += Wh[9 * n1 + q] * Jsig[q];
+  return guard([&]() -> int {
+    if (!h || nsteps < 1 || ckpt_every < 1 || !weights) return DSS_ERR_ARG;
+    // single instance, simple shear, no rolling springs (the taped model)
+    if (h->K != 1 || h->g.wave || h->g.k_r > 0.0) return DSS_ERR_ARG;
+    if (!h->have_state) return DSS_ERR_STATE;
+    ENTER(h);
+    const int64_t nseg = (nsteps + ckpt_every - 1) / ckpt_every;
+    std::vector<std::vector<char>> ck((size_t)nseg);
+    int r;
+    auto save_to = [&](std::vector<char>& buf) -> int {
+      size_t len = 0;
+      int e = dss_save(h, nullptr, &len);
+      if (e) return e;
+      buf.resize(len);
+      return dss_save(h, buf.data(), &len);
+    };
+    // ---- forward, with checkpoints and the objective
+    std::vector<double> Wh(9 * (size_t)nsteps);
+    CK(cudaMemcpy(Wh.data(), weights, sizeof(double) * 9 * nsteps, cudaMemcpyDefault));
+    const bool from_forces = initial_forces != 0;
+    std::vector<double> Jsig(9);
+    double Jacc = 0.0;
+    for (int64_t s = 0; s < nseg; ++s) {
+      if ((r = save_to(ck[(size_t)s]))) return r;
+      const int64_t k1 = std::min<int64_t>(ckpt_every, nsteps - s * ckpt_every);
+      for (int64_t k = 0; k < k1; ++k) {
+        if ((r = dss_step(h, 1))) return r;
+        CK(cudaMemcpyAsync(Jsig.data(), h->sigma, 9 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        const int64_t n1 = s * ckpt_every + k;
+        for (int q = 0; q < 9; ++q) Jacc += Wh[9 * n1 + q] * Jsig[q];
+      }
     }
-  }
-  std::vector<char> ck_end;
-  if ((r = save_to(ck_end))) return r;
-  // ---- reverse
-  const int slots = (int)std::min<int64_t>(ckpt_every, nsteps);
-  if ((r = adj_alloc(h, slots, nsteps))) return r;
-  if ((r = adj_upload_weights(h, Wh.data(), nsteps))) return r;
-  adj_zero(h);
-  for (int64_t s = nseg - 1; s >= 0; --s) {
-    if ((r = dss_load(h, ck[(size_t)s].data(), ck[(size_t)s].size()))) return r;
-    const int64_t k1 = std::min<int64_t>(ckpt_every, nsteps - s * ckpt_every);
-    // taped replay (the same kernels as dss_step, without the graph)
-    for (int64_t k = 0; k < k1; ++k) {
-      const int w = 1 - h->cur;
-      launch_sort(h, true, h->cur, w);
-      launch_enumerate(h, w, 1 - h->hist, 1);
-      adj_tape(h, (int)k, w, 1 - h->hist, h->hist, false);
-      launch_forces(h, w, 1 - h->hist, h->hist, 1, G_STEP, nullptr, nullptr);
-      h->cur = w;
-      h->hist = 1 - h->hist;
-      h->last_list = h->hist;
+    std::vector<char> ck_end;
+    if ((r = save_to(ck_end))) return r;
+    // ---- reverse
+    const int slots = (int)std::min<int64_t>(ckpt_every, nsteps);
+    if ((r = adj_alloc(h, slots, nsteps))) return r;
+    if ((r = adj_upload_weights(h, Wh.data(), nsteps))) return r;
+    adj_zero(h);
+    for (int64_t s = nseg - 1; s >= 0; --s) {
+      if ((r = dss_load(h, ck[(size_t)s].data(), ck[(size_t)s].size()))) return r;
+      const int64_t k1 = std::min<int64_t>(ckpt_every, nsteps - s * ckpt_every);
+      // taped replay (the same kernels as dss_step, without the graph)
+      for (int64_t k = 0; k < k1; ++k) {
+        const int w = 1 - h->cur;
+        launch_sort(h, true, h->cur, w);
+        launch_enumerate(h, w, 1 - h->hist, 1);
+        adj_tape(h, (int)k, w, 1 - h->hist, h->hist, false);
+        launch_forces(h, w, 1 - h->hist, h->hist, 1, G_STEP, nullptr, nullptr);
+        h->cur = w;
+        h->hist = 1 - h->hist;
+        h->last_list = h->hist;
+      }
+      CK(cudaGetLastError());
+      if ((r = sync_status(h))) return r;
+      if ((r = status_error(h))) { clear_err(h); return r; }
+      for (int64_t k = k1 - 1; k >= 0; --k) adj_reverse(h, (int)k, s * ckpt_every + k, false);
+      CK(cudaGetLastError());
+    }
+    if (from_forces) {
+      // alpha^0 came from a force evaluation at the initial state with an
+      // empty history: its reverse adds the dependence through alpha^0
+      if ((r = dss_load(h, ck[0].data(), ck[0].size()))) return r;
+      adj_tape(h, 0, h->cur, h->hist, h->hist, true);
+      CK(cudaStreamSynchronize(h->stream));   // the tape's pair count is read on the host
+      adj_reverse(h, 0, 0, true);
     }
     CK(cudaGetLastError());
     if ((r = sync_status(h))) return r;
     if ((r = status_error(h))) { clear_err(h); return r; }
-    for (int64_t k = k1 - 1; k >= 0; --k) adj_reverse(h, (int)k, s * ckpt_every + k, false);
-    CK(cudaGetLastError());
-  }
-  if (from_forces) {
-    // alpha^0 came from a force evaluation at the initial state with an
-    // empty history: its reverse adds the dependence through alpha^0
-    if ((r = dss_load(h, ck[0].data(), ck[0].size()))) return r;
-    adj_tape(h, 0, h->cur, h->hist, h->hist, true);
-    CK(cudaStreamSynchronize(h->stream));   // the tape's pair count is read on the host
-    adj_reverse(h, 0, 0, true);
-  }
-  CK(cudaGetLastError());
-  if ((r = sync_status(h))) return r;
-  if ((r = status_error(h))) { clear_err(h); return r; }
-  // outputs, then back to the state after the rollout
-  AdjBuf* A = h->adj;
-  const size_t b3 = sizeof(double) * 3 * (size_t)h->n;
-  if (dJ_dx0) CK(cudaMemcpyAsync(dJ_dx0, A->xb, b3, cudaMemcpyDefault, h->stream));
-  if (dJ_du0) CK(cudaMemcpyAsync(dJ_du0, A->ub, b3, cudaMemcpyDefault, h->stream));
-  if (dJ_dw0) CK(cudaMemcpyAsync(dJ_dw0, A->wb, b3, cudaMemcpyDefault, h->stream));
-  if (dJ_dalpha0) CK(cudaMemcpyAsync(dJ_dalpha0, A->ab, b3, cudaMemcpyDefault, h->stream));
-  if (dJ_dbeta0) CK(cudaMemcpyAsync(dJ_dbeta0, A->bb, b3, cudaMemcpyDefault, h->stream));
-  if (dJ_dparams) CK(cudaMemcpyAsync(dJ_dparams, A->thb, 5 * sizeof(double), cudaMemcpyDefault, h->stream));
-  CK(cudaStreamSynchronize(h->stream));
-  if (J) *J = Jacc;
-  return dss_load(h, ck_end.data(), ck_end.size());
+    // outputs, then back to the state after the rollout
+    AdjBuf* A = h->adj;
+    const size_t b3 = sizeof(double) * 3 * (size_t)h->n;
+    if (dJ_dx0) CK(cudaMemcpyAsync(dJ_dx0, A->xb, b3, cudaMemcpyDefault, h->stream));
+    if (dJ_du0) CK(cudaMemcpyAsync(dJ_du0, A->ub, b3, cudaMemcpyDefault, h->stream));
+    if (dJ_dw0) CK(cudaMemcpyAsync(dJ_dw0, A->wb, b3, cudaMemcpyDefault, h->stream));
+    if (dJ_dalpha0) CK(cudaMemcpyAsync(dJ_dalpha0, A->ab, b3, cudaMemcpyDefault, h->stream));
+    if (dJ_dbeta0) CK(cudaMemcpyAsync(dJ_dbeta0, A->bb, b3, cudaMemcpyDefault, h->stream));
+    if (dJ_dparams) CK(cudaMemcpyAsync(dJ_dparams, A->thb, 5 * sizeof(double), cudaMemcpyDefault, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (J) *J = Jacc;
+    return dss_load(h, ck_end.data(), ck_end.size());
+  });
 }
 
 int dss_selftest_bounded_wait(void* cuda_stream) {

@@ -202,14 +202,14 @@ __device__ __forceinline__ PairRes<float> pair_eval_mixed(const Geo& g, const In
   if (le == -1 ? 2 * wx > nx : 2 * wx >= nx) wx -= nx;
   int wz = (cj >> 20) - (ci >> 20);
   if (wz > R) wz -= nz; else if (wz < -R) wz += nz;
-  FF cx = FF{(float)wx * I.csf[0], (float)wx * I.cs_lo[0]};
+  FF cx = cell_shift(wx, I.csf[0], I.cs_lo[0]);
   if (le == 1) cx = ff_add(cx, FF{sg.offr_hi, sg.offr_lo});
   else if (le == -1) cx = ff_add(cx, FF{-sg.offr_hi, -sg.offr_lo});
   const FF dxf = ff_add(two_sum(pj.x, -pi.x), ff_add(cx, FF{lj.x - li.x, 0.f}));
   const FF dyf = ff_add(two_sum(pj.y, -pi.y),
-                        ff_add(FF{(float)wy * I.csf[1], (float)wy * I.cs_lo[1]}, FF{lj.y - li.y, 0.f}));
+                        ff_add(cell_shift(wy, I.csf[1], I.cs_lo[1]), FF{lj.y - li.y, 0.f}));
   const FF dzf = ff_add(two_sum(pj.z, -pi.z),
-                        ff_add(FF{(float)wz * I.csf[2], (float)wz * I.cs_lo[2]}, FF{lj.z - li.z, 0.f}));
+                        ff_add(cell_shift(wz, I.csf[2], I.cs_lo[2]), FF{lj.z - li.z, 0.f}));
   const FF Sff = ff_add(FF{pi.w, li.w}, FF{pj.w, lj.w});
   const FF r2ff = ff_add(ff_add(ff_sqr(dxf), ff_sqr(dyf)), ff_sqr(dzf));
   const FF numff = ff_add(r2ff, ff_neg(ff_sqr(Sff)));          // r^2 - S^2, ~44 bits
@@ -457,6 +457,14 @@ k_pairs(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ sgk, 
   // as many particles as a block has threads), and a lane meets its pairs in
   // increasing owner order, so its instance changes at most once: the
   // stresslet sum of the first instance is parked in shared memory then.
+  // Each pair's stresslet is formed and added to the thread's sum in the pair
+  // arithmetic's precision (the grid covers every owner once, so a thread
+  // meets P/N pairs on average, one to three in these suspensions); in mixed
+  // precision the lanes of a warp are then summed with compensation (as
+  // accurate as FP64 over 32 values) and every sum beyond the warp (over
+  // warps and blocks) is FP64.  FP64 sums per thread or per lane (conversions
+  // and additions on GB300's narrow FP64 pipe, or a compensated sum in
+  // shared memory) made the kernel 1.4-1.6x slower.
   __shared__ R park[kPairThreads][9];
   const int inst0 = s.inst[min((int)(blockIdx.x * blockDim.x), n - 1)];
   int cur_inst = inst0;
@@ -554,31 +562,53 @@ k_pairs(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ sgk, 
     for (int c = 0; c < 6; ++c) acc[wid][lane][c] = R(0);
     __syncwarp();
   }
-  // FP64 block reduction of the stresslet (fixed tree)
-  // (in mixed precision the 32 lanes of a warp are pre-summed in FP32, the
-  // warps and blocks in FP64)
+  // FP64 block reduction of the stresslet (fixed tree over lanes, warps
+  // and blocks)
   __shared__ double red[kWarps][18];
   const bool moved = cur_inst != inst0;
   // With the wave of Eq. 17 the single-particle stresslets 20/3 pi eta0 a^3
   // E_inf(x) carry a local part, (10/3) pi eta0 a^3 U k cos(k y) on xy and
   // yx: one owner per thread (the grid covers each owner once), added to its
   // instance's slot.
-  R ew0 = R(0), ew1 = R(0);
+  double ew0 = 0.0, ew1 = 0.0;
   if (EXT && g.wave) {
     const int il0 = blockIdx.x * blockDim.x + threadIdx.x;
     if (il0 < n) {
       const double a = s.a[il0];
-      const R e = (R)((10.0 / 3.0) * DSS_PI * g.eta0 * a * a * a * s.wv[il0].y);
+      const double e = (10.0 / 3.0) * DSS_PI * g.eta0 * a * a * a * s.wv[il0].y;
       if (s.inst[il0] == inst0) ew0 = e; else ew1 = e;
     }
   }
+  // one instance in the handle: the second slot is always empty
+  const int nq = g.K > 1 ? 18 : 9;
 #pragma unroll
   for (int q = 0; q < 18; ++q) {
-    R v = q < 9 ? (moved ? park[threadIdx.x][q] : Sx[q]) : (moved ? Sx[q - 9] : R(0));
-    if (q == 1 || q == 3) v += ew0;
-    if (q == 10 || q == 12) v += ew1;
-    for (int dlt = 16; dlt > 0; dlt >>= 1) v += __shfl_down_sync(0xffffffffu, v, dlt);
-    if (lane == 0) red[wid][q] = (double)v;
+    if (q >= nq) {
+      if (lane == 0) red[wid][q] = 0.0;
+      continue;
+    }
+    const R x = q < 9 ? (moved ? park[threadIdx.x][q] : Sx[q]) : (moved ? Sx[q - 9] : R(0));
+    const double e = (q == 1 || q == 3) ? ew0 : ((q == 10 || q == 12) ? ew1 : 0.0);
+    if constexpr (MIXED) {
+      // over the 32 lanes as a compensated FP32 sum (hi + lo, Knuth's TwoSum
+      // per addition: ~48 significant bits), one FP64 value per warp: an
+      // FP64 butterfly on every lane costs ~90 additions per thread on
+      // GB300's narrow FP64 pipe (+40% on this kernel)
+      FF v = two_sum(x, (float)e);
+      v.lo += (float)(e - (double)(float)e);
+      for (int dlt = 16; dlt > 0; dlt >>= 1) {
+        const float h2 = __shfl_down_sync(0xffffffffu, v.hi, dlt);
+        const float l2 = __shfl_down_sync(0xffffffffu, v.lo, dlt);
+        const FF t = two_sum(v.hi, h2);
+        v.hi = t.hi;
+        v.lo = (v.lo + l2) + t.lo;
+      }
+      if (lane == 0) red[wid][q] = (double)v.hi + (double)v.lo;
+    } else {
+      double v = (double)x + e;
+      for (int dlt = 16; dlt > 0; dlt >>= 1) v += __shfl_down_sync(0xffffffffu, v, dlt);
+      if (lane == 0) red[wid][q] = v;
+    }
   }
   int c = ncont;
   for (int dlt = 16; dlt > 0; dlt >>= 1) c += __shfl_down_sync(0xffffffffu, c, dlt);
@@ -888,19 +918,25 @@ __device__ __forceinline__ bool gather_one(const Geo& g, const InstGeo* __restri
     F[0] += kd * vx; F[1] += kd * v4.y; F[2] += kd * v4.z;
     T[0] += kr * w4.x; T[1] += kr * w4.y; T[2] += kr * w4.z;
   } else {
-    const double kd = -g.k6 * a, kr = -g.k8 * a * a * a;
+    // FP64: each product and sum rounded on its own (no contraction), in the
+    // order of the plain evaluation -6 pi eta0 a (u - U_inf)
+    const double kd = __dmul_rn(-g.k6, a);
+    const double kr = __dmul_rn(__dmul_rn(__dmul_rn(-g.k8, a), a), a);
+    double vx, wz;
     if (EXT && g.wave) {
       // Faxen velocity (1 + a^2/6 Laplacian) U_inf,x and local Omega_inf
-      F[0] += kd * (u[0] - gd * yj - (1.0 - a * a * fx) * wq.x);
-      T[2] += kr * (w[2] + 0.5 * (gd + wq.y));
+      vx = u[0] - gd * yj - (1.0 - a * a * fx) * wq.x;
+      wz = w[2] + 0.5 * (gd + wq.y);
     } else {
-      F[0] += kd * (u[0] - gd * yj);
-      T[2] += kr * (w[2] + 0.5 * gd);
+      vx = __dsub_rn(u[0], __dmul_rn(gd, yj));
+      wz = __dadd_rn(w[2], __dmul_rn(0.5, gd));
     }
-    F[1] += kd * u[1];
-    F[2] += kd * u[2];
-    T[0] += kr * w[0];
-    T[1] += kr * w[1];
+    F[0] = __dadd_rn(F[0], __dmul_rn(kd, vx));
+    F[1] = __dadd_rn(F[1], __dmul_rn(kd, u[1]));
+    F[2] = __dadd_rn(F[2], __dmul_rn(kd, u[2]));
+    T[0] = __dadd_rn(T[0], __dmul_rn(kr, w[0]));
+    T[1] = __dadd_rn(T[1], __dmul_rn(kr, w[1]));
+    T[2] = __dadd_rn(T[2], __dmul_rn(kr, wz));
   }
   bool bad = false;
   if (!(isfinite(F[0]) && isfinite(F[1]) && isfinite(F[2]) && isfinite(T[0]) && isfinite(T[1]) &&
@@ -914,30 +950,47 @@ __device__ __forceinline__ bool gather_one(const Geo& g, const InstGeo* __restri
     return bad;
   }
   // accelerations: m = 4/3 pi rho a^3, I = 2/5 m a^2
-  R imr, iIr;
+  R al[3], aw[3];
   if constexpr (MIXED) {
     const float af = (float)a;
-    imr = 1.0f / (g.f.mass_c * af * af * af);
-    iIr = imr * (2.5f / (af * af));
+    const float imr = 1.0f / (g.f.mass_c * af * af * af);
+    const float iIr = imr * (2.5f / (af * af));
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      al[c] = F[c] * imr;
+      aw[c] = T[c] * iIr;
+    }
   } else {
-    const double m = 4.0 / 3.0 * DSS_PI * g.rho * a * a * a;
-    imr = 1.0 / m;
-    iIr = imr * (2.5 / (a * a));
+    // FP64: F/m and T/I as IEEE divisions, m and I formed left to right
+    const double m = __dmul_rn(__dmul_rn(__dmul_rn(__dmul_rn(4.0 / 3.0 * DSS_PI, g.rho), a), a), a);
+    const double I = __dmul_rn(__dmul_rn(__dmul_rn(0.4, m), a), a);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      al[c] = __ddiv_rn(F[c], m);
+      aw[c] = __ddiv_rn(T[c], I);
+    }
   }
-  const R al[3] = {F[0] * imr, F[1] * imr, F[2] * imr};
-  const R aw[3] = {T[0] * iIr, T[1] * iIr, T[2] * iIr};
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     s.al[c * n + j] = al[c];
     s.aw[c * n + j] = aw[c];
   }
   if (stepm) {
-    // Eq. 15d from u^{n+1/2}: u^{n+1} = u^{n+1/2} + dt/2 alpha^{n+1}
+    // Eq. 15d from u^{n+1/2}: u^{n+1} = u^{n+1/2} + dt/2 alpha^{n+1} (FP64
+    // mode: product and sum rounded separately)
     const double hdt = g.hdt;
+    if constexpr (MIXED) {
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      s.u[c * n + j] = __fma_rn(hdt, (double)al[c], u[c]);
-      s.w[c * n + j] = __fma_rn(hdt, (double)aw[c], w[c]);
+      for (int c = 0; c < 3; ++c) {
+        s.u[c * n + j] = __fma_rn(hdt, (double)al[c], u[c]);
+        s.w[c * n + j] = __fma_rn(hdt, (double)aw[c], w[c]);
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        s.u[c * n + j] = __dadd_rn(u[c], __dmul_rn(hdt, (double)al[c]));
+        s.w[c * n + j] = __dadd_rn(w[c], __dmul_rn(hdt, (double)aw[c]));
+      }
     }
   }
   return bad;
@@ -1029,7 +1082,7 @@ void launch_forces_t(dss_handle* h, int stbuf, int work_list, int hist_list, int
   const int pb = pair_grid_blocks(h);
   const bool mixed = h->g.precision == DSS_MIXED;
   prof_mark(h, 5);
-  const bool big = pb > 3 * h->sms;
+  const bool big = h->tune_pairs_minb ? h->tune_pairs_minb == 4 : pb > 3 * h->sms;
   if (mixed && big)
     k_pairs<true, 4, EXT><<<pb, kPairThreads, 0, h->stream>>>(
         h->g, h->ig, h->sg, h->st[stbuf], h->lb[work_list], h->lb[hist_list], h->posf, h->own, h->bw_count,

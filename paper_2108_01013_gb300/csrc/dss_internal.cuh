@@ -10,6 +10,7 @@
 
 #define DSS_PI 3.14159265358979323846
 #define DSS_PROF_KERNELS 7
+#define DSS_MULTI_STEPS 8
 
 // Device status word layout (int32 slots in DevStatus::w).
 enum {
@@ -308,6 +309,15 @@ __device__ __forceinline__ FF ff_add(FF a, FF b) {
   return fast_two_sum(s.hi, s.lo);
 }
 __device__ __forceinline__ FF ff_neg(FF a) { return FF{-a.hi, -a.lo}; }
+// w whole cells of edge (cs_hi + cs_lo) as a double-float: the product of
+// the FP32 words is made exact with Dekker's TwoProduct (w cs_hi needs more
+// than 24 bits once |w| >= 3: a pair several cells apart, or across the
+// Lees-Edwards layer).
+__device__ __forceinline__ FF cell_shift(int w, float cs_hi, float cs_lo) {
+  const float wf = (float)w;
+  const float p = wf * cs_hi;
+  return FF{p, fmaf(wf, cs_hi, -p) + wf * cs_lo};
+}
 __device__ __forceinline__ FF ff_sqr(FF a) {
   const float p = a.hi * a.hi;
   const float e = fmaf(a.hi, a.hi, -p);
@@ -473,6 +483,15 @@ struct dss_handle {
   // graphs: one per (cur, hist) combination
   cudaGraphExec_t step_graph[4];
   bool graph_ok[4];
+  // DSS_MULTI_STEPS consecutive steps in one graph (an even count: the
+  // buffers are back in their roles after it), one per (cur, hist) start
+  cudaGraphExec_t multi_graph[4];
+  bool multi_ok[4];
+  // kernel shapes chosen by dss_autotune_kernels (0: the built-in rule):
+  // resident pair blocks per SM the register budget is cut for (3 or 4), and
+  // candidates loaded ahead in the enumeration's loop (1 or 4)
+  int tune_pairs_minb;
+  int tune_enum_unr;
   int64_t bytes;
   int64_t host_steps_done;
   AdjBuf* adj;               // adjoint buffers (allocated by dss_adjoint)
@@ -491,6 +510,7 @@ void launch_images_out(dss_handle* h, int* out);
 void launch_mark(dss_handle* h);
 void launch_dispersion(dss_handle* h, double* sums);
 void launch_clusters(dss_handle* h, int* parent, int* minid, int* count, int* label);
+void launch_phi_profile(dss_handle* h, int nbins, double a_split, const double* unit, unsigned long long* acc);
 int pair_grid_blocks(const dss_handle* h);
 void launch_scan(dss_handle* h, const int* in, int* out, int count, int which, bool zero_in);
 int scan_tiles_for(int count);

@@ -362,7 +362,7 @@ void launch_enumerate(dss_handle* h, int stbuf, int dst_list, int adv) {
   auto kc = ech ? k_enumerate_classes<true> : k_enumerate_classes<false>;
   // cells holding many particles (long ranges, large radius ratios) take
   // the candidate loop with four loads in flight
-  const bool crowded = h->n >= 8 * (int64_t)h->g.ncell;
+  const bool crowded = h->tune_enum_unr ? h->tune_enum_unr == 4 : h->n >= 8 * (int64_t)h->g.ncell;
   // with electro-chemical forces over crowded cells (long ranges) most
   // listed pairs lie beyond the lubrication range: rows put the others
   // first, so that the pair kernel's warps meet runs of pairs without

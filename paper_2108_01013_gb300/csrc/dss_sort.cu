@@ -13,10 +13,12 @@ namespace {
 
 constexpr int kThreads = 256;
 
-// Predictor of Eq. 15a-b (as fused multiply-adds: GB300's FP64 pipe bounds
-// this kernel) and the wrap of Eq. 16 for one particle; computed once per
-// step and stored for the gather.  Returns the y crossing (-1 out through
-// the top, +1 bottom).
+// Predictor of Eq. 15a-b and the wrap of Eq. 16 for one particle; computed
+// once per step and stored for the gather.  In FP64 mode each product and
+// sum is rounded separately (the trajectory then differs from a plain FP64
+// evaluation only through the order of the force sums); in mixed precision
+// as fused multiply-adds (GB300's narrow FP64 pipe bounds this kernel).
+// Returns the y crossing (-1 out through the top, +1 bottom).
 // Comparisons for the wrap on the IEEE bit patterns (integer instructions
 // instead of GB300's narrow FP64 pipe).  For L > 0 and any finite v the
 // signed 64-bit order of the patterns is the order of the values on the
@@ -46,12 +48,23 @@ __device__ __forceinline__ Pred predict_one(const Geo& g, const InstGeo& I, cons
     const double hdt2 = g.hdt2;
     const double hdt = g.hdt;
     double ax = s.al[i], ay = s.al[n + i], az = s.al[2 * n + i];
-    x = __fma_rn(hdt2, ax, __fma_rn(dt, ux, x));
-    y = __fma_rn(hdt2, ay, __fma_rn(dt, uy, y));
-    z = __fma_rn(hdt2, az, __fma_rn(dt, uz, z));
-    ux = __fma_rn(hdt, ax, ux);
-    uy = __fma_rn(hdt, ay, uy);
-    uz = __fma_rn(hdt, az, uz);
+    if (g.precision == DSS_FP64) {
+      // FP64 mode: every product and sum rounded on its own, in the order
+      // x + dt u + (dt/2 dt) alpha of Eq. 15a (no contraction)
+      x = __dadd_rn(__dadd_rn(x, __dmul_rn(dt, ux)), __dmul_rn(hdt2, ax));
+      y = __dadd_rn(__dadd_rn(y, __dmul_rn(dt, uy)), __dmul_rn(hdt2, ay));
+      z = __dadd_rn(__dadd_rn(z, __dmul_rn(dt, uz)), __dmul_rn(hdt2, az));
+      ux = __dadd_rn(ux, __dmul_rn(hdt, ax));
+      uy = __dadd_rn(uy, __dmul_rn(hdt, ay));
+      uz = __dadd_rn(uz, __dmul_rn(hdt, az));
+    } else {
+      x = __fma_rn(hdt2, ax, __fma_rn(dt, ux, x));
+      y = __fma_rn(hdt2, ay, __fma_rn(dt, uy, y));
+      z = __fma_rn(hdt2, az, __fma_rn(dt, uz, z));
+      ux = __fma_rn(hdt, ax, ux);
+      uy = __fma_rn(hdt, ay, uy);
+      uz = __fma_rn(hdt, az, uz);
+    }
     // Lees-Edwards wrap: leaving through y >= L_y re-enters at the bottom
     // shifted by -off along x with u_x - gdot L_y, and vice versa
     const double Ly = I.L[1];
@@ -198,8 +211,12 @@ k_rank_gather(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__
   dst.u[f] = p.ux; dst.u[n + f] = p.uy; dst.u[2 * n + f] = p.uz;
   if (predict) {
     const double hdt = g.hdt;
-    for (int c = 0; c < 3; ++c)
-      dst.w[c * n + f] = __fma_rn(hdt, src.aw[c * n + o], src.w[c * n + o]);
+    if (g.precision == DSS_FP64)
+      for (int c = 0; c < 3; ++c)
+        dst.w[c * n + f] = __dadd_rn(src.w[c * n + o], __dmul_rn(hdt, src.aw[c * n + o]));
+    else
+      for (int c = 0; c < 3; ++c)
+        dst.w[c * n + f] = __fma_rn(hdt, src.aw[c * n + o], src.w[c * n + o]);
   } else {
     for (int c = 0; c < 3; ++c) {
       dst.w[c * n + f] = src.w[c * n + o];
@@ -207,7 +224,7 @@ k_rank_gather(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__
       dst.aw[c * n + f] = src.aw[c * n + o];
     }
   }
-  double a = src.a[o];
+  const double a = src.a[o];
   dst.a[f] = a;
   dst.id[f] = id;
   dst.inst[f] = inst;

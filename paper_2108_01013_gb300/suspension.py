@@ -219,6 +219,14 @@ class Suspension:
                   "dss_contact_clusters")
         return label, int(cnt.value)
 
+    def phi_profile(self, nbins: int, a_split: float) -> np.ndarray:
+        """(K, 2, nbins): local volume fraction along y in nbins slabs of the
+        particles with radius <= a_split (class 0) and > a_split (class 1)."""
+        out = np.zeros((self._instances(), 2, int(nbins)))
+        nat.check(self.lib.dss_phi_profile(self._h, int(nbins), float(a_split), c_void_p(out.ctypes.data)),
+                  "dss_phi_profile")
+        return out
+
     def set_history(self, keys, xi, xr=None):
         """Replace the contact history (keys lo_id << 32 | hi_id, sliding stretch
         lo -> hi, optional rolling stretch)."""
@@ -256,6 +264,19 @@ class Suspension:
         nat.check(self.lib.dss_autotune(self._h, int(trial_steps), f.shape[0], f.ctypes.data_as(dp),
                                         ms.ctypes.data_as(dp), byref(cs)), "dss_autotune")
         return cs.value, dict(zip(f.tolist(), ms.tolist()))
+
+    def autotune_kernels(self, trial_steps: int = 20):
+        """Time the kernel shapes (pair-kernel blocks per SM 3 or 4, candidates
+        ahead in the enumeration 1 or 4), keep the fastest, restore the
+        state.  Returns ((blocks, ahead), {(blocks, ahead): ms/step})."""
+        ms = np.zeros(4)
+        ch = np.zeros(2, dtype=np.int32)
+        dp = ctypes.POINTER(c_double)
+        nat.check(self.lib.dss_autotune_kernels(self._h, int(trial_steps), ms.ctypes.data_as(dp),
+                                                ch.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))),
+                  "dss_autotune_kernels")
+        keys = [(3, 1), (3, 4), (4, 1), (4, 4)]
+        return (int(ch[0]), int(ch[1])), dict(zip(keys, ms.tolist()))
 
     def adjoint(self, nsteps: int, weights, *, ckpt_every: int = 20, initial_forces: bool = True):
         """Reverse-mode gradient of J = sum_n sum_q weights[n, q] sigma^{n+1}_q

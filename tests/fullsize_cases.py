@@ -49,7 +49,3 @@ def contact_history(oracle, po, off, x, a, ids, u, w, idx, seed, scale=3e-4):
 def partners(pairs, k):
     """Sorted partner ids of id k in a (lo, hi) pair list."""
     return np.sort(np.concatenate([pairs[pairs[:, 0] == k, 1], pairs[pairs[:, 1] == k, 0]]))
-
-
-def relerr(a, b):
-    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b))

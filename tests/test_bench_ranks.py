@@ -1,8 +1,8 @@
 """The benchmark's multi-rank host logic (replicas only: no data-path
-collective) on two CPU processes over gloo: rates are whole-job figures over
-the slowest rank, every mode table is reduced the same way on every rank,
-each rank packs its own seeded workload, and the reference arm runs on rank
-0 alone."""
+collective) on two CPU processes over gloo: rates are whole-job figures (the
+units of all ranks, summed) over the slowest rank, every mode table is
+reduced the same way on every rank, each rank packs its own seeded workload,
+and the reference arm runs on rank 0 alone."""
 import os
 import socket
 
@@ -24,6 +24,8 @@ def _worker(rank, world, port, q):
     try:
         t = [2.0, 5.0][rank]
         rate = bench.job_rate(1000.0, t, world)
+        # ranks whose seeded workloads differ in size: units are summed
+        rate_uneven = bench.job_rate([1000.0, 400.0][rank], t, world)
         slow = bench.max_over_ranks([0.3, 0.1][rank], world)
         extra = {"fp64": {"value": 100.0 / [1.0, 4.0][rank], "ms_per_step": [1.0, 4.0][rank]},
                  "echem": {"config": {"workload": "x"},
@@ -31,7 +33,7 @@ def _worker(rank, world, port, q):
                            "b": {"value": 7.0, "ms_per_step": 1.5}},
                  "ratio": 3.0}
         bench.reduce_modes(extra, world)
-        q.put((rank, rate, slow, extra))
+        q.put((rank, rate, rate_uneven, slow, extra))
     finally:
         dist.destroy_process_group()
 
@@ -46,20 +48,22 @@ def test_rates_over_the_slowest_rank():
         p.start()
     out = {}
     for _ in procs:
-        rank, rate, slow, extra = q.get(timeout=120)
-        out[rank] = (rate, slow, extra)
+        rank, rate, rate_uneven, slow, extra = q.get(timeout=120)
+        out[rank] = (rate, rate_uneven, slow, extra)
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
     for rank in (0, 1):
-        rate, slow, extra = out[rank]
+        rate, rate_uneven, slow, extra = out[rank]
         assert rate == pytest.approx(2 * 1000.0 / 5.0)
+        assert rate_uneven == pytest.approx((1000.0 + 400.0) / 5.0)
         assert slow == pytest.approx(0.3)
         # fp64: rank 0 ran 100 units at 1 ms, rank 1 at 4 ms -> 2 x 100 units / 4 ms
         assert extra["fp64"]["ms_per_step"] == pytest.approx(4.0)
         assert extra["fp64"]["value"] == pytest.approx(2 * 100.0 / 4.0)
         assert extra["echem"]["a"]["ms_per_step"] == pytest.approx(3.0)
-        assert extra["echem"]["a"]["value"] == pytest.approx(2 * 10.0 * [2.0, 3.0][rank] / 3.0)
+        # units per step of each rank (value x ms) summed over the slowest rank's ms
+        assert extra["echem"]["a"]["value"] == pytest.approx((10.0 * 2.0 + 10.0 * 3.0) / 3.0)
         assert extra["echem"]["b"]["value"] == pytest.approx(14.0)
         assert extra["ratio"] == 3.0
 

@@ -1,9 +1,13 @@
 """Reverse-mode gradients of a rollout (dss_adjoint) against the FP64 adjoint
 oracle (plain PyTorch autograd over the oracle's model), against central
 finite differences of the GPU forward, and for independence of the
-checkpoint interval (the replayed segments repeat the forward bit for bit)."""
+checkpoint interval (the replayed segments repeat the forward bit for bit).
+Gradients with respect to the initial state are compared per particle, the
+parameter gradients one by one (tests/parity.py)."""
 import numpy as np
 import pytest
+
+from parity import check_per_particle, check_scalars
 
 pytestmark = pytest.mark.gpu
 
@@ -21,12 +25,6 @@ def env():
     dss.build()
     synth.build()
     return dict(oracle=oracle, oadj=oadj, dss=dss, synth=synth, torch=torch)
-
-
-def relerr(a, b):
-    a = np.asarray(a)
-    b = np.asarray(b)
-    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
 def _case(env, taper, n=260, seed=61):
@@ -66,12 +64,12 @@ def test_adjoint_matches_oracle_fp64(env, taper):
     o = env["oadj"].gradients(g["box"], g["x"], g["a"], u0, w0, T, W, **th, **kw, nstep0=3)
     r, st = _gpu(env, g, u0, w0, kw, th, T, W)
     assert r["J"] == pytest.approx(o["J"], rel=1e-11)
-    assert relerr(r["params"], o["params"]) < 1e-8
+    check_scalars(r["params"], o["params"], 1e-8, floor=1e-6, what="dJ/dtheta")
     for k in range(5):
         assert r["params"][k] == pytest.approx(o["params"][k], rel=1e-7, abs=1e-12 * abs(o["J"]))
-    assert relerr(r["x0"], o["x0"]) < 1e-8
-    assert relerr(r["u0"], o["u0"]) < 1e-8
-    assert relerr(r["w0"], o["w0"]) < 1e-8
+    check_per_particle(r["x0"], o["x0"], 1e-8, what="dJ/dx0")
+    check_per_particle(r["u0"], o["u0"], 1e-8, what="dJ/du0")
+    check_per_particle(r["w0"], o["w0"], 1e-8, what="dJ/dw0")
     assert np.abs(r["alpha0"]).max() == 0.0
     # the handle ends after the rollout
     box = g["box"]
@@ -101,7 +99,7 @@ def test_adjoint_mixed_precision_vs_oracle(env):
     assert r["J"] == pytest.approx(o["J"], rel=1e-6)
     for k in range(5):
         assert r["params"][k] == pytest.approx(o["params"][k], rel=1e-4, abs=1e-9 * abs(o["J"]))
-    assert relerr(r["x0"], o["x0"]) < 1e-4
+    check_per_particle(r["x0"], o["x0"], 1e-4, floor=0.1, what="dJ/dx0 (mixed)")
 
 
 def test_adjoint_with_echem_matches_oracle(env):
@@ -123,10 +121,10 @@ def test_adjoint_with_echem_matches_oracle(env):
     o = env["oadj"].gradients(g["box"], g["x"], g["a"], u0, w0, T, W, **th, **kw, nstep0=3)
     r, _ = _gpu(env, g, u0, w0, kw, th, T, W)
     assert r["J"] == pytest.approx(o["J"], rel=1e-11)
-    assert relerr(r["params"], o["params"]) < 1e-8
-    assert relerr(r["x0"], o["x0"]) < 1e-8
-    assert relerr(r["u0"], o["u0"]) < 1e-8
-    assert relerr(r["w0"], o["w0"]) < 1e-8
+    check_scalars(r["params"], o["params"], 1e-8, floor=1e-6, what="dJ/dtheta")
+    check_per_particle(r["x0"], o["x0"], 1e-8, what="dJ/dx0")
+    check_per_particle(r["u0"], o["u0"], 1e-8, what="dJ/du0")
+    check_per_particle(r["w0"], o["w0"], 1e-8, what="dJ/dw0")
 
 
 def test_autograd_function_and_tied_parameters(env):
@@ -148,7 +146,7 @@ def test_autograd_function_and_tied_parameters(env):
     assert J.item() == pytest.approx(o["J"], rel=1e-11)
     assert float(kn.grad) == pytest.approx(o["params"][0] + 0.5 * o["params"][1], rel=1e-7)
     assert float(mu.grad) == pytest.approx(o["params"][3], rel=1e-7)
-    assert relerr(x0.grad.numpy(), o["x0"]) < 1e-8
+    check_per_particle(x0.grad.numpy(), o["x0"], 1e-8, what="dJ/dx0")
 
 
 def test_adjoint_20k_rollout_vs_central_differences(env):
@@ -207,3 +205,59 @@ def test_adjoint_20k_rollout_vs_central_differences(env):
         ad = float((r["x0"] * v).sum())
         assert noise < 1e-2 * abs(fds[0])
         assert abs(ad - fds[0]) <= 1e-4 * abs(fds[0]) + 2.0 * noise
+
+
+def test_adjoint_20k_rollout_mixed_vs_central_differences(env):
+    """The differentiable-rollout workload in the precision the benchmark
+    runs it in: 20,000 spheres, 200 steps, checkpoint every 20, FP32 pair
+    forces with FP64 state (the reverse sweep in FP64 on the taped mixed
+    forward).  The adjoint's parameter gradients against central differences
+    of the same mixed forward, with the event set of the rollout (pairs and
+    contacts of every step) equal on both sides of each difference; the
+    difference quotient is taken at two step sizes and their spread (the
+    FP32 rounding of the forward) is allowed for on top of 1e-4."""
+    dss = env["dss"]
+    synth = env["synth"]
+    g = synth.generate(synth.SPECS["c5"])
+    box = g["box"]
+    T = 200
+    kw = dict(shear_rate=1.0, dt=1e-4, lub_taper=0.2)
+    th = dict(kn=1e4, kt=5e3, gamma_n=1e-3, mu=0.5, delta_lub=0.1)
+    W = dss.viscosity_weights(T, shear_rate=1.0)
+    n = g["a"].shape[0]
+    u0 = np.zeros((3, n))
+    u0[0] = g["x"][1]
+    w0 = np.zeros((3, n))
+    w0[2] = -0.5
+
+    def make(th_):
+        p = dss.default_params(box, precision="mixed", **th_, **kw)
+        return dss.Suspension(g["x"], g["a"], box, p, ids=g["ids"], u=u0, w=w0)
+
+    s = make(th)
+    r = s.adjoint(T, W, ckpt_every=20)
+    s.close()
+
+    def J(th_):
+        s2 = make(th_)
+        v, events = 0.0, []
+        for k in range(T):
+            s2.step(1)
+            v += float((W[k] * s2.stress().reshape(9)).sum())
+            c = s2.counters()
+            events.append((c["npairs"], c["ncontacts"]))
+        s2.close()
+        return v, events
+
+    _, ev0 = J(th)
+    for k, name in ((3, "mu"), (0, "kn"), (4, "delta_lub")):
+        fds = []
+        for rel in (1e-3, 2e-3):
+            h = rel * th[name]
+            jp, evp = J(dict(th, **{name: th[name] + h}))
+            jm, evm = J(dict(th, **{name: th[name] - h}))
+            assert evp == ev0 and evm == ev0, name      # no event changes within the differences
+            fds.append((jp - jm) / (2 * h))
+        noise = abs(fds[0] - fds[1])
+        assert noise < 1e-2 * abs(fds[0]), name
+        assert abs(r["params"][k] - fds[0]) <= 1e-4 * abs(fds[0]) + 2.0 * noise, (name, r["params"][k], fds)

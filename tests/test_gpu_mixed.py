@@ -1,13 +1,15 @@
 """Mixed-precision mode (FP32 pair arithmetic; FP64 positions, gaps,
 Lees-Edwards offset, tangential stretch and stress accumulation) against the
-FP64 oracle: forces, torques and stress within 1e-5 relative (normwise over
-the particles) from the same state, and per-step accelerations within 1e-5."""
+FP64 oracle: per particle, forces and torques within 1e-5 (the per-particle
+bound of tests/parity.py), every stress component and reported quantity
+(sigma_xy, N1, N2, Pi) within 1e-5 of its own value from the same state, and
+the per-step accelerations within 1e-5 per particle."""
 import numpy as np
 import pytest
 
-pytestmark = pytest.mark.gpu
+from parity import KAPPA_MIXED, MIXED_TOL, check_forces, check_per_particle, check_stress
 
-MIXED_TOL = 1e-5
+pytestmark = pytest.mark.gpu
 
 
 @pytest.fixture(scope="module")
@@ -21,10 +23,6 @@ def env():
     oracle.build()
     dss.build()
     return dict(oracle=oracle, dss=dss, synth=synth)
-
-
-def relerr(a, b):
-    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b))
 
 
 def _state_with_history(env, n, phi, seed, gdot, mu, steps):
@@ -47,10 +45,11 @@ def test_mixed_forces_and_stress(env, n, phi, seed, gdot, mu):
     s.set_history(keys, xi)
     F, T = s.forces()
     Fo, To, So = o.forces()
+    Fa, Ta = o.force_scale()
     assert o.ncontacts > 20
-    assert relerr(F.cpu().numpy(), Fo) < MIXED_TOL
-    assert relerr(T.cpu().numpy(), To) < MIXED_TOL
-    assert relerr(s.stress(), So) < MIXED_TOL
+    check_forces(F.cpu().numpy(), Fo, Fa, MIXED_TOL, KAPPA_MIXED, "force")
+    check_forces(T.cpu().numpy(), To, Ta, MIXED_TOL, KAPPA_MIXED, "torque")
+    check_stress(s.stress(), So, MIXED_TOL)
     s.close()
 
 
@@ -66,20 +65,32 @@ def test_mixed_one_step_accelerations(env):
     o.step(1)
     sg = s.state()
     so = o.get_state()
-    assert relerr(sg["al"].cpu().numpy(), so["al"]) < MIXED_TOL
-    assert relerr(sg["aw"].cpu().numpy(), so["aw"]) < MIXED_TOL
-    assert relerr(sg["u"].cpu().numpy() - st["u"], so["u"] - st["u"]) < MIXED_TOL
-    assert relerr(s.stress(), o.get_forces()[2]) < MIXED_TOL
+    Fa, Ta = o.force_scale()
+    # alpha = F / m: the force bound scaled by each particle's mass and inertia
+    a = g["a"]
+    m = 4.0 / 3.0 * np.pi * a ** 3
+    check_forces(sg["al"].cpu().numpy(), so["al"], Fa / m, MIXED_TOL, KAPPA_MIXED, "alpha")
+    check_forces(sg["aw"].cpu().numpy(), so["aw"], Ta / (0.4 * m * a * a), MIXED_TOL, KAPPA_MIXED,
+                 "alpha_w")
+    check_forces(sg["u"].cpu().numpy() - st["u"], so["u"] - st["u"], 1e-4 * Fa / m, MIXED_TOL, KAPPA_MIXED,
+                 "u^{n+1} - u^n")
+    check_stress(s.stress(), o.get_forces()[2], MIXED_TOL)
     k1, x1 = s.history()
     k2, x2 = o.get_history()
     np.testing.assert_array_equal(k1, k2)
-    assert relerr(x1, x2) < MIXED_TOL
+    check_per_particle(x1.T, x2.T, MIXED_TOL, floor=0.1, what="stretch")
     s.close()
 
 
 def test_mixed_trajectory_stays_close(env):
-    """100 steps of the 1000-particle configuration: the mixed trajectory
-    stays within 1e-6 of the FP64 oracle in position (relative to a radius)."""
+    """1000 steps of the 1000-particle configuration: the mixed trajectory
+    stays within 1e-6 of the FP64 oracle in position (relative to a radius);
+    after each 100 steps the reported stress quantities (sigma_xy, N1, N2,
+    Pi) are within 1e-5 of their own values and every component within 1e-5
+    of max(its value, 1e-2 |S|) (the off-diagonal yz, xz components average
+    to zero; the trajectories separate by ~1e-7 per step).  Measured on
+    GB300: positions 2.6e-8 and the stress 1.2e-7 (normwise) after 1000
+    steps."""
     synth = env["synth"]
     g = synth.generate(synth.SPECS["c1"])
     box = g["box"]
@@ -88,11 +99,13 @@ def test_mixed_trajectory_stays_close(env):
     s = env["dss"].Suspension(g["x"], g["a"], box, p, ids=g["ids"])
     o = env["oracle"].System(po, g["x"], g["a"], ids=g["ids"])
     o.init_accel()
-    s.step(100)
-    o.step(100)
-    x = s.state()["x"].cpu().numpy()
-    d = np.abs(x - o.get_state()["x"])
-    d = np.minimum(d, box[:, None] - d)
-    assert d.max() < 1e-6
-    assert relerr(s.stress(), o.get_forces()[2]) < 1e-4
+    for chunk in range(10):
+        s.step(100)
+        o.step(100)
+        x = s.state()["x"].cpu().numpy()
+        d = np.abs(x - o.get_state()["x"])
+        d = np.minimum(d, box[:, None] - d)
+        assert d.max() < 1e-6, (chunk, d.max())
+        check_stress(s.stress(), o.get_forces()[2], MIXED_TOL, floor=1e-2,
+                     what="stress after %d steps" % (100 * chunk + 100))
     s.close()

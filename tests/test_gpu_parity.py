@@ -1,15 +1,18 @@
 """GPU path (libdss via the C ABI) against the CPU FP64 oracle.
 
 Neighbour sets must be equal bit for bit (as sorted (lo id, hi id) pairs);
-FP64 forces, torques and stresses within 1e-10 relative (normwise over the
-particles); FP64 trajectories within the bound stated in each test.
+FP64 forces and torques within 1e-10 of each particle's own (the per-particle
+bound of tests/parity.py), every stress component and reported quantity
+within 1e-10 of its own value; the 1000-step FP64 trajectory of the
+1000-particle configuration within 1e-10 per particle.
 """
 import numpy as np
 import pytest
 
-pytestmark = pytest.mark.gpu
+from parity import (FP64_TOL, KAPPA_FP64, MIXED_TOL, KAPPA_MIXED, check_forces, check_per_particle,
+                    check_stress, periodic_diff)
 
-FP64_TOL = 1e-10
+pytestmark = pytest.mark.gpu
 
 
 @pytest.fixture(scope="module")
@@ -28,17 +31,6 @@ def env():
 
 def _params(env, box, **kw):
     return env["dss"].default_params(box, **kw), env["oracle"].make_params(box, **kw)
-
-
-def relerr(a, b):
-    a = np.asarray(a)
-    b = np.asarray(b)
-    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
-
-
-def periodic_diff(x, y, box):
-    d = np.abs(np.asarray(x) - np.asarray(y))
-    return np.minimum(d, box[:, None] - d)
 
 
 CASES = [
@@ -138,18 +130,20 @@ def test_forces_and_stress_fp64(env, seed, nstep, mu):
     S = s.stress()
     o = env["oracle"].System(po, g["x"], g["a"], ids=g["ids"], u=u, w=w, nstep=nstep)
     Fo, To, So = o.forces()
+    Fa, Ta = o.force_scale()
     assert o.ncontacts > 10
-    assert relerr(F.cpu().numpy(), Fo) < FP64_TOL
-    assert relerr(T.cpu().numpy(), To) < FP64_TOL
-    assert relerr(S, So) < FP64_TOL
+    check_forces(F.cpu().numpy(), Fo, Fa, FP64_TOL, KAPPA_FP64, "force")
+    check_forces(T.cpu().numpy(), To, Ta, FP64_TOL, KAPPA_FP64, "torque")
+    check_stress(S, So, FP64_TOL)
     c = s.counters()
     assert c["npairs"] == o.npairs and c["ncontacts"] == o.ncontacts
     s.close()
 
 
-@pytest.mark.parametrize("precision,tol,mode", [("fp64", FP64_TOL, 0), ("mixed", 1e-5, 0),
-                                                ("fp64", FP64_TOL, 1)])
-def test_forces_with_lubrication_taper(env, precision, tol, mode):
+@pytest.mark.parametrize("precision,tol,kappa,mode", [("fp64", FP64_TOL, KAPPA_FP64, 0),
+                                                      ("mixed", MIXED_TOL, KAPPA_MIXED, 0),
+                                                      ("fp64", FP64_TOL, KAPPA_FP64, 1)])
+def test_forces_with_lubrication_taper(env, precision, tol, kappa, mode):
     """The differentiable cutoff (lubrication scaled down over the last 30% of
     the range) against the oracle, with a wide range so that many pairs sit in
     the band."""
@@ -167,13 +161,14 @@ def test_forces_with_lubrication_taper(env, precision, tol, mode):
     F, T = s.forces()
     o = env["oracle"].System(po, g["x"], g["a"], ids=g["ids"], u=u, w=w)
     Fo, To, So = o.forces()
-    assert relerr(F.cpu().numpy(), Fo) < tol
-    assert relerr(T.cpu().numpy(), To) < tol
-    assert relerr(s.stress(), So) < tol
+    Fa, Ta = o.force_scale()
+    check_forces(F.cpu().numpy(), Fo, Fa, tol, kappa, "force")
+    check_forces(T.cpu().numpy(), To, Ta, tol, kappa, "torque")
+    check_stress(s.stress(), So, tol)
     # the taper changes the answer: the untapered oracle differs
     po0 = env["oracle"].make_params(box, **dict(kw, lub_taper=0.0))
     Fu = env["oracle"].System(po0, g["x"], g["a"], ids=g["ids"], u=u, w=w).forces()[0]
-    assert relerr(Fu, Fo) > 1e-3
+    assert np.linalg.norm(Fu - Fo) > 1e-3 * np.linalg.norm(Fo)
     s.close()
 
 
@@ -196,14 +191,23 @@ def test_forces_with_carried_history(env):
     np.testing.assert_array_equal(x2, xi)
     F, T = s.forces()
     Fo, To, So = o.forces()
-    assert relerr(F.cpu().numpy(), Fo) < FP64_TOL
-    assert relerr(T.cpu().numpy(), To) < FP64_TOL
-    assert relerr(s.stress(), So) < FP64_TOL
+    Fa, Ta = o.force_scale()
+    check_forces(F.cpu().numpy(), Fo, Fa, FP64_TOL, KAPPA_FP64, "force")
+    check_forces(T.cpu().numpy(), To, Ta, FP64_TOL, KAPPA_FP64, "torque")
+    check_stress(s.stress(), So, FP64_TOL)
     s.close()
 
 
 def test_trajectory_fp64_c1(env):
-    """The 1000-particle FP64 configuration: 300 steps on both sides."""
+    """The 1000-particle FP64 configuration over its full 1000 steps on both
+    sides (Eq. 15-16).  In FP64 mode the predictor, the corrector, the drag
+    and the accelerations round every product and sum on their own as the
+    oracle does, so the two trajectories differ only through the order of
+    the force sums; every 100 steps each particle's position is within
+    1e-10 a_min, its velocity and angular velocity within 1e-10 of their own,
+    every stress component within 1e-10.  The divergence is recorded per
+    chunk and must grow by less than a factor 1e3 over the run (measured on
+    GB300: ~1e-14 of the velocities after 50 steps, ~4e-13 after 1000)."""
     synth = env["synth"]
     g = synth.generate(synth.SPECS["c1"])
     box = g["box"]
@@ -213,21 +217,25 @@ def test_trajectory_fp64_c1(env):
     o.init_accel()
     st0 = s.state()
     so = o.get_state()
-    assert relerr(st0["al"].cpu().numpy(), so["al"]) < FP64_TOL
-    for chunk in range(3):
+    check_per_particle(st0["al"].cpu().numpy(), so["al"], FP64_TOL, what="alpha^0")
+    growth = []
+    for chunk in range(10):
         s.step(100)
         o.step(100)
-        st = s.state()
+        st = {k: v.cpu().numpy() for k, v in s.state().items()}
         so = o.get_state()
-        assert periodic_diff(st["x"].cpu().numpy(), so["x"], box).max() < 1e-10
-        assert relerr(st["u"].cpu().numpy(), so["u"]) < 1e-9
-        assert relerr(st["w"].cpu().numpy(), so["w"]) < 1e-9
-        assert relerr(s.stress(), o.get_forces()[2]) < 1e-8
+        dx = periodic_diff(st["x"], so["x"], box).max()
+        assert dx < 1e-10 * g["a"].min(), (chunk, dx)
+        ru = check_per_particle(st["u"], so["u"], FP64_TOL, what="u after %d steps" % (100 * chunk + 100))
+        rw = check_per_particle(st["w"], so["w"], FP64_TOL, what="w after %d steps" % (100 * chunk + 100))
+        check_stress(s.stress(), o.get_forces()[2], FP64_TOL)
+        growth.append(max(ru, rw, dx))
+    assert max(growth) < 1e3 * max(growth[0], 1e-16), growth
     k1, x1 = s.history()
     k2, x2 = o.get_history()
     np.testing.assert_array_equal(k1, k2)
-    assert np.abs(x1 - x2).max() < 1e-9 * max(np.abs(x2).max(), 1e-12)
-    assert s.counters()["steps_done"] == 300
+    assert np.abs(x1 - x2).max() < FP64_TOL * max(np.abs(x2).max(), 1e-12)
+    assert s.counters()["steps_done"] == 1000
     s.close()
 
 

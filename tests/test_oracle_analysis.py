@@ -115,3 +115,52 @@ def test_image_count_keeps_the_unwrapped_y_continuous(vy):
     iy = s.get_images()
     assert iy[0] == (1 if vy > 0 else -1)
     assert st["x"][1, 0] + iy[0] * L == pytest.approx(y0 + 10 * 1e-2 * vy, abs=1e-12)
+
+
+# ---- local volume fraction along y by size class (Sec. III B, Fig. 12)
+
+def test_phi_profile_pins():
+    import math
+    from scipy.integrate import quad
+    from oracle import analysis as an
+    box = np.array([20.0, 16.0, 12.0])
+    nb = 8
+    w = box[1] / nb
+    slab = box[0] * box[2] * w
+    # one sphere in the middle of slab 3, radius below half a slab: all of it there
+    p = an.phi_profile([3.5 * w], [0.7], box, nb, a_split=1.0)
+    want = np.zeros((2, nb))
+    want[0, 3] = 4.0 / 3.0 * math.pi * 0.7 ** 3 / slab
+    np.testing.assert_allclose(p, want, rtol=1e-14, atol=0)
+    # centred on the plane between slabs 4 and 5 (class 1): half in each
+    p = an.phi_profile([5 * w], [1.3], box, nb, a_split=1.0)
+    half = 0.5 * 4.0 / 3.0 * math.pi * 1.3 ** 3 / slab
+    assert p[1, 4] == pytest.approx(half, rel=1e-13) and p[1, 5] == pytest.approx(half, rel=1e-13)
+    assert p[0].sum() == 0.0 and np.count_nonzero(p[1]) == 2
+    # a sphere across y = 0: its parts in the first and the last slab, each
+    # the quadrature of its cross-sections over the part
+    a, yc = 1.5, 0.4
+    p = an.phi_profile([yc], [a], box, nb, a_split=2.0)
+    disk = lambda t: math.pi * (a * a - t * t)
+    top = quad(disk, -a, -yc)[0]          # below y = 0, seen from y = L_y
+    bottom = quad(disk, -yc, a)[0]
+    assert p[0, 0] * slab == pytest.approx(bottom, rel=1e-12)
+    assert p[0, -1] * slab == pytest.approx(top, rel=1e-12)
+    # a packing: each slab against the quadrature of every sphere's
+    # cross-sections, and the mean over slabs is the class volume fraction
+    rng = np.random.default_rng(3)
+    y = rng.uniform(0, box[1], size=40)
+    r = rng.uniform(0.5, 2.5, size=40)
+    p = an.phi_profile(y, r, box, nb, a_split=1.5)
+    q = np.zeros((2, nb))
+    for yy, aa in zip(y, r):
+        for img in (-1, 0, 1):
+            for b in range(nb):
+                lo, hi = max(b * w - (yy + img * box[1]), -aa), min((b + 1) * w - (yy + img * box[1]), aa)
+                if hi > lo:
+                    q[int(aa > 1.5), b] += quad(lambda t: math.pi * (aa * aa - t * t), lo, hi)[0]
+    np.testing.assert_allclose(p * slab, q, rtol=1e-11, atol=1e-12)
+    V = box.prod()
+    for c in (0, 1):
+        sel = (r > 1.5) if c else (r <= 1.5)
+        assert p[c].mean() == pytest.approx(np.sum(4.0 / 3.0 * math.pi * r[sel] ** 3) / V, rel=1e-13)

@@ -6,8 +6,10 @@ allocation): it finds the neighbour pairs using only a fixed array compiled
 into the library.  Here it is called through the C ABI and its pair set is
 compared, bit for bit, with the one the regular entry points
 (dss_neighbour_build + dss_get_pairs) produce, on two calls in a row with
-different systems, so that the second call also shows the shared array is
-cleared between calls.  The file name makes pytest collect it last.
+different systems, so that the later calls also show the shared array is
+cleared between calls, including the cutoff mode with a range fixed in a0 and
+the wider listing ranges of the electro-chemical forces.  The file name makes
+pytest collect it last.
 """
 import ctypes
 
@@ -47,19 +49,24 @@ def test_noalloc_pairs_equal_regular_pairs_on_consecutive_calls():
     from paper_2108_01013_gb300 import _native as nat, synth
     dss.build()
     cases = [
-        (synth.small(3000, 0.52, 31), 0.8, 1e-3, 4321),
-        (synth.small(1200, 0.45, 32), 1.7, 1e-2, 77),
+        (synth.small(3000, 0.52, 31), 0.8, 1e-3, 4321, {}),
+        (synth.small(1200, 0.45, 32), 1.7, 1e-2, 77, {}),
+        # lubrication range a fixed multiple of a0 (cutoff mode 1)
+        (synth.small(2000, 0.50, 33), 1.1, 1e-3, 919, dict(lub_cutoff_mode=1, delta_lub=0.1)),
+        # the electro-chemical ranges of Eq. 6-7 (20 lambda_D, 4 a0) widen the list
+        (synth.small(1500, 0.48, 34), 0.6, 1e-3, 12, dict(f_er=1.0, lambda_d=0.05,
+                                                         hamaker=1e-4, vdw_eps=0.01)),
     ]
-    for g, gdot, dt, nstep in cases:
+    for g, gdot, dt, nstep, extra in cases:
         box = g["box"]
-        p = dss.default_params(box, shear_rate=gdot, dt=dt, mu=0.5)
+        p = dss.default_params(box, shear_rate=gdot, dt=dt, mu=0.5, **extra)
         n = g["a"].shape[0]
         s = dss.Suspension(g["x"], g["a"], box, p, ids=g["ids"], nstep=nstep,
                            alpha_lin=np.zeros((3, n)), alpha_ang=np.zeros((3, n)))
         s.neighbour_build()
         want = s.pairs()
         s.close()
-        cap = 8 * n
+        cap = len(want) + 64            # room for every pair (the electro-chemical ranges list many)
         rc, count, out = _noalloc(nat, g["x"], g["a"], g["ids"], box, p, g["a"].max(), nstep, cap)
         assert rc == 0, nat.ERRORS.get(rc, rc)
         assert count == len(want)
