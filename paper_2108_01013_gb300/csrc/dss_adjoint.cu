@@ -135,10 +135,10 @@ k_adj_tape_pairs(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restric
     double dx, dy, dz;
     int sy;
     min_image(I, off, xi, yi, zi, s.x[j], s.x[n + j], s.x[2 * n + j], dx, dy, dz, sy);
-    const double rr = sqrt(dx * dx + dy * dy + dz * dz);
+    const double rr = exact_dist(dx, dy, dz);
     int pold = -1;
     double xo[3] = {0.0, 0.0, 0.0};
-    if (!empty_history && rr - (ai + s.a[j]) < 0.0) {
+    if (!empty_history && __dsub_rn(rr, __dadd_rn(ai, s.a[j])) < 0.0) {
       const int idj = s.id[j];
       const int oi = H.slot_of_id[idi], oj = H.slot_of_id[idj];
       int q = -1;

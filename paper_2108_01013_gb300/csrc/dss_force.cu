@@ -134,8 +134,8 @@ __device__ __forceinline__ PairRes<double> pair_eval_fp64(const Geo& g, const In
   const int idi = s.id[i], idj = s.id[j];
   const double sgn = idi < idj ? 1.0 : -1.0;
   double xo[3] = {0.0, 0.0, 0.0}, ro[3] = {0.0, 0.0, 0.0};
-  const double rr = sqrt(dot(r, r));
-  if (rr - (ai + aj) < 0.0) {
+  const double rr = exact_dist(dx, dy, dz);
+  if (__dsub_rn(rr, __dadd_rn(ai, aj)) < 0.0) {
     history_lookup<EXT>(g, H, hr, i, j, idi, idj, xo, ro);
     xo[0] *= sgn; xo[1] *= sgn; xo[2] *= sgn;
   }
@@ -230,7 +230,20 @@ __device__ __forceinline__ PairRes<float> pair_eval_mixed(const Geo& g, const In
   F3 Fc = f3(0, 0, 0), nxf = f3(0, 0, 0), Tr = f3(0, 0, 0);
   q.xi[0] = q.xi[1] = q.xi[2] = 0.0;
   q.xr[0] = q.xr[1] = q.xr[2] = 0.0;
-  q.contact = num < 0.0f;
+  // The contact flag is a decision, taken as in FP64: the double-float gap
+  // numerator (~44 bits) decides it unless it lies within 1e-9 S^2 of zero
+  // (spheres touching to the last bits, which relaxed packings produce);
+  // there the FP64 state decides with the operations of the plain FP64
+  // evaluation.
+  if (fabsf(num) > 1e-9f * S * S) {
+    q.contact = num < 0.0f;
+  } else {
+    const int n = g.n;
+    double ex, ey, ez;
+    int sy;
+    min_image(I, sg.off, s.x[i], s.x[n + i], s.x[2 * n + i], s.x[j], s.x[n + j], s.x[2 * n + j], ex, ey, ez, sy);
+    q.contact = __dsub_rn(exact_dist(ex, ey, ez), __dadd_rn(s.a[i], s.a[j])) < 0.0;
+  }
   if (q.contact) {
     const int idi = s.id[i], idj = s.id[j];
     const float sg = idi < idj ? 1.0f : -1.0f;   // stored (lo -> hi) vs i -> j orientation
@@ -579,8 +592,9 @@ k_pairs(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ sgk, 
       if (s.inst[il0] == inst0) ew0 = e; else ew1 = e;
     }
   }
-  // one instance in the handle: the second slot is always empty
-  const int nq = g.K > 1 ? 18 : 9;
+  // the second instance slot holds anything only where a lane of the warp
+  // met a second instance (in its pairs, or as the owner of a wave stresslet)
+  const int nq = __any_sync(0xffffffffu, moved || ew1 != 0.0) ? 18 : 9;
 #pragma unroll
   for (int q = 0; q < 18; ++q) {
     if (q >= nq) {

@@ -156,6 +156,13 @@ __device__ __forceinline__ void min_image(const InstGeo& g, double off, double x
   dz = __dsub_rn(dz, __dmul_rn(g.L[2], rint(__dmul_rn(dz, g.invL[2]))));
 }
 
+// Centre distance |r| with the operations of the plain FP64 evaluation
+// ((dx dx + dy dy) + dz dz, then the square root): the contact decision
+// d = |r| - (a_i + a_j) < 0 of Eq. 4 is then the same bit for bit.
+__device__ __forceinline__ double exact_dist(double dx, double dy, double dz) {
+  return sqrt(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
+}
+
 // Exact neighbour predicate: r^2 < (a_i + a_j + delta_ij)^2, strict.
 __device__ __forceinline__ bool exact_is_pair(const Geo& g, const InstGeo& I, double off, double xi,
                                               double yi, double zi, double ai, double xj,

@@ -219,29 +219,34 @@ k_enumerate(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ s
     const int cb = I.cell_base;
     const int c = cellid[i] - cb;
     const int cx = c % nx, cy = (c / nx) % ny, cz = c / (nx * ny);
+    // neighbouring cell coordinates by conditional wraps (no integer
+    // division in the stencil walk; every offset below stays within one box)
+    const int xm = cx == 0 ? nx - 1 : cx - 1, xp = cx + 1 == nx ? 0 : cx + 1;
+    const int zm = cz == 0 ? nz - 1 : cz - 1, zp = cz + 1 == nz ? 0 : cz + 1;
     // own cell (partners after i) and the cell x+1
     scan_range<ECH, UNR, SPLIT>(e, i + 1, cell_start[cb + c + 1], 0.f, 0.f, 0.f);
     {
-      const int q = cb + (cz * ny + cy) * nx + wrapi(cx + 1, nx);
+      const int q = cb + (cz * ny + cy) * nx + xp;
       scan_range<ECH, UNR, SPLIT>(e, cell_start[q], cell_start[q + 1], I.csf[0], 0.f, 0.f);
     }
     // layer y, z+1: three x cells
     {
-      const int qz = wrapi(cz + 1, nz);
-      for (int ox = -1; ox <= 1; ++ox) {
-        const int q = cb + (qz * ny + cy) * nx + wrapi(cx + ox, nx);
-        scan_range<ECH, UNR, SPLIT>(e, cell_start[q], cell_start[q + 1], (float)ox * I.csf[0], 0.f, I.csf[2]);
-      }
+      const int row = cb + (zp * ny + cy) * nx;
+      scan_range<ECH, UNR, SPLIT>(e, cell_start[row + xm], cell_start[row + xm + 1], -I.csf[0], 0.f, I.csf[2]);
+      scan_range<ECH, UNR, SPLIT>(e, cell_start[row + cx], cell_start[row + cx + 1], 0.f, 0.f, I.csf[2]);
+      scan_range<ECH, UNR, SPLIT>(e, cell_start[row + xp], cell_start[row + xp + 1], I.csf[0], 0.f, I.csf[2]);
     }
     // layer y+1: 3x3 cells, or across y = L_y the 4 x cells covering the
     // image range shifted by the Lees-Edwards offset
     const bool le = cy == ny - 1;
     const int qy = le ? 0 : cy + 1;
     const int x0 = le ? -2 - fsh : -1, x1 = le ? 1 - fsh : 1;
+    const int xs = le ? wrapi(cx + x0, nx) : xm;   // x cell of the first offset
     for (int oz = -1; oz <= 1; ++oz) {
-      const int qz = wrapi(cz + oz, nz);
-      for (int ox = x0; ox <= x1; ++ox) {
-        const int q = cb + (qz * ny + qy) * nx + wrapi(cx + ox, nx);
+      const int qz = oz < 0 ? zm : (oz > 0 ? zp : cz);
+      int qx = xs;
+      for (int ox = x0; ox <= x1; ++ox, qx = qx + 1 == nx ? 0 : qx + 1) {
+        const int q = cb + (qz * ny + qy) * nx + qx;
         float cxo, cyo, czo;
         stencil_shift(I, ox, 1, oz, le ? 1 : 0, fsh, offr, cxo, cyo, czo);
         scan_range<ECH, UNR, SPLIT>(e, cell_start[q], cell_start[q + 1], cxo, cyo, czo);
