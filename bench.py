@@ -139,6 +139,10 @@ def parse():
                          "viscosity of 20k spheres), cpu (the oracle on the host cores: 1000 "
                          "brute-force steps of the 1k configuration, whole steps of the 1M "
                          "and Table 5 packings); 'none' for none")
+    ap.add_argument("--capacity-m", type=int, default=0,
+                    help="row capacity M of the headline workload's half lists (0: the shell "
+                         "estimate of Sec. II A); a smaller M keeps an ncu capture of the 1M "
+                         "workload (--workload c3) within a few GB")
     ap.add_argument("--mode-steps", type=int, default=400)
     ap.add_argument("--batch-instances", type=int, default=256,
                     help="instances of the batched mode (the first K of the 256-instance sweep)")
@@ -702,7 +706,7 @@ def main():
     spec, g = workload(args.workload, rank)
     n = g["a"].shape[0]
     kw = dict(mu=spec.mu, kn=spec.kn, shear_rate=spec.shear_rate, dt=spec.dt)
-    params = dss.default_params(g["box"], precision=args.precision, **kw)
+    params = dss.default_params(g["box"], precision=args.precision, capacity_M=args.capacity_m, **kw)
     stream = torch.cuda.Stream(device=dev)
     with torch.cuda.stream(stream):
         s = dss.Suspension(g["x"], g["a"], g["box"], params, ids=g["ids"], stream=stream)
@@ -806,7 +810,9 @@ def main():
         "dtype": "f64" if args.precision == "fp64" else "f32+f64",
         "data": "synthetic",
         "config": {"workload": spec.name, "n": n, "phi": spec.phi, "mu": spec.mu,
-                   "radii": "1.0/1.4 equal numbers", "precision": args.precision,
+                   "radii": ("log-uniform in [%g, %g]" % (spec.a_min, spec.a_max) if spec.radii == "loguniform"
+                             else "%g/%g, %g%% large" % (spec.a_small, spec.a_large, 100 * spec.frac_large)),
+                   "capacity_M": c["M"], "precision": args.precision,
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "flushed before every timed step (256 MB write)",
                    "pairs": P, "contacts": c["ncontacts"], "cells": list(c["ncell"])},
