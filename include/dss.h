@@ -65,8 +65,9 @@ enum dss_status {
 
 enum dss_precision {
   DSS_FP64 = 0,   /* everything in FP64 */
-  DSS_MIXED = 1   /* pair forces in FP32; positions, gaps, Lees-Edwards offset,
-                     tangential stretch and stress accumulation in FP64 */
+  DSS_MIXED = 1   /* pair forces in FP32; positions, gaps, Lees-Edwards offset
+                     and stress accumulation in FP64 or double-float (two FP32
+                     words, ~48 bits); tangential stretch as double-float */
 };
 
 typedef struct dss_params {

@@ -148,12 +148,14 @@ k_adj_tape_pairs(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restric
         for (int m = 0; m < H.count[oj]; ++m)
           if (H.list[(int64_t)oj * g.Ms + m] == oi) { q = H.start[oj] + m; break; }
       const Xi4 hv = q >= 0 ? H.xi[q] : Xi4{0.0, 0.0, 0.0, 0.0};
-      if (hv.w != 0.0) {
+      if (xi_flag(hv)) {
         const double sgn = idi < idj ? 1.0 : -1.0;
+        double c[3];
+        xi_components(hv, g.precision == DSS_MIXED, c);
         pold = q;
-        xo[0] = sgn * hv.x;
-        xo[1] = sgn * hv.y;
-        xo[2] = sgn * hv.z;
+        xo[0] = sgn * c[0];
+        xo[1] = sgn * c[1];
+        xo[2] = sgn * c[2];
       }
     }
     t.pold[p] = pold;

@@ -110,7 +110,7 @@ __global__ void k_cc_link(Geo g, ListBuf H, int* parent, DevStatus* st) {
   const int p0 = H.start[i];
   for (int k = 0; k < c; ++k) {
     if (p0 + k >= g.pcap) break;
-    if (H.xi[p0 + k].w == 0.0) continue;
+    if (!xi_flag(H.xi[p0 + k])) continue;
     int a = i, b = H.list[(int64_t)i * g.Ms + k];
     bool done = false;
     for (int it = 0; it < (1 << 20) && !done; ++it) {

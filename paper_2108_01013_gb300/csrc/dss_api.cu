@@ -331,20 +331,14 @@ __global__ void k_attach_history(Geo g, StateBuf s, ListBuf L, const long long* 
       if (keys[m] == key) { f = m; break; }
       if (keys[m] < key) l = m + 1; else r = m - 1;
     }
-    Xi4 v, vr;
-    vr.x = vr.y = vr.z = vr.w = 0.0;
+    const bool mixed = g.precision == DSS_MIXED;
+    Xi4 v{0.0, 0.0, 0.0, 0.0}, vr{0.0, 0.0, 0.0, 0.0};
     if (f >= 0) {
-      v.x = xi[3 * (int64_t)f];
-      v.y = xi[3 * (int64_t)f + 1];
-      v.z = xi[3 * (int64_t)f + 2];
-      v.w = 1.0;
+      v = xi_record(xi[3 * (int64_t)f], xi[3 * (int64_t)f + 1], xi[3 * (int64_t)f + 2], true, mixed);
       if (xr) {
-        vr.x = xr[3 * (int64_t)f];
-        vr.y = xr[3 * (int64_t)f + 1];
-        vr.z = xr[3 * (int64_t)f + 2];
+        vr = xi_record(xr[3 * (int64_t)f], xr[3 * (int64_t)f + 1], xr[3 * (int64_t)f + 2], true, mixed);
+        vr.w = 0.0;   // the rolling record carries no flag
       }
-    } else {
-      v.x = v.y = v.z = v.w = 0.0;
     }
     L.xi[p] = v;
     if (L.xr) L.xr[p] = vr;
@@ -358,7 +352,7 @@ __global__ void k_history_out(Geo g, ListBuf L, long long* __restrict__ keys,
   const int P = (int)min((int64_t)L.start[n], g.pcap);
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
     const Xi4 v = L.xi[p];
-    if (v.w == 0.0) continue;
+    if (!xi_flag(v)) continue;
     int lo = 0, hi = n;
     while (hi - lo > 1) {
       int mid = (lo + hi) >> 1;
@@ -369,13 +363,16 @@ __global__ void k_history_out(Geo g, ListBuf L, long long* __restrict__ keys,
     int q = atomicAdd(counter, 1);
     if (q < cap) {
       keys[q] = a < b ? (a << 32) | b : (b << 32) | a;
-      xi[3 * (int64_t)q] = v.x;
-      xi[3 * (int64_t)q + 1] = v.y;
-      xi[3 * (int64_t)q + 2] = v.z;
-      const Xi4 vr = L.xr ? L.xr[p] : Xi4{0.0, 0.0, 0.0, 0.0};
-      xr[3 * (int64_t)q] = vr.x;
-      xr[3 * (int64_t)q + 1] = vr.y;
-      xr[3 * (int64_t)q + 2] = vr.z;
+      const bool mixed = g.precision == DSS_MIXED;
+      double c[3];
+      xi_components(v, mixed, c);
+      xi[3 * (int64_t)q] = c[0];
+      xi[3 * (int64_t)q + 1] = c[1];
+      xi[3 * (int64_t)q + 2] = c[2];
+      xi_components(L.xr ? L.xr[p] : Xi4{0.0, 0.0, 0.0, 0.0}, mixed, c);
+      xr[3 * (int64_t)q] = c[0];
+      xr[3 * (int64_t)q + 1] = c[1];
+      xr[3 * (int64_t)q + 2] = c[2];
     }
   }
 }

@@ -54,6 +54,45 @@ struct HistRef {
   int idorder;
 };
 
+// Where pair (i, j) sat in the committed history: the rows of the previous
+// step's list are searched for it (the owner's row first: ownership in the
+// half stencil rarely changes between steps).  The probe takes one round of
+// loads after the sorted-order map: the owner row's length, offset and first
+// four entries (rows hold at least four entries and start on 16-byte
+// boundaries, so the first int4 is always in bounds).
+struct HistProbe {
+  int oi, oj, cnt, st;
+  int4 r;
+};
+
+__device__ __forceinline__ HistProbe hist_probe(const Geo& g, const ListBuf& H, const HistRef& hr, int i, int j,
+                                                int idi, int idj) {
+  HistProbe p;
+  p.oi = hr.idorder ? H.slot_of_id[idi] : hr.perm[i];
+  p.oj = hr.idorder ? H.slot_of_id[idj] : hr.perm[j];
+  p.cnt = H.count[p.oi];
+  p.st = H.start[p.oi];
+  p.r = *reinterpret_cast<const int4*>(H.list + (int64_t)p.oi * g.Ms);
+  return p;
+}
+
+// Slot of the pair in the committed list's pair arrays, -1 if it was not
+// listed.
+__device__ __forceinline__ int64_t hist_slot(const Geo& g, const ListBuf& H, const HistProbe& p) {
+  int k = -1;
+  if (p.cnt > 0 && p.r.x == p.oj) k = 0;
+  else if (p.cnt > 1 && p.r.y == p.oj) k = 1;
+  else if (p.cnt > 2 && p.r.z == p.oj) k = 2;
+  else if (p.cnt > 3 && p.r.w == p.oj) k = 3;
+  else if (p.cnt > 4) {
+    k = row_find(H.list + (int64_t)p.oi * g.Ms + 4, p.cnt - 4, p.oj);
+    if (k >= 0) k += 4;
+  }
+  if (k >= 0) return (int64_t)p.st + k;
+  k = row_find(H.list + (int64_t)p.oj * g.Ms, H.count[p.oj], p.oi);
+  return k >= 0 ? (int64_t)H.start[p.oj] + k : -1;
+}
+
 // Tangential stretch of pair (i, j) (ids idi, idj) at the last committed
 // step, in the lo -> hi orientation, and (when k_r > 0) its rolling stretch;
 // zero when the pair was not in contact.
@@ -62,19 +101,10 @@ __device__ __forceinline__ void history_lookup(const Geo& g, const ListBuf& H, c
                                                int j, int idi, int idj, double xo[3], double ro[3]) {
   xo[0] = xo[1] = xo[2] = 0.0;
   ro[0] = ro[1] = ro[2] = 0.0;
-  const int oi = hr.idorder ? H.slot_of_id[idi] : hr.perm[i];
-  const int oj = hr.idorder ? H.slot_of_id[idj] : hr.perm[j];
-  int64_t pold = -1;
-  int k = row_find(H.list + (int64_t)oi * g.Ms, H.count[oi], oj);
-  if (k >= 0) {
-    pold = (int64_t)H.start[oi] + k;
-  } else {
-    k = row_find(H.list + (int64_t)oj * g.Ms, H.count[oj], oi);
-    if (k >= 0) pold = (int64_t)H.start[oj] + k;
-  }
+  const int64_t pold = hist_slot(g, H, hist_probe(g, H, hr, i, j, idi, idj));
   if (pold >= 0) {
     const Xi4 v = H.xi[pold];
-    if (v.w != 0.0) {
+    if (xi_flag(v)) {
       xo[0] = v.x;
       xo[1] = v.y;
       xo[2] = v.z;
@@ -105,11 +135,12 @@ __device__ __forceinline__ F3 crossf(F3 a, F3 b) {
 __device__ __forceinline__ F3 tangf(F3 n, F3 v) { return v - dotf(n, v) * n; }
 
 
-// Result of one pair in the arithmetic precision R.
+// Result of one pair in the arithmetic precision R, with its stretch
+// records as they are stored.
 template <typename R>
 struct PairRes {
   R F[3], Ti[3], Tj[3], Fc[3], Fl[3], r[3];
-  double xi[3], xr[3];
+  Xi4 xrec, rrec;
   int contact;
 };
 
@@ -166,8 +197,8 @@ __device__ __forceinline__ PairRes<double> pair_eval_fp64(const Geo& g, const In
   q.Fc[0] = o.Fc.x; q.Fc[1] = o.Fc.y; q.Fc[2] = o.Fc.z;
   q.Fl[0] = o.Fl.x; q.Fl[1] = o.Fl.y; q.Fl[2] = o.Fl.z;
   q.r[0] = dx; q.r[1] = dy; q.r[2] = dz;
-  q.xi[0] = sgn * o.xi.x; q.xi[1] = sgn * o.xi.y; q.xi[2] = sgn * o.xi.z;
-  q.xr[0] = o.xr.x; q.xr[1] = o.xr.y; q.xr[2] = o.xr.z;
+  q.xrec = Xi4{sgn * o.xi.x, sgn * o.xi.y, sgn * o.xi.z, o.contact ? 1.0 : 0.0};
+  q.rrec = Xi4{o.xr.x, o.xr.y, o.xr.z, 0.0};
   q.contact = o.contact;
   return q;
 }
@@ -176,8 +207,9 @@ __device__ __forceinline__ PairRes<double> pair_eval_fp64(const Geo& g, const In
 // in FP64 from the FP64 positions (the lubrication coefficients diverge as
 // 1/(d* + eps), so the gap needs far more than FP32's 7 digits); the gap is
 // then d = (r^2 - S^2)/(r + S) with the division in FP32.  The tangential
-// stretch is carried and updated in FP64; the rest of the pair arithmetic is
-// FP32, on velocities taken relative to the ambient flow.
+// stretch is carried and updated as a double-float (~48 bits); the rest of
+// the pair arithmetic is FP32, on velocities taken relative to the ambient
+// flow.
 template <bool EXT>
 __device__ __forceinline__ PairRes<float> pair_eval_mixed(const Geo& g, const InstGeo& I, const StateBuf& s,
                                                          const ListBuf& H, const HistRef& hr,
@@ -226,10 +258,10 @@ __device__ __forceinline__ PairRes<float> pair_eval_mixed(const Geo& g, const In
   const F3 Wi = f3(wi4.x, wi4.y, wi4.z), Wj = f3(wj4.x, wj4.y, wj4.z);
   const float Ai = pi.w + li.w, Bj = pj.w + lj.w;
   PairRes<float> q;
-  // ---- contact, Eq. 4-5; the stretch stays in FP64
+  // ---- contact, Eq. 4-5: the flag here, the forces after the lubrication
   F3 Fc = f3(0, 0, 0), nxf = f3(0, 0, 0), Tr = f3(0, 0, 0);
-  q.xi[0] = q.xi[1] = q.xi[2] = 0.0;
-  q.xr[0] = q.xr[1] = q.xr[2] = 0.0;
+  q.xrec = Xi4{0.0, 0.0, 0.0, 0.0};
+  q.rrec = Xi4{0.0, 0.0, 0.0, 0.0};
   // The contact flag is a decision, taken as in FP64: the double-float gap
   // numerator (~44 bits) decides it unless it lies within 1e-9 S^2 of zero
   // (spheres touching to the last bits, which relaxed packings produce);
@@ -244,11 +276,22 @@ __device__ __forceinline__ PairRes<float> pair_eval_mixed(const Geo& g, const In
     min_image(I, sg.off, s.x[i], s.x[n + i], s.x[2 * n + i], s.x[j], s.x[n + j], s.x[2 * n + j], ex, ey, ez, sy);
     q.contact = __dsub_rn(exact_dist(ex, ey, ez), __dadd_rn(s.a[i], s.a[j])) < 0.0;
   }
+  Xi4 xrec{0.0, 0.0, 0.0, 0.0}, rrec{0.0, 0.0, 0.0, 0.0};
+  int idi = 0, idj = 0;
   if (q.contact) {
-    const int idi = s.id[i], idj = s.id[j];
+    idi = s.id[i]; idj = s.id[j];
+    const int64_t pold = hist_slot(g, H, hist_probe(g, H, hr, i, j, idi, idj));
+    if (pold >= 0) {
+      xrec = H.xi[pold];
+      if (EXT && g.k_r > 0.0) rrec = H.xr[pold];
+    }
+  }
+  // ---- contact forces and the stretch update (the stretch carried as a
+  // double-float)
+  if (q.contact) {
     const float sg = idi < idj ? 1.0f : -1.0f;   // stored (lo -> hi) vs i -> j orientation
-    double xo[3], ro[3];
-    history_lookup<EXT>(g, H, hr, i, j, idi, idj, xo, ro);
+    if (!xi_flag(xrec)) xrec = rrec = Xi4{0.0, 0.0, 0.0, 0.0};
+    const FF xo[3] = {word_ff(xrec.x), word_ff(xrec.y), word_ff(xrec.z)};
     // u_j(image) - u_i = (V_j - V_i) + gdot dy x (+ the wave's U_inf,x
     // difference); absolute w = W + Omega_inf (local with the wave)
     F3 du = (Vj - Vi) + f3(gd * r.y, 0.f, 0.f);
@@ -260,51 +303,52 @@ __device__ __forceinline__ PairRes<float> pair_eval_mixed(const Geo& g, const In
     }
     const float fn = g.f.kn * d + I.gn_f * dotf(nn, du);
     const F3 ut = tangf(nn, du - crossf(Ai * wi + Bj * wj, nn));
-    // stretch (stored orientation) in FP64: xi + delta, with the small change
-    // delta = -n (n.xi) + s u_t dt (projection onto the new tangent plane and
-    // the increment) formed in FP32
-    const F3 xf = f3((float)xo[0], (float)xo[1], (float)xo[2]);
+    // stretch (stored orientation) as a double-float: xi + delta, with the
+    // small change delta = -n (n.xi) + s u_t dt (projection onto the new
+    // tangent plane and the increment) formed in FP32 from the high words
+    const F3 xf = f3(xo[0].hi, xo[1].hi, xo[2].hi);
     const float pn = dotf(nn, xf);
     const float sdt = sg * g.f.dt;
     const F3 dxs = f3(sdt * ut.x - pn * nn.x, sdt * ut.y - pn * nn.y, sdt * ut.z - pn * nn.z);
-    double xs0 = xo[0] + (double)dxs.x;
-    double xs1 = xo[1] + (double)dxs.y;
-    double xs2 = xo[2] + (double)dxs.z;
-    // the FP32 copy for the force is formed in FP32 (within an ulp of the
-    // rounded FP64 sum; no conversions back from FP64)
+    FF xs0 = ff_add_f(xo[0], dxs.x), xs1 = ff_add_f(xo[1], dxs.y), xs2 = ff_add_f(xo[2], dxs.z);
+    // the FP32 copy for the force (within an ulp of the double-float's value)
     F3 xsf = xf + dxs;
     const float cap = g.f.mu_kt * fabsf(fn);
     const float xm2 = dotf(xsf, xsf);
     if (xm2 > cap * cap) {
       const float fs = cap * rsqrtf(xm2);
-      const double fd = (double)fs;
-      xs0 *= fd; xs1 *= fd; xs2 *= fd;
+      xs0 = ff_mul_f(xs0, fs);
+      xs1 = ff_mul_f(xs1, fs);
+      xs2 = ff_mul_f(xs2, fs);
       xsf = fs * xsf;
     }
     const F3 Ft = (sg * g.f.kt) * xsf;
     Fc = fn * nn + Ft;
     nxf = crossf(nn, Ft);
-    q.xi[0] = xs0; q.xi[1] = xs1; q.xi[2] = xs2;
+    q.xrec = Xi4{ff_word(xs0), ff_word(xs1), ff_word(xs2), ff_word(FF{1.0f, 0.0f})};
     if (EXT && g.k_r > 0.0) {
       // rolling resistance, App. B: the rolling stretch (orientation-free)
-      // carried in FP64 with its FP32 increment, like the sliding one
+      // carried as a double-float with its FP32 increment, like the sliding
+      // one
+      const FF ro[3] = {word_ff(rrec.x), word_ff(rrec.y), word_ff(rrec.z)};
       const float abar = 2.0f * Ai * Bj / (Ai + Bj);
-      const F3 rf = f3((float)ro[0], (float)ro[1], (float)ro[2]);
+      const F3 rf = f3(ro[0].hi, ro[1].hi, ro[2].hi);
       const float rn = dotf(nn, rf);
       const F3 ur = (abar * g.f.dt) * crossf(nn, wi - wj);
       const F3 dr = f3(ur.x - rn * nn.x, ur.y - rn * nn.y, ur.z - rn * nn.z);
-      double r0 = ro[0] + (double)dr.x, r1 = ro[1] + (double)dr.y, r2 = ro[2] + (double)dr.z;
+      FF r0 = ff_add_f(ro[0], dr.x), r1 = ff_add_f(ro[1], dr.y), r2 = ff_add_f(ro[2], dr.z);
       F3 xrf = rf + dr;
       const float capr = g.f.mu_kr * fabsf(fn);
       const float xrm2 = dotf(xrf, xrf);
       if (xrm2 > capr * capr) {
         const float fs = capr * rsqrtf(xrm2);
-        const double fd = (double)fs;
-        r0 *= fd; r1 *= fd; r2 *= fd;
+        r0 = ff_mul_f(r0, fs);
+        r1 = ff_mul_f(r1, fs);
+        r2 = ff_mul_f(r2, fs);
         xrf = fs * xrf;
       }
       Tr = abar * crossf(nn, g.f.k_r * xrf);
-      q.xr[0] = r0; q.xr[1] = r1; q.xr[2] = r2;
+      q.rrec = Xi4{ff_word(r0), ff_word(r1), ff_word(r2), 0.0};
     }
   }
   // ---- electro-chemical forces, Eq. 6-7 (FP32; central, stresslet r (x) F).
@@ -312,6 +356,7 @@ __device__ __forceinline__ PairRes<float> pair_eval_mixed(const Geo& g, const In
   // the FP32 gap unless it lies within 1e-5 of a threshold; there the FP64
   // state decides, in the operations of the neighbour test.
   bool lub_on = true;
+  float m = 0.0f;
   if (g.de > 0.0) {
     const float dl = g.mode == 1 ? g.f.delta_a0 : g.f.delta * 0.5f * S;
     const float tol = 1e-5f * (S + dl);
@@ -332,13 +377,11 @@ __device__ __forceinline__ PairRes<float> pair_eval_mixed(const Geo& g, const In
       in_a = d64 < 4.0 * g.a0;
     }
     const float abar = 2.0f * Ai * Bj / (Ai + Bj);
-    float m = 0.0f;
     if (rep && in_r) m -= g.f.f_er * abar * (d >= 0.0f ? __expf(-d * g.f.inv_lambda) : 1.0f);
     if (att && in_a) {
       const float eps = g.f.vdw_eps * abar, dp = fmaxf(d, 0.0f);
       m += __fdividef(g.f.hamaker12 * abar, fmaf(dp, dp, eps * eps));
     }
-    Fc = Fc + m * nn;
   }
   // ---- lubrication, App. A (FP32), for the pairs within its range (every
   // listed pair unless electro-chemical forces widen the list; a warp whose
@@ -389,6 +432,7 @@ __device__ __forceinline__ PairRes<float> pair_eval_mixed(const Geo& g, const In
       }
     }
   }
+  if (g.de > 0.0) Fc = Fc + m * nn;
   const F3 F = Fc + Fl;
   F3 Ti = Ai * nxf + Tli;
   F3 Tj = Bj * nxf + Tlj;
@@ -531,8 +575,8 @@ k_pairs(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ sgk, 
         } else {
           set_err(st, DSS_ERR_CAPACITY);
         }
-        W.xi[p] = Xi4{q.xi[0], q.xi[1], q.xi[2], q.contact ? 1.0 : 0.0};
-        if (EXT && g.k_r > 0.0) W.xr[p] = Xi4{q.xr[0], q.xr[1], q.xr[2], 0.0};
+        W.xi[p] = q.xrec;
+        if (EXT && g.k_r > 0.0) W.xr[p] = q.rrec;
         ncont += q.contact;
         // Eq. 9: S^C = r (x) F^C, S^L = sym(r (x) F^L), F on the owner
         if (inst != cur_inst) {
@@ -575,9 +619,11 @@ k_pairs(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ sgk, 
     for (int c = 0; c < 6; ++c) acc[wid][lane][c] = R(0);
     __syncwarp();
   }
-  // FP64 block reduction of the stresslet (fixed tree over lanes, warps
-  // and blocks)
-  __shared__ double red[kWarps][18];
+  // Block reduction of the stresslet (fixed tree over lanes, warps and
+  // blocks): FP64 throughout in FP64; in mixed precision a compensated FP32
+  // sum over the block's lanes and warps, one FP64 value per block
+  __shared__ double red[MIXED ? 1 : kWarps][18];
+  __shared__ float redh[MIXED ? kWarps : 1][18], redl[MIXED ? kWarps : 1][18];
   const bool moved = cur_inst != inst0;
   // With the wave of Eq. 17 the single-particle stresslets 20/3 pi eta0 a^3
   // E_inf(x) carry a local part, (10/3) pi eta0 a^3 U k cos(k y) on xy and
@@ -598,18 +644,28 @@ k_pairs(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ sgk, 
 #pragma unroll
   for (int q = 0; q < 18; ++q) {
     if (q >= nq) {
-      if (lane == 0) red[wid][q] = 0.0;
+      if (lane == 0) {
+        if constexpr (MIXED) {
+          redh[wid][q] = 0.0f;
+          redl[wid][q] = 0.0f;
+        } else {
+          red[wid][q] = 0.0;
+        }
+      }
       continue;
     }
     const R x = q < 9 ? (moved ? park[threadIdx.x][q] : Sx[q]) : (moved ? Sx[q - 9] : R(0));
     const double e = (q == 1 || q == 3) ? ew0 : ((q == 10 || q == 12) ? ew1 : 0.0);
     if constexpr (MIXED) {
       // over the 32 lanes as a compensated FP32 sum (hi + lo, Knuth's TwoSum
-      // per addition: ~48 significant bits), one FP64 value per warp: an
-      // FP64 butterfly on every lane costs ~90 additions per thread on
-      // GB300's narrow FP64 pipe (+40% on this kernel)
-      FF v = two_sum(x, (float)e);
-      v.lo += (float)(e - (double)(float)e);
+      // per addition: ~48 significant bits): an FP64 butterfly on every
+      // lane costs ~90 additions per thread on GB300's narrow FP64 pipe
+      // (+40% on this kernel), and so do conversions per warp
+      FF v{x, 0.0f};
+      if (EXT && e != 0.0) {
+        v = two_sum(x, (float)e);
+        v.lo += (float)(e - (double)(float)e);
+      }
       for (int dlt = 16; dlt > 0; dlt >>= 1) {
         const float h2 = __shfl_down_sync(0xffffffffu, v.hi, dlt);
         const float l2 = __shfl_down_sync(0xffffffffu, v.lo, dlt);
@@ -617,7 +673,10 @@ k_pairs(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ sgk, 
         v.hi = t.hi;
         v.lo = (v.lo + l2) + t.lo;
       }
-      if (lane == 0) red[wid][q] = (double)v.hi + (double)v.lo;
+      if (lane == 0) {
+        redh[wid][q] = v.hi;
+        redl[wid][q] = v.lo;
+      }
     } else {
       double v = (double)x + e;
       for (int dlt = 16; dlt > 0; dlt >>= 1) v += __shfl_down_sync(0xffffffffu, v, dlt);
@@ -629,9 +688,20 @@ k_pairs(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ sgk, 
   if (lane == 0 && c) atomicAdd(&st->w[ST_NCONT], c);
   __syncthreads();
   if (threadIdx.x < 18) {
-    double v = 0.0;
-    for (int w = 0; w < kWarps; ++w) v += red[w][threadIdx.x];
-    spart[blockIdx.x * 18 + threadIdx.x] = v;
+    if constexpr (MIXED) {
+      const int q = threadIdx.x;
+      FF v{redh[0][q], redl[0][q]};
+      for (int w = 1; w < kWarps; ++w) {
+        const FF t = two_sum(v.hi, redh[w][q]);
+        v.hi = t.hi;
+        v.lo = (v.lo + redl[w][q]) + t.lo;
+      }
+      spart[blockIdx.x * 18 + q] = (double)v.hi + (double)v.lo;
+    } else {
+      double v = 0.0;
+      for (int w = 0; w < kWarps; ++w) v += red[w][threadIdx.x];
+      spart[blockIdx.x * 18 + threadIdx.x] = v;
+    }
   }
 }
 

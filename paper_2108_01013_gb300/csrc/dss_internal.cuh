@@ -316,6 +316,17 @@ __device__ __forceinline__ FF ff_add(FF a, FF b) {
   return fast_two_sum(s.hi, s.lo);
 }
 __device__ __forceinline__ FF ff_neg(FF a) { return FF{-a.hi, -a.lo}; }
+// a + b for an FP32 increment b (TwoSum on the high words; the stretch
+// changes sign, so no magnitude order is assumed)
+__device__ __forceinline__ FF ff_add_f(FF a, float b) {
+  const FF s = two_sum(a.hi, b);
+  return two_sum(s.hi, s.lo + a.lo);
+}
+// a b for an FP32 factor b (Dekker's TwoProduct on the high word)
+__device__ __forceinline__ FF ff_mul_f(FF a, float b) {
+  const float p = a.hi * b;
+  return fast_two_sum(p, fmaf(a.hi, b, -p) + a.lo * b);
+}
 // w whole cells of edge (cs_hi + cs_lo) as a double-float: the product of
 // the FP32 words is made exact with Dekker's TwoProduct (w cs_hi needs more
 // than 24 bits once |w| >= 3: a pair several cells apart, or across the
@@ -355,10 +366,47 @@ struct StateBuf {
 };
 
 // Tangential stretch of one listed pair and its contact flag (one 32-byte
-// load or store).
+// load or store).  FP64 precision: the components x, y, z and w = 1 when the
+// pair was in contact, else 0.  Mixed precision: each component as a
+// double-float, two FP32 words (hi, lo) in place of the double, and the flag
+// as FP32 1 in the first word of w: words {x.hi, x.lo, y.hi, y.lo, z.hi,
+// z.lo, flag, 0}, so the stretch is carried with ~48 significant bits and
+// updated without GB300's narrow FP64 pipe.  Either way the record is all
+// zero bits when the pair was not in contact (xi_flag).
 struct __align__(32) Xi4 {
   double x, y, z, w;
 };
+
+__device__ __forceinline__ bool xi_flag(const Xi4& v) { return __double_as_longlong(v.w) != 0; }
+// double-float <-> the 8 bytes of one component (first word hi, second lo)
+__device__ __forceinline__ double ff_word(FF v) {
+  return __hiloint2double(__float_as_int(v.lo), __float_as_int(v.hi));
+}
+__device__ __forceinline__ FF word_ff(double d) {
+  return FF{__int_as_float(__double2loint(d)), __int_as_float(__double2hiint(d))};
+}
+// FP64 components of a record (either layout)
+__device__ __forceinline__ void xi_components(const Xi4& v, bool mixed, double o[3]) {
+  if (mixed) {
+    const FF a = word_ff(v.x), b = word_ff(v.y), c = word_ff(v.z);
+    o[0] = (double)a.hi + (double)a.lo;
+    o[1] = (double)b.hi + (double)b.lo;
+    o[2] = (double)c.hi + (double)c.lo;
+  } else {
+    o[0] = v.x;
+    o[1] = v.y;
+    o[2] = v.z;
+  }
+}
+// a record from FP64 components (either layout; the double-float split is
+// exact to ~2^-48)
+__device__ __forceinline__ Xi4 xi_record(double x, double y, double z, bool contact, bool mixed) {
+  if (!contact) return Xi4{0.0, 0.0, 0.0, 0.0};
+  if (!mixed) return Xi4{x, y, z, 1.0};
+  const float xh = (float)x, yh = (float)y, zh = (float)z;
+  return Xi4{ff_word(FF{xh, (float)(x - (double)xh)}), ff_word(FF{yh, (float)(y - (double)yh)}),
+             ff_word(FF{zh, (float)(z - (double)zh)}), ff_word(FF{1.0f, 0.0f})};
+}
 
 struct ListBuf {
   int* count;       // n half-list row lengths
