@@ -40,7 +40,7 @@ void free_buffers(dss_handle* h) {
     memset(&s, 0, sizeof(s));
     ListBuf& L = h->lb[b];
     dfree(L.count); dfree(L.list); dfree(L.start); dfree(L.xi); dfree(L.xr); dfree(L.slot_of_id);
-    dfree(L.id_of_slot);
+    dfree(L.id_of_slot); dfree(L.pown); dfree(L.pj);
     memset(&L, 0, sizeof(L));
   }
   dfree(h->posf); dfree(h->cellid); dfree(h->perm); dfree(h->key); dfree(h->offs); dfree(h->pred);
@@ -48,8 +48,10 @@ void free_buffers(dss_handle* h) {
   dfree(h->xc); dfree(h->mark);
   h->xc = nullptr; h->mark = nullptr; h->marked = false;
   dfree(h->cell_count); dfree(h->cell_start); dfree(h->tmp); dfree(h->spart);
-  dfree(h->own); dfree(h->bw_count); dfree(h->bw_rec);
-  h->own = nullptr; h->bw_count = nullptr; h->bw_rec = nullptr;
+  dfree(h->own); dfree(h->bw_count); dfree(h->bw_rec); dfree(h->carry);
+  h->own = nullptr; h->bw_count = nullptr; h->bw_rec = nullptr; h->carry = nullptr;
+  h->pb_blocks = 0;
+  h->compact_ok[0] = h->compact_ok[1] = false;
   dfree(h->io3); dfree(h->io3b); dfree(h->io_id); dfree(h->stage);
   h->stage = nullptr; dfree(h->scan_status); dfree(h->scan_ticket);
   dfree(h->sigma);
@@ -107,11 +109,34 @@ int alloc_pair_buffers(dss_handle* h, int64_t pcap, bool keep_hist) {
     dfree(L.xr);
     L.xi = xi;
     L.xr = xr;
+    // one instance: the compact owner / partner arrays of the pair-balanced
+    // pair kernel (rewritten by every enumeration of the list)
+    if (h->K == 1) {
+      int *pown = nullptr, *pj = nullptr;
+      if ((r = dalloc(h, &pown, (size_t)pcap))) return r;
+      if ((r = dalloc(h, &pj, (size_t)pcap))) {
+        dfree(pown);
+        return r;
+      }
+      dfree(L.pown);
+      dfree(L.pj);
+      L.pown = pown;
+      L.pj = pj;
+    }
   }
   h->pcap = pcap;
   h->g.pcap = pcap;
+  if (h->K == 1) {
+    const size_t rb = h->p.precision == DSS_MIXED ? sizeof(float) : sizeof(double);
+    char* carry = nullptr;
+    if ((r = dalloc(h, &carry, 12 * rb * (size_t)((pcap + 31) / 32)))) return r;
+    dfree(h->carry);
+    h->carry = carry;
+    h->pb_blocks = pair_pb_blocks(h);
+  }
+  h->compact_ok[0] = h->compact_ok[1] = false;
   double* sp = nullptr;
-  const int pb = pair_grid_blocks(h);
+  const int pb = std::max(pair_grid_blocks(h), pair_pb_blocks(h));
   if ((r = dalloc(h, &sp, 18 * (size_t)pb))) return r;
   dfree(h->spart);
   h->spart = sp;

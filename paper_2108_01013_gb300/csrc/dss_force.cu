@@ -11,6 +11,10 @@
 //   (-F and its torque) is appended to the partner's fixed-capacity row
 //   together with the owner's index.  No float is ever accumulated with an
 //   atomic.
+// k_pairs_pb<MIXED, MINB, EXT> (one instance): the same per pair, with the
+//   pairs in owner order dealt out 32 to a warp over the resident blocks
+//   (every lane busy whatever the row lengths); owners whose pairs cross a
+//   warp boundary leave head / tail partial sums the gather adds in order.
 // k_gather<MIXED, EXT>: one thread per particle: its own sum plus the partner
 //   records of its row taken in increasing owner index (a fixed order, so the
 //   result is bitwise reproducible; rows of 9 to 24 FP32 records and longer
@@ -486,6 +490,128 @@ __device__ __forceinline__ void store_record(double* b, double a0, double a1, do
   reinterpret_cast<double2*>(b)[3] = make_double2(a6, 0.0);
 }
 
+// Per pair after its evaluation: the partner's share (-F and its torque)
+// appended to the partner's row with the owner's index, the stretch records,
+// the contact count and the stresslet of Eq. 9 (S^C = r (x) F^C,
+// S^L = sym(r (x) F^L), F on the owner) added to the thread's sum.
+template <typename R, bool EXT>
+__device__ __forceinline__ void pair_commit(const Geo& g, const PairRes<R>& q, int i, int j, int p, ListBuf& W,
+                                            int* __restrict__ bw_count, R* __restrict__ bw, DevStatus* st,
+                                            R Sx[9], int& ncont) {
+  const int slot = atomicAdd(&bw_count[j], 1);
+  if (slot < g.M) {
+    R* b = bw + ((int64_t)j * g.M + slot) * kSlot;
+    store_record(b, -q.F[0], -q.F[1], -q.F[2], q.Tj[0], q.Tj[1], q.Tj[2], owner_bits<R>(i));
+  } else {
+    set_err(st, DSS_ERR_CAPACITY);
+  }
+  W.xi[p] = q.xrec;
+  if (EXT && g.k_r > 0.0) W.xr[p] = q.rrec;
+  ncont += q.contact;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b2 = 0; b2 < 3; ++b2)
+      Sx[3 * a + b2] += q.r[a] * q.Fc[b2] + R(0.5) * (q.r[a] * q.Fl[b2] + q.r[b2] * q.Fl[a]);
+}
+
+// Warp-segmented inclusive scan of the six force/torque sums over lanes with
+// the same owner (seg; lanes of one owner are contiguous).
+template <typename R>
+__device__ __forceinline__ void owner_scan(int lane, int seg, R v[6]) {
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int so = __shfl_up_sync(0xffffffffu, seg, d);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      const R u = __shfl_up_sync(0xffffffffu, v[c], d);
+      if (lane >= d && so == seg) v[c] += u;
+    }
+  }
+}
+
+// The block's stresslet partials (fixed tree over lanes, warps and blocks):
+// x0 the thread's sums for the instance of the block's first owner, x1 for
+// the next instance (zero unless `second`), e0/e1 the single-particle wave
+// stresslets the thread adds to them.  FP64 throughout in FP64.  In mixed
+// precision the thread sums (one to a few pairs each) are FP32, the lanes and
+// warps of the block are summed with compensation (Knuth's TwoSum on every
+// addition, ~48 significant bits: an FP64 butterfly on every lane costs ~90
+// additions per thread on GB300's narrow FP64 pipe, +40% on this kernel),
+// and the block's sum is converted to FP64 once; every sum beyond the block
+// is FP64.
+template <bool MIXED, bool EXT>
+__device__ __forceinline__ void stress_partials(
+    const typename std::conditional<MIXED, float, double>::type* x0,
+    const typename std::conditional<MIXED, float, double>::type* x1, bool second, double e0, double e1,
+    int ncont, double* __restrict__ spart, DevStatus* st) {
+  using R = typename std::conditional<MIXED, float, double>::type;
+  __shared__ double red[MIXED ? 1 : kWarps][18];
+  __shared__ float redh[MIXED ? kWarps : 1][18], redl[MIXED ? kWarps : 1][18];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  // the second instance slot holds anything only where a lane of the warp
+  // met a second instance (in its pairs, or as the owner of a wave stresslet)
+  const int nq = __any_sync(0xffffffffu, second || e1 != 0.0) ? 18 : 9;
+#pragma unroll
+  for (int q = 0; q < 18; ++q) {
+    if (q >= nq) {
+      if (lane == 0) {
+        if constexpr (MIXED) {
+          redh[wid][q] = 0.0f;
+          redl[wid][q] = 0.0f;
+        } else {
+          red[wid][q] = 0.0;
+        }
+      }
+      continue;
+    }
+    const R x = q < 9 ? x0[q] : (second ? x1[q - 9] : R(0));
+    const double e = (q == 1 || q == 3) ? e0 : ((q == 10 || q == 12) ? e1 : 0.0);
+    if constexpr (MIXED) {
+      FF v{x, 0.0f};
+      if (EXT && e != 0.0) {
+        v = two_sum(x, (float)e);
+        v.lo += (float)(e - (double)(float)e);
+      }
+      for (int dlt = 16; dlt > 0; dlt >>= 1) {
+        const float h2 = __shfl_down_sync(0xffffffffu, v.hi, dlt);
+        const float l2 = __shfl_down_sync(0xffffffffu, v.lo, dlt);
+        const FF t = two_sum(v.hi, h2);
+        v.hi = t.hi;
+        v.lo = (v.lo + l2) + t.lo;
+      }
+      if (lane == 0) {
+        redh[wid][q] = v.hi;
+        redl[wid][q] = v.lo;
+      }
+    } else {
+      double v = (double)x + e;
+      for (int dlt = 16; dlt > 0; dlt >>= 1) v += __shfl_down_sync(0xffffffffu, v, dlt);
+      if (lane == 0) red[wid][q] = v;
+    }
+  }
+  int c = ncont;
+  for (int dlt = 16; dlt > 0; dlt >>= 1) c += __shfl_down_sync(0xffffffffu, c, dlt);
+  if (lane == 0 && c) atomicAdd(&st->w[ST_NCONT], c);
+  __syncthreads();
+  if (threadIdx.x < 18) {
+    if constexpr (MIXED) {
+      const int q = threadIdx.x;
+      FF v{redh[0][q], redl[0][q]};
+      for (int w = 1; w < kWarps; ++w) {
+        const FF t = two_sum(v.hi, redh[w][q]);
+        v.hi = t.hi;
+        v.lo = (v.lo + redl[w][q]) + t.lo;
+      }
+      spart[blockIdx.x * 18 + q] = (double)v.hi + (double)v.lo;
+    } else {
+      double v = 0.0;
+      for (int w = 0; w < kWarps; ++w) v += red[w][threadIdx.x];
+      spart[blockIdx.x * 18 + threadIdx.x] = v;
+    }
+  }
+}
+
 // MINB: resident blocks per SM the register budget is cut for (a grid that
 // fills more than three blocks per SM gains from the fourth; smaller grids
 // run faster with the larger budget).
@@ -493,7 +619,7 @@ template <bool MIXED, int MINB, bool EXT>
 __global__ void __launch_bounds__(kPairThreads, MINB)
 k_pairs(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ sgk, StateBuf s, ListBuf W,
         ListBuf H, const float4* __restrict__ posf, void* __restrict__ own_v, int* __restrict__ bw_count,
-        void* __restrict__ bw_v, double* __restrict__ spart, DevStatus* st, int adv,
+        void* __restrict__ bw_v, double* __restrict__ spart, DevStatus* st,
         const int* __restrict__ perm) {
   using R = typename std::conditional<MIXED, float, double>::type;
   if (dev_err(st)) return;
@@ -514,14 +640,6 @@ k_pairs(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ sgk, 
   // as many particles as a block has threads), and a lane meets its pairs in
   // increasing owner order, so its instance changes at most once: the
   // stresslet sum of the first instance is parked in shared memory then.
-  // Each pair's stresslet is formed and added to the thread's sum in the pair
-  // arithmetic's precision (the grid covers every owner once, so a thread
-  // meets P/N pairs on average, one to three in these suspensions); in mixed
-  // precision the lanes of a warp are then summed with compensation (as
-  // accurate as FP64 over 32 values) and every sum beyond the warp (over
-  // warps and blocks) is FP64.  FP64 sums per thread or per lane (conversions
-  // and additions on GB300's narrow FP64 pipe, or a compensated sum in
-  // shared memory) made the kernel 1.4-1.6x slower.
   __shared__ R park[kPairThreads][9];
   const int inst0 = s.inst[min((int)(blockIdx.x * blockDim.x), n - 1)];
   int cur_inst = inst0;
@@ -567,18 +685,6 @@ k_pairs(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ sgk, 
         else q = pair_eval_fp64<EXT>(g, I, s, H, hr, sg.off, i, j);
         v[0] = q.F[0]; v[1] = q.F[1]; v[2] = q.F[2];
         v[3] = q.Ti[0]; v[4] = q.Ti[1]; v[5] = q.Ti[2];
-        // partner's share, appended to its row with the owner's index
-        const int slot = atomicAdd(&bw_count[j], 1);
-        if (slot < g.M) {
-          R* b = bw + ((int64_t)j * g.M + slot) * kSlot;
-          store_record(b, -q.F[0], -q.F[1], -q.F[2], q.Tj[0], q.Tj[1], q.Tj[2], owner_bits<R>(i));
-        } else {
-          set_err(st, DSS_ERR_CAPACITY);
-        }
-        W.xi[p] = q.xrec;
-        if (EXT && g.k_r > 0.0) W.xr[p] = q.rrec;
-        ncont += q.contact;
-        // Eq. 9: S^C = r (x) F^C, S^L = sym(r (x) F^L), F on the owner
         if (inst != cur_inst) {
 #pragma unroll
           for (int c = 0; c < 9; ++c) {
@@ -587,22 +693,9 @@ k_pairs(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ sgk, 
           }
           cur_inst = inst;
         }
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-          for (int b2 = 0; b2 < 3; ++b2)
-            Sx[3 * a + b2] += q.r[a] * q.Fc[b2] + R(0.5) * (q.r[a] * q.Fl[b2] + q.r[b2] * q.Fl[a]);
+        pair_commit<R, EXT>(g, q, i, j, p, W, bw_count, bw, st, Sx, ncont);
       }
-      // warp-segmented inclusive scan over lanes with the same owner
-#pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        const int so = __shfl_up_sync(0xffffffffu, seg, d);
-#pragma unroll
-        for (int c = 0; c < 6; ++c) {
-          const R u = __shfl_up_sync(0xffffffffu, v[c], d);
-          if (lane >= d && so == seg) v[c] += u;
-        }
-      }
+      owner_scan<R>(lane, seg, v);
       const int nxt = __shfl_down_sync(0xffffffffu, seg, 1);
       if (valid && (lane == 31 || nxt != seg)) {
 #pragma unroll
@@ -619,11 +712,6 @@ k_pairs(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ sgk, 
     for (int c = 0; c < 6; ++c) acc[wid][lane][c] = R(0);
     __syncwarp();
   }
-  // Block reduction of the stresslet (fixed tree over lanes, warps and
-  // blocks): FP64 throughout in FP64; in mixed precision a compensated FP32
-  // sum over the block's lanes and warps, one FP64 value per block
-  __shared__ double red[MIXED ? 1 : kWarps][18];
-  __shared__ float redh[MIXED ? kWarps : 1][18], redl[MIXED ? kWarps : 1][18];
   const bool moved = cur_inst != inst0;
   // With the wave of Eq. 17 the single-particle stresslets 20/3 pi eta0 a^3
   // E_inf(x) carry a local part, (10/3) pi eta0 a^3 U k cos(k y) on xy and
@@ -638,84 +726,115 @@ k_pairs(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ sgk, 
       if (s.inst[il0] == inst0) ew0 = e; else ew1 = e;
     }
   }
-  // the second instance slot holds anything only where a lane of the warp
-  // met a second instance (in its pairs, or as the owner of a wave stresslet)
-  const int nq = __any_sync(0xffffffffu, moved || ew1 != 0.0) ? 18 : 9;
+  R x0[9], x1[9];
 #pragma unroll
-  for (int q = 0; q < 18; ++q) {
-    if (q >= nq) {
-      if (lane == 0) {
-        if constexpr (MIXED) {
-          redh[wid][q] = 0.0f;
-          redl[wid][q] = 0.0f;
-        } else {
-          red[wid][q] = 0.0;
-        }
-      }
-      continue;
+  for (int c = 0; c < 9; ++c) {
+    x0[c] = moved ? park[threadIdx.x][c] : Sx[c];
+    x1[c] = moved ? Sx[c] : R(0);
+  }
+  stress_partials<MIXED, EXT>(x0, x1, moved, ew0, ew1, ncont, spart, st);
+}
+
+// Pair-balanced pair kernel (one instance).  The listed pairs in owner order
+// (the compact arrays pown, pj written with the row offsets by the
+// enumeration) are dealt out 32 to a warp over a grid of resident blocks, so
+// every lane holds a pair whatever the row lengths.  An owner's pairs are
+// contiguous: the warp-segmented scan sums each owner's share; an owner whose
+// pairs lie in one warp is written once (own), one whose pairs cross a warp
+// boundary leaves its part in the warp's head slot (continued from the
+// previous warp) or tail slot (continuing into the next), which the gather
+// adds in warp order.  Deterministic: the sums' order depends on the pair
+// order alone.
+template <bool MIXED, int MINB, bool EXT>
+__global__ void __launch_bounds__(kPairThreads, MINB)
+k_pairs_pb(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ sgk, StateBuf s, ListBuf W,
+           ListBuf H, const float4* __restrict__ posf, void* __restrict__ own_v, void* __restrict__ carry_v,
+           int* __restrict__ bw_count, void* __restrict__ bw_v, double* __restrict__ spart, DevStatus* st,
+           const int* __restrict__ perm) {
+  using R = typename std::conditional<MIXED, float, double>::type;
+  if (dev_err(st)) return;
+  R* __restrict__ own = static_cast<R*>(own_v);
+  R* __restrict__ carry = static_cast<R*>(carry_v);
+  R* __restrict__ bw = static_cast<R*>(bw_v);
+  const int n = g.n;
+  const int P = W.start[n];
+  const HistRef hr{perm, *((volatile const int*)&st->w[ST_IDORDER])};
+  if (P > g.pcap) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      st->w[ST_NPAIRS] = P;
+      set_err(st, DSS_ERR_CAPACITY);
     }
-    const R x = q < 9 ? (moved ? park[threadIdx.x][q] : Sx[q]) : (moved ? Sx[q - 9] : R(0));
-    const double e = (q == 1 || q == 3) ? ew0 : ((q == 10 || q == 12) ? ew1 : 0.0);
-    if constexpr (MIXED) {
-      // over the 32 lanes as a compensated FP32 sum (hi + lo, Knuth's TwoSum
-      // per addition: ~48 significant bits): an FP64 butterfly on every
-      // lane costs ~90 additions per thread on GB300's narrow FP64 pipe
-      // (+40% on this kernel), and so do conversions per warp
-      FF v{x, 0.0f};
-      if (EXT && e != 0.0) {
-        v = two_sum(x, (float)e);
-        v.lo += (float)(e - (double)(float)e);
+    return;
+  }
+  const InstGeo& I = ig[0];
+  const StepGeo sg = sgk[0];
+  R Sx[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  int ncont = 0;
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  const int npw = (P + 31) >> 5;
+  for (int pw = gw; pw < npw; pw += nw) {
+    const int p = pw * 32 + lane;
+    const bool valid = p < P;
+    const int i = valid ? W.pown[p] : -1;
+    const int j = valid ? W.pj[p] : 0;
+    // lane 0: does its owner continue from the previous warp?  lane 31: into
+    // the next?
+    const int before = (lane == 0 && valid && p > 0) ? W.pown[p - 1] : -1;
+    const int after = (lane == 31 && p + 1 < P) ? W.pown[p + 1] : -1;
+    R v[6] = {0, 0, 0, 0, 0, 0};
+    const int seg = valid ? i : -2 - lane;   // owner, unique sentinel when idle
+    if (valid) {
+      PairRes<R> q;
+      if constexpr (MIXED) q = pair_eval_mixed<EXT>(g, I, s, H, hr, sg, posf, i, j);
+      else q = pair_eval_fp64<EXT>(g, I, s, H, hr, sg.off, i, j);
+      v[0] = q.F[0]; v[1] = q.F[1]; v[2] = q.F[2];
+      v[3] = q.Ti[0]; v[4] = q.Ti[1]; v[5] = q.Ti[2];
+      pair_commit<R, EXT>(g, q, i, j, p, W, bw_count, bw, st, Sx, ncont);
+    }
+    owner_scan<R>(lane, seg, v);
+    const int nxt = __shfl_down_sync(0xffffffffu, seg, 1);
+    const int head = __shfl_sync(0xffffffffu, (before >= 0 && before == seg) ? seg : -1, 0);
+    if (valid && (lane == 31 || nxt != seg)) {
+      R* dst = nullptr;
+      if (seg == head) dst = carry + (int64_t)pw * 12;                 // continued from before
+      else if (after == seg) dst = carry + (int64_t)pw * 12 + 6;      // continues after (lane 31)
+      if (dst) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) dst[c] = v[c];
+      } else {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) own[(int64_t)c * n + i] = v[c];
       }
-      for (int dlt = 16; dlt > 0; dlt >>= 1) {
-        const float h2 = __shfl_down_sync(0xffffffffu, v.hi, dlt);
-        const float l2 = __shfl_down_sync(0xffffffffu, v.lo, dlt);
-        const FF t = two_sum(v.hi, h2);
-        v.hi = t.hi;
-        v.lo = (v.lo + l2) + t.lo;
-      }
-      if (lane == 0) {
-        redh[wid][q] = v.hi;
-        redl[wid][q] = v.lo;
-      }
-    } else {
-      double v = (double)x + e;
-      for (int dlt = 16; dlt > 0; dlt >>= 1) v += __shfl_down_sync(0xffffffffu, v, dlt);
-      if (lane == 0) red[wid][q] = v;
     }
   }
-  int c = ncont;
-  for (int dlt = 16; dlt > 0; dlt >>= 1) c += __shfl_down_sync(0xffffffffu, c, dlt);
-  if (lane == 0 && c) atomicAdd(&st->w[ST_NCONT], c);
-  __syncthreads();
-  if (threadIdx.x < 18) {
-    if constexpr (MIXED) {
-      const int q = threadIdx.x;
-      FF v{redh[0][q], redl[0][q]};
-      for (int w = 1; w < kWarps; ++w) {
-        const FF t = two_sum(v.hi, redh[w][q]);
-        v.hi = t.hi;
-        v.lo = (v.lo + redl[w][q]) + t.lo;
-      }
-      spart[blockIdx.x * 18 + q] = (double)v.hi + (double)v.lo;
-    } else {
-      double v = 0.0;
-      for (int w = 0; w < kWarps; ++w) v += red[w][threadIdx.x];
-      spart[blockIdx.x * 18 + threadIdx.x] = v;
+  // the wave's single-particle stresslets (see k_pairs), particles strided
+  // over the grid's threads
+  double ew0 = 0.0;
+  if (EXT && g.wave) {
+    for (int il = blockIdx.x * blockDim.x + threadIdx.x; il < n; il += gridDim.x * blockDim.x) {
+      const double a = s.a[il];
+      ew0 += (10.0 / 3.0) * DSS_PI * g.eta0 * a * a * a * s.wv[il].y;
     }
   }
+  stress_partials<MIXED, EXT>(Sx, Sx, false, ew0, 0.0, ncont, spart, st);
 }
 
 // Bulk stress (Eq. 8) of one instance from the pair blocks' partials, by one
 // block of the gather (fixed strided assignment and fixed tree).  Pair block b
 // holds the sums of the instance containing its first owner (slot 0) and of
 // the next instance (slot 1).
+// With the pair-balanced kernel (one instance, pb_blocks > 0) every block's
+// first slot belongs to the instance.
 __device__ void inst_stress(const Geo& g, const InstGeo& I, const double* __restrict__ spart,
-                            double* __restrict__ sigma) {
+                            double* __restrict__ sigma, int pb_blocks) {
   __shared__ double red[kThreads / 32][9];
   double v[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-  const int b0 = I.p_begin / kPairThreads, b1 = (I.p_end - 1) / kPairThreads;
+  const int b0 = pb_blocks ? 0 : I.p_begin / kPairThreads;
+  const int b1 = pb_blocks ? pb_blocks - 1 : (I.p_end - 1) / kPairThreads;
   for (int b = b0 + threadIdx.x; b <= b1; b += blockDim.x) {
-    const double* p = spart + b * 18 + (b * kPairThreads >= I.p_begin ? 0 : 9);
+    const double* p = spart + b * 18 + (pb_blocks || b * kPairThreads >= I.p_begin ? 0 : 9);
 #pragma unroll
     for (int q = 0; q < 9; ++q) v[q] += p[q];
   }
@@ -914,9 +1033,11 @@ __device__ __forceinline__ bool gather_one(const Geo& g, const InstGeo* __restri
                                            const void* __restrict__ own_v,
                                            const int* __restrict__ bw_count, const void* __restrict__ bw_v,
                                            double* __restrict__ Fout, double* __restrict__ Tout,
-                                           DevStatus* st, int mode, int j0, int* slots) {
+                                           DevStatus* st, int mode, int j0, int* slots,
+                                           const void* __restrict__ carry_v, const int* __restrict__ start) {
   using R = typename std::conditional<MIXED, float, double>::type;
   const R* __restrict__ own = static_cast<const R*>(own_v);
+  const R* __restrict__ carry = static_cast<const R*>(carry_v);
   const R* __restrict__ bw = static_cast<const R*>(bw_v);
   const int n = g.n;
   // every lane of the warp takes part in the long FP64 rows below; lanes
@@ -925,10 +1046,39 @@ __device__ __forceinline__ bool gather_one(const Geo& g, const InstGeo* __restri
   const int j = valid ? j0 : 0;
   int cnt = valid ? __ldg(bw_count + j) : 0;
   R F[3], T[3];
+  if (carry) {
+    // pair-balanced sums: none (no owned pair), the owner's single write, or
+    // the tail slot of its first warp plus the head slots of the next ones
+    const int s0 = __ldg(start + j), s1 = __ldg(start + j + 1);
+    const int w0 = s0 >> 5, w1 = (s1 - 1) >> 5;
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    F[c] = own[(int64_t)c * n + j];
-    T[c] = own[(int64_t)(3 + c) * n + j];
+    for (int c = 0; c < 3; ++c) F[c] = T[c] = R(0);
+    if (s1 > s0 && w0 == w1) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        F[c] = own[(int64_t)c * n + j];
+        T[c] = own[(int64_t)(3 + c) * n + j];
+      }
+    } else if (s1 > s0) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        F[c] = carry[(int64_t)w0 * 12 + 6 + c];
+        T[c] = carry[(int64_t)w0 * 12 + 9 + c];
+      }
+      for (int w = w0 + 1; w <= w1; ++w) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          F[c] += carry[(int64_t)w * 12 + c];
+          T[c] += carry[(int64_t)w * 12 + 3 + c];
+        }
+      }
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      F[c] = own[(int64_t)c * n + j];
+      T[c] = own[(int64_t)(3 + c) * n + j];
+    }
   }
   const double a = __ldg(s.a + j);
   const int id = __ldg(s.id + j);
@@ -1090,7 +1240,8 @@ __global__ void __launch_bounds__(kThreads, 6)
 k_gather(Geo g, const InstGeo* __restrict__ ig, StateBuf s, const void* __restrict__ own_v,
          const int* __restrict__ bw_count, const void* __restrict__ bw_v, double* __restrict__ Fout,
          double* __restrict__ Tout, DevStatus* st, int mode, const double* __restrict__ spart,
-         double* sigma, double* sigma_sum, const int* __restrict__ start, unsigned int* done_blocks) {
+         double* sigma, double* sigma_sum, const int* __restrict__ start, unsigned int* done_blocks,
+         const void* __restrict__ carry_v, int pb_blocks) {
   // An error set before this kernel (an earlier kernel of the step, or an
   // earlier step of the same dss_step call, whose successors still replay)
   // means this step is void: touch no state, since the buffer this step
@@ -1103,12 +1254,12 @@ k_gather(Geo g, const InstGeo* __restrict__ ig, StateBuf s, const void* __restri
   bool fence = false;
   if (!s_err0) {
     if (blockIdx.x < (unsigned)g.K) {
-      inst_stress(g, ig[blockIdx.x], spart, sigma + 9 * blockIdx.x);
+      inst_stress(g, ig[blockIdx.x], spart, sigma + 9 * blockIdx.x, pb_blocks);
       fence = threadIdx.x < 9;
     } else {
       const int j = (int)(blockIdx.x - g.K) * blockDim.x + threadIdx.x;
       fence = gather_one<MIXED, EXT>(g, ig, s, own_v, bw_count, bw_v, Fout, Tout, st, mode, j,
-                                s_slot[threadIdx.x >> 5]);
+                                s_slot[threadIdx.x >> 5], carry_v, start);
     }
   }
   __shared__ bool last;
@@ -1154,6 +1305,13 @@ int pair_grid_blocks(const dss_handle* h) {
   return (int)(need > 0 ? need : 1);
 }
 
+// The pair-balanced kernel's grid (one instance; 0 otherwise): the blocks its
+// register budget keeps resident on every SM (3 of 256 threads in mixed
+// precision, 2 in FP64), their warps striding over the warps of pairs.
+int pair_pb_blocks(const dss_handle* h) {
+  return h->K == 1 ? h->sms * (h->g.precision == DSS_MIXED ? 3 : 2) : 0;
+}
+
 int bw_slot_values() { return kSlot; }
 
 namespace {
@@ -1162,35 +1320,48 @@ namespace {
 template <bool EXT>
 void launch_forces_t(dss_handle* h, int stbuf, int work_list, int hist_list, int adv, int mode,
                      double* F_out, double* T_out) {
+  (void)adv;
   const int n = (int)h->n;
   const int pb = pair_grid_blocks(h);
   const bool mixed = h->g.precision == DSS_MIXED;
   prof_mark(h, 5);
+  // one instance: pairs dealt out 32 to a warp over the resident blocks
+  const bool pbal = h->pb_blocks > 0 && h->compact_ok[work_list];
   const bool big = h->tune_pairs_minb ? h->tune_pairs_minb == 4 : pb > 3 * h->sms;
-  if (mixed && big)
+  if (pbal && mixed)
+    k_pairs_pb<true, 3, EXT><<<h->pb_blocks, kPairThreads, 0, h->stream>>>(
+        h->g, h->ig, h->sg, h->st[stbuf], h->lb[work_list], h->lb[hist_list], h->posf, h->own, h->carry,
+        h->bw_count, h->bw_rec, h->spart, h->status, h->perm);
+  else if (pbal)
+    k_pairs_pb<false, 2, EXT><<<h->pb_blocks, kPairThreads, 0, h->stream>>>(
+        h->g, h->ig, h->sg, h->st[stbuf], h->lb[work_list], h->lb[hist_list], h->posf, h->own, h->carry,
+        h->bw_count, h->bw_rec, h->spart, h->status, h->perm);
+  else if (mixed && big)
     k_pairs<true, 4, EXT><<<pb, kPairThreads, 0, h->stream>>>(
         h->g, h->ig, h->sg, h->st[stbuf], h->lb[work_list], h->lb[hist_list], h->posf, h->own, h->bw_count,
-        h->bw_rec, h->spart, h->status, adv, h->perm);
+        h->bw_rec, h->spart, h->status, h->perm);
   else if (mixed)
     k_pairs<true, 3, EXT><<<pb, kPairThreads, 0, h->stream>>>(
         h->g, h->ig, h->sg, h->st[stbuf], h->lb[work_list], h->lb[hist_list], h->posf, h->own, h->bw_count,
-        h->bw_rec, h->spart, h->status, adv, h->perm);
+        h->bw_rec, h->spart, h->status, h->perm);
   else
     k_pairs<false, 2, EXT><<<pb, kPairThreads, 0, h->stream>>>(
         h->g, h->ig, h->sg, h->st[stbuf], h->lb[work_list], h->lb[hist_list], h->posf, h->own, h->bw_count,
-        h->bw_rec, h->spart, h->status, adv, h->perm);
+        h->bw_rec, h->spart, h->status, h->perm);
   prof_mark(h, 6);
   const int gb = (n + kThreads - 1) / kThreads + h->g.K;
+  const void* carry = pbal ? h->carry : nullptr;
+  const int pbb = pbal ? h->pb_blocks : 0;
   if (mixed)
     k_gather<true, EXT><<<gb, kThreads, 0, h->stream>>>(h->g, h->ig, h->st[stbuf], h->own, h->bw_count,
                                                         h->bw_rec, F_out, T_out, h->status, mode, h->spart,
                                                         h->sigma, h->sigma_sum, h->lb[work_list].start,
-                                                        h->done_blocks);
+                                                        h->done_blocks, carry, pbb);
   else
     k_gather<false, EXT><<<gb, kThreads, 0, h->stream>>>(h->g, h->ig, h->st[stbuf], h->own, h->bw_count,
                                                          h->bw_rec, F_out, T_out, h->status, mode, h->spart,
                                                          h->sigma, h->sigma_sum, h->lb[work_list].start,
-                                                         h->done_blocks);
+                                                         h->done_blocks, carry, pbb);
   prof_mark(h, 7);
 }
 }  // namespace

@@ -417,6 +417,8 @@ struct ListBuf {
   Xi4* xr;          // pcap when k_r > 0: rolling stretch (App. B) per pair slot (w unused)
   int* slot_of_id;  // n: sorted index of each id in this list's index space
   int* id_of_slot;  // n: id of each sorted index of this list
+  int* pown;        // pcap, one instance only (else null): owner of each pair, in pair order
+  int* pj;          // pcap, one instance only: partner of each pair (the rows, compacted)
 };
 
 // Buffers of the adjoint (reverse sweep over a rollout): per-step tapes of
@@ -510,6 +512,11 @@ struct dss_handle {
   bool hist_empty;
   // force accumulation of the last force pass (FP32 in mixed precision)
   void* own;         // 6n: force and torque summed over each particle's own row
+  void* carry;       // one instance: 12 per warp of 32 pairs, the sums of the owners whose
+                     // pairs continue from the previous warp (6) and into the next (6)
+  int pb_blocks;     // one instance: blocks of the pair-balanced pair kernel (0: owner rows)
+  bool compact_ok[2];  // the list's compact pair arrays were written by its last enumeration
+                       // (false after the pair buffers are reallocated)
   int* bw_count;     // n: records appended to each particle's partner row
   void* bw_rec;      // n*M slots of 8 values: partner force (3), torque (3), owner index
   int64_t pcap;
@@ -567,6 +574,7 @@ void launch_dispersion(dss_handle* h, double* sums);
 void launch_clusters(dss_handle* h, int* parent, int* minid, int* count, int* label);
 void launch_phi_profile(dss_handle* h, int nbins, double a_split, const double* unit, unsigned long long* acc);
 int pair_grid_blocks(const dss_handle* h);
+int pair_pb_blocks(const dss_handle* h);
 void launch_scan(dss_handle* h, const int* in, int* out, int count, int which, bool zero_in);
 int scan_tiles_for(int count);
 int enum_tiles_for(int n);

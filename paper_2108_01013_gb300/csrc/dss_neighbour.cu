@@ -190,6 +190,16 @@ __device__ __forceinline__ void finish_rows(const Geo& g, const StateBuf& s, Lis
   const int prefix = lookback_warp(scan_status, wtile, agg, st);
   if (i < n) L.start[i] = prefix + incl - v;
   if (lane == 0 && (wtile + 1) * 32 >= n) L.start[n] = prefix + agg;
+  // one instance: the row, compacted at its offset with its owner (the pair
+  // order of the pair-balanced force kernel; the thread reads back its own
+  // row writes)
+  if (L.pown && i < n) {
+    const int64_t s0 = prefix + incl - v;
+    for (int k = 0; k < v && s0 + k < g.pcap; ++k) {
+      L.pj[s0 + k] = e.row[k];
+      L.pown[s0 + k] = i;
+    }
+  }
 }
 
 template <bool ECH, int UNR, bool SPLIT>
@@ -385,4 +395,5 @@ void launch_enumerate(dss_handle* h, int stbuf, int dst_list, int adv) {
         h->g, h->ig, h->sg, h->st[stbuf], h->posf, h->cellid, h->cell_start, L, h->bw_count,
         h->scan_status + h->scan_tiles_max, h->scan_ticket + 1, h->status, adv);
   h->last_list = dst_list;
+  h->compact_ok[dst_list] = L.pown != nullptr;
 }
