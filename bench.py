@@ -84,9 +84,9 @@ IMPL_BYTES = {
     "k_scan_cells":  ((0, 12, 0, 0),        (0, 12, 0, 0)),
     "k_scatter":     ((16, 0, 0, 0),        (16, 0, 0, 0)),
     "k_rank_gather": ((269, 0, 0, 0),       (301, 0, 0, 0)),
-    "k_enumerate":   ((52, 8, 4, 0),        (52, 8, 4, 0)),
-    "k_pairs":       ((148, 0, 108, 56),    (112, 0, 76, 56)),
-    "k_gather":      ((216, 0, 64, 0),      (216, 0, 32, 0)),
+    "k_enumerate":   ((52, 8, 16, 0),       (52, 8, 16, 0)),     # + rows read back, compacted (12 p)
+    "k_pairs":       ((144, 0, 112, 56),    (108, 0, 80, 56)),   # pair-balanced (one instance)
+    "k_gather":      ((220, 0, 64, 0),      (220, 0, 32, 0)),
 }
 # The neighbour + force step alone (without the integration's 288 n).
 NF_BYTES = ((216, 8, 8, 64), (192, 8, 8, 64))
@@ -98,8 +98,8 @@ KERNELS_PER_STEP = len(ALG_BYTES)
 # was built from and their hash; reported only while those files are
 # unchanged (profiles/ncu_full_c2_mixed_100k.md).
 NCU_TRAFFIC = {
-    ("k_pairs", "mixed"): (21_702_144, ("dss_force.cu", "dss_internal.cuh", "dss_pair_model.cuh"),
-                           "0a11b8a8804d8e18"),
+    ("k_pairs", "mixed"): (27_379_200, ("dss_force.cu", "dss_internal.cuh", "dss_pair_model.cuh"),
+                           "d90fce210634dfbb"),
 }
 
 
