@@ -128,7 +128,7 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="c2")
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
-    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--modes", default="fp64,echem,analysis,wavy,batched,poly1m,adjoint,cpu",
@@ -743,17 +743,18 @@ def main():
         s.set_profiling(False)
 
         # end to end through the public API: per step upload the full state
-        # from pinned host memory, advance, read state and stress back
-        host = {k: torch.empty((3, n), dtype=torch.float64, pin_memory=True)
-                for k in ("x", "u", "w", "al", "aw")}
-        s.get_state_into(*(host[k] for k in ("x", "u", "w", "al", "aw")))
+        # from pinned host memory, advance, read state and stress back, in one
+        # call (dss_step_io: upload, step graph, download and stress read
+        # issued back to back, one synchronisation)
+        host = [torch.empty((3, n), dtype=torch.float64, pin_memory=True) for _ in range(5)]
+        sig = torch.empty(9, dtype=torch.float64, pin_memory=True)
+        s.get_state_into(*host)
+        for _ in range(3):                         # untimed: first calls
+            s.step_io(host, 1, host, sig)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
-            s.load_state(*(host[k] for k in ("x", "u", "w", "al", "aw")))
-            s.step(1)
-            s.get_state_into(*(host[k] for k in ("x", "u", "w", "al", "aw")))
-            sig = s.stress()
+            s.step_io(host, 1, host, sig)
         torch.cuda.synchronize()
         t_e2e = time.perf_counter() - t0
         e2e_value = job_rate(n * args.e2e_steps, t_e2e, world, dev)

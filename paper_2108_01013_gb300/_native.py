@@ -129,6 +129,7 @@ SIGNATURES = {
     "dss_stress": (c_int, [c_void_p, _dp]),
     "dss_get_counters": (c_int, [c_void_p, POINTER(Counters)]),
     "dss_load_state": (c_int, [c_void_p, _vp, _vp, _vp, _vp, _vp]),
+    "dss_step_io": (c_int, [c_void_p, POINTER(c_void_p), c_int64, POINTER(c_void_p), _vp]),
     "dss_set_profiling": (c_int, [c_void_p, c_int]),
     "dss_get_profile": (c_int, [c_void_p, _dp, _lp]),
     "dss_profile_name": (c_char_p, [c_int]),

@@ -956,51 +956,59 @@ int dss_set_state(dss_handle* h, const double* x, const double* a, const int32_t
   });
 }
 
+// The committed state out in id order (any of out[0..4] may be null):
+// enqueued on the stream, not synchronised.
+int get_state_enqueue(dss_handle* h, double* const out[5]) {
+  const int n = (int)h->n;
+  const StateBuf& s = h->st[h->cur];
+  // device outputs are written in place by the scatter; host outputs go
+  // through the staging area, then out by a coalesced copy kernel (mapped
+  // pinned memory) or the copy engine (pageable memory)
+  Dst5 direct, staged, views;
+  for (int k = 0; k < 5; ++k) {
+    direct.d[k] = staged.d[k] = views.d[k] = nullptr;
+    if (!out[k]) continue;
+    cudaPointerAttributes at;
+    const bool is_dev = cudaPointerGetAttributes(&at, out[k]) == cudaSuccess && at.type == cudaMemoryTypeDevice;
+    cudaGetLastError();
+    if (is_dev) {
+      direct.d[k] = out[k];
+    } else {
+      staged.d[k] = h->stage + (size_t)k * 3 * n;
+      views.d[k] = static_cast<double*>(const_cast<void*>(device_view(out[k])));
+    }
+  }
+  Dst5 all = direct;
+  for (int k = 0; k < 5; ++k)
+    if (staged.d[k]) all.d[k] = staged.d[k];
+  k_state_out<<<(n + 255) / 256, 256, 0, h->stream>>>(n, s, all);
+  Dst5 src_c, dst_c;
+  bool any_view = false;
+  for (int k = 0; k < 5; ++k) {
+    src_c.d[k] = dst_c.d[k] = nullptr;
+    if (!staged.d[k]) continue;
+    if (views.d[k]) {
+      src_c.d[k] = staged.d[k];
+      dst_c.d[k] = views.d[k];
+      any_view = true;
+    } else {
+      CK(cudaMemcpyAsync(out[k], staged.d[k], sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, h->stream));
+    }
+  }
+  if (any_view) k_copy5<<<std::min((3 * n + 255) / 256, 8 * h->sms), 256, 0, h->stream>>>(3 * (int64_t)n, src_c, dst_c);
+  CK(cudaGetLastError());
+  return DSS_OK;
+}
+
 int dss_get_state(dss_handle* h, double* x, double* u, double* w, double* alpha_lin,
                   double* alpha_ang) {
   return guard([&]() -> int {
     if (!h) return DSS_ERR_ARG;
     if (!h->have_state) return DSS_ERR_STATE;
     ENTER(h);
-    const int n = (int)h->n;
-    const StateBuf& s = h->st[h->cur];
-    double* out[5] = {x, u, w, alpha_lin, alpha_ang};
-    // device outputs are written in place by the scatter; host outputs go
-    // through the staging area, then out by a coalesced copy kernel (mapped
-    // pinned memory) or the copy engine (pageable memory)
-    Dst5 direct, staged, views;
-    for (int k = 0; k < 5; ++k) {
-      direct.d[k] = staged.d[k] = views.d[k] = nullptr;
-      if (!out[k]) continue;
-      cudaPointerAttributes at;
-      const bool is_dev = cudaPointerGetAttributes(&at, out[k]) == cudaSuccess && at.type == cudaMemoryTypeDevice;
-      cudaGetLastError();
-      if (is_dev) {
-        direct.d[k] = out[k];
-      } else {
-        staged.d[k] = h->stage + (size_t)k * 3 * n;
-        views.d[k] = static_cast<double*>(const_cast<void*>(device_view(out[k])));
-      }
-    }
-    Dst5 all = direct;
-    for (int k = 0; k < 5; ++k)
-      if (staged.d[k]) all.d[k] = staged.d[k];
-    k_state_out<<<(n + 255) / 256, 256, 0, h->stream>>>(n, s, all);
-    Dst5 src_c, dst_c;
-    bool any_view = false;
-    for (int k = 0; k < 5; ++k) {
-      src_c.d[k] = dst_c.d[k] = nullptr;
-      if (!staged.d[k]) continue;
-      if (views.d[k]) {
-        src_c.d[k] = staged.d[k];
-        dst_c.d[k] = views.d[k];
-        any_view = true;
-      } else {
-        CK(cudaMemcpyAsync(out[k], staged.d[k], sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, h->stream));
-      }
-    }
-    if (any_view) k_copy5<<<std::min((3 * n + 255) / 256, 8 * h->sms), 256, 0, h->stream>>>(3 * (int64_t)n, src_c, dst_c);
-    CK(cudaGetLastError());
+    double* const out[5] = {x, u, w, alpha_lin, alpha_ang};
+    int r = get_state_enqueue(h, out);
+    if (r) return r;
     CK(cudaStreamSynchronize(h->stream));
     return DSS_OK;
   });
@@ -1068,84 +1076,162 @@ int dss_force_eval(dss_handle* h, double* F, double* T) {
   return DSS_OK;
 }
 
+// The step graphs of `remaining` steps from the committed (cur, hist)
+// state, enqueued (graphs captured first where missing), between the two
+// step events.  StepRun keeps what the commit needs after the synchronisation.
+struct StepRun {
+  int steps0, cur0, hist0;
+};
+
+int step_launch(dss_handle* h, int64_t remaining, StepRun& run) {
+  int r;
+  if (!h->step_ev[0]) {
+    CK(cudaEventCreate(&h->step_ev[0]));
+    CK(cudaEventCreate(&h->step_ev[1]));
+  }
+  // the host mirror holds the counter of the last synchronisation; only
+  // dss_step and dss_set_state change it, and both end synchronised
+  run.steps0 = h->status_host->w[ST_STEPS];
+  run.cur0 = h->cur;
+  run.hist0 = h->hist;
+  int c = run.cur0, hs = run.hist0;
+  for (int64_t k = 0; k < remaining; ++k) {
+    if (!h->graph_ok[c * 2 + hs]) {
+      h->cur = c;
+      h->hist = hs;
+      r = capture_step(h, c * 2 + hs);
+      if (r) return r;
+    }
+    c = 1 - c;
+    hs = 1 - hs;
+  }
+  c = run.cur0;
+  hs = run.hist0;
+  // runs of DSS_MULTI_STEPS steps go out as one graph launch (not while
+  // profiling, which times each step's kernels)
+  const int64_t multi = h->profiling ? 0 : remaining / DSS_MULTI_STEPS;
+  if (multi > 0 && !h->multi_ok[c * 2 + hs]) {
+    r = capture_multi(h, c * 2 + hs);
+    if (r) return r;
+  }
+  CK(cudaEventRecord(h->step_ev[0], h->stream));
+  for (int64_t k = 0; k < multi; ++k) CK(cudaGraphLaunch(h->multi_graph[c * 2 + hs], h->stream));
+  for (int64_t k = multi * DSS_MULTI_STEPS; k < remaining; ++k) {
+    const int key = c * 2 + hs;
+    CK(cudaGraphLaunch(h->step_graph[key], h->stream));
+    if (h->profiling) {
+      r = accumulate_profile(h);
+      if (r) return r;
+    }
+    c = 1 - c;
+    hs = 1 - hs;
+  }
+  CK(cudaEventRecord(h->step_ev[1], h->stream));
+  return DSS_OK;
+}
+
+// After the synchronisation (the status mirror current): the steps the
+// device committed, the buffer roles after them, the step time; returns the
+// device error (0 when none).
+int step_commit(dss_handle* h, const StepRun& run, int64_t& done) {
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, h->step_ev[0], h->step_ev[1]));
+  h->last_step_ms += ms;
+  done = h->status_host->w[ST_STEPS] - run.steps0;
+  h->cur = (done & 1) ? 1 - run.cur0 : run.cur0;
+  h->hist = (done & 1) ? 1 - run.hist0 : run.hist0;
+  h->host_steps_done += done;
+  h->mean_steps += done;
+  if (done > 0) h->last_list = h->hist;
+  return status_error(h);
+}
+
+// dss_step's loop from the committed state; the caller holds the handle.
+int step_run(dss_handle* h, int64_t nsteps) {
+  int64_t remaining = nsteps;
+  int retries = 0;
+  while (remaining > 0) {
+    StepRun run;
+    int r = step_launch(h, remaining, run);
+    if (r) return r;
+    r = sync_status(h);
+    if (r) return r;
+    int64_t done = 0;
+    const int err = step_commit(h, run, done);
+    remaining -= done;
+    if (!err) break;
+    clear_err(h);
+    // a pair-capacity overflow is recovered by growing the pair buffers
+    const int P = h->status_host->w[ST_NPAIRS];
+    if (err == DSS_ERR_CAPACITY && P > h->pcap && retries < 4) {
+      ++retries;
+      r = alloc_pair_buffers(h, (int64_t)(P * 1.25) + 1024, true);
+      if (r) return r;
+      continue;
+    }
+    return err;
+  }
+  return DSS_OK;
+}
+
 int dss_step(dss_handle* h, int64_t nsteps) {
   return guard([&]() -> int {
     if (!h || nsteps < 0) return DSS_ERR_ARG;
     if (!h->have_state) return DSS_ERR_STATE;
     ENTER(h);
-    int64_t remaining = nsteps;
-    int retries = 0;
     h->last_step_ms = 0.0;
-    if (!h->step_ev[0]) {
-      CK(cudaEventCreate(&h->step_ev[0]));
-      CK(cudaEventCreate(&h->step_ev[1]));
-    }
-    while (remaining > 0) {
-      int r;
-      // the host mirror holds the counter of the last synchronisation; only
-      // dss_step and dss_set_state change it, and both end synchronised
-      const int steps0 = h->status_host->w[ST_STEPS];
-      const int cur0 = h->cur, hist0 = h->hist;
-      int c = cur0, hs = hist0;
-      for (int64_t k = 0; k < remaining; ++k) {
-        if (!h->graph_ok[c * 2 + hs]) {
-          h->cur = c;
-          h->hist = hs;
-          r = capture_step(h, c * 2 + hs);
-          if (r) return r;
-        }
-        c = 1 - c;
-        hs = 1 - hs;
-      }
-      c = cur0;
-      hs = hist0;
-      // runs of DSS_MULTI_STEPS steps go out as one graph launch (not while
-      // profiling, which times each step's kernels)
-      const int64_t multi = h->profiling ? 0 : remaining / DSS_MULTI_STEPS;
-      if (multi > 0 && !h->multi_ok[c * 2 + hs]) {
-        r = capture_multi(h, c * 2 + hs);
-        if (r) return r;
-      }
-      CK(cudaEventRecord(h->step_ev[0], h->stream));
-      for (int64_t k = 0; k < multi; ++k) CK(cudaGraphLaunch(h->multi_graph[c * 2 + hs], h->stream));
-      for (int64_t k = multi * DSS_MULTI_STEPS; k < remaining; ++k) {
-        const int key = c * 2 + hs;
-        CK(cudaGraphLaunch(h->step_graph[key], h->stream));
-        if (h->profiling) {
-          r = accumulate_profile(h);
-          if (r) return r;
-        }
-        c = 1 - c;
-        hs = 1 - hs;
-      }
-      CK(cudaEventRecord(h->step_ev[1], h->stream));
-      r = sync_status(h);
+    return step_run(h, nsteps);
+  });
+}
+
+int load_state_enqueue(dss_handle* h, const double* const in[5]);
+
+int dss_step_io(dss_handle* h, const double* const in[5], int64_t nsteps, double* const out[5],
+                double sigma[9]) {
+  return guard([&]() -> int {
+    if (!h || !in || nsteps < 0) return DSS_ERR_ARG;
+    for (int k = 0; k < 5; ++k)
+      if (!in[k]) return DSS_ERR_ARG;
+    if (!h->have_state) return DSS_ERR_STATE;
+    ENTER(h);
+    h->last_step_ms = 0.0;
+    int r = load_state_enqueue(h, in);
+    if (r) return r;
+    double* const none[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    double* const* dst = out ? out : none;
+    StepRun run;
+    int64_t done = 0;
+    if (nsteps > 0) {
+      r = step_launch(h, nsteps, run);
       if (r) return r;
-      {
-        float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, h->step_ev[0], h->step_ev[1]));
-        h->last_step_ms += ms;
-      }
-      const int done = h->status_host->w[ST_STEPS] - steps0;
-      h->cur = (done & 1) ? 1 - cur0 : cur0;
-      h->hist = (done & 1) ? 1 - hist0 : hist0;
-      h->host_steps_done += done;
-      h->mean_steps += done;
-      remaining -= done;
-      if (done > 0) h->last_list = h->hist;
-      const int err = status_error(h);
-      if (!err) break;
-      clear_err(h);
-      // a pair-capacity overflow is recovered by growing the pair buffers
-      const int P = h->status_host->w[ST_NPAIRS];
-      if (err == DSS_ERR_CAPACITY && P > h->pcap && retries < 4) {
-        ++retries;
-        r = alloc_pair_buffers(h, (int64_t)(P * 1.25) + 1024, true);
-        if (r) return r;
-        continue;
-      }
-      return err;
     }
+    // the state after the steps, as the buffer roles will be once they are
+    // all committed, and the stress: enqueued behind the step graphs (the
+    // commit below sets the roles from what the device did)
+    if (nsteps > 0) h->cur = (nsteps & 1) ? 1 - run.cur0 : run.cur0;
+    r = get_state_enqueue(h, dst);
+    if (r) return r;
+    if (sigma) CK(cudaMemcpyAsync(sigma, h->sigma, 9 * sizeof(double), cudaMemcpyDefault, h->stream));
+    r = sync_status(h);
+    if (r) return r;
+    if (nsteps == 0) return DSS_OK;
+    const int err = step_commit(h, run, done);
+    if (!err && done == nsteps) return DSS_OK;
+    // a step did not commit (what was copied out is not the final state):
+    // finish as dss_step would, then read the state and the stress again
+    if (err) {
+      clear_err(h);
+      const int P = h->status_host->w[ST_NPAIRS];
+      if (err != DSS_ERR_CAPACITY || P <= h->pcap) return err;
+      r = alloc_pair_buffers(h, (int64_t)(P * 1.25) + 1024, true);
+      if (r) return r;
+    }
+    r = step_run(h, nsteps - done);
+    if (r) return r;
+    r = get_state_enqueue(h, dst);
+    if (r) return r;
+    if (sigma) CK(cudaMemcpyAsync(sigma, h->sigma, 9 * sizeof(double), cudaMemcpyDefault, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
     return DSS_OK;
   });
 }
@@ -1463,15 +1549,11 @@ int dss_get_history(dss_handle* h, int64_t* keys, double* xi, int64_t cap, int64
   return dss_get_history_rolling(h, keys, xi, nullptr, cap, count);
 }
 
-int dss_load_state(dss_handle* h, const double* x, const double* u, const double* w,
-                   const double* alpha_lin, const double* alpha_ang) {
-  return guard([&]() -> int {
-    if (!h || !x || !u || !w || !alpha_lin || !alpha_ang) return DSS_ERR_ARG;
-    if (!h->have_state) return DSS_ERR_STATE;
-    ENTER(h);
+// The five state vectors in (id order) into the committed buffer: enqueued,
+// not synchronised.
+int load_state_enqueue(dss_handle* h, const double* const in[5]) {
     const size_t b = sizeof(double) * 3 * (size_t)h->n;
     StateBuf& s = h->st[h->cur];
-    const double* in[5] = {x, u, w, alpha_lin, alpha_ang};
     // device and mapped pinned host buffers are read by one kernel; pageable
     // host buffers go through the staging area with the copy engine first
     Src5 src;
@@ -1489,6 +1571,16 @@ int dss_load_state(dss_handle* h, const double* x, const double* u, const double
     CK(cudaMemsetAsync(&h->status->w[ST_IDORDER], 1, sizeof(int), h->stream));
     CK(cudaGetLastError());
     return DSS_OK;
+}
+
+int dss_load_state(dss_handle* h, const double* x, const double* u, const double* w,
+                   const double* alpha_lin, const double* alpha_ang) {
+  return guard([&]() -> int {
+    if (!h || !x || !u || !w || !alpha_lin || !alpha_ang) return DSS_ERR_ARG;
+    if (!h->have_state) return DSS_ERR_STATE;
+    ENTER(h);
+    const double* const in[5] = {x, u, w, alpha_lin, alpha_ang};
+    return load_state_enqueue(h, in);
   });
 }
 

@@ -106,6 +106,21 @@ class Suspension:
                                                     (x, u, w, alpha_lin, alpha_ang)]),
                   "dss_get_state")
 
+    def step_io(self, state_in, nsteps: int, state_out=None, sigma=None):
+        """Upload (x, u, w, alpha_lin, alpha_ang) (id order), advance nsteps,
+        read the state after them into state_out (five buffers or None) and
+        the last stress into sigma (9 doubles or None), with one
+        synchronisation (dss_step_io).  Buffers are contiguous float64 torch
+        tensors on any device, or numpy arrays (outputs are written in
+        place, so they must be float64 and contiguous already)."""
+        ins = [_Arg(v, np.float64) for v in state_in]
+        outs = [_Arg(v, np.float64) for v in state_out] if state_out is not None else None
+        sg = _Arg(sigma, np.float64) if sigma is not None else None
+        pin = (c_void_p * 5)(*[g.ptr for g in ins])
+        pout = (c_void_p * 5)(*[g.ptr for g in outs]) if outs is not None else None
+        nat.check(self.lib.dss_step_io(self._h, pin, int(nsteps), pout, c_void_p(sg.ptr) if sg else None),
+                  "dss_step_io")
+
     def set_profiling(self, on: bool = True):
         nat.check(self.lib.dss_set_profiling(self._h, 1 if on else 0), "dss_set_profiling")
 
