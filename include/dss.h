@@ -202,6 +202,19 @@ int dss_set_state(dss_handle *h, const double *x, const double *a, const int32_t
 int dss_load_state(dss_handle *h, const double *x, const double *u, const double *w,
                    const double *alpha_lin, const double *alpha_ang);
 
+/* One step loop of a caller that keeps the state in its own memory: loads
+ * x, u, w, alpha_lin, alpha_ang (in[0..4], 3n each, id order, all required,
+ * as dss_load_state), advances nsteps steps (Eq. 15-16, as dss_step), writes
+ * the state after them to out[0..4] (id order; any entry may be NULL, as
+ * dss_get_state) and the last stress to sigma (9 values, or NULL; instance
+ * 0).  Host (pinned or pageable) or device pointers; in and out may be the
+ * same buffers.  The upload, the step graphs, the download and the stress
+ * read are issued back to back and the stream is synchronised once; a step
+ * that fails on the pair capacity is recovered as by dss_step.  Errors as
+ * dss_step. */
+int dss_step_io(dss_handle *h, const double *const in[5], int64_t nsteps, double *const out[5],
+                double sigma[9]);
+
 /* Copies the current state out in id order; any pointer may be NULL. */
 int dss_get_state(dss_handle *h, double *x, double *u, double *w, double *alpha_lin,
                   double *alpha_ang);
