@@ -347,11 +347,15 @@ int dss_autotune_kernels(dss_handle *h, int32_t trial_steps, double *ms_per_step
  * The forward keeps a checkpoint (dss_save) every ckpt_every steps; the
  * reverse sweep replays one segment at a time, taping each step, and walks it
  * backwards: memory is one segment of tapes plus the checkpoints.
- * Derivatives are pathwise: the pair set, contacts, Coulomb slips and the
- * taper ends of each step are those of the forward run and held fixed; with
- * the hard cutoff (lub_taper = 0) J has no pathwise dependence on delta_lub.
- * Single-instance handles without the wave of Eq. 17 or rolling resistance
- * only (DSS_ERR_ARG otherwise).  The handle is left
+ * Derivatives are pathwise: the pair set, contacts, Coulomb slips (of the
+ * sliding and, with k_r > 0, the rolling spring) and the taper ends of each
+ * step are those of the forward run and held fixed; with the hard cutoff
+ * (lub_taper = 0) J has no pathwise dependence on delta_lub.  The wavy shear
+ * flow of Eq. 17 (its y dependence in the ambient flow, the pair strain, the
+ * Faxen drag and the local stresslets) and rolling resistance (App. B; the
+ * rolling stretch carried like the sliding one; k_r itself is not among the
+ * parameters) are differentiated.  Single-instance handles only
+ * (DSS_ERR_ARG otherwise).  The handle is left
  * in the state after the rollout.  Output pointers are host or device
  * memory and may be NULL.  Synchronises the stream. */
 int dss_adjoint(dss_handle *h, int64_t nsteps, int32_t ckpt_every, const double *weights,

@@ -12,19 +12,24 @@
 //                  + dt/2 alpha^{n+1}), the Stokes-drag part of the VJP;
 //   k_adj_pairs    per pair: the vector-Jacobian product of the pair model
 //                  with respect to its 25 inputs (r, y_i, y_j, u_i, u_j, w_i,
-//                  w_j, the carried stretch, k_n, k_t, gamma_n, mu, delta_lub),
+//                  w_j, the carried stretch, k_n, k_t, gamma_n, mu, delta_lub;
+//                  with rolling resistance also the carried rolling stretch),
 //                  built from forward-mode derivative blocks of the shared
 //                  pair model (dss_pair_model.cuh) contracted with the
-//                  cotangents; the stretch adjoint is routed to the pair of the
-//                  previous step it came from;
+//                  cotangents; the stretch adjoints are routed to the pair of
+//                  the previous step they came from;
 //   k_adj_gather   per particle: own-row and partner contributions summed in
 //                  a fixed order (owner rows in list order, partner records by
 //                  increasing pair index), so gradients are bitwise
 //                  reproducible;
 //   k_adj_predict  per particle: the predictor of Eq. 15a-b backwards.
 //
-// Branch decisions (pair set, contact, Coulomb slip, gap clamp, taper ends,
-// box wraps) are those of the forward step and are held fixed.
+// With the wavy shear flow of Eq. 17 the ambient velocity and spin, the
+// pair's strain rate, the Faxen drag and the local single-particle
+// stresslets depend on y; with rolling resistance (App. B) the rolling
+// stretch is carried and differentiated like the sliding one.  Branch
+// decisions (pair set, contact, Coulomb slips, gap clamp, taper ends, box
+// wraps) are those of the forward step and are held fixed.
 #include <algorithm>
 #include <climits>
 #include <cstring>
@@ -35,19 +40,19 @@
 namespace {
 constexpr int kThreads = 128;
 constexpr int kAdjThreads = 128;
-constexpr int kNin = 25;          // pair-model inputs differentiated
+constexpr int kNin = 28;          // pair-model inputs differentiated (25 without rolling springs)
 constexpr int kDualK = 5;         // derivative directions per forward-mode pass
 
 struct PairIn {
   double r[3];
   double yi, yj;
-  double ui[3], uj[3], wi[3], wj[3], xo[3];
+  double ui[3], uj[3], wi[3], wj[3], xo[3], ro[3];
   double ai, aj;
   int sy;
 };
 
 struct PairCot {
-  double F[3], Ti[3], Tj[3], xi[3];
+  double F[3], Ti[3], Tj[3], xi[3], xr[3];
   double Ws[9];      // stress weights / volume
 };
 
@@ -75,6 +80,7 @@ __device__ __noinline__ void vjp_pass(const Geo& g, const InstGeo& I, const Pair
   const Vec3<D> wi = mk3<D>(seed<K>(in.wi[0], 11, base), seed<K>(in.wi[1], 12, base), seed<K>(in.wi[2], 13, base));
   const Vec3<D> wj = mk3<D>(seed<K>(in.wj[0], 14, base), seed<K>(in.wj[1], 15, base), seed<K>(in.wj[2], 16, base));
   const Vec3<D> xo = mk3<D>(seed<K>(in.xo[0], 17, base), seed<K>(in.xo[1], 18, base), seed<K>(in.xo[2], 19, base));
+  const Vec3<D> ro = mk3<D>(seed<K>(in.ro[0], 25, base), seed<K>(in.ro[1], 26, base), seed<K>(in.ro[2], 27, base));
   PairParams<D> q;
   q.kn = seed<K>(g.kn, 20, base);
   q.kt = seed<K>(g.kt, 21, base);
@@ -83,19 +89,29 @@ __device__ __noinline__ void vjp_pass(const Geo& g, const InstGeo& I, const Pair
   q.delta = seed<K>(g.delta, 24, base);
   const D rr = sqrt(dot(r, r));
   const double Om = -0.5 * I.gdot;
-  const Vec3<D> Vi = mk3<D>(ui.x - I.gdot * yi, ui.y, ui.z);
-  const Vec3<D> Vj = mk3<D>(uj.x - I.gdot * yj, uj.y, uj.z);
-  const Vec3<D> Wi = mk3<D>(wi.x, wi.y, wi.z - Om);
-  const Vec3<D> Wj = mk3<D>(wj.x, wj.y, wj.z - Om);
+  Vec3<D> Vi = mk3<D>(ui.x - I.gdot * yi, ui.y, ui.z);
+  Vec3<D> Vj = mk3<D>(uj.x - I.gdot * yj, uj.y, uj.z);
+  Vec3<D> Wi = mk3<D>(wi.x, wi.y, wi.z - Om);
+  Vec3<D> Wj = mk3<D>(wj.x, wj.y, wj.z - Om);
+  D rate = cst<D>(I.gdot);
+  if (g.wave) {
+    // Eq. 17 at each centre: U sin(k y) in U_inf,x, (U k cos(k y))/2 in -Omega_inf,z,
+    // the strain of the mean of the two local rates
+    const D ci = cos(I.wave_k * yi), cj = cos(I.wave_k * yj);
+    Vi.x = Vi.x - g.wave_amp * sin(I.wave_k * yi);
+    Vj.x = Vj.x - g.wave_amp * sin(I.wave_k * yj);
+    Wi.z = Wi.z + (0.5 * g.wave_amp * I.wave_k) * ci;
+    Wj.z = Wj.z + (0.5 * g.wave_amp * I.wave_k) * cj;
+    rate = rate + (0.5 * g.wave_amp * I.wave_k) * (ci + cj);
+  }
   const Vec3<D> du = mk3<D>(uj.x + in.sy * I.gdot * I.L[1] - ui.x, uj.y - ui.y, uj.z - ui.z);
-  // simple shear without rolling springs (dss_adjoint refuses the others)
-  const Vec3<D> ro = mk3<D>(cst<D>(0.0), cst<D>(0.0), cst<D>(0.0));
   const PairModelOut<D> o =
-      pair_model<D>(g, I, q, r, rr, in.ai, in.aj, Vi, Vj, Wi, Wj, du, wi, wj, xo, ro, I.gdot);
+      pair_model<D, true>(g, I, q, r, rr, in.ai, in.aj, Vi, Vj, Wi, Wj, du, wi, wj, xo, ro, rate);
   D v = c.F[0] * o.F.x + c.F[1] * o.F.y + c.F[2] * o.F.z;
   v = v + c.Ti[0] * o.Ti.x + c.Ti[1] * o.Ti.y + c.Ti[2] * o.Ti.z;
   v = v + c.Tj[0] * o.Tj.x + c.Tj[1] * o.Tj.y + c.Tj[2] * o.Tj.z;
   v = v + c.xi[0] * o.xi.x + c.xi[1] * o.xi.y + c.xi[2] * o.xi.z;
+  if (g.k_r > 0.0) v = v + c.xr[0] * o.xr.x + c.xr[1] * o.xr.y + c.xr[2] * o.xr.z;
   // Eq. 9: S = r (x) F^C + sym(r (x) F^L), weighted
   const D rv[3] = {r.x, r.y, r.z};
   const D fc[3] = {o.Fc.x, o.Fc.y, o.Fc.z};
@@ -137,7 +153,7 @@ k_adj_tape_pairs(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restric
     min_image(I, off, xi, yi, zi, s.x[j], s.x[n + j], s.x[2 * n + j], dx, dy, dz, sy);
     const double rr = exact_dist(dx, dy, dz);
     int pold = -1;
-    double xo[3] = {0.0, 0.0, 0.0};
+    double xo[3] = {0.0, 0.0, 0.0}, ro[3] = {0.0, 0.0, 0.0};
     if (!empty_history && __dsub_rn(rr, __dadd_rn(ai, s.a[j])) < 0.0) {
       const int idj = s.id[j];
       const int oi = H.slot_of_id[idi], oj = H.slot_of_id[idj];
@@ -156,12 +172,18 @@ k_adj_tape_pairs(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restric
         xo[0] = sgn * c[0];
         xo[1] = sgn * c[1];
         xo[2] = sgn * c[2];
+        if (t.xro) xi_components(H.xr[q], g.precision == DSS_MIXED, ro);   // orientation-free
       }
     }
     t.pold[p] = pold;
     t.xo[p] = xo[0];
     t.xo[g.pcap + p] = xo[1];
     t.xo[2 * g.pcap + p] = xo[2];
+    if (t.xro) {
+      t.xro[p] = ro[0];
+      t.xro[g.pcap + p] = ro[1];
+      t.xro[2 * g.pcap + p] = ro[2];
+    }
   }
 }
 
@@ -170,7 +192,8 @@ __global__ void __launch_bounds__(kThreads)
 k_adj_pre(Geo g, const InstGeo* __restrict__ ig, AdjTape t, const double* __restrict__ a_by_id,
           double* __restrict__ xb, double* __restrict__ ub, double* __restrict__ wb,
           const double* __restrict__ ab, const double* __restrict__ bb, double* __restrict__ Fb,
-          double* __restrict__ Tb, int* __restrict__ bw_n, int initial) {
+          double* __restrict__ Tb, int* __restrict__ bw_n, int initial, const double* __restrict__ Wn,
+          double inv_vol) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = g.n;
   if (s >= n) return;
@@ -197,7 +220,21 @@ k_adj_pre(Geo g, const InstGeo* __restrict__ ig, AdjTape t, const double* __rest
     ub[c * n + id] -= kd * F[c];
     wb[c * n + id] -= kr * T[c];
   }
-  xb[n + id] += kd * gd * F[0];
+  if (g.wave) {
+    // Eq. 17: dF_x/dy through the Faxen-corrected U_inf,x, dT_z/dy through
+    // Omega_inf,z, and the local single-particle stresslets (xy, yx) of the
+    // weighted stress
+    const InstGeo& I = ig[0];
+    const double k = I.wave_k, U = g.wave_amp, y = t.x[n + s];
+    double sn, cs;
+    sincos(k * y, &sn, &cs);
+    double yb = kd * (gd + U * (1.0 - a * a * I.faxen_c) * k * cs) * F[0];
+    yb += kr * 0.5 * U * k * k * sn * T[2];
+    if (Wn) yb -= (Wn[1] + Wn[3]) * inv_vol * (10.0 / 3.0) * DSS_PI * g.eta0 * a * a * a * U * k * k * sn;
+    xb[n + id] += yb;
+  } else {
+    xb[n + id] += kd * gd * F[0];
+  }
   bw_n[s] = 0;
 }
 
@@ -206,6 +243,7 @@ __global__ void __launch_bounds__(kAdjThreads)
 k_adj_pairs(Geo g, const InstGeo* __restrict__ ig, AdjTape t, const double* __restrict__ a_by_id, int P,
             const double* __restrict__ Fb, const double* __restrict__ Tb,
             const double* __restrict__ xib_cur, double* __restrict__ xib_prev,
+            const double* __restrict__ xrb_cur, double* __restrict__ xrb_prev,
             const double* __restrict__ Wn, double inv_vol, double* __restrict__ pout,
             int* __restrict__ bw_n, int* __restrict__ bw_p, double* __restrict__ thb_part,
             DevStatus* st) {
@@ -232,6 +270,7 @@ k_adj_pairs(Geo g, const InstGeo* __restrict__ ig, AdjTape t, const double* __re
       in.wi[c] = t.w[c * n + i];
       in.wj[c] = t.w[c * n + j];
       in.xo[c] = t.xo[c * g.pcap + p];
+      in.ro[c] = t.xro ? t.xro[c * g.pcap + p] : 0.0;
     }
     PairCot cot;
     const double sgn = idi < idj ? 1.0 : -1.0;
@@ -241,13 +280,15 @@ k_adj_pairs(Geo g, const InstGeo* __restrict__ ig, AdjTape t, const double* __re
       cot.Ti[c] = Tb[c * n + i];
       cot.Tj[c] = Tb[c * n + j];
       cot.xi[c] = sgn * xib_cur[c * g.pcap + p];   // stored lo -> hi, model i -> j
+      cot.xr[c] = xrb_cur ? xrb_cur[c * g.pcap + p] : 0.0;
     }
 #pragma unroll
     for (int q = 0; q < 9; ++q) cot.Ws[q] = Wn ? Wn[q] * inv_vol : 0.0;
     double out[kNin];
 #pragma unroll
     for (int k = 0; k < kNin; ++k) out[k] = 0.0;
-    for (int base = 0; base < kNin; base += K) vjp_pass<K>(g, I, in, cot, base, out);
+    const int nin = g.k_r > 0.0 ? kNin : 25;
+    for (int base = 0; base < nin; base += K) vjp_pass<K>(g, I, in, cot, base, out);
     double* po = pout + (int64_t)p * 18;
     // i side: x = -r_bar + y_i, u_i, w_i; j side: x = +r_bar + y_j, u_j, w_j
     po[0] = -out[0]; po[1] = -out[1] + out[3]; po[2] = -out[2];
@@ -260,6 +301,9 @@ k_adj_pairs(Geo g, const InstGeo* __restrict__ ig, AdjTape t, const double* __re
     if (q >= 0) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) xib_prev[c * g.pcap + q] = sgn * out[17 + c];
+      if (xrb_prev)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) xrb_prev[c * g.pcap + q] = out[25 + c];
     }
 #pragma unroll
     for (int c = 0; c < 5; ++c) th[c] = out[20 + c];
@@ -367,13 +411,14 @@ void adj_free(dss_handle* h) {
   for (int k = 0; k < A->slots; ++k) {
     AdjTape& t = A->tape[k];
     cudaFree(t.x); cudaFree(t.u); cudaFree(t.w); cudaFree(t.id); cudaFree(t.start);
-    cudaFree(t.op); cudaFree(t.pj); cudaFree(t.pold); cudaFree(t.xo); cudaFree(t.sg);
+    cudaFree(t.op); cudaFree(t.pj); cudaFree(t.pold); cudaFree(t.xo); cudaFree(t.xro); cudaFree(t.sg);
   }
   delete[] A->tape;
   if (A->P_host) cudaFreeHost(A->P_host);
   cudaFree(A->xb); cudaFree(A->ub); cudaFree(A->wb); cudaFree(A->ab); cudaFree(A->bb);
   cudaFree(A->Fb); cudaFree(A->Tb); cudaFree(A->pout); cudaFree(A->bw_n); cudaFree(A->bw_p);
-  cudaFree(A->xib[0]); cudaFree(A->xib[1]); cudaFree(A->thb_part); cudaFree(A->thb); cudaFree(A->J);
+  cudaFree(A->xib[0]); cudaFree(A->xib[1]); cudaFree(A->xrb[0]); cudaFree(A->xrb[1]);
+  cudaFree(A->thb_part); cudaFree(A->thb); cudaFree(A->J);
   cudaFree(A->W);
   delete A;
   h->adj = nullptr;
@@ -403,6 +448,7 @@ int adj_alloc(dss_handle* h, int slots, int64_t nsteps) {
         (r = adj_dalloc(h, &t.pj, pc)) || (r = adj_dalloc(h, &t.pold, pc)) ||
         (r = adj_dalloc(h, &t.xo, 3 * pc)) || (r = adj_dalloc(h, &t.sg, 1)))
       return r;
+    if (h->g.k_r > 0.0 && (r = adj_dalloc(h, &t.xro, 3 * pc))) return r;
   }
   if (cudaMallocHost((void**)&A->P_host, sizeof(int) * slots) != cudaSuccess) return DSS_ERR_CUDA;
   const int pb = (int)((pc + kAdjThreads - 1) / kAdjThreads);
@@ -414,6 +460,9 @@ int adj_alloc(dss_handle* h, int slots, int64_t nsteps) {
       (r = adj_dalloc(h, &A->xib[0], 3 * pc)) || (r = adj_dalloc(h, &A->xib[1], 3 * pc)) ||
       (r = adj_dalloc(h, &A->thb_part, 5 * (size_t)std::max(pb, 1))) || (r = adj_dalloc(h, &A->thb, 5)) ||
       (r = adj_dalloc(h, &A->J, 1)) || (r = adj_dalloc(h, &A->W, 9 * (size_t)std::max<int64_t>(nsteps, 1))))
+    return r;
+  if (h->g.k_r > 0.0 &&
+      ((r = adj_dalloc(h, &A->xrb[0], 3 * pc)) || (r = adj_dalloc(h, &A->xrb[1], 3 * pc))))
     return r;
   return DSS_OK;
 }
@@ -435,6 +484,8 @@ void adj_zero(dss_handle* h) {
   cudaMemsetAsync(A->bb, 0, b3, h->stream);
   cudaMemsetAsync(A->xib[0], 0, sizeof(double) * 3 * A->pcap, h->stream);
   cudaMemsetAsync(A->xib[1], 0, sizeof(double) * 3 * A->pcap, h->stream);
+  for (int k = 0; k < 2; ++k)
+    if (A->xrb[k]) cudaMemsetAsync(A->xrb[k], 0, sizeof(double) * 3 * A->pcap, h->stream);
   cudaMemsetAsync(A->thb, 0, sizeof(double) * 5, h->stream);
   cudaMemsetAsync(A->J, 0, sizeof(double), h->stream);
   A->cur = 0;
@@ -477,12 +528,16 @@ void adj_reverse(dss_handle* h, int slot, int64_t step, bool initial) {
   const double vol = I.L[0] * I.L[1] * I.L[2];
   double* xib_cur = A->xib[A->cur];
   double* xib_prev = A->xib[1 - A->cur];
+  double* xrb_cur = A->xrb[A->cur];
+  double* xrb_prev = A->xrb[1 - A->cur];
   cudaMemsetAsync(xib_prev, 0, sizeof(double) * 3 * A->pcap, h->stream);
+  if (xrb_prev) cudaMemsetAsync(xrb_prev, 0, sizeof(double) * 3 * A->pcap, h->stream);
+  const double* Wn = initial ? nullptr : A->W + 9 * step;
   k_adj_pre<<<nb, kThreads, 0, h->stream>>>(h->g, h->ig, t, h->a_by_id, A->xb, A->ub, A->wb, A->ab, A->bb,
-                                            A->Fb, A->Tb, A->bw_n, initial ? 1 : 0);
+                                            A->Fb, A->Tb, A->bw_n, initial ? 1 : 0, Wn, 1.0 / vol);
   const int pb = std::max((P + kAdjThreads - 1) / kAdjThreads, 1);
   k_adj_pairs<kDualK><<<pb, kAdjThreads, 0, h->stream>>>(
-      h->g, h->ig, t, h->a_by_id, P, A->Fb, A->Tb, xib_cur, xib_prev, initial ? nullptr : A->W + 9 * step,
+      h->g, h->ig, t, h->a_by_id, P, A->Fb, A->Tb, xib_cur, xib_prev, xrb_cur, xrb_prev, Wn,
       1.0 / vol, A->pout, A->bw_n, A->bw_p, A->thb_part, h->status);
   k_adj_theta<<<1, 32, 0, h->stream>>>(A->thb_part, pb, A->thb);
   k_adj_gather<<<nb, kThreads, 0, h->stream>>>(h->g, t, A->pout, A->bw_n, A->bw_p, A->xb, A->ub, A->wb);

@@ -1912,8 +1912,9 @@ int dss_adjoint(dss_handle* h, int64_t nsteps, int32_t ckpt_every, const double*
                 double* dJ_du0, double* dJ_dw0, double* dJ_dalpha0, double* dJ_dbeta0) {
   return guard([&]() -> int {
     if (!h || nsteps < 1 || ckpt_every < 1 || !weights) return DSS_ERR_ARG;
-    // single instance, simple shear, no rolling springs (the taped model)
-    if (h->K != 1 || h->g.wave || h->g.k_r > 0.0) return DSS_ERR_ARG;
+    // single instance (the simple shear or the wave of Eq. 17, with or
+    // without rolling springs)
+    if (h->K != 1) return DSS_ERR_ARG;
     if (!h->have_state) return DSS_ERR_STATE;
     ENTER(h);
     const int64_t nseg = (nsteps + ckpt_every - 1) / ckpt_every;

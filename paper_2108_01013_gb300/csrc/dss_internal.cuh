@@ -433,6 +433,7 @@ struct AdjTape {
   int* pj;          // pcap partner (sorted index)
   int* pold;        // pcap index of the pair in the previous step's list, -1 if none
   double* xo;       // 3*pcap stretch carried in (i -> j orientation), 0 if none
+  double* xro;      // 3*pcap rolling stretch carried in (k_r > 0; else null)
   StepGeo* sg;      // Lees-Edwards geometry of the step (instance 0)
 };
 
@@ -448,6 +449,7 @@ struct AdjBuf {
   int* bw_n;             // n partner records per particle
   int* bw_p;             // n*M pair indices of the partner records
   double* xib[2];        // 3*pcap stretch adjoints of the current / previous step's pairs
+  double* xrb[2];        // 3*pcap rolling-stretch adjoints (k_r > 0; else null)
   double* thb_part;      // 5 per pair block
   double* thb;           // 5: kn, kt, gamma_n, mu, delta_lub
   double* J;             // objective

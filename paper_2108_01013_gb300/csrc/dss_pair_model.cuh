@@ -166,6 +166,26 @@ __device__ __forceinline__ Dual<K> exp(const Dual<K>& a) {
   return r;
 }
 template <int K>
+__device__ __forceinline__ Dual<K> sin(const Dual<K>& a) {
+  Dual<K> r;
+  double sn, cs;
+  ::sincos(a.v, &sn, &cs);
+  r.v = sn;
+#pragma unroll
+  for (int k = 0; k < K; ++k) r.d[k] = cs * a.d[k];
+  return r;
+}
+template <int K>
+__device__ __forceinline__ Dual<K> cos(const Dual<K>& a) {
+  Dual<K> r;
+  double sn, cs;
+  ::sincos(a.v, &sn, &cs);
+  r.v = cs;
+#pragma unroll
+  for (int k = 0; k < K; ++k) r.d[k] = -sn * a.d[k];
+  return r;
+}
+template <int K>
 __device__ __forceinline__ Dual<K> fabs(const Dual<K>& a) {
   return a.v < 0.0 ? -a : a;
 }
@@ -229,7 +249,7 @@ __device__ __forceinline__ PairModelOut<T> pair_model(const Geo& g, const InstGe
                                                       const PairParams<T>& q, Vec3<T> r, T rr,
                                                       double ai, double aj, Vec3<T> Vi, Vec3<T> Vj,
                                                       Vec3<T> Wi, Vec3<T> Wj, Vec3<T> du, Vec3<T> wi,
-                                                      Vec3<T> wj, Vec3<T> xo, Vec3<T> ro, double rate) {
+                                                      Vec3<T> wj, Vec3<T> xo, Vec3<T> ro, T rate) {
   (void)I;
   PairModelOut<T> o;
   const T zero = cst<T>(0.0);

@@ -127,6 +127,45 @@ def test_adjoint_with_echem_matches_oracle(env):
     check_per_particle(r["w0"], o["w0"], 1e-8, what="dJ/dw0")
 
 
+@pytest.mark.parametrize("ext", [dict(wave_amp=4.0, wave_n=1), dict(k_r=1e3),
+                                 dict(wave_amp=4.0, wave_n=1, k_r=1e3)],
+                         ids=["wave", "rolling", "wave_rolling"])
+def test_adjoint_wave_and_rolling_match_oracle(env, ext):
+    """The wavy shear flow of Eq. 17 (ambient flow, pair strain, Faxen drag
+    and local stresslets depending on y) and rolling resistance (App. B, the
+    rolling stretch carried between steps) in the differentiated rollout:
+    FP64 gradients equal the FP64 autograd oracle."""
+    g, u0, w0, kw, th = _case(env, 0.3)
+    kw = dict(kw, **ext)
+    T = 12
+    W = _weights(T, kw["shear_rate"])
+    o = env["oadj"].gradients(g["box"], g["x"], g["a"], u0, w0, T, W, **th, **kw, nstep0=3)
+    r, st = _gpu(env, g, u0, w0, kw, th, T, W)
+    assert r["J"] == pytest.approx(o["J"], rel=1e-11)
+    check_scalars(r["params"], o["params"], 1e-8, floor=1e-6, what="dJ/dtheta")
+    check_per_particle(r["x0"], o["x0"], 1e-8, what="dJ/dx0")
+    check_per_particle(r["u0"], o["u0"], 1e-8, what="dJ/du0")
+    check_per_particle(r["w0"], o["w0"], 1e-8, what="dJ/dw0")
+    box = g["box"]
+    d = np.abs(st["x"].cpu().numpy() - o["final"]["x"])
+    d = np.minimum(d, box[:, None] - d)
+    assert d.max() < 1e-12
+
+
+def test_adjoint_wave_rolling_mixed_vs_oracle(env):
+    """Mixed-precision forward (FP64 reverse) with the wave and rolling."""
+    g, u0, w0, kw, th = _case(env, 0.3)
+    kw = dict(kw, wave_amp=4.0, wave_n=1, k_r=1e3)
+    T = 12
+    W = _weights(T, kw["shear_rate"])
+    o = env["oadj"].gradients(g["box"], g["x"], g["a"], u0, w0, T, W, **th, **kw, nstep0=3)
+    r, _ = _gpu(env, g, u0, w0, kw, th, T, W, precision="mixed")
+    assert r["J"] == pytest.approx(o["J"], rel=1e-6)
+    for k in range(5):
+        assert r["params"][k] == pytest.approx(o["params"][k], rel=1e-4, abs=1e-9 * abs(o["J"]))
+    check_per_particle(r["x0"], o["x0"], 1e-4, floor=0.1, what="dJ/dx0 (mixed)")
+
+
 def test_autograd_function_and_tied_parameters(env):
     torch = env["torch"]
     dss = env["dss"]

@@ -189,3 +189,15 @@ def test_batch_rejects_bad_layouts(env):
     with pytest.raises(dss.DssError) as e:
         dss.Batch(x2, a, [m["n"] for m in ms], boxes, [1.0, 2.0], p)
     assert e.value.code == -1
+
+
+def test_adjoint_refuses_batched_handles(env):
+    """The reverse sweep tapes one instance: a batch is refused (DSS_ERR_ARG)
+    and left usable."""
+    ms = _members(env, MEMBERS[:2])
+    b = _batch(env, ms, dt=1e-3)
+    with pytest.raises(RuntimeError, match="DSS_ERR_ARG"):
+        b.adjoint(2, np.zeros((2, 9)))
+    b.step(2)
+    assert b.counters()["steps_done"] == 2
+    b.close()

@@ -213,16 +213,6 @@ def test_batched_instances_take_their_own_wave_number(env):
     b.close()
 
 
-def test_adjoint_refuses_the_wave_and_rolling(env):
-    g, dss = env["g"], env["dss"]
-    for model in ("wave", "rolling"):
-        kw = _kw(model)
-        s = dss.Suspension(g["x"], g["a"], g["box"], dss.default_params(g["box"], **kw), ids=g["ids"])
-        with pytest.raises(RuntimeError, match="DSS_ERR_ARG"):
-            s.adjoint(2, np.zeros((2, 9)))
-        s.close()
-
-
 @pytest.fixture(scope="module")
 def table5(env):
     oracle, synth = env["oracle"], env["synth"]
