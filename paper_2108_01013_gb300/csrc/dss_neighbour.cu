@@ -94,15 +94,18 @@ __device__ __forceinline__ void enum_init(EnumCtx& e, const Geo& g, const InstGe
 template <bool ECH, bool SPLIT>
 __device__ __forceinline__ void take_candidate(EnumCtx& e, float4 pj, int j, float px, float py, float pz) {
   const float dx = pj.x - px, dy = pj.y - py, dz = pj.z - pz;
+  float sv = fmaf(pj.w, e.sc, e.sa);
+  if (ECH) sv = fmaxf(sv, pj.w + e.sa2);
+  const float t = fmaf(-sv, sv, fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
+  // nearly every candidate lies beyond the cutoff by more than the margin:
+  // one test and out (the half-box image test only on boxes narrower than
+  // the stencil)
+  if (t > e.m2 && !e.img) return;
   int dec;
-  if (e.img && (fabsf(dx) > e.hx || fabsf(dy) > e.hy || fabsf(dz) > e.hz)) {
+  if (e.img && (fabsf(dx) > e.hx || fabsf(dy) > e.hy || fabsf(dz) > e.hz))
     dec = -1;
-  } else {
-    float sv = fmaf(pj.w, e.sc, e.sa);
-    if (ECH) sv = fmaxf(sv, pj.w + e.sa2);
-    const float t = fmaf(-sv, sv, fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
+  else
     dec = t < -e.m2 ? 1 : (t > e.m2 ? 0 : -1);
-  }
   if (dec < 0) {
     ++e.band;
     const StateBuf& s = *e.s;
