@@ -14,10 +14,10 @@
 //                  with respect to its 25 inputs (r, y_i, y_j, u_i, u_j, w_i,
 //                  w_j, the carried stretch, k_n, k_t, gamma_n, mu, delta_lub;
 //                  with rolling resistance also the carried rolling stretch),
-//                  built from forward-mode derivative blocks of the shared
-//                  pair model (dss_pair_model.cuh) contracted with the
-//                  cotangents; the stretch adjoints are routed to the pair of
-//                  the previous step they came from;
+//                  the reverse of the pair model of dss_pair_model.cuh written
+//                  out by hand (pair_vjp) and contracted with the cotangents;
+//                  the stretch adjoints are routed to the pair of the previous
+//                  step they came from;
 //   k_adj_gather   per particle: own-row and partner contributions summed in
 //                  a fixed order (owner rows in list order, partner records by
 //                  increasing pair index), so gradients are bitwise
@@ -40,8 +40,7 @@
 namespace {
 constexpr int kThreads = 128;
 constexpr int kAdjThreads = 128;
-constexpr int kNin = 28;          // pair-model inputs differentiated (25 without rolling springs)
-constexpr int kDualK = 5;         // derivative directions per forward-mode pass
+constexpr int kNin = 28;          // pair-model inputs differentiated
 
 struct PairIn {
   double r[3];
@@ -56,76 +55,337 @@ struct PairCot {
   double Ws[9];      // stress weights / volume
 };
 
-template <int K>
-__device__ __forceinline__ Dual<K> seed(double v, int idx, int base) {
-  Dual<K> d = dual_const<K>(v);
-  const int k = idx - base;
-#pragma unroll
-  for (int q = 0; q < K; ++q)
-    if (q == k) d.d[q] = 1.0;
-  return d;
+// The vector-Jacobian product of one pair, written out by hand: one forward sweep
+// through the pair model of dss_pair_model.cuh (Eq. 4-5, App. A, Eq. 6-7,
+// App. B, Eq. 17) keeping its intermediates, then one backward sweep that
+// applies the chain rule operation by operation in reverse order.  Branches
+// (contact, Coulomb slips, gap clamp, taper ends, the electro-chemical and
+// lubrication ranges) are those of the values.  About three forward
+// evaluations of work (forward-mode derivative passes over the 28 inputs
+// took thirty, on GB300's narrow FP64 pipe).
+using V3d = Vec3<double>;
+__device__ __forceinline__ V3d operator-(const V3d& a) { return mk3<double>(-a.x, -a.y, -a.z); }
+__device__ __forceinline__ V3d operator*(const V3d& a, double s) { return mk3<double>(s * a.x, s * a.y, s * a.z); }
+__device__ __forceinline__ void acc3(V3d& a, const V3d& b) { a = a + b; }
+// d/dn and d/dv of c . tang(n, v) = c . (v - (n.v) n)
+__device__ __forceinline__ void tang_rev(const V3d& n, const V3d& v, const V3d& cb, V3d& nb, V3d& vb) {
+  const double nc = dot(n, cb), nv = dot(n, v);
+  acc3(vb, cb - n * nc);
+  acc3(nb, -(cb * nv + v * nc));
+}
+// d/da and d/db of c . (a x b)
+__device__ __forceinline__ void cross_rev(const V3d& a, const V3d& b, const V3d& cb, V3d& ab, V3d& bb) {
+  acc3(ab, cross(b, cb));
+  acc3(bb, cross(cb, a));
+}
+// a Coulomb rescale x = (cap / |x0|) x0 when |x0| > cap: adjoints of x0 and cap
+__device__ __forceinline__ void cap_rev(const V3d& x0, double cap, bool slip, const V3d& xb, V3d& x0b,
+                                        double& capb) {
+  if (!slip) {
+    acc3(x0b, xb);
+    return;
+  }
+  const double xm = ::sqrt(dot(x0, x0)), f = cap / xm, xx = dot(xb, x0);
+  acc3(x0b, xb * f - x0 * (cap * xx / (xm * xm * xm)));
+  capb += xx / xm;
 }
 
-// One forward-mode pass over inputs [base, base + K): writes the input
-// adjoints of those inputs (the contraction of the outputs' derivatives with
-// the cotangents).
-template <int K>
-__device__ __noinline__ void vjp_pass(const Geo& g, const InstGeo& I, const PairIn& in,
-                                      const PairCot& c, int base, double* out) {
-  using D = Dual<K>;
-  const Vec3<D> r = mk3<D>(seed<K>(in.r[0], 0, base), seed<K>(in.r[1], 1, base), seed<K>(in.r[2], 2, base));
-  const D yi = seed<K>(in.yi, 3, base), yj = seed<K>(in.yj, 4, base);
-  const Vec3<D> ui = mk3<D>(seed<K>(in.ui[0], 5, base), seed<K>(in.ui[1], 6, base), seed<K>(in.ui[2], 7, base));
-  const Vec3<D> uj = mk3<D>(seed<K>(in.uj[0], 8, base), seed<K>(in.uj[1], 9, base), seed<K>(in.uj[2], 10, base));
-  const Vec3<D> wi = mk3<D>(seed<K>(in.wi[0], 11, base), seed<K>(in.wi[1], 12, base), seed<K>(in.wi[2], 13, base));
-  const Vec3<D> wj = mk3<D>(seed<K>(in.wj[0], 14, base), seed<K>(in.wj[1], 15, base), seed<K>(in.wj[2], 16, base));
-  const Vec3<D> xo = mk3<D>(seed<K>(in.xo[0], 17, base), seed<K>(in.xo[1], 18, base), seed<K>(in.xo[2], 19, base));
-  const Vec3<D> ro = mk3<D>(seed<K>(in.ro[0], 25, base), seed<K>(in.ro[1], 26, base), seed<K>(in.ro[2], 27, base));
-  PairParams<D> q;
-  q.kn = seed<K>(g.kn, 20, base);
-  q.kt = seed<K>(g.kt, 21, base);
-  q.gn = seed<K>(I.gn, 22, base);
-  q.mu = seed<K>(g.mu, 23, base);
-  q.delta = seed<K>(g.delta, 24, base);
-  const D rr = sqrt(dot(r, r));
-  const double Om = -0.5 * I.gdot;
-  Vec3<D> Vi = mk3<D>(ui.x - I.gdot * yi, ui.y, ui.z);
-  Vec3<D> Vj = mk3<D>(uj.x - I.gdot * yj, uj.y, uj.z);
-  Vec3<D> Wi = mk3<D>(wi.x, wi.y, wi.z - Om);
-  Vec3<D> Wj = mk3<D>(wj.x, wj.y, wj.z - Om);
-  D rate = cst<D>(I.gdot);
+__device__ __noinline__ void pair_vjp(const Geo& g, const InstGeo& I, const PairIn& in, const PairCot& c,
+                                      double* out) {
+  const V3d zero = mk3<double>(0.0, 0.0, 0.0);
+  const double ai = in.ai, aj = in.aj, S = ai + aj;
+  const double gd = I.gdot, kn = g.kn, kt = g.kt, gn = I.gn, mu = g.mu, delta = g.delta;
+  // ---- forward sweep
+  const V3d r = mk3<double>(in.r[0], in.r[1], in.r[2]);
+  const double rr = ::sqrt(dot(r, r));
+  const double ir = 1.0 / rr;
+  const V3d n = r * ir;
+  const double d = rr - S;
+  const V3d ui = mk3<double>(in.ui[0], in.ui[1], in.ui[2]), uj = mk3<double>(in.uj[0], in.uj[1], in.uj[2]);
+  const V3d wi = mk3<double>(in.wi[0], in.wi[1], in.wi[2]), wj = mk3<double>(in.wj[0], in.wj[1], in.wj[2]);
+  V3d Vi = mk3<double>(ui.x - gd * in.yi, ui.y, ui.z), Vj = mk3<double>(uj.x - gd * in.yj, uj.y, uj.z);
+  V3d Wi = mk3<double>(wi.x, wi.y, wi.z + 0.5 * gd), Wj = mk3<double>(wj.x, wj.y, wj.z + 0.5 * gd);
+  double rate = gd, si = 0.0, sj = 0.0, ci = 0.0, cj = 0.0;
+  const double U = g.wave_amp, kw = I.wave_k;
   if (g.wave) {
-    // Eq. 17 at each centre: U sin(k y) in U_inf,x, (U k cos(k y))/2 in -Omega_inf,z,
-    // the strain of the mean of the two local rates
-    const D ci = cos(I.wave_k * yi), cj = cos(I.wave_k * yj);
-    Vi.x = Vi.x - g.wave_amp * sin(I.wave_k * yi);
-    Vj.x = Vj.x - g.wave_amp * sin(I.wave_k * yj);
-    Wi.z = Wi.z + (0.5 * g.wave_amp * I.wave_k) * ci;
-    Wj.z = Wj.z + (0.5 * g.wave_amp * I.wave_k) * cj;
-    rate = rate + (0.5 * g.wave_amp * I.wave_k) * (ci + cj);
+    sincos(kw * in.yi, &si, &ci);
+    sincos(kw * in.yj, &sj, &cj);
+    Vi.x -= U * si;
+    Vj.x -= U * sj;
+    Wi.z += 0.5 * U * kw * ci;
+    Wj.z += 0.5 * U * kw * cj;
+    rate += 0.5 * U * kw * (ci + cj);
   }
-  const Vec3<D> du = mk3<D>(uj.x + in.sy * I.gdot * I.L[1] - ui.x, uj.y - ui.y, uj.z - ui.z);
-  const PairModelOut<D> o =
-      pair_model<D, true>(g, I, q, r, rr, in.ai, in.aj, Vi, Vj, Wi, Wj, du, wi, wj, xo, ro, rate);
-  D v = c.F[0] * o.F.x + c.F[1] * o.F.y + c.F[2] * o.F.z;
-  v = v + c.Ti[0] * o.Ti.x + c.Ti[1] * o.Ti.y + c.Ti[2] * o.Ti.z;
-  v = v + c.Tj[0] * o.Tj.x + c.Tj[1] * o.Tj.y + c.Tj[2] * o.Tj.z;
-  v = v + c.xi[0] * o.xi.x + c.xi[1] * o.xi.y + c.xi[2] * o.xi.z;
-  if (g.k_r > 0.0) v = v + c.xr[0] * o.xr.x + c.xr[1] * o.xr.y + c.xr[2] * o.xr.z;
-  // Eq. 9: S = r (x) F^C + sym(r (x) F^L), weighted
-  const D rv[3] = {r.x, r.y, r.z};
-  const D fc[3] = {o.Fc.x, o.Fc.y, o.Fc.z};
-  const D fl[3] = {o.Fl.x, o.Fl.y, o.Fl.z};
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      const double wab = c.Ws[3 * a + b];
-      if (wab != 0.0) v = v + wab * (rv[a] * fc[b] + 0.5 * (rv[a] * fl[b] + rv[b] * fl[a]));
+  const V3d du = mk3<double>(uj.x + in.sy * gd * I.L[1] - ui.x, uj.y - ui.y, uj.z - ui.z);
+  const V3d xo = mk3<double>(in.xo[0], in.xo[1], in.xo[2]), ro = mk3<double>(in.ro[0], in.ro[1], in.ro[2]);
+  // contact
+  const bool contact = d < 0.0;
+  double fn = 0.0, cap = 0.0, capr = 0.0;
+  bool slip = false, rslip = false;
+  V3d aw = zero, rel = zero, xs0 = zero, xs = zero, Ft = zero, Fc = zero, nxf = zero, wr = zero, xr0 = zero,
+      xr = zero;
+  const double abar = 2.0 * ai * aj / (ai + aj);
+  const bool rolling = contact && g.k_r > 0.0;
+  if (contact) {
+    fn = kn * d + gn * dot(n, du);
+    aw = wi * ai + wj * aj;
+    rel = du - cross(aw, n);
+    xs0 = tang(n, xo) + g.dt * tang(n, rel);
+    cap = mu * fabs(fn) / kt;
+    const double xm = ::sqrt(dot(xs0, xs0));
+    slip = xm > cap;
+    xs = slip ? xs0 * (cap / xm) : xs0;
+    Ft = xs * kt;
+    Fc = n * fn + Ft;
+    nxf = cross(n, Ft);
+    if (rolling) {
+      wr = wi - wj;
+      xr0 = tang(n, ro) + cross(n, wr) * (g.dt * abar);
+      capr = mu * fabs(fn) / g.k_r;
+      const double xrm = ::sqrt(dot(xr0, xr0));
+      rslip = xrm > capr;
+      xr = rslip ? xr0 * (capr / xrm) : xr0;
     }
-#pragma unroll
-  for (int k = 0; k < K; ++k)
-    if (base + k < kNin) out[base + k] = v.d[k];
+  }
+  // electro-chemical forces and the lubrication range
+  bool lub_on = true;
+  double m = 0.0, mp = 0.0;   // m(d) and dm/dd
+  if (g.de > 0.0) {
+    if (g.f_er > 0.0 && d < 20.0 * g.lambda_d) {
+      const double A = g.f_er * (abar / g.a0);
+      if (d >= 0.0) {
+        const double ex = ::exp(-d / g.lambda_d);
+        m -= A * ex;
+        mp += A * ex / g.lambda_d;
+      } else {
+        m -= A;
+      }
+    }
+    if (g.hamaker > 0.0 && d < 4.0 * g.a0) {
+      const double eps = g.vdw_eps * abar, dp = d >= 0.0 ? d : 0.0;
+      const double den = 12.0 * (dp * dp + eps * eps);
+      m += (g.hamaker * abar) / den;
+      if (d >= 0.0) mp -= (g.hamaker * abar) * 24.0 * dp / (den * den);
+    }
+    Fc = Fc + n * m;
+    const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(r.x, r.x), __dmul_rn(r.y, r.y)), __dmul_rn(r.z, r.z));
+    const double dl = g.mode == 1 ? __dmul_rn(delta, g.a0) : __dmul_rn(__dmul_rn(delta, S), 0.5);
+    const double sl = __dadd_rn(S, dl);
+    lub_on = r2 < __dmul_rn(sl, sl);
+  }
+  // lubrication
+  const double A = ai, B = aj, AB = A * B;
+  const double iS = 1.0 / S, iS2 = iS * iS, iS3 = iS2 * iS;
+  const double cxa = 2.0 * AB * AB * iS3;
+  const double cya = (4.0 / 15.0) * AB * (2.0 * A * A + AB + 2.0 * B * B) * iS3;
+  const double cybi = -(2.0 / 15.0) * A * AB * (4.0 * A + B) * iS2;
+  const double cybj = -(2.0 / 15.0) * AB * B * (A + 4.0 * B) * iS2;
+  const double cyci = (8.0 / 15.0) * A * A * AB * iS;
+  const double cycj = (8.0 / 15.0) * AB * B * B * iS;
+  const double cycx = (2.0 / 15.0) * AB * AB * iS;
+  const double cxg = 2.0 * AB * AB * iS2;
+  const double cyg = (1.0 / 15.0) * AB * (4.0 - 6.0 * AB * iS2);
+  const double cyhi = iS2 * ((2.0 / 15.0) * A * A * AB * (2.0 * A - B) + (1.0 / 15.0) * AB * AB * (7.0 * A + B));
+  const double cyhj = iS2 * ((1.0 / 15.0) * AB * AB * (A + 7.0 * B) + (2.0 / 15.0) * AB * B * B * (2.0 * B - A));
+  double X = 0.0, Y = 0.0, dd = 1.0, sw = 1.0, tt = 2.0, dl = 0.0;
+  bool clamped = false, tapered = false;
+  V3d dV = zero, twoEn = zero, Qn = zero, nperp = zero, tWi = zero, tWj = zero, ndV = zero;
+  V3d Fl0 = zero, Tli0 = zero, Tlj0 = zero;
+  double nV = 0.0, P = 0.0;
+  if (lub_on) {
+    double ds = 2.0 * d / S;
+    clamped = !(ds >= 0.0);
+    if (clamped) ds = 0.0;
+    dd = ds + g.eps;
+    X = 1.0 / dd;
+    Y = -::log(dd);
+    dV = Vi - Vj;
+    nV = dot(n, dV);
+    const V3d fr = n * (X * cxa * nV) + tang(n, dV) * (Y * cya) + cross(n, Wi) * (Y * cybi) +
+                   cross(n, Wj) * (Y * cybj);
+    twoEn = mk3<double>(rate * n.y, rate * n.x, 0.0);
+    P = rate * n.x * n.y;
+    Qn = twoEn - n * (2.0 * P);
+    nperp = cross(n, twoEn);
+    const V3d fe = n * (X * cxg * P) + Qn * (Y * cyg);
+    Fl0 = (fe - fr) * g.k6;
+    ndV = cross(n, dV);
+    tWi = tang(n, Wi);
+    tWj = tang(n, Wj);
+    Tli0 = (ndV * (Y * cybi) - (tWi * (Y * cyci) + tWj * (Y * cycx)) + nperp * (Y * cyhi)) * g.k6;
+    Tlj0 = (ndV * (Y * cybj) - (tWi * (Y * cycx) + tWj * (Y * cycj)) + nperp * (Y * cyhj)) * g.k6;
+    if (g.taper > 0.0) {
+      dl = g.mode == 1 ? delta * g.a0 : delta * (0.5 * S);
+      tt = (dl - d) / (g.taper * dl);
+      if (tt < 1.0) {
+        tapered = true;
+        sw = tt > 0.0 ? tt * tt * (3.0 - 2.0 * tt) : 0.0;
+      }
+    }
+  }
+  const V3d Fl = Fl0 * sw;
+  // ---- backward sweep
+  const V3d cF = mk3<double>(c.F[0], c.F[1], c.F[2]);
+  const V3d cTi = mk3<double>(c.Ti[0], c.Ti[1], c.Ti[2]), cTj = mk3<double>(c.Tj[0], c.Tj[1], c.Tj[2]);
+  // stress of Eq. 9, weighted: sum_ab W_ab (r_a Fc_b + (r_a Fl_b + r_b Fl_a) / 2)
+  const double* W = c.Ws;
+  const V3d Wr = mk3<double>(W[0] * r.x + W[1] * r.y + W[2] * r.z, W[3] * r.x + W[4] * r.y + W[5] * r.z,
+                             W[6] * r.x + W[7] * r.y + W[8] * r.z);
+  const V3d WTr = mk3<double>(W[0] * r.x + W[3] * r.y + W[6] * r.z, W[1] * r.x + W[4] * r.y + W[7] * r.z,
+                              W[2] * r.x + W[5] * r.y + W[8] * r.z);
+  const V3d WFc = mk3<double>(W[0] * Fc.x + W[1] * Fc.y + W[2] * Fc.z, W[3] * Fc.x + W[4] * Fc.y + W[5] * Fc.z,
+                              W[6] * Fc.x + W[7] * Fc.y + W[8] * Fc.z);
+  const V3d WFl = mk3<double>(W[0] * Fl.x + W[1] * Fl.y + W[2] * Fl.z, W[3] * Fl.x + W[4] * Fl.y + W[5] * Fl.z,
+                              W[6] * Fl.x + W[7] * Fl.y + W[8] * Fl.z);
+  const V3d WTFl = mk3<double>(W[0] * Fl.x + W[3] * Fl.y + W[6] * Fl.z, W[1] * Fl.x + W[4] * Fl.y + W[7] * Fl.z,
+                               W[2] * Fl.x + W[5] * Fl.y + W[8] * Fl.z);
+  V3d rb = WFc + (WFl + WTFl) * 0.5;
+  const V3d Fcb = cF + WTr;
+  const V3d Flb = cF + (WTr + Wr) * 0.5;
+  V3d nb = zero, Vib = zero, Vjb = zero, Wib = zero, Wjb = zero, dub = zero, wib = zero, wjb = zero;
+  V3d xob = zero, rob = zero;
+  double db = 0.0, rateb = 0.0, knb = 0.0, ktb = 0.0, gnb = 0.0, mub = 0.0, deltab = 0.0;
+  // lubrication
+  if (lub_on) {
+    V3d Fl0b = Flb * sw, Tli0b = cTi * sw, Tlj0b = cTj * sw;
+    if (tapered && tt > 0.0) {
+      const double swb = dot(Flb, Fl0) + dot(cTi, Tli0) + dot(cTj, Tlj0);
+      const double ttb = swb * 6.0 * tt * (1.0 - tt);
+      // tt = (dl - d) / (w dl)
+      db += -ttb / (g.taper * dl);
+      const double dlb = ttb * d / (g.taper * dl * dl);
+      deltab += dlb * (g.mode == 1 ? g.a0 : 0.5 * S);
+    }
+    const V3d feb = Fl0b * g.k6, frb = Fl0b * (-g.k6);
+    const V3d Ab = Tli0b * g.k6, Bb = Tlj0b * g.k6;
+    // torques
+    double Yb = 0.0, Xb = 0.0;
+    Yb += dot(Ab, ndV) * cybi + dot(Bb, ndV) * cybj;
+    const V3d ndVb = Ab * (Y * cybi) + Bb * (Y * cybj);
+    Yb += -dot(Ab, tWi) * cyci - dot(Bb, tWj) * cycj - (dot(Ab, tWj) + dot(Bb, tWi)) * cycx;
+    const V3d tWib = -(Ab * (Y * cyci) + Bb * (Y * cycx));
+    const V3d tWjb = -(Ab * (Y * cycx) + Bb * (Y * cycj));
+    Yb += dot(Ab, nperp) * cyhi + dot(Bb, nperp) * cyhj;
+    V3d nperpb = Ab * (Y * cyhi) + Bb * (Y * cyhj);
+    // fe = (X cxg P) n + (Y cyg) Qn
+    double Pb = 0.0;
+    Xb += dot(feb, n) * cxg * P;
+    Pb += dot(feb, n) * X * cxg;
+    acc3(nb, feb * (X * cxg * P));
+    Yb += dot(feb, Qn) * cyg;
+    const V3d Qnb = feb * (Y * cyg);
+    // Qn = twoEn - 2 P n
+    V3d twoEnb = Qnb;
+    Pb += -2.0 * dot(Qnb, n);
+    acc3(nb, Qnb * (-2.0 * P));
+    // nperp = n x twoEn
+    cross_rev(n, twoEn, nperpb, nb, twoEnb);
+    // P = rate n_x n_y; twoEn = rate (n_y, n_x, 0)
+    rateb += Pb * n.x * n.y + twoEnb.x * n.y + twoEnb.y * n.x;
+    nb.x += Pb * rate * n.y + rate * twoEnb.y;
+    nb.y += Pb * rate * n.x + rate * twoEnb.x;
+    // tang(n, Wi), tang(n, Wj); ndV = n x dV
+    tang_rev(n, Wi, tWib, nb, Wib);
+    tang_rev(n, Wj, tWjb, nb, Wjb);
+    V3d dVb = zero;
+    cross_rev(n, dV, ndVb, nb, dVb);
+    // fr = (X cxa nV) n + (Y cya) tang(n, dV) + (Y cybi) n x Wi + (Y cybj) n x Wj
+    double nVb = 0.0;
+    Xb += dot(frb, n) * cxa * nV;
+    nVb += dot(frb, n) * X * cxa;
+    acc3(nb, frb * (X * cxa * nV));
+    Yb += dot(frb, tang(n, dV)) * cya;
+    tang_rev(n, dV, frb * (Y * cya), nb, dVb);
+    Yb += dot(frb, cross(n, Wi)) * cybi + dot(frb, cross(n, Wj)) * cybj;
+    cross_rev(n, Wi, frb * (Y * cybi), nb, Wib);
+    cross_rev(n, Wj, frb * (Y * cybj), nb, Wjb);
+    // nV = n . dV; dV = Vi - Vj
+    acc3(nb, dV * nVb);
+    acc3(dVb, n * nVb);
+    acc3(Vib, dVb);
+    acc3(Vjb, -dVb);
+    // X = 1 / dd, Y = -log dd, dd = ds + eps, ds = 2 d / S unless clamped
+    const double ddb = -Xb * X * X - Yb / dd;
+    if (!clamped) db += ddb * 2.0 / S;
+  }
+  // electro-chemical central force m(d) n
+  if (g.de > 0.0) {
+    const double mb = dot(Fcb, n);
+    acc3(nb, Fcb * m);
+    db += mb * mp;
+  }
+  // contact
+  if (contact) {
+    V3d nxfb = cTi * ai + cTj * aj;
+    double fnb = dot(Fcb, n);
+    acc3(nb, Fcb * fn);
+    V3d Ftb = Fcb;
+    if (rolling) {
+      // Tr = abar k_r (n x xr), added to T_i and taken from T_j
+      const V3d Trb = cTi - cTj;
+      V3d qb = zero;   // adjoint of q = abar k_r xr
+      cross_rev(n, xr * (abar * g.k_r), Trb, nb, qb);
+      const V3d xrb = mk3<double>(c.xr[0], c.xr[1], c.xr[2]) + qb * (abar * g.k_r);
+      V3d xr0b = zero;
+      double caprb = 0.0;
+      cap_rev(xr0, capr, rslip, xrb, xr0b, caprb);
+      mub += caprb * fabs(fn) / g.k_r;
+      fnb += caprb * mu * (fn >= 0.0 ? 1.0 : -1.0) / g.k_r;
+      // xr0 = tang(n, ro) + (dt abar) n x wr
+      tang_rev(n, ro, xr0b, nb, rob);
+      V3d wrb = zero;
+      cross_rev(n, wr, xr0b * (g.dt * abar), nb, wrb);
+      acc3(wib, wrb);
+      acc3(wjb, -wrb);
+    }
+    // nxf = n x Ft
+    cross_rev(n, Ft, nxfb, nb, Ftb);
+    // Ft = kt xs
+    ktb += dot(Ftb, xs);
+    const V3d xsb = Ftb * kt + mk3<double>(c.xi[0], c.xi[1], c.xi[2]);
+    V3d xs0b = zero;
+    double capb = 0.0;
+    cap_rev(xs0, cap, slip, xsb, xs0b, capb);
+    // cap = mu |fn| / kt
+    mub += capb * fabs(fn) / kt;
+    fnb += capb * mu * (fn >= 0.0 ? 1.0 : -1.0) / kt;
+    ktb += -capb * mu * fabs(fn) / (kt * kt);
+    // xs0 = tang(n, xo) + dt tang(n, rel)
+    tang_rev(n, xo, xs0b, nb, xob);
+    V3d relb = zero;
+    tang_rev(n, rel, xs0b * g.dt, nb, relb);
+    // rel = du - aw x n, aw = ai wi + aj wj
+    acc3(dub, relb);
+    V3d awb = zero;
+    cross_rev(aw, n, -relb, awb, nb);
+    acc3(wib, awb * ai);
+    acc3(wjb, awb * aj);
+    // fn = kn d + gn n.du
+    knb += fnb * d;
+    db += fnb * kn;
+    gnb += fnb * dot(n, du);
+    acc3(nb, du * (fnb * gn));
+    acc3(dub, n * (fnb * gn));
+  }
+  // geometry: n = r / |r|, d = |r| - S
+  acc3(rb, nb * ir - n * (dot(nb, n) * ir) + n * db);
+  // inputs
+  double yib = -gd * Vib.x, yjb = -gd * Vjb.x;
+  if (g.wave) {
+    yib += -U * kw * ci * Vib.x - 0.5 * U * kw * kw * si * (Wib.z + rateb);
+    yjb += -U * kw * cj * Vjb.x - 0.5 * U * kw * kw * sj * (Wjb.z + rateb);
+  }
+  const V3d uib = Vib - dub, ujb = Vjb + dub;
+  const V3d wiab = Wib + wib, wjab = Wjb + wjb;
+  out[0] = rb.x; out[1] = rb.y; out[2] = rb.z;
+  out[3] = yib; out[4] = yjb;
+  out[5] = uib.x; out[6] = uib.y; out[7] = uib.z;
+  out[8] = ujb.x; out[9] = ujb.y; out[10] = ujb.z;
+  out[11] = wiab.x; out[12] = wiab.y; out[13] = wiab.z;
+  out[14] = wjab.x; out[15] = wjab.y; out[16] = wjab.z;
+  out[17] = xob.x; out[18] = xob.y; out[19] = xob.z;
+  out[20] = knb; out[21] = ktb; out[22] = gnb; out[23] = mub; out[24] = deltab;
+  out[25] = rob.x; out[26] = rob.y; out[27] = rob.z;
 }
 
 // ---------------------------------------------------------------- tape
@@ -238,7 +498,6 @@ k_adj_pre(Geo g, const InstGeo* __restrict__ ig, AdjTape t, const double* __rest
   bw_n[s] = 0;
 }
 
-template <int K>
 __global__ void __launch_bounds__(kAdjThreads)
 k_adj_pairs(Geo g, const InstGeo* __restrict__ ig, AdjTape t, const double* __restrict__ a_by_id, int P,
             const double* __restrict__ Fb, const double* __restrict__ Tb,
@@ -287,8 +546,7 @@ k_adj_pairs(Geo g, const InstGeo* __restrict__ ig, AdjTape t, const double* __re
     double out[kNin];
 #pragma unroll
     for (int k = 0; k < kNin; ++k) out[k] = 0.0;
-    const int nin = g.k_r > 0.0 ? kNin : 25;
-    for (int base = 0; base < nin; base += K) vjp_pass<K>(g, I, in, cot, base, out);
+    pair_vjp(g, I, in, cot, out);
     double* po = pout + (int64_t)p * 18;
     // i side: x = -r_bar + y_i, u_i, w_i; j side: x = +r_bar + y_j, u_j, w_j
     po[0] = -out[0]; po[1] = -out[1] + out[3]; po[2] = -out[2];
@@ -536,7 +794,7 @@ void adj_reverse(dss_handle* h, int slot, int64_t step, bool initial) {
   k_adj_pre<<<nb, kThreads, 0, h->stream>>>(h->g, h->ig, t, h->a_by_id, A->xb, A->ub, A->wb, A->ab, A->bb,
                                             A->Fb, A->Tb, A->bw_n, initial ? 1 : 0, Wn, 1.0 / vol);
   const int pb = std::max((P + kAdjThreads - 1) / kAdjThreads, 1);
-  k_adj_pairs<kDualK><<<pb, kAdjThreads, 0, h->stream>>>(
+  k_adj_pairs<<<pb, kAdjThreads, 0, h->stream>>>(
       h->g, h->ig, t, h->a_by_id, P, A->Fb, A->Tb, xib_cur, xib_prev, xrb_cur, xrb_prev, Wn,
       1.0 / vol, A->pout, A->bw_n, A->bw_p, A->thb_part, h->status);
   k_adj_theta<<<1, 32, 0, h->stream>>>(A->thb_part, pb, A->thb);

@@ -1,9 +1,7 @@
-// The pair model of one listed pair (FP64 arithmetic), written once over a
-// scalar type T: T = double for the FP64 force pass, T = Dual<K> (forward-mode
-// derivatives in K directions) for the reverse sweep of the adjoint, which
-// builds each pair's vector-Jacobian product from K-column blocks of its
-// local Jacobian.  Branches (contact, Coulomb slip, gap clamp, taper ends)
-// are taken on the values, so derivatives are those of the branch taken.
+// The pair model of one listed pair (FP64 arithmetic), written over a scalar
+// type T (the FP64 force pass; the adjoint's hand-written reverse in
+// dss_adjoint.cu follows its operations one by one).  Branches (contact,
+// Coulomb slip, gap clamp, taper ends) are taken on the values.
 //
 // Contact: Eq. 4-5 (linear spring-dashpot normal force, tangential spring
 // with the stretch carried between steps, Coulomb rescale of the stretch).
@@ -19,176 +17,10 @@
 // ---------------------------------------------------------------- scalars
 __device__ __forceinline__ double val(double x) { return x; }
 
-template <int K>
-struct Dual {
-  double v;
-  double d[K];
-};
-
-template <int K>
-__device__ __forceinline__ double val(const Dual<K>& x) { return x.v; }
-
 template <typename T>
 __device__ __forceinline__ T cst(double c);
 template <>
 __device__ __forceinline__ double cst<double>(double c) { return c; }
-
-template <int K>
-__device__ __forceinline__ Dual<K> dual_const(double c) {
-  Dual<K> r;
-  r.v = c;
-#pragma unroll
-  for (int k = 0; k < K; ++k) r.d[k] = 0.0;
-  return r;
-}
-
-#define DSS_DUAL_OPS(K)                                                              \
-  template <>                                                                        \
-  __device__ __forceinline__ Dual<K> cst<Dual<K>>(double c) { return dual_const<K>(c); }
-DSS_DUAL_OPS(1)
-DSS_DUAL_OPS(2)
-DSS_DUAL_OPS(3)
-DSS_DUAL_OPS(4)
-DSS_DUAL_OPS(5)
-DSS_DUAL_OPS(6)
-DSS_DUAL_OPS(7)
-DSS_DUAL_OPS(8)
-#undef DSS_DUAL_OPS
-
-template <int K>
-__device__ __forceinline__ Dual<K> operator+(const Dual<K>& a, const Dual<K>& b) {
-  Dual<K> r;
-  r.v = a.v + b.v;
-#pragma unroll
-  for (int k = 0; k < K; ++k) r.d[k] = a.d[k] + b.d[k];
-  return r;
-}
-template <int K>
-__device__ __forceinline__ Dual<K> operator-(const Dual<K>& a, const Dual<K>& b) {
-  Dual<K> r;
-  r.v = a.v - b.v;
-#pragma unroll
-  for (int k = 0; k < K; ++k) r.d[k] = a.d[k] - b.d[k];
-  return r;
-}
-template <int K>
-__device__ __forceinline__ Dual<K> operator-(const Dual<K>& a) {
-  Dual<K> r;
-  r.v = -a.v;
-#pragma unroll
-  for (int k = 0; k < K; ++k) r.d[k] = -a.d[k];
-  return r;
-}
-template <int K>
-__device__ __forceinline__ Dual<K> operator*(const Dual<K>& a, const Dual<K>& b) {
-  Dual<K> r;
-  r.v = a.v * b.v;
-#pragma unroll
-  for (int k = 0; k < K; ++k) r.d[k] = a.d[k] * b.v + a.v * b.d[k];
-  return r;
-}
-template <int K>
-__device__ __forceinline__ Dual<K> operator/(const Dual<K>& a, const Dual<K>& b) {
-  Dual<K> r;
-  const double ib = 1.0 / b.v;
-  r.v = a.v * ib;
-#pragma unroll
-  for (int k = 0; k < K; ++k) r.d[k] = (a.d[k] - r.v * b.d[k]) * ib;
-  return r;
-}
-template <int K>
-__device__ __forceinline__ Dual<K> operator+(const Dual<K>& a, double b) {
-  Dual<K> r = a;
-  r.v = a.v + b;
-  return r;
-}
-template <int K>
-__device__ __forceinline__ Dual<K> operator+(double a, const Dual<K>& b) { return b + a; }
-template <int K>
-__device__ __forceinline__ Dual<K> operator-(const Dual<K>& a, double b) {
-  Dual<K> r = a;
-  r.v = a.v - b;
-  return r;
-}
-template <int K>
-__device__ __forceinline__ Dual<K> operator-(double a, const Dual<K>& b) {
-  Dual<K> r;
-  r.v = a - b.v;
-#pragma unroll
-  for (int k = 0; k < K; ++k) r.d[k] = -b.d[k];
-  return r;
-}
-template <int K>
-__device__ __forceinline__ Dual<K> operator*(const Dual<K>& a, double b) {
-  Dual<K> r;
-  r.v = a.v * b;
-#pragma unroll
-  for (int k = 0; k < K; ++k) r.d[k] = a.d[k] * b;
-  return r;
-}
-template <int K>
-__device__ __forceinline__ Dual<K> operator*(double a, const Dual<K>& b) { return b * a; }
-template <int K>
-__device__ __forceinline__ Dual<K> operator/(const Dual<K>& a, double b) { return a * (1.0 / b); }
-template <int K>
-__device__ __forceinline__ Dual<K> operator/(double a, const Dual<K>& b) {
-  Dual<K> r;
-  const double ib = 1.0 / b.v;
-  r.v = a * ib;
-#pragma unroll
-  for (int k = 0; k < K; ++k) r.d[k] = -r.v * ib * b.d[k];
-  return r;
-}
-template <int K>
-__device__ __forceinline__ Dual<K> sqrt(const Dual<K>& a) {
-  Dual<K> r;
-  r.v = ::sqrt(a.v);
-  const double h = 0.5 / r.v;
-#pragma unroll
-  for (int k = 0; k < K; ++k) r.d[k] = h * a.d[k];
-  return r;
-}
-template <int K>
-__device__ __forceinline__ Dual<K> log(const Dual<K>& a) {
-  Dual<K> r;
-  r.v = ::log(a.v);
-  const double ia = 1.0 / a.v;
-#pragma unroll
-  for (int k = 0; k < K; ++k) r.d[k] = ia * a.d[k];
-  return r;
-}
-template <int K>
-__device__ __forceinline__ Dual<K> exp(const Dual<K>& a) {
-  Dual<K> r;
-  r.v = ::exp(a.v);
-#pragma unroll
-  for (int k = 0; k < K; ++k) r.d[k] = r.v * a.d[k];
-  return r;
-}
-template <int K>
-__device__ __forceinline__ Dual<K> sin(const Dual<K>& a) {
-  Dual<K> r;
-  double sn, cs;
-  ::sincos(a.v, &sn, &cs);
-  r.v = sn;
-#pragma unroll
-  for (int k = 0; k < K; ++k) r.d[k] = cs * a.d[k];
-  return r;
-}
-template <int K>
-__device__ __forceinline__ Dual<K> cos(const Dual<K>& a) {
-  Dual<K> r;
-  double sn, cs;
-  ::sincos(a.v, &sn, &cs);
-  r.v = cs;
-#pragma unroll
-  for (int k = 0; k < K; ++k) r.d[k] = -sn * a.d[k];
-  return r;
-}
-template <int K>
-__device__ __forceinline__ Dual<K> fabs(const Dual<K>& a) {
-  return a.v < 0.0 ? -a : a;
-}
 
 // ---------------------------------------------------------------- vectors
 template <typename T>

@@ -152,6 +152,23 @@ def test_adjoint_wave_and_rolling_match_oracle(env, ext):
     assert d.max() < 1e-12
 
 
+def test_adjoint_cutoff_mode_1_matches_oracle(env):
+    """The lubrication range delta_lub a0 (cutoff mode 1) with the taper:
+    its parameter derivative goes through a0 instead of the mean radius."""
+    g, u0, w0, kw, th = _case(env, 0.3)
+    kw = dict(kw, lub_cutoff_mode=1)
+    th = dict(th, delta_lub=0.3)
+    T = 10
+    W = _weights(T, kw["shear_rate"])
+    o = env["oadj"].gradients(g["box"], g["x"], g["a"], u0, w0, T, W, **th, **kw, nstep0=3)
+    r, _ = _gpu(env, g, u0, w0, kw, th, T, W)
+    assert r["J"] == pytest.approx(o["J"], rel=1e-11)
+    check_scalars(r["params"], o["params"], 1e-8, floor=1e-6, what="dJ/dtheta")
+    check_per_particle(r["x0"], o["x0"], 1e-8, what="dJ/dx0")
+    check_per_particle(r["u0"], o["u0"], 1e-8, what="dJ/du0")
+    check_per_particle(r["w0"], o["w0"], 1e-8, what="dJ/dw0")
+
+
 def test_adjoint_wave_rolling_mixed_vs_oracle(env):
     """Mixed-precision forward (FP64 reverse) with the wave and rolling."""
     g, u0, w0, kw, th = _case(env, 0.3)
