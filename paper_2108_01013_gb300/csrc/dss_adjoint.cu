@@ -637,12 +637,16 @@ k_adj_predict(int n3, double dt, const double* __restrict__ xb, double* __restri
   bb[k] = hdt * wb[k];
 }
 
+// The five parameter adjoints of one step from the pair blocks' partials:
+// warp c sums parameter c, its lanes striding over the blocks, then a fixed
+// butterfly (the order depends on the block count alone).
 __global__ void k_adj_theta(const double* __restrict__ part, int nblocks, double* __restrict__ thb) {
-  const int c = threadIdx.x;
+  const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (c >= 5) return;
   double v = 0.0;
-  for (int b = 0; b < nblocks; ++b) v += part[b * 5 + c];
-  thb[c] += v;
+  for (int b = lane; b < nblocks; b += 32) v += part[b * 5 + c];
+  for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
+  if (lane == 0) thb[c] += v;
 }
 
 __global__ void k_adj_accum_J(const double* __restrict__ sigma, const double* __restrict__ W,
@@ -797,7 +801,7 @@ void adj_reverse(dss_handle* h, int slot, int64_t step, bool initial) {
   k_adj_pairs<<<pb, kAdjThreads, 0, h->stream>>>(
       h->g, h->ig, t, h->a_by_id, P, A->Fb, A->Tb, xib_cur, xib_prev, xrb_cur, xrb_prev, Wn,
       1.0 / vol, A->pout, A->bw_n, A->bw_p, A->thb_part, h->status);
-  k_adj_theta<<<1, 32, 0, h->stream>>>(A->thb_part, pb, A->thb);
+  k_adj_theta<<<1, 160, 0, h->stream>>>(A->thb_part, pb, A->thb);
   k_adj_gather<<<nb, kThreads, 0, h->stream>>>(h->g, t, A->pout, A->bw_n, A->bw_p, A->xb, A->ub, A->wb);
   if (initial) {
     // alpha^0, beta^0 are consumed by the initial evaluation

@@ -48,8 +48,8 @@ void free_buffers(dss_handle* h) {
   dfree(h->xc); dfree(h->mark);
   h->xc = nullptr; h->mark = nullptr; h->marked = false;
   dfree(h->cell_count); dfree(h->cell_start); dfree(h->tmp); dfree(h->spart);
-  dfree(h->own); dfree(h->bw_count); dfree(h->bw_rec); dfree(h->carry);
-  h->own = nullptr; h->bw_count = nullptr; h->bw_rec = nullptr; h->carry = nullptr;
+  dfree(h->own); dfree(h->bw_count); dfree(h->bw_rec); dfree(h->carry); dfree(h->own_s);
+  h->own = nullptr; h->bw_count = nullptr; h->bw_rec = nullptr; h->carry = nullptr; h->own_s = nullptr;
   h->pb_blocks = 0;
   h->compact_ok[0] = h->compact_ok[1] = false;
   dfree(h->io3); dfree(h->io3b); dfree(h->io_id); dfree(h->stage);
@@ -109,9 +109,9 @@ int alloc_pair_buffers(dss_handle* h, int64_t pcap, bool keep_hist) {
     dfree(L.xr);
     L.xi = xi;
     L.xr = xr;
-    // one instance: the compact owner / partner arrays of the pair-balanced
-    // pair kernel (rewritten by every enumeration of the list)
-    if (h->K == 1) {
+    // the compact owner / partner arrays of the pair-balanced pair kernel
+    // (rewritten by every enumeration of the list)
+    {
       int *pown = nullptr, *pj = nullptr;
       if ((r = dalloc(h, &pown, (size_t)pcap))) return r;
       if ((r = dalloc(h, &pj, (size_t)pcap))) {
@@ -126,17 +126,20 @@ int alloc_pair_buffers(dss_handle* h, int64_t pcap, bool keep_hist) {
   }
   h->pcap = pcap;
   h->g.pcap = pcap;
-  if (h->K == 1) {
+  {
     const size_t rb = h->p.precision == DSS_MIXED ? sizeof(float) : sizeof(double);
+    const size_t per = h->K > 1 ? 30 : 12;   // two boundary slots per warp of pairs
     char* carry = nullptr;
-    if ((r = dalloc(h, &carry, 12 * rb * (size_t)((pcap + 31) / 32)))) return r;
+    if ((r = dalloc(h, &carry, per * rb * (size_t)((pcap + 31) / 32)))) return r;
     dfree(h->carry);
     h->carry = carry;
     h->pb_blocks = pair_pb_blocks(h);
   }
   h->compact_ok[0] = h->compact_ok[1] = false;
   double* sp = nullptr;
-  const int pb = std::max(pair_grid_blocks(h), pair_pb_blocks(h));
+  // (the balanced grid holds at most 4 blocks per SM; batched instances keep
+  // 16 stress slices each)
+  const int pb = std::max(std::max(pair_grid_blocks(h), h->K == 1 ? 4 * h->sms : 0), 16 * h->K);
   if ((r = dalloc(h, &sp, 18 * (size_t)pb))) return r;
   dfree(h->spart);
   h->spart = sp;
@@ -191,6 +194,11 @@ int alloc_buffers(dss_handle* h) {
       return r;
     h->own = own;
     h->bw_rec = bwr;
+    if (h->K > 1) {
+      char* own_s = nullptr;
+      if ((r = dalloc(h, &own_s, 9 * n * rb))) return r;
+      h->own_s = own_s;
+    }
   }
   int tiles = std::max(scan_tiles_for(h->g.ncell), enum_scan_tiles_for((int)n));
   h->scan_tiles_max = std::max(tiles, 1);

@@ -515,15 +515,21 @@ __device__ __forceinline__ void pair_commit(const Geo& g, const PairRes<R>& q, i
       Sx[3 * a + b2] += q.r[a] * q.Fc[b2] + R(0.5) * (q.r[a] * q.Fl[b2] + q.r[b2] * q.Fl[a]);
 }
 
+// Number of values per warp-boundary slot of the pair-balanced kernel: force
+// and torque (6), and with per-owner stresslets (batched instances) the
+// owner's stresslet sum (9 more).
+template <bool PERS>
+__host__ __device__ constexpr int pb_slot() { return PERS ? 15 : 6; }
+
 // Warp-segmented inclusive scan of the six force/torque sums over lanes with
 // the same owner (seg; lanes of one owner are contiguous).
-template <typename R>
-__device__ __forceinline__ void owner_scan(int lane, int seg, R v[6]) {
+template <typename R, int NV = 6>
+__device__ __forceinline__ void owner_scan(int lane, int seg, R v[NV]) {
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
     const int so = __shfl_up_sync(0xffffffffu, seg, d);
 #pragma unroll
-    for (int c = 0; c < 6; ++c) {
+    for (int c = 0; c < NV; ++c) {
       const R u = __shfl_up_sync(0xffffffffu, v[c], d);
       if (lane >= d && so == seg) v[c] += u;
     }
@@ -735,25 +741,31 @@ k_pairs(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ sgk, 
   stress_partials<MIXED, EXT>(x0, x1, moved, ew0, ew1, ncont, spart, st);
 }
 
-// Pair-balanced pair kernel (one instance).  The listed pairs in owner order
-// (the compact arrays pown, pj written with the row offsets by the
-// enumeration) are dealt out 32 to a warp over a grid of resident blocks, so
-// every lane holds a pair whatever the row lengths.  An owner's pairs are
-// contiguous: the warp-segmented scan sums each owner's share; an owner whose
-// pairs lie in one warp is written once (own), one whose pairs cross a warp
-// boundary leaves its part in the warp's head slot (continued from the
-// previous warp) or tail slot (continuing into the next), which the gather
-// adds in warp order.  Deterministic: the sums' order depends on the pair
-// order alone.
-template <bool MIXED, int MINB, bool EXT>
+// Pair-balanced pair kernel.  The listed pairs in owner order (the compact
+// arrays pown, pj written with the row offsets by the enumeration) are dealt
+// out 32 to a warp over a grid of resident blocks, so every lane holds a pair
+// whatever the row lengths.  An owner's pairs are contiguous: the
+// warp-segmented scan sums each owner's share; an owner whose pairs lie in
+// one warp is written once (own), one whose pairs cross a warp boundary
+// leaves its part in the warp's head slot (continued from the previous warp)
+// or tail slot (continuing into the next), which the gather adds in warp
+// order.  Deterministic: the sums' order depends on the pair order alone.
+// One instance (PERS = false): each thread sums the stresslets of its pairs
+// and the blocks reduce them (stress_partials).  Batched instances (PERS):
+// the stresslet of Eq. 9 rides along in the owner scan, so that each owner's
+// stresslet sum is written with its force (own_s, or the boundary slots) and
+// the gather's instance blocks add them up over the instance's particles.
+template <bool MIXED, int MINB, bool EXT, bool PERS>
 __global__ void __launch_bounds__(kPairThreads, MINB)
 k_pairs_pb(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ sgk, StateBuf s, ListBuf W,
-           ListBuf H, const float4* __restrict__ posf, void* __restrict__ own_v, void* __restrict__ carry_v,
-           int* __restrict__ bw_count, void* __restrict__ bw_v, double* __restrict__ spart, DevStatus* st,
-           const int* __restrict__ perm) {
+           ListBuf H, const float4* __restrict__ posf, void* __restrict__ own_v, void* __restrict__ own_s_v,
+           void* __restrict__ carry_v, int* __restrict__ bw_count, void* __restrict__ bw_v,
+           double* __restrict__ spart, DevStatus* st, const int* __restrict__ perm) {
   using R = typename std::conditional<MIXED, float, double>::type;
+  constexpr int NV = pb_slot<PERS>();
   if (dev_err(st)) return;
   R* __restrict__ own = static_cast<R*>(own_v);
+  R* __restrict__ own_s = static_cast<R*>(own_s_v);
   R* __restrict__ carry = static_cast<R*>(carry_v);
   R* __restrict__ bw = static_cast<R*>(bw_v);
   const int n = g.n;
@@ -766,8 +778,6 @@ k_pairs_pb(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ sg
     }
     return;
   }
-  const InstGeo& I = ig[0];
-  const StepGeo sg = sgk[0];
   R Sx[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   int ncont = 0;
   const int lane = threadIdx.x & 31;
@@ -783,42 +793,63 @@ k_pairs_pb(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ sg
     // the next?
     const int before = (lane == 0 && valid && p > 0) ? W.pown[p - 1] : -1;
     const int after = (lane == 31 && p + 1 < P) ? W.pown[p + 1] : -1;
-    R v[6] = {0, 0, 0, 0, 0, 0};
+    R v[NV];
+#pragma unroll
+    for (int c = 0; c < NV; ++c) v[c] = R(0);
     const int seg = valid ? i : -2 - lane;   // owner, unique sentinel when idle
     if (valid) {
+      const int inst = PERS ? s.inst[i] : 0;
+      const InstGeo& I = ig[inst];
+      const StepGeo sg = sgk[inst];
       PairRes<R> q;
       if constexpr (MIXED) q = pair_eval_mixed<EXT>(g, I, s, H, hr, sg, posf, i, j);
       else q = pair_eval_fp64<EXT>(g, I, s, H, hr, sg.off, i, j);
       v[0] = q.F[0]; v[1] = q.F[1]; v[2] = q.F[2];
       v[3] = q.Ti[0]; v[4] = q.Ti[1]; v[5] = q.Ti[2];
-      pair_commit<R, EXT>(g, q, i, j, p, W, bw_count, bw, st, Sx, ncont);
+      if constexpr (PERS) {
+        R Sp[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        pair_commit<R, EXT>(g, q, i, j, p, W, bw_count, bw, st, Sp, ncont);
+#pragma unroll
+        for (int c = 0; c < 9; ++c) v[6 + c] = Sp[c];
+      } else {
+        pair_commit<R, EXT>(g, q, i, j, p, W, bw_count, bw, st, Sx, ncont);
+      }
     }
-    owner_scan<R>(lane, seg, v);
+    owner_scan<R, NV>(lane, seg, v);
     const int nxt = __shfl_down_sync(0xffffffffu, seg, 1);
     const int head = __shfl_sync(0xffffffffu, (before >= 0 && before == seg) ? seg : -1, 0);
     if (valid && (lane == 31 || nxt != seg)) {
       R* dst = nullptr;
-      if (seg == head) dst = carry + (int64_t)pw * 12;                 // continued from before
-      else if (after == seg) dst = carry + (int64_t)pw * 12 + 6;      // continues after (lane 31)
+      if (seg == head) dst = carry + (int64_t)pw * 2 * NV;                // continued from before
+      else if (after == seg) dst = carry + (int64_t)pw * 2 * NV + NV;     // continues after (lane 31)
       if (dst) {
 #pragma unroll
-        for (int c = 0; c < 6; ++c) dst[c] = v[c];
+        for (int c = 0; c < NV; ++c) dst[c] = v[c];
       } else {
 #pragma unroll
         for (int c = 0; c < 6; ++c) own[(int64_t)c * n + i] = v[c];
+        if constexpr (PERS) {
+#pragma unroll
+          for (int c = 0; c < 9; ++c) own_s[(int64_t)c * n + i] = v[6 + c];
+        }
       }
     }
   }
-  // the wave's single-particle stresslets (see k_pairs), particles strided
-  // over the grid's threads
-  double ew0 = 0.0;
-  if (EXT && g.wave) {
-    for (int il = blockIdx.x * blockDim.x + threadIdx.x; il < n; il += gridDim.x * blockDim.x) {
-      const double a = s.a[il];
-      ew0 += (10.0 / 3.0) * DSS_PI * g.eta0 * a * a * a * s.wv[il].y;
+  if constexpr (PERS) {
+    const int c = __reduce_add_sync(0xffffffffu, ncont);
+    if (lane == 0 && c) atomicAdd(&st->w[ST_NCONT], c);
+  } else {
+    // the wave's single-particle stresslets (see k_pairs), particles strided
+    // over the grid's threads
+    double ew0 = 0.0;
+    if (EXT && g.wave) {
+      for (int il = blockIdx.x * blockDim.x + threadIdx.x; il < n; il += gridDim.x * blockDim.x) {
+        const double a = s.a[il];
+        ew0 += (10.0 / 3.0) * DSS_PI * g.eta0 * a * a * a * s.wv[il].y;
+      }
     }
+    stress_partials<MIXED, EXT>(Sx, Sx, false, ew0, 0.0, ncont, spart, st);
   }
-  stress_partials<MIXED, EXT>(Sx, Sx, false, ew0, 0.0, ncont, spart, st);
 }
 
 // Bulk stress (Eq. 8) of one instance from the pair blocks' partials, by one
@@ -850,6 +881,72 @@ __device__ void inst_stress(const Geo& g, const InstGeo& I, const double* __rest
     double S = 0.0;
     for (int w = 0; w < kThreads / 32; ++w) S += red[w][q];
     // E_inf: only xy and yx are non-zero (gdot/2)
+    const double E = (q == 1 || q == 3) ? 0.5 * I.gdot : 0.0;
+    const double V = I.L[0] * I.L[1] * I.L[2];
+    const double ein = 20.0 / 3.0 * DSS_PI * g.eta0 * I.sumA3;
+    sigma[q] = 2.0 * g.eta0 * E + (ein * E + S) / V;
+  }
+}
+
+// Bulk stress (Eq. 8) of batched instances from their owners' stresslet sums
+// (the pair-balanced kernel with per-owner stresslets): kOsParts blocks per
+// instance, each summing a slice of its particles in a fixed strided order
+// and tree: per particle its own-row sum, or the tail slot of its first
+// warp plus the head slots of the next ones (as the forces), and with the
+// wave of Eq. 17 its local single-particle stresslet.  The gather's instance
+// blocks add the slices (inst_stress_parts).
+constexpr int kOsParts = 16;
+
+template <bool MIXED, bool EXT>
+__global__ void __launch_bounds__(kPairThreads)
+k_owner_stress(Geo g, const InstGeo* __restrict__ ig, StateBuf s, const void* __restrict__ own_s_v,
+               const void* __restrict__ carry_v, const int* __restrict__ start, double* __restrict__ spart,
+               DevStatus* st) {
+  using R = typename std::conditional<MIXED, float, double>::type;
+  if (dev_err(st)) return;
+  const R* __restrict__ own_s = static_cast<const R*>(own_s_v);
+  const R* __restrict__ carry = static_cast<const R*>(carry_v);
+  constexpr int64_t cs = 2 * 15;
+  const int n = g.n;
+  const int k = blockIdx.x / kOsParts, part = blockIdx.x % kOsParts;
+  const InstGeo& I = ig[k];
+  const int chunk = (I.p_end - I.p_begin + kOsParts - 1) / kOsParts;
+  const int j0 = I.p_begin + part * chunk, j1 = min(I.p_end, j0 + chunk);
+  // each thread sums its particles' owner sums in the pair arithmetic's
+  // precision (a few each), then the block's lanes and warps as in the pair
+  // kernel (compensated in mixed precision), one FP64 value per block
+  R v[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  double ew = 0.0;
+  for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+    const int s0 = start[j], s1 = start[j + 1];
+    if (s1 > s0) {
+      const int w0 = s0 >> 5, w1 = (s1 - 1) >> 5;
+      if (w0 == w1) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) v[q] += own_s[(int64_t)q * n + j];
+      } else {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) v[q] += carry[w0 * cs + 15 + 6 + q];
+        for (int w = w0 + 1; w <= w1; ++w)
+#pragma unroll
+          for (int q = 0; q < 9; ++q) v[q] += carry[w * cs + 6 + q];
+      }
+    }
+    if (EXT && g.wave) {
+      const double a = s.a[j];
+      ew += (10.0 / 3.0) * DSS_PI * g.eta0 * a * a * a * s.wv[j].y;
+    }
+  }
+  stress_partials<MIXED, EXT>(v, v, false, ew, 0.0, 0, spart, st);
+}
+
+// The instance's stress from its kOsParts slices (by one block of the gather).
+__device__ void inst_stress_parts(const Geo& g, const InstGeo& I, const double* __restrict__ parts,
+                                  double* __restrict__ sigma) {
+  if (threadIdx.x < 9) {
+    const int q = threadIdx.x;
+    double S = 0.0;
+    for (int p = 0; p < kOsParts; ++p) S += parts[p * 18 + q];
     const double E = (q == 1 || q == 3) ? 0.5 * I.gdot : 0.0;
     const double V = I.L[0] * I.L[1] * I.L[2];
     const double ein = 20.0 / 3.0 * DSS_PI * g.eta0 * I.sumA3;
@@ -1034,7 +1131,8 @@ __device__ __forceinline__ bool gather_one(const Geo& g, const InstGeo* __restri
                                            const int* __restrict__ bw_count, const void* __restrict__ bw_v,
                                            double* __restrict__ Fout, double* __restrict__ Tout,
                                            DevStatus* st, int mode, int j0, int* slots,
-                                           const void* __restrict__ carry_v, const int* __restrict__ start) {
+                                           const void* __restrict__ carry_v, int cnv,
+                                           const int* __restrict__ start) {
   using R = typename std::conditional<MIXED, float, double>::type;
   const R* __restrict__ own = static_cast<const R*>(own_v);
   const R* __restrict__ carry = static_cast<const R*>(carry_v);
@@ -1060,16 +1158,17 @@ __device__ __forceinline__ bool gather_one(const Geo& g, const InstGeo* __restri
         T[c] = own[(int64_t)(3 + c) * n + j];
       }
     } else if (s1 > s0) {
+      const int64_t cs = 2 * cnv;   // head slot, tail slot
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        F[c] = carry[(int64_t)w0 * 12 + 6 + c];
-        T[c] = carry[(int64_t)w0 * 12 + 9 + c];
+        F[c] = carry[w0 * cs + cnv + c];
+        T[c] = carry[w0 * cs + cnv + 3 + c];
       }
       for (int w = w0 + 1; w <= w1; ++w) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          F[c] += carry[(int64_t)w * 12 + c];
-          T[c] += carry[(int64_t)w * 12 + 3 + c];
+          F[c] += carry[w * cs + c];
+          T[c] += carry[w * cs + 3 + c];
         }
       }
     }
@@ -1241,7 +1340,7 @@ k_gather(Geo g, const InstGeo* __restrict__ ig, StateBuf s, const void* __restri
          const int* __restrict__ bw_count, const void* __restrict__ bw_v, double* __restrict__ Fout,
          double* __restrict__ Tout, DevStatus* st, int mode, const double* __restrict__ spart,
          double* sigma, double* sigma_sum, const int* __restrict__ start, unsigned int* done_blocks,
-         const void* __restrict__ carry_v, int pb_blocks) {
+         const void* __restrict__ carry_v, int pb_blocks, const void* __restrict__ own_s_v) {
   // An error set before this kernel (an earlier kernel of the step, or an
   // earlier step of the same dss_step call, whose successors still replay)
   // means this step is void: touch no state, since the buffer this step
@@ -1254,12 +1353,16 @@ k_gather(Geo g, const InstGeo* __restrict__ ig, StateBuf s, const void* __restri
   bool fence = false;
   if (!s_err0) {
     if (blockIdx.x < (unsigned)g.K) {
-      inst_stress(g, ig[blockIdx.x], spart, sigma + 9 * blockIdx.x, pb_blocks);
+      if (own_s_v)
+        inst_stress_parts(g, ig[blockIdx.x], spart + (int64_t)blockIdx.x * kOsParts * 18,
+                          sigma + 9 * blockIdx.x);
+      else
+        inst_stress(g, ig[blockIdx.x], spart, sigma + 9 * blockIdx.x, pb_blocks);
       fence = threadIdx.x < 9;
     } else {
       const int j = (int)(blockIdx.x - g.K) * blockDim.x + threadIdx.x;
       fence = gather_one<MIXED, EXT>(g, ig, s, own_v, bw_count, bw_v, Fout, Tout, st, mode, j,
-                                s_slot[threadIdx.x >> 5], carry_v, start);
+                                s_slot[threadIdx.x >> 5], carry_v, own_s_v ? 15 : 6, start);
     }
   }
   __shared__ bool last;
@@ -1305,11 +1408,11 @@ int pair_grid_blocks(const dss_handle* h) {
   return (int)(need > 0 ? need : 1);
 }
 
-// The pair-balanced kernel's grid (one instance; 0 otherwise): the blocks its
+// The pair-balanced kernel's grid: the blocks its
 // register budget keeps resident on every SM (3 of 256 threads in mixed
 // precision, 2 in FP64), their warps striding over the warps of pairs.
 int pair_pb_blocks(const dss_handle* h) {
-  return h->K == 1 ? h->sms * (h->g.precision == DSS_MIXED ? 3 : 2) : 0;
+  return h->sms * (h->g.precision == DSS_MIXED ? 3 : 2);
 }
 
 int bw_slot_values() { return kSlot; }
@@ -1325,17 +1428,30 @@ void launch_forces_t(dss_handle* h, int stbuf, int work_list, int hist_list, int
   const int pb = pair_grid_blocks(h);
   const bool mixed = h->g.precision == DSS_MIXED;
   prof_mark(h, 5);
-  // one instance: pairs dealt out 32 to a warp over the resident blocks
+  // pairs dealt out 32 to a warp over the resident blocks (batched
+  // instances: with per-owner stresslets)
   const bool pbal = h->pb_blocks > 0 && h->compact_ok[work_list];
+  const bool pers = h->g.K > 1;
   const bool big = h->tune_pairs_minb ? h->tune_pairs_minb == 4 : pb > 3 * h->sms;
-  if (pbal && mixed)
-    k_pairs_pb<true, 3, EXT><<<h->pb_blocks, kPairThreads, 0, h->stream>>>(
-        h->g, h->ig, h->sg, h->st[stbuf], h->lb[work_list], h->lb[hist_list], h->posf, h->own, h->carry,
-        h->bw_count, h->bw_rec, h->spart, h->status, h->perm);
+  // the balanced grid: the resident blocks of its register budget (mixed
+  // precision: 3 per SM, or, for one instance, 4 when the kernel autotuner
+  // chose the smaller budget)
+  const bool pb4 = pbal && mixed && !pers && h->tune_pairs_minb == 4;
+  const int pbg = pb4 ? 4 * h->sms : h->pb_blocks;
+#define DSS_PB_ARGS                                                                                     \
+  h->g, h->ig, h->sg, h->st[stbuf], h->lb[work_list], h->lb[hist_list], h->posf, h->own, h->own_s,    \
+      h->carry, h->bw_count, h->bw_rec, h->spart, h->status, h->perm
+  if (pb4)
+    k_pairs_pb<true, 4, EXT, false><<<pbg, kPairThreads, 0, h->stream>>>(DSS_PB_ARGS);
+  else if (pbal && mixed && pers)
+    k_pairs_pb<true, 3, EXT, true><<<pbg, kPairThreads, 0, h->stream>>>(DSS_PB_ARGS);
+  else if (pbal && mixed)
+    k_pairs_pb<true, 3, EXT, false><<<pbg, kPairThreads, 0, h->stream>>>(DSS_PB_ARGS);
+  else if (pbal && pers)
+    k_pairs_pb<false, 2, EXT, true><<<pbg, kPairThreads, 0, h->stream>>>(DSS_PB_ARGS);
   else if (pbal)
-    k_pairs_pb<false, 2, EXT><<<h->pb_blocks, kPairThreads, 0, h->stream>>>(
-        h->g, h->ig, h->sg, h->st[stbuf], h->lb[work_list], h->lb[hist_list], h->posf, h->own, h->carry,
-        h->bw_count, h->bw_rec, h->spart, h->status, h->perm);
+    k_pairs_pb<false, 2, EXT, false><<<pbg, kPairThreads, 0, h->stream>>>(DSS_PB_ARGS);
+#undef DSS_PB_ARGS
   else if (mixed && big)
     k_pairs<true, 4, EXT><<<pb, kPairThreads, 0, h->stream>>>(
         h->g, h->ig, h->sg, h->st[stbuf], h->lb[work_list], h->lb[hist_list], h->posf, h->own, h->bw_count,
@@ -1351,17 +1467,26 @@ void launch_forces_t(dss_handle* h, int stbuf, int work_list, int hist_list, int
   prof_mark(h, 6);
   const int gb = (n + kThreads - 1) / kThreads + h->g.K;
   const void* carry = pbal ? h->carry : nullptr;
-  const int pbb = pbal ? h->pb_blocks : 0;
+  const int pbb = pbal ? pbg : 0;
+  const void* own_s = pbal && pers ? h->own_s : nullptr;
+  if (own_s) {
+    if (mixed)
+      k_owner_stress<true, EXT><<<h->g.K * kOsParts, kPairThreads, 0, h->stream>>>(
+          h->g, h->ig, h->st[stbuf], own_s, carry, h->lb[work_list].start, h->spart, h->status);
+    else
+      k_owner_stress<false, EXT><<<h->g.K * kOsParts, kPairThreads, 0, h->stream>>>(
+          h->g, h->ig, h->st[stbuf], own_s, carry, h->lb[work_list].start, h->spart, h->status);
+  }
   if (mixed)
     k_gather<true, EXT><<<gb, kThreads, 0, h->stream>>>(h->g, h->ig, h->st[stbuf], h->own, h->bw_count,
                                                         h->bw_rec, F_out, T_out, h->status, mode, h->spart,
                                                         h->sigma, h->sigma_sum, h->lb[work_list].start,
-                                                        h->done_blocks, carry, pbb);
+                                                        h->done_blocks, carry, pbb, own_s);
   else
     k_gather<false, EXT><<<gb, kThreads, 0, h->stream>>>(h->g, h->ig, h->st[stbuf], h->own, h->bw_count,
                                                          h->bw_rec, F_out, T_out, h->status, mode, h->spart,
                                                          h->sigma, h->sigma_sum, h->lb[work_list].start,
-                                                         h->done_blocks, carry, pbb);
+                                                         h->done_blocks, carry, pbb, own_s);
   prof_mark(h, 7);
 }
 }  // namespace

@@ -417,8 +417,8 @@ struct ListBuf {
   Xi4* xr;          // pcap when k_r > 0: rolling stretch (App. B) per pair slot (w unused)
   int* slot_of_id;  // n: sorted index of each id in this list's index space
   int* id_of_slot;  // n: id of each sorted index of this list
-  int* pown;        // pcap, one instance only (else null): owner of each pair, in pair order
-  int* pj;          // pcap, one instance only: partner of each pair (the rows, compacted)
+  int* pown;        // pcap: owner of each pair, in pair order (pair-balanced kernel)
+  int* pj;          // pcap: partner of each pair (the rows, compacted)
 };
 
 // Buffers of the adjoint (reverse sweep over a rollout): per-step tapes of
@@ -514,9 +514,11 @@ struct dss_handle {
   bool hist_empty;
   // force accumulation of the last force pass (FP32 in mixed precision)
   void* own;         // 6n: force and torque summed over each particle's own row
-  void* carry;       // one instance: 12 per warp of 32 pairs, the sums of the owners whose
-                     // pairs continue from the previous warp (6) and into the next (6)
-  int pb_blocks;     // one instance: blocks of the pair-balanced pair kernel (0: owner rows)
+  void* carry;       // per warp of 32 pairs, the sums of the owners whose pairs continue
+                     // from the previous warp and into the next: force and torque (6 + 6;
+                     // batched instances also the stresslet, 15 + 15)
+  void* own_s;       // batched instances: 9n, each owner's stresslet sum (Eq. 9)
+  int pb_blocks;     // blocks of the pair-balanced pair kernel (0: owner rows)
   bool compact_ok[2];  // the list's compact pair arrays were written by its last enumeration
                        // (false after the pair buffers are reallocated)
   int* bw_count;     // n: records appended to each particle's partner row
