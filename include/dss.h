@@ -344,9 +344,14 @@ int dss_autotune_kernels(dss_handle *h, int32_t trial_steps, double *ms_per_step
  * force evaluation at the initial state with an empty contact history (what
  * dss_set_state computes when given none), and their dependence is folded
  * into the other derivatives (dJ_dalpha0/beta0 then return zero).
- * The forward keeps a checkpoint (dss_save) every ckpt_every steps; the
- * reverse sweep replays one segment at a time, taping each step, and walks it
- * backwards: memory is one segment of tapes plus the checkpoints.
+ * The forward keeps a device copy of the committed state (state, history
+ * list and stretch records, status words, stresses) every ckpt_every steps
+ * and sums J on the device; the reverse sweep restores one segment's copy at
+ * a time, replays it taping each step, and walks it backwards: device memory
+ * is one segment of tapes plus the copies (~ (160 + 4 M) B per particle and
+ * 32 B per pair, 64 with rolling, each; DSS_ERR_CUDA when they do not fit).
+ * A step of the forward that fails on the pair capacity is recovered as by
+ * dss_step.
  * Derivatives are pathwise: the pair set, contacts, Coulomb slips (of the
  * sliding and, with k_r > 0, the rolling spring) and the taper ends of each
  * step are those of the forward run and held fixed; with the hard cutoff

@@ -1915,6 +1915,95 @@ int dss_autotune_kernels(dss_handle* h, int32_t trial_steps, double* ms_per_step
 // Adjoint of a rollout: forward with a checkpoint every ckpt_every steps,
 // then per segment (last first) a taped replay and the reverse sweep.
 // ------------------------------------------------------------------------
+// Device checkpoint of the committed state for the adjoint's replays: the
+// buffers a step reads (the committed state, the history list with its
+// stretch records, the status words with the step counters, the stresses),
+// copied as they are, so that a replayed segment repeats the forward bit for
+// bit without a round trip through host memory.
+}  // extern "C"
+namespace {
+struct DevSnap {
+  char* mem = nullptr;
+  size_t bytes = 0;
+  int cur = 0, hist = 0;
+  int64_t P = 0;
+  int64_t mean_steps = 0, host_steps_done = 0;
+};
+
+// The copies of one snapshot as (device buffer, bytes) pairs, in a fixed order.
+template <typename F>
+void snap_fields(dss_handle* h, int cur, int hist, int64_t P, F&& f) {
+  const size_t n = (size_t)h->n, d3 = sizeof(double) * 3 * n;
+  StateBuf& s = h->st[cur];
+  ListBuf& L = h->lb[hist];
+  f((void*)s.x, d3); f((void*)s.u, d3); f((void*)s.w, d3); f((void*)s.al, d3); f((void*)s.aw, d3);
+  f((void*)s.a, sizeof(double) * n);
+  f((void*)s.id, sizeof(int) * n);
+  f((void*)s.inst, sizeof(int) * n);
+  f((void*)s.cls, n);
+  f((void*)s.iy, sizeof(int) * n);
+  f((void*)L.count, sizeof(int) * n);
+  f((void*)L.list, sizeof(int) * n * (size_t)h->g.Ms);
+  f((void*)L.start, sizeof(int) * (n + 1));
+  f((void*)L.slot_of_id, sizeof(int) * n);
+  f((void*)L.id_of_slot, sizeof(int) * n);
+  f((void*)L.xi, sizeof(Xi4) * (size_t)P);
+  if (L.xr) f((void*)L.xr, sizeof(Xi4) * (size_t)P);
+  f((void*)h->status, sizeof(DevStatus));
+  f((void*)h->sigma, sizeof(double) * 9 * (size_t)h->K);
+  f((void*)h->sigma_sum, sizeof(double) * 9 * (size_t)h->K);
+}
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+int snap_take(dss_handle* h, DevSnap& sn) {
+  int Pd = 0;
+  CK(cudaMemcpyAsync(&Pd, h->lb[h->hist].start + h->n, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  const int64_t P = std::min<int64_t>(std::max(Pd, 0), h->pcap);
+  size_t need = 0;
+  snap_fields(h, h->cur, h->hist, P, [&](void*, size_t b) { need += align256(b); });
+  if (need > sn.bytes) {
+    if (sn.mem) cudaFree(sn.mem);
+    sn.mem = nullptr;
+    sn.bytes = 0;
+    if (cudaMalloc((void**)&sn.mem, need) != cudaSuccess) {
+      cudaGetLastError();
+      return DSS_ERR_CUDA;
+    }
+    sn.bytes = need;
+  }
+  size_t off = 0;
+  snap_fields(h, h->cur, h->hist, P, [&](void* p, size_t b) {
+    cudaMemcpyAsync(sn.mem + off, p, b, cudaMemcpyDeviceToDevice, h->stream);
+    off += align256(b);
+  });
+  sn.cur = h->cur;
+  sn.hist = h->hist;
+  sn.P = P;
+  sn.mean_steps = h->mean_steps;
+  sn.host_steps_done = h->host_steps_done;
+  CK(cudaGetLastError());
+  return DSS_OK;
+}
+
+int snap_restore(dss_handle* h, const DevSnap& sn) {
+  h->cur = sn.cur;
+  h->hist = sn.hist;
+  h->mean_steps = sn.mean_steps;
+  h->host_steps_done = sn.host_steps_done;
+  h->last_list = sn.hist;
+  size_t off = 0;
+  snap_fields(h, sn.cur, sn.hist, sn.P, [&](void* p, size_t b) {
+    cudaMemcpyAsync(p, sn.mem + off, b, cudaMemcpyDeviceToDevice, h->stream);
+    off += align256(b);
+  });
+  CK(cudaGetLastError());
+  return sync_status(h);   // the host mirror of the restored status words
+}
+}  // namespace
+extern "C" {
+
 int dss_adjoint(dss_handle* h, int64_t nsteps, int32_t ckpt_every, const double* weights,
                 int32_t initial_forces, double* J, double* dJ_dparams, double* dJ_dx0,
                 double* dJ_du0, double* dJ_dw0, double* dJ_dalpha0, double* dJ_dbeta0) {
@@ -1926,41 +2015,74 @@ int dss_adjoint(dss_handle* h, int64_t nsteps, int32_t ckpt_every, const double*
     if (!h->have_state) return DSS_ERR_STATE;
     ENTER(h);
     const int64_t nseg = (nsteps + ckpt_every - 1) / ckpt_every;
-    std::vector<std::vector<char>> ck((size_t)nseg);
     int r;
-    auto save_to = [&](std::vector<char>& buf) -> int {
-      size_t len = 0;
-      int e = dss_save(h, nullptr, &len);
-      if (e) return e;
-      buf.resize(len);
-      return dss_save(h, buf.data(), &len);
-    };
-    // ---- forward, with checkpoints and the objective
+    // device checkpoints, freed on every exit
+    std::vector<DevSnap> ck((size_t)nseg);
+    DevSnap ck_end;
+    struct Free {
+      std::vector<DevSnap>& a;
+      DevSnap& b;
+      ~Free() {
+        for (auto& q : a)
+          if (q.mem) cudaFree(q.mem);
+        if (b.mem) cudaFree(b.mem);
+      }
+    } free_snaps{ck, ck_end};
     std::vector<double> Wh(9 * (size_t)nsteps);
     CK(cudaMemcpy(Wh.data(), weights, sizeof(double) * 9 * nsteps, cudaMemcpyDefault));
     const bool from_forces = initial_forces != 0;
-    std::vector<double> Jsig(9);
-    double Jacc = 0.0;
-    for (int64_t s = 0; s < nseg; ++s) {
-      if ((r = save_to(ck[(size_t)s]))) return r;
-      const int64_t k1 = std::min<int64_t>(ckpt_every, nsteps - s * ckpt_every);
-      for (int64_t k = 0; k < k1; ++k) {
-        if ((r = dss_step(h, 1))) return r;
-        CK(cudaMemcpyAsync(Jsig.data(), h->sigma, 9 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-        CK(cudaStreamSynchronize(h->stream));
-        const int64_t n1 = s * ckpt_every + k;
-        for (int q = 0; q < 9; ++q) Jacc += Wh[9 * n1 + q] * Jsig[q];
-      }
-    }
-    std::vector<char> ck_end;
-    if ((r = save_to(ck_end))) return r;
-    // ---- reverse
     const int slots = (int)std::min<int64_t>(ckpt_every, nsteps);
     if ((r = adj_alloc(h, slots, nsteps))) return r;
     if ((r = adj_upload_weights(h, Wh.data(), nsteps))) return r;
     adj_zero(h);
+    // ---- forward, with checkpoints and the objective (J summed on the
+    // device after every step; one synchronisation per segment)
+    double Jacc = 0.0;
+    for (int64_t s = 0; s < nseg; ++s) {
+      if ((r = snap_take(h, ck[(size_t)s]))) return r;
+      const int64_t k1 = std::min<int64_t>(ckpt_every, nsteps - s * ckpt_every);
+      const int steps0 = h->status_host->w[ST_STEPS];
+      for (int64_t k = 0; k < k1; ++k) {
+        StepRun run;
+        if ((r = step_launch(h, 1, run))) return r;
+        // the roles once the step commits (checked below)
+        h->cur = 1 - run.cur0;
+        h->hist = 1 - run.hist0;
+        adj_accum_J(h, s * ckpt_every + k);
+      }
+      if ((r = sync_status(h))) return r;
+      const int done = h->status_host->w[ST_STEPS] - steps0;
+      int err = status_error(h);
+      if (err || done != k1) {
+        // a step did not commit (e.g. the pair capacity grew): the segment
+        // again from its checkpoint, one synchronised step at a time
+        if (err) clear_err(h);
+        if ((r = snap_restore(h, ck[(size_t)s]))) return r;
+        const int P = h->status_host->w[ST_NPAIRS];
+        if (err == DSS_ERR_CAPACITY && P > h->pcap &&
+            (r = alloc_pair_buffers(h, (int64_t)(P * 1.25) + 1024, true)))
+          return r;
+        // J back to its value at the segment's start: the sum so far
+        CK(cudaMemcpy(h->adj->J, &Jacc, sizeof(double), cudaMemcpyHostToDevice));
+        for (int64_t k = 0; k < k1; ++k) {
+          if ((r = step_run(h, 1))) return r;
+          adj_accum_J(h, s * ckpt_every + k);
+        }
+        if ((r = sync_status(h))) return r;
+      } else {
+        h->host_steps_done += done;
+        h->mean_steps += done;
+        h->last_list = h->hist;
+      }
+      CK(cudaMemcpy(&Jacc, h->adj->J, sizeof(double), cudaMemcpyDeviceToHost));
+    }
+    if ((r = snap_take(h, ck_end))) return r;
+    // ---- reverse (the pair buffers may have grown during the forward)
+    if ((r = adj_alloc(h, slots, nsteps))) return r;
+    if ((r = adj_upload_weights(h, Wh.data(), nsteps))) return r;
+    adj_zero(h);
     for (int64_t s = nseg - 1; s >= 0; --s) {
-      if ((r = dss_load(h, ck[(size_t)s].data(), ck[(size_t)s].size()))) return r;
+      if ((r = snap_restore(h, ck[(size_t)s]))) return r;
       const int64_t k1 = std::min<int64_t>(ckpt_every, nsteps - s * ckpt_every);
       // taped replay (the same kernels as dss_step, without the graph)
       for (int64_t k = 0; k < k1; ++k) {
@@ -1982,8 +2104,13 @@ int dss_adjoint(dss_handle* h, int64_t nsteps, int32_t ckpt_every, const double*
     if (from_forces) {
       // alpha^0 came from a force evaluation at the initial state with an
       // empty history: its reverse adds the dependence through alpha^0
-      if ((r = dss_load(h, ck[0].data(), ck[0].size()))) return r;
-      adj_tape(h, 0, h->cur, h->hist, h->hist, true);
+      if ((r = snap_restore(h, ck[0]))) return r;
+      // its pairs, listed again as that evaluation listed them (a sort
+      // without the predictor, the enumeration) over the committed state
+      const int w = 1 - h->cur;
+      launch_sort(h, false, h->cur, w);
+      launch_enumerate(h, w, 1 - h->hist, 0);
+      adj_tape(h, 0, w, 1 - h->hist, h->hist, true);
       CK(cudaStreamSynchronize(h->stream));   // the tape's pair count is read on the host
       adj_reverse(h, 0, 0, true);
     }
@@ -2001,7 +2128,7 @@ int dss_adjoint(dss_handle* h, int64_t nsteps, int32_t ckpt_every, const double*
     if (dJ_dparams) CK(cudaMemcpyAsync(dJ_dparams, A->thb, 5 * sizeof(double), cudaMemcpyDefault, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     if (J) *J = Jacc;
-    return dss_load(h, ck_end.data(), ck_end.size());
+    return snap_restore(h, ck_end);
   });
 }
 

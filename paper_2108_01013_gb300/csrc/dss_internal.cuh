@@ -511,7 +511,6 @@ struct dss_handle {
   // lists: hist = committed (history source), work = being built
   ListBuf lb[2];
   int hist;
-  bool hist_empty;
   // force accumulation of the last force pass (FP32 in mixed precision)
   void* own;         // 6n: force and torque summed over each particle's own row
   void* carry;       // per warp of 32 pairs, the sums of the owners whose pairs continue

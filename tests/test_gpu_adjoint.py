@@ -90,6 +90,40 @@ def test_adjoint_independent_of_checkpoint_interval(env):
     assert a["J"] == b["J"] == c["J"]
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_adjoint_recovers_pair_capacity_growth(env, precision):
+    """A rollout whose first step overflows the pair buffers (allocated for
+    one pair per particle, no enumeration before the rollout): the forward
+    segment is redone from its device checkpoint after the buffers grow, and
+    the objective, the gradients and the final state equal those of a handle
+    that never overflowed."""
+    g, u0, w0, kw, th = _case(env, 0.3)
+    n = g["a"].shape[0]
+    T = 9
+    W = _weights(T, kw["shear_rate"])
+    dss = env["dss"]
+    out = []
+    for pc in (1, 0):
+        p = dss.default_params(g["box"], precision=precision, pair_capacity=pc, **th, **kw)
+        s = dss.Suspension(g["x"], g["a"], g["box"], p, ids=g["ids"], u=u0, w=w0, nstep=3,
+                           alpha_lin=np.zeros((3, n)), alpha_ang=np.zeros((3, n)))
+        b0 = s.device_bytes()
+        r = s.adjoint(T, W, ckpt_every=4, initial_forces=False)
+        grew = s.device_bytes() > b0
+        st = s.state()
+        c = s.counters()
+        s.close()
+        out.append((r, st, grew, c))
+    (ra, sa, grew_a, ca), (rb, sb, _, cb) = out
+    assert grew_a
+    assert ca["steps_done"] == cb["steps_done"] == T
+    assert ra["J"] == rb["J"]
+    for k in ("params", "x0", "u0", "w0", "alpha0", "beta0"):
+        assert np.array_equal(ra[k], rb[k]), k
+    for k in sa:
+        assert env["torch"].equal(sa[k], sb[k]), k
+
+
 def test_adjoint_mixed_precision_vs_oracle(env):
     g, u0, w0, kw, th = _case(env, 0.3)
     T = 12
