@@ -375,6 +375,20 @@ int dss_adjoint(dss_handle *h, int64_t nsteps, int32_t ckpt_every, const double 
  * stream to run on (NULL: legacy default stream); synchronises it. */
 int dss_selftest_bounded_wait(void *cuda_stream);
 
+/* Self-test of the conversions the sort kernels take by integer operations
+ * on the IEEE-754 bit patterns instead of GB300's narrow FP64 pipe; each must
+ * equal the hardware conversion bit for bit.  For k < n: hi[k] =
+ * RN_f32(v[k]); (split_hi[k], split_lo[k]) = (RN_f32(v[k]),
+ * RN_f32(v[k] - split_hi[k])) (the double-float split); back[k] =
+ * (double)hi[k]; floor_out[k] = floor(RN_f64(v[k] * inv)) (the cell
+ * coordinate, int, for |v[k] inv| < 2^31); ints_out[k] = (double)ints[k]
+ * (ints[k] >= 0).  All arrays device memory of n elements.  DSS_ERR_ARG for
+ * n < 0 or a NULL array; DSS_ERR_CUDA on a launch failure.  cuda_stream:
+ * stream to run on (NULL: legacy default stream); synchronises it. */
+int dss_selftest_conversions(const double *v, int64_t n, double inv, float *hi, float *split_hi,
+                             float *split_lo, double *back, int32_t *floor_out, const int32_t *ints,
+                             double *ints_out, void *cuda_stream);
+
 /* ---- Analysis pass (not part of the time step; each call synchronises) ---- */
 
 /* Rheology of every instance from its bulk stress (Sec. II, after Eq. 9):

@@ -109,6 +109,8 @@ SIGNATURES = {
     "dss_autotune": (c_int, [c_void_p, c_int32, c_int32, _dp, _dp, _dp]),
     "dss_autotune_kernels": (c_int, [c_void_p, c_int32, _dp, _ip]),
     "dss_selftest_bounded_wait": (c_int, [c_void_p]),
+    "dss_selftest_conversions": (c_int, [_vp, c_int64, c_double, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                                         c_void_p]),
     "dss_rheology": (c_int, [c_void_p, c_int, _vp]),
     "dss_get_images": (c_int, [c_void_p, _vp]),
     "dss_dispersion_mark": (c_int, [c_void_p]),

@@ -595,6 +595,7 @@ int geometry(dss_handle* h) {
     cells += C * nck;
     const double csmax = std::max(I.cs[0], std::max(I.cs[1], I.cs[2]));
     I.r2_margin = (float)(1e-4 * csmax * csmax);
+    for (int d = 0; d < 3; ++d) I.inv_csf[d] = (float)I.inv_cs[d];
     I.p_begin = (int)pos;
     pos += h->inst_n[k];
     I.p_end = (int)pos;

@@ -226,6 +226,10 @@ __device__ __forceinline__ PairRes<float> pair_eval_mixed(const Geo& g, const In
   // rows differ by more crosses y = L_y, its image shifted by +-off along x)
   const float4 pi = posf[i], pj = posf[j], li = s.posl[i], lj = s.posl[j];
   const int ci = s.cellc[i], cj = s.cellc[j];
+  // the ids and the probe of the committed rows go out with the state loads
+  // (their latency hides behind the geometry; the probe is used by contacts)
+  const int idi = s.id[i], idj = s.id[j];
+  const HistProbe pr = hist_probe(g, H, hr, i, j, idi, idj);
   const int nx = I.nc[0], ny = I.nc[1], nz = I.nc[2];
   const int R = g.reach;
   int wy = ((cj >> 10) & 1023) - ((ci >> 10) & 1023);
@@ -281,10 +285,8 @@ __device__ __forceinline__ PairRes<float> pair_eval_mixed(const Geo& g, const In
     q.contact = __dsub_rn(exact_dist(ex, ey, ez), __dadd_rn(s.a[i], s.a[j])) < 0.0;
   }
   Xi4 xrec{0.0, 0.0, 0.0, 0.0}, rrec{0.0, 0.0, 0.0, 0.0};
-  int idi = 0, idj = 0;
   if (q.contact) {
-    idi = s.id[i]; idj = s.id[j];
-    const int64_t pold = hist_slot(g, H, hist_probe(g, H, hr, i, j, idi, idj));
+    const int64_t pold = hist_slot(g, H, pr);
     if (pold >= 0) {
       xrec = H.xi[pold];
       if (EXT && g.k_r > 0.0) rrec = H.xr[pold];
@@ -491,14 +493,14 @@ __device__ __forceinline__ void store_record(double* b, double a0, double a1, do
 }
 
 // Per pair after its evaluation: the partner's share (-F and its torque)
-// appended to the partner's row with the owner's index, the stretch records,
+// written to slot `slot` of the partner's row (taken by the caller with an
+// atomic on the row's count) with the owner's index, the stretch records,
 // the contact count and the stresslet of Eq. 9 (S^C = r (x) F^C,
 // S^L = sym(r (x) F^L), F on the owner) added to the thread's sum.
 template <typename R, bool EXT>
 __device__ __forceinline__ void pair_commit(const Geo& g, const PairRes<R>& q, int i, int j, int p, ListBuf& W,
-                                            int* __restrict__ bw_count, R* __restrict__ bw, DevStatus* st,
-                                            R Sx[9], int& ncont) {
-  const int slot = atomicAdd(&bw_count[j], 1);
+                                            int slot, R* __restrict__ bw, DevStatus* st, R Sx[9],
+                                            int& ncont) {
   if (slot < g.M) {
     R* b = bw + ((int64_t)j * g.M + slot) * kSlot;
     store_record(b, -q.F[0], -q.F[1], -q.F[2], q.Tj[0], q.Tj[1], q.Tj[2], owner_bits<R>(i));
@@ -699,7 +701,7 @@ k_pairs(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ sgk, 
           }
           cur_inst = inst;
         }
-        pair_commit<R, EXT>(g, q, i, j, p, W, bw_count, bw, st, Sx, ncont);
+        pair_commit<R, EXT>(g, q, i, j, p, W, atomicAdd(&bw_count[j], 1), bw, st, Sx, ncont);
       }
       owner_scan<R>(lane, seg, v);
       const int nxt = __shfl_down_sync(0xffffffffu, seg, 1);
@@ -789,6 +791,8 @@ k_pairs_pb(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ sg
     const bool valid = p < P;
     const int i = valid ? W.pown[p] : -1;
     const int j = valid ? W.pj[p] : 0;
+    // the partner-record slot, taken first (its latency hides behind the pair)
+    const int slot = valid ? atomicAdd(&bw_count[j], 1) : 0;
     // lane 0: does its owner continue from the previous warp?  lane 31: into
     // the next?
     const int before = (lane == 0 && valid && p > 0) ? W.pown[p - 1] : -1;
@@ -808,11 +812,11 @@ k_pairs_pb(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ sg
       v[3] = q.Ti[0]; v[4] = q.Ti[1]; v[5] = q.Ti[2];
       if constexpr (PERS) {
         R Sp[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-        pair_commit<R, EXT>(g, q, i, j, p, W, bw_count, bw, st, Sp, ncont);
+        pair_commit<R, EXT>(g, q, i, j, p, W, slot, bw, st, Sp, ncont);
 #pragma unroll
         for (int c = 0; c < 9; ++c) v[6 + c] = Sp[c];
       } else {
-        pair_commit<R, EXT>(g, q, i, j, p, W, bw_count, bw, st, Sx, ncont);
+        pair_commit<R, EXT>(g, q, i, j, p, W, slot, bw, st, Sx, ncont);
       }
     }
     owner_scan<R, NV>(lane, seg, v);

@@ -82,6 +82,7 @@ struct InstGeo {
   double L[3], halfL[3], invL[3];
   double cs[3], inv_cs[3];      // cell edge per axis
   float csf[3], cs_lo[3];       // double-float cell edges
+  float inv_csf[3];             // FP32 inverse cell edges (the cell test's fast path)
   float halfLf[3];
   float r2_margin;              // FP32 prefilter margin on r^2 (absolute)
   int nc[3];
@@ -178,6 +179,96 @@ __device__ __forceinline__ bool exact_is_pair(const Geo& g, const InstGeo& I, do
 __device__ __forceinline__ int cell_coord(double v, double inv, int nc) {
   int k = __double2int_rd(v * inv);   // floor, one conversion
   return k < 0 ? 0 : (k >= nc ? nc - 1 : k);
+}
+
+// ------------------------------------------------------------------------
+// Conversions by integer operations on the IEEE-754 bit patterns.  GB300's
+// FP64 pipe (two lanes per SM per clock) runs the FP64 conversions too; in
+// the sort's kernels they outnumbered the arithmetic.  Each function returns
+// exactly what the named hardware conversion returns (round to nearest,
+// ties to even) and hands the cases outside its range (zero, subnormal,
+// infinite, NaN, out of the float range) to that conversion, called out of
+// line: a branch the compiler turns into predicated instructions still
+// issues them to the FP64 pipe.
+// ------------------------------------------------------------------------
+static __device__ __noinline__ float f32_rn_slow(double v) { return __double2float_rn(v); }
+static __device__ __noinline__ double f64_of_slow(float f) { return (double)f; }
+static __device__ __noinline__ double f64_of_int_slow(int c) { return (double)c; }
+static __device__ __noinline__ float2 f32_split_slow(double v) {
+  const float hi = __double2float_rn(v);
+  return make_float2(hi, __double2float_rn(v - (double)hi));
+}
+static __device__ __noinline__ int floor_mul_slow(double v, double inv) { return __double2int_rd(v * inv); }
+
+// double -> float, as __double2float_rn.  A double of biased exponent e in
+// [897, 1150] is a normal float after rounding: the top 23 fraction bits are
+// kept, the 29 below decide the rounding, and a carry out of the fraction
+// moves into the exponent field (up to infinity), as IEEE rounding does.
+__device__ __forceinline__ float f32_rn(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const unsigned long long a = b & 0x7FFFFFFFFFFFFFFFull;
+  const unsigned e = (unsigned)(a >> 52);
+  if (e - 897u > 1150u - 897u) return f32_rn_slow(v);
+  unsigned t = (unsigned)((a >> 29) - (896ull << 23));
+  const unsigned rem = (unsigned)a & 0x1FFFFFFFu;
+  t += (rem > 0x10000000u) | ((rem == 0x10000000u) & t);
+  return __uint_as_float(t | ((unsigned)(b >> 32) & 0x80000000u));
+}
+
+// float -> double (exact), as (double)f.
+__device__ __forceinline__ double f64_of(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned a = u & 0x7FFFFFFFu;
+  if (a - 0x00800000u >= 0x7F000000u) return f64_of_slow(f);
+  return __longlong_as_double((long long)((((unsigned long long)a + (896ull << 23)) << 29) |
+                                          ((unsigned long long)(u & 0x80000000u) << 32)));
+}
+
+// Non-negative int -> double (exact), as (double)c.
+__device__ __forceinline__ double f64_of_nonneg(int c) {
+  if (c <= 0) return f64_of_int_slow(c);
+  const int e = 31 - __clz(c);   // c in [2^e, 2^(e+1))
+  const unsigned long long m = ((unsigned long long)c << (52 - e)) & 0xFFFFFFFFFFFFFull;
+  return __longlong_as_double((long long)(((unsigned long long)(e + 1023) << 52) | m));
+}
+
+// The double-float split of v: hi = RN_f32(v), lo = RN_f32(v - hi), as
+// hi = __double2float_rn(v); lo = __double2float_rn(v - (double)hi).  With
+// v = M 2^(e-1075) (M the 53-bit significand), v - hi is exactly
+// (rem - up 2^29) 2^(e-1075) with rem the 29 discarded bits and up the
+// rounding carry; its float is the integer's float (round to nearest) scaled
+// by a power of two, exact while the result is a normal float (e >= 949).
+// Below 2^126 (e <= 1149) hi cannot round up to infinity.
+__device__ __forceinline__ void f32_split(double v, float& hi, float& lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const unsigned long long a = b & 0x7FFFFFFFFFFFFFFFull;
+  const unsigned e = (unsigned)(a >> 52);
+  if (e - 949u > 1149u - 949u) {
+    const float2 q = f32_split_slow(v);
+    hi = q.x;
+    lo = q.y;
+    return;
+  }
+  unsigned t = (unsigned)((a >> 29) - (896ull << 23));
+  const unsigned rem = (unsigned)a & 0x1FFFFFFFu;
+  const unsigned up = (rem > 0x10000000u) | ((rem == 0x10000000u) & t);
+  t += up;
+  const bool neg = (b >> 63) != 0;
+  hi = __uint_as_float(t | (neg ? 0x80000000u : 0u));
+  const int r = (int)rem - (int)(up << 29);
+  lo = __int2float_rn(neg ? -r : r) * __uint_as_float((e - 948u) << 23);
+}
+
+// floor(RN_d(v inv)) as __double2int_rd(v * inv), for |v inv| < 2^22: the
+// FP32 product is within 2^-21 |product| of the FP64 one, so away from an
+// integer by more than that their floors agree; closer, the FP64 product
+// decides.
+__device__ __forceinline__ int floor_mul(double v, double inv, float invf) {
+  const float pf = f32_rn(v) * invf;
+  const float k = floorf(pf);
+  const float tol = fabsf(pf) * 4.76837158203125e-7f;   // 2^-21
+  if (pf - k > tol && (k + 1.0f) - pf > tol && fabsf(pf) < 4194304.0f) return (int)k;
+  return floor_mul_slow(v, inv);
 }
 
 __device__ __forceinline__ int wrapi(int v, int n) {

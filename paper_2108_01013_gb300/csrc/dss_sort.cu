@@ -36,6 +36,40 @@ struct Pred {
   int cross;
 };
 
+// Lees-Edwards wrap of Eq. 16 and the periodic wraps along x and z, for a
+// particle that left the box (out of line: see f32_rn_slow).
+__device__ __noinline__ Pred wrap_out(const Geo& g, const InstGeo& I, const DevStatus* st, int adv, Pred r) {
+  double x = r.x, y = r.y, z = r.z, ux = r.ux;
+  // leaving through y >= L_y re-enters at the bottom shifted by -off along
+  // x with u_x - gdot L_y, and vice versa
+  const double Ly = I.L[1];
+  if (ge_pos(y, Ly)) {
+    y = __dsub_rn(y, Ly);
+    x = __dsub_rn(x, le_offset(g, I, dev_nstep(st) + adv));
+    r.cross = -1;
+  } else if (lt_zero(y)) {
+    y = __dadd_rn(y, Ly);
+    x = __dadd_rn(x, le_offset(g, I, dev_nstep(st) + adv));
+    r.cross = 1;
+    if (ge_pos(y, Ly)) y = 0.0;
+  }
+  // x back into [0, L_x): two conditional shifts give the same bits as
+  // fmod followed by the two corrections, for |x| < 2 L_x
+  const double Lx = I.L[0];
+  if (lt_zero(x)) x = __dadd_rn(x, Lx); else if (ge_pos(x, Lx)) x = __dsub_rn(x, Lx);
+  if (lt_zero(x)) x = __dadd_rn(x, Lx); else if (ge_pos(x, Lx)) x = __dsub_rn(x, Lx);
+  if (ge_pos(z, I.L[2])) {
+    z = __dsub_rn(z, I.L[2]);
+  } else if (lt_zero(z)) {
+    z = __dadd_rn(z, I.L[2]);
+    if (ge_pos(z, I.L[2])) z = 0.0;
+  }
+  if (r.cross != 0)
+    ux = __dadd_rn(ux, __dmul_rn(__dmul_rn((double)r.cross, I.gdot), Ly));
+  r.x = x; r.y = y; r.z = z; r.ux = ux;
+  return r;
+}
+
 __device__ __forceinline__ Pred predict_one(const Geo& g, const InstGeo& I, const DevStatus* st,
                                             int adv, const StateBuf& s, int i, bool predict) {
   const int n = g.n;
@@ -65,43 +99,28 @@ __device__ __forceinline__ Pred predict_one(const Geo& g, const InstGeo& I, cons
       uy = __fma_rn(hdt, ay, uy);
       uz = __fma_rn(hdt, az, uz);
     }
-    // Lees-Edwards wrap: leaving through y >= L_y re-enters at the bottom
-    // shifted by -off along x with u_x - gdot L_y, and vice versa
-    const double Ly = I.L[1];
-    if (ge_pos(y, Ly)) {
-      y = __dsub_rn(y, Ly);
-      x = __dsub_rn(x, le_offset(g, I, dev_nstep(st) + adv));
-      r.cross = -1;
-    } else if (lt_zero(y)) {
-      y = __dadd_rn(y, Ly);
-      x = __dadd_rn(x, le_offset(g, I, dev_nstep(st) + adv));
-      r.cross = 1;
-      if (ge_pos(y, Ly)) y = 0.0;
-    }
-    // x back into [0, L_x): two conditional shifts give the same bits as
-    // fmod followed by the two corrections, for |x| < 2 L_x
-    const double Lx = I.L[0];
-    if (lt_zero(x)) x = __dadd_rn(x, Lx); else if (ge_pos(x, Lx)) x = __dsub_rn(x, Lx);
-    if (lt_zero(x)) x = __dadd_rn(x, Lx); else if (ge_pos(x, Lx)) x = __dsub_rn(x, Lx);
-    if (ge_pos(z, I.L[2])) {
-      z = __dsub_rn(z, I.L[2]);
-    } else if (lt_zero(z)) {
-      z = __dadd_rn(z, I.L[2]);
-      if (ge_pos(z, I.L[2])) z = 0.0;
-    }
-    if (r.cross != 0)
-      ux = __dadd_rn(ux, __dmul_rn(__dmul_rn((double)r.cross, I.gdot), Ly));
   }
   r.x = x; r.y = y; r.z = z;
   r.ux = ux; r.uy = uy; r.uz = uz;
+  // inside the box (nearly every particle): nothing to wrap
+  if (predict && (ge_pos(y, I.L[1]) || lt_zero(y) || ge_pos(x, I.L[0]) || lt_zero(x) || ge_pos(z, I.L[2]) ||
+                  lt_zero(z)))
+    r = wrap_out(g, I, st, adv, r);
   return r;
+}
+
+// Cell coordinate floor(x / cs) along one axis, clamped to the grid (the
+// FP64 product's floor, mostly decided in FP32: floor_mul).
+__device__ __forceinline__ int cell_coord_fast(double v, double inv, float invf, int nc) {
+  const int k = floor_mul(v, inv, invf);
+  return k < 0 ? 0 : (k >= nc ? nc - 1 : k);
 }
 
 // Bin of a particle: its instance's bins, its size class's layer, its cell.
 __device__ __forceinline__ int cell_key(const InstGeo& I, int cls, double x, double y, double z) {
-  int cx = cell_coord(x, I.inv_cs[0], I.nc[0]);
-  int cy = cell_coord(y, I.inv_cs[1], I.nc[1]);
-  int cz = cell_coord(z, I.inv_cs[2], I.nc[2]);
+  int cx = cell_coord_fast(x, I.inv_cs[0], I.inv_csf[0], I.nc[0]);
+  int cy = cell_coord_fast(y, I.inv_cs[1], I.inv_csf[1], I.nc[1]);
+  int cz = cell_coord_fast(z, I.inv_cs[2], I.inv_csf[2], I.nc[2]);
   return I.cell_base + cls * I.ncell_layer + (cz * I.nc[1] + cy) * I.nc[0] + cx;
 }
 
@@ -209,21 +228,24 @@ k_rank_gather(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__
   }
   dst.x[f] = p.x; dst.x[n + f] = p.y; dst.x[2 * n + f] = p.z;
   dst.u[f] = p.ux; dst.u[n + f] = p.uy; dst.u[2 * n + f] = p.uz;
+  double wv3[3];
   if (predict) {
     const double hdt = g.hdt;
     if (g.precision == DSS_FP64)
       for (int c = 0; c < 3; ++c)
-        dst.w[c * n + f] = __dadd_rn(src.w[c * n + o], __dmul_rn(hdt, src.aw[c * n + o]));
+        wv3[c] = __dadd_rn(src.w[c * n + o], __dmul_rn(hdt, src.aw[c * n + o]));
     else
       for (int c = 0; c < 3; ++c)
-        dst.w[c * n + f] = __fma_rn(hdt, src.aw[c * n + o], src.w[c * n + o]);
+        wv3[c] = __fma_rn(hdt, src.aw[c * n + o], src.w[c * n + o]);
   } else {
     for (int c = 0; c < 3; ++c) {
-      dst.w[c * n + f] = src.w[c * n + o];
+      wv3[c] = src.w[c * n + o];
       dst.al[c * n + f] = src.al[c * n + o];
       dst.aw[c * n + f] = src.aw[c * n + o];
     }
   }
+  for (int c = 0; c < 3; ++c) dst.w[c * n + f] = wv3[c];
+  const double w0 = wv3[0], w1 = wv3[1], w2 = wv3[2];
   const double a = src.a[o];
   dst.a[f] = a;
   dst.id[f] = id;
@@ -239,16 +261,14 @@ k_rank_gather(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__
     const double ws = g.wave_amp * sn, wc = g.wave_amp * I.wave_k * cs;
     dst.wv[f] = make_double2(ws, wc);
     if (g.precision == DSS_MIXED) {
-      dst.vf[f] = make_float4((float)(p.ux - I.gdot * p.y - ws), (float)p.uy, (float)p.uz, (float)wc);
-      dst.wf[f] = make_float4((float)dst.w[f], (float)dst.w[n + f],
-                              (float)(dst.w[2 * n + f] + 0.5 * (I.gdot + wc)), (float)ws);
+      dst.vf[f] = make_float4(f32_rn(p.ux - I.gdot * p.y - ws), f32_rn(p.uy), f32_rn(p.uz), f32_rn(wc));
+      dst.wf[f] = make_float4(f32_rn(w0), f32_rn(w1), f32_rn(w2 + 0.5 * (I.gdot + wc)), f32_rn(ws));
     }
   } else if (g.precision == DSS_MIXED) {
     // FP32 copies relative to the ambient flow for the FP32 pair arithmetic:
     // u - U_inf(x) and w - Omega_inf are O(gdot a), free of O(gdot L) terms
-    dst.vf[f] = make_float4((float)(p.ux - I.gdot * p.y), (float)p.uy, (float)p.uz, 0.f);
-    dst.wf[f] = make_float4((float)dst.w[f], (float)dst.w[n + f],
-                            (float)(dst.w[2 * n + f] + 0.5 * I.gdot), 0.f);
+    dst.vf[f] = make_float4(f32_rn(p.ux - I.gdot * p.y), f32_rn(p.uy), f32_rn(p.uz), 0.f);
+    dst.wf[f] = make_float4(f32_rn(w0), f32_rn(w1), f32_rn(w2 + 0.5 * I.gdot), 0.f);
   }
   // cell-local position (FP32 for the enumeration prefilter; in mixed
   // precision also the low words, for double-float pair geometry)
@@ -256,17 +276,19 @@ k_rank_gather(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__
   int cx = kl % I.nc[0];
   int cy = (kl / I.nc[0]) % I.nc[1];
   int cz = kl / (I.nc[0] * I.nc[1]);
-  const double lx = __fma_rn(-(double)cx, I.cs[0], p.x), ly = __fma_rn(-(double)cy, I.cs[1], p.y),
-               lz = __fma_rn(-(double)cz, I.cs[2], p.z);
-  float4 pf;
-  pf.x = (float)lx;
-  pf.y = (float)ly;
-  pf.z = (float)lz;
-  pf.w = (float)a;
+  const double lx = __fma_rn(-f64_of_nonneg(cx), I.cs[0], p.x),
+               ly = __fma_rn(-f64_of_nonneg(cy), I.cs[1], p.y),
+               lz = __fma_rn(-f64_of_nonneg(cz), I.cs[2], p.z);
+  // the FP32 words and (mixed precision) the low words of the double-float
+  // pair geometry
+  float4 pf, pl;
+  f32_split(lx, pf.x, pl.x);
+  f32_split(ly, pf.y, pl.y);
+  f32_split(lz, pf.z, pl.z);
+  f32_split(a, pf.w, pl.w);
   posf[f] = pf;
   if (g.precision == DSS_MIXED) {
-    dst.posl[f] = make_float4((float)(lx - (double)pf.x), (float)(ly - (double)pf.y),
-                              (float)(lz - (double)pf.z), (float)(a - (double)pf.w));
+    dst.posl[f] = pl;
     dst.cellc[f] = cx | (cy << 10) | (cz << 20);
   }
   (void)sgk;
@@ -395,4 +417,37 @@ void launch_sort(dss_handle* h, bool predict, int src, int dst) {
     k_rank_gather<false><<<blocks, kThreads, 0, h->stream>>>(h->g, h->ig, h->sg, h->st[src], h->st[dst], h->key,
                                                              h->cell_start, h->tmp, h->perm, h->cellid,
                                                              h->posf, h->status, predict, h->pred, h->xc);
+}
+
+// Self-test of the integer-operation conversions (f32_rn, f32_split, f64_of,
+// floor_mul, f64_of_nonneg) over caller-chosen inputs.
+namespace {
+__global__ void k_selftest_conversions(const double* __restrict__ v, int64_t n, double inv, float invf,
+                                       float* __restrict__ hi, float* __restrict__ shi,
+                                       float* __restrict__ slo, double* __restrict__ back,
+                                       int* __restrict__ fl, const int* __restrict__ ci,
+                                       double* __restrict__ cd) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    const double x = v[k];
+    const float h = f32_rn(x);
+    hi[k] = h;
+    f32_split(x, shi[k], slo[k]);
+    back[k] = f64_of(h);
+    fl[k] = floor_mul(x, inv, invf);
+    cd[k] = f64_of_nonneg(ci[k]);
+  }
+}
+}  // namespace
+
+extern "C" int dss_selftest_conversions(const double* v, int64_t n, double inv, float* hi, float* split_hi,
+                                        float* split_lo, double* back, int32_t* floor_out,
+                                        const int32_t* ints, double* ints_out, void* cuda_stream) {
+  if (n < 0 || (n > 0 && (!v || !hi || !split_hi || !split_lo || !back || !floor_out || !ints || !ints_out)))
+    return DSS_ERR_ARG;
+  if (n == 0) return DSS_OK;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  k_selftest_conversions<<<(int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096), 256, 0, s>>>(
+      v, n, inv, (float)inv, hi, split_hi, split_lo, back, floor_out, ints, ints_out);
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return DSS_ERR_CUDA;
+  return DSS_OK;
 }
