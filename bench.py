@@ -94,12 +94,18 @@ ALG_BYTES = METHOD_BYTES
 KERNELS_PER_STEP = len(ALG_BYTES)
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
-# an ncu capture of the kernel on the headline workload, with the sources it
-# was built from and their hash; reported only while those files are
-# unchanged (profiles/ncu_full_c2_mixed_100k.md).
+# an ncu capture of the kernel, keyed by kernel, precision and particle count,
+# with the sources it was built from and their hash; reported only while
+# those files are unchanged (profiles/ncu_full_c2_mixed_100k.md,
+# profiles/ncu_full_c3_mixed_1m.md: the 1M capture ran with the row capacity
+# cut to 64, which changes the rows' stride, not the pairs or the work).
+_PAIR_SRC = ("dss_force.cu", "dss_internal.cuh", "dss_pair_model.cuh")
+_ENUM_SRC = ("dss_neighbour.cu", "dss_internal.cuh")
 NCU_TRAFFIC = {
-    ("k_pairs", "mixed"): (27_370_496, ("dss_force.cu", "dss_internal.cuh", "dss_pair_model.cuh"),
-                           "ed0b5b3b1d1a8cee"),
+    ("k_pairs", "mixed", 100_000): (30_699_520, _PAIR_SRC, "9557dfb1c9e0b948"),
+    ("k_enumerate", "mixed", 100_000): (7_248_640, _ENUM_SRC, "9d7575e3c5b30fd9"),
+    ("k_pairs", "mixed", 1_000_000): (300_538_112, _PAIR_SRC, "9557dfb1c9e0b948"),
+    ("k_enumerate", "mixed", 1_000_000): (110_316_544, _ENUM_SRC, "9d7575e3c5b30fd9"),
 }
 
 
@@ -349,7 +355,7 @@ def roofline(prof, nprof, c, n, precision, peaks, src, step_ms):
     d = per_kernel[dom]
     peak = float(peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
     traffic = None
-    rec = NCU_TRAFFIC.get((dom, precision))
+    rec = NCU_TRAFFIC.get((dom, precision, n))
     if rec is not None and src_hash(rec[1]) == rec[2]:
         traffic = rec[0]
     roof = {"bound": "hbm", "kernel": dom, "achieved": d["gbs"], "peak": peak, "unit": "GB/s",
