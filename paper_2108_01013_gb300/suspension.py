@@ -52,6 +52,9 @@ class _Arg:
             return
         if isinstance(v, torch.Tensor):
             tdt = {np.float64: torch.float64, np.int32: torch.int32, np.int64: torch.int64}[dtype]
+            if v.dtype == tdt and v.is_contiguous():
+                self.obj, self.ptr = v, v.data_ptr()   # as it is (the common case)
+                return
             t = v.detach()
             if t.dtype != tdt:
                 t = t.to(tdt)
