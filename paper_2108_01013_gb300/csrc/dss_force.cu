@@ -629,8 +629,6 @@ k_pairs(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ sgk, 
         ListBuf H, const float4* __restrict__ posf, void* __restrict__ own_v, int* __restrict__ bw_count,
         void* __restrict__ bw_v, double* __restrict__ spart, DevStatus* st,
         const int* __restrict__ perm) {
-  pdl_wait();
-  pdl_launch();
   using R = typename std::conditional<MIXED, float, double>::type;
   if (dev_err(st)) return;
   R* __restrict__ own = static_cast<R*>(own_v);
@@ -765,8 +763,6 @@ k_pairs_pb(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ sg
            ListBuf H, const float4* __restrict__ posf, void* __restrict__ own_v, void* __restrict__ own_s_v,
            void* __restrict__ carry_v, int* __restrict__ bw_count, void* __restrict__ bw_v,
            double* __restrict__ spart, DevStatus* st, const int* __restrict__ perm) {
-  pdl_wait();
-  pdl_launch();
   using R = typename std::conditional<MIXED, float, double>::type;
   constexpr int NV = pb_slot<PERS>();
   if (dev_err(st)) return;
@@ -910,8 +906,6 @@ __global__ void __launch_bounds__(kPairThreads)
 k_owner_stress(Geo g, const InstGeo* __restrict__ ig, StateBuf s, const void* __restrict__ own_s_v,
                const void* __restrict__ carry_v, const int* __restrict__ start, double* __restrict__ spart,
                DevStatus* st) {
-  pdl_wait();
-  pdl_launch();
   using R = typename std::conditional<MIXED, float, double>::type;
   if (dev_err(st)) return;
   const R* __restrict__ own_s = static_cast<const R*>(own_s_v);
@@ -1351,8 +1345,6 @@ k_gather(Geo g, const InstGeo* __restrict__ ig, StateBuf s, const void* __restri
          double* __restrict__ Tout, DevStatus* st, int mode, const double* __restrict__ spart,
          double* sigma, double* sigma_sum, const int* __restrict__ start, unsigned int* done_blocks,
          const void* __restrict__ carry_v, int pb_blocks, const void* __restrict__ own_s_v) {
-  pdl_wait();
-  pdl_launch();
   // An error set before this kernel (an earlier kernel of the step, or an
   // earlier step of the same dss_step call, whose successors still replay)
   // means this step is void: touch no state, since the buffer this step
@@ -1454,26 +1446,26 @@ void launch_forces_t(dss_handle* h, int stbuf, int work_list, int hist_list, int
   h->g, h->ig, h->sg, h->st[stbuf], h->lb[work_list], h->lb[hist_list], h->posf, h->own, h->own_s,    \
       h->carry, h->bw_count, h->bw_rec, h->spart, h->status, h->perm
   if (pb4)
-    launch_pdl(k_pairs_pb<true, 4, EXT, false>, pbg, kPairThreads, h->stream, DSS_PB_ARGS);
+    k_pairs_pb<true, 4, EXT, false><<<pbg, kPairThreads, 0, h->stream>>>(DSS_PB_ARGS);
   else if (pbal && mixed && pers)
-    launch_pdl(k_pairs_pb<true, 3, EXT, true>, pbg, kPairThreads, h->stream, DSS_PB_ARGS);
+    k_pairs_pb<true, 3, EXT, true><<<pbg, kPairThreads, 0, h->stream>>>(DSS_PB_ARGS);
   else if (pbal && mixed)
-    launch_pdl(k_pairs_pb<true, 3, EXT, false>, pbg, kPairThreads, h->stream, DSS_PB_ARGS);
+    k_pairs_pb<true, 3, EXT, false><<<pbg, kPairThreads, 0, h->stream>>>(DSS_PB_ARGS);
   else if (pbal && pers)
-    launch_pdl(k_pairs_pb<false, 2, EXT, true>, pbg, kPairThreads, h->stream, DSS_PB_ARGS);
+    k_pairs_pb<false, 2, EXT, true><<<pbg, kPairThreads, 0, h->stream>>>(DSS_PB_ARGS);
   else if (pbal)
-    launch_pdl(k_pairs_pb<false, 2, EXT, false>, pbg, kPairThreads, h->stream, DSS_PB_ARGS);
+    k_pairs_pb<false, 2, EXT, false><<<pbg, kPairThreads, 0, h->stream>>>(DSS_PB_ARGS);
 #undef DSS_PB_ARGS
   else if (mixed && big)
-    launch_pdl(k_pairs<true, 4, EXT>, pb, kPairThreads, h->stream,
+    k_pairs<true, 4, EXT><<<pb, kPairThreads, 0, h->stream>>>(
         h->g, h->ig, h->sg, h->st[stbuf], h->lb[work_list], h->lb[hist_list], h->posf, h->own, h->bw_count,
         h->bw_rec, h->spart, h->status, h->perm);
   else if (mixed)
-    launch_pdl(k_pairs<true, 3, EXT>, pb, kPairThreads, h->stream,
+    k_pairs<true, 3, EXT><<<pb, kPairThreads, 0, h->stream>>>(
         h->g, h->ig, h->sg, h->st[stbuf], h->lb[work_list], h->lb[hist_list], h->posf, h->own, h->bw_count,
         h->bw_rec, h->spart, h->status, h->perm);
   else
-    launch_pdl(k_pairs<false, 2, EXT>, pb, kPairThreads, h->stream,
+    k_pairs<false, 2, EXT><<<pb, kPairThreads, 0, h->stream>>>(
         h->g, h->ig, h->sg, h->st[stbuf], h->lb[work_list], h->lb[hist_list], h->posf, h->own, h->bw_count,
         h->bw_rec, h->spart, h->status, h->perm);
   prof_mark(h, 6);
@@ -1483,19 +1475,19 @@ void launch_forces_t(dss_handle* h, int stbuf, int work_list, int hist_list, int
   const void* own_s = pbal && pers ? h->own_s : nullptr;
   if (own_s) {
     if (mixed)
-      launch_pdl(k_owner_stress<true, EXT>, h->g.K * kOsParts, kPairThreads, h->stream,
+      k_owner_stress<true, EXT><<<h->g.K * kOsParts, kPairThreads, 0, h->stream>>>(
           h->g, h->ig, h->st[stbuf], own_s, carry, h->lb[work_list].start, h->spart, h->status);
     else
-      launch_pdl(k_owner_stress<false, EXT>, h->g.K * kOsParts, kPairThreads, h->stream,
+      k_owner_stress<false, EXT><<<h->g.K * kOsParts, kPairThreads, 0, h->stream>>>(
           h->g, h->ig, h->st[stbuf], own_s, carry, h->lb[work_list].start, h->spart, h->status);
   }
   if (mixed)
-    launch_pdl(k_gather<true, EXT>, gb, kThreads, h->stream, h->g, h->ig, h->st[stbuf], h->own, h->bw_count,
+    k_gather<true, EXT><<<gb, kThreads, 0, h->stream>>>(h->g, h->ig, h->st[stbuf], h->own, h->bw_count,
                                                         h->bw_rec, F_out, T_out, h->status, mode, h->spart,
                                                         h->sigma, h->sigma_sum, h->lb[work_list].start,
                                                         h->done_blocks, carry, pbb, own_s);
   else
-    launch_pdl(k_gather<false, EXT>, gb, kThreads, h->stream, h->g, h->ig, h->st[stbuf], h->own, h->bw_count,
+    k_gather<false, EXT><<<gb, kThreads, 0, h->stream>>>(h->g, h->ig, h->st[stbuf], h->own, h->bw_count,
                                                          h->bw_rec, F_out, T_out, h->status, mode, h->spart,
                                                          h->sigma, h->sigma_sum, h->lb[work_list].start,
                                                          h->done_blocks, carry, pbb, own_s);

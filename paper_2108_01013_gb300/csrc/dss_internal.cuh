@@ -6,8 +6,6 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include <utility>
-
 #include "../../include/dss.h"
 
 #define DSS_PI 3.14159265358979323846
@@ -101,31 +99,6 @@ struct InstGeo {
 // ------------------------------------------------------------------------
 // Small device helpers
 // ------------------------------------------------------------------------
-// Programmatic dependent launch (the step's kernels): a kernel launched with
-// launch_pdl may be scheduled while the kernel before it in the stream is
-// still running; pdl_wait, its first statement, returns once that kernel has
-// completed and its writes are visible, and pdl_launch lets the next kernel
-// be scheduled as soon as every block of this one runs.  Without the launch
-// attribute both are no-ops.
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-
-template <typename... KArgs, typename... Args>
-inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t stream,
-                              Args&&... args) {
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = block;
-  cfg.dynamicSmemBytes = 0;
-  cfg.stream = stream;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
-}
-
 __device__ __forceinline__ int dev_err(const DevStatus* s) {
   return *((volatile const int*)&s->w[ST_ERR]);
 }

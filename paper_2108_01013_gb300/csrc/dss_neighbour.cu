@@ -211,8 +211,6 @@ k_enumerate(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ s
             const float4* __restrict__ posf, const int* __restrict__ cellid,
             const int* __restrict__ cell_start, ListBuf L, int* __restrict__ bw_count,
             unsigned long long* scan_status, int* scan_ticket, DevStatus* st, int adv) {
-  pdl_wait();
-  pdl_launch();
   if (dev_err(st)) return;
   __shared__ int s_tile;
   if (threadIdx.x == 0) s_tile = atomicAdd(scan_ticket, 1);
@@ -287,8 +285,6 @@ k_enumerate_classes(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __rest
                     const float4* __restrict__ posf, const int* __restrict__ cellid,
                     const int* __restrict__ cell_start, ListBuf L, int* __restrict__ bw_count,
                     unsigned long long* scan_status, int* scan_ticket, DevStatus* st) {
-  pdl_wait();
-  pdl_launch();
   if (dev_err(st)) return;
   __shared__ int s_tile;
   if (threadIdx.x == 0) s_tile = atomicAdd(scan_ticket, 1);
@@ -400,11 +396,11 @@ void launch_enumerate(dss_handle* h, int stbuf, int dst_list, int adv) {
                 : medium  ? k_enumerate<false, 2, false>
                           : k_enumerate<false, 1, false>;
   if (h->g.nclass > 1)
-    launch_pdl(kc, enum_tiles_for(n), kThreads, h->stream,
+    kc<<<enum_tiles_for(n), kThreads, 0, h->stream>>>(
         h->g, h->ig, h->sg, h->st[stbuf], h->posf, h->cellid, h->cell_start, L, h->bw_count,
         h->scan_status + h->scan_tiles_max, h->scan_ticket + 1, h->status);
   else
-    launch_pdl(k1, enum_tiles_for(n), kThreads, h->stream,
+    k1<<<enum_tiles_for(n), kThreads, 0, h->stream>>>(
         h->g, h->ig, h->sg, h->st[stbuf], h->posf, h->cellid, h->cell_start, L, h->bw_count,
         h->scan_status + h->scan_tiles_max, h->scan_ticket + 1, h->status, adv);
   h->last_list = dst_list;

@@ -11,7 +11,7 @@
 
 namespace {
 
-constexpr int kThreads = 128;
+constexpr int kThreads = 256;
 
 // Predictor of Eq. 15a-b and the wrap of Eq. 16 for one particle; computed
 // once per step and stored for the gather.  In FP64 mode each product and
@@ -130,8 +130,6 @@ k_key_hist(Geo g, const InstGeo* __restrict__ ig, StepGeo* __restrict__ sg, Stat
            int* __restrict__ key, int* __restrict__ offs, int* __restrict__ cell_count,
            DevStatus* st, bool predict, unsigned long long* scan_status, int* scan_ticket,
            int scan_tiles, double* __restrict__ pred, signed char* __restrict__ xc) {
-  pdl_wait();
-  pdl_launch();
   if (dev_err(st)) return;
   // reset the look-back state of both scans of this operation (spread over
   // the grid), the counters, and set every instance's Lees-Edwards geometry
@@ -189,8 +187,6 @@ k_key_hist(Geo g, const InstGeo* __restrict__ ig, StepGeo* __restrict__ sg, Stat
 __global__ void __launch_bounds__(kThreads)
 k_scatter(int n, const int* __restrict__ key, const int* __restrict__ offs,
           const int* __restrict__ cell_start, int* __restrict__ tmp, const DevStatus* st) {
-  pdl_wait();
-  pdl_launch();
   if (dev_err(st)) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -207,8 +203,6 @@ k_rank_gather(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__
               const int* __restrict__ tmp, int* __restrict__ perm, int* __restrict__ cellid,
               float4* __restrict__ posf, DevStatus* st, bool predict,
               const double* __restrict__ pred, const signed char* __restrict__ xc) {
-  pdl_wait();
-  pdl_launch();
   if (dev_err(st)) return;
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = g.n;
@@ -318,8 +312,6 @@ __host__ __device__ constexpr int scan_pad(int q) { return q + (q >> 5); }   // 
 __global__ void __launch_bounds__(kScanThreads)
 k_scan(const int* __restrict__ in, int* __restrict__ out, int count,
        unsigned long long* status, int* ticket, DevStatus* st, int zero_in) {
-  pdl_wait();
-  pdl_launch();
   __shared__ int s_tile, s_err, s_prefix, s_agg;
   __shared__ int s_warp[kScanThreads / 32];
   __shared__ int s_v[scan_pad(kScanTile)];
@@ -400,28 +392,29 @@ int scan_tiles_for(int count) { return (count + kScanTile - 1) / kScanTile; }
 void launch_scan(dss_handle* h, const int* in, int* out, int count, int which, bool zero_in) {
   int tiles = scan_tiles_for(count);
   if (tiles < 1) tiles = 1;
-  launch_pdl(k_scan, tiles, kScanThreads, h->stream, in, out, count, h->scan_status + which * h->scan_tiles_max,
-             h->scan_ticket + which, h->status, zero_in ? 1 : 0);
+  k_scan<<<tiles, kScanThreads, 0, h->stream>>>(in, out, count,
+                                                 h->scan_status + which * h->scan_tiles_max,
+                                                 h->scan_ticket + which, h->status, zero_in ? 1 : 0);
 }
 
 void launch_sort(dss_handle* h, bool predict, int src, int dst) {
   const int n = (int)h->n;
   const int blocks = (n + kThreads - 1) / kThreads;
   prof_mark(h, 0);
-  launch_pdl(k_key_hist, blocks, kThreads, h->stream, h->g, h->ig, h->sg, h->st[src], h->key, h->offs,
+  k_key_hist<<<blocks, kThreads, 0, h->stream>>>(h->g, h->ig, h->sg, h->st[src], h->key, h->offs,
                                                  h->cell_count, h->status, predict, h->scan_status,
                                                  h->scan_ticket, h->scan_tiles_max, h->pred, h->xc);
   prof_mark(h, 1);
   launch_scan(h, h->cell_count, h->cell_start, h->g.ncell, 0, true);
   prof_mark(h, 2);
-  launch_pdl(k_scatter, blocks, kThreads, h->stream, n, h->key, h->offs, h->cell_start, h->tmp, h->status);
+  k_scatter<<<blocks, kThreads, 0, h->stream>>>(n, h->key, h->offs, h->cell_start, h->tmp, h->status);
   prof_mark(h, 3);
   if (h->g.wave)
-    launch_pdl(k_rank_gather<true>, blocks, kThreads, h->stream, h->g, h->ig, h->sg, h->st[src], h->st[dst], h->key,
+    k_rank_gather<true><<<blocks, kThreads, 0, h->stream>>>(h->g, h->ig, h->sg, h->st[src], h->st[dst], h->key,
                                                             h->cell_start, h->tmp, h->perm, h->cellid,
                                                             h->posf, h->status, predict, h->pred, h->xc);
   else
-    launch_pdl(k_rank_gather<false>, blocks, kThreads, h->stream, h->g, h->ig, h->sg, h->st[src], h->st[dst], h->key,
+    k_rank_gather<false><<<blocks, kThreads, 0, h->stream>>>(h->g, h->ig, h->sg, h->st[src], h->st[dst], h->key,
                                                              h->cell_start, h->tmp, h->perm, h->cellid,
                                                              h->posf, h->status, predict, h->pred, h->xc);
 }
