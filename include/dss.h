@@ -320,12 +320,13 @@ int dss_autotune(dss_handle *h, int32_t trial_steps, int32_t ncand, const double
  * picked by an autotuner"), timed at the current cell grid: the register
  * budget of the pair kernel (cut for 3 or 4 resident 256-thread blocks per
  * SM: 80 or 64 registers; more warps in flight against more spills) and the
- * enumeration's candidate loop (one candidate at a time, or four loaded
- * before they are tested).  Each of the 4 combinations runs 2 + trial_steps
+ * enumeration's candidate loop (one candidate at a time, or screened: four
+ * loaded ahead and rejected by one test into a bit mask, the rest decided
+ * afterwards in order).  Each of the 4 combinations runs 2 + trial_steps
  * steps from a checkpoint of the current state; the fastest is kept and the
  * state restored.  ms_per_step (host, 4 doubles, may be NULL): ms per step of
  * (3 blocks, 1), (3, 4), (4, 1), (4, 4); choice (host, 2 ints, may be NULL):
- * the kept (blocks per SM, candidates ahead).  Errors: DSS_ERR_ARG
+ * the kept (blocks per SM, candidate loop: 1 plain, 4 screened).  Errors: DSS_ERR_ARG
  * (trial_steps < 1), DSS_ERR_STATE, and any error of a trial step (the
  * built-in rule is kept then). */
 int dss_autotune_kernels(dss_handle *h, int32_t trial_steps, double *ms_per_step, int32_t *choice);

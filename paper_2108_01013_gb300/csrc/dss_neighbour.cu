@@ -91,12 +91,23 @@ __device__ __forceinline__ void enum_init(EnumCtx& e, const Geo& g, const InstGe
 // pairs within the lubrication range by an FP32 test go to the row's front
 // in visiting order, the others to its back from the end; the row is closed
 // up afterwards (close_row).  Only the order within the row changes.
-template <bool ECH, bool SPLIT>
-__device__ __forceinline__ void take_candidate(EnumCtx& e, float4 pj, int j, float px, float py, float pz) {
-  const float dx = pj.x - px, dy = pj.y - py, dz = pj.z - pz;
+// r^2 - s^2 of a candidate in FP32 on cell-local coordinates (s: the
+// pair's cutoff), the one value every decision starts from.
+template <bool ECH>
+__device__ __forceinline__ float cand_t(const EnumCtx& e, float4 pj, float px, float py, float pz, float& dx,
+                                       float& dy, float& dz) {
+  dx = pj.x - px;
+  dy = pj.y - py;
+  dz = pj.z - pz;
   float sv = fmaf(pj.w, e.sc, e.sa);
   if (ECH) sv = fmaxf(sv, pj.w + e.sa2);
-  const float t = fmaf(-sv, sv, fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
+  return fmaf(-sv, sv, fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
+}
+
+template <bool ECH, bool SPLIT>
+__device__ __forceinline__ void take_candidate(EnumCtx& e, float4 pj, int j, float px, float py, float pz) {
+  float dx, dy, dz;
+  const float t = cand_t<ECH>(e, pj, px, py, pz, dx, dy, dz);
   // nearly every candidate lies beyond the cutoff by more than the margin:
   // one test and out (the half-box image test only on boxes narrower than
   // the stencil)
@@ -138,24 +149,48 @@ __device__ __forceinline__ void close_row(EnumCtx& e) {
     for (int k = 0; k < nf; ++k) e.row[e.nnear + k] = e.row[e.nnear + gap + k];
 }
 
-// Visits the candidates [jb, je) of one stencil cell (origin displaced by
-// (cxo, cyo, czo) from the owner's cell) in order.  UNR > 1 loads UNR positions before
-// testing them (more loads in flight; pays when cells hold many particles),
-// with the same decisions in the same order, so the rows are identical.
-template <bool ECH, int UNR, bool SPLIT = false>
-__device__ __forceinline__ void scan_range(EnumCtx& e, int jb, int je, float cxo, float cyo, float czo) {
-  const float px = e.pi.x - cxo, py = e.pi.y - cyo, pz = e.pi.z - czo;
-  int j = jb;
-  if (UNR > 1) {
-    for (; j + UNR <= je; j += UNR) {
-      float4 q[UNR];
-#pragma unroll
-      for (int t = 0; t < UNR; ++t) q[t] = __ldg(e.posf + j + t);
-#pragma unroll
-      for (int t = 0; t < UNR; ++t) take_candidate<ECH, SPLIT>(e, q[t], j + t, px, py, pz);
+// SCREEN: the candidates of a range go 32 at a time through a screen first:
+// the one-test rejection alone, unrolled with four loads ahead and no branch
+// in the body, leaves a bit per candidate that may be a pair (about one in a
+// hundred on the polydisperse packings); those take the full decision
+// afterwards in ascending order, so the row is the one the plain loop
+// writes.  It pays on cells of three or more particles (1M log-uniform
+// [1, 10]: 247 -> 212 us; Table 5, radius ratio 3: 59 -> 47 us); on the
+// sparse 100k grid (1.7 per cell) the plain loop is faster (28.7 against
+// 30.7 us).
+template <bool ECH, bool SPLIT>
+__device__ __forceinline__ void scan_screened(EnumCtx& e, int jb, int je, float px, float py, float pz) {
+  for (int base = jb; base < je; base += 32) {
+    const int cnt = min(32, je - base);
+    const float4* __restrict__ q = e.posf + base;
+    unsigned m = 0u;
+#pragma unroll 4
+    for (int k = 0; k < cnt; ++k) {
+      float dx, dy, dz;
+      const float t = cand_t<ECH>(e, __ldg(q + k), px, py, pz, dx, dy, dz);
+      m |= (t > e.m2 ? 0u : 1u) << k;
+    }
+    while (m) {
+      const int k = __ffs(m) - 1;
+      m &= m - 1u;
+      take_candidate<ECH, SPLIT>(e, __ldg(q + k), base + k, px, py, pz);
     }
   }
-  for (; j < je; ++j) take_candidate<ECH, SPLIT>(e, __ldg(e.posf + j), j, px, py, pz);
+}
+
+// Visits the candidates [jb, je) of one stencil cell (origin displaced by
+// (cxo, cyo, czo) from the owner's cell) in order, plainly or (SCREEN) through
+// the screen; boxes narrower than the stencil, where every candidate takes
+// the image test, always take the plain loop.  Both make the same decisions
+// in the same order, so the rows are identical.
+template <bool ECH, bool SCREEN, bool SPLIT = false>
+__device__ __forceinline__ void scan_range(EnumCtx& e, int jb, int je, float cxo, float cyo, float czo) {
+  const float px = e.pi.x - cxo, py = e.pi.y - cyo, pz = e.pi.z - czo;
+  if (SCREEN && !e.img) {
+    scan_screened<ECH, SPLIT>(e, jb, je, px, py, pz);
+    return;
+  }
+  for (int j = jb; j < je; ++j) take_candidate<ECH, SPLIT>(e, __ldg(e.posf + j), j, px, py, pz);
 }
 
 // Row lengths, counters and the fused exclusive scan of the row lengths:
@@ -205,7 +240,7 @@ __device__ __forceinline__ void finish_rows(const Geo& g, const StateBuf& s, Lis
   }
 }
 
-template <bool ECH, int UNR, bool SPLIT>
+template <bool ECH, bool SCREEN, bool SPLIT>
 __global__ void __launch_bounds__(kThreads, 8)
 k_enumerate(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ sgk, StateBuf s,
             const float4* __restrict__ posf, const int* __restrict__ cellid,
@@ -237,17 +272,17 @@ k_enumerate(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ s
     const int xm = cx == 0 ? nx - 1 : cx - 1, xp = cx + 1 == nx ? 0 : cx + 1;
     const int zm = cz == 0 ? nz - 1 : cz - 1, zp = cz + 1 == nz ? 0 : cz + 1;
     // own cell (partners after i) and the cell x+1
-    scan_range<ECH, UNR, SPLIT>(e, i + 1, cell_start[cb + c + 1], 0.f, 0.f, 0.f);
+    scan_range<ECH, SCREEN, SPLIT>(e, i + 1, cell_start[cb + c + 1], 0.f, 0.f, 0.f);
     {
       const int q = cb + (cz * ny + cy) * nx + xp;
-      scan_range<ECH, UNR, SPLIT>(e, cell_start[q], cell_start[q + 1], I.csf[0], 0.f, 0.f);
+      scan_range<ECH, SCREEN, SPLIT>(e, cell_start[q], cell_start[q + 1], I.csf[0], 0.f, 0.f);
     }
     // layer y, z+1: three x cells
     {
       const int row = cb + (zp * ny + cy) * nx;
-      scan_range<ECH, UNR, SPLIT>(e, cell_start[row + xm], cell_start[row + xm + 1], -I.csf[0], 0.f, I.csf[2]);
-      scan_range<ECH, UNR, SPLIT>(e, cell_start[row + cx], cell_start[row + cx + 1], 0.f, 0.f, I.csf[2]);
-      scan_range<ECH, UNR, SPLIT>(e, cell_start[row + xp], cell_start[row + xp + 1], I.csf[0], 0.f, I.csf[2]);
+      scan_range<ECH, SCREEN, SPLIT>(e, cell_start[row + xm], cell_start[row + xm + 1], -I.csf[0], 0.f, I.csf[2]);
+      scan_range<ECH, SCREEN, SPLIT>(e, cell_start[row + cx], cell_start[row + cx + 1], 0.f, 0.f, I.csf[2]);
+      scan_range<ECH, SCREEN, SPLIT>(e, cell_start[row + xp], cell_start[row + xp + 1], I.csf[0], 0.f, I.csf[2]);
     }
     // layer y+1: 3x3 cells, or across y = L_y the 4 x cells covering the
     // image range shifted by the Lees-Edwards offset
@@ -262,7 +297,7 @@ k_enumerate(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __restrict__ s
         const int q = cb + (qz * ny + qy) * nx + qx;
         float cxo, cyo, czo;
         stencil_shift(I, ox, 1, oz, le ? 1 : 0, fsh, offr, cxo, cyo, czo);
-        scan_range<ECH, UNR, SPLIT>(e, cell_start[q], cell_start[q + 1], cxo, cyo, czo);
+        scan_range<ECH, SCREEN, SPLIT>(e, cell_start[q], cell_start[q + 1], cxo, cyo, czo);
       }
     }
   }
@@ -308,7 +343,7 @@ k_enumerate_classes(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __rest
     const int c = (cellid[i] - I.cell_base) % layer;
     const int cx = c % nx, cy = (c / nx) % ny, cz = c / (nx * ny);
     // own bin, partners after i
-    scan_range<ECH, 1>(e, i + 1, cell_start[cellid[i] + 1], 0.f, 0.f, 0.f);
+    scan_range<ECH, false>(e, i + 1, cell_start[cellid[i] + 1], 0.f, 0.f, 0.f);
     for (int c2 = cls; c2 >= 0; --c2) {
       const int R = g.rtab[cls][c2];
       const bool half = c2 == cls;
@@ -354,7 +389,7 @@ k_enumerate_classes(Geo g, const InstGeo* __restrict__ ig, const StepGeo* __rest
                   } while (j >= kend);
                   stencil_shift(I, ox + k, oy, oz, le, fsh, offr, cxo, cyo, czo);
                 }
-                scan_range<ECH, 1>(e, j, j + 1, cxo, cyo, czo);
+                scan_range<ECH, false>(e, j, j + 1, cxo, cyo, czo);
               }
             }
             ox += m;
@@ -378,23 +413,21 @@ void launch_enumerate(dss_handle* h, int stbuf, int dst_list, int adv) {
   // by a maximum, which only that case needs in the candidate test
   const bool ech = h->g.de > 0.0 && h->g.mode == 0;
   auto kc = ech ? k_enumerate_classes<true> : k_enumerate_classes<false>;
-  // cells holding many particles (long ranges, large radius ratios) take
-  // the candidate loop with four loads in flight
+  // cells holding many particles (long ranges, large radius ratios)
   const bool crowded = h->tune_enum_unr ? h->tune_enum_unr == 4 : h->n >= 8 * (int64_t)h->g.ncell;
   // with electro-chemical forces over crowded cells (long ranges) most
   // listed pairs lie beyond the lubrication range: rows put the others
   // first, so that the pair kernel's warps meet runs of pairs without
   // lubrication (short rows gain less than the reordering costs)
   const bool split = h->g.de > 0.0 && crowded;
-  // cells of three to eight particles on average (the 1M log-uniform
-  // packing: 7.5) take two candidates ahead (1M: 273 -> 246 us; with under
-  // two per cell, as at 100k, the plain loop is faster)
-  const bool medium = !h->tune_enum_unr && h->n >= 3 * (int64_t)h->g.ncell;
-  auto k1 = ech ? (split ? k_enumerate<true, 4, true> : k_enumerate<true, 1, false>)
-                : split   ? k_enumerate<false, 4, true>
-                : crowded ? k_enumerate<false, 4, false>
-                : medium  ? k_enumerate<false, 2, false>
-                          : k_enumerate<false, 1, false>;
+  // cells of three or more particles on average (the 1M log-uniform
+  // packing: 7.5; Table 5: 24) take the screened candidate loop; under two
+  // per cell (the 100k packing: 1.7) the plain loop is faster
+  const bool screen = crowded || (!h->tune_enum_unr && h->n >= 3 * (int64_t)h->g.ncell);
+  auto k1 = ech ? (split ? k_enumerate<true, true, true> : k_enumerate<true, false, false>)
+                : split  ? k_enumerate<false, true, true>
+                : screen ? k_enumerate<false, true, false>
+                         : k_enumerate<false, false, false>;
   if (h->g.nclass > 1)
     kc<<<enum_tiles_for(n), kThreads, 0, h->stream>>>(
         h->g, h->ig, h->sg, h->st[stbuf], h->posf, h->cellid, h->cell_start, L, h->bw_count,

@@ -141,7 +141,7 @@ def test_multi_step_graphs_repeat_single_steps(env, precision):
 
 def test_kernel_shape_autotune_keeps_the_trajectory(env):
     """dss_autotune_kernels times the four kernel shapes (pair-kernel blocks
-    per SM 3 or 4, enumeration candidates ahead 1 or 4), keeps the fastest
+    per SM 3 or 4, enumeration candidate loop plain or screened), keeps the fastest
     and restores the state; the shapes change neither the pairs nor the
     arithmetic, so the run continues bit for bit as an untuned one."""
     g = env["synth"].small(3000, 0.52, 48)
