@@ -645,7 +645,7 @@ struct dss_handle {
   bool multi_ok[4];
   // kernel shapes chosen by dss_autotune_kernels (0: the built-in rule):
   // resident pair blocks per SM the register budget is cut for (3 or 4), and
-  // the enumeration's candidate loop (1: plain, 4: screened, four loads ahead)
+  // candidates loaded ahead in the enumeration's loop (1 or 4)
   int tune_pairs_minb;
   int tune_enum_unr;
   int64_t bytes;
