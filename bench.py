@@ -96,16 +96,18 @@ KERNELS_PER_STEP = len(ALG_BYTES)
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
 # an ncu capture of the kernel, keyed by kernel, precision and particle count,
 # with the sources it was built from and their hash; reported only while
-# those files are unchanged (profiles/ncu_full_c2_mixed_100k.md,
-# profiles/ncu_full_c3_mixed_1m.md: the 1M capture ran with the row capacity
-# cut to 64, which changes the rows' stride, not the pairs or the work).
+# those files are unchanged (pair kernel: profiles/ncu_full_c2_mixed_100k.md,
+# profiles/ncu_full_c3_mixed_1m.md; enumeration:
+# profiles/ncu_enumerate_screened_c3_mixed_1m.md; the 1M captures ran with the
+# row capacity cut to 64, which changes the rows' stride, not the pairs or the
+# work).
 _PAIR_SRC = ("dss_force.cu", "dss_internal.cuh", "dss_pair_model.cuh")
 _ENUM_SRC = ("dss_neighbour.cu", "dss_internal.cuh")
 NCU_TRAFFIC = {
     ("k_pairs", "mixed", 100_000): (30_699_520, _PAIR_SRC, "9557dfb1c9e0b948"),
-    ("k_enumerate", "mixed", 100_000): (7_248_640, _ENUM_SRC, "9d7575e3c5b30fd9"),
+    ("k_enumerate", "mixed", 100_000): (7_125_760, _ENUM_SRC, "614103effa34d4d4"),
     ("k_pairs", "mixed", 1_000_000): (300_538_112, _PAIR_SRC, "9557dfb1c9e0b948"),
-    ("k_enumerate", "mixed", 1_000_000): (110_316_544, _ENUM_SRC, "9d7575e3c5b30fd9"),
+    ("k_enumerate", "mixed", 1_000_000): (110_382_848, _ENUM_SRC, "614103effa34d4d4"),
 }
 
 
