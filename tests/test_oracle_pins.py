@@ -316,6 +316,41 @@ def test_lubrication_antisymmetric_swap_and_dissipative(orc):
                 np.testing.assert_allclose(u_, v_, atol=1e-11 * sc)
 
 
+def _lub_resistance(orc, p, r, ai, aj):
+    """The 12x12 matrix R with (F_i, F_j, T_i, T_j) = -R (U_i, U_j, W_i, W_j)
+    at rest in a quiescent fluid, column by column from unit motions."""
+    R = np.zeros((12, 12))
+    for k in range(12):
+        V = np.zeros(12)
+        V[k] = 1.0
+        out = orc.lubrication(p, r, ai, aj, V[0:3], V[3:6], V[6:9], V[9:12])
+        R[:, k] = -np.concatenate(out)
+    return R
+
+
+@pytest.mark.parametrize("ratio", [1.0, 1.4, 3.0, 10.0, 0.37])
+def test_lubrication_resistance_is_reciprocal(orc, ratio):
+    """Lorentz reciprocal theorem: the resistance matrix of the pair (forces
+    and torques on both spheres against both spheres' velocities and
+    angular velocities) is symmetric, and positive semi-definite.  Symmetry
+    ties each cross coefficient of App. A between i and j (X^A, Y^A, Y^B,
+    Y^C) at size ratio alpha to the same formula at 1/alpha, so a wrong power
+    of alpha, a dropped term, a sign or an exchanged argument in one of them
+    breaks it at the intermediate ratios where the paper prints no value."""
+    rng = np.random.default_rng(int(ratio * 100))
+    p = orc.make_params([100] * 3, shear_rate=0.0)
+    for _ in range(6):
+        ai = rng.uniform(0.5, 3.0)
+        aj = ratio * ai
+        n = unit(rng.normal(size=3))
+        ds = rng.uniform(1e-4, 0.04)          # normalised gap inside the cutoff
+        r = n * (ai + aj) * (1 + ds / 2)
+        R = _lub_resistance(orc, p, r, ai, aj)
+        scale = np.abs(R).max()
+        np.testing.assert_allclose(R, R.T, rtol=0, atol=1e-12 * scale)
+        assert np.linalg.eigvalsh(0.5 * (R + R.T)).min() >= -1e-12 * scale
+
+
 def test_overlap_clamps_gap(orc):
     p = orc.make_params([100] * 3, shear_rate=0.0)
     n = unit([1, 1, 0])
