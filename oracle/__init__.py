@@ -27,7 +27,9 @@ Parity status of each function (see the pins in ``tests/test_oracle_*.py``):
                                     squeeze law for equal spheres, zero
                                     force/torque for rigid motion of the pair
                                     and for particles at rest in a linear
-                                    flow, antisymmetry, dissipation >= 0).
+                                    flow, antisymmetry, dissipation >= 0,
+                                    a symmetric resistance matrix by the
+                                    reciprocal theorem).
                                     The absolute values of the log-order
                                     coefficients for unequal radii beyond
                                     these invariants are parity unpinned.
