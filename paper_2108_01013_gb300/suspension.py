@@ -284,9 +284,10 @@ class Suspension:
         return cs.value, dict(zip(f.tolist(), ms.tolist()))
 
     def autotune_kernels(self, trial_steps: int = 20):
-        """Time the kernel shapes (pair-kernel blocks per SM 3 or 4, candidates
-        ahead in the enumeration 1 or 4), keep the fastest, restore the
-        state.  Returns ((blocks, ahead), {(blocks, ahead): ms/step})."""
+        """Time the kernel shapes (pair-kernel blocks per SM 3 or 4; the
+        enumeration's candidate loop 1: plain, 4: screened with four loads
+        ahead), keep the fastest, restore the state.  Returns
+        ((blocks, loop), {(blocks, loop): ms/step})."""
         ms = np.zeros(4)
         ch = np.zeros(2, dtype=np.int32)
         dp = ctypes.POINTER(c_double)
